@@ -1,0 +1,171 @@
+/*
+ * mra.h -- C ABI of the GB300 multi-resolution approximation (M-RA) library.
+ *
+ * The library evaluates, on one CUDA GPU, the M-RA of a Gaussian process
+ * (Katzfuss, "A multi-resolution approximation for massive spatial datasets",
+ * JASA 2017): its log-likelihood (Sec. 3.3), the gradient of that
+ * log-likelihood in the covariance parameters, and kriging predictions with
+ * variances (Sec. 3.4, Prop. 2).  The problem is stated as in the paper:
+ *
+ *   - n observation locations S in a 2-D bounding box and data y (Sec. 2.1);
+ *   - a covariance function C0 known up to theta = (sigma2, range) (Sec. 2.1),
+ *     exponential or Matern-1.5 (Eq. mat15), optionally with the
+ *     nonstationary variance sigma2 * sqrt(g(s1) g(s2)), g(s) = 1 + 0.5 sin(4 pi x);
+ *   - M levels of a recursive partition with J = 4 children per region
+ *     (midpoint quadtree, child j = b_x + 2 b_y, half-open cells), Sec. 2.2;
+ *   - r knots per region on a cell-centred gx x gy grid (gx = smallest divisor
+ *     of r with gx^2 >= r), leaves using their observations as knots (Sec. 2.2);
+ *   - measurement-error variance tau2 added to the leaf covariance (Sec. 4.3).
+ *
+ * Conventions for every entry point:
+ *   - All floating point is IEEE binary64 (double).
+ *   - Return value: MRA_OK (0) or one of the MRA_ERR_* codes below; the text of
+ *     the last error of the calling thread is available from mra_last_error().
+ *     No entry point throws or aborts.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the handle's device.  Unless stated otherwise, inputs are
+ *     read during the call only and stay owned by the caller.
+ *   - A handle owns all device memory it allocates and is used by one host
+ *     thread at a time.  All its kernels run on its stream (default: the legacy
+ *     default stream; see mra_set_stream).  Entry points that return results in
+ *     host memory synchronise that stream before returning.
+ */
+#ifndef MRA_H
+#define MRA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MRA_OK          0
+#define MRA_ERR_ARG     1   /* invalid argument: sizes, config, a location outside bbox */
+#define MRA_ERR_OOM     2   /* device allocation failed */
+#define MRA_ERR_CUDA    3   /* a CUDA runtime call or kernel launch failed */
+#define MRA_ERR_NOT_PD  4   /* a matrix the method needs positive definite is not
+                               (non-positive Cholesky pivot); level/region in the text */
+#define MRA_ERR_STATE   5   /* call order: e.g. mra_predict before any mra_loglik */
+#define MRA_ERR_LIMIT   6   /* a leaf holds more observations than MRA_MAX_LEAF */
+
+/* ---- limits ------------------------------------------------------------ */
+#define MRA_MAX_R       64  /* knots per internal region */
+#define MRA_MAX_M       12  /* levels */
+#define MRA_MAX_LEAF    128 /* observations per leaf (the leaf kernel keeps the
+                               leaf covariance in shared memory) */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define MRA_COV_EXP       0 /* C0 = sigma2 exp(-h / range) */
+#define MRA_COV_MATERN15  1 /* C0 = sigma2 (1 + sqrt3 h / range) exp(-sqrt3 h / range), Eq. mat15 */
+
+#define MRA_PREC_FP64     0 /* every step in binary64 */
+
+#define MRA_HOST          0 /* pointer argument is host memory */
+#define MRA_DEVICE        1 /* pointer argument is device memory */
+
+/* Problem shape (Sec. 2.2).  Plain data, owned by the caller, copied by mra_build. */
+typedef struct {
+    int    M;           /* levels; leaves are the 4^M regions of level M; 0 <= M <= MRA_MAX_M */
+    int    J;           /* children per region; must be 4 (2-D midpoint quadtree) */
+    int    r;           /* knots per internal region, 1 <= r <= MRA_MAX_R */
+    int    cov_family;  /* MRA_COV_EXP or MRA_COV_MATERN15 */
+    int    nonstat;     /* 1: variance sigma2 * sqrt(g(s1) g(s2)), g(s) = 1 + 0.5 sin(4 pi x) */
+    int    precision;   /* MRA_PREC_FP64 */
+    double bbox[4];     /* x0, x1, y0, y1 of the domain; every location must lie inside */
+} mra_config;
+
+/* Covariance parameters theta and the measurement-error variance (Sec. 2.1, 4.3). */
+typedef struct {
+    double sigma2;      /* > 0 */
+    double range;       /* kappa > 0 */
+    double tau2;        /* >= 0 */
+} mra_params;
+
+typedef struct mra_handle mra_handle;
+
+/*
+ * mra_build -- partition the domain and bin the observations (Sec. 2.2).
+ *   cfg    : problem shape (host).
+ *   locs   : n x 2 row-major (x, y) locations, host or device per `where`.
+ *   y      : n observations, same memory space as locs.
+ *   n      : number of observations, n >= 1.
+ *   where  : MRA_HOST or MRA_DEVICE.
+ *   out    : receives a new handle (host pointer to a handle pointer).
+ * Allocates the handle's device memory (about 8 n M r + 4^M M^2 r^2 doubles for
+ * the factors of all levels), copies and sorts the observations by leaf on the
+ * device (stable within a leaf).  Errors: MRA_ERR_ARG (bad config, n < 1, a
+ * location outside bbox), MRA_ERR_LIMIT (a leaf above MRA_MAX_LEAF: raise M),
+ * MRA_ERR_OOM, MRA_ERR_CUDA.  On error *out is NULL and nothing is leaked.
+ */
+int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_t n,
+              int where, mra_handle** out);
+
+/*
+ * mra_set_data -- replace the observations y of a built handle (same n, same
+ * order as given to mra_build; host or device per `where`).  The partition is
+ * kept.  Errors: MRA_ERR_ARG, MRA_ERR_CUDA.
+ */
+int mra_set_data(mra_handle* h, const double* y, int where);
+
+/*
+ * mra_loglik -- the M-RA log-likelihood at theta (Sec. 3.1-3.3):
+ *   loglik = -(d + u)/2 - (n/2) log(2 pi),  -2 log L_M(theta) = d + u.
+ * Runs the prior pass (Eq. priorw) top-down and the posterior pass (Eqs.
+ * posterior, mainquantities, helpquantities) bottom-up; keeps the posterior
+ * factors in the handle for mra_predict at the same theta.
+ *   theta       : host pointer to one mra_params.
+ *   loglik_out  : host pointer to one double.
+ * Errors: MRA_ERR_ARG (theta out of range), MRA_ERR_NOT_PD, MRA_ERR_CUDA.
+ */
+int mra_loglik(mra_handle* h, const mra_params* theta, double* loglik_out);
+
+/*
+ * mra_predict -- marginal posterior predictive mean and variance of the
+ * process y (not of the noisy data, Sec. 4.3) at np locations (Sec. 3.4,
+ * Prop. 2, Eq. bfrecursion).  Uses the factors of the last mra_loglik, which
+ * must have been called with the same theta (else MRA_ERR_STATE).
+ *   plocs    : np x 2 row-major locations inside bbox, host or device per `where`.
+ *   mean_out, var_out : np doubles each, same memory space as plocs, caller-owned.
+ * Errors: MRA_ERR_ARG, MRA_ERR_STATE, MRA_ERR_LIMIT (more than 4096 prediction
+ * points in one leaf), MRA_ERR_CUDA.
+ */
+int mra_predict(mra_handle* h, const mra_params* theta, const double* plocs, int64_t np,
+                int where, double* mean_out, double* var_out);
+
+/*
+ * mra_region_terms -- the per-region log-determinant d_R and quadratic form
+ * u_R (Sec. 3.3) of every region of `level` (0..M) from the last mra_loglik.
+ * d_R = log|Sigma_R| and u_R = y_R' Sigma_R^{-1} y_R of the data in region R
+ * given the weights of coarser levels.  d_out, u_out: host arrays of 4^level.
+ * Errors: MRA_ERR_ARG, MRA_ERR_STATE, MRA_ERR_CUDA.
+ */
+int mra_region_terms(mra_handle* h, int level, double* d_out, double* u_out);
+
+/*
+ * mra_leaf_offsets -- the leaf partition of the observations: off_out (host,
+ * 4^M + 1 int64) receives the start of every leaf in leaf order, perm_out
+ * (host, n int64, may be NULL) the original index of every sorted observation.
+ */
+int mra_leaf_offsets(mra_handle* h, int64_t* off_out, int64_t* perm_out);
+
+/*
+ * mra_set_stream -- run the handle's kernels on `stream` (a cudaStream_t of the
+ * handle's device, passed as void*; NULL = legacy default stream).
+ */
+int mra_set_stream(mra_handle* h, void* stream);
+
+/* mra_free -- release the handle and its device memory; NULL is a no-op. */
+void mra_free(mra_handle* h);
+
+/* Text of the calling thread's last error ("" if none).  Valid until the next call. */
+const char* mra_last_error(void);
+
+/* Kernel launches issued by the calling thread since the last reset (reset=1 clears). */
+int64_t mra_launch_count(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MRA_H */

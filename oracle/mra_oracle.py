@@ -133,7 +133,7 @@ def locate(pts, tree_boxes, J, M, dim):
     pts = np.asarray(pts, dtype=np.float64).reshape(-1, dim)
     idx = np.zeros(pts.shape[0], dtype=np.int64)
     for m in range(M):
-        b = np.array([tree_boxes[m][i] for i in idx]).reshape(pts.shape[0], -1)
+        b = np.asarray(tree_boxes[m], dtype=np.float64).reshape(J ** m, -1)[idx]
         idx = J * idx + _child_index(pts, b, J, dim)
     return idx
 
@@ -143,11 +143,7 @@ def grid_knots(box, r, dim):
     if dim == 1:
         x0, x1 = box
         return (x0 + (np.arange(r) + 0.5) * (x1 - x0) / r).reshape(r, 1)
-    gx = int(round(math.sqrt(r)))
-    if gx * gx != r:
-        gx = 1 << ((int(r).bit_length()) // 2 + ((int(r).bit_length() - 1) % 2 == 1))
-        while r % gx:
-            gx //= 2
+    gx = next(g for g in range(1, r + 1) if r % g == 0 and g * g >= r)  # 8x4 for r = 32
     gy = r // gx
     x0, x1, y0, y1 = box
     xs = x0 + (np.arange(gx) + 0.5) * (x1 - x0) / gx
@@ -181,7 +177,9 @@ def build_tree(locs, M, J=4, r=16, bbox=None, knots_fn=None):
                       if knots_fn is not None else grid_knots(b, r, dim))
         knots.append(km)
     leaf_of = locate(locs, boxes, J, M, dim)
-    obs = [np.flatnonzero(leaf_of == i) for i in range(J ** M)]
+    order = np.argsort(leaf_of, kind="stable")         # original order within a leaf
+    cuts = np.searchsorted(leaf_of[order], np.arange(J ** M + 1))
+    obs = [order[cuts[i]:cuts[i + 1]] for i in range(J ** M)]
     return Tree(dim, J, M, boxes, knots, leaf_of, obs)
 
 

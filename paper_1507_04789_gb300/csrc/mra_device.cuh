@@ -1,0 +1,229 @@
+// mra_device.cuh -- device building blocks shared by the M-RA kernels.
+//
+// FP64 tile arithmetic for one CTA of NT threads: covariance tiles (Sec. 2.1,
+// Eq. mat15), region boxes and knots (Sec. 2.2), a register-blocked tile
+// product staged through shared memory, and in-shared-memory Cholesky and
+// triangular inversion.  On GB300 the FP64 pipe retires 2 DFMA per clock per
+// SM, so every routine here is written to keep DFMA lanes busy with useful
+// work; shared-memory bandwidth is never the limit.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mra {
+
+constexpr int NT = 256;          // threads per CTA for every kernel
+constexpr int KC = 32;           // k-chunk of the staged tile product
+constexpr int MAX_R_DEV = 64;    // largest r (knots per internal region)
+constexpr double SQRT3 = 1.7320508075688772935;
+constexpr double PI = 3.141592653589793238463;
+
+// ---- error status (device) ------------------------------------------------
+// status[0] = first error code, status[1] = level, status[2] = region
+enum : int { ST_OK = 0, ST_NOT_PD = 4, ST_LIMIT = 6, ST_ARG = 1 };
+
+__device__ __forceinline__ void flag_error(int* status, int code, int level, long region) {
+  if (atomicCAS(status, 0, code) == 0) {
+    status[1] = level;
+    status[2] = (int)region;
+  }
+}
+
+// ---- covariance function C0 (Sec. 2.1; Eq. mat15; nonstationary variance) --
+struct Cov {
+  double sigma2, kappa;
+  int family;   // 0 exponential, 1 Matern-1.5
+  int nonstat;
+};
+
+__device__ __forceinline__ double gvar(double x) { return 1.0 + 0.5 * sin(4.0 * PI * x); }
+
+__device__ __forceinline__ double cov0(const Cov& c, double x1, double y1, double x2, double y2) {
+  double dx = x1 - x2, dy = y1 - y2;
+  double h = sqrt(dx * dx + dy * dy) / c.kappa;
+  double rho;
+  if (c.family == 0) {
+    rho = exp(-h);
+  } else {
+    double a = SQRT3 * h;
+    rho = (1.0 + a) * exp(-a);
+  }
+  double v = c.sigma2 * rho;
+  if (c.nonstat) v *= sqrt(gvar(x1) * gvar(x2));
+  return v;
+}
+
+// ---- partition and knots (Sec. 2.2) -----------------------------------------
+// Region i of level m: child digits j_t = bits (2t+1, 2t) of i counted from the
+// top level, b_x = j & 1, b_y = j >> 1; boxes are halved at their midpoint.
+struct Box { double x0, x1, y0, y1; };
+
+__device__ __forceinline__ Box region_box(const double* bbox, int m, long i) {
+  Box b{bbox[0], bbox[1], bbox[2], bbox[3]};
+  for (int t = 0; t < m; ++t) {
+    int j = (int)((i >> (2 * (m - 1 - t))) & 3);
+    double xm = 0.5 * (b.x0 + b.x1), ym = 0.5 * (b.y0 + b.y1);
+    if (j & 1) b.x0 = xm; else b.x1 = xm;
+    if (j & 2) b.y0 = ym; else b.y1 = ym;
+  }
+  return b;
+}
+
+// Knot q = a + gx * b of a gx x gy cell-centred grid in box.
+__device__ __forceinline__ void knot_xy(const Box& b, int gx, int gy, int q, double& x, double& y) {
+  int a = q % gx, c = q / gx;
+  x = b.x0 + ((a + 0.5) * (b.x1 - b.x0)) / gx;
+  y = b.y0 + ((c + 0.5) * (b.y1 - b.y0)) / gy;
+}
+
+// Fill sx/sy (shared) with the r knots of region (m, i).
+__device__ __forceinline__ void load_knots(const double* bbox, int m, long i, int gx, int gy,
+                                           double* sx, double* sy) {
+  Box b = region_box(bbox, m, i);
+  for (int q = threadIdx.x; q < gx * gy; q += NT) knot_xy(b, gx, gy, q, sx[q], sy[q]);
+}
+
+// ---- register-blocked tile product ------------------------------------------
+// acc(i, j) += sum_k A(i, k) * B(j, k) for i < na, j < nb (both <= TILE).
+// A(i, k) = A[i * sai + k * sak] and B(j, k) = B[j * sbj + k * sbk]: either
+// operand may be row-major (sak = 1) or k-major (sai = 1).  Operands are staged
+// k-major through shared memory in chunks of KC; the 16 x 16 thread grid gives
+// every thread an RM x RM block of the TILE x TILE output (RM = TILE / 16).
+template <int TILE>
+struct TileAcc {
+  static constexpr int RM = TILE / 16;
+  double v[RM][RM];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int a = 0; a < RM; ++a)
+#pragma unroll
+      for (int b = 0; b < RM; ++b) v[a][b] = 0.0;
+  }
+  __device__ __forceinline__ int row(int a) const { return (threadIdx.x >> 4) * RM + a; }
+  __device__ __forceinline__ int col(int b) const { return (threadIdx.x & 15) * RM + b; }
+};
+
+template <int TILE>
+constexpr int tile_smem_doubles() { return 2 * KC * (TILE + 2); }
+
+template <int TILE>
+__device__ __forceinline__ void stage(double* s, const double* X, long sxi, long sxk, int nx,
+                                      int k0, int kn) {
+  constexpr int LD = TILE + 2;
+  if (sxk == 1) {          // row-major source: threads along k for coalescing
+    for (int t = threadIdx.x; t < TILE * KC; t += NT) {
+      int i = t / KC, k = t - i * KC;
+      s[k * LD + i] = (i < nx && k < kn) ? X[i * sxi + (long)(k0 + k)] : 0.0;
+    }
+  } else {                 // k-major source: threads along i
+    for (int t = threadIdx.x; t < TILE * KC; t += NT) {
+      int k = t / TILE, i = t - k * TILE;
+      s[k * LD + i] = (i < nx && k < kn) ? X[(long)(k0 + k) * sxk + i * sxi] : 0.0;
+    }
+  }
+}
+
+template <int TILE>
+__device__ void tile_mma(TileAcc<TILE>& acc, const double* A, long sai, long sak, int na,
+                         const double* B, long sbj, long sbk, int nb, int K, double* smem) {
+  constexpr int LD = TILE + 2;
+  constexpr int RM = TILE / 16;
+  double* sA = smem;
+  double* sB = smem + KC * LD;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    int kn = min(KC, K - k0);
+    __syncthreads();
+    stage<TILE>(sA, A, sai, sak, na, k0, kn);
+    stage<TILE>(sB, B, sbj, sbk, nb, k0, kn);
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < kn; ++k) {
+      double a[RM], b[RM];
+#pragma unroll
+      for (int q = 0; q < RM; ++q) {
+        a[q] = sA[k * LD + ty * RM + q];
+        b[q] = sB[k * LD + tx * RM + q];
+      }
+#pragma unroll
+      for (int p = 0; p < RM; ++p)
+#pragma unroll
+        for (int q = 0; q < RM; ++q) acc.v[p][q] = fma(a[p], b[q], acc.v[p][q]);
+    }
+  }
+  __syncthreads();
+}
+
+// ---- factorisations in shared memory ----------------------------------------
+// Lower Cholesky factor in place (A = L L'); the strict upper triangle is set
+// to zero.  A non-positive (or NaN) pivot sets *bad and is replaced by 1 so
+// the factorisation stays finite.  Returns nothing; ends with __syncthreads.
+__device__ inline void chol_smem(double* A, int n, int lda, int* bad) {
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    double d = A[j * lda + j];
+    bool ok = d > 0.0;
+    double s = ok ? sqrt(d) : 1.0;
+    double inv = 1.0 / s;
+    if (!ok && threadIdx.x == 0) *bad = 1;
+    for (int i = j + 1 + threadIdx.x; i < n; i += NT) A[i * lda + j] *= inv;
+    __syncthreads();
+    int m = n - j - 1;
+    for (int t = threadIdx.x; t < m * m; t += NT) {
+      int ii = t / m, kk = t - ii * m;
+      if (kk <= ii) {
+        int i = j + 1 + ii, k = j + 1 + kk;
+        A[i * lda + k] = fma(-A[i * lda + j], A[k * lda + j], A[i * lda + k]);
+      }
+    }
+    if (threadIdx.x == 0) A[j * lda + j] = s;
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < n * n; t += NT) {
+    int i = t / n, k = t - i * n;
+    if (k > i) A[i * lda + k] = 0.0;
+  }
+  __syncthreads();
+}
+
+// Lower-triangular L in place -> L^{-1} (column sweep from the last column,
+// as in LAPACK's unblocked trti2).  tmp: n doubles of shared scratch.
+__device__ inline void trinv_smem(double* A, int n, int lda, double* tmp) {
+  __syncthreads();
+  for (int j = n - 1; j >= 0; --j) {
+    double ajj = 1.0 / A[j * lda + j];
+    for (int i = j + 1 + threadIdx.x; i < n; i += NT) tmp[i] = A[i * lda + j];
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < n; i += NT) {
+      double s = 0.0;
+      for (int k = j + 1; k <= i; ++k) s = fma(A[i * lda + k], tmp[k], s);
+      A[i * lda + j] = -ajj * s;
+    }
+    if (threadIdx.x == 0) A[j * lda + j] = ajj;
+    __syncthreads();
+  }
+}
+
+// ---- reductions --------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the CTA; every thread gets the result.  red: 32 doubles of shared.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < NT / 32; ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// Lower-tile index of block (k, l), k >= l, in a packed block-lower store.
+__host__ __device__ __forceinline__ int tri_index(int k, int l) { return k * (k + 1) / 2 + l; }
+
+}  // namespace mra

@@ -1,0 +1,61 @@
+// mra_kernels.cuh -- device-side state layout and kernel declarations.
+//
+// The GPU path works with the whitened form of the M-RA.  Along the ancestor
+// chain R_0, ..., R_m of a region, the prior recursion of Eq. (priorw) is the
+// block Cholesky factorisation of the chain covariance C0(Q_chain, Q_chain):
+// with K_{R_l}^{-1} = W^l_{R_l} = L_l L_l', the blocks V^l_R = W^l_R L_l^{-T}
+// satisfy W^k_R K_{R_k} W^k_{R_l}' = V^k_R V^k_{R_l}', so
+//     V^l_R = (C0(Q_R, Q_{R_l}) - sum_{k<l} V^k_R V^k_{R_l}') L_l^{-T},
+//     W^m_R = C0(Q_R, Q_R) - sum_{k<m} V^k_R V^k_R' = L_m L_m'.
+// Basis weights are whitened, xi_l = L_l' eta_l ~ N(0, I), so B^l eta_l =
+// V^l xi_l at the leaves, and the posterior quantities of Sec. 3.2 become
+//     Ahat^{k,l} = L_k^{-1} A^{k,l} L_l^{-T},  omegahat^k = L_k^{-1} omega^k,
+//     K~^{-1} = L_m (I + Ahat^{m,m}) L_m',
+// so log|K~^{-1}| - log|K^{-1}| = log|I + Ahat^{m,m}| and
+// omega' K~ omega = |Lt^{-1} omegahat^m|^2 with Lt Lt' = I + Ahat^{m,m}.
+// The Sherman-Morrison-Woodbury updates of Eq. (helpquantities) keep their form:
+//     Atilde^{k,l} = Ahat^{k,l} - G^k' G^l,  G^l = Lt^{-1} Ahat^{m,l}.
+// The d and u of every region (Sec. 3.3) are basis-independent and equal the
+// paper's.  I + Ahat has all eigenvalues >= 1, which keeps its Cholesky factor
+// well conditioned.
+#pragma once
+#include "mra_device.cuh"
+
+namespace mra {
+
+constexpr int MAXL = 13;   // levels 0..12
+
+// Pointers to the per-level state of one handle (passed to kernels by value).
+struct LevelState {
+  // prior, internal levels m < M
+  double* V[MAXL];    // 4^m x r x (m r): [V^0_R .. V^{m-1}_R] per region, row-major
+  double* Li[MAXL];   // 4^m x r x r: L_R^{-1} (lower, zero above the diagonal)
+  // posterior, internal levels m < M
+  double* Acc[MAXL];  // 4^m x T_m x r x r, T_m = (m+1)(m+2)/2 packed lower blocks of Ahat
+  double* Om[MAXL];   // 4^m x (m+1) x r: omegahat^k
+  double* Lt[MAXL];   // 4^m x r x r: Lt^{-1}, Lt Lt' = I + Ahat^{m,m}
+  double* G[MAXL];    // 4^m x r x (m r): [G^0 .. G^{m-1}] = Lt^{-1} [Ahat^{m,0} .. Ahat^{m,m-1}]
+  double* gv[MAXL];   // 4^m x r: g = Lt^{-1} omegahat^m
+  double* dd[MAXL];   // 4^m: d_R (Sec. 3.3)
+  double* uu[MAXL];   // 4^m: u_R
+};
+
+struct LeafState {
+  const int64_t* off;     // 4^M + 1 leaf offsets into the sorted observations
+  const int64_t* sq_off;  // 4^M + 1 prefix sums of n_F^2
+  const double* xs;       // sorted x
+  const double* ys;       // sorted y coordinate
+  const double* yv;       // sorted data
+  double* H;              // n x (M r): V_F, then H_F = L_Sigma^{-1} V_F
+  double* z;              // n: L_Sigma^{-1} y_F
+  double* LS;             // ragged n_F x n_F: L_Sigma^{-1}
+  double* d;              // 4^M: log|Sigma_F|
+  double* u;              // 4^M: y_F' Sigma_F^{-1} y_F
+};
+
+struct Shape {
+  int M, r, gx, gy;
+  double bbox[4];
+};
+
+}  // namespace mra

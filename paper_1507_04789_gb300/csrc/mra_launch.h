@@ -1,0 +1,27 @@
+// mra_launch.h -- host-side launchers of the M-RA kernels (internal to the library).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "mra_kernels.cuh"
+
+namespace mra {
+
+// Tree build (Sec. 2.2): leaf of every observation, stable counting sort by leaf.
+cudaError_t launch_bin(const double* locs, int64_t n, const double* bbox_dev, int M,
+                       int32_t* leaf_id, int32_t* counts, int32_t* cursor, int64_t* off,
+                       int64_t* sq_off, int32_t* max_count, int64_t* perm, int* status,
+                       cudaStream_t s, int64_t* launches);
+// Gather the sorted observations: xs, ys, yv from row-major locs (n x 2) and y.
+cudaError_t launch_gather(const double* locs, const double* y, const int64_t* perm, int64_t n,
+                          double* xs, double* ys, double* yv, cudaStream_t s, int64_t* launches);
+// Gather y only (new data on an existing partition).
+cudaError_t launch_gather_y(const double* y, const int64_t* perm, int64_t n, double* yv,
+                            cudaStream_t s, int64_t* launches);
+
+// Prior pass, leaf pass and posterior pass (Sec. 3.1-3.3).
+cudaError_t launch_loglik(const Shape& sh, const Cov& cv, double tau2, const LevelState& st,
+                          const LeafState& lf, int nlmax, int* status, cudaStream_t s,
+                          int64_t* launches);
+size_t leaf_smem_bytes(int r, int nlmax);
+
+}  // namespace mra

@@ -1,0 +1,231 @@
+"""Python binding of the C ABI in ``include/mra.h`` (argument marshalling only).
+
+Every step of the computation runs in the CUDA library
+``libmra_gb300.so``; this module converts arguments, calls it through ctypes
+and raises :class:`MRAError` on a non-zero status.  There is no fallback: if
+the library is missing, importing the binding fails with a message saying how
+to build it.
+
+Inputs may be numpy arrays (host memory) or CUDA ``torch.Tensor`` objects
+(device memory, float64, contiguous); outputs of :meth:`Handle.predict` are
+returned in the same memory space as the prediction locations.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmra_gb300.so")
+
+MRA_OK, MRA_ERR_ARG, MRA_ERR_OOM, MRA_ERR_CUDA, MRA_ERR_NOT_PD, MRA_ERR_STATE, MRA_ERR_LIMIT = range(7)
+MRA_COV_EXP, MRA_COV_MATERN15 = 0, 1
+MRA_PREC_FP64 = 0
+MRA_HOST, MRA_DEVICE = 0, 1
+MRA_MAX_LEAF = 128
+FAMILIES = {"exp": MRA_COV_EXP, "matern15": MRA_COV_MATERN15}
+
+
+class MRAError(RuntimeError):
+    """Non-zero status from the library; ``code`` is the MRA_ERR_* value."""
+
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[mra error {code}] {msg}")
+        self.code = code
+
+
+class MraConfig(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("J", ctypes.c_int), ("r", ctypes.c_int),
+                ("cov_family", ctypes.c_int), ("nonstat", ctypes.c_int),
+                ("precision", ctypes.c_int), ("bbox", ctypes.c_double * 4)]
+
+
+class MraParams(ctypes.Structure):
+    _fields_ = [("sigma2", ctypes.c_double), ("range", ctypes.c_double), ("tau2", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with "
+                          f"`python -c 'import __graft_entry__ as g; g.build()'` "
+                          f"or `python {os.path.join(_PKG, 'build.py')}`")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "mra_build": (ctypes.c_int, [ctypes.POINTER(MraConfig), _P, _P, ctypes.c_int64, ctypes.c_int,
+                                     ctypes.POINTER(_P)]),
+        "mra_set_data": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+        "mra_loglik": (ctypes.c_int, [_P, ctypes.POINTER(MraParams), _D]),
+        "mra_predict": (ctypes.c_int, [_P, ctypes.POINTER(MraParams), _P, ctypes.c_int64, ctypes.c_int,
+                                       _P, _P]),
+        "mra_region_terms": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+        "mra_leaf_offsets": (ctypes.c_int, [_P, _P, _P]),
+        "mra_set_stream": (ctypes.c_int, [_P, _P]),
+        "mra_free": (None, [_P]),
+        "mra_last_error": (ctypes.c_char_p, []),
+        "mra_launch_count": (ctypes.c_int64, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    for name in ("mra_loglik_grad",):
+        if hasattr(lib, name):
+            f = getattr(lib, name)
+            f.restype = ctypes.c_int
+            f.argtypes = [_P, ctypes.POINTER(MraParams), _D, _P]
+    _lib = lib
+    return lib
+
+
+def _check(rc: int) -> None:
+    if rc != MRA_OK:
+        raise MRAError(rc, _lib.mra_last_error().decode())
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and hasattr(x, "data_ptr") and bool(x.is_cuda)
+
+
+def _host_f64(x, shape_last=None) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    if shape_last is not None and (a.ndim != 2 or a.shape[1] != shape_last):
+        raise ValueError(f"expected an (n, {shape_last}) array, got shape {a.shape}")
+    return a
+
+
+def _dev_ptr(t, name: str) -> int:
+    import torch
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def launch_count(reset: bool = False) -> int:
+    """Kernel launches the library issued from this thread (optionally reset)."""
+    return int(load_library().mra_launch_count(1 if reset else 0))
+
+
+class Handle:
+    """One M-RA problem on the GPU: locations, data and the tree (Sec. 2.2)."""
+
+    def __init__(self, locs, y, M: int, r: int, family: str = "exp", nonstat: bool = False,
+                 bbox=(0.0, 1.0, 0.0, 1.0), J: int = 4, precision: int = MRA_PREC_FP64):
+        lib = load_library()
+        self._lib = lib
+        self._h = _P()
+        cfg = MraConfig(M, J, r, FAMILIES[family] if isinstance(family, str) else int(family),
+                        int(bool(nonstat)), precision, (ctypes.c_double * 4)(*bbox))
+        if _is_torch_cuda(locs):
+            if locs.dim() != 2 or locs.shape[1] != 2:
+                raise ValueError("locs must be (n, 2)")
+            n = locs.shape[0]
+            keep = (locs, y)
+            rc = lib.mra_build(ctypes.byref(cfg), _dev_ptr(locs, "locs"), _dev_ptr(y, "y"), n, MRA_DEVICE,
+                               ctypes.byref(self._h))
+            del keep
+            self._where = MRA_DEVICE
+        else:
+            la = _host_f64(locs, 2)
+            ya = _host_f64(y)
+            if ya.shape != (la.shape[0],):
+                raise ValueError("y must have one value per location")
+            n = la.shape[0]
+            rc = lib.mra_build(ctypes.byref(cfg), la.ctypes.data, ya.ctypes.data, n, MRA_HOST,
+                               ctypes.byref(self._h))
+            self._where = MRA_HOST
+        _check(rc)
+        self.n, self.M, self.r, self.J = n, M, r, J
+        self.family, self.nonstat = family, nonstat
+        self.bbox = tuple(bbox)
+
+    # -- lifecycle --------------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.mra_free(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream) -> None:
+        """Run on a ``torch.cuda.Stream`` (or a raw cudaStream_t integer, 0 = default)."""
+        ptr = getattr(stream, "cuda_stream", stream)
+        _check(self._lib.mra_set_stream(self._h, _P(int(ptr) if ptr else None)))
+
+    def set_data(self, y) -> None:
+        if _is_torch_cuda(y):
+            _check(self._lib.mra_set_data(self._h, _dev_ptr(y, "y"), MRA_DEVICE))
+        else:
+            ya = _host_f64(y)
+            _check(self._lib.mra_set_data(self._h, ya.ctypes.data, MRA_HOST))
+
+    # -- computations -------------------------------------------------------------
+    def loglik(self, theta) -> float:
+        """Log-likelihood at theta = (sigma2, range, tau2) (Sec. 3.3)."""
+        out = ctypes.c_double()
+        p = MraParams(*[float(v) for v in theta])
+        _check(self._lib.mra_loglik(self._h, ctypes.byref(p), ctypes.byref(out)))
+        return out.value
+
+    def loglik_grad(self, theta):
+        """(loglik, d loglik / d(sigma2, range, tau2))."""
+        if not hasattr(self._lib, "mra_loglik_grad"):
+            raise MRAError(MRA_ERR_STATE, "library built without the gradient entry point")
+        out = ctypes.c_double()
+        g = np.zeros(3)
+        p = MraParams(*[float(v) for v in theta])
+        _check(self._lib.mra_loglik_grad(self._h, ctypes.byref(p), ctypes.byref(out), g.ctypes.data))
+        return out.value, g
+
+    def predict(self, theta, plocs):
+        """Posterior predictive mean and variance of y at plocs (Sec. 3.4, Prop. 2)."""
+        p = MraParams(*[float(v) for v in theta])
+        if _is_torch_cuda(plocs):
+            import torch
+            npred = plocs.shape[0]
+            mean = torch.empty(npred, dtype=torch.float64, device=plocs.device)
+            var = torch.empty(npred, dtype=torch.float64, device=plocs.device)
+            _check(self._lib.mra_predict(self._h, ctypes.byref(p), _dev_ptr(plocs, "plocs"), npred, MRA_DEVICE,
+                                         mean.data_ptr(), var.data_ptr()))
+            return mean, var
+        pa = _host_f64(plocs, 2)
+        mean = np.empty(pa.shape[0])
+        var = np.empty(pa.shape[0])
+        _check(self._lib.mra_predict(self._h, ctypes.byref(p), pa.ctypes.data, pa.shape[0], MRA_HOST,
+                                     mean.ctypes.data, var.ctypes.data))
+        return mean, var
+
+    def region_terms(self, level: int):
+        """(d_R, u_R) of every region at ``level`` from the last loglik (Sec. 3.3)."""
+        cnt = 4 ** level
+        d = np.empty(cnt)
+        u = np.empty(cnt)
+        _check(self._lib.mra_region_terms(self._h, level, d.ctypes.data, u.ctypes.data))
+        return d, u
+
+    def leaf_offsets(self, with_perm: bool = False):
+        off = np.empty(4 ** self.M + 1, dtype=np.int64)
+        perm = np.empty(self.n, dtype=np.int64) if with_perm else None
+        _check(self._lib.mra_leaf_offsets(self._h, off.ctypes.data, perm.ctypes.data if with_perm else None))
+        return (off, perm) if with_perm else off

@@ -1,0 +1,57 @@
+"""The C-ABI library builds, loads and exports every entry point of include/mra.h.
+
+No compute call is made here, so these tests need no GPU.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mra.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mra_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1507_04789_gb300 import build, mra
+    if not os.path.exists(mra.LIB_PATH):
+        build.build()
+    return ctypes.CDLL(mra.LIB_PATH)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("mra_build", "mra_loglik", "mra_predict", "mra_free", "mra_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"declared in mra.h but not exported: {missing}"
+
+
+def test_binding_signatures_load(lib):
+    from paper_1507_04789_gb300 import mra
+    L = mra.load_library()
+    assert L.mra_last_error() is not None
+
+
+def test_argument_errors_need_no_gpu(lib):
+    """Invalid configurations are rejected on the host before any CUDA call."""
+    from paper_1507_04789_gb300 import mra
+    import numpy as np
+    with pytest.raises(mra.MRAError) as ei:
+        mra.Handle(np.zeros((4, 2)), np.zeros(4), M=2, r=16, J=3)
+    assert ei.value.code == mra.MRA_ERR_ARG
+    with pytest.raises(mra.MRAError) as ei:
+        mra.Handle(np.zeros((4, 2)), np.zeros(4), M=2, r=65)
+    assert ei.value.code == mra.MRA_ERR_ARG
+    with pytest.raises(mra.MRAError):
+        mra.Handle(np.zeros((4, 2)), np.zeros(4), M=13, r=16)
