@@ -110,6 +110,15 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
 int mra_set_data(mra_handle* h, const double* y, int where);
 
 /*
+ * mra_update -- replace locations and data of a built handle with a new set of
+ * the same size n (host or device per `where`), re-partitioning on the device
+ * without allocating.  Errors: MRA_ERR_ARG (a location outside bbox),
+ * MRA_ERR_LIMIT (the new partition needs a fuller leaf, or more leaf-factor
+ * storage, than the handle was built for: build a new handle), MRA_ERR_CUDA.
+ */
+int mra_update(mra_handle* h, const double* locs, const double* y, int where);
+
+/*
  * mra_loglik -- the M-RA log-likelihood at theta (Sec. 3.1-3.3):
  *   loglik = -(d + u)/2 - (n/2) log(2 pi),  -2 log L_M(theta) = d + u.
  * Runs the prior pass (Eq. priorw) top-down and the posterior pass (Eqs.
@@ -155,6 +164,21 @@ int mra_leaf_offsets(mra_handle* h, int64_t* off_out, int64_t* perm_out);
  * handle's device, passed as void*; NULL = legacy default stream).
  */
 int mra_set_stream(mra_handle* h, void* stream);
+
+/*
+ * Per-kernel timing with CUDA events recorded on the handle's stream around
+ * every launch (for roofline measurements).  mra_enable_timing(h, 1) resets the
+ * totals and starts recording; mra_kernel_times returns the summed device time
+ * (ms) and launch count of one kernel kind since then.  Kinds:
+ */
+#define MRA_K_PRIOR      0  /* prior pass, one launch per level (Eq. priorw) */
+#define MRA_K_LEAF       1  /* leaf factorisation (Sec. 3.1-3.2 at m = M) */
+#define MRA_K_LEAF_SYRK  2  /* leaf Gram products summed into level M-1 */
+#define MRA_K_POST       3  /* posterior factorisation, one launch per level */
+#define MRA_K_AGGREGATE  4  /* child-to-parent updates (Eqs. mainquantities, helpquantities) */
+#define MRA_K_PREDICT    5  /* prediction (Sec. 3.4) */
+int mra_enable_timing(mra_handle* h, int on);
+int mra_kernel_times(mra_handle* h, int kind, double* total_ms, int64_t* launches);
 
 /* mra_free -- release the handle and its device memory; NULL is a no-op. */
 void mra_free(mra_handle* h);

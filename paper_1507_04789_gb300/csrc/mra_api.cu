@@ -97,6 +97,11 @@ struct mra_handle {
   mra::LeafState lf{};
   // host
   double* pinned = nullptr;    // small pinned readback buffer
+  int64_t ls_cap = 0;          // capacity of the ragged leaf-factor store (doubles)
+  mra::Timer timer;
+  bool timer_events = false;
+  double ktime[8] = {0};
+  int64_t kcount[8] = {0};
   bool have_post = false;
   mra_params last{};
 };
@@ -114,6 +119,18 @@ cudaError_t sync_status(mra_handle* h, int* host_status, double* extra, int next
   memcpy(host_status, h->pinned, sizeof(int) * 4);
   for (int k = 0; k < nextra; ++k) extra[k] = h->pinned[4 + k];
   return cudaSuccess;
+}
+
+void collect_times(mra_handle* h) {
+  if (!h->timer.on) return;
+  for (int k = 0; k < h->timer.count; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->timer.ev[2 * k], h->timer.ev[2 * k + 1]) == cudaSuccess) {
+      h->ktime[h->timer.kind[k]] += ms;
+      h->kcount[h->timer.kind[k]] += 1;
+    }
+  }
+  h->timer.count = 0;
 }
 
 int status_error(const int* s) {
@@ -152,6 +169,8 @@ int64_t mra_launch_count(int reset) {
 
 void mra_free(mra_handle* h) {
   if (!h) return;
+  if (h->timer_events)
+    for (int k = 0; k < 2 * mra::MAX_TIMED; ++k) cudaEventDestroy(h->timer.ev[k]);
   h->tree.release();
   h->state.release();
   if (h->pinned) cudaFreeHost(h->pinned);
@@ -209,10 +228,8 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   A.want(&h->xs, n);
   A.want(&h->ys, n);
   A.want(&h->yv, n);
-  if (where == MRA_HOST) {
-    A.want(&h->in_locs, 2 * n);
-    A.want(&h->in_y, n);
-  }
+  A.want(&h->in_locs, 2 * n);   // staging for host inputs (mra_build, mra_update, mra_set_data)
+  A.want(&h->in_y, n);
   if ((e = A.commit())) { mra_free(h); return fail(MRA_ERR_OOM, "device allocation (tree): %s", cudaGetErrorString(e)); }
   if ((e = cudaMallocHost((void**)&h->pinned, 64 * sizeof(double)))) { mra_free(h); return cuda_fail(e, "cudaMallocHost"); }
 
@@ -268,6 +285,7 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
     B.want(&H, n * (int64_t)M * r);
     B.want(&z, n);
     B.want(&LS, (size_t)tail[0]);
+    h->ls_cap = tail[0];
     B.want(&d, nl);
     B.want(&u, nl);
     if ((e = B.commit())) { mra_free(h); return fail(MRA_ERR_OOM, "device allocation (factors): %s", cudaGetErrorString(e)); }
@@ -300,7 +318,6 @@ int mra_set_data(mra_handle* h, const double* y, int where) {
   const double* dy = y;
   cudaError_t e;
   if (where == MRA_HOST) {
-    if (!h->in_y) return fail(MRA_ERR_ARG, "handle was built from device inputs; pass device data");
     if ((e = cudaMemcpyAsync(h->in_y, y, sizeof(double) * h->n, cudaMemcpyHostToDevice, h->stream)))
       return cuda_fail(e, "copy y");
     dy = h->in_y;
@@ -321,7 +338,7 @@ int mra_loglik(mra_handle* h, const mra_params* theta, double* loglik_out) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream))) return cuda_fail(e, "memset");
   if ((e = mra::launch_loglik(shape_of(h), cv, theta->tau2, h->st, h->lf, h->nlmax, h->status, h->stream,
-                              &g_launches)))
+                              &g_launches, &h->timer)))
     return cuda_fail(e, "loglik launch");
   int hs[4];
   double du[2];
@@ -329,6 +346,7 @@ int mra_loglik(mra_handle* h, const mra_params* theta, double* loglik_out) {
   if (h->M > 0) { srcs[0] = h->st.dd[0]; srcs[1] = h->st.uu[0]; }
   else { srcs[0] = h->lf.d; srcs[1] = h->lf.u; }
   if ((e = sync_status(h, hs, du, 2, srcs))) return cuda_fail(e, "loglik");
+  collect_times(h);
   if (hs[0]) return status_error(hs);
   *loglik_out = -0.5 * (du[0] + du[1]) - 0.5 * (double)h->n * std::log(2.0 * M_PI);
   h->have_post = true;
@@ -362,6 +380,67 @@ int mra_leaf_offsets(mra_handle* h, int64_t* off_out, int64_t* perm_out) {
   if (perm_out && (e = cudaMemcpyAsync(perm_out, h->perm, sizeof(int64_t) * h->n, cudaMemcpyDeviceToHost, h->stream)))
     return cuda_fail(e, "perm");
   if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "offsets");
+  return MRA_OK;
+}
+
+int mra_update(mra_handle* h, const double* locs, const double* y, int where) {
+  g_err.clear();
+  if (!h || !locs || !y) return fail(MRA_ERR_ARG, "null argument");
+  if (where != MRA_HOST && where != MRA_DEVICE) return fail(MRA_ERR_ARG, "where must be MRA_HOST or MRA_DEVICE");
+  const int64_t n = h->n, nl = int64_t(1) << (2 * h->M);
+  cudaError_t e;
+  const double* dl = locs;
+  const double* dy = y;
+  h->have_post = false;
+  if (where == MRA_HOST) {
+    if ((e = cudaMemcpyAsync(h->in_locs, locs, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, h->stream)) ||
+        (e = cudaMemcpyAsync(h->in_y, y, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream)))
+      return cuda_fail(e, "copy inputs");
+    dl = h->in_locs;
+    dy = h->in_y;
+  }
+  if ((e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream))) return cuda_fail(e, "memset");
+  if ((e = mra::launch_bin(dl, n, h->bbox, h->M, h->leaf_id, h->counts, h->cursor, h->off, h->sq_off,
+                           h->max_count, h->perm, h->status, h->stream, &g_launches)) ||
+      (e = mra::launch_gather(dl, dy, h->perm, n, h->xs, h->ys, h->yv, h->stream, &g_launches)))
+    return cuda_fail(e, "binning");
+  int hs[4];
+  double got[2];
+  const double* srcs[2] = {(const double*)(h->sq_off + nl), (const double*)h->max_count};
+  if ((e = sync_status(h, hs, got, 2, srcs))) return cuda_fail(e, "binning");
+  if (hs[0]) return status_error(hs);
+  int64_t tail;
+  int32_t mc;
+  memcpy(&tail, &got[0], sizeof tail);
+  memcpy(&mc, &got[1], sizeof mc);
+  if (mc > h->nlmax || tail > h->ls_cap)
+    return fail(MRA_ERR_LIMIT, "new partition needs leaves of %d (handle has %d) or %lld leaf-factor doubles "
+                "(handle has %lld); build a new handle", mc, h->nlmax, (long long)tail, (long long)h->ls_cap);
+  return MRA_OK;
+}
+
+int mra_enable_timing(mra_handle* h, int on) {
+  g_err.clear();
+  if (!h) return fail(MRA_ERR_ARG, "null handle");
+  if (on && !h->timer_events) {
+    for (int k = 0; k < 2 * mra::MAX_TIMED; ++k) {
+      cudaError_t e = cudaEventCreate(&h->timer.ev[k]);
+      if (e) return cuda_fail(e, "cudaEventCreate");
+    }
+    h->timer_events = true;
+  }
+  h->timer.on = on != 0;
+  h->timer.count = 0;
+  for (int k = 0; k < 8; ++k) { h->ktime[k] = 0.0; h->kcount[k] = 0; }
+  return MRA_OK;
+}
+
+int mra_kernel_times(mra_handle* h, int kind, double* total_ms, int64_t* launches) {
+  g_err.clear();
+  if (!h || !total_ms || !launches) return fail(MRA_ERR_ARG, "null argument");
+  if (kind < 0 || kind >= 8) return fail(MRA_ERR_ARG, "unknown kernel kind %d", kind);
+  *total_ms = h->ktime[kind];
+  *launches = h->kcount[kind];
   return MRA_OK;
 }
 

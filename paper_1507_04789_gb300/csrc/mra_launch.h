@@ -6,6 +6,25 @@
 
 namespace mra {
 
+// Optional per-launch CUDA-event timing (kinds match MRA_K_* in mra.h).
+constexpr int MAX_TIMED = 256;
+struct Timer {
+  bool on = false;
+  int count = 0;
+  int kind[MAX_TIMED];
+  cudaEvent_t ev[2 * MAX_TIMED];
+  void start(int k, cudaStream_t s) {
+    if (!on || count >= MAX_TIMED) return;
+    kind[count] = k;
+    cudaEventRecord(ev[2 * count], s);
+  }
+  void stop(cudaStream_t s) {
+    if (!on || count >= MAX_TIMED) return;
+    cudaEventRecord(ev[2 * count + 1], s);
+    ++count;
+  }
+};
+
 // Tree build (Sec. 2.2): leaf of every observation, stable counting sort by leaf.
 cudaError_t launch_bin(const double* locs, int64_t n, const double* bbox_dev, int M,
                        int32_t* leaf_id, int32_t* counts, int32_t* cursor, int64_t* off,
@@ -21,7 +40,7 @@ cudaError_t launch_gather_y(const double* y, const int64_t* perm, int64_t n, dou
 // Prior pass, leaf pass and posterior pass (Sec. 3.1-3.3).
 cudaError_t launch_loglik(const Shape& sh, const Cov& cv, double tau2, const LevelState& st,
                           const LeafState& lf, int nlmax, int* status, cudaStream_t s,
-                          int64_t* launches);
+                          int64_t* launches, Timer* timer);
 size_t leaf_smem_bytes(int r, int nlmax);
 
 }  // namespace mra

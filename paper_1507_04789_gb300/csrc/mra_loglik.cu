@@ -410,40 +410,51 @@ static size_t syrk_smem(int tile) { return sizeof(double) * 2 * KC * (tile + 2);
 
 
 cudaError_t launch_loglik(const Shape& sh, const Cov& cv, double tau2, const LevelState& st,
-                          const LeafState& lf, int nlmax, int* status, cudaStream_t s, int64_t* launches) {
+                          const LeafState& lf, int nlmax, int* status, cudaStream_t s, int64_t* launches,
+                          Timer* tm) {
   const int tile = tile_for(sh.r);
   cudaError_t e;
   // prior pass, top-down
   for (int m = 0; m < sh.M; ++m) {
     size_t sm = prior_smem(tile);
     unsigned grid = 1u << (2 * m);
+    tm->start(0, s);
     MRA_LAUNCH(tile, prior_level_kernel, grid, sm, s, m, sh, cv, st, status);
+    tm->stop(s);
     ++*launches;
   }
   // leaves
   {
     size_t sm = leaf_smem(tile, nlmax);
     unsigned grid = 1u << (2 * sh.M);
+    tm->start(1, s);
     MRA_LAUNCH(tile, leaf_kernel, grid, sm, s, sh, cv, tau2, st, lf, nlmax, status);
+    tm->stop(s);
     ++*launches;
   }
   if (sh.M > 0) {
     const int m = sh.M - 1;
     dim3 grid(1u << (2 * m), (m + 1) * (m + 2) / 2);
     size_t sm = syrk_smem(tile);
+    tm->start(2, s);
     MRA_LAUNCH(tile, leaf_syrk_kernel, grid, sm, s, sh, st, lf);
+    tm->stop(s);
     ++*launches;
   }
   // posterior pass, bottom-up
   for (int m = sh.M - 1; m >= 0; --m) {
     size_t sm = post_smem(tile);
     unsigned grid = 1u << (2 * m);
+    tm->start(3, s);
     MRA_LAUNCH(tile, post_level_kernel, grid, sm, s, m, sh, st, lf, status);
+    tm->stop(s);
     ++*launches;
     if (m > 0) {
       dim3 g2(1u << (2 * (m - 1)), m * (m + 1) / 2);
       size_t s2 = syrk_smem(tile);
+      tm->start(4, s);
       MRA_LAUNCH(tile, aggregate_kernel, g2, s2, s, m, sh, st);
+      tm->stop(s);
       ++*launches;
     }
   }

@@ -26,6 +26,7 @@ MRA_PREC_FP64 = 0
 MRA_HOST, MRA_DEVICE = 0, 1
 MRA_MAX_LEAF = 128
 FAMILIES = {"exp": MRA_COV_EXP, "matern15": MRA_COV_MATERN15}
+KERNEL_KINDS = ("prior", "leaf", "leaf_syrk", "post", "aggregate", "predict")
 
 
 class MRAError(RuntimeError):
@@ -66,6 +67,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "mra_build": (ctypes.c_int, [ctypes.POINTER(MraConfig), _P, _P, ctypes.c_int64, ctypes.c_int,
                                      ctypes.POINTER(_P)]),
         "mra_set_data": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+        "mra_update": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+        "mra_enable_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+        "mra_kernel_times": (ctypes.c_int, [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int64)]),
         "mra_loglik": (ctypes.c_int, [_P, ctypes.POINTER(MraParams), _D]),
         "mra_predict": (ctypes.c_int, [_P, ctypes.POINTER(MraParams), _P, ctypes.c_int64, ctypes.c_int,
                                        _P, _P]),
@@ -179,6 +183,28 @@ class Handle:
         else:
             ya = _host_f64(y)
             _check(self._lib.mra_set_data(self._h, ya.ctypes.data, MRA_HOST))
+
+    def update(self, locs, y) -> None:
+        """New locations and data of the same size, re-partitioned in place."""
+        if _is_torch_cuda(locs):
+            _check(self._lib.mra_update(self._h, _dev_ptr(locs, "locs"), _dev_ptr(y, "y"), MRA_DEVICE))
+        else:
+            la = _host_f64(locs, 2)
+            ya = _host_f64(y)
+            _check(self._lib.mra_update(self._h, la.ctypes.data, ya.ctypes.data, MRA_HOST))
+
+    def enable_timing(self, on: bool = True) -> None:
+        _check(self._lib.mra_enable_timing(self._h, 1 if on else 0))
+
+    def kernel_times(self) -> dict:
+        """{kind: (total_ms, launches)} since enable_timing."""
+        out = {}
+        for k, name in enumerate(KERNEL_KINDS):
+            ms = ctypes.c_double()
+            cnt = ctypes.c_int64()
+            _check(self._lib.mra_kernel_times(self._h, k, ctypes.byref(ms), ctypes.byref(cnt)))
+            out[name] = (ms.value, cnt.value)
+        return out
 
     # -- computations -------------------------------------------------------------
     def loglik(self, theta) -> float:

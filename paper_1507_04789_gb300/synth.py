@@ -41,7 +41,7 @@ def uniform_locations(n: int, seed: int, dim: int = 2) -> np.ndarray:
 
 
 def rff_field(locs: np.ndarray, nu: float, kappa: float, sigma2: float,
-              seed: int, features: int = 4096, chunk: int = 1 << 16) -> np.ndarray:
+              seed: int, features: int = 4096) -> np.ndarray:
     """Random-Fourier-feature approximation of a zero-mean GP draw at ``locs``."""
     rng = np.random.default_rng(seed)
     d = locs.shape[1]
@@ -51,6 +51,7 @@ def rff_field(locs: np.ndarray, nu: float, kappa: float, sigma2: float,
     b = rng.uniform(0.0, 2.0 * math.pi, size=features)
     out = np.empty(locs.shape[0])
     amp = math.sqrt(sigma2) * math.sqrt(2.0 / features)
+    chunk = max(256, (1 << 22) // features)
     for i in range(0, locs.shape[0], chunk):
         ph = locs[i:i + chunk] @ w.T + b
         out[i:i + chunk] = amp * np.cos(ph).sum(axis=1)
@@ -125,12 +126,13 @@ class Workload:
     n_pred: int
     seed: int = 0
     J: int = 4
+    features: int = 4096     # random Fourier features of the field draw
 
     def generate(self):
         """Return (locs (n,2), y (n,), plocs (n_pred,2)), all float64."""
         nu = 0.5 if self.family == "exp" else 1.5
         locs = uniform_locations(self.n, self.seed)
-        field = rff_field(locs, nu, self.kappa, self.sigma2, self.seed + 1)
+        field = rff_field(locs, nu, self.kappa, self.sigma2, self.seed + 1, self.features)
         y = noisy_observations(field, self.tau2, self.seed + 2)
         plocs = uniform_locations(self.n_pred, self.seed + 3)
         return locs, y, plocs
@@ -142,7 +144,8 @@ WORKLOADS = {
     "n4096_exp_M3_r16": Workload("n4096_exp_M3_r16", 4096, 3, 16, "exp", 1.0, 0.05, 0.05, 1024),
     # n=2^20 uniform, Matern-1.5 (sigma2=1, range 0.1), tau2=0.01, M=7, J=4,
     # r=64 (8x8 grid per region), ~64 observations per leaf.
-    "n1M_matern15_M7_r64": Workload("n1M_matern15_M7_r64", 1 << 20, 7, 64, "matern15", 1.0, 0.1, 0.01, 1 << 14),
+    "n1M_matern15_M7_r64": Workload("n1M_matern15_M7_r64", 1 << 20, 7, 64, "matern15", 1.0, 0.1, 0.01, 1 << 14,
+                                    features=256),
     # n=2^14 with the same leaf shape (gradient parity size).
     "n16k_matern15_M4_r64": Workload("n16k_matern15_M4_r64", 1 << 14, 4, 64, "matern15", 1.0, 0.1, 0.01, 1024),
 }

@@ -80,12 +80,13 @@ def test_parity_grid(mra, n, M, r, family, nonstat, clustered, seed):
 def test_ragged_full_leaves(mra):
     """Leaves from 0 up to the 128-observation maximum, several row tiles."""
     rng = np.random.default_rng(9)
-    parts = [0.25 * rng.random((128, 2)), 0.5 + 0.25 * rng.random((37, 2)), rng.random((200, 2))]
+    q = 0.5 * rng.random((255, 2))
+    parts = [q[:128], q[128:165] + [0.5, 0.0], q[165:] + [0.5, 0.5]]   # leaves of 128, 37, 0, 90
     locs = np.concatenate(parts)
     y = rng.standard_normal(locs.shape[0])
     with mra.Handle(locs, y, M=1, r=16) as h:
         off = h.leaf_offsets()
-    assert np.diff(off).max() <= 128
+    np.testing.assert_array_equal(np.diff(off), [128, 37, 0, 90])
     _compare(mra, locs, y, 1, 16, "exp", (1.0, 0.3, 0.1))
 
 
