@@ -146,6 +146,9 @@ WORKLOADS = {
     # r=64 (8x8 grid per region), ~64 observations per leaf.
     "n1M_matern15_M7_r64": Workload("n1M_matern15_M7_r64", 1 << 20, 7, 64, "matern15", 1.0, 0.1, 0.01, 1 << 14,
                                     features=256),
+    # n=2^18 with the same leaf shape: profiling size (a few GB on the device).
+    "n256k_matern15_M6_r64": Workload("n256k_matern15_M6_r64", 1 << 18, 6, 64, "matern15", 1.0, 0.1, 0.01, 1 << 12,
+                                      features=256),
     # n=2^14 with the same leaf shape (gradient parity size).
     "n16k_matern15_M4_r64": Workload("n16k_matern15_M4_r64", 1 << 14, 4, 64, "matern15", 1.0, 0.1, 0.01, 1024),
 }
