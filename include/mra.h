@@ -180,6 +180,35 @@ int mra_set_stream(mra_handle* h, void* stream);
 int mra_enable_timing(mra_handle* h, int on);
 int mra_kernel_times(mra_handle* h, int kind, double* total_ms, int64_t* launches);
 
+/*
+ * mra_loglik_noalloc -- the log-likelihood of mra_build + mra_loglik in one
+ * call that allocates no memory at all (no cudaMalloc, cudaFree, host pinning
+ * or allocating library routine).  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory themselves or
+ * let a library do so -- code running under a framework whose caching
+ * allocator owns the device heap, plug-ins in processes that forbid
+ * allocation after start-up, or paths that must not fail half way on memory
+ * exhaustion.  Every intermediate lives in one fixed scratch array inside the
+ * library image, MRA_NOALLOC_SCRATCH_BYTES per device, which every GPU that
+ * loads the library holds until the process exits (enough for problems of
+ * roughly n = 16k with M = 4, r = 16, or n = 4096 with M = 3, r = 64).
+ *   cfg, theta : as for mra_build / mra_loglik (host).
+ *   locs, y    : device pointers, n x 2 row-major locations and n data.
+ *   stream     : cudaStream_t (as void*, NULL = legacy default stream).
+ *   loglik_out : host pointer to one double.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the array and it keeps the last call's
+ * contents; calls that overlap on the GPU (several host threads or streams)
+ * race on it and must be serialised by the caller.  The call synchronises
+ * `stream` before returning.  Errors: MRA_ERR_ARG, MRA_ERR_LIMIT (the problem
+ * needs more scratch than MRA_NOALLOC_SCRATCH_BYTES, or a leaf above
+ * MRA_MAX_LEAF), MRA_ERR_NOT_PD, MRA_ERR_CUDA.
+ */
+#define MRA_NOALLOC_SCRATCH_BYTES (32u << 20)
+int mra_loglik_noalloc(const mra_config* cfg, const mra_params* theta, const double* locs,
+                       const double* y, int64_t n, void* stream, double* loglik_out);
+
 /* mra_free -- release the handle and its device memory; NULL is a no-op. */
 void mra_free(mra_handle* h);
 

@@ -70,6 +70,13 @@ int gx_for(int r) {
 
 }  // namespace
 
+namespace mra {
+// Lets other translation units of the library report errors through
+// mra_last_error() and count their launches in mra_launch_count().
+void set_last_error(const char* msg) { g_err = msg; }
+int64_t* launch_counter() { return &g_launches; }
+}  // namespace mra
+
 struct mra_handle {
   mra_config cfg;
   int64_t n = 0;

@@ -43,4 +43,8 @@ cudaError_t launch_loglik(const Shape& sh, const Cov& cv, double tau2, const Lev
                           int64_t* launches, Timer* timer);
 size_t leaf_smem_bytes(int r, int nlmax);
 
+// Error text and launch counter shared by every entry point (mra_api.cu).
+void set_last_error(const char* msg);
+int64_t* launch_counter();
+
 }  // namespace mra
