@@ -137,8 +137,10 @@ int mra_loglik(mra_handle* h, const mra_params* theta, double* loglik_out);
  * must have been called with the same theta (else MRA_ERR_STATE).
  *   plocs    : np x 2 row-major locations inside bbox, host or device per `where`.
  *   mean_out, var_out : np doubles each, same memory space as plocs, caller-owned.
- * Errors: MRA_ERR_ARG, MRA_ERR_STATE, MRA_ERR_LIMIT (more than 4096 prediction
- * points in one leaf), MRA_ERR_CUDA.
+ * The handle keeps a prediction buffer (about np (M r + 8) doubles) that is
+ * allocated on the first call and grown when np exceeds every earlier call's.
+ * Errors: MRA_ERR_ARG (a location outside bbox), MRA_ERR_STATE, MRA_ERR_OOM,
+ * MRA_ERR_CUDA.
  */
 int mra_predict(mra_handle* h, const mra_params* theta, const double* plocs, int64_t np,
                 int where, double* mean_out, double* var_out);

@@ -3,8 +3,9 @@
 // A handle owns the device state of one problem: the sorted observations, the
 // per-level factors of the prior and posterior passes and the leaf factors.
 // Device memory is taken in two arenas at build time (the leaf-factor size
-// depends on the occupancy of the leaves, known after binning); no entry point
-// allocates afterwards.
+// depends on the occupancy of the leaves, known after binning) and, for
+// prediction, a third arena that mra_predict grows when it is given more
+// points than before; no other entry point allocates after mra_build.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -105,6 +106,12 @@ struct mra_handle {
   // host
   double* pinned = nullptr;    // small pinned readback buffer
   int64_t ls_cap = 0;          // capacity of the ragged leaf-factor store (doubles)
+  // prediction points (arena 3, grown on demand by mra_predict)
+  Arena pred;
+  int64_t pred_cap = 0;
+  double *p_in = nullptr, *p_xs = nullptr, *p_ys = nullptr, *p_U = nullptr, *p_mean = nullptr, *p_var = nullptr;
+  int32_t *p_leaf = nullptr, *p_counts = nullptr, *p_cursor = nullptr, *p_max = nullptr;
+  int64_t *p_off = nullptr, *p_sq = nullptr, *p_perm = nullptr;
   mra::Timer timer;
   bool timer_events = false;
   double ktime[8] = {0};
@@ -180,6 +187,7 @@ void mra_free(mra_handle* h) {
     for (int k = 0; k < 2 * mra::MAX_TIMED; ++k) cudaEventDestroy(h->timer.ev[k]);
   h->tree.release();
   h->state.release();
+  h->pred.release();
   if (h->pinned) cudaFreeHost(h->pinned);
   delete h;
 }
@@ -454,9 +462,75 @@ int mra_kernel_times(mra_handle* h, int kind, double* total_ms, int64_t* launche
 int mra_predict(mra_handle* h, const mra_params* theta, const double* plocs, int64_t np, int where,
                 double* mean_out, double* var_out) {
   g_err.clear();
-  (void)theta; (void)plocs; (void)np; (void)where; (void)mean_out; (void)var_out;
-  if (!h) return fail(MRA_ERR_ARG, "null handle");
-  return fail(MRA_ERR_STATE, "prediction not available");
+  if (!h || !theta || !plocs || !mean_out || !var_out) return fail(MRA_ERR_ARG, "null argument");
+  if (np < 1) return fail(MRA_ERR_ARG, "np must be >= 1");
+  if (where != MRA_HOST && where != MRA_DEVICE) return fail(MRA_ERR_ARG, "where must be MRA_HOST or MRA_DEVICE");
+  if (!h->have_post) return fail(MRA_ERR_STATE, "call mra_loglik before mra_predict");
+  if (theta->sigma2 != h->last.sigma2 || theta->range != h->last.range || theta->tau2 != h->last.tau2)
+    return fail(MRA_ERR_STATE, "theta differs from the last mra_loglik; evaluate the log-likelihood at it first");
+  const int M = h->M, r = h->r;
+  const int64_t nl = int64_t(1) << (2 * M);
+  cudaError_t e;
+  if (np > h->pred_cap) {
+    h->pred.release();
+    Arena& P = h->pred;
+    P.want(&h->p_in, 2 * np);
+    P.want(&h->p_xs, np);
+    P.want(&h->p_ys, np);
+    P.want(&h->p_U, np * (int64_t)M * r);
+    P.want(&h->p_mean, np);
+    P.want(&h->p_var, np);
+    P.want(&h->p_leaf, np);
+    P.want(&h->p_counts, nl);
+    P.want(&h->p_cursor, nl);
+    P.want(&h->p_max, 2);
+    P.want(&h->p_off, nl + 1);
+    P.want(&h->p_sq, nl + 1);
+    P.want(&h->p_perm, np);
+    if ((e = P.commit())) {
+      h->pred_cap = 0;
+      return fail(MRA_ERR_OOM, "device allocation (prediction): %s", cudaGetErrorString(e));
+    }
+    h->pred_cap = np;
+  }
+  const double* dp = plocs;
+  if (where == MRA_HOST) {
+    if ((e = cudaMemcpyAsync(h->p_in, plocs, sizeof(double) * 2 * np, cudaMemcpyHostToDevice, h->stream)))
+      return cuda_fail(e, "copy prediction locations");
+    dp = h->p_in;
+  }
+  if ((e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream))) return cuda_fail(e, "memset");
+  if ((e = mra::launch_bin(dp, np, h->bbox, M, h->p_leaf, h->p_counts, h->p_cursor, h->p_off, h->p_sq, h->p_max,
+                           h->p_perm, h->status, h->stream, &g_launches, false)) ||
+      (e = mra::launch_gather(dp, nullptr, h->p_perm, np, h->p_xs, h->p_ys, nullptr, h->stream, &g_launches)))
+    return cuda_fail(e, "binning prediction points");
+  int hs[4];
+  double got[1];
+  const double* srcs[1] = {(const double*)h->p_max};
+  if ((e = sync_status(h, hs, got, 1, srcs))) return cuda_fail(e, "binning prediction points");
+  if (hs[0]) return status_error(hs);
+  int32_t maxp;
+  memcpy(&maxp, &got[0], sizeof maxp);
+  mra::PredState ps;
+  ps.off = h->p_off;
+  ps.perm = h->p_perm;
+  ps.xs = h->p_xs;
+  ps.ys = h->p_ys;
+  ps.U = h->p_U;
+  ps.mean = where == MRA_DEVICE ? mean_out : h->p_mean;
+  ps.var = where == MRA_DEVICE ? var_out : h->p_var;
+  mra::Cov cv{theta->sigma2, theta->range, h->cfg.cov_family, h->cfg.nonstat};
+  if ((e = mra::launch_predict(shape_of(h), cv, h->st, h->lf, h->nlmax, ps, maxp, h->stream, &g_launches,
+                               &h->timer)))
+    return cuda_fail(e, "predict launch");
+  if (where == MRA_HOST) {
+    if ((e = cudaMemcpyAsync(mean_out, h->p_mean, sizeof(double) * np, cudaMemcpyDeviceToHost, h->stream)) ||
+        (e = cudaMemcpyAsync(var_out, h->p_var, sizeof(double) * np, cudaMemcpyDeviceToHost, h->stream)))
+      return cuda_fail(e, "copy predictions");
+  }
+  if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "predict");
+  collect_times(h);
+  return MRA_OK;
 }
 
 }  // extern "C"

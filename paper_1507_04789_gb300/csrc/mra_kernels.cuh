@@ -53,6 +53,17 @@ struct LeafState {
   double* u;              // 4^M: y_F' Sigma_F^{-1} y_F
 };
 
+// Prediction points of one mra_predict call, sorted by leaf.
+struct PredState {
+  const int64_t* off;     // 4^M + 1 offsets of the prediction points per leaf
+  const int64_t* perm;    // sorted position -> caller's index
+  const double* xs;
+  const double* ys;
+  double* U;              // np x (M r) scratch: Uhat, then the posterior basis Bhat
+  double* mean;           // np, caller's order
+  double* var;            // np, caller's order
+};
+
 struct Shape {
   int M, r, gx, gy;
   double bbox[4];

@@ -29,7 +29,7 @@ struct Timer {
 cudaError_t launch_bin(const double* locs, int64_t n, const double* bbox_dev, int M,
                        int32_t* leaf_id, int32_t* counts, int32_t* cursor, int64_t* off,
                        int64_t* sq_off, int32_t* max_count, int64_t* perm, int* status,
-                       cudaStream_t s, int64_t* launches);
+                       cudaStream_t s, int64_t* launches, bool stable = true);
 // Gather the sorted observations: xs, ys, yv from row-major locs (n x 2) and y.
 cudaError_t launch_gather(const double* locs, const double* y, const int64_t* perm, int64_t n,
                           double* xs, double* ys, double* yv, cudaStream_t s, int64_t* launches);
@@ -42,6 +42,11 @@ cudaError_t launch_loglik(const Shape& sh, const Cov& cv, double tau2, const Lev
                           const LeafState& lf, int nlmax, int* status, cudaStream_t s,
                           int64_t* launches, Timer* timer);
 size_t leaf_smem_bytes(int r, int nlmax);
+
+// Prediction (Sec. 3.4, Prop. 2) at points binned into ps.
+cudaError_t launch_predict(const Shape& sh, const Cov& cv, const LevelState& st, const LeafState& lf, int nlmax,
+                           const PredState& ps, int max_per_leaf, cudaStream_t s, int64_t* launches, Timer* tm);
+size_t predict_smem_bytes(int r, int nlmax);
 
 // Error text and launch counter shared by every entry point (mra_api.cu).
 void set_last_error(const char* msg);

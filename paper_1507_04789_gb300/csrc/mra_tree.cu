@@ -118,7 +118,7 @@ __global__ void gather_kernel(const double* __restrict__ locs, const double* __r
   int64_t p = perm[i];
   xs[i] = locs[2 * p];
   ys[i] = locs[2 * p + 1];
-  if (yv) yv[i] = y[p];
+  if (yv && y) yv[i] = y[p];
 }
 
 __global__ void gather_y_kernel(const double* __restrict__ y, const int64_t* __restrict__ perm, int64_t n,
@@ -133,7 +133,7 @@ static unsigned blocks_for(int64_t n) { return (unsigned)((n + 255) / 256); }
 cudaError_t launch_bin(const double* locs, int64_t n, const double* bbox_dev, int M,
                        int32_t* leaf_id, int32_t* counts, int32_t* cursor, int64_t* off,
                        int64_t* sq_off, int32_t* max_count, int64_t* perm, int* status,
-                       cudaStream_t s, int64_t* launches) {
+                       cudaStream_t s, int64_t* launches, bool stable) {
   const int64_t nl = int64_t(1) << (2 * M);
   cudaError_t e;
   if ((e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * nl, s))) return e;
@@ -141,8 +141,8 @@ cudaError_t launch_bin(const double* locs, int64_t n, const double* bbox_dev, in
   leaf_id_kernel<<<blocks_for(n), 256, 0, s>>>(locs, n, bbox_dev, M, leaf_id, counts, status);
   scan_kernel<<<1, 1024, 0, s>>>(counts, nl, off, sq_off, max_count);
   scatter_kernel<<<blocks_for(n), 256, 0, s>>>(leaf_id, n, off, cursor, perm);
-  segsort_kernel<<<(unsigned)nl, 256, 0, s>>>(off, perm, status);
-  *launches += 4;
+  if (stable) segsort_kernel<<<(unsigned)nl, 256, 0, s>>>(off, perm, status);
+  *launches += stable ? 4 : 3;
   return cudaGetLastError();
 }
 
