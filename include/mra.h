@@ -131,6 +131,21 @@ int mra_update(mra_handle* h, const double* locs, const double* y, int where);
 int mra_loglik(mra_handle* h, const mra_params* theta, double* loglik_out);
 
 /*
+ * mra_loglik_grad -- the log-likelihood (as mra_loglik) and its gradient
+ * d loglik / d(sigma2, range, tau2).  The paper gives no gradient; it serves
+ * the numerical maximum-likelihood fit of Sec. 4.3.  The gradient is the exact
+ * reverse-mode adjoint of the evaluation (Cholesky, triangular-solve and
+ * A-update chains of Sec. 3.1-3.2 in reverse), in FP64.
+ *   theta      : host pointer to one mra_params.
+ *   loglik_out : host pointer to one double.
+ *   grad_out   : host pointer to 3 doubles (d/dsigma2, d/drange, d/dtau2).
+ * The first call allocates the adjoint storage (about 4 n M r doubles plus the
+ * per-level adjoints); later calls allocate nothing.  Also leaves the posterior
+ * factors for mra_predict at theta.  Errors: as mra_loglik, and MRA_ERR_OOM.
+ */
+int mra_loglik_grad(mra_handle* h, const mra_params* theta, double* loglik_out, double* grad_out);
+
+/*
  * mra_predict -- marginal posterior predictive mean and variance of the
  * process y (not of the noisy data, Sec. 4.3) at np locations (Sec. 3.4,
  * Prop. 2, Eq. bfrecursion).  Uses the factors of the last mra_loglik, which
@@ -179,6 +194,7 @@ int mra_set_stream(mra_handle* h, void* stream);
 #define MRA_K_POST       3  /* posterior factorisation, one launch per level */
 #define MRA_K_AGGREGATE  4  /* child-to-parent updates (Eqs. mainquantities, helpquantities) */
 #define MRA_K_PREDICT    5  /* prediction (Sec. 3.4) */
+#define MRA_K_GRAD       6  /* reverse-mode gradient pass (all adjoint kernels) */
 int mra_enable_timing(mra_handle* h, int on);
 int mra_kernel_times(mra_handle* h, int kind, double* total_ms, int64_t* launches);
 

@@ -112,6 +112,11 @@ struct mra_handle {
   double *p_in = nullptr, *p_xs = nullptr, *p_ys = nullptr, *p_U = nullptr, *p_mean = nullptr, *p_var = nullptr;
   int32_t *p_leaf = nullptr, *p_counts = nullptr, *p_cursor = nullptr, *p_max = nullptr;
   int64_t *p_off = nullptr, *p_sq = nullptr, *p_perm = nullptr;
+  // gradient (arena 4, allocated by the first mra_loglik_grad)
+  Arena grad;
+  bool have_grad_arena = false;
+  mra::GradState gs{};
+  double* d_grad = nullptr;
   mra::Timer timer;
   bool timer_events = false;
   double ktime[8] = {0};
@@ -188,6 +193,7 @@ void mra_free(mra_handle* h) {
   h->tree.release();
   h->state.release();
   h->pred.release();
+  h->grad.release();
   if (h->pinned) cudaFreeHost(h->pinned);
   delete h;
 }
@@ -398,6 +404,79 @@ int mra_leaf_offsets(mra_handle* h, int64_t* off_out, int64_t* perm_out) {
   return MRA_OK;
 }
 
+static int ensure_grad_arena(mra_handle* h) {
+  if (h->have_grad_arena) return MRA_OK;
+  const int M = h->M, r = h->r;
+  const int64_t n = h->n, nl = int64_t(1) << (2 * M);
+  Arena& G = h->grad;
+  for (int m = 0; m < M; ++m) {
+    const int64_t R = int64_t(1) << (2 * m);
+    G.want(&h->st.L[m], R * r * r);
+    G.want(&h->st.Ltf[m], R * r * r);
+    G.want(&h->gs.Abar[m], R * r * (int64_t)(m + 1) * r);
+    G.want(&h->gs.Obar[m], R * r);
+    G.want(&h->gs.GB[m], R * r * (int64_t)m * r);
+    G.want(&h->gs.VB[m], R * r * (int64_t)m * r);
+    G.want(&h->gs.XB[m], R * r * (int64_t)m * r);
+    G.want(&h->gs.Up[m], R * (int64_t)m * (m + 1) / 2 * r * r);
+  }
+  if (M > 0) G.want(&h->gs.PartLeaf, (nl / 4) * (int64_t)M * (M + 1) / 2 * r * r);
+  G.want(&h->lf.VF, n * (int64_t)M * r);
+  G.want(&h->lf.LSf, (size_t)h->ls_cap);
+  G.want(&h->gs.HB, n * (int64_t)M * r);
+  G.want(&h->gs.VBF, n * (int64_t)M * r);
+  G.want(&h->gs.XBF, n * (int64_t)M * r);
+  G.want(&h->gs.T, 3 * (size_t)h->ls_cap);
+  int64_t slots = nl;
+  for (int m = 0; m < M; ++m) slots += int64_t(1) << (2 * m);
+  G.want(&h->gs.gpart, 3 * slots);
+  G.want(&h->d_grad, 4);
+  cudaError_t e = G.commit();
+  if (e) {
+    for (int m = 0; m < M; ++m) { h->st.L[m] = nullptr; h->st.Ltf[m] = nullptr; }
+    h->lf.VF = nullptr;
+    h->lf.LSf = nullptr;
+    return fail(MRA_ERR_OOM, "device allocation (gradient): %s", cudaGetErrorString(e));
+  }
+  h->have_grad_arena = true;
+  return MRA_OK;
+}
+
+int mra_loglik_grad(mra_handle* h, const mra_params* theta, double* loglik_out, double* grad_out) {
+  g_err.clear();
+  if (!h || !loglik_out || !grad_out) return fail(MRA_ERR_ARG, "null argument");
+  if (!params_ok(theta)) return fail(MRA_ERR_ARG, "theta needs sigma2 > 0, range > 0, tau2 >= 0, all finite");
+  int rc = ensure_grad_arena(h);
+  if (rc) return rc;
+  h->have_post = false;
+  mra::Cov cv{theta->sigma2, theta->range, h->cfg.cov_family, h->cfg.nonstat};
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream))) return cuda_fail(e, "memset");
+  if ((e = mra::launch_loglik(shape_of(h), cv, theta->tau2, h->st, h->lf, h->nlmax, h->status, h->stream,
+                              &g_launches, &h->timer)))
+    return cuda_fail(e, "loglik launch");
+  if ((e = mra::launch_grad(shape_of(h), cv, h->st, h->lf, h->gs, h->d_grad, h->stream, &g_launches, &h->timer)))
+    return cuda_fail(e, "gradient launch");
+  int hs[4];
+  double vals[5];
+  const double* srcs[5];
+  if (h->M > 0) { srcs[0] = h->st.dd[0]; srcs[1] = h->st.uu[0]; }
+  else { srcs[0] = h->lf.d; srcs[1] = h->lf.u; }
+  srcs[2] = h->d_grad;
+  srcs[3] = h->d_grad + 1;
+  srcs[4] = h->d_grad + 2;
+  if ((e = sync_status(h, hs, vals, 5, srcs))) return cuda_fail(e, "gradient");
+  collect_times(h);
+  if (hs[0]) return status_error(hs);
+  *loglik_out = -0.5 * (vals[0] + vals[1]) - 0.5 * (double)h->n * std::log(2.0 * M_PI);
+  grad_out[0] = vals[2];
+  grad_out[1] = vals[3];
+  grad_out[2] = vals[4];
+  h->have_post = true;
+  h->last = *theta;
+  return MRA_OK;
+}
+
 int mra_update(mra_handle* h, const double* locs, const double* y, int where) {
   g_err.clear();
   if (!h || !locs || !y) return fail(MRA_ERR_ARG, "null argument");
@@ -473,6 +552,7 @@ int mra_predict(mra_handle* h, const mra_params* theta, const double* plocs, int
   cudaError_t e;
   if (np > h->pred_cap) {
     h->pred.release();
+  h->grad.release();
     Arena& P = h->pred;
     P.want(&h->p_in, 2 * np);
     P.want(&h->p_xs, np);

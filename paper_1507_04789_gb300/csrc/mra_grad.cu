@@ -1,0 +1,676 @@
+// mra_grad.cu -- reverse-mode adjoint of the M-RA log-likelihood.
+//
+// The gradient d loglik / d(sigma2, kappa, tau2) is not in the paper (it
+// serves the likelihood-based inference of Sec. 3.3 and the maximum-likelihood
+// fit of Sec. 4.3).  It is the exact reverse of the whitened forward pass of
+// mra_loglik.cu, with symmetric adjoints S (d loglik = <S, dA> over the full
+// symmetric matrix) for every symmetric quantity and these rules:
+//   Cholesky  L = chol(A):    Abar = sym(L^{-T} Phi(L' Lbar) L^{-1}),
+//             Phi = lower triangle with the diagonal halved (Murray 2016);
+//   inverse   Li = L^{-1}:    Lbar = lower(-Li' Libar Li');
+//   products  Y = X Li':      Xbar = Ybar Li,  Libar += lower(Ybar' X);
+//   Gram      Ahat = H' H:    Hbar = 2 H S.
+// The kernels run in the reverse order of the forward pass:
+//   post_adjoint   m = 0..M-1  Ahat-adjoint row m and omegahat-adjoint of every
+//                              region (the rows of coarser levels are owned by
+//                              the ancestors, which are shared by all children)
+//   leaf_adjoint   level M     Hbar, Vbar_F, the Sigma_F adjoint (C0 and tau2
+//                              terms), the chain adjoint Xbar_F
+//   leaf_partial   level M-1   contributions of the leaves to the adjoints of
+//                              every ancestor's V and L^{-1}, summed per parent
+//   prior_adjoint  m = M-1..0  a region's own V / L^{-1} adjoints from the
+//                              partial sums of its children, its Cholesky
+//                              adjoint, its chain adjoint, and the partial sums
+//                              it passes up
+//   grad_reduce                the per-CTA sums of Cbar * dC0/dtheta
+// Every C0 evaluation whose adjoint Cbar is formed contributes
+// sum Cbar_ij dC0_ij/dtheta, with dC0/dsigma2 = C0 / sigma2 and dC0/dkappa in
+// closed form for both families.  Sums over children and rows are in a fixed
+// order: the gradient is deterministic.
+#include "mra_launch.h"
+
+namespace mra {
+
+// d C0 / d sigma2 and d C0 / d kappa at one pair of points.
+__device__ __forceinline__ void dcov0(const Cov& c, double x1, double y1, double x2, double y2, double& ds2,
+                                      double& dk) {
+  double dx = x1 - x2, dy = y1 - y2;
+  double h = sqrt(dx * dx + dy * dy) / c.kappa;
+  double rho, drho;   // rho(h/kappa) and kappa * d rho / d kappa
+  if (c.family == 0) {
+    rho = exp(-h);
+    drho = rho * h;
+  } else {
+    double a = SQRT3 * h;
+    double e = exp(-a);
+    rho = (1.0 + a) * e;
+    drho = a * a * e;
+  }
+  double gg = c.nonstat ? sqrt(gvar(x1) * gvar(x2)) : 1.0;
+  ds2 = rho * gg;
+  dk = c.sigma2 * drho * gg / c.kappa;
+}
+
+// Symmetric adjoint block (k, l) of region chain `anc` (ancestor index per
+// level): S^{k,l} is stored in the row of the level-max(k,l) ancestor.
+// Returns pointer and strides for B(j, kk) = S^{k,l}[kk][j].
+struct SRef {
+  const double* p;
+  long sj, sk;
+};
+__device__ __forceinline__ SRef sblock(const GradState& gs, const long* anc, int r, int k, int l) {
+  if (k >= l) {   // S^{k,l}[kk][j] = row k of ancestor k, block l
+    const long ld = (long)(k + 1) * r;
+    return {gs.Abar[k] + anc[k] * (long)r * ld + l * r, 1, ld};
+  }
+  const long ld = (long)(l + 1) * r;   // S^{k,l}[kk][j] = S^{l,k}[j][kk]
+  return {gs.Abar[l] + anc[l] * (long)r * ld + k * r, ld, 1};
+}
+
+template <int TILE>
+__device__ __forceinline__ void store_tile(const TileAcc<TILE>& acc, double* dst, long ld, int nr, int nc,
+                                           double scale) {
+#pragma unroll
+  for (int p = 0; p < TileAcc<TILE>::RM; ++p)
+#pragma unroll
+    for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
+      int row = acc.row(p), col = acc.col(q);
+      if (row < nr && col < nc) dst[(long)row * ld + col] = scale * acc.v[p][q];
+    }
+}
+
+// Phi(Y): lower triangle, halved diagonal, zero above (in place, square n).
+__device__ __forceinline__ void phi_inplace(double* Y, int n, long ld) {
+  for (int t = threadIdx.x; t < n * n; t += NT) {
+    int i = t / n, j = t - i * n;
+    if (j > i) Y[i * ld + j] = 0.0;
+    else if (j == i) Y[i * ld + j] *= 0.5;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void lower_inplace(double* Y, int n, long ld) {
+  for (int t = threadIdx.x; t < n * n; t += NT) {
+    int i = t / n, j = t - i * n;
+    if (j > i) Y[i * ld + j] = 0.0;
+  }
+  __syncthreads();
+}
+
+// Cholesky-factor adjoint chain shared by every level:
+//   given Ybar (adjoint of Li = L^{-1}, lower) in B0, L and Li (row-major n x n,
+//   global or shared), diag term dlog (adjoint of each log L_ii, 0 if none):
+//   Lbar = lower(-Li' Ybar Li') + dlog / L_ii;  S = sym(Li' Phi(L' Lbar) Li)
+// Result S in B2 (full, symmetric).  B0, B1, B2: n x ld shared buffers.
+template <int TILE>
+__device__ void chol_inverse_adjoint(double* B0, double* B1, double* B2, long ld, int n, const double* L, long ldl,
+                                     const double* Li, long ldi, double dlog, double* stg) {
+  TileAcc<TILE> acc;
+  const int nt = (n + TILE - 1) / TILE;
+  // B1 = Ybar Li'
+  for (int bi = 0; bi < nt; ++bi)
+    for (int bj = 0; bj < nt; ++bj) {
+      acc.zero();
+      tile_mma<TILE>(acc, B0 + bi * TILE * ld, ld, 1, min(TILE, n - bi * TILE), Li + bj * TILE * ldi, ldi, 1,
+                     min(TILE, n - bj * TILE), n, stg);
+      store_tile<TILE>(acc, B1 + bi * TILE * ld + bj * TILE, ld, min(TILE, n - bi * TILE), min(TILE, n - bj * TILE), 1.0);
+    }
+  __syncthreads();
+  // B2 = lower(-Li' B1) + dlog / L_ii
+  for (int bi = 0; bi < nt; ++bi)
+    for (int bj = 0; bj < nt; ++bj) {
+      acc.zero();
+      tile_mma<TILE>(acc, Li + bi * TILE, 1, ldi, min(TILE, n - bi * TILE), B1 + bj * TILE, 1, ld,
+                     min(TILE, n - bj * TILE), n, stg);
+      store_tile<TILE>(acc, B2 + bi * TILE * ld + bj * TILE, ld, min(TILE, n - bi * TILE), min(TILE, n - bj * TILE), -1.0);
+    }
+  __syncthreads();
+  lower_inplace(B2, n, ld);
+  if (dlog != 0.0)
+    for (int t = threadIdx.x; t < n; t += NT) B2[t * ld + t] += dlog / L[t * ldl + t];
+  __syncthreads();
+  // B0 = Phi(L' B2)
+  for (int bi = 0; bi < nt; ++bi)
+    for (int bj = 0; bj < nt; ++bj) {
+      acc.zero();
+      tile_mma<TILE>(acc, L + bi * TILE, 1, ldl, min(TILE, n - bi * TILE), B2 + bj * TILE, 1, ld,
+                     min(TILE, n - bj * TILE), n, stg);
+      store_tile<TILE>(acc, B0 + bi * TILE * ld + bj * TILE, ld, min(TILE, n - bi * TILE), min(TILE, n - bj * TILE), 1.0);
+    }
+  __syncthreads();
+  phi_inplace(B0, n, ld);
+  // B1 = B0 Li
+  for (int bi = 0; bi < nt; ++bi)
+    for (int bj = 0; bj < nt; ++bj) {
+      acc.zero();
+      tile_mma<TILE>(acc, B0 + bi * TILE * ld, ld, 1, min(TILE, n - bi * TILE), Li + bj * TILE, 1, ldi,
+                     min(TILE, n - bj * TILE), n, stg);
+      store_tile<TILE>(acc, B1 + bi * TILE * ld + bj * TILE, ld, min(TILE, n - bi * TILE), min(TILE, n - bj * TILE), 1.0);
+    }
+  __syncthreads();
+  // B2 = Li' B1, then symmetrise in place
+  for (int bi = 0; bi < nt; ++bi)
+    for (int bj = 0; bj < nt; ++bj) {
+      acc.zero();
+      tile_mma<TILE>(acc, Li + bi * TILE, 1, ldi, min(TILE, n - bi * TILE), B1 + bj * TILE, 1, ld,
+                     min(TILE, n - bj * TILE), n, stg);
+      store_tile<TILE>(acc, B2 + bi * TILE * ld + bj * TILE, ld, min(TILE, n - bi * TILE), min(TILE, n - bj * TILE), 1.0);
+    }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += NT) {
+    int i = t / n, j = t - i * n;
+    if (j < i) {
+      double v = 0.5 * (B2[i * ld + j] + B2[j * ld + i]);
+      B2[i * ld + j] = v;
+      B2[j * ld + i] = v;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Posterior adjoint, level m (top-down).
+// ---------------------------------------------------------------------------
+template <int TILE>
+__global__ void __launch_bounds__(NT) post_adjoint_kernel(int m, Shape sh, LevelState st, GradState gs) {
+  extern __shared__ double smem[];
+  const int r = sh.r, mr = m * r;
+  const long i = blockIdx.x;
+  const long ld = r + 1;
+  double* wbar = smem;                       // m r: omega~ adjoint (from ancestors)
+  double* gbar = wbar + MAXL * MAX_R_DEV;    // r
+  double* B0 = gbar + MAX_R_DEV;
+  double* B1 = B0 + MAX_R_DEV * (MAX_R_DEV + 1);
+  double* B2 = B1 + MAX_R_DEV * (MAX_R_DEV + 1);
+  double* stg = B2 + MAX_R_DEV * (MAX_R_DEV + 1);
+  long anc[MAXL];
+  for (int l = 0; l <= m; ++l) anc[l] = i >> (2 * (m - l));
+  for (int t = threadIdx.x; t < mr; t += NT) {
+    int k = t / r;
+    wbar[t] = gs.Obar[k][anc[k] * r + (t - k * r)];
+  }
+  __syncthreads();
+  const double* G = st.G[m] + i * (long)r * mr;
+  const double* g = st.gv[m] + i * r;
+  const int T = (m + 1) * (m + 2) / 2;
+  const double* A = st.Acc[m] + i * (long)T * r * r;
+  // gbar = g - G omega~bar
+  for (int q = threadIdx.x; q < r; q += NT) {
+    double s = g[q];
+    for (int c = 0; c < mr; ++c) s = fma(-G[(long)q * mr + c], wbar[c], s);
+    gbar[q] = s;
+  }
+  // Gbar^l = -2 sum_k G^k S^{k,l} - g omega~bar^l'   -> gs.GB
+  double* GB = gs.GB[m] + i * (long)r * mr;
+  TileAcc<TILE> acc;
+  for (int l = 0; l < m; ++l) {
+    acc.zero();
+    for (int k = 0; k < m; ++k) {
+      SRef b = sblock(gs, anc, r, k, l);
+      tile_mma<TILE>(acc, G + k * r, mr, 1, r, b.p, b.sj, b.sk, r, r, stg);
+    }
+#pragma unroll
+    for (int p = 0; p < TileAcc<TILE>::RM; ++p)
+#pragma unroll
+      for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
+        int row = acc.row(p), col = acc.col(q);
+        if (row < r && col < r) GB[(long)row * mr + l * r + col] = -2.0 * acc.v[p][q] - g[row] * wbar[l * r + col];
+      }
+  }
+  __syncthreads();
+  // Ltbar = sum_l Gbar^l (Ahat^{m,l})' + gbar omegahat^m'   -> B0 (lower)
+  const double* om = st.Om[m] + (i * (m + 1) + m) * (long)r;
+  acc.zero();
+  for (int l = 0; l < m; ++l)
+    tile_mma<TILE>(acc, GB + l * r, mr, 1, r, A + (long)tri_index(m, l) * r * r, r, 1, r, r, stg);
+#pragma unroll
+  for (int p = 0; p < TileAcc<TILE>::RM; ++p)
+#pragma unroll
+    for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
+      int row = acc.row(p), col = acc.col(q);
+      if (row < r && col < r) B0[row * ld + col] = row >= col ? acc.v[p][q] + gbar[row] * om[col] : 0.0;
+    }
+  __syncthreads();
+  const double* Ltf = st.Ltf[m] + i * (long)r * r;   // Cholesky factor of I + Ahat^{m,m}
+  const double* Lti = st.Lt[m] + i * (long)r * r;    // its inverse
+  // S^{m,m} = sym(Lti' Phi(Ltf' Lbar) Lti), Lbar = lower(-Lti' Ltbar Lti') - 1 / Ltf_ii
+  chol_inverse_adjoint<TILE>(B0, B1, B2, ld, r, Ltf, r, Lti, r, -1.0, stg);
+  double* Ab = gs.Abar[m] + i * (long)r * (mr + r);
+  for (int t = threadIdx.x; t < r * r; t += NT) {
+    int a = t / r, b = t - a * r;
+    Ab[(long)a * (mr + r) + mr + b] = B2[a * ld + b];
+  }
+  // S^{m,l} = 1/2 Lti' Gbar^l
+  for (int l = 0; l < m; ++l) {
+    acc.zero();
+    tile_mma<TILE>(acc, Lti, 1, r, r, GB + l * r, 1, mr, r, r, stg);
+    store_tile<TILE>(acc, Ab + l * r, mr + r, r, r, 0.5);
+  }
+  // omegahat^m bar = Lti' gbar
+  for (int q = threadIdx.x; q < r; q += NT) {
+    double s = 0.0;
+    for (int c = q; c < r; ++c) s = fma(Lti[(long)c * r + q], gbar[c], s);
+    gs.Obar[m][i * r + q] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Leaf adjoint: one CTA per leaf.
+// ---------------------------------------------------------------------------
+template <int TILE>
+__global__ void __launch_bounds__(NT) leaf_adjoint_kernel(Shape sh, Cov cv, LevelState st, LeafState lf,
+                                                          GradState gs, long slot0) {
+  extern __shared__ double smem[];
+  const int M = sh.M, r = sh.r, Mr = M * r;
+  const long F = blockIdx.x;
+  const long o0 = lf.off[F];
+  const int nF = (int)(lf.off[F + 1] - o0);
+  double* wbar = smem;                      // M r
+  double* zb = wbar + MAXL * MAX_R_DEV;     // nF (<= MAX_LEAF)
+  double* sx = zb + 128;
+  double* sy = sx + 128;
+  double* ax = sy + 128;
+  double* ay = ax + MAX_R_DEV;
+  double* red = ay + MAX_R_DEV;
+  double* stg = red + 32;
+  double g_s2 = 0.0, g_k = 0.0, g_t = 0.0;
+  if (nF > 0) {
+    long anc[MAXL];
+    for (int l = 0; l < M; ++l) anc[l] = F >> (2 * (M - l));
+    for (int t = threadIdx.x; t < Mr; t += NT) {
+      int k = t / r;
+      wbar[t] = gs.Obar[k][anc[k] * r + (t - k * r)];
+    }
+    for (int t = threadIdx.x; t < nF; t += NT) {
+      sx[t] = lf.xs[o0 + t];
+      sy[t] = lf.ys[o0 + t];
+    }
+    __syncthreads();
+    const double* H = lf.H + o0 * Mr;
+    const double* VF = lf.VF + o0 * Mr;
+    const double* z = lf.z + o0;
+    const double* yv = lf.yv + o0;
+    double* HB = gs.HB + o0 * Mr;
+    double* VB = gs.VBF + o0 * Mr;
+    double* XB = gs.XBF + o0 * Mr;
+    const double* LSi = lf.LS + lf.sq_off[F];
+    const double* LSf = lf.LSf + lf.sq_off[F];
+    double* T1 = gs.T + 3 * lf.sq_off[F];     // three nF x nF scratch blocks per leaf
+    double* T2 = T1 + (long)nF * nF;
+    double* T3 = T2 + (long)nF * nF;
+    const int nrt = (nF + TILE - 1) / TILE;
+    TileAcc<TILE> acc;
+    // Hbar = 2 H S_p + z omegabar'
+    for (int rt = 0; rt < nrt; ++rt) {
+      const int nrow = min(TILE, nF - rt * TILE);
+      for (int l = 0; l < M; ++l) {
+        acc.zero();
+        for (int k = 0; k < M; ++k) {
+          SRef b = sblock(gs, anc, r, k, l);
+          tile_mma<TILE>(acc, H + (long)rt * TILE * Mr + k * r, Mr, 1, nrow, b.p, b.sj, b.sk, r, r, stg);
+        }
+#pragma unroll
+        for (int p = 0; p < TileAcc<TILE>::RM; ++p)
+#pragma unroll
+          for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
+            int row = acc.row(p), col = acc.col(q);
+            if (row < nrow && col < r) {
+              int o = rt * TILE + row;
+              HB[(long)o * Mr + l * r + col] = 2.0 * acc.v[p][q] + z[o] * wbar[l * r + col];
+            }
+          }
+      }
+    }
+    // zbar = H omegabar - z
+    for (int t = threadIdx.x; t < nF; t += NT) {
+      double s = -z[t];
+      for (int c = 0; c < Mr; ++c) s = fma(H[(long)t * Mr + c], wbar[c], s);
+      zb[t] = s;
+    }
+    __syncthreads();
+    // Vbar_F = LSi' Hbar
+    for (int l = 0; l < M; ++l)
+      for (int rt = 0; rt < nrt; ++rt) {
+        const int nrow = min(TILE, nF - rt * TILE);
+        acc.zero();
+        tile_mma<TILE>(acc, LSi + rt * TILE, 1, nF, nrow, HB + l * r, 1, Mr, r, nF, stg);
+        store_tile<TILE>(acc, VB + (long)rt * TILE * Mr + l * r, Mr, nrow, r, 1.0);
+      }
+    // LSibar = lower(Hbar V_F' + zbar y')  -> T1
+    for (int bi = 0; bi < nrt; ++bi)
+      for (int bj = 0; bj <= bi; ++bj) {
+        const int ni = min(TILE, nF - bi * TILE), nj = min(TILE, nF - bj * TILE);
+        acc.zero();
+        tile_mma<TILE>(acc, HB + (long)bi * TILE * Mr, Mr, 1, ni, VF + (long)bj * TILE * Mr, Mr, 1, nj, Mr, stg);
+#pragma unroll
+        for (int p = 0; p < TileAcc<TILE>::RM; ++p)
+#pragma unroll
+          for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
+            int row = acc.row(p), col = acc.col(q);
+            if (row < ni && col < nj) {
+              int oi = bi * TILE + row, oj = bj * TILE + col;
+              T1[(long)oi * nF + oj] = oi >= oj ? acc.v[p][q] + zb[oi] * yv[oj] : 0.0;
+            }
+          }
+        if (bj < bi) {   // zero the mirrored upper block
+          for (int t = threadIdx.x; t < nj * ni; t += NT) {
+            int a = t / ni, b = t - a * ni;
+            T1[(long)(bj * TILE + a) * nF + bi * TILE + b] = 0.0;
+          }
+        }
+      }
+    __syncthreads();
+    // Cholesky/inverse adjoint of Sigma_F in the leaf's global scratch: T3 = Sigmabar
+    chol_inverse_adjoint<TILE>(T1, T2, T3, nF, nF, LSf, nF, LSi, nF, -1.0, stg);
+    // T3 = Sigmabar (symmetric): C0 and tau2 terms
+    for (int t = threadIdx.x; t < nF * nF; t += NT) {
+      int a = t / nF, b = t - a * nF;
+      double sb = T3[t];
+      double d1, d2;
+      dcov0(cv, sx[a], sy[a], sx[b], sy[b], d1, d2);
+      g_s2 = fma(sb, d1, g_s2);
+      g_k = fma(sb, d2, g_k);
+      if (a == b) g_t += sb;
+    }
+    // Vbar_F -= 2 Sigmabar V_F
+    for (int l = 0; l < M; ++l)
+      for (int rt = 0; rt < nrt; ++rt) {
+        const int nrow = min(TILE, nF - rt * TILE);
+        acc.zero();
+        tile_mma<TILE>(acc, T3 + (long)rt * TILE * nF, nF, 1, nrow, VF + l * r, 1, Mr, r, nF, stg);
+#pragma unroll
+        for (int p = 0; p < TileAcc<TILE>::RM; ++p)
+#pragma unroll
+          for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
+            int row = acc.row(p), col = acc.col(q);
+            if (row < nrow && col < r) VB[(long)(rt * TILE + row) * Mr + l * r + col] -= 2.0 * acc.v[p][q];
+          }
+      }
+    __syncthreads();
+    // chain adjoint, l = M-1..0: Xbar^l = Vbar^l Li_a ; Vbar^k -= Xbar^l V^k_a (k < l)
+    for (int l = M - 1; l >= 0; --l) {
+      const long a = anc[l];
+      const double* Lia = st.Li[l] + a * (long)r * r;
+      const double* Va = st.V[l] + a * (long)r * (l * r);
+      __syncthreads();
+      load_knots(sh.bbox, l, a, sh.gx, sh.gy, ax, ay);
+      __syncthreads();
+      for (int rt = 0; rt < nrt; ++rt) {
+        const int nrow = min(TILE, nF - rt * TILE);
+        acc.zero();
+        tile_mma<TILE>(acc, VB + (long)rt * TILE * Mr + l * r, Mr, 1, nrow, Lia, 1, r, r, r, stg);
+#pragma unroll
+        for (int p = 0; p < TileAcc<TILE>::RM; ++p)
+#pragma unroll
+          for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
+            int row = acc.row(p), col = acc.col(q);
+            if (row < nrow && col < r) {
+              int o = rt * TILE + row;
+              double xb = acc.v[p][q];
+              XB[(long)o * Mr + l * r + col] = xb;
+              double d1, d2;
+              dcov0(cv, sx[o], sy[o], ax[col], ay[col], d1, d2);
+              g_s2 = fma(xb, d1, g_s2);
+              g_k = fma(xb, d2, g_k);
+            }
+          }
+      }
+      __syncthreads();
+      for (int k = 0; k < l; ++k)
+        for (int rt = 0; rt < nrt; ++rt) {
+          const int nrow = min(TILE, nF - rt * TILE);
+          acc.zero();
+          tile_mma<TILE>(acc, XB + (long)rt * TILE * Mr + l * r, Mr, 1, nrow, Va + k * r, 1, l * r, r, r, stg);
+#pragma unroll
+          for (int p = 0; p < TileAcc<TILE>::RM; ++p)
+#pragma unroll
+            for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
+              int row = acc.row(p), col = acc.col(q);
+              if (row < nrow && col < r) VB[(long)(rt * TILE + row) * Mr + k * r + col] -= acc.v[p][q];
+            }
+        }
+    }
+  }
+  g_s2 = block_sum(g_s2, red);
+  g_k = block_sum(g_k, red);
+  g_t = block_sum(g_t, red);
+  if (threadIdx.x == 0) {
+    gs.gpart[3 * (slot0 + F) + 0] = g_s2;
+    gs.gpart[3 * (slot0 + F) + 1] = g_k;
+    gs.gpart[3 * (slot0 + F) + 2] = g_t;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Leaf partials: parent p (level M-1), packed tile t = (l, k), k <= l <= M-1:
+//   k < l : -sum_rows Xbar^l' V^k      (adjoint of V^k of the level-l ancestor)
+//   k = l :  sum_rows Vbar^l' V^l      (times L_l' at the ancestor: adjoint of L_l^{-1})
+// ---------------------------------------------------------------------------
+template <int TILE>
+__global__ void __launch_bounds__(NT) leaf_partial_kernel(Shape sh, LeafState lf, GradState gs) {
+  extern __shared__ double smem[];
+  const int M = sh.M, r = sh.r, Mr = M * r;
+  const long p = blockIdx.x;
+  const int t = blockIdx.y;
+  int l = 0;
+  while (tri_index(l + 1, 0) <= t) ++l;
+  const int k = t - tri_index(l, 0);
+  const long row0 = lf.off[4 * p], row1 = lf.off[4 * p + 4];
+  const int K = (int)(row1 - row0);
+  const double* Ab = (k < l ? gs.XBF : gs.VBF) + row0 * Mr + l * r;
+  const double* Bb = lf.VF + row0 * Mr + k * r;
+  TileAcc<TILE> acc;
+  acc.zero();
+  tile_mma<TILE>(acc, Ab, 1, Mr, r, Bb, 1, Mr, r, K, smem);
+  const int T = M * (M + 1) / 2;
+  store_tile<TILE>(acc, gs.PartLeaf + (p * T + t) * (long)r * r, r, r, r, k < l ? -1.0 : 1.0);
+}
+
+// ---------------------------------------------------------------------------
+// Prior adjoint, level m (bottom-up): one CTA per region.
+// ---------------------------------------------------------------------------
+template <int TILE>
+__global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, Shape sh, Cov cv, LevelState st, GradState gs,
+                                                           long slot0) {
+  extern __shared__ double smem[];
+  const int r = sh.r, mr = m * r;
+  const long i = blockIdx.x;
+  const long ld = r + 1;
+  double* qx = smem;
+  double* qy = qx + MAX_R_DEV;
+  double* ax = qy + MAX_R_DEV;
+  double* ay = ax + MAX_R_DEV;
+  double* red = ay + MAX_R_DEV;
+  double* B0 = red + 32;
+  double* B1 = B0 + MAX_R_DEV * (MAX_R_DEV + 1);
+  double* B2 = B1 + MAX_R_DEV * (MAX_R_DEV + 1);
+  double* stg = B2 + MAX_R_DEV * (MAX_R_DEV + 1);
+  const bool from_leaves = (m + 1 == sh.M);
+  const int Tin = (m + 1) * (m + 2) / 2;   // incoming tiles, l <= m
+  // incoming tile (l, k): sum over children (fixed order)
+  auto incoming = [&](int l, int k, int a, int b) -> double {
+    const long t = tri_index(l, k);
+    if (from_leaves) return gs.PartLeaf[(i * Tin + t) * (long)r * r + a * r + b];
+    double s = 0.0;
+    for (int c = 0; c < 4; ++c) s += gs.Up[m + 1][((4 * i + c) * Tin + t) * (long)r * r + a * r + b];
+    return s;
+  };
+  double g_s2 = 0.0, g_k = 0.0;
+  load_knots(sh.bbox, m, i, sh.gx, sh.gy, qx, qy);
+  const double* L = st.L[m] + i * (long)r * r;
+  const double* Li = st.Li[m] + i * (long)r * r;
+  const double* V = st.V[m] + i * (long)r * mr;
+  // Libar = lower(incoming(m, m) L')  -> B0   (the adjoint of L^{-1} gathered from the subtree)
+  for (int t = threadIdx.x; t < r * r; t += NT) {
+    int a = t / r, b = t - a * r;
+    B1[a * ld + b] = incoming(m, m, a, b);
+  }
+  __syncthreads();
+  TileAcc<TILE> acc;
+  acc.zero();
+  tile_mma<TILE>(acc, B1, ld, 1, r, L, r, 1, r, r, stg);
+#pragma unroll
+  for (int p = 0; p < TileAcc<TILE>::RM; ++p)
+#pragma unroll
+    for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
+      int row = acc.row(p), col = acc.col(q);
+      if (row < r && col < r) B0[row * ld + col] = row >= col ? acc.v[p][q] : 0.0;
+    }
+  __syncthreads();
+  chol_inverse_adjoint<TILE>(B0, B1, B2, ld, r, L, r, Li, r, 0.0, stg);   // B2 = Wbar
+  for (int t = threadIdx.x; t < r * r; t += NT) {
+    int a = t / r, b = t - a * r;
+    double d1, d2;
+    dcov0(cv, qx[a], qy[a], qx[b], qy[b], d1, d2);
+    g_s2 = fma(B2[a * ld + b], d1, g_s2);
+    g_k = fma(B2[a * ld + b], d2, g_k);
+  }
+  double* VB = gs.VB[m] + i * (long)r * mr;
+  double* XB = gs.XB[m] + i * (long)r * mr;
+  // Vbar^k = incoming(m, k) - 2 Wbar V^k
+  for (int k = 0; k < m; ++k) {
+    acc.zero();
+    tile_mma<TILE>(acc, B2, ld, 1, r, V + k * r, 1, mr, r, r, stg);
+#pragma unroll
+    for (int p = 0; p < TileAcc<TILE>::RM; ++p)
+#pragma unroll
+      for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
+        int row = acc.row(p), col = acc.col(q);
+        if (row < r && col < r) VB[(long)row * mr + k * r + col] = incoming(m, k, row, col) - 2.0 * acc.v[p][q];
+      }
+  }
+  // chain adjoint
+  for (int l = m - 1; l >= 0; --l) {
+    const long a = i >> (2 * (m - l));
+    const double* Lia = st.Li[l] + a * (long)r * r;
+    const double* Va = st.V[l] + a * (long)r * (l * r);
+    __syncthreads();
+    load_knots(sh.bbox, l, a, sh.gx, sh.gy, ax, ay);
+    __syncthreads();
+    acc.zero();
+    tile_mma<TILE>(acc, VB + l * r, mr, 1, r, Lia, 1, r, r, r, stg);
+#pragma unroll
+    for (int p = 0; p < TileAcc<TILE>::RM; ++p)
+#pragma unroll
+      for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
+        int row = acc.row(p), col = acc.col(q);
+        if (row < r && col < r) {
+          double xb = acc.v[p][q];
+          XB[(long)row * mr + l * r + col] = xb;
+          double d1, d2;
+          dcov0(cv, qx[row], qy[row], ax[col], ay[col], d1, d2);
+          g_s2 = fma(xb, d1, g_s2);
+          g_k = fma(xb, d2, g_k);
+        }
+      }
+    __syncthreads();
+    for (int k = 0; k < l; ++k) {
+      acc.zero();
+      tile_mma<TILE>(acc, XB + l * r, mr, 1, r, Va + k * r, 1, l * r, r, r, stg);
+#pragma unroll
+      for (int p = 0; p < TileAcc<TILE>::RM; ++p)
+#pragma unroll
+        for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
+          int row = acc.row(p), col = acc.col(q);
+          if (row < r && col < r) VB[(long)row * mr + k * r + col] -= acc.v[p][q];
+        }
+    }
+  }
+  __syncthreads();
+  // partial sums passed up: tiles (l, k), k <= l < m
+  if (m > 0) {
+    const int Tup = m * (m + 1) / 2;
+    double* Up = gs.Up[m] + i * (long)Tup * r * r;
+    for (int l = 0; l < m; ++l)
+      for (int k = 0; k <= l; ++k) {
+        acc.zero();
+        const double* Ab = (k < l ? XB : VB) + l * r;
+        tile_mma<TILE>(acc, Ab, 1, mr, r, V + k * r, 1, mr, r, r, stg);
+        double* out = Up + (long)tri_index(l, k) * r * r;
+        const double sgn = k < l ? -1.0 : 1.0;
+#pragma unroll
+        for (int p = 0; p < TileAcc<TILE>::RM; ++p)
+#pragma unroll
+          for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
+            int row = acc.row(p), col = acc.col(q);
+            if (row < r && col < r) out[row * r + col] = incoming(l, k, row, col) + sgn * acc.v[p][q];
+          }
+      }
+  }
+  g_s2 = block_sum(g_s2, red);
+  g_k = block_sum(g_k, red);
+  if (threadIdx.x == 0) {
+    gs.gpart[3 * (slot0 + i) + 0] = g_s2;
+    gs.gpart[3 * (slot0 + i) + 1] = g_k;
+    gs.gpart[3 * (slot0 + i) + 2] = 0.0;
+  }
+}
+
+// Sum of the per-CTA partial gradients (fixed assignment: deterministic).
+__global__ void __launch_bounds__(NT) grad_reduce_kernel(const double* gpart, long nslots, double* out) {
+  __shared__ double red[32];
+  for (int c = 0; c < 3; ++c) {
+    double s = 0.0;
+    for (long t = threadIdx.x; t < nslots; t += NT) s += gpart[3 * t + c];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[c] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+static int tile_of(int r) { return r <= 16 ? 16 : (r <= 32 ? 32 : 64); }
+
+#define MRA_GRAD_LAUNCH(tile, KERNEL, grid, smem, stream, ...)                                          \
+  do {                                                                                                  \
+    if ((tile) == 16) {                                                                                 \
+      if ((e = cudaFuncSetAttribute(KERNEL<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem)))) return e; \
+      KERNEL<16><<<grid, NT, smem, stream>>>(__VA_ARGS__);                                              \
+    } else if ((tile) == 32) {                                                                          \
+      if ((e = cudaFuncSetAttribute(KERNEL<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem)))) return e; \
+      KERNEL<32><<<grid, NT, smem, stream>>>(__VA_ARGS__);                                              \
+    } else {                                                                                            \
+      if ((e = cudaFuncSetAttribute(KERNEL<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smem)))) return e; \
+      KERNEL<64><<<grid, NT, smem, stream>>>(__VA_ARGS__);                                              \
+    }                                                                                                   \
+  } while (0)
+
+cudaError_t launch_grad(const Shape& sh, const Cov& cv, const LevelState& st, const LeafState& lf,
+                        const GradState& gs, double* grad_out_dev, cudaStream_t s, int64_t* launches, Timer* tm) {
+  const int tile = tile_of(sh.r);
+  const int M = sh.M;
+  cudaError_t e;
+  const size_t stg = sizeof(double) * 2 * KC * (tile + 2);
+  const size_t sq = sizeof(double) * 3 * MAX_R_DEV * (MAX_R_DEV + 1);
+  // slots: prior-adjoint CTAs of levels 0..M-1, then the leaves
+  long slot_leaf = 0;
+  for (int m = 0; m < M; ++m) slot_leaf += 1L << (2 * m);
+  tm->start(6, s);
+  for (int m = 0; m < M; ++m) {
+    size_t sm = sizeof(double) * (MAXL * MAX_R_DEV + MAX_R_DEV) + sq + stg;
+    MRA_GRAD_LAUNCH(tile, post_adjoint_kernel, dim3(1u << (2 * m)), sm, s, m, sh, st, gs);
+    ++*launches;
+  }
+  {
+    size_t sm = sizeof(double) * (MAXL * MAX_R_DEV + 3 * 128 + 2 * MAX_R_DEV + 32) + stg;
+    MRA_GRAD_LAUNCH(tile, leaf_adjoint_kernel, dim3(1u << (2 * M)), sm, s, sh, cv, st, lf, gs, slot_leaf);
+    ++*launches;
+  }
+  if (M > 0) {
+    dim3 grid(1u << (2 * (M - 1)), M * (M + 1) / 2);
+    MRA_GRAD_LAUNCH(tile, leaf_partial_kernel, grid, stg, s, sh, lf, gs);
+    ++*launches;
+  }
+  long slot = slot_leaf;
+  for (int m = M - 1; m >= 0; --m) {
+    slot -= 1L << (2 * m);
+    size_t sm = sizeof(double) * (4 * MAX_R_DEV + 32) + sq + stg;
+    MRA_GRAD_LAUNCH(tile, prior_adjoint_kernel, dim3(1u << (2 * m)), sm, s, m, sh, cv, st, gs, slot);
+    ++*launches;
+  }
+  grad_reduce_kernel<<<1, NT, 0, s>>>(gs.gpart, slot_leaf + (1L << (2 * M)), grad_out_dev);
+  ++*launches;
+  tm->stop(s);
+  return cudaGetLastError();
+}
+
+}  // namespace mra

@@ -38,6 +38,9 @@ struct LevelState {
   double* gv[MAXL];   // 4^m x r: g = Lt^{-1} omegahat^m
   double* dd[MAXL];   // 4^m: d_R (Sec. 3.3)
   double* uu[MAXL];   // 4^m: u_R
+  // saved for the gradient (null when no gradient is requested)
+  double* L[MAXL];    // 4^m x r x r: L_R (prior Cholesky factor)
+  double* Ltf[MAXL];  // 4^m x r x r: Lt (Cholesky factor of I + Ahat^{m,m})
 };
 
 struct LeafState {
@@ -51,6 +54,25 @@ struct LeafState {
   double* LS;             // ragged n_F x n_F: L_Sigma^{-1}
   double* d;              // 4^M: log|Sigma_F|
   double* u;              // 4^M: y_F' Sigma_F^{-1} y_F
+  // saved for the gradient (null when no gradient is requested)
+  double* VF;             // n x (M r): V_F before the L_Sigma^{-1} solve
+  double* LSf;            // ragged n_F x n_F: L_Sigma
+};
+
+// Adjoint state of the gradient pass (mra_grad.cu).
+struct GradState {
+  double* Abar[MAXL];   // 4^m x r x (m+1) r: row m of the symmetric adjoint of Ahat
+  double* Obar[MAXL];   // 4^m x r: adjoint of omegahat^m
+  double* GB[MAXL];     // 4^m x r x (m r): adjoint of G
+  double* VB[MAXL];     // 4^m x r x (m r): adjoint of V_R
+  double* XB[MAXL];     // 4^m x r x (m r): adjoint of the chain blocks X^l_R
+  double* Up[MAXL];     // 4^m x m(m+1)/2 x r x r: ancestor adjoints passed up from level m
+  double* PartLeaf;     // 4^(M-1) x M(M+1)/2 x r x r: ancestor adjoints from the leaves
+  double* HB;           // n x (M r): adjoint of H
+  double* VBF;          // n x (M r): adjoint of V_F
+  double* XBF;          // n x (M r): adjoint of X^l_F
+  double* T;            // ragged 3 n_F^2 per leaf: scratch of the leaf adjoint
+  double* gpart;        // 3 per CTA: partial d/d(sigma2, kappa, tau2)
 };
 
 // Prediction points of one mra_predict call, sorted by leaf.

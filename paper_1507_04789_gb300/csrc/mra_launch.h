@@ -48,6 +48,10 @@ cudaError_t launch_predict(const Shape& sh, const Cov& cv, const LevelState& st,
                            const PredState& ps, int max_per_leaf, cudaStream_t s, int64_t* launches, Timer* tm);
 size_t predict_smem_bytes(int r, int nlmax);
 
+// Reverse-mode gradient after a forward pass that saved L, Lt, V_F and L_Sigma.
+cudaError_t launch_grad(const Shape& sh, const Cov& cv, const LevelState& st, const LeafState& lf,
+                        const GradState& gs, double* grad_out_dev, cudaStream_t s, int64_t* launches, Timer* tm);
+
 // Error text and launch counter shared by every entry point (mra_api.cu).
 void set_last_error(const char* msg);
 int64_t* launch_counter();

@@ -77,6 +77,11 @@ __global__ void __launch_bounds__(NT) prior_level_kernel(int m, Shape sh, Cov cv
       if (row < r && col < r) W[row * ldw + col] = cov0(cv, qx[row], qy[row], qx[col], qy[col]) - acc.v[p][q];
     }
   chol_smem(W, r, ldw, &bad);
+  if (st.L[m]) {
+    double* Lr = st.L[m] + i * (long)r * r;
+    for (int t = threadIdx.x; t < r * r; t += NT) Lr[t] = W[(t / r) * ldw + (t % r)];
+    __syncthreads();
+  }
   trinv_smem(W, r, ldw, tmp);
   double* Li = st.Li[m] + i * (long)r * r;
   for (int t = threadIdx.x; t < r * r; t += NT) Li[t] = W[(t / r) * ldw + (t % r)];
@@ -180,6 +185,13 @@ __global__ void __launch_bounds__(NT) leaf_kernel(Shape sh, Cov cv, double tau2,
   double ld = 0.0;
   for (int t = threadIdx.x; t < nF; t += NT) ld += log(S[t * lds + t]);
   ld = 2.0 * block_sum(ld, red);
+  if (lf.LSf) {
+    double* Lf = lf.LSf + lf.sq_off[F];
+    for (int t = threadIdx.x; t < nF * nF; t += NT) Lf[t] = S[(t / nF) * lds + (t % nF)];
+  }
+  if (lf.VF) {
+    for (long t = threadIdx.x; t < (long)nF * Mr; t += NT) lf.VF[o0 * Mr + t] = Hrow[t];
+  }
   trinv_smem(S, nF, lds, tmp);
   double* LS = lf.LS + lf.sq_off[F];
   for (int t = threadIdx.x; t < nF * nF; t += NT) LS[t] = S[(t / nF) * lds + (t % nF)];
@@ -286,6 +298,11 @@ __global__ void __launch_bounds__(NT) post_level_kernel(int m, Shape sh, LevelSt
   double ld = 0.0;
   for (int t = threadIdx.x; t < r; t += NT) ld += log(W[t * ldw + t]);
   ld = 2.0 * block_sum(ld, red);
+  if (st.Ltf[m]) {
+    double* Lf = st.Ltf[m] + i * (long)r * r;
+    for (int t = threadIdx.x; t < r * r; t += NT) Lf[t] = W[(t / r) * ldw + (t % r)];
+    __syncthreads();
+  }
   trinv_smem(W, r, ldw, tmp);
   double* Lt = st.Lt[m] + i * (long)r * r;
   for (int t = threadIdx.x; t < r * r; t += NT) Lt[t] = W[(t / r) * ldw + (t % r)];

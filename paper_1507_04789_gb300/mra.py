@@ -26,7 +26,7 @@ MRA_PREC_FP64 = 0
 MRA_HOST, MRA_DEVICE = 0, 1
 MRA_MAX_LEAF = 128
 FAMILIES = {"exp": MRA_COV_EXP, "matern15": MRA_COV_MATERN15}
-KERNEL_KINDS = ("prior", "leaf", "leaf_syrk", "post", "aggregate", "predict")
+KERNEL_KINDS = ("prior", "leaf", "leaf_syrk", "post", "aggregate", "predict", "grad")
 
 
 class MRAError(RuntimeError):
@@ -84,11 +84,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
-    for name in ("mra_loglik_grad",):
-        if hasattr(lib, name):
-            f = getattr(lib, name)
-            f.restype = ctypes.c_int
-            f.argtypes = [_P, ctypes.POINTER(MraParams), _D, _P]
+    lib.mra_loglik_grad.restype = ctypes.c_int
+    lib.mra_loglik_grad.argtypes = [_P, ctypes.POINTER(MraParams), _D, _P]
     _lib = lib
     return lib
 
@@ -216,8 +213,6 @@ class Handle:
 
     def loglik_grad(self, theta):
         """(loglik, d loglik / d(sigma2, range, tau2))."""
-        if not hasattr(self._lib, "mra_loglik_grad"):
-            raise MRAError(MRA_ERR_STATE, "library built without the gradient entry point")
         out = ctypes.c_double()
         g = np.zeros(3)
         p = MraParams(*[float(v) for v in theta])
