@@ -108,3 +108,21 @@ def test_gradient_then_predict(mra):
         m2, v2 = h.predict(theta, plocs)
     np.testing.assert_array_equal(m1, m2)
     np.testing.assert_array_equal(v1, v2)
+
+
+def test_autograd_function_and_mle(mra):
+    """torch.autograd path and 20 steps of gradient-based MLE from range = 0.3."""
+    torch = pytest.importorskip("torch")
+    from paper_1507_04789_gb300 import autograd as ag
+    w = synth.workload("n4096_exp_M3_r16")
+    locs, y, _ = w.generate()
+    with mra.Handle(locs, y, M=w.M, r=w.r, family=w.family) as h:
+        theta = torch.tensor([1.0, 0.3, 0.05], dtype=torch.float64, requires_grad=True)
+        ll = ag.loglik(h, theta)
+        ll.backward()
+        _, g = h.loglik_grad(theta.detach().numpy())
+        np.testing.assert_allclose(theta.grad.numpy(), g, rtol=0, atol=0)
+        th, hist = ag.fit_mle(h, (1.0, 0.3, 0.05), steps=20, lr=0.1)
+    lls = [v for _, v in hist]
+    assert lls[-1] > lls[0] + 1.0            # the fit climbs the likelihood
+    assert th[1] < 0.3                       # towards the generating range 0.05
