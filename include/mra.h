@@ -61,6 +61,10 @@ extern "C" {
 #define MRA_COV_MATERN15  1 /* C0 = sigma2 (1 + sqrt3 h / range) exp(-sqrt3 h / range), Eq. mat15 */
 
 #define MRA_PREC_FP64     0 /* every step in binary64 */
+#define MRA_PREC_MIXED    1 /* prior chain, leaf covariance and leaf solve products on the
+                               tensor cores (tcgen05, 3xTF32 with FP64 accumulation every 64
+                               terms); factorisations, log-determinants, quadratic forms and
+                               the Gram products of the posterior pass in binary64 */
 
 #define MRA_HOST          0 /* pointer argument is host memory */
 #define MRA_DEVICE        1 /* pointer argument is device memory */
@@ -72,7 +76,7 @@ typedef struct {
     int    r;           /* knots per internal region, 1 <= r <= MRA_MAX_R */
     int    cov_family;  /* MRA_COV_EXP or MRA_COV_MATERN15 */
     int    nonstat;     /* 1: variance sigma2 * sqrt(g(s1) g(s2)), g(s) = 1 + 0.5 sin(4 pi x) */
-    int    precision;   /* MRA_PREC_FP64 */
+    int    precision;   /* MRA_PREC_FP64 or MRA_PREC_MIXED */
     double bbox[4];     /* x0, x1, y0, y1 of the domain; every location must lie inside */
 } mra_config;
 

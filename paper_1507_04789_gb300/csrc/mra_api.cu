@@ -159,6 +159,8 @@ int status_error(const int* s) {
     return fail(MRA_ERR_LIMIT, "leaf %d holds more points than the kernels accept", s[2]);
   if (s[0] == mra::ST_ARG)
     return fail(MRA_ERR_ARG, "location %d is outside the bounding box or not finite", s[2]);
+  if (s[0] == mra::ST_TIMEOUT)
+    return fail(MRA_ERR_CUDA, "a tensor-core wait timed out at level %d, region %d", s[1], s[2]);
   return fail(MRA_ERR_CUDA, "device status %d", s[0]);
 }
 
@@ -166,6 +168,7 @@ mra::Shape shape_of(const mra_handle* h) {
   mra::Shape sh;
   sh.M = h->M; sh.r = h->r; sh.gx = h->gx; sh.gy = h->gy;
   for (int k = 0; k < 4; ++k) sh.bbox[k] = h->cfg.bbox[k];
+  sh.mixed = h->cfg.precision == MRA_PREC_MIXED;
   return sh;
 }
 
@@ -217,7 +220,8 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   if (cfg->cov_family != MRA_COV_EXP && cfg->cov_family != MRA_COV_MATERN15)
     return fail(MRA_ERR_ARG, "unknown covariance family %d", cfg->cov_family);
   if (cfg->nonstat != 0 && cfg->nonstat != 1) return fail(MRA_ERR_ARG, "nonstat must be 0 or 1");
-  if (cfg->precision != MRA_PREC_FP64) return fail(MRA_ERR_ARG, "unknown precision %d", cfg->precision);
+  if (cfg->precision != MRA_PREC_FP64 && cfg->precision != MRA_PREC_MIXED)
+    return fail(MRA_ERR_ARG, "unknown precision %d", cfg->precision);
   if (!(cfg->bbox[0] < cfg->bbox[1]) || !(cfg->bbox[2] < cfg->bbox[3]))
     return fail(MRA_ERR_ARG, "empty or invalid bounding box");
   if (where != MRA_HOST && where != MRA_DEVICE) return fail(MRA_ERR_ARG, "where must be MRA_HOST or MRA_DEVICE");
@@ -321,7 +325,7 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
     h->lf.d = d;
     h->lf.u = u;
   }
-  size_t need = mra::leaf_smem_bytes(r, h->nlmax);
+  size_t need = cfg->precision == MRA_PREC_MIXED ? mra::leaf_tc_smem_bytes(h->nlmax) : mra::leaf_smem_bytes(r, h->nlmax);
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

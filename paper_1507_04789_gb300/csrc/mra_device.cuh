@@ -20,7 +20,7 @@ constexpr double PI = 3.141592653589793238463;
 
 // ---- error status (device) ------------------------------------------------
 // status[0] = first error code, status[1] = level, status[2] = region
-enum : int { ST_OK = 0, ST_NOT_PD = 4, ST_LIMIT = 6, ST_ARG = 1 };
+enum : int { ST_OK = 0, ST_NOT_PD = 4, ST_LIMIT = 6, ST_ARG = 1, ST_TIMEOUT = 7 };
 
 __device__ __forceinline__ void flag_error(int* status, int code, int level, long region) {
   if (atomicCAS(status, 0, code) == 0) {

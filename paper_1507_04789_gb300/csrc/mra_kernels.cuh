@@ -89,6 +89,7 @@ struct PredState {
 struct Shape {
   int M, r, gx, gy;
   double bbox[4];
+  int mixed;              // 1: tensor-core (3xTF32) prior and leaf contractions
 };
 
 }  // namespace mra

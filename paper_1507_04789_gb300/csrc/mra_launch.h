@@ -43,6 +43,13 @@ cudaError_t launch_loglik(const Shape& sh, const Cov& cv, double tau2, const Lev
                           int64_t* launches, Timer* timer);
 size_t leaf_smem_bytes(int r, int nlmax);
 
+// Mixed-precision prior level and leaf pass (tensor cores, mra_mixed.cu).
+cudaError_t launch_prior_tc(int m, const Shape& sh, const Cov& cv, const LevelState& st, int* status,
+                            cudaStream_t s);
+cudaError_t launch_leaf_tc(const Shape& sh, const Cov& cv, double tau2, const LevelState& st, const LeafState& lf,
+                           int nlmax, int* status, cudaStream_t s);
+size_t leaf_tc_smem_bytes(int nlmax);
+
 // Prediction (Sec. 3.4, Prop. 2) at points binned into ps.
 cudaError_t launch_predict(const Shape& sh, const Cov& cv, const LevelState& st, const LeafState& lf, int nlmax,
                            const PredState& ps, int max_per_leaf, cudaStream_t s, int64_t* launches, Timer* tm);

@@ -436,7 +436,11 @@ cudaError_t launch_loglik(const Shape& sh, const Cov& cv, double tau2, const Lev
     size_t sm = prior_smem(tile);
     unsigned grid = 1u << (2 * m);
     tm->start(0, s);
-    MRA_LAUNCH(tile, prior_level_kernel, grid, sm, s, m, sh, cv, st, status);
+    if (sh.mixed) {
+      if ((e = launch_prior_tc(m, sh, cv, st, status, s))) return e;
+    } else {
+      MRA_LAUNCH(tile, prior_level_kernel, grid, sm, s, m, sh, cv, st, status);
+    }
     tm->stop(s);
     ++*launches;
   }
@@ -445,7 +449,11 @@ cudaError_t launch_loglik(const Shape& sh, const Cov& cv, double tau2, const Lev
     size_t sm = leaf_smem(tile, nlmax);
     unsigned grid = 1u << (2 * sh.M);
     tm->start(1, s);
-    MRA_LAUNCH(tile, leaf_kernel, grid, sm, s, sh, cv, tau2, st, lf, nlmax, status);
+    if (sh.mixed) {
+      if ((e = launch_leaf_tc(sh, cv, tau2, st, lf, nlmax, status, s))) return e;
+    } else {
+      MRA_LAUNCH(tile, leaf_kernel, grid, sm, s, sh, cv, tau2, st, lf, nlmax, status);
+    }
     tm->stop(s);
     ++*launches;
   }

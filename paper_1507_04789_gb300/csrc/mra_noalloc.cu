@@ -196,6 +196,7 @@ extern "C" int mra_loglik_noalloc(const mra_config* cfg, const mra_params* theta
   sh.gx = gx_of(r);
   sh.gy = r / sh.gx;
   for (int k = 0; k < 4; ++k) sh.bbox[k] = cfg->bbox[k];
+  sh.mixed = 0;
   mra::Cov cv{theta->sigma2, theta->range, cfg->cov_family, cfg->nonstat};
   mra::Timer no_timer;
   if ((e = mra::launch_gather(locs, y, perm, n, xs, ys, yv, s, launches)) ||

@@ -22,7 +22,8 @@ LIB_PATH = os.path.join(_PKG, "libmra_gb300.so")
 
 MRA_OK, MRA_ERR_ARG, MRA_ERR_OOM, MRA_ERR_CUDA, MRA_ERR_NOT_PD, MRA_ERR_STATE, MRA_ERR_LIMIT = range(7)
 MRA_COV_EXP, MRA_COV_MATERN15 = 0, 1
-MRA_PREC_FP64 = 0
+MRA_PREC_FP64, MRA_PREC_MIXED = 0, 1
+PRECISIONS = {"fp64": MRA_PREC_FP64, "mixed": MRA_PREC_MIXED}
 MRA_HOST, MRA_DEVICE = 0, 1
 MRA_MAX_LEAF = 128
 FAMILIES = {"exp": MRA_COV_EXP, "matern15": MRA_COV_MATERN15}
@@ -122,12 +123,13 @@ class Handle:
     """One M-RA problem on the GPU: locations, data and the tree (Sec. 2.2)."""
 
     def __init__(self, locs, y, M: int, r: int, family: str = "exp", nonstat: bool = False,
-                 bbox=(0.0, 1.0, 0.0, 1.0), J: int = 4, precision: int = MRA_PREC_FP64):
+                 bbox=(0.0, 1.0, 0.0, 1.0), J: int = 4, precision="fp64"):
         lib = load_library()
         self._lib = lib
         self._h = _P()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         cfg = MraConfig(M, J, r, FAMILIES[family] if isinstance(family, str) else int(family),
-                        int(bool(nonstat)), precision, (ctypes.c_double * 4)(*bbox))
+                        int(bool(nonstat)), prec, (ctypes.c_double * 4)(*bbox))
         if _is_torch_cuda(locs):
             if locs.dim() != 2 or locs.shape[1] != 2:
                 raise ValueError("locs must be (n, 2)")
