@@ -77,6 +77,8 @@ typedef struct {
     int    cov_family;  /* MRA_COV_EXP or MRA_COV_MATERN15 */
     int    nonstat;     /* 1: variance sigma2 * sqrt(g(s1) g(s2)), g(s) = 1 + 0.5 sin(4 pi x) */
     int    precision;   /* MRA_PREC_FP64 or MRA_PREC_MIXED */
+    int    prune;       /* 1: keep only regions whose subtree holds observations (empty subtrees
+                           contribute nothing to the likelihood); 0: complete tree */
     double bbox[4];     /* x0, x1, y0, y1 of the domain; every location must lie inside */
 } mra_config;
 
@@ -185,6 +187,41 @@ int mra_leaf_offsets(mra_handle* h, int64_t* off_out, int64_t* perm_out);
  * handle's device, passed as void*; NULL = legacy default stream).
  */
 int mra_set_stream(mra_handle* h, void* stream);
+
+/*
+ * mra_build_batch -- many independent datasets evaluated together (each with
+ * its own shape cfgs[d], locations locs[d] (n x 2 row-major), data ys[d] and
+ * size ns[d], all in the memory space `where`).  Every dataset gets its own
+ * partition and factors; the batch evaluates them with one launch per level
+ * (the paper's regions of one resolution are independent, Sec. 3.5), whose
+ * CTAs map to (dataset, region) pairs, and replays that launch sequence as a
+ * CUDA graph.  All datasets must share r and precision; M, the covariance
+ * family and the bounding box may differ.  Swath-like data should use
+ * prune = 1 (empty subtrees are skipped, Sec. 3.3).  Errors: as mra_build,
+ * with the failing dataset's index in the text.
+ */
+int mra_build_batch(const mra_config* cfgs, const double* const* locs, const double* const* ys,
+                    const int64_t* ns, int ndata, int where, mra_handle** out);
+
+/*
+ * mra_loglik_batch -- log-likelihoods of every dataset of a batch handle at
+ * its own parameters: thetas[d] (host, ndata entries) -> loglik_out[d] (host).
+ * The first call autotunes the tile size (mra_autotune) and captures the
+ * launch sequence as a CUDA graph; later calls replay it.  Errors: MRA_ERR_ARG,
+ * MRA_ERR_STATE (not a batch handle), MRA_ERR_NOT_PD, MRA_ERR_CUDA.
+ */
+int mra_loglik_batch(mra_handle* h, const mra_params* thetas, double* loglik_out);
+
+/*
+ * mra_autotune -- time the evaluation with every tile size the kernels offer
+ * for this r (16, 32 or 64 rows/columns per tile, at least r) at `thetas`
+ * (one mra_params, or ndata for a batch handle) and keep the fastest;
+ * *tile_out (may be NULL) receives it.
+ */
+int mra_autotune(mra_handle* h, const mra_params* thetas, int* tile_out);
+
+/* mra_batch_info -- number of datasets of a handle (0 for a single handle) and its tile size. */
+int mra_batch_info(mra_handle* h, int* ndata_out, int* tile_out);
 
 /*
  * Per-kernel timing with CUDA events recorded on the handle's stream around

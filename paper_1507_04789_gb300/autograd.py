@@ -52,7 +52,7 @@ def fit_mle(handle: Handle, theta0, steps: int = 20, lr: float = 0.1, fixed=()):
         ll = loglik(handle, theta)
         (-ll).backward()
         log_t.grad *= mask
-        hist.append((theta.detach().numpy().copy(), float(ll)))
+        hist.append((theta.detach().numpy().copy(), float(ll.detach())))
         opt.step()
     theta = torch.exp(log_t).detach().numpy()
     hist.append((theta.copy(), handle.loglik(theta)))

@@ -1,11 +1,18 @@
 // mra_api.cu -- the extern "C" boundary of the library (declared in include/mra.h).
 //
 // A handle owns the device state of one problem: the sorted observations, the
-// per-level factors of the prior and posterior passes and the leaf factors.
-// Device memory is taken in two arenas at build time (the leaf-factor size
-// depends on the occupancy of the leaves, known after binning) and, for
-// prediction, a third arena that mra_predict grows when it is given more
-// points than before; no other entry point allocates after mra_build.
+// tree tables, the per-level factors of the prior and posterior passes and the
+// leaf factors, plus a descriptor of all of it in device memory that every
+// kernel reads.  Device memory is taken in arenas at build time (the sizes
+// depend on the leaf occupancy, known after binning); mra_predict grows a
+// prediction arena and the first mra_loglik_grad allocates the adjoint arena;
+// no other entry point allocates after mra_build.
+//
+// A batch handle (mra_build_batch) owns one handle per dataset and evaluates
+// all of them with one launch per level: every CTA of a launch is mapped to a
+// (dataset, region) pair by a work list.  The launch sequence is captured once
+// as a CUDA graph and replayed for every new set of parameters.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -48,7 +55,11 @@ struct Arena {
     for (auto& q : plan) size += align(q.second);
     if (size == 0) size = 256;
     cudaError_t e = cudaMalloc((void**)&base, size);
-    if (e != cudaSuccess) { base = nullptr; return e; }
+    if (e != cudaSuccess) {
+      base = nullptr;
+      plan.clear();
+      return e;
+    }
     used = 0;
     for (auto& q : plan) {
       *q.first = q.second ? base + used : nullptr;
@@ -69,6 +80,85 @@ int gx_for(int r) {
   return r;
 }
 
+bool params_ok(const mra_params* t) {
+  return t && std::isfinite(t->sigma2) && std::isfinite(t->range) && std::isfinite(t->tau2) && t->sigma2 > 0 &&
+         t->range > 0 && t->tau2 >= 0;
+}
+
+int check_config(const mra_config* cfg) {
+  if (cfg->M < 0 || cfg->M > MRA_MAX_M) return fail(MRA_ERR_ARG, "M must be in [0, %d]", MRA_MAX_M);
+  if (cfg->J != 4) return fail(MRA_ERR_ARG, "J must be 4 (2-D midpoint quadtree)");
+  if (cfg->r < 1 || cfg->r > MRA_MAX_R) return fail(MRA_ERR_ARG, "r must be in [1, %d]", MRA_MAX_R);
+  if (cfg->cov_family != MRA_COV_EXP && cfg->cov_family != MRA_COV_MATERN15)
+    return fail(MRA_ERR_ARG, "unknown covariance family %d", cfg->cov_family);
+  if (cfg->nonstat != 0 && cfg->nonstat != 1) return fail(MRA_ERR_ARG, "nonstat must be 0 or 1");
+  if (cfg->precision != MRA_PREC_FP64 && cfg->precision != MRA_PREC_MIXED)
+    return fail(MRA_ERR_ARG, "unknown precision %d", cfg->precision);
+  if (cfg->prune != 0 && cfg->prune != 1) return fail(MRA_ERR_ARG, "prune must be 0 or 1");
+  if (!(cfg->bbox[0] < cfg->bbox[1]) || !(cfg->bbox[2] < cfg->bbox[3]))
+    return fail(MRA_ERR_ARG, "empty or invalid bounding box");
+  return MRA_OK;
+}
+
+// Host tree tables (Sec. 2.2): active regions of every level in Morton order.
+struct Tables {
+  std::vector<std::vector<int32_t>> mort, par, cfirst, ccnt, cid;
+  std::vector<int32_t> nreg;
+};
+
+void build_tables(int M, bool prune, const std::vector<int32_t>& counts, Tables& T) {
+  T.mort.assign(M + 1, {});
+  T.par.assign(M + 1, {});
+  T.cfirst.assign(M + 1, {});
+  T.ccnt.assign(M + 1, {});
+  T.cid.assign(M + 1, {});
+  T.nreg.assign(M + 1, 0);
+  std::vector<std::vector<uint8_t>> act(M + 1);
+  act[M].resize(counts.size());
+  for (size_t f = 0; f < counts.size(); ++f) act[M][f] = !prune || counts[f] > 0;
+  for (int m = M - 1; m >= 0; --m) {
+    const size_t cnt = size_t(1) << (2 * m);
+    act[m].assign(cnt, 0);
+    for (size_t i = 0; i < cnt; ++i)
+      act[m][i] = !prune || act[m + 1][4 * i] || act[m + 1][4 * i + 1] || act[m + 1][4 * i + 2] || act[m + 1][4 * i + 3];
+  }
+  act[0][0] = 1;
+  for (int m = 0; m <= M; ++m) {
+    const size_t cnt = size_t(1) << (2 * m);
+    T.cid[m].assign(cnt, -1);
+    for (size_t i = 0; i < cnt; ++i)
+      if (act[m][i]) {
+        T.cid[m][i] = (int32_t)T.mort[m].size();
+        T.mort[m].push_back((int32_t)i);
+      }
+    T.nreg[m] = (int32_t)T.mort[m].size();
+  }
+  for (int m = 0; m <= M; ++m) {
+    const int32_t n = T.nreg[m];
+    if (m > 0) {
+      T.par[m].resize(n);
+      for (int32_t c = 0; c < n; ++c) T.par[m][c] = T.cid[m - 1][T.mort[m][c] >> 2];
+    }
+    if (m < M) {
+      T.cfirst[m].assign(n, 0);
+      T.ccnt[m].assign(n, 0);
+      for (int32_t c = 0; c < n; ++c) {
+        const size_t base = 4 * (size_t)T.mort[m][c];
+        int32_t first = -1, k = 0;
+        for (int j = 0; j < 4; ++j) {
+          const int32_t id = T.cid[m + 1][base + j];
+          if (id >= 0) {
+            if (first < 0) first = id;
+            ++k;
+          }
+        }
+        T.cfirst[m][c] = first < 0 ? 0 : first;
+        T.ccnt[m][c] = k;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 namespace mra {
@@ -85,7 +175,7 @@ struct mra_handle {
   int nlmax = 0;
   cudaStream_t stream = nullptr;
   Arena tree, state;
-  // tree (arena 1)
+  // tree and sorted observations (arena 1)
   double* bbox = nullptr;
   int32_t* leaf_id = nullptr;
   int32_t* counts = nullptr;
@@ -100,10 +190,13 @@ struct mra_handle {
   double* yv = nullptr;
   double* in_locs = nullptr;   // staging of host inputs
   double* in_y = nullptr;
-  // state (arena 2)
+  // factors and tables (arena 2) and the device descriptor
+  Tables tab;
   mra::LevelState st{};
   mra::LeafState lf{};
-  // host
+  mra::Desc hd{};
+  mra::Desc* d_desc = nullptr;
+  mra::Plan plan;
   double* pinned = nullptr;    // small pinned readback buffer
   int64_t ls_cap = 0;          // capacity of the ragged leaf-factor store (doubles)
   // prediction points (arena 3, grown on demand by mra_predict)
@@ -117,22 +210,33 @@ struct mra_handle {
   bool have_grad_arena = false;
   mra::GradState gs{};
   double* d_grad = nullptr;
+  // timing
   mra::Timer timer;
   bool timer_events = false;
   double ktime[8] = {0};
   int64_t kcount[8] = {0};
   bool have_post = false;
   mra_params last{};
+  // batch of datasets
+  std::vector<mra_handle*> parts;
+  Arena batch;
+  std::vector<mra::Desc> h_descs;
+  mra::Desc* pinned_descs = nullptr;
+  mra::Desc* d_descs = nullptr;
+  double* d_roots = nullptr;
+  int own_stream = 0;
+  bool tuned = false;
+  int64_t graph_launches = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
 };
 
 namespace {
 
-cudaError_t sync_status(mra_handle* h, int* host_status, double* extra, int nextra,
-                        const double* const* srcs) {
+cudaError_t sync_status(mra_handle* h, int* host_status, double* extra, int nextra, const double* const* srcs) {
   cudaError_t e;
   for (int k = 0; k < nextra; ++k)
-    if ((e = cudaMemcpyAsync(h->pinned + 4 + k, srcs[k], sizeof(double), cudaMemcpyDeviceToHost, h->stream)))
-      return e;
+    if ((e = cudaMemcpyAsync(h->pinned + 4 + k, srcs[k], sizeof(double), cudaMemcpyDeviceToHost, h->stream))) return e;
   if ((e = cudaMemcpyAsync(h->pinned, h->status, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream))) return e;
   if ((e = cudaStreamSynchronize(h->stream))) return e;
   memcpy(host_status, h->pinned, sizeof(int) * 4);
@@ -155,26 +259,68 @@ void collect_times(mra_handle* h) {
 int status_error(const int* s) {
   if (s[0] == mra::ST_NOT_PD)
     return fail(MRA_ERR_NOT_PD, "matrix not positive definite at level %d, region %d", s[1], s[2]);
-  if (s[0] == mra::ST_LIMIT)
-    return fail(MRA_ERR_LIMIT, "leaf %d holds more points than the kernels accept", s[2]);
-  if (s[0] == mra::ST_ARG)
+  if (s[0] == mra::ST_LIMIT) return fail(MRA_ERR_LIMIT, "leaf %d holds more points than the kernels accept", s[2]);
+  if (s[0] == mra::ST_ARG) {
+    if (s[1] >= 0)
+      return fail(MRA_ERR_ARG, "prediction location in leaf %d lies under a level-%d region without observations "
+                  "(the tree was built with prune = 1)", s[2], s[1]);
     return fail(MRA_ERR_ARG, "location %d is outside the bounding box or not finite", s[2]);
+  }
   if (s[0] == mra::ST_TIMEOUT)
     return fail(MRA_ERR_CUDA, "a tensor-core wait timed out at level %d, region %d", s[1], s[2]);
   return fail(MRA_ERR_CUDA, "device status %d", s[0]);
 }
 
-mra::Shape shape_of(const mra_handle* h) {
-  mra::Shape sh;
-  sh.M = h->M; sh.r = h->r; sh.gx = h->gx; sh.gy = h->gy;
-  for (int k = 0; k < 4; ++k) sh.bbox[k] = h->cfg.bbox[k];
-  sh.mixed = h->cfg.precision == MRA_PREC_MIXED;
-  return sh;
+void single_plan(mra_handle* h) {
+  mra::Plan& p = h->plan;
+  p = mra::Plan();
+  p.maxM = h->M;
+  p.tile = mra::tile_for_r(h->r);
+  p.mixed = h->cfg.precision == MRA_PREC_MIXED;
+  p.nlmax = h->nlmax;
+  for (int m = 0; m < h->M; ++m) {
+    p.n_lvl[m] = h->tab.nreg[m];
+    if (m > 0) p.n_agg[m] = h->tab.nreg[m - 1];
+  }
+  p.n_leaf = h->tab.nreg[h->M];
+  if (h->M > 0) {
+    p.n_syrk = h->tab.nreg[h->M - 1];
+    p.t_syrk = h->M * (h->M + 1) / 2;
+  }
 }
 
-bool params_ok(const mra_params* t) {
-  return t && std::isfinite(t->sigma2) && std::isfinite(t->range) && std::isfinite(t->tau2) &&
-         t->sigma2 > 0 && t->range > 0 && t->tau2 >= 0;
+cudaError_t upload_desc(mra_handle* h, const mra_params* theta) {
+  h->hd.sh.M = h->M;
+  h->hd.sh.r = h->r;
+  h->hd.sh.gx = h->gx;
+  h->hd.sh.gy = h->gy;
+  for (int k = 0; k < 4; ++k) h->hd.sh.bbox[k] = h->cfg.bbox[k];
+  h->hd.sh.mixed = h->cfg.precision == MRA_PREC_MIXED;
+  if (theta) {
+    h->hd.cv = mra::Cov{theta->sigma2, theta->range, h->cfg.cov_family, h->cfg.nonstat};
+    h->hd.tau2 = theta->tau2;
+  }
+  h->hd.nlmax = h->nlmax;
+  h->hd.st = h->st;
+  h->hd.lf = h->lf;
+  return cudaMemcpyAsync(h->d_desc, &h->hd, sizeof(mra::Desc), cudaMemcpyHostToDevice, h->stream);
+}
+
+// Binning into an existing tree arena (used by mra_build and mra_update).
+cudaError_t bin(mra_handle* h, const double* dl, const double* dy, int* hs, int64_t* tail, int32_t* mc) {
+  const int64_t nl = int64_t(1) << (2 * h->M);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream))) return e;
+  if ((e = mra::launch_bin(dl, h->n, h->bbox, h->M, h->leaf_id, h->counts, h->cursor, h->off, h->sq_off,
+                           h->max_count, h->perm, h->status, h->stream, &g_launches)) ||
+      (e = mra::launch_gather(dl, dy, h->perm, h->n, h->xs, h->ys, h->yv, h->stream, &g_launches)))
+    return e;
+  double got[2];
+  const double* srcs[2] = {(const double*)(h->sq_off + nl), (const double*)h->max_count};
+  if ((e = sync_status(h, hs, got, 2, srcs))) return e;
+  memcpy(tail, &got[0], sizeof(int64_t));
+  memcpy(mc, &got[1], sizeof(int32_t));
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -191,19 +337,36 @@ int64_t mra_launch_count(int reset) {
 
 void mra_free(mra_handle* h) {
   if (!h) return;
+  for (mra_handle* p : h->parts) mra_free(p);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
   if (h->timer_events)
     for (int k = 0; k < 2 * mra::MAX_TIMED; ++k) cudaEventDestroy(h->timer.ev[k]);
   h->tree.release();
   h->state.release();
   h->pred.release();
   h->grad.release();
+  h->batch.release();
   if (h->pinned) cudaFreeHost(h->pinned);
+  if (h->pinned_descs) cudaFreeHost(h->pinned_descs);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
 }
 
 int mra_set_stream(mra_handle* h, void* stream) {
   if (!h) return fail(MRA_ERR_ARG, "null handle");
+  if (!h->parts.empty() && !stream) return fail(MRA_ERR_ARG, "a batch handle needs a non-default stream");
+  if (h->own_stream) {
+    cudaStreamDestroy(h->stream);
+    h->own_stream = 0;
+  }
   h->stream = (cudaStream_t)stream;
+  if (h->gexec) {   // the captured graph belongs to the old stream's work; recapture on next use
+    cudaGraphExecDestroy(h->gexec);
+    cudaGraphDestroy(h->graph);
+    h->gexec = nullptr;
+    h->graph = nullptr;
+  }
   return MRA_OK;
 }
 
@@ -214,16 +377,8 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   *out = nullptr;
   if (!cfg || !locs || !y) return fail(MRA_ERR_ARG, "null argument");
   if (n < 1) return fail(MRA_ERR_ARG, "n must be >= 1 (got %lld)", (long long)n);
-  if (cfg->M < 0 || cfg->M > MRA_MAX_M) return fail(MRA_ERR_ARG, "M must be in [0, %d]", MRA_MAX_M);
-  if (cfg->J != 4) return fail(MRA_ERR_ARG, "J must be 4 (2-D midpoint quadtree)");
-  if (cfg->r < 1 || cfg->r > MRA_MAX_R) return fail(MRA_ERR_ARG, "r must be in [1, %d]", MRA_MAX_R);
-  if (cfg->cov_family != MRA_COV_EXP && cfg->cov_family != MRA_COV_MATERN15)
-    return fail(MRA_ERR_ARG, "unknown covariance family %d", cfg->cov_family);
-  if (cfg->nonstat != 0 && cfg->nonstat != 1) return fail(MRA_ERR_ARG, "nonstat must be 0 or 1");
-  if (cfg->precision != MRA_PREC_FP64 && cfg->precision != MRA_PREC_MIXED)
-    return fail(MRA_ERR_ARG, "unknown precision %d", cfg->precision);
-  if (!(cfg->bbox[0] < cfg->bbox[1]) || !(cfg->bbox[2] < cfg->bbox[3]))
-    return fail(MRA_ERR_ARG, "empty or invalid bounding box");
+  int rc = check_config(cfg);
+  if (rc) return rc;
   if (where != MRA_HOST && where != MRA_DEVICE) return fail(MRA_ERR_ARG, "where must be MRA_HOST or MRA_DEVICE");
 
   mra_handle* h = new mra_handle();
@@ -236,10 +391,9 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   const int M = h->M, r = h->r;
   const int64_t nl = int64_t(1) << (2 * M);
   cudaError_t e;
-  int rc = MRA_OK;
   int hs[4];
 
-  // ---- arena 1: inputs, tree, sorted observations --------------------------
+  // ---- arena 1: inputs, partition, sorted observations -----------------------
   Arena& A = h->tree;
   A.want(&h->bbox, 4);
   A.want(&h->leaf_id, n);
@@ -247,7 +401,7 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   A.want(&h->cursor, nl);
   A.want(&h->off, nl + 1);
   A.want(&h->sq_off, nl + 1);
-  A.want(&h->max_count, 1);
+  A.want(&h->max_count, 2);
   A.want(&h->perm, n);
   A.want(&h->status, 4);
   A.want(&h->xs, n);
@@ -257,7 +411,6 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   A.want(&h->in_y, n);
   if ((e = A.commit())) { mra_free(h); return fail(MRA_ERR_OOM, "device allocation (tree): %s", cudaGetErrorString(e)); }
   if ((e = cudaMallocHost((void**)&h->pinned, 64 * sizeof(double)))) { mra_free(h); return cuda_fail(e, "cudaMallocHost"); }
-
   const double* dl = locs;
   const double* dy = y;
   if (where == MRA_HOST) {
@@ -268,63 +421,83 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
     dl = h->in_locs;
     dy = h->in_y;
   }
-  if ((e = cudaMemcpyAsync(h->bbox, cfg->bbox, sizeof(double) * 4, cudaMemcpyHostToDevice, h->stream)) ||
-      (e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream))) {
+  if ((e = cudaMemcpyAsync(h->bbox, cfg->bbox, sizeof(double) * 4, cudaMemcpyHostToDevice, h->stream))) {
     mra_free(h); return cuda_fail(e, "init");
   }
-  if ((e = mra::launch_bin(dl, n, h->bbox, M, h->leaf_id, h->counts, h->cursor, h->off, h->sq_off,
-                           h->max_count, h->perm, h->status, h->stream, &g_launches)) ||
-      (e = mra::launch_gather(dl, dy, h->perm, n, h->xs, h->ys, h->yv, h->stream, &g_launches))) {
-    mra_free(h); return cuda_fail(e, "binning");
+  int64_t tail = 0;
+  int32_t mc = 0;
+  if ((e = bin(h, dl, dy, hs, &tail, &mc))) { mra_free(h); return cuda_fail(e, "binning"); }
+  if (hs[0]) { rc = status_error(hs); mra_free(h); return rc; }
+  if (mc > MRA_MAX_LEAF) {
+    mra_free(h);
+    return fail(MRA_ERR_LIMIT, "a leaf holds %d observations (max %d); increase M", mc, MRA_MAX_LEAF);
   }
+  h->nlmax = mc < 1 ? 1 : mc;
+  // ---- tree tables (active regions) ------------------------------------------
   {
-    int64_t tail[2];
-    double got[2];
-    const double* srcs[2] = {(const double*)(h->sq_off + nl), (const double*)h->max_count};
-    if ((e = sync_status(h, hs, got, 2, srcs))) { mra_free(h); return cuda_fail(e, "binning"); }
-    memcpy(&tail[0], &got[0], sizeof(int64_t));
-    int32_t mc;
-    memcpy(&mc, &got[1], sizeof(int32_t));
-    if (hs[0]) { rc = status_error(hs); mra_free(h); return rc; }
-    if (mc > MRA_MAX_LEAF) {
-      mra_free(h);
-      return fail(MRA_ERR_LIMIT, "a leaf holds %d observations (max %d); increase M", mc, MRA_MAX_LEAF);
+    std::vector<int32_t> counts(nl);
+    if ((e = cudaMemcpyAsync(counts.data(), h->counts, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost, h->stream)) ||
+        (e = cudaStreamSynchronize(h->stream))) {
+      mra_free(h); return cuda_fail(e, "leaf counts");
     }
-    h->nlmax = mc < 1 ? 1 : mc;
-    // ---- arena 2: factors of every level and of the leaves ------------------
-    Arena& B = h->state;
-    for (int m = 0; m < M; ++m) {
-      const int64_t R = int64_t(1) << (2 * m);
-      const int64_t T = int64_t(m + 1) * (m + 2) / 2;
-      B.want(&h->st.V[m], R * r * (int64_t)m * r);
-      B.want(&h->st.Li[m], R * r * r);
-      B.want(&h->st.Acc[m], R * T * r * r);
-      B.want(&h->st.Om[m], R * (m + 1) * r);
-      B.want(&h->st.Lt[m], R * r * r);
-      B.want(&h->st.G[m], R * r * (int64_t)m * r);
-      B.want(&h->st.gv[m], R * r);
-      B.want(&h->st.dd[m], R);
-      B.want(&h->st.uu[m], R);
-    }
-    double *H, *z, *LS, *d, *u;
-    B.want(&H, n * (int64_t)M * r);
-    B.want(&z, n);
-    B.want(&LS, (size_t)tail[0]);
-    h->ls_cap = tail[0];
-    B.want(&d, nl);
-    B.want(&u, nl);
-    if ((e = B.commit())) { mra_free(h); return fail(MRA_ERR_OOM, "device allocation (factors): %s", cudaGetErrorString(e)); }
-    h->lf.off = h->off;
-    h->lf.sq_off = h->sq_off;
-    h->lf.xs = h->xs;
-    h->lf.ys = h->ys;
-    h->lf.yv = h->yv;
-    h->lf.H = H;
-    h->lf.z = z;
-    h->lf.LS = LS;
-    h->lf.d = d;
-    h->lf.u = u;
+    build_tables(M, cfg->prune != 0, counts, h->tab);
   }
+  const std::vector<int32_t>& nreg = h->tab.nreg;
+  // ---- arena 2: tables, factors of every level and of the leaves -------------
+  Arena& B = h->state;
+  for (int m = 0; m <= M; ++m) {
+    h->st.nreg[m] = nreg[m];
+    B.want(&h->st.mort[m], nreg[m]);
+    B.want(&h->st.cid[m], size_t(1) << (2 * m));
+    if (m > 0) B.want(&h->st.par[m], nreg[m]);
+    if (m < M) {
+      B.want(&h->st.cfirst[m], nreg[m]);
+      B.want(&h->st.ccnt[m], nreg[m]);
+    }
+  }
+  for (int m = 0; m < M; ++m) {
+    const int64_t R = nreg[m];
+    const int64_t T = int64_t(m + 1) * (m + 2) / 2;
+    B.want(&h->st.V[m], R * r * (int64_t)m * r);
+    B.want(&h->st.Li[m], R * r * r);
+    B.want(&h->st.Acc[m], R * T * r * r);
+    B.want(&h->st.Om[m], R * (m + 1) * r);
+    B.want(&h->st.Lt[m], R * r * r);
+    B.want(&h->st.G[m], R * r * (int64_t)m * r);
+    B.want(&h->st.gv[m], R * r);
+    B.want(&h->st.dd[m], R);
+    B.want(&h->st.uu[m], R);
+  }
+  double *H, *z, *LS, *d, *u;
+  B.want(&H, n * (int64_t)M * r);
+  B.want(&z, n);
+  B.want(&LS, (size_t)tail);
+  B.want(&d, nreg[M]);
+  B.want(&u, nreg[M]);
+  B.want(&h->d_desc, 1);
+  h->ls_cap = tail;
+  if ((e = B.commit())) { mra_free(h); return fail(MRA_ERR_OOM, "device allocation (factors): %s", cudaGetErrorString(e)); }
+  for (int m = 0; m <= M; ++m) {
+    if ((e = cudaMemcpyAsync(h->st.mort[m], h->tab.mort[m].data(), sizeof(int32_t) * nreg[m], cudaMemcpyHostToDevice, h->stream)) ||
+        (e = cudaMemcpyAsync(h->st.cid[m], h->tab.cid[m].data(), sizeof(int32_t) * h->tab.cid[m].size(), cudaMemcpyHostToDevice, h->stream)) ||
+        (m > 0 && (e = cudaMemcpyAsync(h->st.par[m], h->tab.par[m].data(), sizeof(int32_t) * nreg[m], cudaMemcpyHostToDevice, h->stream))) ||
+        (m < M && (e = cudaMemcpyAsync(h->st.cfirst[m], h->tab.cfirst[m].data(), sizeof(int32_t) * nreg[m], cudaMemcpyHostToDevice, h->stream))) ||
+        (m < M && (e = cudaMemcpyAsync(h->st.ccnt[m], h->tab.ccnt[m].data(), sizeof(int32_t) * nreg[m], cudaMemcpyHostToDevice, h->stream)))) {
+      mra_free(h); return cuda_fail(e, "tree tables");
+    }
+  }
+  if ((e = cudaStreamSynchronize(h->stream))) { mra_free(h); return cuda_fail(e, "tree tables"); }
+  h->lf.off = h->off;
+  h->lf.sq_off = h->sq_off;
+  h->lf.xs = h->xs;
+  h->lf.ys = h->ys;
+  h->lf.yv = h->yv;
+  h->lf.H = H;
+  h->lf.z = z;
+  h->lf.LS = LS;
+  h->lf.d = d;
+  h->lf.u = u;
+  single_plan(h);
   size_t need = cfg->precision == MRA_PREC_MIXED ? mra::leaf_tc_smem_bytes(h->nlmax) : mra::leaf_smem_bytes(r, h->nlmax);
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
@@ -340,6 +513,7 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
 int mra_set_data(mra_handle* h, const double* y, int where) {
   g_err.clear();
   if (!h || !y) return fail(MRA_ERR_ARG, "null argument");
+  if (!h->parts.empty()) return fail(MRA_ERR_STATE, "not available on a batch handle");
   const double* dy = y;
   cudaError_t e;
   if (where == MRA_HOST) {
@@ -357,13 +531,13 @@ int mra_set_data(mra_handle* h, const double* y, int where) {
 int mra_loglik(mra_handle* h, const mra_params* theta, double* loglik_out) {
   g_err.clear();
   if (!h || !loglik_out) return fail(MRA_ERR_ARG, "null argument");
+  if (!h->parts.empty()) return fail(MRA_ERR_STATE, "use mra_loglik_batch on a batch handle");
   if (!params_ok(theta)) return fail(MRA_ERR_ARG, "theta needs sigma2 > 0, range > 0, tau2 >= 0, all finite");
   h->have_post = false;
-  mra::Cov cv{theta->sigma2, theta->range, h->cfg.cov_family, h->cfg.nonstat};
   cudaError_t e;
-  if ((e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream))) return cuda_fail(e, "memset");
-  if ((e = mra::launch_loglik(shape_of(h), cv, theta->tau2, h->st, h->lf, h->nlmax, h->status, h->stream,
-                              &g_launches, &h->timer)))
+  if ((e = upload_desc(h, theta)) || (e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream)))
+    return cuda_fail(e, "descriptor");
+  if ((e = mra::launch_loglik(h->plan, h->d_desc, h->status, h->stream, &g_launches, &h->timer)))
     return cuda_fail(e, "loglik launch");
   int hs[4];
   double du[2];
@@ -382,22 +556,31 @@ int mra_loglik(mra_handle* h, const mra_params* theta, double* loglik_out) {
 int mra_region_terms(mra_handle* h, int level, double* d_out, double* u_out) {
   g_err.clear();
   if (!h || !d_out || !u_out) return fail(MRA_ERR_ARG, "null argument");
+  if (!h->parts.empty()) return fail(MRA_ERR_STATE, "not available on a batch handle");
   if (level < 0 || level > h->M) return fail(MRA_ERR_ARG, "level must be in [0, M]");
   if (!h->have_post) return fail(MRA_ERR_STATE, "no log-likelihood evaluated yet");
-  const int64_t R = int64_t(1) << (2 * level);
+  const int64_t full = int64_t(1) << (2 * level);
+  const int32_t cnt = h->tab.nreg[level];
   const double* d = level == h->M ? h->lf.d : h->st.dd[level];
   const double* u = level == h->M ? h->lf.u : h->st.uu[level];
+  std::vector<double> dv(cnt), uv(cnt);
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(d_out, d, sizeof(double) * R, cudaMemcpyDeviceToHost, h->stream)) ||
-      (e = cudaMemcpyAsync(u_out, u, sizeof(double) * R, cudaMemcpyDeviceToHost, h->stream)) ||
+  if ((e = cudaMemcpyAsync(dv.data(), d, sizeof(double) * cnt, cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaMemcpyAsync(uv.data(), u, sizeof(double) * cnt, cudaMemcpyDeviceToHost, h->stream)) ||
       (e = cudaStreamSynchronize(h->stream)))
     return cuda_fail(e, "region terms");
+  for (int64_t k = 0; k < full; ++k) d_out[k] = u_out[k] = 0.0;     // inactive regions contribute 0 (R10)
+  for (int32_t c = 0; c < cnt; ++c) {
+    d_out[h->tab.mort[level][c]] = dv[c];
+    u_out[h->tab.mort[level][c]] = uv[c];
+  }
   return MRA_OK;
 }
 
 int mra_leaf_offsets(mra_handle* h, int64_t* off_out, int64_t* perm_out) {
   g_err.clear();
   if (!h || !off_out) return fail(MRA_ERR_ARG, "null argument");
+  if (!h->parts.empty()) return fail(MRA_ERR_STATE, "not available on a batch handle");
   const int64_t nl = int64_t(1) << (2 * h->M);
   cudaError_t e;
   if ((e = cudaMemcpyAsync(off_out, h->off, sizeof(int64_t) * (nl + 1), cudaMemcpyDeviceToHost, h->stream)))
@@ -408,13 +591,54 @@ int mra_leaf_offsets(mra_handle* h, int64_t* off_out, int64_t* perm_out) {
   return MRA_OK;
 }
 
+int mra_update(mra_handle* h, const double* locs, const double* y, int where) {
+  g_err.clear();
+  if (!h || !locs || !y) return fail(MRA_ERR_ARG, "null argument");
+  if (!h->parts.empty()) return fail(MRA_ERR_STATE, "not available on a batch handle");
+  if (where != MRA_HOST && where != MRA_DEVICE) return fail(MRA_ERR_ARG, "where must be MRA_HOST or MRA_DEVICE");
+  const int64_t n = h->n, nl = int64_t(1) << (2 * h->M);
+  cudaError_t e;
+  const double* dl = locs;
+  const double* dy = y;
+  h->have_post = false;
+  if (where == MRA_HOST) {
+    if ((e = cudaMemcpyAsync(h->in_locs, locs, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, h->stream)) ||
+        (e = cudaMemcpyAsync(h->in_y, y, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream)))
+      return cuda_fail(e, "copy inputs");
+    dl = h->in_locs;
+    dy = h->in_y;
+  }
+  int hs[4];
+  int64_t tail = 0;
+  int32_t mc = 0;
+  if ((e = bin(h, dl, dy, hs, &tail, &mc))) return cuda_fail(e, "binning");
+  if (hs[0]) return status_error(hs);
+  if (mc > h->nlmax || tail > h->ls_cap)
+    return fail(MRA_ERR_LIMIT, "new partition needs leaves of %d (handle has %d) or %lld leaf-factor doubles "
+                "(handle has %lld); build a new handle", mc, h->nlmax, (long long)tail, (long long)h->ls_cap);
+  if (h->cfg.prune) {   // the active regions must not change
+    std::vector<int32_t> counts(nl);
+    if ((e = cudaMemcpyAsync(counts.data(), h->counts, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost, h->stream)) ||
+        (e = cudaStreamSynchronize(h->stream)))
+      return cuda_fail(e, "leaf counts");
+    for (int64_t f = 0; f < nl; ++f)
+      if ((counts[f] > 0) != (h->tab.cid[h->M][f] >= 0))
+        return fail(MRA_ERR_LIMIT, "the new data occupies other leaves than the pruned tree; build a new handle");
+  }
+  return MRA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Gradient
+// ---------------------------------------------------------------------------
 static int ensure_grad_arena(mra_handle* h) {
   if (h->have_grad_arena) return MRA_OK;
   const int M = h->M, r = h->r;
-  const int64_t n = h->n, nl = int64_t(1) << (2 * M);
+  const int64_t n = h->n;
+  const std::vector<int32_t>& nreg = h->tab.nreg;
   Arena& G = h->grad;
   for (int m = 0; m < M; ++m) {
-    const int64_t R = int64_t(1) << (2 * m);
+    const int64_t R = nreg[m];
     G.want(&h->st.L[m], R * r * r);
     G.want(&h->st.Ltf[m], R * r * r);
     G.want(&h->gs.Abar[m], R * r * (int64_t)(m + 1) * r);
@@ -424,15 +648,15 @@ static int ensure_grad_arena(mra_handle* h) {
     G.want(&h->gs.XB[m], R * r * (int64_t)m * r);
     G.want(&h->gs.Up[m], R * (int64_t)m * (m + 1) / 2 * r * r);
   }
-  if (M > 0) G.want(&h->gs.PartLeaf, (nl / 4) * (int64_t)M * (M + 1) / 2 * r * r);
+  if (M > 0) G.want(&h->gs.PartLeaf, (int64_t)nreg[M - 1] * M * (M + 1) / 2 * r * r);
   G.want(&h->lf.VF, n * (int64_t)M * r);
   G.want(&h->lf.LSf, (size_t)h->ls_cap);
   G.want(&h->gs.HB, n * (int64_t)M * r);
   G.want(&h->gs.VBF, n * (int64_t)M * r);
   G.want(&h->gs.XBF, n * (int64_t)M * r);
   G.want(&h->gs.T, 3 * (size_t)h->ls_cap);
-  int64_t slots = nl;
-  for (int m = 0; m < M; ++m) slots += int64_t(1) << (2 * m);
+  int64_t slots = 0;
+  for (int m = 0; m <= M; ++m) slots += nreg[m];
   G.want(&h->gs.gpart, 3 * slots);
   G.want(&h->d_grad, 4);
   cudaError_t e = G.commit();
@@ -449,17 +673,17 @@ static int ensure_grad_arena(mra_handle* h) {
 int mra_loglik_grad(mra_handle* h, const mra_params* theta, double* loglik_out, double* grad_out) {
   g_err.clear();
   if (!h || !loglik_out || !grad_out) return fail(MRA_ERR_ARG, "null argument");
+  if (!h->parts.empty()) return fail(MRA_ERR_STATE, "not available on a batch handle");
   if (!params_ok(theta)) return fail(MRA_ERR_ARG, "theta needs sigma2 > 0, range > 0, tau2 >= 0, all finite");
   int rc = ensure_grad_arena(h);
   if (rc) return rc;
   h->have_post = false;
-  mra::Cov cv{theta->sigma2, theta->range, h->cfg.cov_family, h->cfg.nonstat};
   cudaError_t e;
-  if ((e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream))) return cuda_fail(e, "memset");
-  if ((e = mra::launch_loglik(shape_of(h), cv, theta->tau2, h->st, h->lf, h->nlmax, h->status, h->stream,
-                              &g_launches, &h->timer)))
+  if ((e = upload_desc(h, theta)) || (e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream)))
+    return cuda_fail(e, "descriptor");
+  if ((e = mra::launch_loglik(h->plan, h->d_desc, h->status, h->stream, &g_launches, &h->timer)))
     return cuda_fail(e, "loglik launch");
-  if ((e = mra::launch_grad(shape_of(h), cv, h->st, h->lf, h->gs, h->d_grad, h->stream, &g_launches, &h->timer)))
+  if ((e = mra::launch_grad(h->hd, h->d_desc, h->gs, h->d_grad, h->stream, &g_launches, &h->timer)))
     return cuda_fail(e, "gradient launch");
   int hs[4];
   double vals[5];
@@ -481,42 +705,9 @@ int mra_loglik_grad(mra_handle* h, const mra_params* theta, double* loglik_out, 
   return MRA_OK;
 }
 
-int mra_update(mra_handle* h, const double* locs, const double* y, int where) {
-  g_err.clear();
-  if (!h || !locs || !y) return fail(MRA_ERR_ARG, "null argument");
-  if (where != MRA_HOST && where != MRA_DEVICE) return fail(MRA_ERR_ARG, "where must be MRA_HOST or MRA_DEVICE");
-  const int64_t n = h->n, nl = int64_t(1) << (2 * h->M);
-  cudaError_t e;
-  const double* dl = locs;
-  const double* dy = y;
-  h->have_post = false;
-  if (where == MRA_HOST) {
-    if ((e = cudaMemcpyAsync(h->in_locs, locs, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, h->stream)) ||
-        (e = cudaMemcpyAsync(h->in_y, y, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream)))
-      return cuda_fail(e, "copy inputs");
-    dl = h->in_locs;
-    dy = h->in_y;
-  }
-  if ((e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream))) return cuda_fail(e, "memset");
-  if ((e = mra::launch_bin(dl, n, h->bbox, h->M, h->leaf_id, h->counts, h->cursor, h->off, h->sq_off,
-                           h->max_count, h->perm, h->status, h->stream, &g_launches)) ||
-      (e = mra::launch_gather(dl, dy, h->perm, n, h->xs, h->ys, h->yv, h->stream, &g_launches)))
-    return cuda_fail(e, "binning");
-  int hs[4];
-  double got[2];
-  const double* srcs[2] = {(const double*)(h->sq_off + nl), (const double*)h->max_count};
-  if ((e = sync_status(h, hs, got, 2, srcs))) return cuda_fail(e, "binning");
-  if (hs[0]) return status_error(hs);
-  int64_t tail;
-  int32_t mc;
-  memcpy(&tail, &got[0], sizeof tail);
-  memcpy(&mc, &got[1], sizeof mc);
-  if (mc > h->nlmax || tail > h->ls_cap)
-    return fail(MRA_ERR_LIMIT, "new partition needs leaves of %d (handle has %d) or %lld leaf-factor doubles "
-                "(handle has %lld); build a new handle", mc, h->nlmax, (long long)tail, (long long)h->ls_cap);
-  return MRA_OK;
-}
-
+// ---------------------------------------------------------------------------
+// Timing
+// ---------------------------------------------------------------------------
 int mra_enable_timing(mra_handle* h, int on) {
   g_err.clear();
   if (!h) return fail(MRA_ERR_ARG, "null handle");
@@ -542,10 +733,14 @@ int mra_kernel_times(mra_handle* h, int kind, double* total_ms, int64_t* launche
   return MRA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Prediction
+// ---------------------------------------------------------------------------
 int mra_predict(mra_handle* h, const mra_params* theta, const double* plocs, int64_t np, int where,
                 double* mean_out, double* var_out) {
   g_err.clear();
   if (!h || !theta || !plocs || !mean_out || !var_out) return fail(MRA_ERR_ARG, "null argument");
+  if (!h->parts.empty()) return fail(MRA_ERR_STATE, "not available on a batch handle");
   if (np < 1) return fail(MRA_ERR_ARG, "np must be >= 1");
   if (where != MRA_HOST && where != MRA_DEVICE) return fail(MRA_ERR_ARG, "where must be MRA_HOST or MRA_DEVICE");
   if (!h->have_post) return fail(MRA_ERR_STATE, "call mra_loglik before mra_predict");
@@ -556,7 +751,6 @@ int mra_predict(mra_handle* h, const mra_params* theta, const double* plocs, int
   cudaError_t e;
   if (np > h->pred_cap) {
     h->pred.release();
-  h->grad.release();
     Arena& P = h->pred;
     P.want(&h->p_in, 2 * np);
     P.want(&h->p_xs, np);
@@ -603,17 +797,263 @@ int mra_predict(mra_handle* h, const mra_params* theta, const double* plocs, int
   ps.U = h->p_U;
   ps.mean = where == MRA_DEVICE ? mean_out : h->p_mean;
   ps.var = where == MRA_DEVICE ? var_out : h->p_var;
-  mra::Cov cv{theta->sigma2, theta->range, h->cfg.cov_family, h->cfg.nonstat};
-  if ((e = mra::launch_predict(shape_of(h), cv, h->st, h->lf, h->nlmax, ps, maxp, h->stream, &g_launches,
-                               &h->timer)))
+  if ((e = mra::launch_predict(h->d_desc, M, r, h->nlmax, ps, maxp, h->status, h->stream, &g_launches, &h->timer)))
     return cuda_fail(e, "predict launch");
   if (where == MRA_HOST) {
     if ((e = cudaMemcpyAsync(mean_out, h->p_mean, sizeof(double) * np, cudaMemcpyDeviceToHost, h->stream)) ||
         (e = cudaMemcpyAsync(var_out, h->p_var, sizeof(double) * np, cudaMemcpyDeviceToHost, h->stream)))
       return cuda_fail(e, "copy predictions");
   }
-  if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "predict");
+  if ((e = sync_status(h, hs, got, 0, srcs))) return cuda_fail(e, "predict");
   collect_times(h);
+  if (hs[0]) return status_error(hs);
+  return MRA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches of datasets
+// ---------------------------------------------------------------------------
+int mra_build_batch(const mra_config* cfgs, const double* const* locs, const double* const* ys, const int64_t* ns,
+                    int ndata, int where, mra_handle** out) {
+  g_err.clear();
+  if (!out) return fail(MRA_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (!cfgs || !locs || !ys || !ns || ndata < 1) return fail(MRA_ERR_ARG, "need at least one dataset");
+  for (int d = 1; d < ndata; ++d)
+    if (cfgs[d].r != cfgs[0].r || cfgs[d].precision != cfgs[0].precision)
+      return fail(MRA_ERR_ARG, "all datasets of a batch need the same r and precision (dataset %d differs)", d);
+  mra_handle* h = new mra_handle();
+  h->cfg = cfgs[0];
+  h->r = cfgs[0].r;
+  for (int d = 0; d < ndata; ++d) {
+    mra_handle* p = nullptr;
+    int rc = mra_build(&cfgs[d], locs[d], ys[d], ns[d], where, &p);
+    if (rc) {
+      std::string msg = g_err;
+      mra_free(h);
+      return fail(rc, "dataset %d: %s", d, msg.c_str());
+    }
+    h->parts.push_back(p);
+    h->M = std::max(h->M, p->M);
+    h->nlmax = std::max(h->nlmax, p->nlmax);
+    h->n += p->n;
+  }
+  // work lists: one launch per level over every dataset's regions at that depth
+  std::vector<int2> items;
+  std::vector<std::pair<int, size_t>> lists;   // (count, start) in the order below
+  auto add_list = [&](auto&& gen) {
+    const size_t start = items.size();
+    gen();
+    lists.push_back({(int)(items.size() - start), start});
+  };
+  const int maxM = h->M;
+  for (int m = 0; m < maxM; ++m)
+    add_list([&] {
+      for (int d = 0; d < ndata; ++d)
+        if (h->parts[d]->M > m)
+          for (int32_t c = 0; c < h->parts[d]->tab.nreg[m]; ++c) items.push_back(make_int2(d, c));
+    });
+  for (int m = 1; m < maxM; ++m)
+    add_list([&] {
+      for (int d = 0; d < ndata; ++d)
+        if (h->parts[d]->M > m)
+          for (int32_t c = 0; c < h->parts[d]->tab.nreg[m - 1]; ++c) items.push_back(make_int2(d, c));
+    });
+  add_list([&] {
+    for (int d = 0; d < ndata; ++d)
+      for (int32_t c = 0; c < h->parts[d]->tab.nreg[h->parts[d]->M]; ++c) items.push_back(make_int2(d, c));
+  });
+  add_list([&] {
+    for (int d = 0; d < ndata; ++d)
+      if (h->parts[d]->M > 0)
+        for (int32_t c = 0; c < h->parts[d]->tab.nreg[h->parts[d]->M - 1]; ++c) items.push_back(make_int2(d, c));
+  });
+  int2* d_items = nullptr;
+  Arena& A = h->batch;
+  A.want(&d_items, std::max<size_t>(items.size(), 1));
+  A.want(&h->d_descs, ndata);
+  A.want(&h->d_roots, 2 * (size_t)ndata);
+  A.want(&h->status, 4);
+  cudaError_t e;
+  if ((e = A.commit())) { mra_free(h); return fail(MRA_ERR_OOM, "device allocation (batch): %s", cudaGetErrorString(e)); }
+  if ((e = cudaMallocHost((void**)&h->pinned, (64 + 2 * (size_t)ndata) * sizeof(double))) ||
+      (e = cudaMallocHost((void**)&h->pinned_descs, sizeof(mra::Desc) * ndata))) {
+    mra_free(h); return cuda_fail(e, "cudaMallocHost");
+  }
+  if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking))) { mra_free(h); return cuda_fail(e, "stream"); }
+  h->own_stream = 1;
+  if (!items.empty() &&
+      (e = cudaMemcpy(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice))) {
+    mra_free(h); return cuda_fail(e, "work lists");
+  }
+  mra::Plan& p = h->plan;
+  p = mra::Plan();
+  p.maxM = maxM;
+  p.tile = mra::tile_for_r(h->r);
+  p.mixed = h->cfg.precision == MRA_PREC_MIXED;
+  p.nlmax = h->nlmax;
+  int li = 0;
+  for (int m = 0; m < maxM; ++m, ++li) { p.n_lvl[m] = lists[li].first; p.w_lvl[m] = d_items + lists[li].second; }
+  for (int m = 1; m < maxM; ++m, ++li) { p.n_agg[m] = lists[li].first; p.w_agg[m] = d_items + lists[li].second; }
+  p.n_leaf = lists[li].first; p.w_leaf = d_items + lists[li].second; ++li;
+  p.n_syrk = lists[li].first; p.w_syrk = d_items + lists[li].second; ++li;
+  for (int d = 0; d < ndata; ++d) p.t_syrk = std::max(p.t_syrk, h->parts[d]->M * (h->parts[d]->M + 1) / 2);
+  h->h_descs.resize(ndata);
+  for (int d = 0; d < ndata; ++d) {
+    mra_handle* q = h->parts[d];
+    mra_params th{1.0, 1.0, 0.0};
+    upload_desc(q, &th);               // fills q->hd (the copy to q's own descriptor is harmless)
+    h->h_descs[d] = q->hd;
+    h->h_descs[d].nlmax = h->nlmax;    // one shared-memory layout for the whole batch
+  }
+  if ((e = cudaDeviceSynchronize())) { mra_free(h); return cuda_fail(e, "batch set-up"); }
+  size_t need = p.mixed ? mra::leaf_tc_smem_bytes(h->nlmax) : mra::leaf_smem_bytes(h->r, h->nlmax);
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if ((size_t)optin < need) { mra_free(h); return fail(MRA_ERR_LIMIT, "leaf kernel shared memory exceeds the device limit"); }
+  *out = h;
+  return MRA_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Descriptors, one batched evaluation, roots to the pinned buffer (stream-ordered).
+cudaError_t batch_sequence(mra_handle* h) {
+  const int nd = (int)h->parts.size();
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(h->d_descs, h->pinned_descs, sizeof(mra::Desc) * nd, cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream)))
+    return e;
+  if ((e = mra::launch_loglik(h->plan, h->d_descs, h->status, h->stream, &g_launches, &h->timer))) return e;
+  if ((e = mra::launch_gather_roots(h->d_descs, nd, h->d_roots, h->stream, &g_launches))) return e;
+  if ((e = cudaMemcpyAsync(h->pinned + 64, h->d_roots, sizeof(double) * 2 * nd, cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaMemcpyAsync(h->pinned, h->status, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream)))
+    return e;
+  return cudaSuccess;
+}
+
+int batch_results(mra_handle* h, double* loglik_out) {
+  int hs[4];
+  memcpy(hs, h->pinned, sizeof hs);
+  if (hs[0]) return status_error(hs);
+  for (size_t d = 0; d < h->parts.size(); ++d)
+    loglik_out[d] = -0.5 * (h->pinned[64 + 2 * d] + h->pinned[64 + 2 * d + 1]) -
+                    0.5 * (double)h->parts[d]->n * std::log(2.0 * M_PI);
+  return MRA_OK;
+}
+
+int set_batch_params(mra_handle* h, const mra_params* thetas) {
+  for (size_t d = 0; d < h->parts.size(); ++d) {
+    if (!params_ok(&thetas[d])) return fail(MRA_ERR_ARG, "theta of dataset %zu is invalid", d);
+    h->h_descs[d].cv = mra::Cov{thetas[d].sigma2, thetas[d].range, h->parts[d]->cfg.cov_family, h->parts[d]->cfg.nonstat};
+    h->h_descs[d].tau2 = thetas[d].tau2;
+  }
+  memcpy(h->pinned_descs, h->h_descs.data(), sizeof(mra::Desc) * h->parts.size());
+  return MRA_OK;
+}
+
+void drop_graph(mra_handle* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->gexec = nullptr;
+  h->graph = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mra_autotune(mra_handle* h, const mra_params* thetas, int* tile_out) {
+  g_err.clear();
+  if (!h || !thetas) return fail(MRA_ERR_ARG, "null argument");
+  const bool is_batch = !h->parts.empty();
+  int cands[3], nc = 0;
+  const int base = mra::tile_for_r(h->r);
+  for (int t : {16, 32, 64})
+    if (t >= base) cands[nc++] = t;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return fail(MRA_ERR_CUDA, "cudaEventCreate failed");
+  float best = 1e30f;
+  int best_tile = base;
+  std::vector<double> tmp(is_batch ? h->parts.size() : 1);
+  const bool timer_was_on = h->timer.on;
+  h->timer.on = false;
+  int rc = MRA_OK;
+  for (int k = 0; k < nc && !rc; ++k) {
+    h->plan.tile = cands[k];
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && !rc; ++rep) {
+      cudaEventRecord(e0, h->stream);
+      if (is_batch) {
+        rc = set_batch_params(h, thetas);
+        if (!rc) {
+          cudaError_t e = batch_sequence(h);
+          if (!e) e = cudaStreamSynchronize(h->stream);
+          rc = e ? cuda_fail(e, "autotune") : batch_results(h, tmp.data());
+        }
+      } else {
+        rc = mra_loglik(h, thetas, tmp.data());
+      }
+      cudaEventRecord(e1, h->stream);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (!rc && ms < best) { best = ms; best_tile = cands[k]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->timer.on = timer_was_on;
+  h->plan.tile = best_tile;
+  if (rc) return rc;
+  h->tuned = true;
+  drop_graph(h);
+  if (tile_out) *tile_out = best_tile;
+  return MRA_OK;
+}
+
+int mra_loglik_batch(mra_handle* h, const mra_params* thetas, double* loglik_out) {
+  g_err.clear();
+  if (!h || !thetas || !loglik_out) return fail(MRA_ERR_ARG, "null argument");
+  if (h->parts.empty()) return fail(MRA_ERR_STATE, "not a batch handle (use mra_build_batch)");
+  int rc;
+  if (!h->tuned && (rc = mra_autotune(h, thetas, nullptr))) return rc;
+  if ((rc = set_batch_params(h, thetas))) return rc;
+  cudaError_t e;
+  if (h->timer.on) {   // per-kernel events: run the launches directly
+    if ((e = batch_sequence(h)) || (e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "batch");
+    collect_times(h);
+    return batch_results(h, loglik_out);
+  }
+  if (!h->gexec) {
+    if ((e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal))) return cuda_fail(e, "graph capture");
+    const int64_t before = g_launches;
+    cudaError_t e1 = batch_sequence(h);
+    h->graph_launches = g_launches - before;
+    g_launches = before;
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &h->graph);
+    if (e1 || e2) {
+      drop_graph(h);
+      return cuda_fail(e1 ? e1 : e2, "graph capture");
+    }
+    if ((e = cudaGraphInstantiate(&h->gexec, h->graph, 0))) {
+      drop_graph(h);
+      return cuda_fail(e, "graph instantiate");
+    }
+  }
+  if ((e = cudaGraphLaunch(h->gexec, h->stream)) || (e = cudaStreamSynchronize(h->stream)))
+    return cuda_fail(e, "graph launch");
+  g_launches += h->graph_launches;
+  return batch_results(h, loglik_out);
+}
+
+int mra_batch_info(mra_handle* h, int* ndata_out, int* tile_out) {
+  g_err.clear();
+  if (!h || !ndata_out) return fail(MRA_ERR_ARG, "null argument");
+  *ndata_out = (int)h->parts.size();
+  if (tile_out) *tile_out = h->plan.tile;
   return MRA_OK;
 }
 

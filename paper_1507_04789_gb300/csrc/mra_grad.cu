@@ -172,8 +172,11 @@ __device__ void chol_inverse_adjoint(double* B0, double* B1, double* B2, long ld
 // Posterior adjoint, level m (top-down).
 // ---------------------------------------------------------------------------
 template <int TILE>
-__global__ void __launch_bounds__(NT) post_adjoint_kernel(int m, Shape sh, LevelState st, GradState gs) {
+__global__ void __launch_bounds__(NT) post_adjoint_kernel(int m, const Desc* __restrict__ D, GradState gs) {
   extern __shared__ double smem[];
+  const Desc& ds = D[0];
+  const Shape sh = ds.sh;
+  const LevelState& st = ds.st;
   const int r = sh.r, mr = m * r;
   const long i = blockIdx.x;
   const long ld = r + 1;
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(NT) post_adjoint_kernel(int m, Shape sh, Level
   double* B2 = B1 + MAX_R_DEV * (MAX_R_DEV + 1);
   double* stg = B2 + MAX_R_DEV * (MAX_R_DEV + 1);
   long anc[MAXL];
-  for (int l = 0; l <= m; ++l) anc[l] = i >> (2 * (m - l));
+  for (int l = 0; l <= m; ++l) anc[l] = ancestor(st, m, i, l);
   for (int t = threadIdx.x; t < mr; t += NT) {
     int k = t / r;
     wbar[t] = gs.Obar[k][anc[k] * r + (t - k * r)];
@@ -258,13 +261,18 @@ __global__ void __launch_bounds__(NT) post_adjoint_kernel(int m, Shape sh, Level
 // Leaf adjoint: one CTA per leaf.
 // ---------------------------------------------------------------------------
 template <int TILE>
-__global__ void __launch_bounds__(NT) leaf_adjoint_kernel(Shape sh, Cov cv, LevelState st, LeafState lf,
-                                                          GradState gs, long slot0) {
+__global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict__ D, GradState gs, long slot0) {
   extern __shared__ double smem[];
+  const Desc& ds = D[0];
+  const Shape sh = ds.sh;
+  const Cov cv = ds.cv;
+  const LevelState& st = ds.st;
+  const LeafState& lf = ds.lf;
   const int M = sh.M, r = sh.r, Mr = M * r;
-  const long F = blockIdx.x;
-  const long o0 = lf.off[F];
-  const int nF = (int)(lf.off[F + 1] - o0);
+  const long F = blockIdx.x;                     // compact leaf id
+  const long Fm = st.mort[M][F];
+  const long o0 = lf.off[Fm];
+  const int nF = (int)(lf.off[Fm + 1] - o0);
   double* wbar = smem;                      // M r
   double* zb = wbar + MAXL * MAX_R_DEV;     // nF (<= MAX_LEAF)
   double* sx = zb + 128;
@@ -276,7 +284,7 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(Shape sh, Cov cv, Leve
   double g_s2 = 0.0, g_k = 0.0, g_t = 0.0;
   if (nF > 0) {
     long anc[MAXL];
-    for (int l = 0; l < M; ++l) anc[l] = F >> (2 * (M - l));
+    for (int l = 0; l < M; ++l) anc[l] = ancestor(st, M, F, l);
     for (int t = threadIdx.x; t < Mr; t += NT) {
       int k = t / r;
       wbar[t] = gs.Obar[k][anc[k] * r + (t - k * r)];
@@ -293,9 +301,9 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(Shape sh, Cov cv, Leve
     double* HB = gs.HB + o0 * Mr;
     double* VB = gs.VBF + o0 * Mr;
     double* XB = gs.XBF + o0 * Mr;
-    const double* LSi = lf.LS + lf.sq_off[F];
-    const double* LSf = lf.LSf + lf.sq_off[F];
-    double* T1 = gs.T + 3 * lf.sq_off[F];     // three nF x nF scratch blocks per leaf
+    const double* LSi = lf.LS + lf.sq_off[Fm];
+    const double* LSf = lf.LSf + lf.sq_off[Fm];
+    double* T1 = gs.T + 3 * lf.sq_off[Fm];     // three nF x nF scratch blocks per leaf
     double* T2 = T1 + (long)nF * nF;
     double* T3 = T2 + (long)nF * nF;
     const int nrt = (nF + TILE - 1) / TILE;
@@ -393,7 +401,7 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(Shape sh, Cov cv, Leve
       const double* Lia = st.Li[l] + a * (long)r * r;
       const double* Va = st.V[l] + a * (long)r * (l * r);
       __syncthreads();
-      load_knots(sh.bbox, l, a, sh.gx, sh.gy, ax, ay);
+      load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
       __syncthreads();
       for (int rt = 0; rt < nrt; ++rt) {
         const int nrow = min(TILE, nF - rt * TILE);
@@ -447,15 +455,19 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(Shape sh, Cov cv, Leve
 //   k = l :  sum_rows Vbar^l' V^l      (times L_l' at the ancestor: adjoint of L_l^{-1})
 // ---------------------------------------------------------------------------
 template <int TILE>
-__global__ void __launch_bounds__(NT) leaf_partial_kernel(Shape sh, LeafState lf, GradState gs) {
+__global__ void __launch_bounds__(NT) leaf_partial_kernel(const Desc* __restrict__ D, GradState gs) {
   extern __shared__ double smem[];
+  const Desc& ds = D[0];
+  const Shape sh = ds.sh;
+  const LeafState& lf = ds.lf;
   const int M = sh.M, r = sh.r, Mr = M * r;
-  const long p = blockIdx.x;
+  const long p = blockIdx.x;                     // compact id at level M-1
+  const long pm = ds.st.mort[M - 1][p];
   const int t = blockIdx.y;
   int l = 0;
   while (tri_index(l + 1, 0) <= t) ++l;
   const int k = t - tri_index(l, 0);
-  const long row0 = lf.off[4 * p], row1 = lf.off[4 * p + 4];
+  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
   const int K = (int)(row1 - row0);
   const double* Ab = (k < l ? gs.XBF : gs.VBF) + row0 * Mr + l * r;
   const double* Bb = lf.VF + row0 * Mr + k * r;
@@ -470,9 +482,13 @@ __global__ void __launch_bounds__(NT) leaf_partial_kernel(Shape sh, LeafState lf
 // Prior adjoint, level m (bottom-up): one CTA per region.
 // ---------------------------------------------------------------------------
 template <int TILE>
-__global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, Shape sh, Cov cv, LevelState st, GradState gs,
+__global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __restrict__ D, GradState gs,
                                                            long slot0) {
   extern __shared__ double smem[];
+  const Desc& ds = D[0];
+  const Shape sh = ds.sh;
+  const Cov cv = ds.cv;
+  const LevelState& st = ds.st;
   const int r = sh.r, mr = m * r;
   const long i = blockIdx.x;
   const long ld = r + 1;
@@ -487,16 +503,17 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, Shape sh, Cov 
   double* stg = B2 + MAX_R_DEV * (MAX_R_DEV + 1);
   const bool from_leaves = (m + 1 == sh.M);
   const int Tin = (m + 1) * (m + 2) / 2;   // incoming tiles, l <= m
-  // incoming tile (l, k): sum over children (fixed order)
+  const long cf = from_leaves ? 0 : st.cfirst[m][i], cc = from_leaves ? 0 : st.ccnt[m][i];
+  // incoming tile (l, k): sum over the active children (fixed order)
   auto incoming = [&](int l, int k, int a, int b) -> double {
     const long t = tri_index(l, k);
     if (from_leaves) return gs.PartLeaf[(i * Tin + t) * (long)r * r + a * r + b];
     double s = 0.0;
-    for (int c = 0; c < 4; ++c) s += gs.Up[m + 1][((4 * i + c) * Tin + t) * (long)r * r + a * r + b];
+    for (long c = cf; c < cf + cc; ++c) s += gs.Up[m + 1][(c * Tin + t) * (long)r * r + a * r + b];
     return s;
   };
   double g_s2 = 0.0, g_k = 0.0;
-  load_knots(sh.bbox, m, i, sh.gx, sh.gy, qx, qy);
+  load_knots(sh.bbox, m, st.mort[m][i], sh.gx, sh.gy, qx, qy);
   const double* L = st.L[m] + i * (long)r * r;
   const double* Li = st.Li[m] + i * (long)r * r;
   const double* V = st.V[m] + i * (long)r * mr;
@@ -541,11 +558,11 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, Shape sh, Cov 
   }
   // chain adjoint
   for (int l = m - 1; l >= 0; --l) {
-    const long a = i >> (2 * (m - l));
+    const long a = ancestor(st, m, i, l);
     const double* Lia = st.Li[l] + a * (long)r * r;
     const double* Va = st.V[l] + a * (long)r * (l * r);
     __syncthreads();
-    load_knots(sh.bbox, l, a, sh.gx, sh.gy, ax, ay);
+    load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
     __syncthreads();
     acc.zero();
     tile_mma<TILE>(acc, VB + l * r, mr, 1, r, Lia, 1, r, r, r, stg);
@@ -634,40 +651,41 @@ static int tile_of(int r) { return r <= 16 ? 16 : (r <= 32 ? 32 : 64); }
     }                                                                                                   \
   } while (0)
 
-cudaError_t launch_grad(const Shape& sh, const Cov& cv, const LevelState& st, const LeafState& lf,
-                        const GradState& gs, double* grad_out_dev, cudaStream_t s, int64_t* launches, Timer* tm) {
-  const int tile = tile_of(sh.r);
-  const int M = sh.M;
+cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs, double* grad_out_dev,
+                        cudaStream_t s, int64_t* launches, Timer* tm) {
+  const int tile = tile_of(hd.sh.r);
+  const int M = hd.sh.M;
+  const LevelState& st = hd.st;
   cudaError_t e;
   const size_t stg = sizeof(double) * 2 * KC * (tile + 2);
   const size_t sq = sizeof(double) * 3 * MAX_R_DEV * (MAX_R_DEV + 1);
   // slots: prior-adjoint CTAs of levels 0..M-1, then the leaves
   long slot_leaf = 0;
-  for (int m = 0; m < M; ++m) slot_leaf += 1L << (2 * m);
+  for (int m = 0; m < M; ++m) slot_leaf += st.nreg[m];
   tm->start(6, s);
   for (int m = 0; m < M; ++m) {
     size_t sm = sizeof(double) * (MAXL * MAX_R_DEV + MAX_R_DEV) + sq + stg;
-    MRA_GRAD_LAUNCH(tile, post_adjoint_kernel, dim3(1u << (2 * m)), sm, s, m, sh, st, gs);
+    MRA_GRAD_LAUNCH(tile, post_adjoint_kernel, dim3(st.nreg[m]), sm, s, m, d_desc, gs);
     ++*launches;
   }
   {
     size_t sm = sizeof(double) * (MAXL * MAX_R_DEV + 3 * 128 + 2 * MAX_R_DEV + 32) + stg;
-    MRA_GRAD_LAUNCH(tile, leaf_adjoint_kernel, dim3(1u << (2 * M)), sm, s, sh, cv, st, lf, gs, slot_leaf);
+    MRA_GRAD_LAUNCH(tile, leaf_adjoint_kernel, dim3(st.nreg[M]), sm, s, d_desc, gs, slot_leaf);
     ++*launches;
   }
   if (M > 0) {
-    dim3 grid(1u << (2 * (M - 1)), M * (M + 1) / 2);
-    MRA_GRAD_LAUNCH(tile, leaf_partial_kernel, grid, stg, s, sh, lf, gs);
+    dim3 grid(st.nreg[M - 1], M * (M + 1) / 2);
+    MRA_GRAD_LAUNCH(tile, leaf_partial_kernel, grid, stg, s, d_desc, gs);
     ++*launches;
   }
   long slot = slot_leaf;
   for (int m = M - 1; m >= 0; --m) {
-    slot -= 1L << (2 * m);
+    slot -= st.nreg[m];
     size_t sm = sizeof(double) * (4 * MAX_R_DEV + 32) + sq + stg;
-    MRA_GRAD_LAUNCH(tile, prior_adjoint_kernel, dim3(1u << (2 * m)), sm, s, m, sh, cv, st, gs, slot);
+    MRA_GRAD_LAUNCH(tile, prior_adjoint_kernel, dim3(st.nreg[m]), sm, s, m, d_desc, gs, slot);
     ++*launches;
   }
-  grad_reduce_kernel<<<1, NT, 0, s>>>(gs.gpart, slot_leaf + (1L << (2 * M)), grad_out_dev);
+  grad_reduce_kernel<<<1, NT, 0, s>>>(gs.gpart, slot_leaf + st.nreg[M], grad_out_dev);
   ++*launches;
   tm->stop(s);
   return cudaGetLastError();

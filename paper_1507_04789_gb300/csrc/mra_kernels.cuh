@@ -27,6 +27,14 @@ constexpr int MAXL = 13;   // levels 0..12
 
 // Pointers to the per-level state of one handle (passed to kernels by value).
 struct LevelState {
+  // tree: the active regions of every level (those whose subtree holds at
+  // least one observation), in Morton order; a complete tree has identity tables
+  int32_t* mort[MAXL];    // level m (0..M): compact id -> Morton id
+  int32_t* par[MAXL];     // level m (1..M): compact id -> compact id of the parent
+  int32_t* cfirst[MAXL];  // level m (0..M-1): compact id of the first active child
+  int32_t* ccnt[MAXL];    // number of active children (consecutive compact ids)
+  int32_t* cid[MAXL];     // level m: Morton id -> compact id, -1 if inactive (4^m entries)
+  int nreg[MAXL];         // active regions per level
   // prior, internal levels m < M
   double* V[MAXL];    // 4^m x r x (m r): [V^0_R .. V^{m-1}_R] per region, row-major
   double* Li[MAXL];   // 4^m x r x r: L_R^{-1} (lower, zero above the diagonal)
@@ -43,17 +51,23 @@ struct LevelState {
   double* Ltf[MAXL];  // 4^m x r x r: Lt (Cholesky factor of I + Ahat^{m,m})
 };
 
+// Compact id of the level-l ancestor of compact region c of level m.
+__device__ __forceinline__ long ancestor(const LevelState& st, int m, long c, int l) {
+  for (int t = m; t > l; --t) c = st.par[t][c];
+  return c;
+}
+
 struct LeafState {
-  const int64_t* off;     // 4^M + 1 leaf offsets into the sorted observations
-  const int64_t* sq_off;  // 4^M + 1 prefix sums of n_F^2
+  const int64_t* off;     // 4^M + 1 leaf offsets into the sorted observations (by Morton id)
+  const int64_t* sq_off;  // 4^M + 1 prefix sums of n_F^2 (by Morton id)
   const double* xs;       // sorted x
   const double* ys;       // sorted y coordinate
   const double* yv;       // sorted data
   double* H;              // n x (M r): V_F, then H_F = L_Sigma^{-1} V_F
   double* z;              // n: L_Sigma^{-1} y_F
   double* LS;             // ragged n_F x n_F: L_Sigma^{-1}
-  double* d;              // 4^M: log|Sigma_F|
-  double* u;              // 4^M: y_F' Sigma_F^{-1} y_F
+  double* d;              // per active leaf: log|Sigma_F|
+  double* u;              // per active leaf: y_F' Sigma_F^{-1} y_F
   // saved for the gradient (null when no gradient is requested)
   double* VF;             // n x (M r): V_F before the L_Sigma^{-1} solve
   double* LSf;            // ragged n_F x n_F: L_Sigma
@@ -91,5 +105,31 @@ struct Shape {
   double bbox[4];
   int mixed;              // 1: tensor-core (3xTF32) prior and leaf contractions
 };
+
+// Everything a kernel needs about one dataset, in device memory.  A single
+// problem is a batch of one; batched launches map every CTA to a (dataset,
+// region) pair through a work list.
+struct Desc {
+  Shape sh;
+  Cov cv;
+  double tau2;
+  int nlmax;          // largest leaf occupancy (shared-memory layout of the leaf kernels)
+  int pad;
+  LevelState st;
+  LeafState lf;
+};
+
+// (dataset, compact region) of this CTA; `work` null means dataset 0, region blockIdx.x.
+struct Item {
+  int d;
+  long i;
+};
+__device__ __forceinline__ Item work_item(const int2* work) {
+  if (work) {
+    const int2 w = work[blockIdx.x];
+    return {w.x, (long)w.y};
+  }
+  return {0, (long)blockIdx.x};
+}
 
 }  // namespace mra

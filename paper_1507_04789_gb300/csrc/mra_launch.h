@@ -37,27 +37,46 @@ cudaError_t launch_gather(const double* locs, const double* y, const int64_t* pe
 cudaError_t launch_gather_y(const double* y, const int64_t* perm, int64_t n, double* yv,
                             cudaStream_t s, int64_t* launches);
 
+// Launch plan of one evaluation: per level, the CTAs (work items, or null for
+// "dataset 0, compact region blockIdx.x") of the prior/posterior kernels
+// (n_lvl[m]), of the aggregation into level m-1 (n_agg[m]), of the leaves and
+// of the leaf Gram products.
+struct Plan {
+  int maxM = 0, tile = 64, mixed = 0, nlmax = 1;
+  const int2* w_lvl[MAXL] = {};
+  int n_lvl[MAXL] = {};
+  const int2* w_agg[MAXL] = {};
+  int n_agg[MAXL] = {};
+  const int2* w_leaf = nullptr;
+  int n_leaf = 0;
+  const int2* w_syrk = nullptr;
+  int n_syrk = 0, t_syrk = 1;
+};
+
 // Prior pass, leaf pass and posterior pass (Sec. 3.1-3.3).
-cudaError_t launch_loglik(const Shape& sh, const Cov& cv, double tau2, const LevelState& st,
-                          const LeafState& lf, int nlmax, int* status, cudaStream_t s,
-                          int64_t* launches, Timer* timer);
+cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaStream_t s, int64_t* launches,
+                          Timer* timer);
+int tile_for_r(int r);
+// Root terms (d, u) of every dataset of a batch into out[2 d], out[2 d + 1].
+cudaError_t launch_gather_roots(const Desc* d_desc, int nd, double* out, cudaStream_t s, int64_t* launches);
 size_t leaf_smem_bytes(int r, int nlmax);
 
 // Mixed-precision prior level and leaf pass (tensor cores, mra_mixed.cu).
-cudaError_t launch_prior_tc(int m, const Shape& sh, const Cov& cv, const LevelState& st, int* status,
-                            cudaStream_t s);
-cudaError_t launch_leaf_tc(const Shape& sh, const Cov& cv, double tau2, const LevelState& st, const LeafState& lf,
-                           int nlmax, int* status, cudaStream_t s);
+cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nblocks, int* status, cudaStream_t s);
+cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int* status, cudaStream_t s);
 size_t leaf_tc_smem_bytes(int nlmax);
 
 // Prediction (Sec. 3.4, Prop. 2) at points binned into ps.
-cudaError_t launch_predict(const Shape& sh, const Cov& cv, const LevelState& st, const LeafState& lf, int nlmax,
-                           const PredState& ps, int max_per_leaf, cudaStream_t s, int64_t* launches, Timer* tm);
+cudaError_t launch_predict(const Desc* d_desc, int M, int r, int nlmax, const PredState& ps, int max_per_leaf,
+                           int* status, cudaStream_t s, int64_t* launches, Timer* tm);
 size_t predict_smem_bytes(int r, int nlmax);
 
 // Reverse-mode gradient after a forward pass that saved L, Lt, V_F and L_Sigma.
-cudaError_t launch_grad(const Shape& sh, const Cov& cv, const LevelState& st, const LeafState& lf,
-                        const GradState& gs, double* grad_out_dev, cudaStream_t s, int64_t* launches, Timer* tm);
+cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs, double* grad_out_dev,
+                        cudaStream_t s, int64_t* launches, Timer* tm);
+
+// Identity tables of a complete tree with M levels (for callers without host tables).
+cudaError_t launch_identity_tree(const LevelState& st, int M, cudaStream_t s, int64_t* launches);
 
 // Error text and launch counter shared by every entry point (mra_api.cu).
 void set_last_error(const char* msg);

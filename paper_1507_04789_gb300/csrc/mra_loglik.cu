@@ -20,11 +20,16 @@ namespace mra {
 // Prior pass, level m: region i computes its block row of the chain factor.
 // ---------------------------------------------------------------------------
 template <int TILE>
-__global__ void __launch_bounds__(NT) prior_level_kernel(int m, Shape sh, Cov cv, LevelState st,
-                                                         int* status) {
+__global__ void __launch_bounds__(NT) prior_level_kernel(int m, const Desc* __restrict__ D,
+                                                         const int2* __restrict__ work, int* status) {
   extern __shared__ double smem[];
+  const Item it = work_item(work);
+  const Desc& ds = D[it.d];
+  const Shape sh = ds.sh;
+  const Cov cv = ds.cv;
+  const LevelState& st = ds.st;
   const int r = sh.r, mr = m * r;
-  const long i = blockIdx.x;
+  const long i = it.i;
   double* qx = smem;                 // own knots
   double* qy = qx + MAX_R_DEV;
   double* ax = qy + MAX_R_DEV;       // ancestor knots
@@ -35,13 +40,13 @@ __global__ void __launch_bounds__(NT) prior_level_kernel(int m, Shape sh, Cov cv
   double* stg = W + MAX_R_DEV * (MAX_R_DEV + 1);
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
-  load_knots(sh.bbox, m, i, sh.gx, sh.gy, qx, qy);
+  load_knots(sh.bbox, m, st.mort[m][i], sh.gx, sh.gy, qx, qy);
   double* Vrow = st.V[m] + i * (long)r * mr;
   TileAcc<TILE> acc;
   for (int l = 0; l < m; ++l) {
-    const long a = i >> (2 * (m - l));
+    const long a = ancestor(st, m, i, l);
     __syncthreads();
-    load_knots(sh.bbox, l, a, sh.gx, sh.gy, ax, ay);
+    load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
     const double* Vanc = st.V[l] + a * (long)r * (l * r);
     acc.zero();
     if (l > 0) tile_mma<TILE>(acc, Vrow, mr, 1, r, Vanc, l * r, 1, r, l * r, stg);
@@ -93,13 +98,22 @@ __global__ void __launch_bounds__(NT) prior_level_kernel(int m, Shape sh, Cov cv
 // terms from the definition, Sec. 4.3 nugget).
 // ---------------------------------------------------------------------------
 template <int TILE>
-__global__ void __launch_bounds__(NT) leaf_kernel(Shape sh, Cov cv, double tau2, LevelState st,
-                                                  LeafState lf, int nlmax, int* status) {
+__global__ void __launch_bounds__(NT) leaf_kernel(const Desc* __restrict__ D, const int2* __restrict__ work,
+                                                  int* status) {
   extern __shared__ double smem[];
+  const Item it = work_item(work);
+  const Desc& ds = D[it.d];
+  const Shape sh = ds.sh;
+  const Cov cv = ds.cv;
+  const double tau2 = ds.tau2;
+  const int nlmax = ds.nlmax;
+  const LevelState& st = ds.st;
+  const LeafState& lf = ds.lf;
   const int M = sh.M, r = sh.r, Mr = M * r;
-  const long F = blockIdx.x;
-  const long o0 = lf.off[F];
-  const int nF = (int)(lf.off[F + 1] - o0);
+  const long F = it.i;                           // compact leaf id
+  const long Fm = st.mort[M][F];                 // its Morton id
+  const long o0 = lf.off[Fm];
+  const int nF = (int)(lf.off[Fm + 1] - o0);
   if (nF == 0) {
     if (threadIdx.x == 0) { lf.d[F] = 0.0; lf.u[F] = 0.0; }
     return;
@@ -127,9 +141,9 @@ __global__ void __launch_bounds__(NT) leaf_kernel(Shape sh, Cov cv, double tau2,
   constexpr int RM = TileAcc<TILE>::RM;
   // chain: V^l_F = (C0(S_F, Q_l) - sum_{k<l} V^k_F V^k_{R_l}') L_l^{-T}
   for (int l = 0; l < M; ++l) {
-    const long a = F >> (2 * (M - l));
+    const long a = ancestor(st, M, F, l);
     __syncthreads();
-    load_knots(sh.bbox, l, a, sh.gx, sh.gy, ax, ay);
+    load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
     const double* Vanc = st.V[l] + a * (long)r * (l * r);
     __syncthreads();
     for (int rt = 0; rt < nrt; ++rt) {
@@ -186,14 +200,14 @@ __global__ void __launch_bounds__(NT) leaf_kernel(Shape sh, Cov cv, double tau2,
   for (int t = threadIdx.x; t < nF; t += NT) ld += log(S[t * lds + t]);
   ld = 2.0 * block_sum(ld, red);
   if (lf.LSf) {
-    double* Lf = lf.LSf + lf.sq_off[F];
+    double* Lf = lf.LSf + lf.sq_off[Fm];
     for (int t = threadIdx.x; t < nF * nF; t += NT) Lf[t] = S[(t / nF) * lds + (t % nF)];
   }
   if (lf.VF) {
     for (long t = threadIdx.x; t < (long)nF * Mr; t += NT) lf.VF[o0 * Mr + t] = Hrow[t];
   }
   trinv_smem(S, nF, lds, tmp);
-  double* LS = lf.LS + lf.sq_off[F];
+  double* LS = lf.LS + lf.sq_off[Fm];
   for (int t = threadIdx.x; t < nF * nF; t += NT) LS[t] = S[(t / nF) * lds + (t % nF)];
   // z = L_Sigma^{-1} y
   double zz = 0.0;
@@ -234,15 +248,22 @@ __global__ void __launch_bounds__(NT) leaf_kernel(Shape sh, Cov cv, double tau2,
 // The children of p are leaves 4p..4p+3, whose rows are contiguous.
 // ---------------------------------------------------------------------------
 template <int TILE>
-__global__ void __launch_bounds__(NT) leaf_syrk_kernel(Shape sh, LevelState st, LeafState lf) {
+__global__ void __launch_bounds__(NT) leaf_syrk_kernel(const Desc* __restrict__ D, const int2* __restrict__ work) {
   extern __shared__ double smem[];
+  const Item it = work_item(work);
+  const Desc& ds = D[it.d];
+  const Shape sh = ds.sh;
+  const LevelState& st = ds.st;
+  const LeafState& lf = ds.lf;
   const int M = sh.M, r = sh.r, Mr = M * r;
-  const long p = blockIdx.x;
+  const long p = it.i;                           // compact id at level M-1
   const int t = blockIdx.y;
+  if (t >= M * (M + 1) / 2) return;              // fewer blocks in a shallower dataset
+  const long pm = st.mort[M - 1][p];
   int k = 0;
   while (tri_index(k + 1, 0) <= t) ++k;
   const int l = t - tri_index(k, 0);
-  const long row0 = lf.off[4 * p], row1 = lf.off[4 * p + 4];
+  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
   const int K = (int)(row1 - row0);
   const double* Hb = lf.H + row0 * Mr;
   TileAcc<TILE> acc;
@@ -274,11 +295,16 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel(Shape sh, LevelState st, 
 // u_R = sum_children u - g'g  (Sec. 3.3 in whitened form).
 // ---------------------------------------------------------------------------
 template <int TILE>
-__global__ void __launch_bounds__(NT) post_level_kernel(int m, Shape sh, LevelState st, LeafState lf,
-                                                        int* status) {
+__global__ void __launch_bounds__(NT) post_level_kernel(int m, const Desc* __restrict__ D,
+                                                        const int2* __restrict__ work, int* status) {
   extern __shared__ double smem[];
+  const Item it = work_item(work);
+  const Desc& ds = D[it.d];
+  const Shape sh = ds.sh;
+  const LevelState& st = ds.st;
+  const LeafState& lf = ds.lf;
   const int r = sh.r, mr = m * r;
-  const long i = blockIdx.x;
+  const long i = it.i;
   const int T = (m + 1) * (m + 2) / 2;
   const int ldw = r + 1;
   double* tmp = smem;
@@ -334,8 +360,8 @@ __global__ void __launch_bounds__(NT) post_level_kernel(int m, Shape sh, LevelSt
   }
   if (threadIdx.x == 0) {
     double dsum = 0.0, usum = 0.0;
-    for (int c = 0; c < 4; ++c) {
-      long ci = 4 * i + c;
+    const long cf = st.cfirst[m][i], cc = st.ccnt[m][i];
+    for (long ci = cf; ci < cf + cc; ++ci) {
       if (m + 1 == sh.M) { dsum += lf.d[ci]; usum += lf.u[ci]; }
       else { dsum += st.dd[m + 1][ci]; usum += st.uu[m + 1][ci]; }
     }
@@ -352,20 +378,27 @@ __global__ void __launch_bounds__(NT) post_level_kernel(int m, Shape sh, LevelSt
 // helpquantities).  The G rows of the four children are contiguous.
 // ---------------------------------------------------------------------------
 template <int TILE>
-__global__ void __launch_bounds__(NT) aggregate_kernel(int m, Shape sh, LevelState st) {
+__global__ void __launch_bounds__(NT) aggregate_kernel(int m, const Desc* __restrict__ D,
+                                                       const int2* __restrict__ work) {
   extern __shared__ double smem[];
+  const Item it = work_item(work);
+  const Desc& ds = D[it.d];
+  const Shape sh = ds.sh;
+  const LevelState& st = ds.st;
   const int r = sh.r, mr = m * r;
-  const long p = blockIdx.x;
+  const long p = it.i;                           // compact id at level m-1
   const int t = blockIdx.y;
+  if (t >= m * (m + 1) / 2) return;
   int k = 0;
   while (tri_index(k + 1, 0) <= t) ++k;
   const int l = t - tri_index(k, 0);
   const int Tc = (m + 1) * (m + 2) / 2;   // blocks per child (level m)
   const int Tp = m * (m + 1) / 2;         // blocks per parent (level m-1)
-  const double* Gb = st.G[m] + 4 * p * (long)r * mr;
+  const long cf = st.cfirst[m - 1][p], cc = st.ccnt[m - 1][p];   // children: compact ids cf..cf+cc-1
+  const double* Gb = st.G[m] + cf * (long)r * mr;
   TileAcc<TILE> acc;
   acc.zero();
-  tile_mma<TILE>(acc, Gb + k * r, 1, mr, r, Gb + l * r, 1, mr, r, 4 * r, smem);
+  tile_mma<TILE>(acc, Gb + k * r, 1, mr, r, Gb + l * r, 1, mr, r, (int)(cc * r), smem);
   double* out = st.Acc[m - 1] + (p * Tp + t) * (long)r * r;
 #pragma unroll
   for (int a = 0; a < TileAcc<TILE>::RM; ++a)
@@ -374,8 +407,7 @@ __global__ void __launch_bounds__(NT) aggregate_kernel(int m, Shape sh, LevelSta
       int row = acc.row(a), col = acc.col(b);
       if (row < r && col < r) {
         double s = -acc.v[a][b];
-        for (int c = 0; c < 4; ++c)
-          s += st.Acc[m][((4 * p + c) * Tc + t) * (long)r * r + row * r + col];
+        for (long c = cf; c < cf + cc; ++c) s += st.Acc[m][(c * Tc + t) * (long)r * r + row * r + col];
         out[row * r + col] = s;
       }
     }
@@ -383,8 +415,7 @@ __global__ void __launch_bounds__(NT) aggregate_kernel(int m, Shape sh, LevelSta
     double* om = st.Om[m - 1] + (p * m + k) * (long)r;
     for (int a = threadIdx.x; a < r; a += NT) {
       double s = 0.0;
-      for (int c = 0; c < 4; ++c) {
-        const long ci = 4 * p + c;
+      for (long ci = cf; ci < cf + cc; ++ci) {
         s += st.Om[m][(ci * (m + 1) + k) * (long)r + a];
         const double* Gc = st.G[m] + ci * (long)r * mr;
         const double* gc = st.gv[m] + ci * r;
@@ -426,63 +457,78 @@ static size_t syrk_smem(int tile) { return sizeof(double) * 2 * KC * (tile + 2);
   } while (0)
 
 
-cudaError_t launch_loglik(const Shape& sh, const Cov& cv, double tau2, const LevelState& st,
-                          const LeafState& lf, int nlmax, int* status, cudaStream_t s, int64_t* launches,
+cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaStream_t s, int64_t* launches,
                           Timer* tm) {
-  const int tile = tile_for(sh.r);
+  const int tile = pl.tile;
   cudaError_t e;
   // prior pass, top-down
-  for (int m = 0; m < sh.M; ++m) {
-    size_t sm = prior_smem(tile);
-    unsigned grid = 1u << (2 * m);
+  for (int m = 0; m < pl.maxM; ++m) {
+    if (pl.n_lvl[m] == 0) continue;
     tm->start(0, s);
-    if (sh.mixed) {
-      if ((e = launch_prior_tc(m, sh, cv, st, status, s))) return e;
+    if (pl.mixed) {
+      if ((e = launch_prior_tc(m, d_desc, pl.w_lvl[m], pl.n_lvl[m], status, s))) return e;
     } else {
-      MRA_LAUNCH(tile, prior_level_kernel, grid, sm, s, m, sh, cv, st, status);
+      MRA_LAUNCH(tile, prior_level_kernel, pl.n_lvl[m], prior_smem(tile), s, m, d_desc, pl.w_lvl[m], status);
     }
     tm->stop(s);
     ++*launches;
   }
   // leaves
-  {
-    size_t sm = leaf_smem(tile, nlmax);
-    unsigned grid = 1u << (2 * sh.M);
+  if (pl.n_leaf > 0) {
     tm->start(1, s);
-    if (sh.mixed) {
-      if ((e = launch_leaf_tc(sh, cv, tau2, st, lf, nlmax, status, s))) return e;
+    if (pl.mixed) {
+      if ((e = launch_leaf_tc(d_desc, pl.w_leaf, pl.n_leaf, pl.nlmax, status, s))) return e;
     } else {
-      MRA_LAUNCH(tile, leaf_kernel, grid, sm, s, sh, cv, tau2, st, lf, nlmax, status);
+      MRA_LAUNCH(tile, leaf_kernel, pl.n_leaf, leaf_smem(tile, pl.nlmax), s, d_desc, pl.w_leaf, status);
     }
     tm->stop(s);
     ++*launches;
   }
-  if (sh.M > 0) {
-    const int m = sh.M - 1;
-    dim3 grid(1u << (2 * m), (m + 1) * (m + 2) / 2);
-    size_t sm = syrk_smem(tile);
+  if (pl.n_syrk > 0) {
+    dim3 grid(pl.n_syrk, pl.t_syrk);
     tm->start(2, s);
-    MRA_LAUNCH(tile, leaf_syrk_kernel, grid, sm, s, sh, st, lf);
+    MRA_LAUNCH(tile, leaf_syrk_kernel, grid, syrk_smem(tile), s, d_desc, pl.w_syrk);
     tm->stop(s);
     ++*launches;
   }
   // posterior pass, bottom-up
-  for (int m = sh.M - 1; m >= 0; --m) {
-    size_t sm = post_smem(tile);
-    unsigned grid = 1u << (2 * m);
-    tm->start(3, s);
-    MRA_LAUNCH(tile, post_level_kernel, grid, sm, s, m, sh, st, lf, status);
-    tm->stop(s);
-    ++*launches;
-    if (m > 0) {
-      dim3 g2(1u << (2 * (m - 1)), m * (m + 1) / 2);
-      size_t s2 = syrk_smem(tile);
+  for (int m = pl.maxM - 1; m >= 0; --m) {
+    if (pl.n_lvl[m] > 0) {
+      tm->start(3, s);
+      MRA_LAUNCH(tile, post_level_kernel, pl.n_lvl[m], post_smem(tile), s, m, d_desc, pl.w_lvl[m], status);
+      tm->stop(s);
+      ++*launches;
+    }
+    if (m > 0 && pl.n_agg[m] > 0) {
+      dim3 g2(pl.n_agg[m], m * (m + 1) / 2);
       tm->start(4, s);
-      MRA_LAUNCH(tile, aggregate_kernel, g2, s2, s, m, sh, st);
+      MRA_LAUNCH(tile, aggregate_kernel, g2, syrk_smem(tile), s, m, d_desc, pl.w_agg[m]);
       tm->stop(s);
       ++*launches;
     }
   }
+  return cudaGetLastError();
+}
+
+int tile_for_r(int r) { return tile_for(r); }
+
+// -2 log L terms (d, u) at the root of every dataset of a batch.
+__global__ void gather_roots_kernel(const Desc* __restrict__ D, int nd, double* out) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= nd) return;
+  const Desc& ds = D[d];
+  if (ds.sh.M > 0) {
+    out[2 * d] = ds.st.dd[0][0];
+    out[2 * d + 1] = ds.st.uu[0][0];
+  } else {
+    out[2 * d] = ds.lf.d[0];
+    out[2 * d + 1] = ds.lf.u[0];
+  }
+}
+
+cudaError_t launch_gather_roots(const Desc* d_desc, int nd, double* out, cudaStream_t s, int64_t* launches) {
+  gather_roots_kernel<<<(nd + 127) / 128, 128, 0, s>>>(d_desc, nd, out);
+  ++*launches;
   return cudaGetLastError();
 }
 

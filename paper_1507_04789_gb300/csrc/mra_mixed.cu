@@ -13,13 +13,19 @@
 
 namespace mra {
 
-__global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, Shape sh, Cov cv, LevelState st, int* status) {
+__global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* __restrict__ D,
+                                                             const int2* __restrict__ work, int* status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ int fail, bad;
+  const Item it = work_item(work);
+  const Desc& ds = D[it.d];
+  const Shape sh = ds.sh;
+  const Cov cv = ds.cv;
+  const LevelState& st = ds.st;
   const int r = sh.r, mr = m * r;
-  const long i = blockIdx.x;
+  const long i = it.i;
   uint32_t* stage = reinterpret_cast<uint32_t*>(dsm);
   double* qx = reinterpret_cast<double*>(dsm + TC_STAGE_BYTES);
   double* qy = qx + MAX_R_DEV;
@@ -30,15 +36,15 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, Shape sh, Cov
   if (threadIdx.x == 0) bad = 0;
   TcCtx cx{stage, &mbar, 0, 0, &fail};
   tc_init(cx, &tmem_slot);
-  load_knots(sh.bbox, m, i, sh.gx, sh.gy, qx, qy);
+  load_knots(sh.bbox, m, st.mort[m][i], sh.gx, sh.gy, qx, qy);
   double* Vrow = st.V[m] + i * (long)r * mr;
   TcAcc acc;
   bool ok = true;
   const int row = acc.row(), c0 = acc.col0();
   for (int l = 0; l < m && ok; ++l) {
-    const long a = i >> (2 * (m - l));
+    const long a = ancestor(st, m, i, l);
     __syncthreads();
-    load_knots(sh.bbox, l, a, sh.gx, sh.gy, ax, ay);
+    load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
     const double* Vanc = st.V[l] + a * (long)r * (l * r);
     acc.zero();
     __syncthreads();
@@ -88,16 +94,25 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, Shape sh, Cov
   }
 }
 
-__global__ void __launch_bounds__(NT) leaf_kernel_tc(Shape sh, Cov cv, double tau2, LevelState st, LeafState lf,
-                                                     int nlmax, int* status) {
+__global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D, const int2* __restrict__ work,
+                                                     int* status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ int fail, bad;
+  const Item it = work_item(work);
+  const Desc& ds = D[it.d];
+  const Shape sh = ds.sh;
+  const Cov cv = ds.cv;
+  const double tau2 = ds.tau2;
+  const int nlmax = ds.nlmax;
+  const LevelState& st = ds.st;
+  const LeafState& lf = ds.lf;
   const int M = sh.M, r = sh.r, Mr = M * r;
-  const long F = blockIdx.x;
-  const long o0 = lf.off[F];
-  const int nF = (int)(lf.off[F + 1] - o0);
+  const long F = it.i;                           // compact leaf id
+  const long Fm = st.mort[M][F];
+  const long o0 = lf.off[Fm];
+  const int nF = (int)(lf.off[Fm + 1] - o0);
   if (nF == 0) {
     if (threadIdx.x == 0) { lf.d[F] = 0.0; lf.u[F] = 0.0; }
     return;
@@ -126,9 +141,9 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(Shape sh, Cov cv, double ta
   const int row = acc.row(), c0 = acc.col0();
   // chain: V^l_F = (C0(S_F, Q_l) - sum_{k<l} V^k_F V^k_{R_l}') L_l^{-T}  (one 128-row tile)
   for (int l = 0; l < M && ok; ++l) {
-    const long a = F >> (2 * (M - l));
+    const long a = ancestor(st, M, F, l);
     __syncthreads();
-    load_knots(sh.bbox, l, a, sh.gx, sh.gy, ax, ay);
+    load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
     const double* Vanc = st.V[l] + a * (long)r * (l * r);
     acc.zero();
     __syncthreads();
@@ -174,13 +189,13 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(Shape sh, Cov cv, double ta
     for (int t = threadIdx.x; t < nF; t += NT) ld += log(S[t * lds + t]);
     ld = 2.0 * block_sum(ld, red);
     if (lf.LSf) {
-      double* Lf = lf.LSf + lf.sq_off[F];
+      double* Lf = lf.LSf + lf.sq_off[Fm];
       for (int t = threadIdx.x; t < nF * nF; t += NT) Lf[t] = S[(t / nF) * lds + (t % nF)];
     }
     if (lf.VF)
       for (long t = threadIdx.x; t < (long)nF * Mr; t += NT) lf.VF[o0 * Mr + t] = Hrow[t];
     trinv_smem(S, nF, lds, tmp);
-    double* LS = lf.LS + lf.sq_off[F];
+    double* LS = lf.LS + lf.sq_off[Fm];
     for (int t = threadIdx.x; t < nF * nF; t += NT) LS[t] = S[(t / nF) * lds + (t % nF)];
     for (int t = threadIdx.x; t < nF; t += NT) {
       double s = 0.0;
@@ -218,21 +233,19 @@ size_t leaf_tc_smem_bytes(int nlmax) {
   return TC_STAGE_BYTES + sizeof(double) * (4 * (size_t)nlmax + 2 * MAX_R_DEV + 32 + (size_t)nlmax * (nlmax + 1));
 }
 
-cudaError_t launch_prior_tc(int m, const Shape& sh, const Cov& cv, const LevelState& st, int* status,
-                            cudaStream_t s) {
+cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nblocks, int* status, cudaStream_t s) {
   const size_t sm = prior_tc_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(prior_level_kernel_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e) return e;
-  prior_level_kernel_tc<<<1u << (2 * m), NT, sm, s>>>(m, sh, cv, st, status);
+  prior_level_kernel_tc<<<nblocks, NT, sm, s>>>(m, d_desc, work, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_leaf_tc(const Shape& sh, const Cov& cv, double tau2, const LevelState& st, const LeafState& lf,
-                           int nlmax, int* status, cudaStream_t s) {
+cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int* status, cudaStream_t s) {
   const size_t sm = leaf_tc_smem_bytes(nlmax);
   cudaError_t e = cudaFuncSetAttribute(leaf_kernel_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e) return e;
-  leaf_kernel_tc<<<1u << (2 * sh.M), NT, sm, s>>>(sh, cv, tau2, st, lf, nlmax, status);
+  leaf_kernel_tc<<<nblocks, NT, sm, s>>>(d_desc, work, status);
   return cudaGetLastError();
 }
 

@@ -106,7 +106,7 @@ extern "C" int mra_loglik_noalloc(const mra_config* cfg, const mra_params* theta
   if (n < 1) return err(MRA_ERR_ARG, "n must be >= 1");
   if (cfg->M < 0 || cfg->M > MRA_MAX_M || cfg->J != 4 || cfg->r < 1 || cfg->r > MRA_MAX_R ||
       (cfg->cov_family != MRA_COV_EXP && cfg->cov_family != MRA_COV_MATERN15) ||
-      (cfg->nonstat != 0 && cfg->nonstat != 1) || cfg->precision != MRA_PREC_FP64 ||
+      (cfg->nonstat != 0 && cfg->nonstat != 1) || cfg->precision != MRA_PREC_FP64 || cfg->prune != 0 ||
       !(cfg->bbox[0] < cfg->bbox[1]) || !(cfg->bbox[2] < cfg->bbox[3]))
     return err(MRA_ERR_ARG, "invalid configuration");
   if (!(std::isfinite(theta->sigma2) && std::isfinite(theta->range) && std::isfinite(theta->tau2) &&
@@ -155,8 +155,19 @@ extern "C" int mra_loglik_noalloc(const mra_config* cfg, const mra_params* theta
   if (mc > MRA_MAX_LEAF)
     return err(MRA_ERR_LIMIT, "a leaf holds %d observations (max %d); increase M", mc, MRA_MAX_LEAF);
   const int nlmax = mc < 1 ? 1 : mc;
-  // ---- factors of every level and of the leaves -----------------------------
+  // ---- tree tables (complete tree: identity), factors of every level and of the leaves
   mra::LevelState st{};
+  for (int m = 0; m <= M; ++m) {
+    const int64_t R = int64_t(1) << (2 * m);
+    st.nreg[m] = (int)R;
+    st.mort[m] = C.take<int32_t>(R);
+    st.cid[m] = C.take<int32_t>(R);
+    if (m > 0) st.par[m] = C.take<int32_t>(R);
+    if (m < M) {
+      st.cfirst[m] = C.take<int32_t>(R);
+      st.ccnt[m] = C.take<int32_t>(R);
+    }
+  }
   for (int m = 0; m < M; ++m) {
     const int64_t R = int64_t(1) << (2 * m);
     const int64_t T = int64_t(m + 1) * (m + 2) / 2;
@@ -181,6 +192,7 @@ extern "C" int mra_loglik_noalloc(const mra_config* cfg, const mra_params* theta
   lf.LS = C.take<double>((size_t)tail);
   lf.d = C.take<double>(nl);
   lf.u = C.take<double>(nl);
+  mra::Desc* d_desc = C.take<mra::Desc>(1);
   if (!C.fits())
     return err(MRA_ERR_LIMIT, "problem needs %zu bytes of scratch; the allocation-free entry point has %zu",
                C.used, kScratchBytes);
@@ -197,10 +209,32 @@ extern "C" int mra_loglik_noalloc(const mra_config* cfg, const mra_params* theta
   sh.gy = r / sh.gx;
   for (int k = 0; k < 4; ++k) sh.bbox[k] = cfg->bbox[k];
   sh.mixed = 0;
-  mra::Cov cv{theta->sigma2, theta->range, cfg->cov_family, cfg->nonstat};
+  mra::Desc hd{};
+  hd.sh = sh;
+  hd.cv = mra::Cov{theta->sigma2, theta->range, cfg->cov_family, cfg->nonstat};
+  hd.tau2 = theta->tau2;
+  hd.nlmax = nlmax;
+  hd.st = st;
+  hd.lf = lf;
+  mra::Plan plan;
+  plan.maxM = M;
+  plan.tile = mra::tile_for_r(r);
+  plan.mixed = 0;
+  plan.nlmax = nlmax;
+  for (int m = 0; m < M; ++m) {
+    plan.n_lvl[m] = st.nreg[m];
+    if (m > 0) plan.n_agg[m] = st.nreg[m - 1];
+  }
+  plan.n_leaf = st.nreg[M];
+  if (M > 0) {
+    plan.n_syrk = st.nreg[M - 1];
+    plan.t_syrk = M * (M + 1) / 2;
+  }
   mra::Timer no_timer;
-  if ((e = mra::launch_gather(locs, y, perm, n, xs, ys, yv, s, launches)) ||
-      (e = mra::launch_loglik(sh, cv, theta->tau2, st, lf, nlmax, status, s, launches, &no_timer)))
+  if ((e = mra::launch_identity_tree(st, M, s, launches)) ||
+      (e = cudaMemcpyAsync(d_desc, &hd, sizeof hd, cudaMemcpyHostToDevice, s)) ||
+      (e = mra::launch_gather(locs, y, perm, n, xs, ys, yv, s, launches)) ||
+      (e = mra::launch_loglik(plan, d_desc, status, s, launches, &no_timer)))
     return cuda_err(e, "loglik launch");
   double d = 0.0, u = 0.0;
   const double* dsrc = M > 0 ? st.dd[0] : lf.d;

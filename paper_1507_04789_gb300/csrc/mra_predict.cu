@@ -17,15 +17,28 @@
 namespace mra {
 
 template <int TILE>
-__global__ void __launch_bounds__(NT) predict_kernel(Shape sh, Cov cv, LevelState st, LeafState lf, int nlmax,
-                                                     PredState ps) {
+__global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D, PredState ps, int* status) {
   extern __shared__ double smem[];
+  const Desc& ds = D[0];
+  const Shape sh = ds.sh;
+  const Cov cv = ds.cv;
+  const int nlmax = ds.nlmax;
+  const LevelState& st = ds.st;
+  const LeafState& lf = ds.lf;
   const int M = sh.M, r = sh.r, Mr = M * r;
-  const long F = blockIdx.x;
+  const long F = blockIdx.x;                     // Morton id of the leaf
   const long p0 = ps.off[F] + (long)blockIdx.y * TILE;
   const long p1 = min(ps.off[F + 1], p0 + TILE);
   if (p0 >= p1) return;
   const int nP = (int)(p1 - p0);
+  long anc[MAXL];                                // compact ids of the ancestors
+  for (int l = 0; l < M; ++l) {
+    anc[l] = st.cid[l][F >> (2 * (M - l))];
+    if (anc[l] < 0) {                            // pruned tree: no data above this point
+      if (threadIdx.x == 0) flag_error(status, ST_ARG, l, F);
+      return;
+    }
+  }
   const long o0 = lf.off[F];
   const int nF = (int)(lf.off[F + 1] - o0);
   const int ldp = nlmax + 1, ldy = r + 1;
@@ -49,9 +62,9 @@ __global__ void __launch_bounds__(NT) predict_kernel(Shape sh, Cov cv, LevelStat
   constexpr int RM = TileAcc<TILE>::RM;
   // ---- Uhat chain (same recursion as the leaf basis) --------------------------
   for (int l = 0; l < M; ++l) {
-    const long a = F >> (2 * (M - l));
+    const long a = anc[l];
     __syncthreads();
-    load_knots(sh.bbox, l, a, sh.gx, sh.gy, ax, ay);
+    load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
     __syncthreads();
     acc.zero();
     if (l > 0) tile_mma<TILE>(acc, U, Mr, 1, nP, st.V[l] + a * (long)r * (l * r), l * r, 1, r, l * r, stg);
@@ -138,7 +151,7 @@ __global__ void __launch_bounds__(NT) predict_kernel(Shape sh, Cov cv, LevelStat
   }
   // ---- posterior basis recursion, l = M-1..0 -----------------------------------
   for (int l = M - 1; l >= 0; --l) {
-    const long a = F >> (2 * (M - l));
+    const long a = anc[l];
     __syncthreads();
     acc.zero();
     tile_mma<TILE>(acc, U + l * r, Mr, 1, nP, st.Lt[l] + a * (long)r * r, r, 1, r, r, stg);
@@ -190,11 +203,11 @@ size_t predict_smem_bytes(int r, int nlmax) {
                            (size_t)tile * (r + 1) + 2 * KC * (tile + 2));
 }
 
-cudaError_t launch_predict(const Shape& sh, const Cov& cv, const LevelState& st, const LeafState& lf, int nlmax,
-                           const PredState& ps, int max_per_leaf, cudaStream_t s, int64_t* launches, Timer* tm) {
-  const int tile = tile_of(sh.r);
-  const size_t sm = predict_smem_bytes(sh.r, nlmax);
-  dim3 grid(1u << (2 * sh.M), (unsigned)((max_per_leaf + tile - 1) / tile));
+cudaError_t launch_predict(const Desc* d_desc, int M, int r, int nlmax, const PredState& ps, int max_per_leaf,
+                           int* status, cudaStream_t s, int64_t* launches, Timer* tm) {
+  const int tile = tile_of(r);
+  const size_t sm = predict_smem_bytes(r, nlmax);
+  dim3 grid(1u << (2 * M), (unsigned)((max_per_leaf + tile - 1) / tile));
   if (grid.y == 0) return cudaSuccess;
   cudaError_t e;
   tm->start(5, s);
@@ -202,7 +215,7 @@ cudaError_t launch_predict(const Shape& sh, const Cov& cv, const LevelState& st,
   {                                                                                                     \
     e = cudaFuncSetAttribute(predict_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);  \
     if (e) return e;                                                                                    \
-    predict_kernel<T><<<grid, NT, sm, s>>>(sh, cv, st, lf, nlmax, ps);                                  \
+    predict_kernel<T><<<grid, NT, sm, s>>>(d_desc, ps, status);                                         \
   }
   if (tile == 16) MRA_PRED_LAUNCH(16)
   else if (tile == 32) MRA_PRED_LAUNCH(32)

@@ -161,3 +161,29 @@ cudaError_t launch_gather_y(const double* y, const int64_t* perm, int64_t n, dou
 }
 
 }  // namespace mra
+
+namespace mra {
+
+// Tables of a complete tree (every region active): identity maps.
+__global__ void identity_tree_kernel(LevelState st, int M) {
+  for (int m = 0; m <= M; ++m) {
+    const long cnt = 1L << (2 * m);
+    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < cnt; c += (long)gridDim.x * blockDim.x) {
+      st.mort[m][c] = (int32_t)c;
+      st.cid[m][c] = (int32_t)c;
+      if (m > 0) st.par[m][c] = (int32_t)(c >> 2);
+      if (m < M) {
+        st.cfirst[m][c] = (int32_t)(4 * c);
+        st.ccnt[m][c] = 4;
+      }
+    }
+  }
+}
+
+cudaError_t launch_identity_tree(const LevelState& st, int M, cudaStream_t s, int64_t* launches) {
+  identity_tree_kernel<<<256, 256, 0, s>>>(st, M);
+  *launches += 1;
+  return cudaGetLastError();
+}
+
+}  // namespace mra

@@ -41,7 +41,7 @@ class MRAError(RuntimeError):
 class MraConfig(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("J", ctypes.c_int), ("r", ctypes.c_int),
                 ("cov_family", ctypes.c_int), ("nonstat", ctypes.c_int),
-                ("precision", ctypes.c_int), ("bbox", ctypes.c_double * 4)]
+                ("precision", ctypes.c_int), ("prune", ctypes.c_int), ("bbox", ctypes.c_double * 4)]
 
 
 class MraParams(ctypes.Structure):
@@ -80,6 +80,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "mra_free": (None, [_P]),
         "mra_last_error": (ctypes.c_char_p, []),
         "mra_launch_count": (ctypes.c_int64, [ctypes.c_int]),
+        "mra_build_batch": (ctypes.c_int, [ctypes.POINTER(MraConfig), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                           ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(_P)]),
+        "mra_loglik_batch": (ctypes.c_int, [_P, ctypes.POINTER(MraParams), _P]),
+        "mra_autotune": (ctypes.c_int, [_P, ctypes.POINTER(MraParams), ctypes.POINTER(ctypes.c_int)]),
+        "mra_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -123,13 +129,13 @@ class Handle:
     """One M-RA problem on the GPU: locations, data and the tree (Sec. 2.2)."""
 
     def __init__(self, locs, y, M: int, r: int, family: str = "exp", nonstat: bool = False,
-                 bbox=(0.0, 1.0, 0.0, 1.0), J: int = 4, precision="fp64"):
+                 bbox=(0.0, 1.0, 0.0, 1.0), J: int = 4, precision="fp64", prune: bool = False):
         lib = load_library()
         self._lib = lib
         self._h = _P()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         cfg = MraConfig(M, J, r, FAMILIES[family] if isinstance(family, str) else int(family),
-                        int(bool(nonstat)), prec, (ctypes.c_double * 4)(*bbox))
+                        int(bool(nonstat)), prec, int(bool(prune)), (ctypes.c_double * 4)(*bbox))
         if _is_torch_cuda(locs):
             if locs.dim() != 2 or locs.shape[1] != 2:
                 raise ValueError("locs must be (n, 2)")
@@ -252,3 +258,89 @@ class Handle:
         perm = np.empty(self.n, dtype=np.int64) if with_perm else None
         _check(self._lib.mra_leaf_offsets(self._h, off.ctypes.data, perm.ctypes.data if with_perm else None))
         return (off, perm) if with_perm else off
+
+
+class Batch:
+    """Many independent datasets evaluated together, one launch per level.
+
+    ``datasets`` is a list of dicts with keys ``locs`` (n x 2), ``y`` (n),
+    ``M`` and optionally ``family``, ``nonstat``, ``bbox``, ``prune``
+    (default True).  All datasets share ``r`` and ``precision``.
+    """
+
+    def __init__(self, datasets, r: int, precision="fp64"):
+        lib = load_library()
+        self._lib = lib
+        self._h = _P()
+        nd = len(datasets)
+        cfgs = (MraConfig * nd)()
+        keep = []
+        lp = (_P * nd)()
+        yp = (_P * nd)()
+        ns = (ctypes.c_int64 * nd)()
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        for d, ds in enumerate(datasets):
+            la = _host_f64(ds["locs"], 2)
+            ya = _host_f64(ds["y"])
+            keep += [la, ya]
+            fam = ds.get("family", "exp")
+            cfgs[d] = MraConfig(int(ds["M"]), 4, r, FAMILIES[fam] if isinstance(fam, str) else int(fam),
+                                int(bool(ds.get("nonstat", False))), prec, int(bool(ds.get("prune", True))),
+                                (ctypes.c_double * 4)(*ds.get("bbox", (0.0, 1.0, 0.0, 1.0))))
+            lp[d] = la.ctypes.data
+            yp[d] = ya.ctypes.data
+            ns[d] = la.shape[0]
+        _check(lib.mra_build_batch(cfgs, lp, yp, ns, nd, MRA_HOST, ctypes.byref(self._h)))
+        self.ndata = nd
+        self.n = [int(v) for v in ns]
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.mra_free(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _params(self, thetas):
+        arr = (MraParams * self.ndata)()
+        for d, t in enumerate(thetas):
+            arr[d] = MraParams(*[float(v) for v in t])
+        return arr
+
+    def loglik(self, thetas):
+        """Log-likelihood of every dataset at its own theta (Sec. 3.3)."""
+        out = np.empty(self.ndata)
+        _check(self._lib.mra_loglik_batch(self._h, self._params(thetas), out.ctypes.data))
+        return out
+
+    def autotune(self, thetas) -> int:
+        tile = ctypes.c_int()
+        _check(self._lib.mra_autotune(self._h, self._params(thetas), ctypes.byref(tile)))
+        return tile.value
+
+    def info(self):
+        nd, tile = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.mra_batch_info(self._h, ctypes.byref(nd), ctypes.byref(tile)))
+        return nd.value, tile.value
+
+    def enable_timing(self, on: bool = True) -> None:
+        _check(self._lib.mra_enable_timing(self._h, 1 if on else 0))
+
+    def kernel_times(self) -> dict:
+        out = {}
+        for k, name in enumerate(KERNEL_KINDS):
+            ms = ctypes.c_double()
+            cnt = ctypes.c_int64()
+            _check(self._lib.mra_kernel_times(self._h, k, ctypes.byref(ms), ctypes.byref(cnt)))
+            out[name] = (ms.value, cnt.value)
+        return out

@@ -31,6 +31,7 @@ __all__ = [
     "Workload",
     "workload",
     "WORKLOADS",
+    "swath_batch",
 ]
 
 
@@ -156,3 +157,27 @@ WORKLOADS = {
 
 def workload(name: str) -> Workload:
     return WORKLOADS[name]
+
+
+def swath_batch(ndata: int = 64, seed: int = 0, n_min: float = 1e4, n_max: float = 1e6,
+                width: float = 0.02, drop: float = 0.3, features: int = 256):
+    """Independent swath datasets of log-uniform size (the ragged batch workload).
+
+    Dataset i: n_i = floor(10^U(log10 n_min, log10 n_max)) locations on
+    K_i ~ U{8..32} parallel swaths of the given width at a common random angle,
+    each swath dropped with probability ``drop``; field = exponential-covariance
+    draw with sigma2 = 1 and range kappa_i ~ U(0.02, 0.3), plus N(0, 0.05) noise.
+    Returns a list of dicts with locs, y, kappa, sigma2, tau2.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(ndata):
+        n = int(10 ** rng.uniform(math.log10(n_min), math.log10(n_max)))
+        k = int(rng.integers(8, 33))
+        kappa = float(rng.uniform(0.02, 0.3))
+        s = int(rng.integers(0, 2 ** 31 - 1))
+        locs = swath_locations(n, k, width, s, drop=drop)
+        field = rff_field(locs, 0.5, kappa, 1.0, s + 1, features)
+        y = noisy_observations(field, 0.05, s + 2)
+        out.append({"locs": locs, "y": y, "kappa": kappa, "sigma2": 1.0, "tau2": 0.05})
+    return out

@@ -47,7 +47,7 @@ def test_noalloc_matches_handle_path_twice():
     for locs, y, M, r, fam, theta in cases:
         with mra.Handle(locs, y, M=M, r=r, family=fam) as h:
             ref = h.loglik(theta)
-        cfg = mra.MraConfig(M, 4, r, mra.FAMILIES[fam], 0, mra.MRA_PREC_FP64,
+        cfg = mra.MraConfig(M, 4, r, mra.FAMILIES[fam], 0, mra.MRA_PREC_FP64, 0,
                             (ctypes.c_double * 4)(0.0, 1.0, 0.0, 1.0))
         p = mra.MraParams(*theta)
         dl = torch.tensor(locs, device="cuda", dtype=torch.float64)
@@ -64,7 +64,7 @@ def test_noalloc_rejects_oversized_problems():
     rng = np.random.default_rng(22)
     dl = torch.tensor(rng.random((n, 2)), device="cuda")
     dy = torch.tensor(rng.standard_normal(n), device="cuda")
-    cfg = mra.MraConfig(6, 4, 64, mra.MRA_COV_EXP, 0, mra.MRA_PREC_FP64,
+    cfg = mra.MraConfig(6, 4, 64, mra.MRA_COV_EXP, 0, mra.MRA_PREC_FP64, 0,
                         (ctypes.c_double * 4)(0.0, 1.0, 0.0, 1.0))
     with pytest.raises(mra.MRAError) as ei:
         _noalloc(lib, mra, cfg, mra.MraParams(1.0, 0.1, 0.01), dl, dy, n)
