@@ -91,18 +91,26 @@ def swath_locations(n: int, n_swaths: int, width: float, seed: int,
     if segment is not None:
         n_seg = int(math.ceil(2.0 / segment)) + 1
         seg_keep = rng.random((n_swaths, n_seg)) >= drop
-    out = np.empty((0, 2))
-    while out.shape[0] < n:
-        cand = rng.random((max(4 * (n - out.shape[0]), 1024), 2))
+    order = np.argsort(offs)
+    so, sk = offs[order], keep_sw[order]
+    chunks, have = [], 0
+    while have < n:
+        cand = rng.random((max(4 * (n - have), 1024), 2))
         cv = cand @ v
         cu = cand @ u
-        dist = np.abs(cv[:, None] - offs[None, :])
-        inside = (dist <= 0.5 * width) & keep_sw[None, :]
-        if seg_keep is not None:
-            si = np.clip(((cu + 1.0) / segment).astype(np.int64), 0, seg_keep.shape[1] - 1)
-            inside &= seg_keep[:, si].T
-        ok = inside.any(axis=1)
-        out = np.concatenate([out, cand[ok]], axis=0)
+        # nearest swath centre lines below and above each candidate (sorted offsets)
+        j = np.searchsorted(so, cv)
+        inside = np.zeros(cand.shape[0], dtype=bool)
+        for jj in (np.clip(j - 1, 0, len(so) - 1), np.clip(j, 0, len(so) - 1)):
+            hit = (np.abs(cv - so[jj]) <= 0.5 * width) & sk[jj]
+            if seg_keep is not None:
+                si = np.clip(((cu + 1.0) / segment).astype(np.int64), 0, seg_keep.shape[1] - 1)
+                hit &= seg_keep[order[jj], si]
+            inside |= hit
+        acc = cand[inside]
+        chunks.append(acc)
+        have += acc.shape[0]
+    out = np.concatenate(chunks, axis=0)
     return out[:n].copy()
 
 
