@@ -65,6 +65,12 @@ extern "C" {
                                tensor cores (tcgen05, 3xTF32 with FP64 accumulation every 64
                                terms); factorisations, log-determinants, quadratic forms and
                                the Gram products of the posterior pass in binary64 */
+#define MRA_PREC_EMU      2 /* every large contraction (prior chain, leaf covariance and solve,
+                               leaf and child-to-parent Gram products) on the tensor cores as an
+                               FP64-grade emulation: operands cut into seven 7-bit bf16 slices
+                               per 64-column group, exact FP32 accumulation, double-float sums
+                               (about 1e-14 relative error per product); factorisations and
+                               the rest in binary64 */
 
 #define MRA_HOST          0 /* pointer argument is host memory */
 #define MRA_DEVICE        1 /* pointer argument is device memory */
@@ -76,7 +82,7 @@ typedef struct {
     int    r;           /* knots per internal region, 1 <= r <= MRA_MAX_R */
     int    cov_family;  /* MRA_COV_EXP or MRA_COV_MATERN15 */
     int    nonstat;     /* 1: variance sigma2 * sqrt(g(s1) g(s2)), g(s) = 1 + 0.5 sin(4 pi x) */
-    int    precision;   /* MRA_PREC_FP64 or MRA_PREC_MIXED */
+    int    precision;   /* MRA_PREC_FP64, MRA_PREC_MIXED or MRA_PREC_EMU */
     int    prune;       /* 1: keep only regions whose subtree holds observations (empty subtrees
                            contribute nothing to the likelihood); 0: complete tree */
     double bbox[4];     /* x0, x1, y0, y1 of the domain; every location must lie inside */

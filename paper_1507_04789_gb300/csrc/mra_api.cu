@@ -92,7 +92,7 @@ int check_config(const mra_config* cfg) {
   if (cfg->cov_family != MRA_COV_EXP && cfg->cov_family != MRA_COV_MATERN15)
     return fail(MRA_ERR_ARG, "unknown covariance family %d", cfg->cov_family);
   if (cfg->nonstat != 0 && cfg->nonstat != 1) return fail(MRA_ERR_ARG, "nonstat must be 0 or 1");
-  if (cfg->precision != MRA_PREC_FP64 && cfg->precision != MRA_PREC_MIXED)
+  if (cfg->precision != MRA_PREC_FP64 && cfg->precision != MRA_PREC_MIXED && cfg->precision != MRA_PREC_EMU)
     return fail(MRA_ERR_ARG, "unknown precision %d", cfg->precision);
   if (cfg->prune != 0 && cfg->prune != 1) return fail(MRA_ERR_ARG, "prune must be 0 or 1");
   if (!(cfg->bbox[0] < cfg->bbox[1]) || !(cfg->bbox[2] < cfg->bbox[3]))
@@ -276,7 +276,7 @@ void single_plan(mra_handle* h) {
   p = mra::Plan();
   p.maxM = h->M;
   p.tile = mra::tile_for_r(h->r);
-  p.mixed = h->cfg.precision == MRA_PREC_MIXED;
+  p.mixed = h->cfg.precision == MRA_PREC_MIXED ? 1 : (h->cfg.precision == MRA_PREC_EMU ? 2 : 0);
   p.nlmax = h->nlmax;
   for (int m = 0; m < h->M; ++m) {
     p.n_lvl[m] = h->tab.nreg[m];
@@ -295,7 +295,7 @@ cudaError_t upload_desc(mra_handle* h, const mra_params* theta) {
   h->hd.sh.gx = h->gx;
   h->hd.sh.gy = h->gy;
   for (int k = 0; k < 4; ++k) h->hd.sh.bbox[k] = h->cfg.bbox[k];
-  h->hd.sh.mixed = h->cfg.precision == MRA_PREC_MIXED;
+  h->hd.sh.mixed = h->cfg.precision == MRA_PREC_MIXED ? 1 : (h->cfg.precision == MRA_PREC_EMU ? 2 : 0);
   if (theta) {
     h->hd.cv = mra::Cov{theta->sigma2, theta->range, h->cfg.cov_family, h->cfg.nonstat};
     h->hd.tau2 = theta->tau2;
@@ -498,7 +498,8 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   h->lf.d = d;
   h->lf.u = u;
   single_plan(h);
-  size_t need = cfg->precision == MRA_PREC_MIXED ? mra::leaf_tc_smem_bytes(h->nlmax) : mra::leaf_smem_bytes(r, h->nlmax);
+  size_t need = cfg->precision != MRA_PREC_FP64 ? mra::leaf_tc_smem_bytes(h->nlmax, cfg->precision == MRA_PREC_EMU)
+                                                 : mra::leaf_smem_bytes(r, h->nlmax);
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -890,7 +891,7 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
   p = mra::Plan();
   p.maxM = maxM;
   p.tile = mra::tile_for_r(h->r);
-  p.mixed = h->cfg.precision == MRA_PREC_MIXED;
+  p.mixed = h->cfg.precision == MRA_PREC_MIXED ? 1 : (h->cfg.precision == MRA_PREC_EMU ? 2 : 0);
   p.nlmax = h->nlmax;
   int li = 0;
   for (int m = 0; m < maxM; ++m, ++li) { p.n_lvl[m] = lists[li].first; p.w_lvl[m] = d_items + lists[li].second; }
@@ -907,7 +908,7 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
     h->h_descs[d].nlmax = h->nlmax;    // one shared-memory layout for the whole batch
   }
   if ((e = cudaDeviceSynchronize())) { mra_free(h); return cuda_fail(e, "batch set-up"); }
-  size_t need = p.mixed ? mra::leaf_tc_smem_bytes(h->nlmax) : mra::leaf_smem_bytes(h->r, h->nlmax);
+  size_t need = p.mixed ? mra::leaf_tc_smem_bytes(h->nlmax, p.mixed == 2) : mra::leaf_smem_bytes(h->r, h->nlmax);
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -42,7 +42,7 @@ cudaError_t launch_gather_y(const double* y, const int64_t* perm, int64_t n, dou
 // (n_lvl[m]), of the aggregation into level m-1 (n_agg[m]), of the leaves and
 // of the leaf Gram products.
 struct Plan {
-  int maxM = 0, tile = 64, mixed = 0, nlmax = 1;
+  int maxM = 0, tile = 64, mixed = 0, nlmax = 1;   // mixed: 0 FP64, 1 3xTF32, 2 FP64 emulation
   const int2* w_lvl[MAXL] = {};
   int n_lvl[MAXL] = {};
   const int2* w_agg[MAXL] = {};
@@ -62,9 +62,16 @@ cudaError_t launch_gather_roots(const Desc* d_desc, int nd, double* out, cudaStr
 size_t leaf_smem_bytes(int r, int nlmax);
 
 // Mixed-precision prior level and leaf pass (tensor cores, mra_mixed.cu).
-cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nblocks, int* status, cudaStream_t s);
-cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int* status, cudaStream_t s);
-size_t leaf_tc_smem_bytes(int nlmax);
+// emu = 1: FP64-grade bf16-slice emulation engine; 0: 3xTF32.
+cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nblocks, int emu, int* status,
+                            cudaStream_t s);
+cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int emu, int* status,
+                           cudaStream_t s);
+size_t leaf_tc_smem_bytes(int nlmax, int emu);
+cudaError_t launch_leaf_syrk_em(const Desc* d_desc, const int2* work, int nblocks, int ntiles, int* status,
+                                cudaStream_t s);
+cudaError_t launch_aggregate_em(int m, const Desc* d_desc, const int2* work, int nblocks, int* status,
+                                cudaStream_t s);
 
 // Prediction (Sec. 3.4, Prop. 2) at points binned into ps.
 cudaError_t launch_predict(const Desc* d_desc, int M, int r, int nlmax, const PredState& ps, int max_per_leaf,

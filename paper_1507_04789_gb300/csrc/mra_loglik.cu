@@ -466,7 +466,7 @@ cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaS
     if (pl.n_lvl[m] == 0) continue;
     tm->start(0, s);
     if (pl.mixed) {
-      if ((e = launch_prior_tc(m, d_desc, pl.w_lvl[m], pl.n_lvl[m], status, s))) return e;
+      if ((e = launch_prior_tc(m, d_desc, pl.w_lvl[m], pl.n_lvl[m], pl.mixed == 2, status, s))) return e;
     } else {
       MRA_LAUNCH(tile, prior_level_kernel, pl.n_lvl[m], prior_smem(tile), s, m, d_desc, pl.w_lvl[m], status);
     }
@@ -477,7 +477,7 @@ cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaS
   if (pl.n_leaf > 0) {
     tm->start(1, s);
     if (pl.mixed) {
-      if ((e = launch_leaf_tc(d_desc, pl.w_leaf, pl.n_leaf, pl.nlmax, status, s))) return e;
+      if ((e = launch_leaf_tc(d_desc, pl.w_leaf, pl.n_leaf, pl.nlmax, pl.mixed == 2, status, s))) return e;
     } else {
       MRA_LAUNCH(tile, leaf_kernel, pl.n_leaf, leaf_smem(tile, pl.nlmax), s, d_desc, pl.w_leaf, status);
     }
@@ -487,7 +487,11 @@ cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaS
   if (pl.n_syrk > 0) {
     dim3 grid(pl.n_syrk, pl.t_syrk);
     tm->start(2, s);
-    MRA_LAUNCH(tile, leaf_syrk_kernel, grid, syrk_smem(tile), s, d_desc, pl.w_syrk);
+    if (pl.mixed == 2) {
+      if ((e = launch_leaf_syrk_em(d_desc, pl.w_syrk, pl.n_syrk, pl.t_syrk, status, s))) return e;
+    } else {
+      MRA_LAUNCH(tile, leaf_syrk_kernel, grid, syrk_smem(tile), s, d_desc, pl.w_syrk);
+    }
     tm->stop(s);
     ++*launches;
   }
@@ -502,7 +506,11 @@ cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaS
     if (m > 0 && pl.n_agg[m] > 0) {
       dim3 g2(pl.n_agg[m], m * (m + 1) / 2);
       tm->start(4, s);
-      MRA_LAUNCH(tile, aggregate_kernel, g2, syrk_smem(tile), s, m, d_desc, pl.w_agg[m]);
+      if (pl.mixed == 2) {
+        if ((e = launch_aggregate_em(m, d_desc, pl.w_agg[m], pl.n_agg[m], status, s))) return e;
+      } else {
+        MRA_LAUNCH(tile, aggregate_kernel, g2, syrk_smem(tile), s, m, d_desc, pl.w_agg[m]);
+      }
       tm->stop(s);
       ++*launches;
     }

@@ -1,24 +1,70 @@
-// mra_mixed.cu -- mixed-precision prior and leaf kernels (MRA_PREC_MIXED).
+// mra_mixed.cu -- tensor-core prior and leaf kernels (MRA_PREC_MIXED and
+// MRA_PREC_EMU).
 //
 // The same whitened prior pass (Eq. priorw in block-Cholesky form) and leaf
 // pass (Sec. 3.1-3.2 at m = M, Sec. 4.3 nugget) as mra_loglik.cu, with the
 // dense contractions -- the chain updates C - V V', the products with L^{-T},
 // the leaf covariance C - V_F V_F' and the leaf solve L_Sigma^{-1} V_F -- on the
-// tensor cores through tc_mma (3xTF32 with FP64 accumulation every 64 terms).
+// tensor cores, through one of two engines:
+//  * MRA_PREC_MIXED: tc_mma (3xTF32 with FP64 accumulation every 64 terms);
+//    the Gram products of the posterior pass (leaf_syrk, aggregate) stay in
+//    the FP64 kernels, since they need more than FP32 accuracy;
+//  * MRA_PREC_EMU: em_mma (bf16-slice FP64 emulation, about 1e-14 relative),
+//    which also runs the two Gram products (leaf_syrk_kernel_em,
+//    aggregate_kernel_em below).
 // The Cholesky factorisations, triangular inverses, log-determinants and the
-// quadratic form stay in FP64, and so do all Gram products of the posterior
-// pass (leaf_syrk, aggregate), which need more than FP32 accuracy.
+// quadratic form stay in FP64.
+#include <algorithm>
+
+#include "mra_emu.cuh"
 #include "mra_launch.h"
 #include "mra_tc.cuh"
 
 namespace mra {
 
+// The tensor-core engine of a kernel: 3xTF32 (EMU = false) or the FP64-grade
+// bf16-slice emulation (EMU = true); both write the same TcAcc layout.
+template <bool EMU>
+struct Engine;
+
+template <>
+struct Engine<false> {
+  static constexpr int STAGE = TC_STAGE_BYTES;
+  TcCtx cx;
+  __device__ void init(unsigned char* stage, uint64_t* mbar, uint32_t* tmem_slot, int* fail, int*, int*) {
+    cx = TcCtx{reinterpret_cast<uint32_t*>(stage), mbar, 0, 0, fail};
+    tc_init(cx, tmem_slot);
+  }
+  __device__ bool mma(TcAcc& acc, const double* A, long sai, long sak, int na, const double* B, long sbj, long sbk,
+                      int nb, int K) {
+    return tc_mma(cx, acc, A, sai, sak, na, B, sbj, sbk, nb, K);
+  }
+  __device__ void release() { tc_release(cx); }
+};
+
+template <>
+struct Engine<true> {
+  static constexpr int STAGE = EM_STAGE_BYTES;
+  EmCtx cx;
+  __device__ void init(unsigned char* stage, uint64_t* mbar, uint32_t* tmem_slot, int* fail, int* rexp, int* cexp) {
+    cx = EmCtx{reinterpret_cast<uint16_t*>(stage), rexp, cexp, mbar, 0, 0, fail};
+    em_init(cx, tmem_slot);
+  }
+  __device__ bool mma(TcAcc& acc, const double* A, long sai, long sak, int na, const double* B, long sbj, long sbk,
+                      int nb, int K) {
+    return em_mma(cx, acc, A, sai, sak, na, B, sbj, sbk, nb, K);
+  }
+  __device__ void release() { em_release(cx); }
+};
+
+template <bool EMU>
 __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* __restrict__ D,
                                                              const int2* __restrict__ work, int* status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ int fail, bad;
+  __shared__ int rexp[TC_M], cexp[TC_N];
   const Item it = work_item(work);
   const Desc& ds = D[it.d];
   const Shape sh = ds.sh;
@@ -26,16 +72,15 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
   const LevelState& st = ds.st;
   const int r = sh.r, mr = m * r;
   const long i = it.i;
-  uint32_t* stage = reinterpret_cast<uint32_t*>(dsm);
-  double* qx = reinterpret_cast<double*>(dsm + TC_STAGE_BYTES);
+  double* qx = reinterpret_cast<double*>(dsm + Engine<EMU>::STAGE);
   double* qy = qx + MAX_R_DEV;
   double* ax = qy + MAX_R_DEV;
   double* ay = ax + MAX_R_DEV;
   double* tmp = ay + MAX_R_DEV;
   double* W = tmp + MAX_R_DEV;                 // r x (r + 1)
   if (threadIdx.x == 0) bad = 0;
-  TcCtx cx{stage, &mbar, 0, 0, &fail};
-  tc_init(cx, &tmem_slot);
+  Engine<EMU> eng;
+  eng.init(dsm, &mbar, &tmem_slot, &fail, rexp, cexp);
   load_knots(sh.bbox, m, st.mort[m][i], sh.gx, sh.gy, qx, qy);
   double* Vrow = st.V[m] + i * (long)r * mr;
   TcAcc acc;
@@ -48,7 +93,7 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
     const double* Vanc = st.V[l] + a * (long)r * (l * r);
     acc.zero();
     __syncthreads();
-    if (l > 0) ok = tc_mma(cx, acc, Vrow, mr, 1, r, Vanc, l * r, 1, r, l * r);
+    if (l > 0) ok = eng.mma(acc, Vrow, mr, 1, r, Vanc, l * r, 1, r, l * r);
     if (!ok) break;
     if (row < r)
       for (int c = 0; c < 32; ++c) {
@@ -57,7 +102,7 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
       }
     __syncthreads();
     acc.zero();
-    ok = tc_mma(cx, acc, Vrow + l * r, mr, 1, r, st.Li[l] + a * (long)r * r, r, 1, r, r);
+    ok = eng.mma(acc, Vrow + l * r, mr, 1, r, st.Li[l] + a * (long)r * r, r, 1, r, r);
     if (!ok) break;
     if (row < r)
       for (int c = 0; c < 32; ++c) {
@@ -68,7 +113,7 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
   __syncthreads();
   if (ok) {
     acc.zero();
-    if (m > 0) ok = tc_mma(cx, acc, Vrow, mr, 1, r, Vrow, mr, 1, r, mr);
+    if (m > 0) ok = eng.mma(acc, Vrow, mr, 1, r, Vrow, mr, 1, r, mr);
   }
   if (ok) {
     const int ldw = r + 1;
@@ -87,19 +132,21 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
     double* Li = st.Li[m] + i * (long)r * r;
     for (int t = threadIdx.x; t < r * r; t += NT) Li[t] = W[(t / r) * ldw + (t % r)];
   }
-  tc_release(cx);
+  eng.release();
   if (threadIdx.x == 0) {
     if (!ok) flag_error(status, ST_TIMEOUT, m, i);
     else if (bad) flag_error(status, ST_NOT_PD, m, i);
   }
 }
 
+template <bool EMU>
 __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D, const int2* __restrict__ work,
                                                      int* status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ int fail, bad;
+  __shared__ int rexp[TC_M], cexp[TC_N];
   const Item it = work_item(work);
   const Desc& ds = D[it.d];
   const Shape sh = ds.sh;
@@ -118,8 +165,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
     return;
   }
   const int lds = nlmax + 1;
-  uint32_t* stage = reinterpret_cast<uint32_t*>(dsm);
-  double* sx = reinterpret_cast<double*>(dsm + TC_STAGE_BYTES);
+  double* sx = reinterpret_cast<double*>(dsm + Engine<EMU>::STAGE);
   double* sy = sx + nlmax;
   double* sv = sy + nlmax;
   double* tmp = sv + nlmax;
@@ -128,8 +174,8 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
   double* red = ay + MAX_R_DEV;
   double* S = red + 32;                         // nlmax x (nlmax + 1)
   if (threadIdx.x == 0) bad = 0;
-  TcCtx cx{stage, &mbar, 0, 0, &fail};
-  tc_init(cx, &tmem_slot);
+  Engine<EMU> eng;
+  eng.init(dsm, &mbar, &tmem_slot, &fail, rexp, cexp);
   for (int t = threadIdx.x; t < nF; t += NT) {
     sx[t] = lf.xs[o0 + t];
     sy[t] = lf.ys[o0 + t];
@@ -147,7 +193,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
     const double* Vanc = st.V[l] + a * (long)r * (l * r);
     acc.zero();
     __syncthreads();
-    if (l > 0) ok = tc_mma(cx, acc, Hrow, Mr, 1, nF, Vanc, l * r, 1, r, l * r);
+    if (l > 0) ok = eng.mma(acc, Hrow, Mr, 1, nF, Vanc, l * r, 1, r, l * r);
     if (!ok) break;
     if (row < nF)
       for (int c = 0; c < 32; ++c) {
@@ -156,7 +202,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
       }
     __syncthreads();
     acc.zero();
-    ok = tc_mma(cx, acc, Hrow + l * r, Mr, 1, nF, st.Li[l] + a * (long)r * r, r, 1, r, r);
+    ok = eng.mma(acc, Hrow + l * r, Mr, 1, nF, st.Li[l] + a * (long)r * r, r, 1, r, r);
     if (!ok) break;
     if (row < nF)
       for (int c = 0; c < 32; ++c) {
@@ -170,7 +216,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
   for (int ct = 0; ct < nct && ok; ++ct) {
     const int ncol = min(TC_N, nF - ct * TC_N);
     acc.zero();
-    if (M > 0) ok = tc_mma(cx, acc, Hrow, Mr, 1, nF, Hrow + (long)ct * TC_N * Mr, Mr, 1, ncol, Mr);
+    if (M > 0) ok = eng.mma(acc, Hrow, Mr, 1, nF, Hrow + (long)ct * TC_N * Mr, Mr, 1, ncol, Mr);
     if (!ok) break;
     if (row < nF)
       for (int c = 0; c < 32; ++c) {
@@ -207,7 +253,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
     // H^l = L_Sigma^{-1} V^l_F (whole block read before it is overwritten)
     for (int l = 0; l < M && ok; ++l) {
       acc.zero();
-      ok = tc_mma(cx, acc, S, lds, 1, nF, Hrow + l * r, 1, Mr, r, nF);
+      ok = eng.mma(acc, S, lds, 1, nF, Hrow + l * r, 1, Mr, r, nF);
       if (!ok) break;
       if (row < nF)
         for (int c = 0; c < 32; ++c) {
@@ -217,7 +263,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
       __syncthreads();
     }
   }
-  tc_release(cx);
+  eng.release();
   if (threadIdx.x == 0) {
     lf.d[F] = ld;
     lf.u[F] = zz;
@@ -226,26 +272,177 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
   }
 }
 
-size_t prior_tc_smem_bytes() {
-  return TC_STAGE_BYTES + sizeof(double) * (5 * MAX_R_DEV + MAX_R_DEV * (MAX_R_DEV + 1));
-}
-size_t leaf_tc_smem_bytes(int nlmax) {
-  return TC_STAGE_BYTES + sizeof(double) * (4 * (size_t)nlmax + 2 * MAX_R_DEV + 32 + (size_t)nlmax * (nlmax + 1));
+// ---------------------------------------------------------------------------
+// Gram products of the posterior pass on the emulation engine (MRA_PREC_EMU):
+// leaf_syrk and aggregate with the same tiles and sums as the FP64 kernels.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict__ D, const int2* __restrict__ work,
+                                                          int* status) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  __shared__ int rexp[TC_M], cexp[TC_N];
+  const Item it = work_item(work);
+  const Desc& ds = D[it.d];
+  const int M = ds.sh.M, r = ds.sh.r, Mr = M * r;
+  const LevelState& st = ds.st;
+  const LeafState& lf = ds.lf;
+  const long p = it.i;
+  const int t = blockIdx.y;
+  if (t >= M * (M + 1) / 2) return;
+  const long pm = st.mort[M - 1][p];
+  int k = 0;
+  while (tri_index(k + 1, 0) <= t) ++k;
+  const int l = t - tri_index(k, 0);
+  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
+  const int K = (int)(row1 - row0);
+  const double* Hb = lf.H + row0 * Mr;
+  Engine<true> eng;
+  eng.init(dsm, &mbar, &tmem_slot, &fail, rexp, cexp);
+  TcAcc acc;
+  acc.zero();
+  const bool ok = eng.mma(acc, Hb + k * r, 1, Mr, r, Hb + l * r, 1, Mr, r, K);
+  const int m = M - 1, T = (m + 1) * (m + 2) / 2;
+  double* out = st.Acc[m] + (p * T + t) * (long)r * r;
+  const int row = acc.row(), c0 = acc.col0();
+  if (ok && row < r)
+    for (int c = 0; c < 32; ++c)
+      if (c0 + c < r) out[row * r + c0 + c] = acc.v[c];
+  eng.release();
+  if (k == l) {
+    double* om = st.Om[m] + (p * (m + 1) + k) * (long)r;
+    for (int a = threadIdx.x; a < r; a += NT) {
+      double s = 0.0;
+      for (long o = 0; o < K; ++o) s = fma(Hb[o * Mr + k * r + a], lf.z[row0 + o], s);
+      om[a] = s;
+    }
+  }
+  if (!ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, M - 1, p);
 }
 
-cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nblocks, int* status, cudaStream_t s) {
-  const size_t sm = prior_tc_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(prior_level_kernel_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e) return e;
-  prior_level_kernel_tc<<<nblocks, NT, sm, s>>>(m, d_desc, work, status);
+__global__ void __launch_bounds__(NT) aggregate_kernel_em(int m, const Desc* __restrict__ D,
+                                                          const int2* __restrict__ work, int* status) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  __shared__ int rexp[TC_M], cexp[TC_N];
+  const Item it = work_item(work);
+  const Desc& ds = D[it.d];
+  const int r = ds.sh.r, mr = m * r;
+  const LevelState& st = ds.st;
+  const long p = it.i;
+  const int t = blockIdx.y;
+  if (t >= m * (m + 1) / 2) return;
+  int k = 0;
+  while (tri_index(k + 1, 0) <= t) ++k;
+  const int l = t - tri_index(k, 0);
+  const int Tc = (m + 1) * (m + 2) / 2, Tp = m * (m + 1) / 2;
+  const long cf = st.cfirst[m - 1][p], cc = st.ccnt[m - 1][p];
+  const double* Gb = st.G[m] + cf * (long)r * mr;
+  Engine<true> eng;
+  eng.init(dsm, &mbar, &tmem_slot, &fail, rexp, cexp);
+  TcAcc acc;
+  acc.zero();
+  const bool ok = eng.mma(acc, Gb + k * r, 1, mr, r, Gb + l * r, 1, mr, r, (int)(cc * r));
+  double* out = st.Acc[m - 1] + (p * Tp + t) * (long)r * r;
+  const int row = acc.row(), c0 = acc.col0();
+  if (ok && row < r)
+    for (int c = 0; c < 32; ++c) {
+      const int col = c0 + c;
+      if (col < r) {
+        double s = -acc.v[c];
+        for (long ch = cf; ch < cf + cc; ++ch) s += st.Acc[m][(ch * Tc + t) * (long)r * r + row * r + col];
+        out[row * r + col] = s;
+      }
+    }
+  eng.release();
+  if (k == l) {
+    double* om = st.Om[m - 1] + (p * m + k) * (long)r;
+    for (int a = threadIdx.x; a < r; a += NT) {
+      double s = 0.0;
+      for (long ci = cf; ci < cf + cc; ++ci) {
+        s += st.Om[m][(ci * (m + 1) + k) * (long)r + a];
+        const double* Gc = st.G[m] + ci * (long)r * mr;
+        const double* gc = st.gv[m] + ci * r;
+        for (int q = 0; q < r; ++q) s = fma(-Gc[(long)q * mr + k * r + a], gc[q], s);
+      }
+      om[a] = s;
+    }
+  }
+  if (!ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, m - 1, p);
+}
+
+// The emulation engine takes 512 TMEM columns, all of an SM's; its kernels ask
+// for more than half of the SM's shared memory so that a second CTA is never
+// resident (it would only wait in tcgen05.alloc).
+constexpr size_t EM_SOLO_SMEM = 116 * 1024;
+
+template <bool EMU>
+static size_t prior_tc_smem() {
+  const size_t b = Engine<EMU>::STAGE + sizeof(double) * (5 * MAX_R_DEV + MAX_R_DEV * (MAX_R_DEV + 1));
+  return EMU ? std::max(b, EM_SOLO_SMEM) : b;
+}
+template <bool EMU>
+static size_t leaf_tc_smem(int nlmax) {
+  const size_t b =
+      Engine<EMU>::STAGE + sizeof(double) * (4 * (size_t)nlmax + 2 * MAX_R_DEV + 32 + (size_t)nlmax * (nlmax + 1));
+  return EMU ? std::max(b, EM_SOLO_SMEM) : b;
+}
+// Dynamic plus (an upper bound of) static shared memory of the leaf kernel.
+size_t leaf_tc_smem_bytes(int nlmax, int emu) {
+  return 1024 + (emu ? leaf_tc_smem<true>(nlmax) : leaf_tc_smem<false>(nlmax));
+}
+
+
+cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nblocks, int emu, int* status,
+                            cudaStream_t s) {
+  cudaError_t e;
+  if (emu) {
+    const size_t sm = prior_tc_smem<true>();
+    if ((e = cudaFuncSetAttribute(prior_level_kernel_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+      return e;
+    prior_level_kernel_tc<true><<<nblocks, NT, sm, s>>>(m, d_desc, work, status);
+  } else {
+    const size_t sm = prior_tc_smem<false>();
+    if ((e = cudaFuncSetAttribute(prior_level_kernel_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+      return e;
+    prior_level_kernel_tc<false><<<nblocks, NT, sm, s>>>(m, d_desc, work, status);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int* status, cudaStream_t s) {
-  const size_t sm = leaf_tc_smem_bytes(nlmax);
-  cudaError_t e = cudaFuncSetAttribute(leaf_kernel_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e) return e;
-  leaf_kernel_tc<<<nblocks, NT, sm, s>>>(d_desc, work, status);
+cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int emu, int* status,
+                           cudaStream_t s) {
+  cudaError_t e;
+  if (emu) {
+    const size_t sm = leaf_tc_smem<true>(nlmax);
+    if ((e = cudaFuncSetAttribute(leaf_kernel_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
+    leaf_kernel_tc<true><<<nblocks, NT, sm, s>>>(d_desc, work, status);
+  } else {
+    const size_t sm = leaf_tc_smem<false>(nlmax);
+    if ((e = cudaFuncSetAttribute(leaf_kernel_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
+    leaf_kernel_tc<false><<<nblocks, NT, sm, s>>>(d_desc, work, status);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_leaf_syrk_em(const Desc* d_desc, const int2* work, int nblocks, int ntiles, int* status,
+                                cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(leaf_syrk_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
+    return e;
+  leaf_syrk_kernel_em<<<dim3(nblocks, ntiles), NT, EM_SOLO_SMEM, s>>>(d_desc, work, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aggregate_em(int m, const Desc* d_desc, const int2* work, int nblocks, int* status,
+                                cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(aggregate_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
+    return e;
+  aggregate_kernel_em<<<dim3(nblocks, m * (m + 1) / 2), NT, EM_SOLO_SMEM, s>>>(m, d_desc, work, status);
   return cudaGetLastError();
 }
 

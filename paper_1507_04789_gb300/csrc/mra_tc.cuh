@@ -133,18 +133,29 @@ __device__ __forceinline__ void tc_issue(uint32_t tmem, uint64_t da, uint64_t db
       "l"(da), "l"(db), "r"(TC_IDESC), "r"(accumulate));
 }
 
-// Wait for the MMAs committed to the mbarrier (bounded); returns false on timeout.
-__device__ __forceinline__ bool tc_wait(TcCtx& cx) {
+// Wait (bounded) for the MMAs committed to an mbarrier; flips the phase once
+// they completed.  Returns false on timeout (phase unchanged).
+__device__ __forceinline__ bool tc_wait_phase(uint64_t* mbar, uint32_t& phase) {
   uint32_t done = 0;
   for (long it = 0; it < TC_WAIT_LIMIT && !done; ++it) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done)
-        : "r"(smem_addr(cx.mbar)), "r"(cx.phase));
+        : "r"(smem_addr(mbar)), "r"(phase));
   }
-  cx.phase ^= 1;
+  if (done) phase ^= 1;
   return done != 0;
 }
+
+// After a timed-out wait: flag the failure and give the MMAs still in flight
+// one more bounded wait before the caller frees tensor memory.
+__device__ __forceinline__ void tc_abandon(uint64_t* mbar, uint32_t& phase, int* fail) {
+  if (threadIdx.x == 0) *fail = 1;
+  tc_wait_phase(mbar, phase);
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool tc_wait(TcCtx& cx) { return tc_wait_phase(cx.mbar, cx.phase); }
 
 // Add the FP32 accumulator to the FP64 registers of this thread.
 __device__ __forceinline__ void tc_drain(TcCtx& cx, TcAcc& acc) {
@@ -195,7 +206,7 @@ __device__ inline bool tc_mma(TcCtx& cx, TcAcc& acc, const double* A, long sai, 
     }
     const bool done = tc_wait(cx);
     if (__syncthreads_or(!done)) {            // uniform: every thread leaves the loop
-      if (threadIdx.x == 0) *cx.fail = 1;
+      tc_abandon(cx.mbar, cx.phase, cx.fail);
       ok = false;
       break;
     }

@@ -22,8 +22,8 @@ LIB_PATH = os.path.join(_PKG, "libmra_gb300.so")
 
 MRA_OK, MRA_ERR_ARG, MRA_ERR_OOM, MRA_ERR_CUDA, MRA_ERR_NOT_PD, MRA_ERR_STATE, MRA_ERR_LIMIT = range(7)
 MRA_COV_EXP, MRA_COV_MATERN15 = 0, 1
-MRA_PREC_FP64, MRA_PREC_MIXED = 0, 1
-PRECISIONS = {"fp64": MRA_PREC_FP64, "mixed": MRA_PREC_MIXED}
+MRA_PREC_FP64, MRA_PREC_MIXED, MRA_PREC_EMU = 0, 1, 2
+PRECISIONS = {"fp64": MRA_PREC_FP64, "mixed": MRA_PREC_MIXED, "emu": MRA_PREC_EMU}
 MRA_HOST, MRA_DEVICE = 0, 1
 MRA_MAX_LEAF = 128
 FAMILIES = {"exp": MRA_COV_EXP, "matern15": MRA_COV_MATERN15}
