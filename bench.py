@@ -6,19 +6,28 @@ parameter value: the prior pass over every level, the leaf factorisation, the
 leaf Gram products, the posterior pass and the root scalar (Sec. 3.1-3.3).
 The workload is n = 2^20 uniform locations on [0,1]^2 with a Matern-1.5 field
 (sigma2 = 1, range 0.1, tau2 = 0.01), M = 7, J = 4, r = 64 (about 64
-observations per leaf).  Both forms are timed on the same steps: the mixed
-form (tensor-core 3xTF32 prior/leaf contractions) is the headline when its
-log-likelihoods stay within |d loglik| / n <= 1e-6 of the plain FP64 form,
-which is reported beside it ("fp64"), together with loglik + gradient
-evaluations ("gradient", FP64 adjoint).
+observations per leaf).  Three forms are timed on the same steps:
+
+  fp64   every product on the FP64 pipe
+  mixed  prior and leaf contractions on the tensor cores as 3xTF32
+  emu    every large contraction (prior, leaf and both Gram products) on the
+         tensor cores as a bf16-slice FP64 emulation (about 1e-14 per product)
+
+The headline is the fastest form whose log-likelihoods stay within
+|d loglik| / n <= 1e-6 of the FP64 form; the others are reported beside it,
+together with loglik + gradient evaluations ("gradient", FP64 adjoint).
 
   value        evals/s with the inputs resident in HBM (CUDA events on the
                library's stream, max over ranks)
   e2e          the same metric through the C ABI with host inputs: every step
                copies locations and data from pinned host memory, re-partitions
                them on the device and reads the result back
-  roofline     the dominant kernel's algorithmic FP64 FLOP/s (counts below)
-               over its CUDA-event time, against the FP64 pipe's peak
+  roofline     the dominant kernel of the headline form: for a tensor-core
+               kernel, the bf16 (emu) or TF32 (mixed) tensor FLOP/s its
+               contractions need (algorithmic FP64 MACs x slice products) over
+               its CUDA-event time, against the measured bf16 peak (TF32 at the
+               nominal TF32/bf16 ratio); for an FP64 kernel, algorithmic FP64
+               FLOP/s against the FP64 pipe's peak
   cpu_baseline the FP64 CPU oracle (numpy, one thread) on one level-2 subtree
                of the same problem (1/16 of the leaves), scaled to evals/s
 
@@ -47,6 +56,10 @@ if ROOT not in sys.path:
 METRIC = "M-RA loglik(+grad) evals/s at n=2^20, mixed vs FP64 plain; % of TC/FP64 peak"
 WORKLOAD = "n1M_matern15_M7_r64"
 FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (nominal)
+BF16_PEAK_FALLBACK = 1900.0  # TFLOP/s, used only without a measured peak file
+TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 / bf16 tensor rates
+EMU_PAIRS = 28               # bf16 slice products per emulated FP64 MAC (7 slices, weights t <= 8)
+TF32_PAIRS = 3               # TF32 products per 3xTF32 MAC
 ORACLE_SAMPLE_LEVEL = 2     # cpu baseline: one level-2 subtree = 1/16 of the leaves
 
 
@@ -90,6 +103,32 @@ def algorithmic_flops(M: int, r: int, nF):
             mr = m * r
             out["aggregate"] += P * (mr * (mr + 1) * 4 * r + 2.0 * mr * 4 * r)
     return out
+
+
+def contraction_flops(M: int, r: int, nF, precision: str):
+    """The part of algorithmic_flops that a tensor-core form runs on the tensor
+    cores (everything but the factorisations, inverses and vector terms)."""
+    import numpy as np
+    if precision == "fp64":
+        return {}
+    full = algorithmic_flops(M, r, nF)
+    c = np.asarray(nF, dtype=np.float64)
+    out = {"prior": full["prior"] - sum(4.0 ** m * 2.0 * r ** 3 / 3.0 for m in range(M)),
+           "leaf": full["leaf"] - float((2.0 * c ** 3 / 3.0 + c * (c + 1)).sum())}
+    if precision == "emu":
+        Mr = M * r
+        rows = c.reshape(-1, 4).sum(axis=1) if M > 0 else c
+        out["leaf_syrk"] = float((Mr * (Mr + 1) * rows).sum()) if M > 0 else 0.0
+        out["aggregate"] = sum(4.0 ** (m - 1) * (m * r) * (m * r + 1) * 4 * r for m in range(1, M))
+    return out
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return None
 
 
 # ---------------------------------------------------------------------------
@@ -229,29 +268,35 @@ def run_reference(args):
 def run_batch(args, world, rank, mra, np, torch):
     """64 independent swath datasets (n log-uniform in [1e4, 1e6], r = 32,
     exponential covariance with per-dataset range), pruned trees, one launch
-    per level, replayed as a CUDA graph."""
+    per level, replayed as a CUDA graph; FP64 and FP64-emulation forms."""
     from paper_1507_04789_gb300 import plan, synth
     data = synth.swath_batch(args.batch_datasets, seed=7 + rank, features=64)
     datasets = [{"locs": d["locs"], "y": d["y"], "M": plan.choose_levels(d["locs"], 64), "family": "exp"}
                 for d in data]
     thetas = [(d["sigma2"], d["kappa"], d["tau2"]) for d in data]
-    b = mra.Batch(datasets, r=32)
-    t0 = time.perf_counter()
-    b.loglik(thetas)                      # autotune + graph capture
-    t_first = time.perf_counter() - t0
-    reps = 3
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(reps):
-        b.loglik([(t[0], t[1] * (1.0 + 0.01 * k), t[2]) for t in thetas])
-    dt = (time.perf_counter() - t0) / reps
-    nd, tile = b.info()
-    b.close()
     ns = [len(d["y"]) for d in datasets]
-    return {"workload": f"{nd} swath datasets, n log-uniform in [1e4, 1e6], r = 32, exponential, pruned trees",
-            "datasets": nd, "total_n": int(sum(ns)), "M_range": [min(d["M"] for d in datasets), max(d["M"] for d in datasets)],
-            "ms_per_batch": dt * 1e3, "dataset_evals_per_s": world * nd / dt, "autotuned_tile": tile,
-            "first_call_s": t_first, "timing": "host wall clock around graph replays (each ends in a stream sync)"}
+    out = {"workload": f"{len(datasets)} swath datasets, n log-uniform in [1e4, 1e6], r = 32, exponential, "
+                       f"pruned trees", "datasets": len(datasets), "total_n": int(sum(ns)),
+           "M_range": [min(d["M"] for d in datasets), max(d["M"] for d in datasets)],
+           "timing": "host wall clock around graph replays (each ends in a stream sync)"}
+    lls = {}
+    for prec in ("fp64", "emu"):
+        b = mra.Batch(datasets, r=32, precision=prec)
+        t0 = time.perf_counter()
+        b.loglik(thetas)                      # autotune + graph capture
+        t_first = time.perf_counter() - t0
+        reps = 3
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(reps):
+            lls[prec] = b.loglik([(t[0], t[1] * (1.0 + 0.01 * k), t[2]) for t in thetas])
+        dt = (time.perf_counter() - t0) / reps
+        nd, tile = b.info()
+        b.close()
+        out[prec] = {"ms_per_batch": dt * 1e3, "dataset_evals_per_s": world * nd / dt, "autotuned_tile": tile,
+                     "first_call_s": t_first}
+    out["emu_max_rel_dloglik_vs_fp64"] = float(np.max(np.abs(lls["emu"] - lls["fp64"]) / np.abs(lls["fp64"])))
+    return out
 
 
 def main():
@@ -306,15 +351,14 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    def time_form(precision, with_clocks):
+    def time_form(precision):
         h = mra.Handle(locs, y, M=w.M, r=w.r, family=w.family, precision=precision)
         h.set_stream(stream)
         lls = [h.loglik(thetas[k]) for k in range(args.warmup)]
         h.enable_timing(True)
         mra.launch_count(reset=True)
-        clk = ClockSampler(local) if with_clocks else None
-        if clk:
-            clk.start()
+        clk = ClockSampler(local)
+        clk.start()
         barrier()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -324,7 +368,7 @@ def main():
             lls.append(h.loglik(thetas[k]))
         e1.record(stream)
         torch.cuda.synchronize()
-        clocks = clk.stop() if clk else None
+        clocks = clk.stop()
         ms = max_over_ranks(e0.elapsed_time(e1))
         launches = mra.launch_count(reset=True)
         kt = h.kernel_times()
@@ -332,13 +376,19 @@ def main():
         return h, {"ms_per_step": ms / args.steps, "value": world * 1e3 * args.steps / ms, "lls": lls,
                    "kernels": kt, "launches": launches, "clocks": clocks}
 
-    # ---- mixed form (headline when within the error bound), then plain FP64 ----
-    hm, mixed = time_form("mixed", True)
-    off = hm.leaf_offsets()
+    # ---- the three forms on the same steps ----
+    forms, handles = {}, {}
+    for prec in ("emu", "mixed", "fp64"):
+        handles[prec], forms[prec] = time_form(prec)
+    off = handles["fp64"].leaf_offsets()
     flops = algorithmic_flops(w.M, w.r, np.diff(off))
     total_flops = sum(flops.values())
-    h64, plain = time_form("fp64", False)
-    dll = max(abs(a - b) for a, b in zip(mixed["lls"], plain["lls"])) / w.n
+    for prec in ("emu", "mixed"):
+        forms[prec]["dll"] = max(abs(a - b) for a, b in zip(forms[prec]["lls"], forms["fp64"]["lls"])) / w.n
+    for prec in ("emu", "mixed"):
+        if prec != "emu":
+            handles[prec].close()
+    h64 = handles["fp64"]
 
     # ---- gradient (FP64 adjoint) ----
     g_steps = max(2, args.steps // 2)
@@ -359,26 +409,59 @@ def main():
                 "what": "loglik + d/d(sigma2, range, tau2), FP64 reverse-mode adjoint",
                 "adjoint_ms_per_step": g_kt["grad"][0] / g_steps, "grad": [float(v) for v in grad]}
 
-    def kernel_table(res):
-        return {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
-                    "fp64_alg_tflops": (flops[k] * args.steps / (v[0] * 1e-3) / 1e12) if v[0] > 0 else None}
-                for k, v in res["kernels"].items() if v[1] > 0 and k in flops}
+    peaks = measured_peaks()
+    bf16_peak = peaks["bf16_tflops_sustained"] if peaks else BF16_PEAK_FALLBACK
+    peak_src = "of measured (bf16 sustained, MEASURED_PEAKS.json)" if peaks else "of fallback (recipe)"
 
-    use_mixed = dll <= 1e-6
-    head = mixed if use_mixed else plain
-    h = hm if use_mixed else h64
-    # roofline of the dominant FP64 kernel of the headline form
+    def kernel_table(prec):
+        res = forms[prec]
+        cf = contraction_flops(w.M, w.r, np.diff(off), prec)
+        pairs = EMU_PAIRS if prec == "emu" else TF32_PAIRS
+        tab = {}
+        for k, v in res["kernels"].items():
+            if v[1] == 0 or k not in flops:
+                continue
+            sec = v[0] * 1e-3 / args.steps
+            row = {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps,
+                   "fp64_alg_tflops": flops[k] / sec / 1e12 if sec > 0 else None}
+            if k in cf and sec > 0:
+                row["tensor_tflops"] = pairs * cf[k] / sec / 1e12
+            tab[k] = row
+        return tab
+
+    ok = [p for p in ("emu", "mixed") if forms[p]["dll"] <= 1e-6]
+    best = min(ok, key=lambda p: forms[p]["ms_per_step"]) if ok else "fp64"
+    if forms["fp64"]["ms_per_step"] < forms[best]["ms_per_step"]:
+        best = "fp64"
+    head = forms[best]
+    # roofline of the dominant kernel of the headline form
     kt = head["kernels"]
     dom = max((k for k in kt if kt[k][1] > 0 and k in flops), key=lambda k: kt[k][0])
     dom_ms, dom_n = kt[dom]
-    achieved = flops[dom] * args.steps / (dom_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dom,
-                "launches_per_step": dom_n / args.steps,
-                "peak_source": "nominal FP64 pipe (recipe); DFMA loop measured 1.19 TFLOP/s at 1995 MHz",
-                "kernels": kernel_table(head), "step_fp64_alg_tflops": total_flops / (head["ms_per_step"] * 1e-3) / 1e12}
+    sec = dom_ms * 1e-3 / args.steps
+    cf = contraction_flops(w.M, w.r, np.diff(off), best)
+    if dom in cf:
+        pairs = EMU_PAIRS if best == "emu" else TF32_PAIRS
+        peak = bf16_peak * (1.0 if best == "emu" else TF32_PER_BF16)
+        achieved = pairs * cf[dom] / sec / 1e12
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "kernel": dom,
+                    "peak_source": peak_src + ("" if best == "emu" else " x nominal TF32/bf16 ratio"),
+                    "per_unit": f"{pairs} {'bf16' if best == 'emu' else 'TF32'} MACs per FP64 MAC of the "
+                                f"kernel's contractions",
+                    "fp64_alg_tflops": flops[dom] / sec / 1e12}
+    else:
+        achieved = flops[dom] / sec / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dom,
+                    "peak_source": "nominal FP64 pipe (recipe); DFMA loop measured 1.19 TFLOP/s at 1995 MHz"}
+    roofline.update({"launches_per_step": dom_n / args.steps, "kernels": kernel_table(best),
+                     "step_fp64_alg_tflops": total_flops / (head["ms_per_step"] * 1e-3) / 1e12})
 
     # ---- end to end through the C ABI with host inputs (headline form) ----
+    h = handles[best] if best in ("emu", "fp64") else mra.Handle(locs, y, M=w.M, r=w.r, family=w.family,
+                                                                 precision=best)
+    h.set_stream(stream)
     pin_l = torch.from_numpy(np.ascontiguousarray(locs)).pin_memory()
     pin_y = torch.from_numpy(np.ascontiguousarray(y)).pin_memory()
     nl, ny = pin_l.numpy(), pin_y.numpy()
@@ -394,27 +477,34 @@ def main():
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps)
     e2e = {"value": world / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": int(locs.nbytes + y.nbytes),
            "d2h_bytes_per_step": 32}
-
-    hm.close()
-    h64.close()
+    h.close()
+    for p in ("emu", "fp64"):
+        if handles[p] is not h:
+            handles[p].close()
     batch = None if args.no_batch else run_batch(args, world, rank, mra, np, torch)
 
     if rank == 0:
+        dtypes = {"fp64": "f64", "mixed": "f64+tf32x3", "emu": "f64+bf16x7 (emulated f64)"}
+
+        def form_line(p):
+            out = {"value": forms[p]["value"], "ms_per_step": forms[p]["ms_per_step"], "kernels": kernel_table(p),
+                   "clocks": forms[p]["clocks"]}
+            if p != "fp64":
+                out["dloglik_per_obs_vs_fp64"] = forms[p]["dll"]
+            return out
+
         line = {
             "metric": METRIC, "value": head["value"], "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64+tf32x3" if use_mixed else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": dtypes[best], "data": "synthetic",
             "config": {"workload": w.name, "n": w.n, "M": w.M, "J": w.J, "r": w.r, "family": w.family,
-                       "sigma2": w.sigma2, "range": w.kappa, "tau2": w.tau2,
-                       "precision": "mixed" if use_mixed else "fp64",
+                       "sigma2": w.sigma2, "range": w.kappa, "tau2": w.tau2, "precision": best,
                        "max_leaf": int(np.diff(off).max()), "step": "one log-likelihood evaluation",
                        "l2": "working set ~10 GB per evaluation, far larger than the 129 MB L2 (no flush)",
                        "parallelism": f"replicas{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(head["launches"]),
-            "clocks": mixed["clocks"],
-            "mixed": {"value": mixed["value"], "ms_per_step": mixed["ms_per_step"], "dloglik_per_obs_vs_fp64": dll,
-                      "kernels": kernel_table(mixed)},
-            "fp64": {"value": plain["value"], "ms_per_step": plain["ms_per_step"], "kernels": kernel_table(plain)},
+            "clocks": head["clocks"],
+            "emu": form_line("emu"), "mixed": form_line("mixed"), "fp64": form_line("fp64"),
             "gradient": gradient, "loglik": head["lls"][-1], "flops_per_step": total_flops,
             "batch": batch,
         }

@@ -5,22 +5,31 @@
 // transformations of matrix multiplication by using fast routines of matrix
 // multiplication and its applications"), written here for bf16 tensor cores:
 //
-//  * every row of A and of B is scaled, per group of 64 K-columns, by a power of
-//    two 2^e with |x| < 2^e over the group, and its 49 leading bits are cut into
-//    S = 7 slices of 7 bits: x = sum_p a_p 2^(e - 7p), a_p integer, |a_p| < 128,
-//    exact in bf16;
+//  * every row of A and of B is scaled, per group of 128 K-columns, by a power
+//    of two 2^e with |x| < 2^e over the group, and its 49 leading bits are cut
+//    into S = 7 slices of 7 bits: x = sum_p a_p 2^(e - 7p), a_p integer,
+//    |a_p| < 128, exact in bf16;
 //  * a_p b_q products are exact (< 2^14) and the FP32 sums of every pair with
-//    the same weight t = p + q over a group stay below 64 * 7 * 127^2 < 2^24, so
-//    the tensor-memory accumulation is exact too; the 28 pairs with t <= S + 1
-//    go to 7 accumulators (one per t, 64 TMEM columns each);
-//  * every group is drained: accumulator t is scaled by 2^(e_i + f_j - 7t)
-//    (exact) and added to a double-float (hi + lo FP32 pair, TwoSum) register
-//    accumulator, converted to FP64 once at the end.
+//    the same weight t = p + q over a group stay below 128 * 7 * 127^2 < 2^24,
+//    so the tensor-memory accumulation is exact too; the 28 pairs with
+//    t <= S + 1 go to 7 accumulators (one per t, 64 TMEM columns each);
+//  * every group is drained: the 7 accumulators of a column are combined in
+//    units of the leading weight (double-float, TwoSum for the three largest
+//    corrections), scaled by 2^(e_i + f_j - 14) (exact) and added to a
+//    double-float register accumulator, converted to FP64 once at the end.
 //
 // The only rounding is the truncation of each operand to 49 bits below its
-// group's largest element and the double-float sum (about 2^-48 relative), so
+// group's largest element and the double-float sums (about 2^-48 relative), so
 // a product matches FP64 to about 1e-14 relative to sum |a b| while running on
-// the tensor cores; the FP64 pipe only does the final conversion.
+// the tensor cores; the FP64 pipe only does the final conversion.  Range: the
+// running sums are FP32 pairs, so |results| < 2^127, and a group whose scale
+// product 2^(e_i + f_j) is below 2^-88 is dropped (its contribution is below
+// 2^-80 in absolute value).
+//
+// Pipeline: the K range is staged in chunks of 16 (one MMA K-step) into two
+// shared-memory buffers; while the MMAs of one chunk run, the CTA splits the
+// next chunk into the other buffer.  Row scales of up to four groups are found
+// in one pass before the chunks that use them.
 #pragma once
 #include "mra_tc.cuh"
 
@@ -28,25 +37,32 @@ namespace mra {
 
 constexpr int EM_S = 7;                       // slices per operand
 constexpr int EM_BITS = EM_S * 7;             // 49 leading bits
-constexpr int EM_KC = 32;                     // staged K chunk (bf16 elements)
-constexpr int EM_KG = 64;                     // K group sharing one scale per row (drain period)
-constexpr int EM_NACC = EM_S;                 // accumulators, t = 2 .. S + 1
-constexpr int EM_KCORES = EM_KC / 8;          // 16-byte core columns (8 bf16) per chunk
-constexpr int EM_A_HALFS = TC_M * EM_KC;      // bf16 per slice plane of A
-constexpr int EM_B_HALFS = TC_N * EM_KC;
-constexpr int EM_STAGE_BYTES = 2 * EM_S * (EM_A_HALFS + EM_B_HALFS);   // 86016
+constexpr int EM_KC = 16;                     // staged K chunk (bf16 elements) = one MMA K-step
+constexpr int EM_KG = 128;                    // K group sharing one scale per row (drain period)
+constexpr int EM_MAXG = 4;                    // groups whose scales one pass finds
+constexpr int EM_CC = EM_KC / 8;              // 16-byte core columns (8 bf16) per chunk
+constexpr int EM_A_HALFS = TC_M * EM_KC;      // bf16 per slice plane of A (4 KB)
+constexpr int EM_B_HALFS = TC_N * EM_KC;      // (2 KB)
+constexpr int EM_BUF_HALFS = EM_S * (EM_A_HALFS + EM_B_HALFS);
+constexpr int EM_STAGE_BYTES = 2 * 2 * EM_BUF_HALFS;                    // two buffers: 86016
+constexpr int EM_REXP = EM_MAXG * TC_M;       // ints of row scales of A (shared)
+constexpr int EM_CEXP = EM_MAXG * TC_N;       // ints of row scales of B (shared)
 constexpr uint32_t EM_TMEM_COLS = 512;
+static_assert(EM_KG * EM_S * 127 * 127 < (1 << 24), "group sums must stay exact in FP32");
+static_assert(EM_S * TC_N <= (int)EM_TMEM_COLS, "accumulators exceed the tensor-memory allocation");
 // kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, 128 x 64.
 constexpr uint32_t EM_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
                               ((uint32_t)(TC_M >> 4) << 24);
 
+// Shared-memory matrix descriptor, no swizzle, K-major core matrices of 8 rows x
+// 16 bytes: 128 B between K-adjacent cores, EM_CC * 128 B between 8-row groups.
 __device__ __forceinline__ uint64_t em_desc(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((128u >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)(((EM_KCORES * 128u) >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+         ((uint64_t)(((EM_CC * 128u) >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
 __device__ __forceinline__ int em_cm(int row, int k) {   // bf16 index in a staged plane
-  return (((row >> 3) * EM_KCORES + (k >> 3)) << 6) + ((row & 7) << 3) + (k & 7);
+  return (((row >> 3) * EM_CC + (k >> 3)) << 6) + ((row & 7) << 3) + (k & 7);
 }
 
 // Binary exponent e with |x| < 2^e (x != 0, normal); -2000 for zero.
@@ -57,12 +73,14 @@ __device__ __forceinline__ int em_exp(double x) {
 }
 
 struct EmCtx {
-  uint16_t* stage;   // EM_STAGE_BYTES of shared memory: 7 A planes, then 7 B planes
-  int* rexp;         // TC_M row scales of A (shared)
-  int* cexp;         // TC_N row scales of B (shared)
-  uint64_t* mbar;
+  uint16_t* stage;   // EM_STAGE_BYTES of shared memory: two buffers of 7 A planes, then 7 B planes
+  int* rexp;         // EM_REXP row scales of A, [group][row]
+  int* cexp;         // EM_CEXP row scales of B
+  uint64_t* mbar;    // two mbarriers, one per staging buffer
   uint32_t tmem;
-  uint32_t phase;
+  uint32_t phase;    // bit b: parity of the next completion of mbar[b]
+  uint32_t pending;  // bit b: MMAs committed to mbar[b] and not yet waited for
+  int buf;           // buffer the next chunk is staged into
   int* fail;
 };
 
@@ -73,7 +91,8 @@ __device__ inline void em_init(EmCtx& cx, uint32_t* tmem_slot) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(cx.mbar)), "r"(1));
+    for (int b = 0; b < 2; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(cx.mbar + b)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
     *cx.fail = 0;
   }
@@ -82,6 +101,8 @@ __device__ inline void em_init(EmCtx& cx, uint32_t* tmem_slot) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   cx.tmem = *tmem_slot;
   cx.phase = 0;
+  cx.pending = 0;
+  cx.buf = 0;
 }
 
 __device__ inline void em_release(EmCtx& cx) {
@@ -91,66 +112,147 @@ __device__ inline void em_release(EmCtx& cx) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(cx.tmem), "r"(EM_TMEM_COLS));
 }
 
-// Row scales over K columns [k0, k0 + kn <= 64) of rows [0, nx): one warp per
-// row for row-major operands (coalesced along K), one thread per row otherwise.
-__device__ __forceinline__ void em_scales(int* ex, int rows, const double* X, long sxi, long sxk, int nx, int k0,
-                                          int kn) {
-  if (sxk == 1) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = warp; i < rows; i += NT / 32) {
-      int e = -2000;
-      if (i < nx)
-        for (int k = lane; k < kn; k += 32) e = max(e, em_exp(X[i * sxi + (long)(k0 + k)]));
+// Wait (bounded, every thread) for the MMAs committed to buffer b; false
+// (uniformly) on timeout, after one more bounded wait for what is in flight.
+__device__ __forceinline__ bool em_poll(EmCtx& cx, int b) {
+  uint32_t ph = (cx.phase >> b) & 1u;
+  const bool done = tc_wait_phase(cx.mbar + b, ph);
+  if (done) cx.phase ^= 1u << b;
+  return done;
+}
+
+__device__ inline bool em_wait_buf(EmCtx& cx, int b) {
+  if (!((cx.pending >> b) & 1u)) return true;
+  const bool done = em_poll(cx, b);
+  if (__syncthreads_or(!done)) {
+    if (threadIdx.x == 0) *cx.fail = 1;
+    for (int q = 0; q < 2; ++q)
+      if ((cx.pending >> q) & 1u) em_poll(cx, q);
+    cx.pending = 0;
+    __syncthreads();
+    return false;
+  }
+  cx.pending &= ~(1u << b);
+  return true;
+}
+
+// Largest exponent over the 8 K columns [8 kc, 8 kc + 8) of row i (-2000 if none).
+__device__ __forceinline__ int em_item_exp(const double* X, long si, long sk, int n, int i, int kc, int K0, int KS) {
+  int e = -2000;
+  if (i < n) {
+    const double* p = X + (long)i * si + (long)(K0 + 8 * kc) * sk;
+    const int kn = min(8, KS - 8 * kc);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-      if (lane == 0) ex[i] = e;
+    for (int j = 0; j < 8; ++j)
+      if (j < kn) e = max(e, em_exp(p[(long)j * sk]));
+  }
+  return e;
+}
+
+// Row scales of the groups of K columns [K0, K0 + KS), KS <= EM_MAXG * EM_KG:
+// rexp[g * TC_M + i] = max exponent of row i of A over group g (cexp for B).
+// Item = 8 consecutive K of one row; consecutive threads take consecutive rows;
+// four items per thread are loaded before their maxima are merged.
+__device__ inline void em_scales(EmCtx& cx, const double* A, long sai, long sak, int na, const double* B, long sbj,
+                                 long sbk, int nb, int K0, int KS) {
+  __syncthreads();                                   // previous scales are no longer read
+  const int ng = (KS + EM_KG - 1) / EM_KG;
+  for (int t = threadIdx.x; t < ng * (TC_M + TC_N); t += NT) {
+    if (t < ng * TC_M) cx.rexp[t] = -2000;
+    else cx.cexp[t - ng * TC_M] = -2000;
+  }
+  __syncthreads();
+  const int ncore = (KS + 7) >> 3;
+  const int itemsA = TC_M * ncore, items = (TC_M + TC_N) * ncore;
+  for (int base = 0; base < items; base += 4 * NT) {
+    int e[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int it = base + u * NT + threadIdx.x;
+      e[u] = -2000;
+      if (it < itemsA) e[u] = em_item_exp(A, sai, sak, na, it % TC_M, it / TC_M, K0, KS);
+      else if (it < items) e[u] = em_item_exp(B, sbj, sbk, nb, (it - itemsA) % TC_N, (it - itemsA) / TC_N, K0, KS);
     }
-  } else {
-    for (int i = threadIdx.x; i < rows; i += NT) {
-      int e = -2000;
-      if (i < nx)
-        for (int k = 0; k < kn; ++k) e = max(e, em_exp(X[(long)(k0 + k) * sxk + i * sxi]));
-      ex[i] = e;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int it = base + u * NT + threadIdx.x;
+      if (e[u] <= -2000) continue;
+      if (it < itemsA) atomicMax(cx.rexp + ((8 * (it / TC_M)) / EM_KG) * TC_M + it % TC_M, e[u]);
+      else {
+        const int jt = it - itemsA;
+        atomicMax(cx.cexp + ((8 * (jt / TC_N)) / EM_KG) * TC_N + jt % TC_N, e[u]);
+      }
     }
   }
   __syncthreads();
 }
 
-// 7 bf16 slices of x relative to scale e (|x| < 2^e) into planes[p * pstride + w].
-__device__ __forceinline__ void em_split(double x, int e, uint16_t* planes, int pstride, int w) {
+// The 7 slices of x relative to scale e (|x| < 2^e), as FP32 integers with x's sign.
+__device__ __forceinline__ void em_split(double x, int e, float* f) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int be = (int)((u >> 52) & 0x7FF);
   unsigned long long X = 0;
   if (be != 0) {
-    const int E = be - 1023;
-    const unsigned long long m = (u & ((1ull << 52) - 1)) | (1ull << 52);   // x = m 2^(E - 52)
-    const int sh = (52 - EM_BITS) + e - E;                                   // >= 4
-    X = sh < 64 ? (m >> sh) : 0ull;                                          // x 2^(49 - e), truncated
+    const unsigned long long m = (u & ((1ull << 52) - 1)) | (1ull << 52);   // |x| = m 2^(be - 1075)
+    const int sh = (52 - EM_BITS) + e - (be - 1023);                         // >= 4
+    X = sh < 53 ? (m >> sh) : 0ull;                                          // |x| 2^(49 - e), truncated
   }
-  const uint16_t sgn = (uint16_t)((u >> 48) & 0x8000u);
+  const uint32_t xh = (uint32_t)(X >> 32), xl = (uint32_t)X;
+  uint32_t a[EM_S];
+  a[0] = xh >> 10;
+  a[1] = (xh >> 3) & 127u;
+  a[2] = ((xh << 4) | (xl >> 28)) & 127u;
+  a[3] = (xl >> 21) & 127u;
+  a[4] = (xl >> 14) & 127u;
+  a[5] = (xl >> 7) & 127u;
+  a[6] = xl & 127u;
+  const float sg = (u >> 63) ? -1.0f : 1.0f;
+  // (2^23 + a) sg - 2^23 sg = a sg exactly (a < 2^23)
 #pragma unroll
-  for (int p = 1; p <= EM_S; ++p) {
-    const unsigned a = (unsigned)((X >> (EM_BITS - 7 * p)) & 127ull);
-    const uint16_t h = (uint16_t)(__float_as_uint((float)a) >> 16);          // exact: a < 128
-    planes[(p - 1) * pstride + w] = (uint16_t)(h | sgn);
-  }
+  for (int p = 0; p < EM_S; ++p) f[p] = fmaf(__uint_as_float(0x4B000000u | a[p]), sg, -8388608.0f * sg);
 }
 
-__device__ __forceinline__ void em_stage(uint16_t* planes, int pstride, const int* ex, int rows, const double* X,
-                                         long sxi, long sxk, int nx, int k0, int kn) {
-  const int total = rows * EM_KC;
-  if (sxk == 1) {
-    for (int t = threadIdx.x; t < total; t += NT) {
-      const int i = t / EM_KC, k = t - i * EM_KC;
-      const double x = (i < nx && k < kn) ? X[i * sxi + (long)(k0 + k)] : 0.0;
-      em_split(x, ex[i], planes, pstride, em_cm(i, k));
+__device__ __forceinline__ uint32_t em_pack(float hi, float lo) {   // exact: small integers
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
+// Split K columns [k0, k0 + kn) (kn <= EM_KC) of A and B into buffer b.
+// Item = one 16-byte core row (8 K) of one row; eight consecutive threads take
+// eight consecutive rows of one core column (128 contiguous bytes per plane).
+__device__ inline void em_stage(EmCtx& cx, int b, int g, const double* A, long sai, long sak, int na,
+                                const double* B, long sbj, long sbk, int nb, int k0, int kn) {
+  uint16_t* base = cx.stage + b * EM_BUF_HALFS;
+  constexpr int itemsA = TC_M * EM_CC, items = (TC_M + TC_N) * EM_CC;
+  for (int it = threadIdx.x; it < items; it += NT) {
+    const bool isA = it < itemsA;
+    const int jt = isA ? it : it - itemsA;
+    const int rows8 = (isA ? TC_M : TC_N) >> 3;
+    const int i = (jt & 7) + 8 * ((jt >> 3) % rows8), kc = (jt >> 3) / rows8;
+    const double* X = isA ? A : B;
+    const long si = isA ? sai : sbj, sk = isA ? sak : sbk;
+    const int n = isA ? na : nb;
+    const int e = (isA ? cx.rexp + g * TC_M : cx.cexp + g * TC_N)[i];
+    double x[8];
+    const double* p = X + (long)i * si + (long)(k0 + 8 * kc) * sk;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = (i < n && 8 * kc + j < kn) ? p[(long)j * sk] : 0.0;
+    uint32_t w[EM_S][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float f0[EM_S], f1[EM_S];
+      em_split(x[2 * q], e, f0);
+      em_split(x[2 * q + 1], e, f1);
+#pragma unroll
+      for (int s = 0; s < EM_S; ++s) w[s][q] = em_pack(f1[s], f0[s]);
     }
-  } else {
-    for (int t = threadIdx.x; t < total; t += NT) {
-      const int k = t / rows, i = t - k * rows;
-      const double x = (i < nx && k < kn) ? X[(long)(k0 + k) * sxk + i * sxi] : 0.0;
-      em_split(x, ex[i], planes, pstride, em_cm(i, k));
-    }
+    uint16_t* planes = isA ? base : base + EM_S * EM_A_HALFS;
+    const int pstride = isA ? EM_A_HALFS : EM_B_HALFS;
+    const int off = em_cm(i, 8 * kc);
+#pragma unroll
+    for (int s = 0; s < EM_S; ++s)
+      *reinterpret_cast<uint4*>(planes + s * pstride + off) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
   }
 }
 
@@ -169,86 +271,92 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
   lo += err;
 }
 
+__device__ __forceinline__ void em_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
+// Drain the group with row scale ei and column scales cexp[c0 + c] into the
+// running double-float sums (hi, lo) of this thread's 32 columns.
+__device__ inline void em_drain(EmCtx& cx, const int* cexp, int ei, int c0, float* hi, float* lo) {
+  const uint32_t lane_off = (uint32_t)((threadIdx.x >> 5) & 3) << 21;
+#pragma unroll
+  for (int cb = 0; cb < 32; cb += 8) {
+    uint32_t v[EM_S][8];
+#pragma unroll
+    for (int t = 0; t < EM_S; ++t) em_ld8(cx.tmem + lane_off + (uint32_t)(t * TC_N + c0 + cb), v[t]);
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      // group value in units of 2^(e_i + f_j - 14): sum_t v_t 2^(-7 (t - 2))
+      float gh = __uint_as_float(v[0][c]), gl = 0.0f;
+      two_sum_add(gh, gl, __uint_as_float(v[1][c]) * 0x1p-7f);
+      two_sum_add(gh, gl, __uint_as_float(v[2][c]) * 0x1p-14f);
+      two_sum_add(gh, gl, __uint_as_float(v[3][c]) * 0x1p-21f);
+      gl = fmaf(__uint_as_float(v[4][c]), 0x1p-28f, gl);
+      gl = fmaf(__uint_as_float(v[5][c]), 0x1p-35f, gl);
+      gl = fmaf(__uint_as_float(v[6][c]), 0x1p-42f, gl);
+      const int e = ei + cexp[c0 + cb + c] - 14;
+      if (e >= -102 && e <= 127) {
+        const float s = __int_as_float((e + 127) << 23);
+        two_sum_add(hi[cb + c], lo[cb + c], gh * s);
+        lo[cb + c] = fmaf(gl, s, lo[cb + c]);
+      }
+    }
+  }
+}
+
 // acc(i, j) += sum_k A(i, k) B(j, k) with FP64-grade accuracy, i < na <= 128,
 // j < nb <= 64.  Returns false (uniformly) if a tensor-core wait timed out.
 __device__ inline bool em_mma(EmCtx& cx, TcAcc& acc, const double* A, long sai, long sak, int na, const double* B,
                               long sbj, long sbk, int nb, int K) {
-  uint16_t* aP = cx.stage;
-  uint16_t* bP = cx.stage + EM_S * EM_A_HALFS;
   const int row = acc.row(), c0 = acc.col0();
   float hi[32], lo[32];
 #pragma unroll
   for (int c = 0; c < 32; ++c) hi[c] = lo[c] = 0.f;
-  bool ok = true;
-  for (int g0 = 0; g0 < K && ok; g0 += EM_KG) {
-    const int gn = min(EM_KG, K - g0);
-    em_scales(cx.rexp, TC_M, A, sai, sak, na, g0, gn);
-    em_scales(cx.cexp, TC_N, B, sbj, sbk, nb, g0, gn);
-    for (int k0 = g0; k0 < g0 + gn; k0 += EM_KC) {
-      const int kn = min(EM_KC, g0 + gn - k0);
-      em_stage(aP, EM_A_HALFS, cx.rexp, TC_M, A, sai, sak, na, k0, kn);
-      em_stage(bP, EM_B_HALFS, cx.cexp, TC_N, B, sbj, sbk, nb, k0, kn);
+  for (int K0 = 0; K0 < K; K0 += EM_MAXG * EM_KG) {
+    const int KS = min(EM_MAXG * EM_KG, K - K0);
+    em_scales(cx, A, sai, sak, na, B, sbj, sbk, nb, K0, KS);
+    for (int kk = 0; kk < KS; kk += EM_KC) {
+      const int b = cx.buf;
+      if (!em_wait_buf(cx, b)) return false;          // the MMAs of two chunks ago released buffer b
+      const int g = kk / EM_KG;
+      em_stage(cx, b, g, A, sai, sak, na, B, sbj, sbk, nb, K0 + kk, min(EM_KC, KS - kk));
       asm volatile("fence.proxy.async.shared::cta;");
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncthreads();
       asm volatile("tcgen05.fence::after_thread_sync;");
       if (threadIdx.x == 0) {
-        for (int j = 0; j < EM_KC / 16; ++j) {
-          const uint32_t off = (uint32_t)j * 256u;           // K-step of 16 bf16 = two core columns
-          for (int t = 2; t <= EM_S + 1; ++t) {
-            const uint32_t dt = cx.tmem + (uint32_t)(t - 2) * TC_N;
-            bool first = (k0 == g0) && (j == 0);
-            for (int p = max(1, t - EM_S); p <= min(EM_S, t - 1); ++p) {
-              const int q = t - p;
-              const uint64_t da = em_desc(smem_addr(aP + (p - 1) * EM_A_HALFS) + off);
-              const uint64_t db = em_desc(smem_addr(bP + (q - 1) * EM_B_HALFS) + off);
-              em_issue(dt, da, db, first ? 0u : 1u);
-              first = false;
-            }
+        const uint16_t* aP = cx.stage + b * EM_BUF_HALFS;
+        const uint16_t* bP = aP + EM_S * EM_A_HALFS;
+        const bool gfirst = (kk % EM_KG) == 0;
+#pragma unroll
+        for (int t = 2; t <= EM_S + 1; ++t) {
+          const uint32_t dt = cx.tmem + (uint32_t)(t - 2) * TC_N;
+#pragma unroll
+          for (int p = 1; p < t; ++p) {                 // q = t - p in [1, 7] since t <= 8
+            const uint64_t da = em_desc(smem_addr(aP + (p - 1) * EM_A_HALFS));
+            const uint64_t db = em_desc(smem_addr(bP + (t - p - 1) * EM_B_HALFS));
+            em_issue(dt, da, db, (gfirst && p == 1) ? 0u : 1u);
           }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_addr(cx.mbar)));
+            smem_addr(cx.mbar + b)));
       }
-      const bool done = tc_wait_phase(cx.mbar, cx.phase);
-      if (__syncthreads_or(!done)) {
-        tc_abandon(cx.mbar, cx.phase, cx.fail);
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
-    }
-    if (!ok) break;
-    // drain the group: accumulator t weighs 2^(e_i + f_j - 7t)
-    const uint32_t lane_off = (uint32_t)((threadIdx.x >> 5) & 3) << 21;
-    const int ei = cx.rexp[row];
-    for (int t = 2; t <= EM_S + 1; ++t) {
-      uint32_t r[32];
-      const uint32_t taddr = cx.tmem + lane_off + (uint32_t)((t - 2) * TC_N + c0);
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-            "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        const int e = ei + cx.cexp[c0 + c] - 7 * t;
-        const float v = __uint_as_float(r[c]);
-        if (v != 0.f && e >= -126 && e <= 127) two_sum_add(hi[c], lo[c], v * __int_as_float((e + 127) << 23));
+      cx.pending |= 1u << b;
+      cx.buf ^= 1;
+      if ((kk + EM_KC) % EM_KG == 0 || kk + EM_KC >= KS) {   // group complete: drain it
+        if (!em_wait_buf(cx, b ^ 1) || !em_wait_buf(cx, b)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        em_drain(cx, cx.cexp + g * TC_N, cx.rexp[g * TC_M + row], c0, hi, lo);
+        asm volatile("tcgen05.fence::before_thread_sync;");
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();   // scales and TMEM are reused by the next group
   }
 #pragma unroll
   for (int c = 0; c < 32; ++c) acc.v[c] += (double)hi[c] + (double)lo[c];
-  return ok;
+  return true;
 }
 
 }  // namespace mra

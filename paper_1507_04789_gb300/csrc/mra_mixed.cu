@@ -47,7 +47,11 @@ struct Engine<true> {
   static constexpr int STAGE = EM_STAGE_BYTES;
   EmCtx cx;
   __device__ void init(unsigned char* stage, uint64_t* mbar, uint32_t* tmem_slot, int* fail, int* rexp, int* cexp) {
-    cx = EmCtx{reinterpret_cast<uint16_t*>(stage), rexp, cexp, mbar, 0, 0, fail};
+    cx.stage = reinterpret_cast<uint16_t*>(stage);
+    cx.rexp = rexp;
+    cx.cexp = cexp;
+    cx.mbar = mbar;
+    cx.fail = fail;
     em_init(cx, tmem_slot);
   }
   __device__ bool mma(TcAcc& acc, const double* A, long sai, long sak, int na, const double* B, long sbj, long sbk,
@@ -61,10 +65,10 @@ template <bool EMU>
 __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* __restrict__ D,
                                                              const int2* __restrict__ work, int* status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail, bad;
-  __shared__ int rexp[TC_M], cexp[TC_N];
+  __shared__ int rexp[EMU ? EM_REXP : 1], cexp[EMU ? EM_CEXP : 1];
   const Item it = work_item(work);
   const Desc& ds = D[it.d];
   const Shape sh = ds.sh;
@@ -80,7 +84,7 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
   double* W = tmp + MAX_R_DEV;                 // r x (r + 1)
   if (threadIdx.x == 0) bad = 0;
   Engine<EMU> eng;
-  eng.init(dsm, &mbar, &tmem_slot, &fail, rexp, cexp);
+  eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
   load_knots(sh.bbox, m, st.mort[m][i], sh.gx, sh.gy, qx, qy);
   double* Vrow = st.V[m] + i * (long)r * mr;
   TcAcc acc;
@@ -96,6 +100,7 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
     if (l > 0) ok = eng.mma(acc, Vrow, mr, 1, r, Vanc, l * r, 1, r, l * r);
     if (!ok) break;
     if (row < r)
+      #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int col = c0 + c;
         if (col < r) Vrow[(long)row * mr + l * r + col] = cov0(cv, qx[row], qy[row], ax[col], ay[col]) - acc.v[c];
@@ -105,6 +110,7 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
     ok = eng.mma(acc, Vrow + l * r, mr, 1, r, st.Li[l] + a * (long)r * r, r, 1, r, r);
     if (!ok) break;
     if (row < r)
+      #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int col = c0 + c;
         if (col < r) Vrow[(long)row * mr + l * r + col] = acc.v[c];
@@ -118,6 +124,7 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
   if (ok) {
     const int ldw = r + 1;
     if (row < r)
+      #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int col = c0 + c;
         if (col < r) W[row * ldw + col] = cov0(cv, qx[row], qy[row], qx[col], qy[col]) - acc.v[c];
@@ -143,10 +150,10 @@ template <bool EMU>
 __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D, const int2* __restrict__ work,
                                                      int* status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail, bad;
-  __shared__ int rexp[TC_M], cexp[TC_N];
+  __shared__ int rexp[EMU ? EM_REXP : 1], cexp[EMU ? EM_CEXP : 1];
   const Item it = work_item(work);
   const Desc& ds = D[it.d];
   const Shape sh = ds.sh;
@@ -175,7 +182,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
   double* S = red + 32;                         // nlmax x (nlmax + 1)
   if (threadIdx.x == 0) bad = 0;
   Engine<EMU> eng;
-  eng.init(dsm, &mbar, &tmem_slot, &fail, rexp, cexp);
+  eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
   for (int t = threadIdx.x; t < nF; t += NT) {
     sx[t] = lf.xs[o0 + t];
     sy[t] = lf.ys[o0 + t];
@@ -196,6 +203,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
     if (l > 0) ok = eng.mma(acc, Hrow, Mr, 1, nF, Vanc, l * r, 1, r, l * r);
     if (!ok) break;
     if (row < nF)
+      #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int col = c0 + c;
         if (col < r) Hrow[(long)row * Mr + l * r + col] = cov0(cv, sx[row], sy[row], ax[col], ay[col]) - acc.v[c];
@@ -205,6 +213,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
     ok = eng.mma(acc, Hrow + l * r, Mr, 1, nF, st.Li[l] + a * (long)r * r, r, 1, r, r);
     if (!ok) break;
     if (row < nF)
+      #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int col = c0 + c;
         if (col < r) Hrow[(long)row * Mr + l * r + col] = acc.v[c];
@@ -219,6 +228,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
     if (M > 0) ok = eng.mma(acc, Hrow, Mr, 1, nF, Hrow + (long)ct * TC_N * Mr, Mr, 1, ncol, Mr);
     if (!ok) break;
     if (row < nF)
+      #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int col = c0 + c;
         if (col < ncol) {
@@ -256,6 +266,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
       ok = eng.mma(acc, S, lds, 1, nF, Hrow + l * r, 1, Mr, r, nF);
       if (!ok) break;
       if (row < nF)
+        #pragma unroll
         for (int c = 0; c < 32; ++c) {
           const int col = c0 + c;
           if (col < r) Hrow[(long)row * Mr + l * r + col] = acc.v[c];
@@ -279,10 +290,10 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
 __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict__ D, const int2* __restrict__ work,
                                                           int* status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
-  __shared__ int rexp[TC_M], cexp[TC_N];
+  __shared__ int rexp[EM_REXP], cexp[EM_CEXP];
   const Item it = work_item(work);
   const Desc& ds = D[it.d];
   const int M = ds.sh.M, r = ds.sh.r, Mr = M * r;
@@ -299,7 +310,7 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict
   const int K = (int)(row1 - row0);
   const double* Hb = lf.H + row0 * Mr;
   Engine<true> eng;
-  eng.init(dsm, &mbar, &tmem_slot, &fail, rexp, cexp);
+  eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
   TcAcc acc;
   acc.zero();
   const bool ok = eng.mma(acc, Hb + k * r, 1, Mr, r, Hb + l * r, 1, Mr, r, K);
@@ -307,6 +318,7 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict
   double* out = st.Acc[m] + (p * T + t) * (long)r * r;
   const int row = acc.row(), c0 = acc.col0();
   if (ok && row < r)
+    #pragma unroll
     for (int c = 0; c < 32; ++c)
       if (c0 + c < r) out[row * r + c0 + c] = acc.v[c];
   eng.release();
@@ -324,10 +336,10 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict
 __global__ void __launch_bounds__(NT) aggregate_kernel_em(int m, const Desc* __restrict__ D,
                                                           const int2* __restrict__ work, int* status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
-  __shared__ int rexp[TC_M], cexp[TC_N];
+  __shared__ int rexp[EM_REXP], cexp[EM_CEXP];
   const Item it = work_item(work);
   const Desc& ds = D[it.d];
   const int r = ds.sh.r, mr = m * r;
@@ -342,13 +354,14 @@ __global__ void __launch_bounds__(NT) aggregate_kernel_em(int m, const Desc* __r
   const long cf = st.cfirst[m - 1][p], cc = st.ccnt[m - 1][p];
   const double* Gb = st.G[m] + cf * (long)r * mr;
   Engine<true> eng;
-  eng.init(dsm, &mbar, &tmem_slot, &fail, rexp, cexp);
+  eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
   TcAcc acc;
   acc.zero();
   const bool ok = eng.mma(acc, Gb + k * r, 1, mr, r, Gb + l * r, 1, mr, r, (int)(cc * r));
   double* out = st.Acc[m - 1] + (p * Tp + t) * (long)r * r;
   const int row = acc.row(), c0 = acc.col0();
   if (ok && row < r)
+    #pragma unroll
     for (int c = 0; c < 32; ++c) {
       const int col = c0 + c;
       if (col < r) {
@@ -392,7 +405,7 @@ static size_t leaf_tc_smem(int nlmax) {
 }
 // Dynamic plus (an upper bound of) static shared memory of the leaf kernel.
 size_t leaf_tc_smem_bytes(int nlmax, int emu) {
-  return 1024 + (emu ? leaf_tc_smem<true>(nlmax) : leaf_tc_smem<false>(nlmax));
+  return emu ? 1024 + sizeof(int) * (EM_REXP + EM_CEXP) + leaf_tc_smem<true>(nlmax) : 1024 + leaf_tc_smem<false>(nlmax);
 }
 
 
