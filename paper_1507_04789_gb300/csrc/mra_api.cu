@@ -276,6 +276,7 @@ void single_plan(mra_handle* h) {
   p = mra::Plan();
   p.maxM = h->M;
   p.tile = mra::tile_for_r(h->r);
+  p.r = h->r;
   p.mixed = h->cfg.precision == MRA_PREC_MIXED ? 1 : (h->cfg.precision == MRA_PREC_EMU ? 2 : 0);
   p.nlmax = h->nlmax;
   for (int m = 0; m < h->M; ++m) {
@@ -891,6 +892,7 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
   p = mra::Plan();
   p.maxM = maxM;
   p.tile = mra::tile_for_r(h->r);
+  p.r = h->r;
   p.mixed = h->cfg.precision == MRA_PREC_MIXED ? 1 : (h->cfg.precision == MRA_PREC_EMU ? 2 : 0);
   p.nlmax = h->nlmax;
   int li = 0;

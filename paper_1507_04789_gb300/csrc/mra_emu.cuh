@@ -136,23 +136,30 @@ __device__ inline bool em_wait_buf(EmCtx& cx, int b) {
   return true;
 }
 
-// Largest exponent over the 8 K columns [8 kc, 8 kc + 8) of row i (-2000 if none).
+// Largest exponent over the 8 K columns [8 kc, 8 kc + 8) of row i (-2000 if
+// none), from the high words of the doubles only.
 __device__ __forceinline__ int em_item_exp(const double* X, long si, long sk, int n, int i, int kc, int K0, int KS) {
   int e = -2000;
   if (i < n) {
-    const double* p = X + (long)i * si + (long)(K0 + 8 * kc) * sk;
+    const unsigned* p = reinterpret_cast<const unsigned*>(X + (long)i * si + (long)(K0 + 8 * kc) * sk) + 1;
     const int kn = min(8, KS - 8 * kc);
+    unsigned w[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j)
-      if (j < kn) e = max(e, em_exp(p[(long)j * sk]));
+    for (int j = 0; j < 8; ++j) w[j] = j < kn ? p[2 * (long)j * sk] : 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int be = (int)((w[j] >> 20) & 0x7FFu);
+      if (be) e = max(e, be - 1022);
+    }
   }
   return e;
 }
 
 // Row scales of the groups of K columns [K0, K0 + KS), KS <= EM_MAXG * EM_KG:
-// rexp[g * TC_M + i] = max exponent of row i of A over group g (cexp for B).
-// Item = 8 consecutive K of one row; consecutive threads take consecutive rows;
-// four items per thread are loaded before their maxima are merged.
+// rexp[g * TC_M + i] = max exponent of row i < na of A over group g (cexp for
+// B, rows < nb).  Item = 8 consecutive K of one row; consecutive threads take
+// consecutive rows (rows padded to a power of two); four items per thread are
+// loaded before their maxima are merged.
 __device__ inline void em_scales(EmCtx& cx, const double* A, long sai, long sak, int na, const double* B, long sbj,
                                  long sbk, int nb, int K0, int KS) {
   __syncthreads();                                   // previous scales are no longer read
@@ -162,25 +169,29 @@ __device__ inline void em_scales(EmCtx& cx, const double* A, long sai, long sak,
     else cx.cexp[t - ng * TC_M] = -2000;
   }
   __syncthreads();
+  const int la = na <= 32 ? 5 : (na <= 64 ? 6 : 7), lb = nb <= 32 ? 5 : 6;   // log2 of padded rows
   const int ncore = (KS + 7) >> 3;
-  const int itemsA = TC_M * ncore, items = (TC_M + TC_N) * ncore;
+  const int itemsA = ncore << la, items = itemsA + (ncore << lb);
   for (int base = 0; base < items; base += 4 * NT) {
     int e[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int it = base + u * NT + threadIdx.x;
       e[u] = -2000;
-      if (it < itemsA) e[u] = em_item_exp(A, sai, sak, na, it % TC_M, it / TC_M, K0, KS);
-      else if (it < items) e[u] = em_item_exp(B, sbj, sbk, nb, (it - itemsA) % TC_N, (it - itemsA) / TC_N, K0, KS);
+      if (it < itemsA) e[u] = em_item_exp(A, sai, sak, na, it & ((1 << la) - 1), it >> la, K0, KS);
+      else if (it < items) {
+        const int jt = it - itemsA;
+        e[u] = em_item_exp(B, sbj, sbk, nb, jt & ((1 << lb) - 1), jt >> lb, K0, KS);
+      }
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int it = base + u * NT + threadIdx.x;
       if (e[u] <= -2000) continue;
-      if (it < itemsA) atomicMax(cx.rexp + ((8 * (it / TC_M)) / EM_KG) * TC_M + it % TC_M, e[u]);
+      if (it < itemsA) atomicMax(cx.rexp + ((8 * (it >> la)) / EM_KG) * TC_M + (it & ((1 << la) - 1)), e[u]);
       else {
         const int jt = it - itemsA;
-        atomicMax(cx.cexp + ((8 * (jt / TC_N)) / EM_KG) * TC_N + jt % TC_N, e[u]);
+        atomicMax(cx.cexp + ((8 * (jt >> lb)) / EM_KG) * TC_N + (jt & ((1 << lb) - 1)), e[u]);
       }
     }
   }
@@ -218,41 +229,45 @@ __device__ __forceinline__ uint32_t em_pack(float hi, float lo) {   // exact: sm
   return d;
 }
 
-// Split K columns [k0, k0 + kn) (kn <= EM_KC) of A and B into buffer b.
-// Item = one 16-byte core row (8 K) of one row; eight consecutive threads take
-// eight consecutive rows of one core column (128 contiguous bytes per plane).
+// Split K columns [k0, k0 + kn) (kn <= EM_KC) of rows i < na of A and j < nb of
+// B into buffer b.  Rows beyond na (nb) are left as they are: they only reach
+// output rows (columns) that the caller discards.  Item = one 16-byte core row
+// (8 K) of one row; eight consecutive threads take eight consecutive rows of
+// one core column (128 contiguous bytes per plane).
+__device__ __forceinline__ void em_stage_item(uint16_t* planes, int pstride, int e, const double* X, long si, long sk,
+                                              int n, int i, int kc, int k0, int kn) {
+  double x[8];
+  const double* p = X + (long)i * si + (long)(k0 + 8 * kc) * sk;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = (i < n && 8 * kc + j < kn) ? p[(long)j * sk] : 0.0;
+  uint32_t w[EM_S][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float f0[EM_S], f1[EM_S];
+    em_split(x[2 * q], e, f0);
+    em_split(x[2 * q + 1], e, f1);
+#pragma unroll
+    for (int s = 0; s < EM_S; ++s) w[s][q] = em_pack(f1[s], f0[s]);
+  }
+  const int off = em_cm(i, 8 * kc);
+#pragma unroll
+  for (int s = 0; s < EM_S; ++s)
+    *reinterpret_cast<uint4*>(planes + s * pstride + off) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+}
+
 __device__ inline void em_stage(EmCtx& cx, int b, int g, const double* A, long sai, long sak, int na,
                                 const double* B, long sbj, long sbk, int nb, int k0, int kn) {
   uint16_t* base = cx.stage + b * EM_BUF_HALFS;
-  constexpr int itemsA = TC_M * EM_CC, items = (TC_M + TC_N) * EM_CC;
+  const int ia = 2 * ((na + 7) & ~7), items = ia + 2 * ((nb + 7) & ~7);
   for (int it = threadIdx.x; it < items; it += NT) {
-    const bool isA = it < itemsA;
-    const int jt = isA ? it : it - itemsA;
-    const int rows8 = (isA ? TC_M : TC_N) >> 3;
-    const int i = (jt & 7) + 8 * ((jt >> 3) % rows8), kc = (jt >> 3) / rows8;
-    const double* X = isA ? A : B;
-    const long si = isA ? sai : sbj, sk = isA ? sak : sbk;
-    const int n = isA ? na : nb;
-    const int e = (isA ? cx.rexp + g * TC_M : cx.cexp + g * TC_N)[i];
-    double x[8];
-    const double* p = X + (long)i * si + (long)(k0 + 8 * kc) * sk;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) x[j] = (i < n && 8 * kc + j < kn) ? p[(long)j * sk] : 0.0;
-    uint32_t w[EM_S][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float f0[EM_S], f1[EM_S];
-      em_split(x[2 * q], e, f0);
-      em_split(x[2 * q + 1], e, f1);
-#pragma unroll
-      for (int s = 0; s < EM_S; ++s) w[s][q] = em_pack(f1[s], f0[s]);
+    if (it < ia) {
+      const int i = (it & 7) | ((it >> 4) << 3), kc = (it >> 3) & 1;
+      em_stage_item(base, EM_A_HALFS, cx.rexp[g * TC_M + i], A, sai, sak, na, i, kc, k0, kn);
+    } else {
+      const int jt = it - ia;
+      const int j = (jt & 7) | ((jt >> 4) << 3), kc = (jt >> 3) & 1;
+      em_stage_item(base + EM_S * EM_A_HALFS, EM_B_HALFS, cx.cexp[g * TC_N + j], B, sbj, sbk, nb, j, kc, k0, kn);
     }
-    uint16_t* planes = isA ? base : base + EM_S * EM_A_HALFS;
-    const int pstride = isA ? EM_A_HALFS : EM_B_HALFS;
-    const int off = em_cm(i, 8 * kc);
-#pragma unroll
-    for (int s = 0; s < EM_S; ++s)
-      *reinterpret_cast<uint4*>(planes + s * pstride + off) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
   }
 }
 
@@ -279,10 +294,13 @@ __device__ __forceinline__ void em_ld8(uint32_t taddr, uint32_t* r) {
 
 // Drain the group with row scale ei and column scales cexp[c0 + c] into the
 // running double-float sums (hi, lo) of this thread's 32 columns.
-__device__ inline void em_drain(EmCtx& cx, const int* cexp, int ei, int c0, float* hi, float* lo) {
-  const uint32_t lane_off = (uint32_t)((threadIdx.x >> 5) & 3) << 21;
+__device__ inline void em_drain(EmCtx& cx, const int* cexp, int ei, int c0, int na, int nb, float* hi, float* lo) {
+  const int wq = (threadIdx.x >> 5) & 3;
+  if (wq * 32 >= na) return;                         // warp-uniform: every row of this warp is discarded
+  const uint32_t lane_off = (uint32_t)wq << 21;
 #pragma unroll
   for (int cb = 0; cb < 32; cb += 8) {
+    if (c0 + cb >= nb) break;                        // warp-uniform
     uint32_t v[EM_S][8];
 #pragma unroll
     for (int t = 0; t < EM_S; ++t) em_ld8(cx.tmem + lane_off + (uint32_t)(t * TC_N + c0 + cb), v[t]);
@@ -349,7 +367,7 @@ __device__ inline bool em_mma(EmCtx& cx, TcAcc& acc, const double* A, long sai, 
       if ((kk + EM_KC) % EM_KG == 0 || kk + EM_KC >= KS) {   // group complete: drain it
         if (!em_wait_buf(cx, b ^ 1) || !em_wait_buf(cx, b)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        em_drain(cx, cx.cexp + g * TC_N, cx.rexp[g * TC_M + row], c0, hi, lo);
+        em_drain(cx, cx.cexp + g * TC_N, cx.rexp[g * TC_M + row], c0, na, nb, hi, lo);
         asm volatile("tcgen05.fence::before_thread_sync;");
       }
     }

@@ -43,6 +43,7 @@ cudaError_t launch_gather_y(const double* y, const int64_t* perm, int64_t n, dou
 // of the leaf Gram products.
 struct Plan {
   int maxM = 0, tile = 64, mixed = 0, nlmax = 1;   // mixed: 0 FP64, 1 3xTF32, 2 FP64 emulation
+  int r = 0;
   const int2* w_lvl[MAXL] = {};
   int n_lvl[MAXL] = {};
   const int2* w_agg[MAXL] = {};
@@ -68,9 +69,9 @@ cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nbl
 cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int emu, int* status,
                            cudaStream_t s);
 size_t leaf_tc_smem_bytes(int nlmax, int emu);
-cudaError_t launch_leaf_syrk_em(const Desc* d_desc, const int2* work, int nblocks, int ntiles, int* status,
+cudaError_t launch_leaf_syrk_em(const Desc* d_desc, const int2* work, int nblocks, int maxM, int r, int* status,
                                 cudaStream_t s);
-cudaError_t launch_aggregate_em(int m, const Desc* d_desc, const int2* work, int nblocks, int* status,
+cudaError_t launch_aggregate_em(int m, int r, const Desc* d_desc, const int2* work, int nblocks, int* status,
                                 cudaStream_t s);
 
 // Prediction (Sec. 3.4, Prop. 2) at points binned into ps.

@@ -488,7 +488,7 @@ cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaS
     dim3 grid(pl.n_syrk, pl.t_syrk);
     tm->start(2, s);
     if (pl.mixed == 2) {
-      if ((e = launch_leaf_syrk_em(d_desc, pl.w_syrk, pl.n_syrk, pl.t_syrk, status, s))) return e;
+      if ((e = launch_leaf_syrk_em(d_desc, pl.w_syrk, pl.n_syrk, pl.maxM, pl.r, status, s))) return e;
     } else {
       MRA_LAUNCH(tile, leaf_syrk_kernel, grid, syrk_smem(tile), s, d_desc, pl.w_syrk);
     }
@@ -507,7 +507,7 @@ cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaS
       dim3 g2(pl.n_agg[m], m * (m + 1) / 2);
       tm->start(4, s);
       if (pl.mixed == 2) {
-        if ((e = launch_aggregate_em(m, d_desc, pl.w_agg[m], pl.n_agg[m], status, s))) return e;
+        if ((e = launch_aggregate_em(m, pl.r, d_desc, pl.w_agg[m], pl.n_agg[m], status, s))) return e;
       } else {
         MRA_LAUNCH(tile, aggregate_kernel, g2, syrk_smem(tile), s, m, d_desc, pl.w_agg[m]);
       }

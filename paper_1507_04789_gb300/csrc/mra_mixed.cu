@@ -285,8 +285,33 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
 
 // ---------------------------------------------------------------------------
 // Gram products of the posterior pass on the emulation engine (MRA_PREC_EMU):
-// leaf_syrk and aggregate with the same tiles and sums as the FP64 kernels.
+// leaf_syrk and aggregate with the same sums as the FP64 kernels.  One tile
+// stacks up to S = 128 / r consecutive row blocks k0 .. k0 + S - 1 (all >= l)
+// against one column block l, so the 128 rows of the MMA carry S output blocks
+// and the column block is split once for all of them.
 // ---------------------------------------------------------------------------
+__host__ __device__ inline int em_stack(int r) { return r > 64 ? 1 : TC_M / r; }
+
+// Tiles of the packed lower blocks (k >= l, k, l < nblk) for stack height S.
+__host__ __device__ inline int em_tiles(int nblk, int S) {
+  int n = 0;
+  for (int l = 0; l < nblk; ++l) n += (nblk - l + S - 1) / S;
+  return n;
+}
+
+// Tile t -> column block l and first row block k0.
+__device__ inline bool em_tile(int t, int nblk, int S, int& l, int& k0) {
+  for (l = 0; l < nblk; ++l) {
+    const int nt = (nblk - l + S - 1) / S;
+    if (t < nt) {
+      k0 = l + t * S;
+      return true;
+    }
+    t -= nt;
+  }
+  return false;
+}
+
 __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict__ D, const int2* __restrict__ work,
                                                           int* status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
@@ -300,12 +325,11 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict
   const LevelState& st = ds.st;
   const LeafState& lf = ds.lf;
   const long p = it.i;
-  const int t = blockIdx.y;
-  if (t >= M * (M + 1) / 2) return;
+  const int S = em_stack(r);
+  int l, k0;
+  if (!em_tile(blockIdx.y, M, S, l, k0)) return;     // fewer tiles in a shallower dataset
+  const int nk = min(S, M - k0);                      // row blocks k0 .. k0 + nk - 1
   const long pm = st.mort[M - 1][p];
-  int k = 0;
-  while (tri_index(k + 1, 0) <= t) ++k;
-  const int l = t - tri_index(k, 0);
   const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
   const int K = (int)(row1 - row0);
   const double* Hb = lf.H + row0 * Mr;
@@ -313,20 +337,22 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict
   eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
   TcAcc acc;
   acc.zero();
-  const bool ok = eng.mma(acc, Hb + k * r, 1, Mr, r, Hb + l * r, 1, Mr, r, K);
+  const bool ok = eng.mma(acc, Hb + k0 * r, 1, Mr, nk * r, Hb + l * r, 1, Mr, r, K);
   const int m = M - 1, T = (m + 1) * (m + 2) / 2;
-  double* out = st.Acc[m] + (p * T + t) * (long)r * r;
   const int row = acc.row(), c0 = acc.col0();
-  if (ok && row < r)
-    #pragma unroll
+  if (ok && row < nk * r) {
+    const int k = k0 + row / r, ri = row % r;
+    double* out = st.Acc[m] + (p * T + tri_index(k, l)) * (long)r * r + (long)ri * r;
+#pragma unroll
     for (int c = 0; c < 32; ++c)
-      if (c0 + c < r) out[row * r + c0 + c] = acc.v[c];
+      if (c0 + c < r) out[c0 + c] = acc.v[c];
+  }
   eng.release();
-  if (k == l) {
-    double* om = st.Om[m] + (p * (m + 1) + k) * (long)r;
+  if (k0 == l) {
+    double* om = st.Om[m] + (p * (m + 1) + l) * (long)r;
     for (int a = threadIdx.x; a < r; a += NT) {
       double s = 0.0;
-      for (long o = 0; o < K; ++o) s = fma(Hb[o * Mr + k * r + a], lf.z[row0 + o], s);
+      for (long o = 0; o < K; ++o) s = fma(Hb[o * Mr + l * r + a], lf.z[row0 + o], s);
       om[a] = s;
     }
   }
@@ -345,11 +371,10 @@ __global__ void __launch_bounds__(NT) aggregate_kernel_em(int m, const Desc* __r
   const int r = ds.sh.r, mr = m * r;
   const LevelState& st = ds.st;
   const long p = it.i;
-  const int t = blockIdx.y;
-  if (t >= m * (m + 1) / 2) return;
-  int k = 0;
-  while (tri_index(k + 1, 0) <= t) ++k;
-  const int l = t - tri_index(k, 0);
+  const int S = em_stack(r);
+  int l, k0;
+  if (!em_tile(blockIdx.y, m, S, l, k0)) return;
+  const int nk = min(S, m - k0);
   const int Tc = (m + 1) * (m + 2) / 2, Tp = m * (m + 1) / 2;
   const long cf = st.cfirst[m - 1][p], cc = st.ccnt[m - 1][p];
   const double* Gb = st.G[m] + cf * (long)r * mr;
@@ -357,29 +382,31 @@ __global__ void __launch_bounds__(NT) aggregate_kernel_em(int m, const Desc* __r
   eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
   TcAcc acc;
   acc.zero();
-  const bool ok = eng.mma(acc, Gb + k * r, 1, mr, r, Gb + l * r, 1, mr, r, (int)(cc * r));
-  double* out = st.Acc[m - 1] + (p * Tp + t) * (long)r * r;
+  const bool ok = eng.mma(acc, Gb + k0 * r, 1, mr, nk * r, Gb + l * r, 1, mr, r, (int)(cc * r));
   const int row = acc.row(), c0 = acc.col0();
-  if (ok && row < r)
-    #pragma unroll
+  if (ok && row < nk * r) {
+    const int k = k0 + row / r, ri = row % r, t = tri_index(k, l);
+    double* out = st.Acc[m - 1] + (p * Tp + t) * (long)r * r + (long)ri * r;
+#pragma unroll
     for (int c = 0; c < 32; ++c) {
       const int col = c0 + c;
       if (col < r) {
         double s = -acc.v[c];
-        for (long ch = cf; ch < cf + cc; ++ch) s += st.Acc[m][(ch * Tc + t) * (long)r * r + row * r + col];
-        out[row * r + col] = s;
+        for (long ch = cf; ch < cf + cc; ++ch) s += st.Acc[m][(ch * Tc + t) * (long)r * r + (long)ri * r + col];
+        out[col] = s;
       }
     }
+  }
   eng.release();
-  if (k == l) {
-    double* om = st.Om[m - 1] + (p * m + k) * (long)r;
+  if (k0 == l) {
+    double* om = st.Om[m - 1] + (p * m + l) * (long)r;
     for (int a = threadIdx.x; a < r; a += NT) {
       double s = 0.0;
       for (long ci = cf; ci < cf + cc; ++ci) {
-        s += st.Om[m][(ci * (m + 1) + k) * (long)r + a];
+        s += st.Om[m][(ci * (m + 1) + l) * (long)r + a];
         const double* Gc = st.G[m] + ci * (long)r * mr;
         const double* gc = st.gv[m] + ci * r;
-        for (int q = 0; q < r; ++q) s = fma(-Gc[(long)q * mr + k * r + a], gc[q], s);
+        for (int q = 0; q < r; ++q) s = fma(-Gc[(long)q * mr + l * r + a], gc[q], s);
       }
       om[a] = s;
     }
@@ -441,21 +468,21 @@ cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_leaf_syrk_em(const Desc* d_desc, const int2* work, int nblocks, int ntiles, int* status,
+cudaError_t launch_leaf_syrk_em(const Desc* d_desc, const int2* work, int nblocks, int maxM, int r, int* status,
                                 cudaStream_t s) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(leaf_syrk_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
     return e;
-  leaf_syrk_kernel_em<<<dim3(nblocks, ntiles), NT, EM_SOLO_SMEM, s>>>(d_desc, work, status);
+  leaf_syrk_kernel_em<<<dim3(nblocks, em_tiles(maxM, em_stack(r))), NT, EM_SOLO_SMEM, s>>>(d_desc, work, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_aggregate_em(int m, const Desc* d_desc, const int2* work, int nblocks, int* status,
+cudaError_t launch_aggregate_em(int m, int r, const Desc* d_desc, const int2* work, int nblocks, int* status,
                                 cudaStream_t s) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(aggregate_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
     return e;
-  aggregate_kernel_em<<<dim3(nblocks, m * (m + 1) / 2), NT, EM_SOLO_SMEM, s>>>(m, d_desc, work, status);
+  aggregate_kernel_em<<<dim3(nblocks, em_tiles(m, em_stack(r))), NT, EM_SOLO_SMEM, s>>>(m, d_desc, work, status);
   return cudaGetLastError();
 }
 
