@@ -298,7 +298,7 @@ cudaError_t upload_desc(mra_handle* h, const mra_params* theta) {
   for (int k = 0; k < 4; ++k) h->hd.sh.bbox[k] = h->cfg.bbox[k];
   h->hd.sh.mixed = h->cfg.precision == MRA_PREC_MIXED ? 1 : (h->cfg.precision == MRA_PREC_EMU ? 2 : 0);
   if (theta) {
-    h->hd.cv = mra::Cov{theta->sigma2, theta->range, h->cfg.cov_family, h->cfg.nonstat};
+    h->hd.cv = mra::make_cov(theta->sigma2, theta->range, h->cfg.cov_family, h->cfg.nonstat);
     h->hd.tau2 = theta->tau2;
   }
   h->hd.nlmax = h->nlmax;
@@ -951,7 +951,7 @@ int batch_results(mra_handle* h, double* loglik_out) {
 int set_batch_params(mra_handle* h, const mra_params* thetas) {
   for (size_t d = 0; d < h->parts.size(); ++d) {
     if (!params_ok(&thetas[d])) return fail(MRA_ERR_ARG, "theta of dataset %zu is invalid", d);
-    h->h_descs[d].cv = mra::Cov{thetas[d].sigma2, thetas[d].range, h->parts[d]->cfg.cov_family, h->parts[d]->cfg.nonstat};
+    h->h_descs[d].cv = mra::make_cov(thetas[d].sigma2, thetas[d].range, h->parts[d]->cfg.cov_family, h->parts[d]->cfg.nonstat);
     h->h_descs[d].tau2 = thetas[d].tau2;
   }
   memcpy(h->pinned_descs, h->h_descs.data(), sizeof(mra::Desc) * h->parts.size());

@@ -34,13 +34,18 @@ struct Cov {
   double sigma2, kappa;
   int family;   // 0 exponential, 1 Matern-1.5
   int nonstat;
+  double ik;    // 1 / kappa (set by make_cov)
 };
+
+__host__ __device__ inline Cov make_cov(double sigma2, double kappa, int family, int nonstat) {
+  return Cov{sigma2, kappa, family, nonstat, 1.0 / kappa};
+}
 
 __device__ __forceinline__ double gvar(double x) { return 1.0 + 0.5 * sin(4.0 * PI * x); }
 
 __device__ __forceinline__ double cov0(const Cov& c, double x1, double y1, double x2, double y2) {
   double dx = x1 - x2, dy = y1 - y2;
-  double h = sqrt(dx * dx + dy * dy) / c.kappa;
+  double h = sqrt(dx * dx + dy * dy) * c.ik;
   double rho;
   if (c.family == 0) {
     rho = exp(-h);
@@ -158,25 +163,53 @@ __device__ void tile_mma(TileAcc<TILE>& acc, const double* A, long sai, long sak
 // Lower Cholesky factor in place (A = L L'); the strict upper triangle is set
 // to zero.  A non-positive (or NaN) pivot sets *bad and is replaced by 1 so
 // the factorisation stays finite.  Returns nothing; ends with __syncthreads.
+// Packed lower-triangle index t -> (i, k), k <= i, t = i (i + 1) / 2 + k.
+__device__ __forceinline__ void tri_decode(int t, int& i, int& k) {
+  int ii = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while (ii * (ii + 1) / 2 > t) --ii;
+  while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
+  i = ii;
+  k = t - ii * (ii + 1) / 2;
+}
+
 __device__ inline void chol_smem(double* A, int n, int lda, int* bad) {
+  // The pivot of column j (L_jj = d rsqrt(d), and rsqrt(d) to scale the
+  // column; long sequences on this chip's narrow FP64 pipe) is formed by
+  // thread 0 alone, right after it has
+  // applied the previous column's update to A_jj (element t = 0 of the
+  // trailing update is always its own), while the other threads update the
+  // rest of the trailing block.
+  __shared__ double piv;
+  __syncthreads();
+  if (threadIdx.x == 0 && n > 0) {
+    const double d = A[0];
+    const bool ok = d > 0.0;
+    const double rs = ok ? rsqrt(d) : 1.0;
+    if (!ok) *bad = 1;
+    A[0] = ok ? d * rs : 1.0;
+    piv = rs;
+  }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
-    double d = A[j * lda + j];
-    bool ok = d > 0.0;
-    double s = ok ? sqrt(d) : 1.0;
-    double inv = 1.0 / s;
-    if (!ok && threadIdx.x == 0) *bad = 1;
+    const double inv = piv;
     for (int i = j + 1 + threadIdx.x; i < n; i += NT) A[i * lda + j] *= inv;
-    __syncthreads();
-    int m = n - j - 1;
-    for (int t = threadIdx.x; t < m * m; t += NT) {
-      int ii = t / m, kk = t - ii * m;
-      if (kk <= ii) {
-        int i = j + 1 + ii, k = j + 1 + kk;
-        A[i * lda + k] = fma(-A[i * lda + j], A[k * lda + j], A[i * lda + k]);
+    __syncthreads();                       // column j scaled; piv read by every thread
+    const int m = n - j - 1;
+    for (int t = threadIdx.x; t < m * (m + 1) / 2; t += NT) {   // lower triangle of the trailing block
+      int ii, kk;
+      tri_decode(t, ii, kk);
+      const int i = j + 1 + ii, k = j + 1 + kk;
+      const double v = fma(-A[i * lda + j], A[k * lda + j], A[i * lda + k]);
+      if (t == 0) {                        // A_{j+1,j+1}: the next pivot
+        const bool ok = v > 0.0;
+        const double rs = ok ? rsqrt(v) : 1.0;
+        if (!ok) *bad = 1;
+        A[i * lda + k] = ok ? v * rs : 1.0;
+        piv = rs;
+      } else {
+        A[i * lda + k] = v;
       }
     }
-    if (threadIdx.x == 0) A[j * lda + j] = s;
     __syncthreads();
   }
   for (int t = threadIdx.x; t < n * n; t += NT) {
@@ -186,20 +219,31 @@ __device__ inline void chol_smem(double* A, int n, int lda, int* bad) {
   __syncthreads();
 }
 
-// Lower-triangular L in place -> L^{-1} (column sweep from the last column,
-// as in LAPACK's unblocked trti2).  tmp: n doubles of shared scratch.
+// Lower-triangular L in place -> L^{-1}, by forward substitution on the rows
+// of the identity (right-looking): step k scales row k by 1 / L_kk and
+// subtracts L_ik times it from every row i > k.  Each step is a rank-1 update
+// over all threads, so the FP64 work is spread over every warp (the pipe of
+// every SM sub-partition).  tmp: n doubles of shared scratch.
 __device__ inline void trinv_smem(double* A, int n, int lda, double* tmp) {
+  __shared__ double piv;
   __syncthreads();
-  for (int j = n - 1; j >= 0; --j) {
-    double ajj = 1.0 / A[j * lda + j];
-    for (int i = j + 1 + threadIdx.x; i < n; i += NT) tmp[i] = A[i * lda + j];
+  if (threadIdx.x == 0 && n > 0) piv = 1.0 / A[0];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    // phase 1: row k of X (columns < k) scaled by 1 / L_kk, X_kk = 1 / L_kk;
+    // column k of L below the diagonal saved before it is overwritten
+    const double rk = piv;
+    for (int t = threadIdx.x; t <= k; t += NT) A[k * lda + t] = t < k ? A[k * lda + t] * rk : rk;
+    for (int i = k + 1 + threadIdx.x; i < n; i += NT) tmp[i] = A[i * lda + k];
     __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < n; i += NT) {
-      double s = 0.0;
-      for (int k = j + 1; k <= i; ++k) s = fma(A[i * lda + k], tmp[k], s);
-      A[i * lda + j] = -ajj * s;
+    if (threadIdx.x == 0 && k + 1 < n) piv = 1.0 / A[(k + 1) * lda + k + 1];   // next step's reciprocal
+    // phase 2: X_ij -= L_ik X_kj for i > k, j <= k (X_ik starts from 0)
+    const int w = k + 1, nr = n - k - 1;
+    for (int t = threadIdx.x; t < nr * w; t += NT) {
+      const int ii = t / w, j = t - ii * w, i = k + 1 + ii;
+      const double x0 = j == k ? 0.0 : A[i * lda + j];
+      A[i * lda + j] = fma(-tmp[i], A[k * lda + j], x0);
     }
-    if (threadIdx.x == 0) A[j * lda + j] = ajj;
     __syncthreads();
   }
 }

@@ -78,9 +78,7 @@ struct EmCtx {
   int* cexp;         // EM_CEXP row scales of B
   uint64_t* mbar;    // two mbarriers, one per staging buffer
   uint32_t tmem;
-  uint32_t phase;    // bit b: parity of the next completion of mbar[b]
-  uint32_t pending;  // bit b: MMAs committed to mbar[b] and not yet waited for
-  int buf;           // buffer the next chunk is staged into
+  uint32_t phase;    // bit b: parity of the next completion of mbar[b] (tracked by warp 0)
   int* fail;
 };
 
@@ -101,8 +99,6 @@ __device__ inline void em_init(EmCtx& cx, uint32_t* tmem_slot) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   cx.tmem = *tmem_slot;
   cx.phase = 0;
-  cx.pending = 0;
-  cx.buf = 0;
 }
 
 __device__ inline void em_release(EmCtx& cx) {
@@ -112,47 +108,13 @@ __device__ inline void em_release(EmCtx& cx) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(cx.tmem), "r"(EM_TMEM_COLS));
 }
 
-// Wait (bounded, every thread) for the MMAs committed to buffer b; false
-// (uniformly) on timeout, after one more bounded wait for what is in flight.
+// Wait (bounded) for the MMAs committed to buffer b; flips b's phase once they
+// completed.  Called by warp 0 only, which alone tracks the phases.
 __device__ __forceinline__ bool em_poll(EmCtx& cx, int b) {
   uint32_t ph = (cx.phase >> b) & 1u;
   const bool done = tc_wait_phase(cx.mbar + b, ph);
   if (done) cx.phase ^= 1u << b;
   return done;
-}
-
-__device__ inline bool em_wait_buf(EmCtx& cx, int b) {
-  if (!((cx.pending >> b) & 1u)) return true;
-  const bool done = em_poll(cx, b);
-  if (__syncthreads_or(!done)) {
-    if (threadIdx.x == 0) *cx.fail = 1;
-    for (int q = 0; q < 2; ++q)
-      if ((cx.pending >> q) & 1u) em_poll(cx, q);
-    cx.pending = 0;
-    __syncthreads();
-    return false;
-  }
-  cx.pending &= ~(1u << b);
-  return true;
-}
-
-// Largest exponent over the 8 K columns [8 kc, 8 kc + 8) of row i (-2000 if
-// none), from the high words of the doubles only.
-__device__ __forceinline__ int em_item_exp(const double* X, long si, long sk, int n, int i, int kc, int K0, int KS) {
-  int e = -2000;
-  if (i < n) {
-    const unsigned* p = reinterpret_cast<const unsigned*>(X + (long)i * si + (long)(K0 + 8 * kc) * sk) + 1;
-    const int kn = min(8, KS - 8 * kc);
-    unsigned w[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) w[j] = j < kn ? p[2 * (long)j * sk] : 0u;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int be = (int)((w[j] >> 20) & 0x7FFu);
-      if (be) e = max(e, be - 1022);
-    }
-  }
-  return e;
 }
 
 // Row scales of the groups of K columns [K0, K0 + KS), KS <= EM_MAXG * EM_KG:
@@ -173,26 +135,40 @@ __device__ inline void em_scales(EmCtx& cx, const double* A, long sai, long sak,
   const int ncore = (KS + 7) >> 3;
   const int itemsA = ncore << la, items = itemsA + (ncore << lb);
   for (int base = 0; base < items; base += 4 * NT) {
-    int e[4];
+    // item -> (operand, row, core column), without branches, so that the 32
+    // high-word loads of the four items are all in flight together
+    const unsigned* ptr[4];
+    long sk2[4];
+    int kn[4], slot[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int it = base + u * NT + threadIdx.x;
-      e[u] = -2000;
-      if (it < itemsA) e[u] = em_item_exp(A, sai, sak, na, it & ((1 << la) - 1), it >> la, K0, KS);
-      else if (it < items) {
-        const int jt = it - itemsA;
-        e[u] = em_item_exp(B, sbj, sbk, nb, jt & ((1 << lb) - 1), jt >> lb, K0, KS);
-      }
+      const bool isA = it < itemsA;
+      const int jt = isA ? it : it - itemsA;
+      const int lg = isA ? la : lb;
+      const int i = jt & ((1 << lg) - 1), kc = jt >> lg;
+      const bool valid = it < items && i < (isA ? na : nb);
+      const double* X = isA ? A : B;
+      const long si = isA ? sai : sbj, sk = isA ? sak : sbk;
+      ptr[u] = reinterpret_cast<const unsigned*>(X + (long)i * si + (long)(K0 + 8 * kc) * sk) + 1;
+      sk2[u] = 2 * sk;
+      kn[u] = valid ? min(8, KS - 8 * kc) : 0;
+      slot[u] = (isA ? ((8 * kc) / EM_KG) * TC_M : EM_REXP + ((8 * kc) / EM_KG) * TC_N) + i;
     }
+    unsigned w[4][8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[u][j] = j < kn[u] ? ptr[u][j * sk2[u]] : 0u;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int it = base + u * NT + threadIdx.x;
-      if (e[u] <= -2000) continue;
-      if (it < itemsA) atomicMax(cx.rexp + ((8 * (it >> la)) / EM_KG) * TC_M + (it & ((1 << la) - 1)), e[u]);
-      else {
-        const int jt = it - itemsA;
-        atomicMax(cx.cexp + ((8 * (jt >> lb)) / EM_KG) * TC_N + (jt & ((1 << lb) - 1)), e[u]);
+      int e = -2000;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int be = (int)((w[u][j] >> 20) & 0x7FFu);
+        if (be) e = max(e, be - 1022);
       }
+      if (e > -2000) atomicMax(slot[u] < EM_REXP ? cx.rexp + slot[u] : cx.cexp + (slot[u] - EM_REXP), e);
     }
   }
   __syncthreads();
@@ -229,45 +205,60 @@ __device__ __forceinline__ uint32_t em_pack(float hi, float lo) {   // exact: sm
   return d;
 }
 
-// Split K columns [k0, k0 + kn) (kn <= EM_KC) of rows i < na of A and j < nb of
-// B into buffer b.  Rows beyond na (nb) are left as they are: they only reach
-// output rows (columns) that the caller discards.  Item = one 16-byte core row
-// (8 K) of one row; eight consecutive threads take eight consecutive rows of
-// one core column (128 contiguous bytes per plane).
-__device__ __forceinline__ void em_stage_item(uint16_t* planes, int pstride, int e, const double* X, long si, long sk,
-                                              int n, int i, int kc, int k0, int kn) {
-  double x[8];
-  const double* p = X + (long)i * si + (long)(k0 + 8 * kc) * sk;
+// The 7 slice planes of 4 consecutive K of row i, as bf16 pairs, into planes.
+__device__ __forceinline__ void em_split_store(uint16_t* planes, int pstride, int e, const double* x, int i, int k4) {
+  uint32_t w[EM_S][2];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) x[j] = (i < n && 8 * kc + j < kn) ? p[(long)j * sk] : 0.0;
-  uint32_t w[EM_S][4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < 2; ++q) {
     float f0[EM_S], f1[EM_S];
     em_split(x[2 * q], e, f0);
     em_split(x[2 * q + 1], e, f1);
 #pragma unroll
     for (int s = 0; s < EM_S; ++s) w[s][q] = em_pack(f1[s], f0[s]);
   }
-  const int off = em_cm(i, 8 * kc);
+  const int off = em_cm(i, 4 * k4);
 #pragma unroll
-  for (int s = 0; s < EM_S; ++s)
-    *reinterpret_cast<uint4*>(planes + s * pstride + off) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+  for (int s = 0; s < EM_S; ++s) *reinterpret_cast<uint2*>(planes + s * pstride + off) = make_uint2(w[s][0], w[s][1]);
 }
 
+constexpr int EM_MAX_ITEMS = (4 * (TC_M + TC_N) + NT - 32 - 1) / (NT - 32);   // per staging thread
+
+// Split K columns [k0, k0 + kn) (kn <= EM_KC) of rows i < na of A and j < nb of
+// B into buffer b.  Rows beyond na (nb) are left as they are: they only reach
+// output rows (columns) that the caller discards.  Item = half a 16-byte core
+// row (4 K) of one row; the 32 lanes of a warp cover 8 rows x 2 core columns
+// x 2 halves, i.e. 256 contiguous bytes per plane.  Warp 0 issues the MMAs of
+// the previous chunk meanwhile, so the items go to warps 1..7.
 __device__ inline void em_stage(EmCtx& cx, int b, int g, const double* A, long sai, long sak, int na,
                                 const double* B, long sbj, long sbk, int nb, int k0, int kn) {
+  if (threadIdx.x < 32) return;
   uint16_t* base = cx.stage + b * EM_BUF_HALFS;
-  const int ia = 2 * ((na + 7) & ~7), items = ia + 2 * ((nb + 7) & ~7);
-  for (int it = threadIdx.x; it < items; it += NT) {
-    if (it < ia) {
-      const int i = (it & 7) | ((it >> 4) << 3), kc = (it >> 3) & 1;
-      em_stage_item(base, EM_A_HALFS, cx.rexp[g * TC_M + i], A, sai, sak, na, i, kc, k0, kn);
-    } else {
-      const int jt = it - ia;
-      const int j = (jt & 7) | ((jt >> 4) << 3), kc = (jt >> 3) & 1;
-      em_stage_item(base + EM_S * EM_A_HALFS, EM_B_HALFS, cx.cexp[g * TC_N + j], B, sbj, sbk, nb, j, kc, k0, kn);
-    }
+  const int ia = 4 * ((na + 7) & ~7), items = ia + 4 * ((nb + 7) & ~7);
+  // every load of this thread's items first, so that one memory latency
+  // covers the chunk; then the splits
+  double x[EM_MAX_ITEMS][4];
+#pragma unroll
+  for (int u = 0; u < EM_MAX_ITEMS; ++u) {
+    const int it = threadIdx.x - 32 + u * (NT - 32);
+    const bool isA = it < ia;
+    const int jt = isA ? it : it - ia;
+    const int i = ((jt >> 1) & 7) | ((jt >> 5) << 3), k4 = ((jt >> 4) & 1) * 2 + (jt & 1);
+    const double* X = isA ? A : B;
+    const long si = isA ? sai : sbj, sk = isA ? sak : sbk;
+    const bool ok = it < items && i < (isA ? na : nb);
+    const double* p = X + (long)i * si + (long)(k0 + 4 * k4) * sk;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) x[u][j] = (ok && 4 * k4 + j < kn) ? p[(long)j * sk] : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < EM_MAX_ITEMS; ++u) {
+    const int it = threadIdx.x - 32 + u * (NT - 32);
+    if (it >= items) break;
+    const bool isA = it < ia;
+    const int jt = isA ? it : it - ia;
+    const int i = ((jt >> 1) & 7) | ((jt >> 5) << 3), k4 = ((jt >> 4) & 1) * 2 + (jt & 1);
+    if (isA) em_split_store(base, EM_A_HALFS, cx.rexp[g * TC_M + i], x[u], i, k4);
+    else em_split_store(base + EM_S * EM_A_HALFS, EM_B_HALFS, cx.cexp[g * TC_N + i], x[u], i, k4);
   }
 }
 
@@ -325,8 +316,33 @@ __device__ inline void em_drain(EmCtx& cx, const int* cexp, int ei, int c0, int 
   }
 }
 
+// Issue the 28 slice-pair MMAs of one staged chunk (lane 0 of warp 0).
+__device__ __forceinline__ void em_issue_chunk(const EmCtx& cx, int b, bool gfirst) {
+  // plane descriptors differ only in the start-address field (addr >> 4, 14 bits; shared memory
+  // addresses stay below 2^18, so the offsets below never carry out of the field)
+  const uint16_t* aP = cx.stage + b * EM_BUF_HALFS;
+  const uint64_t da0 = em_desc(smem_addr(aP)), db0 = em_desc(smem_addr(aP + EM_S * EM_A_HALFS));
+#pragma unroll
+  for (int t = 2; t <= EM_S + 1; ++t) {
+    const uint32_t dt = cx.tmem + (uint32_t)(t - 2) * TC_N;
+#pragma unroll
+    for (int p = 1; p < t; ++p) {                 // q = t - p in [1, 7] since t <= 8
+      const uint64_t da = da0 + (uint64_t)(((p - 1) * EM_A_HALFS * 2) >> 4);
+      const uint64_t db = db0 + (uint64_t)(((t - p - 1) * EM_B_HALFS * 2) >> 4);
+      em_issue(dt, da, db, (gfirst && p == 1) ? 0u : 1u);
+    }
+  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      smem_addr(cx.mbar + b)));
+}
+
 // acc(i, j) += sum_k A(i, k) B(j, k) with FP64-grade accuracy, i < na <= 128,
 // j < nb <= 64.  Returns false (uniformly) if a tensor-core wait timed out.
+//
+// Software pipeline over the 16-column chunks of each scale pass: in step c,
+// warps 1..7 split chunk c into buffer c & 1 while warp 0 issues the MMAs of
+// chunk c - 1 (buffer (c - 1) & 1) and waits for them; the barrier that ends
+// the step therefore leaves buffer c & 1 staged and buffer (c - 1) & 1 free.
 __device__ inline bool em_mma(EmCtx& cx, TcAcc& acc, const double* A, long sai, long sak, int na, const double* B,
                               long sbj, long sbk, int nb, int K) {
   const int row = acc.row(), c0 = acc.col0();
@@ -336,39 +352,35 @@ __device__ inline bool em_mma(EmCtx& cx, TcAcc& acc, const double* A, long sai, 
   for (int K0 = 0; K0 < K; K0 += EM_MAXG * EM_KG) {
     const int KS = min(EM_MAXG * EM_KG, K - K0);
     em_scales(cx, A, sai, sak, na, B, sbj, sbk, nb, K0, KS);
-    for (int kk = 0; kk < KS; kk += EM_KC) {
-      const int b = cx.buf;
-      if (!em_wait_buf(cx, b)) return false;          // the MMAs of two chunks ago released buffer b
-      const int g = kk / EM_KG;
-      em_stage(cx, b, g, A, sai, sak, na, B, sbj, sbk, nb, K0 + kk, min(EM_KC, KS - kk));
-      asm volatile("fence.proxy.async.shared::cta;");
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      if (threadIdx.x == 0) {
-        const uint16_t* aP = cx.stage + b * EM_BUF_HALFS;
-        const uint16_t* bP = aP + EM_S * EM_A_HALFS;
-        const bool gfirst = (kk % EM_KG) == 0;
-#pragma unroll
-        for (int t = 2; t <= EM_S + 1; ++t) {
-          const uint32_t dt = cx.tmem + (uint32_t)(t - 2) * TC_N;
-#pragma unroll
-          for (int p = 1; p < t; ++p) {                 // q = t - p in [1, 7] since t <= 8
-            const uint64_t da = em_desc(smem_addr(aP + (p - 1) * EM_A_HALFS));
-            const uint64_t db = em_desc(smem_addr(bP + (t - p - 1) * EM_B_HALFS));
-            em_issue(dt, da, db, (gfirst && p == 1) ? 0u : 1u);
-          }
+    const int nch = (KS + EM_KC - 1) / EM_KC;
+    for (int c = 0; c <= nch; ++c) {
+      bool done = true;
+      if (threadIdx.x < 32) {
+        if (c > 0) {
+          if (threadIdx.x == 0) em_issue_chunk(cx, (c - 1) & 1, ((c - 1) * EM_KC) % EM_KG == 0);
+          __syncwarp();
+          done = em_poll(cx, (c - 1) & 1);
+          asm volatile("tcgen05.fence::before_thread_sync;");
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_addr(cx.mbar + b)));
+      } else if (c < nch) {
+        em_stage(cx, c & 1, (c * EM_KC) / EM_KG, A, sai, sak, na, B, sbj, sbk, nb, K0 + c * EM_KC,
+                 min(EM_KC, KS - c * EM_KC));
+        asm volatile("fence.proxy.async.shared::cta;");
       }
-      cx.pending |= 1u << b;
-      cx.buf ^= 1;
-      if ((kk + EM_KC) % EM_KG == 0 || kk + EM_KC >= KS) {   // group complete: drain it
-        if (!em_wait_buf(cx, b ^ 1) || !em_wait_buf(cx, b)) return false;
-        asm volatile("tcgen05.fence::after_thread_sync;");
+      if (__syncthreads_or(!done)) {                     // uniform: every thread leaves
+        if (threadIdx.x == 0) *cx.fail = 1;
+        if (threadIdx.x < 32) em_poll(cx, (c - 1) & 1);  // one more bounded wait for the MMAs in flight
+        __syncthreads();
+        return false;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int last = (c - 1) * EM_KC;                   // first column of the chunk whose MMAs completed
+      if (c > 0 && ((last + EM_KC) % EM_KG == 0 || last + EM_KC >= KS)) {   // its group is complete
+        const int g = last / EM_KG;
         em_drain(cx, cx.cexp + g * TC_N, cx.rexp[g * TC_M + row], c0, na, nb, hi, lo);
         asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();                                  // accumulators are read before the next group's MMAs
+        asm volatile("tcgen05.fence::after_thread_sync;");
       }
     }
   }

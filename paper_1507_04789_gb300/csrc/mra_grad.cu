@@ -35,7 +35,7 @@ namespace mra {
 __device__ __forceinline__ void dcov0(const Cov& c, double x1, double y1, double x2, double y2, double& ds2,
                                       double& dk) {
   double dx = x1 - x2, dy = y1 - y2;
-  double h = sqrt(dx * dx + dy * dy) / c.kappa;
+  double h = sqrt(dx * dx + dy * dy) * c.ik;
   double rho, drho;   // rho(h/kappa) and kappa * d rho / d kappa
   if (c.family == 0) {
     rho = exp(-h);
@@ -48,7 +48,7 @@ __device__ __forceinline__ void dcov0(const Cov& c, double x1, double y1, double
   }
   double gg = c.nonstat ? sqrt(gvar(x1) * gvar(x2)) : 1.0;
   ds2 = rho * gg;
-  dk = c.sigma2 * drho * gg / c.kappa;
+  dk = c.sigma2 * drho * gg * c.ik;
 }
 
 // Symmetric adjoint block (k, l) of region chain `anc` (ancestor index per

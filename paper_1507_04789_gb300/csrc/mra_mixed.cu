@@ -95,16 +95,25 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
     __syncthreads();
     load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
     const double* Vanc = st.V[l] + a * (long)r * (l * r);
+    __syncthreads();
+    // C0(Q_R, Q_{R_l}) into block l, spread over every warp (the FP64 pipe of
+    // every SM sub-partition); the product below reads only blocks < l
+    for (int t = threadIdx.x; t < r * r; t += NT) {
+      const int qi = t / r, qj = t - qi * r;
+      Vrow[(long)qi * mr + l * r + qj] = cov0(cv, qx[qi], qy[qi], ax[qj], ay[qj]);
+    }
     acc.zero();
     __syncthreads();
-    if (l > 0) ok = eng.mma(acc, Vrow, mr, 1, r, Vanc, l * r, 1, r, l * r);
-    if (!ok) break;
-    if (row < r)
-      #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        const int col = c0 + c;
-        if (col < r) Vrow[(long)row * mr + l * r + col] = cov0(cv, qx[row], qy[row], ax[col], ay[col]) - acc.v[c];
-      }
+    if (l > 0) {
+      ok = eng.mma(acc, Vrow, mr, 1, r, Vanc, l * r, 1, r, l * r);
+      if (!ok) break;
+      if (row < r)
+        #pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int col = c0 + c;
+          if (col < r) Vrow[(long)row * mr + l * r + col] -= acc.v[c];
+        }
+    }
     __syncthreads();
     acc.zero();
     ok = eng.mma(acc, Vrow + l * r, mr, 1, r, st.Li[l] + a * (long)r * r, r, 1, r, r);
@@ -116,18 +125,25 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
         if (col < r) Vrow[(long)row * mr + l * r + col] = acc.v[c];
       }
   }
+  __syncthreads();                             // knots loaded, chain blocks written
+  const int ldw = r + 1;
+  // lower triangle of C0(Q_R, Q_R), every warp
+  for (int t = threadIdx.x; t < r * (r + 1) / 2; t += NT) {
+    int qi, qj;
+    tri_decode(t, qi, qj);
+    W[qi * ldw + qj] = cov0(cv, qx[qi], qy[qi], qx[qj], qy[qj]);
+  }
   __syncthreads();
   if (ok) {
     acc.zero();
     if (m > 0) ok = eng.mma(acc, Vrow, mr, 1, r, Vrow, mr, 1, r, mr);
   }
   if (ok) {
-    const int ldw = r + 1;
-    if (row < r)
+    if (m > 0 && row < r)
       #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int col = c0 + c;
-        if (col < r) W[row * ldw + col] = cov0(cv, qx[row], qy[row], qx[col], qy[col]) - acc.v[c];
+        if (col <= row) W[row * ldw + col] -= acc.v[c];
       }
     chol_smem(W, r, ldw, &bad);
     if (st.L[m]) {
@@ -198,16 +214,25 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
     __syncthreads();
     load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
     const double* Vanc = st.V[l] + a * (long)r * (l * r);
+    __syncthreads();
+    // C0(S_F, Q_l) into block l, spread over every warp; the product below
+    // reads only blocks < l
+    for (int t = threadIdx.x; t < nF * r; t += NT) {
+      const int fi = t / r, qj = t - fi * r;
+      Hrow[(long)fi * Mr + l * r + qj] = cov0(cv, sx[fi], sy[fi], ax[qj], ay[qj]);
+    }
     acc.zero();
     __syncthreads();
-    if (l > 0) ok = eng.mma(acc, Hrow, Mr, 1, nF, Vanc, l * r, 1, r, l * r);
-    if (!ok) break;
-    if (row < nF)
-      #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        const int col = c0 + c;
-        if (col < r) Hrow[(long)row * Mr + l * r + col] = cov0(cv, sx[row], sy[row], ax[col], ay[col]) - acc.v[c];
-      }
+    if (l > 0) {
+      ok = eng.mma(acc, Hrow, Mr, 1, nF, Vanc, l * r, 1, r, l * r);
+      if (!ok) break;
+      if (row < nF)
+        #pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int col = c0 + c;
+          if (col < r) Hrow[(long)row * Mr + l * r + col] -= acc.v[c];
+        }
+    }
     __syncthreads();
     acc.zero();
     ok = eng.mma(acc, Hrow + l * r, Mr, 1, nF, st.Li[l] + a * (long)r * r, r, 1, r, r);
@@ -219,24 +244,26 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
         if (col < r) Hrow[(long)row * Mr + l * r + col] = acc.v[c];
       }
   }
+  __syncthreads();                             // points loaded, chain blocks written
+  // Sigma_F = C0(S_F, S_F) - V_F V_F' + tau2 I (lower triangle), the
+  // covariance by every warp first, then the product 64 columns at a time
+  for (int t = threadIdx.x; t < nF * (nF + 1) / 2; t += NT) {
+    int fi, fj;
+    tri_decode(t, fi, fj);
+    S[fi * lds + fj] = cov0(cv, sx[fi], sy[fi], sx[fj], sy[fj]) + (fi == fj ? tau2 : 0.0);
+  }
   __syncthreads();
-  // Sigma_F = C0(S_F, S_F) - V_F V_F' + tau2 I, 64 columns at a time
   const int nct = (nF + TC_N - 1) / TC_N;
-  for (int ct = 0; ct < nct && ok; ++ct) {
+  for (int ct = 0; ct < nct && ok && M > 0; ++ct) {
     const int ncol = min(TC_N, nF - ct * TC_N);
     acc.zero();
-    if (M > 0) ok = eng.mma(acc, Hrow, Mr, 1, nF, Hrow + (long)ct * TC_N * Mr, Mr, 1, ncol, Mr);
+    ok = eng.mma(acc, Hrow, Mr, 1, nF, Hrow + (long)ct * TC_N * Mr, Mr, 1, ncol, Mr);
     if (!ok) break;
     if (row < nF)
       #pragma unroll
       for (int c = 0; c < 32; ++c) {
-        const int col = c0 + c;
-        if (col < ncol) {
-          const int oj = ct * TC_N + col;
-          double v = cov0(cv, sx[row], sy[row], sx[oj], sy[oj]) - acc.v[c];
-          if (row == oj) v += tau2;
-          S[row * lds + oj] = v;
-        }
+        const int oj = ct * TC_N + c0 + c;
+        if (c0 + c < ncol && oj <= row) S[row * lds + oj] -= acc.v[c];
       }
   }
   double ld = 0.0, zz = 0.0;

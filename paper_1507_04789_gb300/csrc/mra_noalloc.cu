@@ -211,7 +211,7 @@ extern "C" int mra_loglik_noalloc(const mra_config* cfg, const mra_params* theta
   sh.mixed = 0;
   mra::Desc hd{};
   hd.sh = sh;
-  hd.cv = mra::Cov{theta->sigma2, theta->range, cfg->cov_family, cfg->nonstat};
+  hd.cv = mra::make_cov(theta->sigma2, theta->range, cfg->cov_family, cfg->nonstat);
   hd.tau2 = theta->tau2;
   hd.nlmax = nlmax;
   hd.st = st;
