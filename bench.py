@@ -123,6 +123,33 @@ def contraction_flops(M: int, r: int, nF, precision: str):
     return out
 
 
+# DRAM bytes per launch of a dominant kernel, from one ncu capture, valid only
+# while the kernel's sources are the ones it was taken from (else null).
+TRAFFIC = {
+    ("emu", "leaf", "n1M_matern15_M7_r64"): {
+        "bytes": 5.50e9,
+        "how": "dram__bytes_read.sum + dram__bytes_write.sum of leaf_kernel_tc<1> at n = 2^18, M = 6 "
+               "(1.18 GB, profiles/leaf_kernel_tc_emu_n256k.md) scaled by n M r to n = 2^20, M = 7",
+        "sources": ["mra_mixed.cu", "mra_emu.cuh", "mra_tc.cuh", "mra_device.cuh", "mra_kernels.cuh"],
+        "sha1": "b95245e5f2c736b0e4e60d7dc8e750b9df4dda15",
+    },
+}
+
+
+def kernel_traffic(form: str, kernel: str, workload: str):
+    import hashlib
+    t = TRAFFIC.get((form, kernel, workload))
+    if t is None:
+        return None, None
+    h = hashlib.sha1()
+    for f in t["sources"]:
+        with open(os.path.join(ROOT, "paper_1507_04789_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != t["sha1"]:
+        return None, "kernel sources changed since the ncu capture"
+    return t["bytes"], t["how"]
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -455,6 +482,10 @@ def main():
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dom,
                     "peak_source": "nominal FP64 pipe (recipe); DFMA loop measured 1.19 TFLOP/s at 1995 MHz"}
+    traffic, how = kernel_traffic(best, dom, w.name)
+    roofline["traffic"] = traffic
+    if how:
+        roofline["traffic_source"] = how
     roofline.update({"launches_per_step": dom_n / args.steps, "kernels": kernel_table(best),
                      "step_fp64_alg_tflops": total_flops / (head["ms_per_step"] * 1e-3) / 1e12})
 
