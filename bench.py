@@ -417,24 +417,32 @@ def main():
             handles[prec].close()
     h64 = handles["fp64"]
 
-    # ---- gradient (FP64 adjoint) ----
-    g_steps = max(2, args.steps // 2)
-    h64.loglik_grad(theta0)
-    h64.enable_timing(True)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(g_steps):
-        ll_g, grad = h64.loglik_grad(thetas[k])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    g_ms = max_over_ranks(e0.elapsed_time(e1)) / g_steps
-    g_kt = h64.kernel_times()
-    h64.enable_timing(False)
-    gradient = {"value": world * 1e3 / g_ms, "unit": "evals/s", "ms_per_step": g_ms,
-                "what": "loglik + d/d(sigma2, range, tau2), FP64 reverse-mode adjoint",
+    # ---- loglik + gradient: forward in the emulated and in the FP64 form, FP64 adjoint ----
+    def time_grad(h):
+        g_steps = max(2, args.steps // 2)
+        h.loglik_grad(theta0)
+        h.enable_timing(True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(g_steps):
+            ll_g, grad = h.loglik_grad(thetas[k])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        g_ms = max_over_ranks(e0.elapsed_time(e1)) / g_steps
+        g_kt = h.kernel_times()
+        h.enable_timing(False)
+        return {"value": world * 1e3 / g_ms, "unit": "evals/s", "ms_per_step": g_ms,
                 "adjoint_ms_per_step": g_kt["grad"][0] / g_steps, "grad": [float(v) for v in grad]}
+
+    g_emu = time_grad(handles["emu"])
+    g_64 = time_grad(h64)
+    gradient = dict(g_emu)
+    gradient["what"] = ("loglik + d/d(sigma2, range, tau2): emulated-FP64 forward pass, FP64 reverse-mode adjoint")
+    gradient["max_rel_diff_vs_fp64_form"] = max(abs(a - b) / max(abs(b), 1e-300)
+                                                for a, b in zip(g_emu["grad"], g_64["grad"]))
+    gradient["fp64"] = g_64
 
     peaks = measured_peaks()
     bf16_peak = peaks["bf16_tflops_sustained"] if peaks else BF16_PEAK_FALLBACK

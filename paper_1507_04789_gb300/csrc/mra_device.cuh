@@ -7,6 +7,7 @@
 // SM, so every routine here is written to keep DFMA lanes busy with useful
 // work; shared-memory bandwidth is never the limit.
 #pragma once
+#include <cstring>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -43,15 +44,93 @@ __host__ __device__ inline Cov make_cov(double sigma2, double kappa, int family,
 
 __device__ __forceinline__ double gvar(double x) { return 1.0 + 0.5 * sin(4.0 * PI * x); }
 
+// ---- e^{-a}, a >= 0, for the covariance evaluations --------------------------
+// Table-driven argument reduction (Tang, "Table-driven implementation of the
+// exponential function in IEEE floating-point arithmetic", ACM TOMS 15, 1989):
+// -a = k ln2/64 + r with k = round(-a 64/ln2), |r| <= ln2/128, so
+// e^{-a} = 2^floor(k/64) 2^{(k mod 64)/64} e^r; 2^{j/64} comes from a table built
+// at compile time from its Taylor series in long double, e^r - 1 from the
+// Taylor polynomial of degree 5 (truncation below 4e-17 relative).  About 11
+// FP64 operations; error about 1.5 ulp.  Returns 0 for a > 708 (below 1e-307).
+constexpr long double MRA_LN2L = 0.693147180559945309417232121458176568L;
+
+constexpr double exp2_frac(int j) {            // 2^(j/64)
+  long double x = (long double)j / 64.0L * MRA_LN2L, term = 1.0L, sum = 1.0L;
+  for (int k = 1; k < 40; ++k) {
+    term *= x / (long double)k;
+    sum += term;
+  }
+  return (double)sum;
+}
+#define MRA_EXP2_T8(b)                                                                                      \
+  exp2_frac(b), exp2_frac(b + 1), exp2_frac(b + 2), exp2_frac(b + 3), exp2_frac(b + 4), exp2_frac(b + 5), \
+      exp2_frac(b + 6), exp2_frac(b + 7)
+#define MRA_EXP2_TAB                                                                                           \
+  {                                                                                                           \
+    MRA_EXP2_T8(0), MRA_EXP2_T8(8), MRA_EXP2_T8(16), MRA_EXP2_T8(24), MRA_EXP2_T8(32), MRA_EXP2_T8(40),         \
+        MRA_EXP2_T8(48), MRA_EXP2_T8(56)                                                                      \
+  }
+static __device__ const double k_exp2_tab[64] = MRA_EXP2_TAB;
+constexpr double k_exp2_tab_host[64] = MRA_EXP2_TAB;
+
+constexpr double MRA_EXP_INV = (double)(64.0L / MRA_LN2L);                 // 64 / ln2
+constexpr double MRA_EXP_C1 = (double)((long double)(long long)(MRA_LN2L / 64.0L * 4398046511104.0L) /
+                                       4398046511104.0L);                  // ln2/64 to 36 bits: k C1 exact
+constexpr double MRA_EXP_C2 = (double)(MRA_LN2L / 64.0L - (long double)MRA_EXP_C1);
+
+__host__ __device__ inline double exp_neg_tab(double a, const double* tab) {
+  if (!(a <= 708.0)) return 0.0;
+  const double t = -a;
+  const double magic = 6755399441055744.0;     // 1.5 2^52: adding it rounds to an integer
+  const double kd0 = fma(t, MRA_EXP_INV, magic);
+  long long kb;
+#ifdef __CUDA_ARCH__
+  kb = __double_as_longlong(kd0);
+#else
+  memcpy(&kb, &kd0, 8);
+#endif
+  const int k = (int)(unsigned)(kb & 0xFFFFFFFFll);
+  const double kd = kd0 - magic;
+  double r = fma(-kd, MRA_EXP_C1, t);
+  r = fma(-kd, MRA_EXP_C2, r);
+  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  q = fma(q, r, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  q = fma(q, r, 1.0);
+  q *= r;                                      // e^r - 1
+  const int j = k & 63, m = k >> 6;            // k <= 0: m = floor(k / 64)
+#ifdef __CUDA_ARCH__
+  const double tj = __ldg(tab + j);
+#else
+  const double tj = tab[j];
+#endif
+  const double v = fma(tj, q, tj);
+  const long long sb = (long long)(m + 1023) << 52;
+  double s2;
+#ifdef __CUDA_ARCH__
+  s2 = __longlong_as_double(sb);
+#else
+  memcpy(&s2, &sb, 8);
+#endif
+  return v * s2;
+}
+
+__device__ __forceinline__ double exp_neg(double a) { return exp_neg_tab(a, k_exp2_tab); }
+
+// Euclidean distance times s, sqrt through the reciprocal square root.
+__device__ __forceinline__ double dist_scaled(double dx, double dy, double s) {
+  const double u = fma(dx, dx, dy * dy);
+  return u > 0.0 ? u * rsqrt(u) * s : 0.0;
+}
+
 __device__ __forceinline__ double cov0(const Cov& c, double x1, double y1, double x2, double y2) {
-  double dx = x1 - x2, dy = y1 - y2;
-  double h = sqrt(dx * dx + dy * dy) * c.ik;
   double rho;
   if (c.family == 0) {
-    rho = exp(-h);
+    rho = exp_neg(dist_scaled(x1 - x2, y1 - y2, c.ik));
   } else {
-    double a = SQRT3 * h;
-    rho = (1.0 + a) * exp(-a);
+    const double a = dist_scaled(x1 - x2, y1 - y2, SQRT3 * c.ik);
+    const double e = exp_neg(a);
+    rho = fma(a, e, e);                        // (1 + a) e^{-a}
   }
   double v = c.sigma2 * rho;
   if (c.nonstat) v *= sqrt(gvar(x1) * gvar(x2));

@@ -119,56 +119,62 @@ __device__ __forceinline__ bool em_poll(EmCtx& cx, int b) {
 
 // Row scales of the groups of K columns [K0, K0 + KS), KS <= EM_MAXG * EM_KG:
 // rexp[g * TC_M + i] = max exponent of row i < na of A over group g (cexp for
-// B, rows < nb).  Item = 8 consecutive K of one row; consecutive threads take
-// consecutive rows (rows padded to a power of two); four items per thread are
-// loaded before their maxima are merged.
+// B, rows < nb).  The high words of the doubles (sign, exponent, top of the
+// mantissa) are brought into the idle staging buffers with asynchronous
+// copies, a slab of 64 K columns of every kept row at a time, so that one
+// memory latency covers a slab; one thread per row then scans its words.
+constexpr int EM_SLAB = 64;                    // K columns per slab (a divisor of EM_KG)
+constexpr int EM_SLAB_LD = EM_SLAB + 1;        // padded words per row in shared memory
+static_assert((TC_M + TC_N) * EM_SLAB_LD * 4 <= EM_STAGE_BYTES, "slab exceeds the staging buffers");
+
+__device__ __forceinline__ void em_cp4(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+
 __device__ inline void em_scales(EmCtx& cx, const double* A, long sai, long sak, int na, const double* B, long sbj,
                                  long sbk, int nb, int K0, int KS) {
-  __syncthreads();                                   // previous scales are no longer read
-  const int ng = (KS + EM_KG - 1) / EM_KG;
-  for (int t = threadIdx.x; t < ng * (TC_M + TC_N); t += NT) {
-    if (t < ng * TC_M) cx.rexp[t] = -2000;
-    else cx.cexp[t - ng * TC_M] = -2000;
-  }
-  __syncthreads();
-  const int la = na <= 32 ? 5 : (na <= 64 ? 6 : 7), lb = nb <= 32 ? 5 : 6;   // log2 of padded rows
-  const int ncore = (KS + 7) >> 3;
-  const int itemsA = ncore << la, items = itemsA + (ncore << lb);
-  for (int base = 0; base < items; base += 4 * NT) {
-    // item -> (operand, row, core column), without branches, so that the 32
-    // high-word loads of the four items are all in flight together
-    const unsigned* ptr[4];
-    long sk2[4];
-    int kn[4], slot[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int it = base + u * NT + threadIdx.x;
-      const bool isA = it < itemsA;
-      const int jt = isA ? it : it - itemsA;
-      const int lg = isA ? la : lb;
-      const int i = jt & ((1 << lg) - 1), kc = jt >> lg;
-      const bool valid = it < items && i < (isA ? na : nb);
-      const double* X = isA ? A : B;
-      const long si = isA ? sai : sbj, sk = isA ? sak : sbk;
-      ptr[u] = reinterpret_cast<const unsigned*>(X + (long)i * si + (long)(K0 + 8 * kc) * sk) + 1;
-      sk2[u] = 2 * sk;
-      kn[u] = valid ? min(8, KS - 8 * kc) : 0;
-      slot[u] = (isA ? ((8 * kc) / EM_KG) * TC_M : EM_REXP + ((8 * kc) / EM_KG) * TC_N) + i;
-    }
-    unsigned w[4][8];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) w[u][j] = j < kn[u] ? ptr[u][j * sk2[u]] : 0u;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      int e = -2000;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int be = (int)((w[u][j] >> 20) & 0x7FFu);
-        if (be) e = max(e, be - 1022);
+  uint32_t* words = reinterpret_cast<uint32_t*>(cx.stage);   // [row][EM_SLAB_LD]; rows of A, then of B
+  const uint32_t wbase = smem_addr(words);
+  const int rows = na + nb;
+  for (int s0 = 0; s0 < KS; s0 += EM_SLAB) {
+    const int sn = min(EM_SLAB, KS - s0);
+    __syncthreads();                         // scratch (and, on the first slab, earlier scales) no longer read
+    if (s0 == 0) {
+      const int ng = (KS + EM_KG - 1) / EM_KG;
+      for (int t = threadIdx.x; t < ng * (TC_M + TC_N); t += NT) {
+        if (t < ng * TC_M) cx.rexp[t] = -2000;
+        else cx.cexp[t - ng * TC_M] = -2000;
       }
-      if (e > -2000) atomicMax(slot[u] < EM_REXP ? cx.rexp + slot[u] : cx.cexp + (slot[u] - EM_REXP), e);
+    }
+    // copies: along K for row-major operands, along rows otherwise (coalesced
+    // either way); an operand that already lives in shared memory is read
+    // directly (the asynchronous copy takes global sources only)
+    for (int q = 0; q < 2; ++q) {
+      const double* X = q == 0 ? A : B;
+      const long si = q == 0 ? sai : sbj, sk = q == 0 ? sak : sbk;
+      const int n = q == 0 ? na : nb, r0 = q == 0 ? 0 : na;
+      const bool in_smem = __isShared(X);
+      const int cnt = n * sn;
+      for (int t = threadIdx.x; t < cnt; t += NT) {
+        int i, k;
+        if (sk == 1) { i = t / sn; k = t - i * sn; }
+        else { k = t / n; i = t - k * n; }
+        const unsigned* src = reinterpret_cast<const unsigned*>(X + (long)i * si + (long)(K0 + s0 + k) * sk) + 1;
+        if (in_smem) words[(r0 + i) * EM_SLAB_LD + k] = *src;
+        else em_cp4(wbase + 4u * (uint32_t)((r0 + i) * EM_SLAB_LD + k), src);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const int g = s0 / EM_KG;
+    for (int i = threadIdx.x; i < rows; i += NT) {
+      const uint32_t* wr = words + i * EM_SLAB_LD;
+      int be = 0;
+      for (int k = 0; k < sn; ++k) be = max(be, (int)((wr[k] >> 20) & 0x7FFu));
+      if (be) {
+        int* slot = i < na ? cx.rexp + g * TC_M + i : cx.cexp + g * TC_N + (i - na);
+        *slot = max(*slot, be - 1022);       // one thread per row: no race
+      }
     }
   }
   __syncthreads();

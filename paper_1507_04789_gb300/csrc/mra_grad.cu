@@ -34,16 +34,15 @@ namespace mra {
 // d C0 / d sigma2 and d C0 / d kappa at one pair of points.
 __device__ __forceinline__ void dcov0(const Cov& c, double x1, double y1, double x2, double y2, double& ds2,
                                       double& dk) {
-  double dx = x1 - x2, dy = y1 - y2;
-  double h = sqrt(dx * dx + dy * dy) * c.ik;
   double rho, drho;   // rho(h/kappa) and kappa * d rho / d kappa
   if (c.family == 0) {
-    rho = exp(-h);
+    const double h = dist_scaled(x1 - x2, y1 - y2, c.ik);
+    rho = exp_neg(h);
     drho = rho * h;
   } else {
-    double a = SQRT3 * h;
-    double e = exp(-a);
-    rho = (1.0 + a) * e;
+    const double a = dist_scaled(x1 - x2, y1 - y2, SQRT3 * c.ik);
+    const double e = exp_neg(a);
+    rho = fma(a, e, e);
     drho = a * a * e;
   }
   double gg = c.nonstat ? sqrt(gvar(x1) * gvar(x2)) : 1.0;
