@@ -468,6 +468,10 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
     B.want(&h->st.gv[m], R * r);
     B.want(&h->st.dd[m], R);
     B.want(&h->st.uu[m], R);
+    if (cfg->precision == MRA_PREC_EMU) {
+      if (m > 0) B.want(&h->st.vexp[m], R * ((int64_t)(m * r + 127) / 128) * r);
+      B.want(&h->st.liexp[m], R * r);
+    }
   }
   double *H, *z, *LS, *d, *u;
   B.want(&H, n * (int64_t)M * r);

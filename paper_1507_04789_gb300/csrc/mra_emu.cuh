@@ -74,8 +74,11 @@ __device__ __forceinline__ int em_exp(double x) {
 
 struct EmCtx {
   uint16_t* stage;   // EM_STAGE_BYTES of shared memory: two buffers of 7 A planes, then 7 B planes
-  int* rexp;         // EM_REXP row scales of A, [group][row]
+  int* rexp;         // EM_REXP row scales of A, [group][row], when the scale pass forms them
   int* cexp;         // EM_CEXP row scales of B
+  const int* ra;     // row scales of A in use: ra[g * rs + i] (rexp or a producer's table)
+  const int* cb;     // row scales of B in use: cb[g * cs + j]
+  int rs, cs;
   uint64_t* mbar;    // two mbarriers, one per staging buffer
   uint32_t tmem;
   uint32_t phase;    // bit b: parity of the next completion of mbar[b] (tracked by warp 0)
@@ -135,7 +138,11 @@ __device__ inline void em_scales(EmCtx& cx, const double* A, long sai, long sak,
                                  long sbk, int nb, int K0, int KS) {
   uint32_t* words = reinterpret_cast<uint32_t*>(cx.stage);   // [row][EM_SLAB_LD]; rows of A, then of B
   const uint32_t wbase = smem_addr(words);
-  const int rows = na + nb;
+  const int rows = na + nb;                  // na (nb) = 0: that operand's scales come from its producer
+  if (rows == 0) {
+    __syncthreads();
+    return;
+  }
   for (int s0 = 0; s0 < KS; s0 += EM_SLAB) {
     const int sn = min(EM_SLAB, KS - s0);
     __syncthreads();                         // scratch (and, on the first slab, earlier scales) no longer read
@@ -167,7 +174,7 @@ __device__ inline void em_scales(EmCtx& cx, const double* A, long sai, long sak,
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
     __syncthreads();
     const int g = s0 / EM_KG;
-    for (int i = threadIdx.x; i < rows; i += NT) {
+    for (int i = threadIdx.x; i < rows; i += NT) {   // (the scanned rows are the kept ones)
       const uint32_t* wr = words + i * EM_SLAB_LD;
       int be = 0;
       for (int k = 0; k < sn; ++k) be = max(be, (int)((wr[k] >> 20) & 0x7FFu));
@@ -263,8 +270,8 @@ __device__ inline void em_stage(EmCtx& cx, int b, int g, const double* A, long s
     const bool isA = it < ia;
     const int jt = isA ? it : it - ia;
     const int i = ((jt >> 1) & 7) | ((jt >> 5) << 3), k4 = ((jt >> 4) & 1) * 2 + (jt & 1);
-    if (isA) em_split_store(base, EM_A_HALFS, cx.rexp[g * TC_M + i], x[u], i, k4);
-    else em_split_store(base + EM_S * EM_A_HALFS, EM_B_HALFS, cx.cexp[g * TC_N + i], x[u], i, k4);
+    if (isA) em_split_store(base, EM_A_HALFS, cx.ra[g * cx.rs + i], x[u], i, k4);
+    else em_split_store(base + EM_S * EM_A_HALFS, EM_B_HALFS, cx.cb[g * cx.cs + i], x[u], i, k4);
   }
 }
 
@@ -342,22 +349,44 @@ __device__ __forceinline__ void em_issue_chunk(const EmCtx& cx, int b, bool gfir
       smem_addr(cx.mbar + b)));
 }
 
-// acc(i, j) += sum_k A(i, k) B(j, k) with FP64-grade accuracy, i < na <= 128,
-// j < nb <= 64.  Returns false (uniformly) if a tensor-core wait timed out.
+// Exact float -> double by bit moves (subnormal floats, below 2^-126, become 0).
+__device__ __forceinline__ double em_widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0) return 0.0;
+  const uint32_t de = e == 0xFFu ? 0x7FFu : e + 896u;          // 1023 - 127
+  const uint32_t hi = (u & 0x80000000u) | (de << 20) | ((u >> 3) & 0xFFFFFu);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// acc(i, j) = sum_k A(i, k) B(j, k) with FP64-grade accuracy, i < na <= 128,
+// j < nb <= 64 (acc is overwritten).  Returns false (uniformly) if a
+// tensor-core wait timed out.
 //
 // Software pipeline over the 16-column chunks of each scale pass: in step c,
 // warps 1..7 split chunk c into buffer c & 1 while warp 0 issues the MMAs of
 // chunk c - 1 (buffer (c - 1) & 1) and waits for them; the barrier that ends
 // the step therefore leaves buffer c & 1 staged and buffer (c - 1) & 1 free.
+//
+// pa / pb, when not null, hold the operands' row scales from their producers:
+// pa[g * pas + i] = the exponent e with |A(i, k)| < 2^e over K group g (any
+// upper bound a producer can form cheaply, e.g. a maximum over a superset of
+// the group's columns); the scale pass then skips that operand.
 __device__ inline bool em_mma(EmCtx& cx, TcAcc& acc, const double* A, long sai, long sak, int na, const double* B,
-                              long sbj, long sbk, int nb, int K) {
+                              long sbj, long sbk, int nb, int K, const int* pa = nullptr, int pas = 0,
+                              const int* pb = nullptr, int pbs = 0) {
   const int row = acc.row(), c0 = acc.col0();
   float hi[32], lo[32];
 #pragma unroll
   for (int c = 0; c < 32; ++c) hi[c] = lo[c] = 0.f;
   for (int K0 = 0; K0 < K; K0 += EM_MAXG * EM_KG) {
     const int KS = min(EM_MAXG * EM_KG, K - K0);
-    em_scales(cx, A, sai, sak, na, B, sbj, sbk, nb, K0, KS);
+    const int g0 = K0 / EM_KG;
+    cx.ra = pa ? pa + g0 * pas : cx.rexp;
+    cx.rs = pa ? pas : TC_M;
+    cx.cb = pb ? pb + g0 * pbs : cx.cexp;
+    cx.cs = pb ? pbs : TC_N;
+    em_scales(cx, A, sai, sak, pa ? 0 : na, B, sbj, sbk, pb ? 0 : nb, K0, KS);
     const int nch = (KS + EM_KC - 1) / EM_KC;
     for (int c = 0; c <= nch; ++c) {
       bool done = true;
@@ -383,15 +412,17 @@ __device__ inline bool em_mma(EmCtx& cx, TcAcc& acc, const double* A, long sai, 
       const int last = (c - 1) * EM_KC;                   // first column of the chunk whose MMAs completed
       if (c > 0 && ((last + EM_KC) % EM_KG == 0 || last + EM_KC >= KS)) {   // its group is complete
         const int g = last / EM_KG;
-        em_drain(cx, cx.cexp + g * TC_N, cx.rexp[g * TC_M + row], c0, na, nb, hi, lo);
+        em_drain(cx, cx.cb + g * cx.cs, row < na ? cx.ra[g * cx.rs + row] : -2000, c0, na, nb, hi, lo);
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();                                  // accumulators are read before the next group's MMAs
         asm volatile("tcgen05.fence::after_thread_sync;");
       }
     }
   }
+  // hi + lo to FP64 with one DADD: the float-to-double widening is done on the
+  // integer pipe (exact bit moves), not as a conversion on the narrow FP64 pipe
 #pragma unroll
-  for (int c = 0; c < 32; ++c) acc.v[c] += (double)hi[c] + (double)lo[c];
+  for (int c = 0; c < 32; ++c) acc.v[c] = em_widen(hi[c]) + em_widen(lo[c]);
   return true;
 }
 

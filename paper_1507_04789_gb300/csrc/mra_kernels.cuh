@@ -46,6 +46,10 @@ struct LevelState {
   double* gv[MAXL];   // 4^m x r: g = Lt^{-1} omegahat^m
   double* dd[MAXL];   // 4^m: d_R (Sec. 3.3)
   double* uu[MAXL];   // 4^m: u_R
+  // row scales for the FP64-emulation engine (MRA_PREC_EMU only, else null):
+  // the binary exponent e with |x| < 2^e over each 128-column group of a row
+  int32_t* vexp[MAXL];   // level m >= 1: 4^m x ceil(m r / 128) x r, rows of V_R per group
+  int32_t* liexp[MAXL];  // 4^m x r: rows of L_R^{-1}
   // saved for the gradient (null when no gradient is requested)
   double* L[MAXL];    // 4^m x r x r: L_R (prior Cholesky factor)
   double* Ltf[MAXL];  // 4^m x r x r: Lt (Cholesky factor of I + Ahat^{m,m})

@@ -23,7 +23,9 @@
 namespace mra {
 
 // The tensor-core engine of a kernel: 3xTF32 (EMU = false) or the FP64-grade
-// bf16-slice emulation (EMU = true); both write the same TcAcc layout.
+// bf16-slice emulation (EMU = true); both write the same TcAcc layout.  Every
+// call site zeroes the accumulator first: the 3xTF32 engine adds to it, the
+// emulation engine overwrites it.
 template <bool EMU>
 struct Engine;
 
@@ -36,7 +38,7 @@ struct Engine<false> {
     tc_init(cx, tmem_slot);
   }
   __device__ bool mma(TcAcc& acc, const double* A, long sai, long sak, int na, const double* B, long sbj, long sbk,
-                      int nb, int K) {
+                      int nb, int K, const int* = nullptr, int = 0, const int* = nullptr, int = 0) {
     return tc_mma(cx, acc, A, sai, sak, na, B, sbj, sbk, nb, K);
   }
   __device__ void release() { tc_release(cx); }
@@ -54,12 +56,21 @@ struct Engine<true> {
     cx.fail = fail;
     em_init(cx, tmem_slot);
   }
+  // pa / pb: the operands' row scales from their producers (see em_mma), or null
   __device__ bool mma(TcAcc& acc, const double* A, long sai, long sak, int na, const double* B, long sbj, long sbk,
-                      int nb, int K) {
-    return em_mma(cx, acc, A, sai, sak, na, B, sbj, sbk, nb, K);
+                      int nb, int K, const int* pa = nullptr, int pas = 0, const int* pb = nullptr, int pbs = 0) {
+    return em_mma(cx, acc, A, sai, sak, na, B, sbj, sbk, nb, K, pa, pas, pb, pbs);
   }
   __device__ void release() { em_release(cx); }
 };
+
+// Binary exponent e with |x| < 2^e (-2000 for zero), for the producer-side row
+// scales of the emulation engine.
+__device__ __forceinline__ int xexp_of(double x) {
+  const int be = (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
+  return be == 0 ? -2000 : be - 1022;
+}
+constexpr int EM_GMAX = 6;   // 128-column groups of a row of at most MRA_MAX_M x MAX_R_DEV = 768 columns
 
 template <bool EMU>
 __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* __restrict__ D,
@@ -69,12 +80,16 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
   __shared__ uint32_t tmem_slot;
   __shared__ int fail, bad;
   __shared__ int rexp[EMU ? EM_REXP : 1], cexp[EMU ? EM_CEXP : 1];
+  // emulation: row scales of this region's V rows per 128-column group, and of the current X^l block
+  __shared__ int vsc[EMU ? EM_GMAX * MAX_R_DEV : 1], xsc[EMU ? MAX_R_DEV : 1];
   const Item it = work_item(work);
   const Desc& ds = D[it.d];
   const Shape sh = ds.sh;
   const Cov cv = ds.cv;
   const LevelState& st = ds.st;
   const int r = sh.r, mr = m * r;
+  if (EMU)
+    for (int t = threadIdx.x; t < EM_GMAX * MAX_R_DEV; t += NT) vsc[t] = -2000;
   const long i = it.i;
   double* qx = reinterpret_cast<double*>(dsm + Engine<EMU>::STAGE);
   double* qy = qx + MAX_R_DEV;
@@ -95,35 +110,60 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
     __syncthreads();
     load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
     const double* Vanc = st.V[l] + a * (long)r * (l * r);
+    if (EMU)
+      for (int t = threadIdx.x; t < MAX_R_DEV; t += NT) xsc[t] = -2000;
     __syncthreads();
     // C0(Q_R, Q_{R_l}) into block l, spread over every warp (the FP64 pipe of
     // every SM sub-partition); the product below reads only blocks < l
     for (int t = threadIdx.x; t < r * r; t += NT) {
       const int qi = t / r, qj = t - qi * r;
-      Vrow[(long)qi * mr + l * r + qj] = cov0(cv, qx[qi], qy[qi], ax[qj], ay[qj]);
+      const double v = cov0(cv, qx[qi], qy[qi], ax[qj], ay[qj]);
+      Vrow[(long)qi * mr + l * r + qj] = v;
+      if (EMU && l == 0) atomicMax(xsc + qi, xexp_of(v));
     }
     acc.zero();
     __syncthreads();
     if (l > 0) {
-      ok = eng.mma(acc, Vrow, mr, 1, r, Vanc, l * r, 1, r, l * r);
+      const int* vsa = EMU ? st.vexp[l] + a * (long)((l * r + 127) / 128) * r : nullptr;
+      ok = eng.mma(acc, Vrow, mr, 1, r, Vanc, l * r, 1, r, l * r, vsc, MAX_R_DEV, vsa, r);
       if (!ok) break;
-      if (row < r)
+      if (row < r) {
+        int e = -2000;
         #pragma unroll
         for (int c = 0; c < 32; ++c) {
           const int col = c0 + c;
-          if (col < r) Vrow[(long)row * mr + l * r + col] -= acc.v[c];
+          if (col < r) {
+            const double v = Vrow[(long)row * mr + l * r + col] - acc.v[c];
+            Vrow[(long)row * mr + l * r + col] = v;
+            e = max(e, xexp_of(v));
+          }
         }
+        if (EMU) atomicMax(xsc + row, e);
+      }
     }
     __syncthreads();
     acc.zero();
-    ok = eng.mma(acc, Vrow + l * r, mr, 1, r, st.Li[l] + a * (long)r * r, r, 1, r, r);
+    ok = eng.mma(acc, Vrow + l * r, mr, 1, r, st.Li[l] + a * (long)r * r, r, 1, r, r, xsc, 0,
+                 EMU ? st.liexp[l] + a * r : nullptr, 0);
     if (!ok) break;
-    if (row < r)
+    if (row < r) {
+      int e0 = -2000, e1 = -2000;       // a thread's 32 columns touch at most two groups
+      const int gbase = (l * r + c0) / 128;
       #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int col = c0 + c;
-        if (col < r) Vrow[(long)row * mr + l * r + col] = acc.v[c];
+        if (col < r) {
+          Vrow[(long)row * mr + l * r + col] = acc.v[c];
+          const int e = xexp_of(acc.v[c]);
+          if ((l * r + col) / 128 == gbase) e0 = max(e0, e);
+          else e1 = max(e1, e);
+        }
       }
+      if (EMU) {
+        atomicMax(vsc + gbase * MAX_R_DEV + row, e0);
+        if (e1 > -2000) atomicMax(vsc + (gbase + 1) * MAX_R_DEV + row, e1);
+      }
+    }
   }
   __syncthreads();                             // knots loaded, chain blocks written
   const int ldw = r + 1;
@@ -136,7 +176,7 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
   __syncthreads();
   if (ok) {
     acc.zero();
-    if (m > 0) ok = eng.mma(acc, Vrow, mr, 1, r, Vrow, mr, 1, r, mr);
+    if (m > 0) ok = eng.mma(acc, Vrow, mr, 1, r, Vrow, mr, 1, r, mr, vsc, MAX_R_DEV, vsc, MAX_R_DEV);
   }
   if (ok) {
     if (m > 0 && row < r)
@@ -154,6 +194,18 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
     trinv_smem(W, r, ldw, tmp);
     double* Li = st.Li[m] + i * (long)r * r;
     for (int t = threadIdx.x; t < r * r; t += NT) Li[t] = W[(t / r) * ldw + (t % r)];
+    if (EMU) {   // row scales of V_R and L_R^{-1} for the descendants' products
+      for (int t = threadIdx.x; t < r; t += NT) {
+        int e = -2000;
+        for (int k = 0; k <= t; ++k) e = max(e, xexp_of(W[t * ldw + k]));
+        st.liexp[m][i * r + t] = e;
+      }
+      if (m > 0) {
+        const int ng = (mr + 127) / 128;
+        for (int t = threadIdx.x; t < ng * r; t += NT)
+          st.vexp[m][(i * ng + t / r) * (long)r + t % r] = vsc[(t / r) * MAX_R_DEV + t % r];
+      }
+    }
   }
   eng.release();
   if (threadIdx.x == 0) {
@@ -170,6 +222,8 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
   __shared__ uint32_t tmem_slot;
   __shared__ int fail, bad;
   __shared__ int rexp[EMU ? EM_REXP : 1], cexp[EMU ? EM_CEXP : 1];
+  // emulation: row scales of H rows per 128-column group, of the current X^l block, of L_Sigma^{-1}
+  __shared__ int hsc[EMU ? EM_GMAX * TC_M : 1], xsc[EMU ? TC_M : 1], ssc[EMU ? TC_M : 1];
   const Item it = work_item(work);
   const Desc& ds = D[it.d];
   const Shape sh = ds.sh;
@@ -204,6 +258,8 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
     sy[t] = lf.ys[o0 + t];
     sv[t] = lf.yv[o0 + t];
   }
+  if (EMU)
+    for (int t = threadIdx.x; t < EM_GMAX * TC_M; t += NT) hsc[t] = -2000;
   double* Hrow = lf.H + o0 * Mr;
   TcAcc acc;
   bool ok = true;
@@ -214,35 +270,60 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
     __syncthreads();
     load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
     const double* Vanc = st.V[l] + a * (long)r * (l * r);
+    if (EMU)
+      for (int t = threadIdx.x; t < TC_M; t += NT) xsc[t] = -2000;
     __syncthreads();
     // C0(S_F, Q_l) into block l, spread over every warp; the product below
     // reads only blocks < l
     for (int t = threadIdx.x; t < nF * r; t += NT) {
       const int fi = t / r, qj = t - fi * r;
-      Hrow[(long)fi * Mr + l * r + qj] = cov0(cv, sx[fi], sy[fi], ax[qj], ay[qj]);
+      const double v = cov0(cv, sx[fi], sy[fi], ax[qj], ay[qj]);
+      Hrow[(long)fi * Mr + l * r + qj] = v;
+      if (EMU && l == 0) atomicMax(xsc + fi, xexp_of(v));
     }
     acc.zero();
     __syncthreads();
     if (l > 0) {
-      ok = eng.mma(acc, Hrow, Mr, 1, nF, Vanc, l * r, 1, r, l * r);
+      const int* vsa = EMU ? st.vexp[l] + a * (long)((l * r + 127) / 128) * r : nullptr;
+      ok = eng.mma(acc, Hrow, Mr, 1, nF, Vanc, l * r, 1, r, l * r, hsc, TC_M, vsa, r);
       if (!ok) break;
-      if (row < nF)
+      if (row < nF) {
+        int e = -2000;
         #pragma unroll
         for (int c = 0; c < 32; ++c) {
           const int col = c0 + c;
-          if (col < r) Hrow[(long)row * Mr + l * r + col] -= acc.v[c];
+          if (col < r) {
+            const double v = Hrow[(long)row * Mr + l * r + col] - acc.v[c];
+            Hrow[(long)row * Mr + l * r + col] = v;
+            e = max(e, xexp_of(v));
+          }
         }
+        if (EMU) atomicMax(xsc + row, e);
+      }
     }
     __syncthreads();
     acc.zero();
-    ok = eng.mma(acc, Hrow + l * r, Mr, 1, nF, st.Li[l] + a * (long)r * r, r, 1, r, r);
+    ok = eng.mma(acc, Hrow + l * r, Mr, 1, nF, st.Li[l] + a * (long)r * r, r, 1, r, r, xsc, 0,
+                 EMU ? st.liexp[l] + a * r : nullptr, 0);
     if (!ok) break;
-    if (row < nF)
+    if (row < nF) {
+      int e0 = -2000, e1 = -2000;       // a thread's 32 columns touch at most two groups
+      const int gbase = (l * r + c0) / 128;
       #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int col = c0 + c;
-        if (col < r) Hrow[(long)row * Mr + l * r + col] = acc.v[c];
+        if (col < r) {
+          Hrow[(long)row * Mr + l * r + col] = acc.v[c];
+          const int e = xexp_of(acc.v[c]);
+          if ((l * r + col) / 128 == gbase) e0 = max(e0, e);
+          else e1 = max(e1, e);
+        }
       }
+      if (EMU) {
+        atomicMax(hsc + gbase * TC_M + row, e0);
+        if (e1 > -2000) atomicMax(hsc + (gbase + 1) * TC_M + row, e1);
+      }
+    }
   }
   __syncthreads();                             // points loaded, chain blocks written
   // Sigma_F = C0(S_F, S_F) - V_F V_F' + tau2 I (lower triangle), the
@@ -257,7 +338,8 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
   for (int ct = 0; ct < nct && ok && M > 0; ++ct) {
     const int ncol = min(TC_N, nF - ct * TC_N);
     acc.zero();
-    ok = eng.mma(acc, Hrow, Mr, 1, nF, Hrow + (long)ct * TC_N * Mr, Mr, 1, ncol, Mr);
+    ok = eng.mma(acc, Hrow, Mr, 1, nF, Hrow + (long)ct * TC_N * Mr, Mr, 1, ncol, Mr, hsc, TC_M,
+                 hsc + ct * TC_N, TC_M);
     if (!ok) break;
     if (row < nF)
       #pragma unroll
@@ -278,6 +360,13 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
     if (lf.VF)
       for (long t = threadIdx.x; t < (long)nF * Mr; t += NT) lf.VF[o0 * Mr + t] = Hrow[t];
     trinv_smem(S, nF, lds, tmp);
+    if (EMU) {   // row scales of L_Sigma^{-1} (lower triangular) for the solve below
+      for (int t = threadIdx.x; t < nF; t += NT) {
+        int e = -2000;
+        for (int q = 0; q <= t; ++q) e = max(e, xexp_of(S[t * lds + q]));
+        ssc[t] = e;
+      }
+    }
     double* LS = lf.LS + lf.sq_off[Fm];
     for (int t = threadIdx.x; t < nF * nF; t += NT) LS[t] = S[(t / nF) * lds + (t % nF)];
     for (int t = threadIdx.x; t < nF; t += NT) {
@@ -290,7 +379,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
     // H^l = L_Sigma^{-1} V^l_F (whole block read before it is overwritten)
     for (int l = 0; l < M && ok; ++l) {
       acc.zero();
-      ok = eng.mma(acc, S, lds, 1, nF, Hrow + l * r, 1, Mr, r, nF);
+      ok = eng.mma(acc, S, lds, 1, nF, Hrow + l * r, 1, Mr, r, nF, EMU ? ssc : nullptr, 0);
       if (!ok) break;
       if (row < nF)
         #pragma unroll
@@ -459,7 +548,8 @@ static size_t leaf_tc_smem(int nlmax) {
 }
 // Dynamic plus (an upper bound of) static shared memory of the leaf kernel.
 size_t leaf_tc_smem_bytes(int nlmax, int emu) {
-  return emu ? 1024 + sizeof(int) * (EM_REXP + EM_CEXP) + leaf_tc_smem<true>(nlmax) : 1024 + leaf_tc_smem<false>(nlmax);
+  return emu ? 1024 + sizeof(int) * (EM_REXP + EM_CEXP + EM_GMAX * TC_M + 2 * TC_M) + leaf_tc_smem<true>(nlmax)
+             : 1024 + leaf_tc_smem<false>(nlmax);
 }
 
 
