@@ -470,6 +470,7 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
     B.want(&h->st.uu[m], R);
     if (cfg->precision == MRA_PREC_EMU) {
       if (m > 0) B.want(&h->st.vexp[m], R * ((int64_t)(m * r + 127) / 128) * r);
+      if (m > 0) B.want(&h->st.gcol[m], R * (int64_t)m * r);
       B.want(&h->st.liexp[m], R * r);
     }
   }
@@ -479,6 +480,8 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   B.want(&LS, (size_t)tail);
   B.want(&d, nreg[M]);
   B.want(&u, nreg[M]);
+  int32_t* hcol = nullptr;
+  if (cfg->precision == MRA_PREC_EMU) B.want(&hcol, nreg[M] * (int64_t)M * r);
   B.want(&h->d_desc, 1);
   h->ls_cap = tail;
   if ((e = B.commit())) { mra_free(h); return fail(MRA_ERR_OOM, "device allocation (factors): %s", cudaGetErrorString(e)); }
@@ -502,6 +505,7 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   h->lf.LS = LS;
   h->lf.d = d;
   h->lf.u = u;
+  h->lf.hcol = hcol;
   single_plan(h);
   size_t need = cfg->precision != MRA_PREC_FP64 ? mra::leaf_tc_smem_bytes(h->nlmax, cfg->precision == MRA_PREC_EMU)
                                                  : mra::leaf_smem_bytes(r, h->nlmax);

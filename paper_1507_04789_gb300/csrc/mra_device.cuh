@@ -137,6 +137,13 @@ __device__ __forceinline__ double cov0(const Cov& c, double x1, double y1, doubl
   return v;
 }
 
+// Binary exponent e with |x| < 2^e (-2000 for zero): the row and column
+// scales of the FP64-emulation engine.
+__device__ __forceinline__ int xexp_of(double x) {
+  const int be = (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
+  return be == 0 ? -2000 : be - 1022;
+}
+
 // ---- partition and knots (Sec. 2.2) -----------------------------------------
 // Region i of level m: child digits j_t = bits (2t+1, 2t) of i counted from the
 // top level, b_x = j & 1, b_y = j >> 1; boxes are halved at their midpoint.

@@ -50,6 +50,7 @@ struct LevelState {
   // the binary exponent e with |x| < 2^e over each 128-column group of a row
   int32_t* vexp[MAXL];   // level m >= 1: 4^m x ceil(m r / 128) x r, rows of V_R per group
   int32_t* liexp[MAXL];  // 4^m x r: rows of L_R^{-1}
+  int32_t* gcol[MAXL];   // level m >= 1: 4^m x (m r): columns of G_R over its r rows
   // saved for the gradient (null when no gradient is requested)
   double* L[MAXL];    // 4^m x r x r: L_R (prior Cholesky factor)
   double* Ltf[MAXL];  // 4^m x r x r: Lt (Cholesky factor of I + Ahat^{m,m})
@@ -75,6 +76,8 @@ struct LeafState {
   // saved for the gradient (null when no gradient is requested)
   double* VF;             // n x (M r): V_F before the L_Sigma^{-1} solve
   double* LSf;            // ragged n_F x n_F: L_Sigma
+  // column scales of H_F over the leaf's rows for the emulation engine (else null)
+  int32_t* hcol;          // per active leaf x (M r)
 };
 
 // Adjoint state of the gradient pass (mra_grad.cu).

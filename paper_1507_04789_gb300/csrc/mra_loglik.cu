@@ -358,6 +358,14 @@ __global__ void __launch_bounds__(NT) post_level_kernel(int m, const Desc* __res
         if (row < r && col < r) Gr[(long)row * mr + l * r + col] = acc.v[a][b];
       }
   }
+  if (st.gcol[m]) {   // emulation: column scales of G over its r rows, for the aggregation above
+    __syncthreads();
+    for (int c = threadIdx.x; c < mr; c += NT) {
+      int e = -2000;
+      for (int a = 0; a < r; ++a) e = max(e, xexp_of(Gr[(long)a * mr + c]));
+      st.gcol[m][i * (long)mr + c] = e;
+    }
+  }
   if (threadIdx.x == 0) {
     double dsum = 0.0, usum = 0.0;
     const long cf = st.cfirst[m][i], cc = st.ccnt[m][i];

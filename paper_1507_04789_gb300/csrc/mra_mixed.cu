@@ -64,12 +64,6 @@ struct Engine<true> {
   __device__ void release() { em_release(cx); }
 };
 
-// Binary exponent e with |x| < 2^e (-2000 for zero), for the producer-side row
-// scales of the emulation engine.
-__device__ __forceinline__ int xexp_of(double x) {
-  const int be = (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
-  return be == 0 ? -2000 : be - 1022;
-}
 constexpr int EM_GMAX = 6;   // 128-column groups of a row of at most MRA_MAX_M x MAX_R_DEV = 768 columns
 
 template <bool EMU>
@@ -377,6 +371,9 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
     }
     zz = block_sum(zz, red);
     // H^l = L_Sigma^{-1} V^l_F (whole block read before it is overwritten)
+    int32_t* hcol = EMU ? lf.hcol + F * (long)Mr : nullptr;   // column scales of H_F for the Gram kernel
+    if (EMU)
+      for (int t = threadIdx.x; t < Mr; t += NT) hcol[t] = -2000;
     for (int l = 0; l < M && ok; ++l) {
       acc.zero();
       ok = eng.mma(acc, S, lds, 1, nF, Hrow + l * r, 1, Mr, r, nF, EMU ? ssc : nullptr, 0);
@@ -387,6 +384,14 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
           const int col = c0 + c;
           if (col < r) Hrow[(long)row * Mr + l * r + col] = acc.v[c];
         }
+      if (EMU && ((threadIdx.x >> 5) & 3) * 32 < nF) {   // warp-uniform: the warp holds a kept row
+        const int lane = threadIdx.x & 31;
+        #pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int e = __reduce_max_sync(0xffffffffu, row < nF ? xexp_of(acc.v[c]) : -2000);
+          if (lane == c && c0 + c < r && e > -2000) atomicMax(hcol + l * r + c0 + c, e);
+        }
+      }
       __syncthreads();
     }
   }
@@ -451,9 +456,30 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict
   const double* Hb = lf.H + row0 * Mr;
   Engine<true> eng;
   eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
+  // scales per 128-row group of the parent's rows: the largest column scale of
+  // the leaves whose rows meet the group (an upper bound of the group's maximum)
+  const int ng = (K + EM_KG - 1) / EM_KG;
+  for (int t = threadIdx.x; t < ng * (TC_M + TC_N); t += NT) {
+    const bool isA = t < ng * TC_M;
+    const int u = isA ? t : t - ng * TC_M;
+    const int g = isA ? u / TC_M : u / TC_N, i = isA ? u % TC_M : u % TC_N;
+    int e = -2000;
+    if (i < (isA ? nk * r : r)) {
+      const int col = isA ? k0 * r + i : l * r + i;
+      for (int c = 0; c < 4; ++c) {
+        const long lo = lf.off[4 * pm + c] - row0, hi = lf.off[4 * pm + c + 1] - row0;
+        if (hi > lo && lo < (long)(g + 1) * EM_KG && hi > (long)g * EM_KG) {
+          const int cl = st.cid[M][4 * pm + c];
+          e = max(e, lf.hcol[(long)cl * Mr + col]);
+        }
+      }
+    }
+    (isA ? rexp : cexp)[u] = e;
+  }
+  __syncthreads();
   TcAcc acc;
   acc.zero();
-  const bool ok = eng.mma(acc, Hb + k0 * r, 1, Mr, nk * r, Hb + l * r, 1, Mr, r, K);
+  const bool ok = eng.mma(acc, Hb + k0 * r, 1, Mr, nk * r, Hb + l * r, 1, Mr, r, K, rexp, TC_M, cexp, TC_N);
   const int m = M - 1, T = (m + 1) * (m + 2) / 2;
   const int row = acc.row(), c0 = acc.col0();
   if (ok && row < nk * r) {
@@ -496,9 +522,26 @@ __global__ void __launch_bounds__(NT) aggregate_kernel_em(int m, const Desc* __r
   const double* Gb = st.G[m] + cf * (long)r * mr;
   Engine<true> eng;
   eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
+  // scales per 128-row group of the stacked children (r rows each): the
+  // largest column scale of the children whose rows meet the group
+  const int K = (int)(cc * r), ng = (K + EM_KG - 1) / EM_KG;
+  for (int t = threadIdx.x; t < ng * (TC_M + TC_N); t += NT) {
+    const bool isA = t < ng * TC_M;
+    const int u = isA ? t : t - ng * TC_M;
+    const int g = isA ? u / TC_M : u / TC_N, i = isA ? u % TC_M : u % TC_N;
+    int e = -2000;
+    if (i < (isA ? nk * r : r)) {
+      const int col = isA ? k0 * r + i : l * r + i;
+      for (long ch = 0; ch < cc; ++ch)
+        if (ch * r < (long)(g + 1) * EM_KG && (ch + 1) * r > (long)g * EM_KG)
+          e = max(e, st.gcol[m][(cf + ch) * (long)mr + col]);
+    }
+    (isA ? rexp : cexp)[u] = e;
+  }
+  __syncthreads();
   TcAcc acc;
   acc.zero();
-  const bool ok = eng.mma(acc, Gb + k0 * r, 1, mr, nk * r, Gb + l * r, 1, mr, r, (int)(cc * r));
+  const bool ok = eng.mma(acc, Gb + k0 * r, 1, mr, nk * r, Gb + l * r, 1, mr, r, K, rexp, TC_M, cexp, TC_N);
   const int row = acc.row(), c0 = acc.col0();
   if (ok && row < nk * r) {
     const int k = k0 + row / r, ri = row % r, t = tri_index(k, l);
