@@ -187,51 +187,58 @@ __device__ inline void em_scales(EmCtx& cx, const double* A, long sai, long sak,
   __syncthreads();
 }
 
-// The 7 slices of x relative to scale e (|x| < 2^e), as FP32 integers with x's sign.
-__device__ __forceinline__ void em_split(double x, int e, float* f) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const int be = (int)((u >> 52) & 0x7FF);
-  unsigned long long X = 0;
-  if (be != 0) {
-    const unsigned long long m = (u & ((1ull << 52) - 1)) | (1ull << 52);   // |x| = m 2^(be - 1075)
-    const int sh = (52 - EM_BITS) + e - (be - 1023);                         // >= 4
-    X = sh < 53 ? (m >> sh) : 0ull;                                          // |x| 2^(49 - e), truncated
-  }
-  const uint32_t xh = (uint32_t)(X >> 32), xl = (uint32_t)X;
-  uint32_t a[EM_S];
-  a[0] = xh >> 10;
-  a[1] = (xh >> 3) & 127u;
-  a[2] = ((xh << 4) | (xl >> 28)) & 127u;
-  a[3] = (xl >> 21) & 127u;
-  a[4] = (xl >> 14) & 127u;
-  a[5] = (xl >> 7) & 127u;
-  a[6] = xl & 127u;
-  const float sg = (u >> 63) ? -1.0f : 1.0f;
-  // (2^23 + a) sg - 2^23 sg = a sg exactly (a < 2^23)
-#pragma unroll
-  for (int p = 0; p < EM_S; ++p) f[p] = fmaf(__uint_as_float(0x4B000000u | a[p]), sg, -8388608.0f * sg);
+// The 49-bit magnitude window of x relative to scale e (|x| < 2^e):
+// X = floor(|x| 2^(49 - e)) as h (top 17 bits) and l (low 32 bits); 0 for zero.
+__device__ __forceinline__ void em_window(double x, int e, uint32_t& h, uint32_t& l) {
+  const uint32_t hw = (uint32_t)__double2hiint(x), lw = (uint32_t)__double2loint(x);
+  const int be = (int)((hw >> 20) & 0x7FFu);
+  const uint32_t mh = (hw & 0xFFFFFu) | 0x100000u;                   // mantissa = mh : lw (53 bits)
+  const int sh = min(e + 1026 - be, 63);                              // >= 4 when |x| < 2^e
+  const uint32_t l_lo = __funnelshift_r(lw, mh, (uint32_t)sh);        // used when sh < 32
+  const uint32_t l_hi = sh < 53 ? mh >> (sh - 32 < 0 ? 0 : sh - 32) : 0u;
+  l = be == 0 ? 0u : (sh < 32 ? l_lo : l_hi);
+  h = (be == 0 || sh >= 32) ? 0u : mh >> sh;
 }
 
-__device__ __forceinline__ uint32_t em_pack(float hi, float lo) {   // exact: small integers
+// bf16x2 fused multiply-add: exact here (small integers).
+__device__ __forceinline__ uint32_t em_hfma2(uint32_t a, uint32_t b, uint32_t c) {
   uint32_t d;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
   return d;
+}
+
+// The 7 slice planes of a pair of elements (x0 low half, x1 high half) as
+// bf16x2 words: slice p of X is the 7-bit field at bits 49 - 7 (p + 1); the two
+// fields go to bits 0-6 and 16-22 of a word biased to bf16 (128 + a), and one
+// bf16x2 FMA gives sg (128 + a) - 128 sg = sg a exactly.
+__device__ __forceinline__ void em_split_pair(double x0, double x1, int e, uint32_t* w) {
+  uint32_t h0, l0, h1, l1;
+  em_window(x0, e, h0, l0);
+  em_window(x1, e, h1, l1);
+  const uint32_t sgn = (((uint32_t)__double2hiint(x0) >> 16) & 0x8000u) | ((uint32_t)__double2hiint(x1) & 0x80000000u);
+  const uint32_t sg = 0x3F803F80u | sgn;              // (+-1, +-1) in bf16
+  const uint32_t nb = 0xC300C300u ^ sgn;              // -128 sg
+  const uint32_t bias = 0x43004300u;
+  const uint32_t M0 = 0x7Fu, M1 = 0x7F0000u;
+  // field of element 0 in bits 0-6 (t0), of element 1 in bits 16-22 (t1)
+  uint32_t t0, t1;
+  t0 = h0 >> 10;                        t1 = h1 << 6;                        w[0] = em_hfma2(t0 | (t1 & M1) | bias, sg, nb);
+  t0 = h0 >> 3;                         t1 = h1 << 13;                       w[1] = em_hfma2((t0 & M0) | (t1 & M1) | bias, sg, nb);
+  t0 = __funnelshift_r(l0, h0, 28);     t1 = __funnelshift_r(l1, h1, 12);    w[2] = em_hfma2((t0 & M0) | (t1 & M1) | bias, sg, nb);
+  t0 = l0 >> 21;                        t1 = l1 >> 5;                        w[3] = em_hfma2((t0 & M0) | (t1 & M1) | bias, sg, nb);
+  t0 = l0 >> 14;                        t1 = l1 << 2;                        w[4] = em_hfma2((t0 & M0) | (t1 & M1) | bias, sg, nb);
+  t0 = l0 >> 7;                         t1 = l1 << 9;                        w[5] = em_hfma2((t0 & M0) | (t1 & M1) | bias, sg, nb);
+  t0 = l0;                              t1 = l1 << 16;                       w[6] = em_hfma2((t0 & M0) | (t1 & M1) | bias, sg, nb);
 }
 
 // The 7 slice planes of 4 consecutive K of row i, as bf16 pairs, into planes.
 __device__ __forceinline__ void em_split_store(uint16_t* planes, int pstride, int e, const double* x, int i, int k4) {
-  uint32_t w[EM_S][2];
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    float f0[EM_S], f1[EM_S];
-    em_split(x[2 * q], e, f0);
-    em_split(x[2 * q + 1], e, f1);
-#pragma unroll
-    for (int s = 0; s < EM_S; ++s) w[s][q] = em_pack(f1[s], f0[s]);
-  }
+  uint32_t w0[EM_S], w1[EM_S];
+  em_split_pair(x[0], x[1], e, w0);
+  em_split_pair(x[2], x[3], e, w1);
   const int off = em_cm(i, 4 * k4);
 #pragma unroll
-  for (int s = 0; s < EM_S; ++s) *reinterpret_cast<uint2*>(planes + s * pstride + off) = make_uint2(w[s][0], w[s][1]);
+  for (int s = 0; s < EM_S; ++s) *reinterpret_cast<uint2*>(planes + s * pstride + off) = make_uint2(w0[s], w1[s]);
 }
 
 constexpr int EM_MAX_ITEMS = (4 * (TC_M + TC_N) + NT - 32 - 1) / (NT - 32);   // per staging thread
