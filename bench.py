@@ -127,11 +127,11 @@ def contraction_flops(M: int, r: int, nF, precision: str):
 # while the kernel's sources are the ones it was taken from (else null).
 TRAFFIC = {
     ("emu", "leaf", "n1M_matern15_M7_r64"): {
-        "bytes": 5.50e9,
+        "bytes": 5.44e9,
         "how": "dram__bytes_read.sum + dram__bytes_write.sum of leaf_kernel_tc<1> at n = 2^18, M = 6 "
-               "(1.18 GB, profiles/leaf_kernel_tc_emu_n256k.md) scaled by n M r to n = 2^20, M = 7",
+               "(1.17 GB, profiles/leaf_kernel_tc_emu_n256k.md) scaled by n M r to n = 2^20, M = 7",
         "sources": ["mra_mixed.cu", "mra_emu.cuh", "mra_tc.cuh", "mra_device.cuh", "mra_kernels.cuh"],
-        "sha1": "b95245e5f2c736b0e4e60d7dc8e750b9df4dda15",
+        "sha1": "05d1d8496653b9e8f8b064528ff76fc736fbd50b",
     },
 }
 
