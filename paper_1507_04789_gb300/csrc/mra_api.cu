@@ -659,6 +659,16 @@ static int ensure_grad_arena(mra_handle* h) {
     G.want(&h->gs.Up[m], R * (int64_t)m * (m + 1) / 2 * r * r);
   }
   if (M > 0) G.want(&h->gs.PartLeaf, (int64_t)nreg[M - 1] * M * (M + 1) / 2 * r * r);
+  // emulated form: the per-parent adjoint S for Hbar on the tensor cores, when
+  // it takes at most four times the memory of H (else the leaf adjoint forms
+  // Hbar in FP64 from the ancestors' blocks directly)
+  h->gs.SF = nullptr;
+  h->gs.SFexp = nullptr;
+  if (M > 0 && h->cfg.precision == MRA_PREC_EMU && (int64_t)nreg[M - 1] * M * r <= 4 * n) {
+    const int64_t Mr = (int64_t)M * r;
+    G.want(&h->gs.SF, (int64_t)nreg[M - 1] * Mr * Mr);
+    G.want(&h->gs.SFexp, (int64_t)nreg[M - 1] * ((Mr + 127) / 128) * Mr + 8);   // + the rows the engine rounds up to 8
+  }
   G.want(&h->lf.VF, n * (int64_t)M * r);
   G.want(&h->lf.LSf, (size_t)h->ls_cap);
   G.want(&h->gs.HB, n * (int64_t)M * r);
@@ -674,6 +684,8 @@ static int ensure_grad_arena(mra_handle* h) {
     for (int m = 0; m < M; ++m) { h->st.L[m] = nullptr; h->st.Ltf[m] = nullptr; }
     h->lf.VF = nullptr;
     h->lf.LSf = nullptr;
+    h->gs.SF = nullptr;
+    h->gs.SFexp = nullptr;
     return fail(MRA_ERR_OOM, "device allocation (gradient): %s", cudaGetErrorString(e));
   }
   h->have_grad_arena = true;
@@ -693,7 +705,7 @@ int mra_loglik_grad(mra_handle* h, const mra_params* theta, double* loglik_out, 
     return cuda_fail(e, "descriptor");
   if ((e = mra::launch_loglik(h->plan, h->d_desc, h->status, h->stream, &g_launches, &h->timer)))
     return cuda_fail(e, "loglik launch");
-  if ((e = mra::launch_grad(h->hd, h->d_desc, h->gs, h->d_grad, h->stream, &g_launches, &h->timer)))
+  if ((e = mra::launch_grad(h->hd, h->d_desc, h->gs, h->d_grad, h->status, h->stream, &g_launches, &h->timer)))
     return cuda_fail(e, "gradient launch");
   int hs[4];
   double vals[5];

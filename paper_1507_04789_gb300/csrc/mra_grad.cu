@@ -50,22 +50,6 @@ __device__ __forceinline__ void dcov0(const Cov& c, double x1, double y1, double
   dk = c.sigma2 * drho * gg * c.ik;
 }
 
-// Symmetric adjoint block (k, l) of region chain `anc` (ancestor index per
-// level): S^{k,l} is stored in the row of the level-max(k,l) ancestor.
-// Returns pointer and strides for B(j, kk) = S^{k,l}[kk][j].
-struct SRef {
-  const double* p;
-  long sj, sk;
-};
-__device__ __forceinline__ SRef sblock(const GradState& gs, const long* anc, int r, int k, int l) {
-  if (k >= l) {   // S^{k,l}[kk][j] = row k of ancestor k, block l
-    const long ld = (long)(k + 1) * r;
-    return {gs.Abar[k] + anc[k] * (long)r * ld + l * r, 1, ld};
-  }
-  const long ld = (long)(l + 1) * r;   // S^{k,l}[kk][j] = S^{l,k}[j][kk]
-  return {gs.Abar[l] + anc[l] * (long)r * ld + k * r, ld, 1};
-}
-
 template <int TILE>
 __device__ __forceinline__ void store_tile(const TileAcc<TILE>& acc, double* dst, long ld, int nr, int nc,
                                            double scale) {
@@ -260,7 +244,8 @@ __global__ void __launch_bounds__(NT) post_adjoint_kernel(int m, const Desc* __r
 // Leaf adjoint: one CTA per leaf.
 // ---------------------------------------------------------------------------
 template <int TILE>
-__global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict__ D, GradState gs, long slot0) {
+__global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict__ D, GradState gs, long slot0,
+                                                           int hb_ready) {
   extern __shared__ double smem[];
   const Desc& ds = D[0];
   const Shape sh = ds.sh;
@@ -307,8 +292,8 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
     double* T3 = T2 + (long)nF * nF;
     const int nrt = (nF + TILE - 1) / TILE;
     TileAcc<TILE> acc;
-    // Hbar = 2 H S_p + z omegabar'
-    for (int rt = 0; rt < nrt; ++rt) {
+    // Hbar = 2 H S_p + z omegabar' (already in HB when the emulated form formed it)
+    for (int rt = 0; rt < nrt && !hb_ready; ++rt) {
       const int nrow = min(TILE, nF - rt * TILE);
       for (int l = 0; l < M; ++l) {
         acc.zero();
@@ -650,7 +635,7 @@ static int tile_of(int r) { return r <= 16 ? 16 : (r <= 32 ? 32 : 64); }
     }                                                                                                   \
   } while (0)
 
-cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs, double* grad_out_dev,
+cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs, double* grad_out_dev, int* status,
                         cudaStream_t s, int64_t* launches, Timer* tm) {
   const int tile = tile_of(hd.sh.r);
   const int M = hd.sh.M;
@@ -667,9 +652,12 @@ cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs,
     MRA_GRAD_LAUNCH(tile, post_adjoint_kernel, dim3(st.nreg[m]), sm, s, m, d_desc, gs);
     ++*launches;
   }
+  // emulated form: Hbar on the tensor cores (when its per-parent S was allocated)
+  const int hb_ready = hd.sh.mixed == 2 && gs.SF != nullptr && M > 0;
+  if (hb_ready && (e = launch_hbar_em(hd, d_desc, gs, status, s, launches))) return e;
   {
     size_t sm = sizeof(double) * (MAXL * MAX_R_DEV + 3 * 128 + 2 * MAX_R_DEV + 32) + stg;
-    MRA_GRAD_LAUNCH(tile, leaf_adjoint_kernel, dim3(st.nreg[M]), sm, s, d_desc, gs, slot_leaf);
+    MRA_GRAD_LAUNCH(tile, leaf_adjoint_kernel, dim3(st.nreg[M]), sm, s, d_desc, gs, slot_leaf, hb_ready);
     ++*launches;
   }
   if (M > 0) {

@@ -94,7 +94,28 @@ struct GradState {
   double* XBF;          // n x (M r): adjoint of X^l_F
   double* T;            // ragged 3 n_F^2 per leaf: scratch of the leaf adjoint
   double* gpart;        // 3 per CTA: partial d/d(sigma2, kappa, tau2)
+  // emulated form only (else null): per level-(M-1) region, the full symmetric
+  // adjoint S of Ahat along its ancestor chain (M r x M r, row-major) and the
+  // scales of its rows per 128-column group, for the leaves' Hbar = 2 H S
+  double* SF;
+  int32_t* SFexp;       // [region][group][M r]
 };
+
+// Symmetric adjoint block (k, l) of region chain `anc` (ancestor index per
+// level): S^{k,l} is stored in the row of the level-max(k,l) ancestor.
+// Returns pointer and strides for B(j, kk) = S^{k,l}[kk][j].
+struct SRef {
+  const double* p;
+  long sj, sk;
+};
+__device__ __forceinline__ SRef sblock(const GradState& gs, const long* anc, int r, int k, int l) {
+  if (k >= l) {   // S^{k,l}[kk][j] = row k of ancestor k, block l
+    const long ld = (long)(k + 1) * r;
+    return {gs.Abar[k] + anc[k] * (long)r * ld + l * r, 1, ld};
+  }
+  const long ld = (long)(l + 1) * r;   // S^{k,l}[kk][j] = S^{l,k}[j][kk]
+  return {gs.Abar[l] + anc[l] * (long)r * ld + k * r, ld, 1};
+}
 
 // Prediction points of one mra_predict call, sorted by leaf.
 struct PredState {

@@ -80,8 +80,12 @@ cudaError_t launch_predict(const Desc* d_desc, int M, int r, int nlmax, const Pr
 size_t predict_smem_bytes(int r, int nlmax);
 
 // Reverse-mode gradient after a forward pass that saved L, Lt, V_F and L_Sigma.
-cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs, double* grad_out_dev,
+cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs, double* grad_out_dev, int* status,
                         cudaStream_t s, int64_t* launches, Timer* tm);
+// Emulated form: Hbar = 2 H S + z omegabar' of every leaf on the tensor cores
+// (mra_mixed.cu), from the assembled per-parent S of GradState.
+cudaError_t launch_hbar_em(const Desc& hd, const Desc* d_desc, const GradState& gs, int* status, cudaStream_t s,
+                           int64_t* launches);
 
 // Identity tables of a complete tree with M levels (for callers without host tables).
 cudaError_t launch_identity_tree(const LevelState& st, int M, cudaStream_t s, int64_t* launches);

@@ -637,6 +637,131 @@ cudaError_t launch_leaf_syrk_em(const Desc* d_desc, const int2* work, int nblock
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Gradient, emulated form: the adjoint of H_F = L_Sigma^{-1} V_F of every leaf,
+//     Hbar_F = 2 H_F S + z_F omegabar',
+// where S (M r x M r) is the symmetric adjoint of Ahat along the leaf's
+// ancestor chain and omegabar that of omegahat (Sec. 3.2 quantities in the
+// whitened basis).  S and omegabar are the same for all children of one
+// level-(M-1) region, so the product runs per parent over the parent's
+// contiguous rows of H, in tiles of 128 rows, on the emulation engine.
+// ---------------------------------------------------------------------------
+
+// One CTA per level-(M-1) region p: St_p[l r + j][k r + kk] = S^{k,l}[kk][j]
+// (the operand rows of the product, K contiguous), assembled from the row
+// blocks of the ancestors' adjoints, and the exponent of every row of St_p
+// per 128-column group (the engine's B scales).
+__global__ void __launch_bounds__(NT) s_full_kernel(const Desc* __restrict__ D, GradState gs) {
+  extern __shared__ double tile[];                       // r x (r + 1): one transposed block
+  const Desc& ds = D[0];
+  const int M = ds.sh.M, r = ds.sh.r, Mr = M * r, ng = (Mr + EM_KG - 1) / EM_KG;
+  int* sexp = reinterpret_cast<int*>(tile + r * (r + 1));   // [group][row] exponents
+  const LevelState& st = ds.st;
+  const long p = blockIdx.x;
+  const int lane = threadIdx.x & 31;
+  long anc[MAXL];
+  for (int l = 0; l < M; ++l) anc[l] = ancestor(st, M - 1, p, l);
+  for (int t = threadIdx.x; t < ng * Mr; t += NT) sexp[t] = -2000;
+  double* St = gs.SF + p * (long)Mr * Mr;
+  for (int k = 0; k < M; ++k)
+    for (int l = 0; l < M; ++l) {
+      const SRef b = sblock(gs, anc, r, k, l);   // B(j, kk) = b.p[j * b.sj + kk * b.sk]
+      const bool tr = b.sk != 1;                 // then b.sj == 1: read along j, transpose in shared memory
+      __syncthreads();                           // previous block's tile and the scale reset are done
+      if (tr)
+        for (int t = threadIdx.x; t < r * r; t += NT) {
+          const int kk = t / r, j = t - kk * r;
+          tile[kk * (r + 1) + j] = b.p[j + (long)kk * b.sk];
+        }
+      __syncthreads();
+      for (int t0 = 0; t0 < r * r; t0 += NT) {   // uniform trip count: the warp intrinsics see full warps
+        const int t = t0 + threadIdx.x;
+        const bool ok = t < r * r;
+        const int j = ok ? t / r : 0, kk = ok ? t - j * r : 0;
+        const double v = !ok ? 0.0 : tr ? tile[kk * (r + 1) + j] : b.p[(long)j * b.sj + kk];
+        const int R = l * r + j, C = k * r + kk;
+        if (ok) St[(long)R * Mr + C] = v;
+        const int key = ok ? (C / EM_KG) * Mr + R : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        const int e = __reduce_max_sync(grp, ok ? em_exp(v) : -2000);
+        if (ok && lane == __ffs(grp) - 1) atomicMax(&sexp[key], e);
+      }
+    }
+  __syncthreads();
+  int32_t* E = gs.SFexp + p * (long)ng * Mr;
+  for (int t = threadIdx.x; t < ng * Mr; t += NT) E[t] = sexp[t];
+}
+
+// Grid (level-(M-1) regions, M): column block l of Hbar for all rows under region p.
+__global__ void __launch_bounds__(NT) hbar_kernel_em(const Desc* __restrict__ D, GradState gs, int* status) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  __shared__ int rexp[EM_REXP], cexp[EM_CEXP];
+  __shared__ int hsc[EM_GMAX * TC_M];            // row scales of the current 128 rows of H per group
+  __shared__ double wb[MAX_R_DEV];               // omegabar of block l
+  const Desc& ds = D[0];
+  const int M = ds.sh.M, r = ds.sh.r, Mr = M * r, ng = (Mr + EM_KG - 1) / EM_KG;
+  const LevelState& st = ds.st;
+  const LeafState& lf = ds.lf;
+  const long p = blockIdx.x;
+  const int l = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long pm = st.mort[M - 1][p];
+  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
+  const long al = ancestor(st, M - 1, p, l);
+  for (int t = threadIdx.x; t < r; t += NT) wb[t] = gs.Obar[l][al * r + t];
+  Engine<true> eng;
+  eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
+  const double* Sl = gs.SF + p * (long)Mr * Mr + (long)l * r * Mr;
+  const int* Se = gs.SFexp + p * (long)ng * Mr + l * r;
+  TcAcc acc;
+  bool ok = true;
+  const int row = acc.row(), c0 = acc.col0();
+  for (long t0 = row0; t0 < row1 && ok; t0 += TC_M) {
+    const int na = (int)min((long)TC_M, row1 - t0);
+    const double* Ht = lf.H + t0 * Mr;
+    __syncthreads();                             // the previous tile's scales are no longer read
+    for (int i = warp; i < TC_M; i += NT / 32)
+      for (int g = 0; g < ng; ++g) {
+        int e = -2000;
+        if (i < na)
+          for (int c = g * EM_KG + lane; c < min(Mr, (g + 1) * EM_KG); c += 32) e = max(e, em_exp(Ht[(long)i * Mr + c]));
+        e = __reduce_max_sync(0xffffffffu, e);
+        if (lane == 0) hsc[g * TC_M + i] = e;
+      }
+    __syncthreads();
+    ok = eng.mma(acc, Ht, Mr, 1, na, Sl, Mr, 1, r, Mr, hsc, TC_M, Se, Mr);
+    if (ok && row < na) {
+      const double zr = lf.z[t0 + row];
+      double* out = gs.HB + (t0 + row) * Mr + l * r;
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c0 + c < r) out[c0 + c] = 2.0 * acc.v[c] + zr * wb[c0 + c];
+    }
+  }
+  eng.release();
+  if (!ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, M, p);
+}
+
+cudaError_t launch_hbar_em(const Desc& hd, const Desc* d_desc, const GradState& gs, int* status, cudaStream_t s,
+                           int64_t* launches) {
+  const int M = hd.sh.M, r = hd.sh.r;
+  const int np = hd.st.nreg[M - 1];
+  if (np == 0) return cudaSuccess;
+  cudaError_t e;
+  const int Mr = M * r;
+  const size_t sm = sizeof(double) * r * (r + 1) + sizeof(int) * ((Mr + EM_KG - 1) / EM_KG) * Mr;
+  if ((e = cudaFuncSetAttribute(s_full_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
+  s_full_kernel<<<np, NT, sm, s>>>(d_desc, gs);
+  if ((e = cudaGetLastError())) return e;
+  if ((e = cudaFuncSetAttribute(hbar_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM))) return e;
+  hbar_kernel_em<<<dim3(np, M), NT, EM_SOLO_SMEM, s>>>(d_desc, gs, status);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_aggregate_em(int m, int r, const Desc* d_desc, const int2* work, int nblocks, int* status,
                                 cudaStream_t s) {
   cudaError_t e;

@@ -48,8 +48,12 @@ def test_emu_loglik_matches_oracle(mra, name):
     assert em <= PRED_RTOL and ev <= PRED_RTOL
 
 
-def test_emu_gradient(mra):
-    w = synth.workload("n4096_exp_M3_r16")
+@pytest.mark.parametrize("name", ["n4096_exp_M3_r16", "n16k_matern15_M4_r64"])
+def test_emu_gradient(mra, name):
+    """Hbar = 2 H S + z omegabar' on the tensor cores: one 48-column group per
+    row (M r = 48), and two 128-column groups with ragged 128-row tiles of each
+    parent's rows (M r = 256)."""
+    w = synth.workload(name)
     locs, y, _ = w.generate()
     theta = np.array([w.sigma2, w.kappa, w.tau2])
     p = O.Problem(locs, y, M=w.M, r=w.r, family=w.family)
@@ -57,8 +61,27 @@ def test_emu_gradient(mra):
     with mra.Handle(locs, y, M=w.M, r=w.r, family=w.family, precision="emu") as h:
         _, g = h.loglik_grad(theta)
     rel = np.abs(g - g_o).max() / np.abs(g_o).max()
-    print(f"emu gradient max rel err {rel:.3e}")
+    print(f"{name}: emu gradient max rel err {rel:.3e}")
     assert rel <= 1e-8                                   # the FP64 form's gradient bar
+
+
+def test_emu_gradient_pruned_tree_and_memory_rule(mra):
+    """Clustered data, M = 4, r = 48: column blocks of S straddle the 128-column
+    scale groups.  On the complete tree the per-parent S would take more than
+    four times the memory of H and the leaf adjoint forms Hbar in FP64; on the
+    pruned tree (20 of 64 parents) the tensor cores form it."""
+    rng = np.random.default_rng(21)
+    locs = np.concatenate([0.25 * rng.random((1200, 2)), 0.6 + 0.4 * rng.random((1700, 2))])
+    y = synth.noisy_observations(synth.rff_field(locs, 1.5, 0.1, 1.0, 4), 0.05, 9)
+    theta = np.array([1.0, 0.1, 0.05])
+    ll_o, g_o = O.loglik_grad(O.Problem(locs, y, M=4, r=48, family="matern15"), theta)
+    for prune in (False, True):
+        with mra.Handle(locs, y, M=4, r=48, family="matern15", precision="emu", prune=prune) as h:
+            ll, g = h.loglik_grad(theta)
+        rel = np.abs(g - g_o).max() / np.abs(g_o).max()
+        print(f"prune={prune}: emu gradient max rel err {rel:.3e}")
+        assert ll == pytest.approx(ll_o, rel=LL_RTOL)
+        assert rel <= 1e-8
 
 
 def test_emu_region_terms_and_ragged(mra):
