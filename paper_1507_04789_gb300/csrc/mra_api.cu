@@ -677,6 +677,7 @@ static int ensure_grad_arena(mra_handle* h) {
   G.want(&h->gs.T, 3 * (size_t)h->ls_cap);
   int64_t slots = 0;
   for (int m = 0; m <= M; ++m) slots += nreg[m];
+  if (M > 0) slots += nreg[M - 1];   // the emulated chain adjoint's, one per level-(M-1) region
   G.want(&h->gs.gpart, 3 * slots);
   G.want(&h->d_grad, 4);
   cudaError_t e = G.commit();

@@ -341,6 +341,25 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// d C0 / d sigma2 and d C0 / d kappa at one pair of points.
+__device__ __forceinline__ void dcov0(const Cov& c, double x1, double y1, double x2, double y2, double& ds2,
+                                      double& dk) {
+  double rho, drho;   // rho(h/kappa) and kappa * d rho / d kappa
+  if (c.family == 0) {
+    const double h = dist_scaled(x1 - x2, y1 - y2, c.ik);
+    rho = exp_neg(h);
+    drho = rho * h;
+  } else {
+    const double a = dist_scaled(x1 - x2, y1 - y2, SQRT3 * c.ik);
+    const double e = exp_neg(a);
+    rho = fma(a, e, e);
+    drho = a * a * e;
+  }
+  double gg = c.nonstat ? sqrt(gvar(x1) * gvar(x2)) : 1.0;
+  ds2 = rho * gg;
+  dk = c.sigma2 * drho * gg * c.ik;
+}
+
 // Sum over the CTA; every thread gets the result.  red: 32 doubles of shared.
 __device__ __forceinline__ double block_sum(double v, double* red) {
   v = warp_sum(v);

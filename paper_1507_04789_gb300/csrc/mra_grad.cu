@@ -31,25 +31,6 @@
 
 namespace mra {
 
-// d C0 / d sigma2 and d C0 / d kappa at one pair of points.
-__device__ __forceinline__ void dcov0(const Cov& c, double x1, double y1, double x2, double y2, double& ds2,
-                                      double& dk) {
-  double rho, drho;   // rho(h/kappa) and kappa * d rho / d kappa
-  if (c.family == 0) {
-    const double h = dist_scaled(x1 - x2, y1 - y2, c.ik);
-    rho = exp_neg(h);
-    drho = rho * h;
-  } else {
-    const double a = dist_scaled(x1 - x2, y1 - y2, SQRT3 * c.ik);
-    const double e = exp_neg(a);
-    rho = fma(a, e, e);
-    drho = a * a * e;
-  }
-  double gg = c.nonstat ? sqrt(gvar(x1) * gvar(x2)) : 1.0;
-  ds2 = rho * gg;
-  dk = c.sigma2 * drho * gg * c.ik;
-}
-
 template <int TILE>
 __device__ __forceinline__ void store_tile(const TileAcc<TILE>& acc, double* dst, long ld, int nr, int nc,
                                            double scale) {
@@ -243,9 +224,11 @@ __global__ void __launch_bounds__(NT) post_adjoint_kernel(int m, const Desc* __r
 // ---------------------------------------------------------------------------
 // Leaf adjoint: one CTA per leaf.
 // ---------------------------------------------------------------------------
+// em_parts: bit 0, Hbar is already in HB; bit 1, the chain adjoint runs in
+// chain_adjoint_kernel_em (both on the emulation engine).
 template <int TILE>
 __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict__ D, GradState gs, long slot0,
-                                                           int hb_ready) {
+                                                           int em_parts) {
   extern __shared__ double smem[];
   const Desc& ds = D[0];
   const Shape sh = ds.sh;
@@ -293,7 +276,7 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
     const int nrt = (nF + TILE - 1) / TILE;
     TileAcc<TILE> acc;
     // Hbar = 2 H S_p + z omegabar' (already in HB when the emulated form formed it)
-    for (int rt = 0; rt < nrt && !hb_ready; ++rt) {
+    for (int rt = 0; rt < nrt && !(em_parts & 1); ++rt) {
       const int nrow = min(TILE, nF - rt * TILE);
       for (int l = 0; l < M; ++l) {
         acc.zero();
@@ -380,7 +363,7 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
       }
     __syncthreads();
     // chain adjoint, l = M-1..0: Xbar^l = Vbar^l Li_a ; Vbar^k -= Xbar^l V^k_a (k < l)
-    for (int l = M - 1; l >= 0; --l) {
+    for (int l = M - 1; l >= 0 && !(em_parts & 2); --l) {
       const long a = anc[l];
       const double* Lia = st.Li[l] + a * (long)r * r;
       const double* Va = st.V[l] + a * (long)r * (l * r);
@@ -653,14 +636,24 @@ cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs,
     ++*launches;
   }
   // emulated form: Hbar on the tensor cores (when its per-parent S was allocated)
-  const int hb_ready = hd.sh.mixed == 2 && gs.SF != nullptr && M > 0;
-  if (hb_ready && (e = launch_hbar_em(hd, d_desc, gs, status, s, launches))) return e;
+  const bool emu = hd.sh.mixed == 2 && M > 0;
+  const int em_parts = (emu && gs.SF != nullptr ? 1 : 0) | (emu ? 2 : 0);
+  if ((em_parts & 1) && (e = launch_hbar_em(hd, d_desc, gs, status, s, launches))) return e;
   {
     size_t sm = sizeof(double) * (MAXL * MAX_R_DEV + 3 * 128 + 2 * MAX_R_DEV + 32) + stg;
-    MRA_GRAD_LAUNCH(tile, leaf_adjoint_kernel, dim3(st.nreg[M]), sm, s, d_desc, gs, slot_leaf, hb_ready);
+    MRA_GRAD_LAUNCH(tile, leaf_adjoint_kernel, dim3(st.nreg[M]), sm, s, d_desc, gs, slot_leaf, em_parts);
     ++*launches;
   }
-  if (M > 0) {
+  // slots after the leaves': the emulated chain adjoint's, one per level-(M-1) region
+  const long slot_chain = slot_leaf + st.nreg[M];
+  if (em_parts & 2) {
+    if ((e = launch_chain_adjoint_em(hd, d_desc, gs, slot_chain, status, s))) return e;
+    ++*launches;
+  }
+  if (M > 0 && hd.sh.mixed == 2) {
+    if ((e = launch_leaf_partial_em(hd, d_desc, gs, status, s))) return e;
+    ++*launches;
+  } else if (M > 0) {
     dim3 grid(st.nreg[M - 1], M * (M + 1) / 2);
     MRA_GRAD_LAUNCH(tile, leaf_partial_kernel, grid, stg, s, d_desc, gs);
     ++*launches;
@@ -672,7 +665,7 @@ cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs,
     MRA_GRAD_LAUNCH(tile, prior_adjoint_kernel, dim3(st.nreg[m]), sm, s, m, d_desc, gs, slot);
     ++*launches;
   }
-  grad_reduce_kernel<<<1, NT, 0, s>>>(gs.gpart, slot_leaf + st.nreg[M], grad_out_dev);
+  grad_reduce_kernel<<<1, NT, 0, s>>>(gs.gpart, slot_chain + ((em_parts & 2) ? st.nreg[M - 1] : 0), grad_out_dev);
   ++*launches;
   tm->stop(s);
   return cudaGetLastError();

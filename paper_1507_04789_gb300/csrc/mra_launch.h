@@ -84,6 +84,13 @@ cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs,
                         cudaStream_t s, int64_t* launches, Timer* tm);
 // Emulated form: Hbar = 2 H S + z omegabar' of every leaf on the tensor cores
 // (mra_mixed.cu), from the assembled per-parent S of GradState.
+// Emulated form: the leaves' partial ancestor adjoints (leaf_partial_kernel's tiles).
+cudaError_t launch_leaf_partial_em(const Desc& hd, const Desc* d_desc, const GradState& gs, int* status,
+                                   cudaStream_t s);
+// Emulated form: the leaves' chain adjoint (Xbar and the Vbar updates), per parent;
+// its C0 terms go to gradient slots slot0 .. slot0 + nreg[M-1] - 1.
+cudaError_t launch_chain_adjoint_em(const Desc& hd, const Desc* d_desc, const GradState& gs, long slot0,
+                                    int* status, cudaStream_t s);
 cudaError_t launch_hbar_em(const Desc& hd, const Desc* d_desc, const GradState& gs, int* status, cudaStream_t s,
                            int64_t* launches);
 

@@ -745,6 +745,169 @@ __global__ void __launch_bounds__(NT) hbar_kernel_em(const Desc* __restrict__ D,
   if (!ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, M, p);
 }
 
+// Leaf partials on the emulation engine: for parent p and k <= l <= M-1,
+//   k < l : -sum over p's rows of Xbar^l' V^k_F,   k = l : sum of Vbar^l' V^l_F
+// (the FP64 leaf_partial_kernel's tiles).  Per column block k, the diagonal
+// tile (operand Vbar) runs alone and the tiles l > k (operand Xbar, adjacent
+// columns) are stacked em_stack(r) high.
+__host__ __device__ inline int partial_tiles(int M, int S) {
+  int n = 0;
+  for (int k = 0; k < M; ++k) n += 1 + (M - 1 - k + S - 1) / S;
+  return n;
+}
+__device__ inline bool partial_tile(int t, int M, int S, int& k, int& l0, int& nl) {
+  for (k = 0; k < M; ++k) {
+    const int nt = 1 + (M - 1 - k + S - 1) / S;
+    if (t < nt) {
+      l0 = t == 0 ? k : k + 1 + (t - 1) * S;
+      nl = t == 0 ? 1 : min(S, M - l0);
+      return true;
+    }
+    t -= nt;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(NT) leaf_partial_kernel_em(const Desc* __restrict__ D, GradState gs, int* status) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  __shared__ int rexp[EM_REXP], cexp[EM_CEXP];
+  const Desc& ds = D[0];
+  const int M = ds.sh.M, r = ds.sh.r, Mr = M * r, T = M * (M + 1) / 2;
+  const LeafState& lf = ds.lf;
+  const long p = blockIdx.x;
+  int k, l0, nl;
+  if (!partial_tile(blockIdx.y, M, em_stack(r), k, l0, nl)) return;
+  const bool diag = l0 == k;
+  const long pm = ds.st.mort[M - 1][p];
+  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
+  const int K = (int)(row1 - row0);
+  const double* A = (diag ? gs.VBF : gs.XBF) + row0 * Mr + l0 * r;
+  const double* B = lf.VF + row0 * Mr + k * r;
+  Engine<true> eng;
+  eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
+  TcAcc acc;
+  const bool ok = eng.mma(acc, A, 1, Mr, nl * r, B, 1, Mr, r, K);
+  const int row = acc.row(), c0 = acc.col0();
+  if (ok && row < nl * r) {
+    const int l = l0 + row / r, i = row % r;
+    const double sg = diag ? 1.0 : -1.0;
+    double* out = gs.PartLeaf + (p * T + tri_index(l, k)) * (long)r * r + (long)i * r;
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c0 + c < r) out[c0 + c] = sg * acc.v[c];
+  }
+  eng.release();
+  if (!ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, M - 1, p);
+}
+
+cudaError_t launch_leaf_partial_em(const Desc& hd, const Desc* d_desc, const GradState& gs, int* status,
+                                   cudaStream_t s) {
+  const int M = hd.sh.M, r = hd.sh.r;
+  const int np = hd.st.nreg[M - 1];
+  if (np == 0) return cudaSuccess;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(leaf_partial_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
+    return e;
+  leaf_partial_kernel_em<<<dim3(np, partial_tiles(M, em_stack(r))), NT, EM_SOLO_SMEM, s>>>(d_desc, gs, status);
+  return cudaGetLastError();
+}
+
+// Chain adjoint of the leaves on the emulation engine.  The forward chain
+// V^l_F = (C0(Q_F, Q_{a_l}) - sum_{k<l} V^k_F V^k_{a_l}') L_{a_l}^{-T} reverses,
+// for l = M-1..0, to
+//   Xbar^l = Vbar^l L_{a_l}^{-1}   (C0 terms: Xbar^l_{o,j} dC0(s_o, q_j)/dtheta),
+//   Vbar^k -= Xbar^l V^k_{a_l},    k < l,
+// row by row; the ancestors a_l (l < M) are shared by all children of one
+// level-(M-1) region, so one CTA takes the region's contiguous rows in tiles of
+// 128.  Its C0 terms go to gradient slot slot0 + p.
+__global__ void __launch_bounds__(NT) chain_adjoint_kernel_em(const Desc* __restrict__ D, GradState gs, long slot0,
+                                                              int* status) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  __shared__ int rexp[EM_REXP], cexp[EM_CEXP];
+  __shared__ double ax[MAX_R_DEV], ay[MAX_R_DEV], red[32];
+  const Desc& ds = D[0];
+  const Shape sh = ds.sh;
+  const Cov cv = ds.cv;
+  const int M = sh.M, r = sh.r, Mr = M * r;
+  const LevelState& st = ds.st;
+  const LeafState& lf = ds.lf;
+  const long p = blockIdx.x;
+  const long pm = st.mort[M - 1][p];
+  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
+  Engine<true> eng;
+  eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
+  TcAcc acc;
+  const int row = acc.row(), c0 = acc.col0();
+  double g_s2 = 0.0, g_k = 0.0;
+  bool ok = true;
+  for (long t0 = row0; t0 < row1 && ok; t0 += TC_M) {
+    const int na = (int)min((long)TC_M, row1 - t0);
+    double* VB = gs.VBF + t0 * Mr;
+    double* XB = gs.XBF + t0 * Mr;
+    const double so_x = row < na ? lf.xs[t0 + row] : 0.0, so_y = row < na ? lf.ys[t0 + row] : 0.0;
+    for (int l = M - 1; l >= 0 && ok; --l) {
+      const long a = ancestor(st, M - 1, p, l);
+      const double* Lia = st.Li[l] + a * (long)r * r;
+      const double* Va = st.V[l] + a * (long)r * (l * r);
+      __syncthreads();                           // the previous level's knots are no longer read
+      load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
+      __syncthreads();
+      ok = eng.mma(acc, VB + l * r, Mr, 1, na, Lia, 1, r, r, r);
+      if (ok && row < na) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int col = c0 + c;
+          if (col < r) {
+            const double xb = acc.v[c];
+            XB[(long)row * Mr + l * r + col] = xb;
+            double d1, d2;
+            dcov0(cv, so_x, so_y, ax[col], ay[col], d1, d2);
+            g_s2 = fma(xb, d1, g_s2);
+            g_k = fma(xb, d2, g_k);
+          }
+        }
+      }
+      // (the next product's scale pass opens with a barrier: Xbar^l is complete)
+      for (int k = 0; k < l && ok; ++k) {
+        ok = eng.mma(acc, XB + l * r, Mr, 1, na, Va + k * r, 1, l * r, r, r);
+        if (ok && row < na) {
+          double* out = VB + (long)row * Mr + k * r;
+#pragma unroll
+          for (int c = 0; c < 32; ++c)
+            if (c0 + c < r) out[c0 + c] -= acc.v[c];
+        }
+      }
+    }
+  }
+  eng.release();
+  g_s2 = block_sum(g_s2, red);
+  g_k = block_sum(g_k, red);
+  if (threadIdx.x == 0) {
+    gs.gpart[3 * (slot0 + p) + 0] = g_s2;
+    gs.gpart[3 * (slot0 + p) + 1] = g_k;
+    gs.gpart[3 * (slot0 + p) + 2] = 0.0;
+    if (!ok) flag_error(status, ST_TIMEOUT, M - 1, p);
+  }
+}
+
+cudaError_t launch_chain_adjoint_em(const Desc& hd, const Desc* d_desc, const GradState& gs, long slot0,
+                                    int* status, cudaStream_t s) {
+  const int M = hd.sh.M;
+  const int np = hd.st.nreg[M - 1];
+  if (np == 0) return cudaSuccess;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(chain_adjoint_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
+    return e;
+  chain_adjoint_kernel_em<<<np, NT, EM_SOLO_SMEM, s>>>(d_desc, gs, slot0, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_hbar_em(const Desc& hd, const Desc* d_desc, const GradState& gs, int* status, cudaStream_t s,
                            int64_t* launches) {
   const int M = hd.sh.M, r = hd.sh.r;
