@@ -48,6 +48,10 @@ constexpr int EM_STAGE_BYTES = 2 * 2 * EM_BUF_HALFS;                    // two b
 constexpr int EM_REXP = EM_MAXG * TC_M;       // ints of row scales of A (shared)
 constexpr int EM_CEXP = EM_MAXG * TC_N;       // ints of row scales of B (shared)
 constexpr uint32_t EM_TMEM_COLS = 512;
+// The engine takes all 512 TMEM columns of an SM; its kernels ask for more than
+// half of the SM's shared memory so that a second CTA is never resident (it
+// would only wait in tcgen05.alloc).
+constexpr size_t EM_SOLO_SMEM = 116 * 1024;
 static_assert(EM_KG * EM_S * 127 * 127 < (1 << 24), "group sums must stay exact in FP32");
 static_assert(EM_S * TC_N <= (int)EM_TMEM_COLS, "accumulators exceed the tensor-memory allocation");
 // kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, 128 x 64.

@@ -27,6 +27,7 @@
 // sum Cbar_ij dC0_ij/dtheta, with dC0/dsigma2 = C0 / sigma2 and dC0/dkappa in
 // closed form for both families.  Sums over children and rows are in a fixed
 // order: the gradient is deterministic.
+#include "mra_emu.cuh"
 #include "mra_launch.h"
 
 namespace mra {
@@ -225,11 +226,18 @@ __global__ void __launch_bounds__(NT) post_adjoint_kernel(int m, const Desc* __r
 // Leaf adjoint: one CTA per leaf.
 // ---------------------------------------------------------------------------
 // em_parts: bit 0, Hbar is already in HB; bit 1, the chain adjoint runs in
-// chain_adjoint_kernel_em (both on the emulation engine).
-template <int TILE>
+// chain_adjoint_kernel_em (both on the emulation engine).  EMU: the products
+// LSi' Hbar, Hbar V_F' and Sigmabar V_F run on the emulation engine (its
+// staging buffers open the dynamic shared memory); a timeout sets status.
+template <int TILE, bool EMU>
 __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict__ D, GradState gs, long slot0,
-                                                           int em_parts) {
-  extern __shared__ double smem[];
+                                                           int em_parts, int* status) {
+  extern __shared__ __align__(1024) double smem_all[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  __shared__ int rexp[EMU ? EM_REXP : 1], cexp[EMU ? EM_CEXP : 1];
+  double* smem = smem_all + (EMU ? EM_STAGE_BYTES / sizeof(double) : 0);
   const Desc& ds = D[0];
   const Shape sh = ds.sh;
   const Cov cv = ds.cv;
@@ -249,6 +257,18 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
   double* red = ay + MAX_R_DEV;
   double* stg = red + 32;
   double g_s2 = 0.0, g_k = 0.0, g_t = 0.0;
+  EmCtx cx;
+  bool ok = true;
+  if (EMU) {
+    cx.stage = reinterpret_cast<uint16_t*>(smem_all);
+    cx.rexp = rexp;
+    cx.cexp = cexp;
+    cx.mbar = mbar;
+    cx.fail = &fail;
+    em_init(cx, &tmem_slot);
+  }
+  TcAcc ea;                                  // EMU: the engine's accumulator
+  const int erow = ea.row(), ec0 = ea.col0();
   if (nF > 0) {
     long anc[MAXL];
     for (int l = 0; l < M; ++l) anc[l] = ancestor(st, M, F, l);
@@ -304,7 +324,16 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
     }
     __syncthreads();
     // Vbar_F = LSi' Hbar
-    for (int l = 0; l < M; ++l)
+    for (int l = 0; l < M && EMU && ok; ++l) {
+      ok = em_mma(cx, ea, LSi, 1, nF, nF, HB + l * r, 1, Mr, r, nF);
+      if (ok && erow < nF) {
+        double* out = VB + (long)erow * Mr + l * r;
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (ec0 + c < r) out[ec0 + c] = ea.v[c];
+      }
+    }
+    for (int l = 0; l < M && !EMU; ++l)
       for (int rt = 0; rt < nrt; ++rt) {
         const int nrow = min(TILE, nF - rt * TILE);
         acc.zero();
@@ -312,7 +341,18 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
         store_tile<TILE>(acc, VB + (long)rt * TILE * Mr + l * r, Mr, nrow, r, 1.0);
       }
     // LSibar = lower(Hbar V_F' + zbar y')  -> T1
-    for (int bi = 0; bi < nrt; ++bi)
+    for (int j0 = 0; j0 < nF && EMU && ok; j0 += TC_N) {
+      const int nb = min(TC_N, nF - j0);
+      ok = em_mma(cx, ea, HB, Mr, 1, nF, VF + (long)j0 * Mr, Mr, 1, nb, Mr);
+      if (ok && erow < nF) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int j = j0 + ec0 + c;
+          if (ec0 + c < nb) T1[(long)erow * nF + j] = erow >= j ? ea.v[c] + zb[erow] * yv[j] : 0.0;
+        }
+      }
+    }
+    for (int bi = 0; bi < nrt && !EMU; ++bi)
       for (int bj = 0; bj <= bi; ++bj) {
         const int ni = min(TILE, nF - bi * TILE), nj = min(TILE, nF - bj * TILE);
         acc.zero();
@@ -348,7 +388,16 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
       if (a == b) g_t += sb;
     }
     // Vbar_F -= 2 Sigmabar V_F
-    for (int l = 0; l < M; ++l)
+    for (int l = 0; l < M && EMU && ok; ++l) {
+      ok = em_mma(cx, ea, T3, nF, 1, nF, VF + l * r, 1, Mr, r, nF);
+      if (ok && erow < nF) {
+        double* out = VB + (long)erow * Mr + l * r;
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (ec0 + c < r) out[ec0 + c] -= 2.0 * ea.v[c];
+      }
+    }
+    for (int l = 0; l < M && !EMU; ++l)
       for (int rt = 0; rt < nrt; ++rt) {
         const int nrow = min(TILE, nF - rt * TILE);
         acc.zero();
@@ -406,9 +455,11 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
         }
     }
   }
+  if (EMU) em_release(cx);
   g_s2 = block_sum(g_s2, red);
   g_k = block_sum(g_k, red);
   g_t = block_sum(g_t, red);
+  if (EMU && !ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, M, F);
   if (threadIdx.x == 0) {
     gs.gpart[3 * (slot0 + F) + 0] = g_s2;
     gs.gpart[3 * (slot0 + F) + 1] = g_k;
@@ -618,6 +669,26 @@ static int tile_of(int r) { return r <= 16 ? 16 : (r <= 32 ? 32 : 64); }
     }                                                                                                   \
   } while (0)
 
+template <bool EMU>
+static cudaError_t launch_leaf_adjoint(int tile, int nleaves, size_t sm, cudaStream_t s, const Desc* d_desc,
+                                       const GradState& gs, long slot0, int em_parts, int* status) {
+  cudaError_t e;
+#define MRA_LEAF_ADJ(T)                                                                                       \
+  if ((e = cudaFuncSetAttribute(leaf_adjoint_kernel<T, EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                (int)sm)))                                                                    \
+    return e;                                                                                                 \
+  leaf_adjoint_kernel<T, EMU><<<nleaves, NT, sm, s>>>(d_desc, gs, slot0, em_parts, status);
+  if (tile == 16) {
+    MRA_LEAF_ADJ(16)
+  } else if (tile == 32) {
+    MRA_LEAF_ADJ(32)
+  } else {
+    MRA_LEAF_ADJ(64)
+  }
+#undef MRA_LEAF_ADJ
+  return cudaGetLastError();
+}
+
 cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs, double* grad_out_dev, int* status,
                         cudaStream_t s, int64_t* launches, Timer* tm) {
   const int tile = tile_of(hd.sh.r);
@@ -641,7 +712,14 @@ cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs,
   if ((em_parts & 1) && (e = launch_hbar_em(hd, d_desc, gs, status, s, launches))) return e;
   {
     size_t sm = sizeof(double) * (MAXL * MAX_R_DEV + 3 * 128 + 2 * MAX_R_DEV + 32) + stg;
-    MRA_GRAD_LAUNCH(tile, leaf_adjoint_kernel, dim3(st.nreg[M]), sm, s, d_desc, gs, slot_leaf, em_parts);
+    if (emu) {
+      sm += EM_STAGE_BYTES;
+      if (sm < EM_SOLO_SMEM) sm = EM_SOLO_SMEM;
+      e = launch_leaf_adjoint<true>(tile, st.nreg[M], sm, s, d_desc, gs, slot_leaf, em_parts, status);
+    } else {
+      e = launch_leaf_adjoint<false>(tile, st.nreg[M], sm, s, d_desc, gs, slot_leaf, em_parts, status);
+    }
+    if (e) return e;
     ++*launches;
   }
   // slots after the leaves': the emulated chain adjoint's, one per level-(M-1) region

@@ -573,10 +573,6 @@ __global__ void __launch_bounds__(NT) aggregate_kernel_em(int m, const Desc* __r
   if (!ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, m - 1, p);
 }
 
-// The emulation engine takes 512 TMEM columns, all of an SM's; its kernels ask
-// for more than half of the SM's shared memory so that a second CTA is never
-// resident (it would only wait in tcgen05.alloc).
-constexpr size_t EM_SOLO_SMEM = 116 * 1024;
 
 template <bool EMU>
 static size_t prior_tc_smem() {
