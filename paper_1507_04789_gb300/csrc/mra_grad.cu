@@ -137,7 +137,8 @@ __device__ void chol_inverse_adjoint(double* B0, double* B1, double* B2, long ld
 // Posterior adjoint, level m (top-down).
 // ---------------------------------------------------------------------------
 template <int TILE>
-__global__ void __launch_bounds__(NT) post_adjoint_kernel(int m, const Desc* __restrict__ D, GradState gs) {
+__global__ void __launch_bounds__(NT) post_adjoint_kernel(int m, const Desc* __restrict__ D, GradState gs,
+                                                          int gb_ready) {
   extern __shared__ double smem[];
   const Desc& ds = D[0];
   const Shape sh = ds.sh;
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(NT) post_adjoint_kernel(int m, const Desc* __r
   // Gbar^l = -2 sum_k G^k S^{k,l} - g omega~bar^l'   -> gs.GB
   double* GB = gs.GB[m] + i * (long)r * mr;
   TileAcc<TILE> acc;
-  for (int l = 0; l < m; ++l) {
+  for (int l = 0; l < m && !gb_ready; ++l) {   // (gb_ready: formed by gbar_kernel_em)
     acc.zero();
     for (int k = 0; k < m; ++k) {
       SRef b = sblock(gs, anc, r, k, l);
@@ -701,13 +702,16 @@ cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs,
   long slot_leaf = 0;
   for (int m = 0; m < M; ++m) slot_leaf += st.nreg[m];
   tm->start(6, s);
+  const bool emu = hd.sh.mixed == 2 && M > 0;
   for (int m = 0; m < M; ++m) {
+    // emulated form with the per-region S buffer: Gbar on the tensor cores first
+    const int gb_ready = emu && gs.SF != nullptr && m > 0;
+    if (gb_ready && (e = launch_gbar_em(m, hd, d_desc, gs, status, s, launches))) return e;
     size_t sm = sizeof(double) * (MAXL * MAX_R_DEV + MAX_R_DEV) + sq + stg;
-    MRA_GRAD_LAUNCH(tile, post_adjoint_kernel, dim3(st.nreg[m]), sm, s, m, d_desc, gs);
+    MRA_GRAD_LAUNCH(tile, post_adjoint_kernel, dim3(st.nreg[m]), sm, s, m, d_desc, gs, gb_ready);
     ++*launches;
   }
   // emulated form: Hbar on the tensor cores (when its per-parent S was allocated)
-  const bool emu = hd.sh.mixed == 2 && M > 0;
   const int em_parts = (emu && gs.SF != nullptr ? 1 : 0) | (emu ? 2 : 0);
   if ((em_parts & 1) && (e = launch_hbar_em(hd, d_desc, gs, status, s, launches))) return e;
   {

@@ -91,6 +91,10 @@ cudaError_t launch_leaf_partial_em(const Desc& hd, const Desc* d_desc, const Gra
 // its C0 terms go to gradient slots slot0 .. slot0 + nreg[M-1] - 1.
 cudaError_t launch_chain_adjoint_em(const Desc& hd, const Desc* d_desc, const GradState& gs, long slot0,
                                     int* status, cudaStream_t s);
+// Emulated form: Gbar of level m (1 <= m < M) per level-(m-1) region, from its
+// assembled S (mra_mixed.cu); post_adjoint_kernel then skips its own product.
+cudaError_t launch_gbar_em(int m, const Desc& hd, const Desc* d_desc, const GradState& gs, int* status,
+                           cudaStream_t s, int64_t* launches);
 cudaError_t launch_hbar_em(const Desc& hd, const Desc* d_desc, const GradState& gs, int* status, cudaStream_t s,
                            int64_t* launches);
 

@@ -643,20 +643,20 @@ cudaError_t launch_leaf_syrk_em(const Desc* d_desc, const int2* work, int nblock
 // contiguous rows of H, in tiles of 128 rows, on the emulation engine.
 // ---------------------------------------------------------------------------
 
-// One CTA per level-(M-1) region p: St_p[l r + j][k r + kk] = S^{k,l}[kk][j]
-// (the operand rows of the product, K contiguous), assembled from the row
-// blocks of the ancestors' adjoints, and the exponent of every row of St_p
-// per 128-column group (the engine's B scales).
-__global__ void __launch_bounds__(NT) s_full_kernel(const Desc* __restrict__ D, GradState gs) {
+// One CTA per region p of level L: St_p[l r + j][k r + kk] = S^{k,l}[kk][j],
+// k, l <= L (the operand rows of the products with S, K contiguous), assembled
+// from the row blocks of the adjoints of p and its ancestors, and the exponent
+// of every row of St_p per 128-column group (the engine's B scales).
+__global__ void __launch_bounds__(NT) s_full_kernel(int L, const Desc* __restrict__ D, GradState gs) {
   extern __shared__ double tile[];                       // r x (r + 1): one transposed block
   const Desc& ds = D[0];
-  const int M = ds.sh.M, r = ds.sh.r, Mr = M * r, ng = (Mr + EM_KG - 1) / EM_KG;
+  const int M = L + 1, r = ds.sh.r, Mr = M * r, ng = (Mr + EM_KG - 1) / EM_KG;
   int* sexp = reinterpret_cast<int*>(tile + r * (r + 1));   // [group][row] exponents
   const LevelState& st = ds.st;
   const long p = blockIdx.x;
   const int lane = threadIdx.x & 31;
   long anc[MAXL];
-  for (int l = 0; l < M; ++l) anc[l] = ancestor(st, M - 1, p, l);
+  for (int l = 0; l < M; ++l) anc[l] = ancestor(st, L, p, l);
   for (int t = threadIdx.x; t < ng * Mr; t += NT) sexp[t] = -2000;
   double* St = gs.SF + p * (long)Mr * Mr;
   for (int k = 0; k < M; ++k)
@@ -904,19 +904,91 @@ cudaError_t launch_chain_adjoint_em(const Desc& hd, const Desc* d_desc, const Gr
   return cudaGetLastError();
 }
 
+// St of every region of level L into gs.SF / gs.SFexp.
+static cudaError_t launch_s_full(int L, const Desc& hd, const Desc* d_desc, const GradState& gs, cudaStream_t s) {
+  const int r = hd.sh.r, Mr = (L + 1) * r;
+  const size_t sm = sizeof(double) * r * (r + 1) + sizeof(int) * ((Mr + EM_KG - 1) / EM_KG) * Mr;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(s_full_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
+  s_full_kernel<<<hd.st.nreg[L], NT, sm, s>>>(L, d_desc, gs);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_hbar_em(const Desc& hd, const Desc* d_desc, const GradState& gs, int* status, cudaStream_t s,
                            int64_t* launches) {
-  const int M = hd.sh.M, r = hd.sh.r;
+  const int M = hd.sh.M;
   const int np = hd.st.nreg[M - 1];
   if (np == 0) return cudaSuccess;
   cudaError_t e;
-  const int Mr = M * r;
-  const size_t sm = sizeof(double) * r * (r + 1) + sizeof(int) * ((Mr + EM_KG - 1) / EM_KG) * Mr;
-  if ((e = cudaFuncSetAttribute(s_full_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-  s_full_kernel<<<np, NT, sm, s>>>(d_desc, gs);
-  if ((e = cudaGetLastError())) return e;
+  if ((e = launch_s_full(M - 1, hd, d_desc, gs, s))) return e;
   if ((e = cudaFuncSetAttribute(hbar_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM))) return e;
   hbar_kernel_em<<<dim3(np, M), NT, EM_SOLO_SMEM, s>>>(d_desc, gs, status);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+// Gbar of level m (1 <= m < M) on the emulation engine:
+//     Gbar^l = -2 sum_k G^k S^{k,l} - g omegabar^l',  l < m,
+// for all children of each level-(m-1) region P at once (they share P's chain
+// S and omegabar; their rows of G are contiguous), from St_P assembled first.
+__global__ void __launch_bounds__(NT) gbar_kernel_em(int m, const Desc* __restrict__ D, GradState gs, int* status) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  __shared__ int rexp[EM_REXP], cexp[EM_CEXP];
+  __shared__ int gsc[EM_GMAX * TC_M];            // row scales of the current 128 rows of G per group
+  __shared__ double wb[MAX_R_DEV];
+  const Desc& ds = D[0];
+  const int r = ds.sh.r, mr = m * r, ng = (mr + EM_KG - 1) / EM_KG;
+  const LevelState& st = ds.st;
+  const long P = blockIdx.x;
+  const int l = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long row0 = (long)st.cfirst[m - 1][P] * r, row1 = row0 + (long)st.ccnt[m - 1][P] * r;
+  const long al = ancestor(st, m - 1, P, l);
+  for (int t = threadIdx.x; t < r; t += NT) wb[t] = gs.Obar[l][al * r + t];
+  Engine<true> eng;
+  eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
+  const double* Sl = gs.SF + P * (long)mr * mr + (long)l * r * mr;
+  const int* Se = gs.SFexp + P * (long)ng * mr + l * r;
+  TcAcc acc;
+  bool ok = true;
+  const int row = acc.row(), c0 = acc.col0();
+  for (long t0 = row0; t0 < row1 && ok; t0 += TC_M) {
+    const int na = (int)min((long)TC_M, row1 - t0);
+    const double* Gt = st.G[m] + t0 * mr;
+    __syncthreads();                             // the previous tile's scales are no longer read
+    for (int i = warp; i < TC_M; i += NT / 32)
+      for (int g = 0; g < ng; ++g) {
+        int e = -2000;
+        if (i < na)
+          for (int c = g * EM_KG + lane; c < min(mr, (g + 1) * EM_KG); c += 32) e = max(e, em_exp(Gt[(long)i * mr + c]));
+        e = __reduce_max_sync(0xffffffffu, e);
+        if (lane == 0) gsc[g * TC_M + i] = e;
+      }
+    __syncthreads();
+    ok = eng.mma(acc, Gt, mr, 1, na, Sl, mr, 1, r, mr, gsc, TC_M, Se, mr);
+    if (ok && row < na) {
+      const double gr = st.gv[m][t0 + row];
+      double* out = gs.GB[m] + (t0 + row) * mr + l * r;
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c0 + c < r) out[c0 + c] = -2.0 * acc.v[c] - gr * wb[c0 + c];
+    }
+  }
+  eng.release();
+  if (!ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, m, P);
+}
+
+cudaError_t launch_gbar_em(int m, const Desc& hd, const Desc* d_desc, const GradState& gs, int* status,
+                           cudaStream_t s, int64_t* launches) {
+  const int np = hd.st.nreg[m - 1];
+  if (np == 0) return cudaSuccess;
+  cudaError_t e;
+  if ((e = launch_s_full(m - 1, hd, d_desc, gs, s))) return e;
+  if ((e = cudaFuncSetAttribute(gbar_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM))) return e;
+  gbar_kernel_em<<<dim3(np, m), NT, EM_SOLO_SMEM, s>>>(m, d_desc, gs, status);
   *launches += 2;
   return cudaGetLastError();
 }
