@@ -338,6 +338,8 @@ def main():
     ap.add_argument("--oracle-reps", type=int, default=1)
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-dataset swath batch")
     ap.add_argument("--batch-datasets", type=int, default=64)
+    ap.add_argument("--grad-only", action="store_true",
+                    help="time only loglik + gradient in the emulated form (the launch list of the gradient)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -366,6 +368,27 @@ def main():
     stream = torch.cuda.Stream()
     # thetas vary per step (an MLE-like sweep over the range parameter)
     thetas = [(theta0[0], theta0[1] * (1.0 + 0.01 * (k % 7)), theta0[2]) for k in range(args.warmup + args.steps)]
+
+    if args.grad_only:
+        with mra.Handle(locs, y, M=w.M, r=w.r, family=w.family, precision="emu") as h:
+            h.set_stream(stream)
+            for k in range(args.warmup):
+                h.loglik_grad(thetas[k])
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(args.warmup, args.warmup + args.steps):
+                ll, g = h.loglik_grad(thetas[k])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+        if rank == 0:
+            print(json.dumps({"metric": "M-RA loglik + grad evals/s (emulated FP64 forward and adjoint)",
+                              "value": 1e3 / ms, "unit": "evals/s", "ms_per_step": ms, "steps": args.steps,
+                              "warmup": args.warmup, "config": {"workload": args.workload},
+                              "grad": [float(v) for v in g]}))
+        return
 
     def barrier():
         if world > 1:

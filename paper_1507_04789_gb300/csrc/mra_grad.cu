@@ -133,6 +133,55 @@ __device__ void chol_inverse_adjoint(double* B0, double* B1, double* B2, long ld
   __syncthreads();
 }
 
+// The same chain with its five n x n products on the emulation engine (n <=
+// 128; B0..B2 may live in global or shared memory).  Returns false (uniformly)
+// if a tensor-core wait timed out; the buffers are then incomplete.
+__device__ inline bool em_store_product(EmCtx& cx, const double* A, long sai, long sak, const double* B, long sbj,
+                                        long sbk, int n, double* C, long ldc, double scale) {
+  TcAcc acc;
+  const int row = acc.row(), c0 = acc.col0();
+  for (int j0 = 0; j0 < n; j0 += TC_N) {
+    const int nb = min(TC_N, n - j0);
+    if (!em_mma(cx, acc, A, sai, sak, n, B + (long)j0 * sbj, sbj, sbk, nb, n)) return false;
+    if (row < n) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c0 + c < nb) C[(long)row * ldc + j0 + c0 + c] = scale * acc.v[c];
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
+__device__ inline bool chol_inverse_adjoint_em(EmCtx& cx, double* B0, double* B1, double* B2, long ld, int n,
+                                               const double* L, long ldl, const double* Li, long ldi, double dlog) {
+  // B1 = Ybar Li'
+  if (!em_store_product(cx, B0, ld, 1, Li, ldi, 1, n, B1, ld, 1.0)) return false;
+  // B2 = lower(-Li' B1) + dlog / L_ii
+  if (!em_store_product(cx, Li, 1, ldi, B1, 1, ld, n, B2, ld, -1.0)) return false;
+  lower_inplace(B2, n, ld);
+  if (dlog != 0.0)
+    for (int t = threadIdx.x; t < n; t += NT) B2[t * ld + t] += dlog / L[t * ldl + t];
+  __syncthreads();
+  // B0 = Phi(L' B2)
+  if (!em_store_product(cx, L, 1, ldl, B2, 1, ld, n, B0, ld, 1.0)) return false;
+  phi_inplace(B0, n, ld);
+  // B1 = B0 Li
+  if (!em_store_product(cx, B0, ld, 1, Li, 1, ldi, n, B1, ld, 1.0)) return false;
+  // B2 = Li' B1, then symmetrise in place
+  if (!em_store_product(cx, Li, 1, ldi, B1, 1, ld, n, B2, ld, 1.0)) return false;
+  for (int t = threadIdx.x; t < n * n; t += NT) {
+    int i = t / n, j = t - i * n;
+    if (j < i) {
+      double v = 0.5 * (B2[i * ld + j] + B2[j * ld + i]);
+      B2[i * ld + j] = v;
+      B2[j * ld + i] = v;
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
 // ---------------------------------------------------------------------------
 // Posterior adjoint, level m (top-down).
 // ---------------------------------------------------------------------------
@@ -377,7 +426,11 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
       }
     __syncthreads();
     // Cholesky/inverse adjoint of Sigma_F in the leaf's global scratch: T3 = Sigmabar
-    chol_inverse_adjoint<TILE>(T1, T2, T3, nF, nF, LSf, nF, LSi, nF, -1.0, stg);
+    if (EMU) {
+      if (ok) ok = chol_inverse_adjoint_em(cx, T1, T2, T3, nF, nF, LSf, nF, LSi, nF, -1.0);
+    } else {
+      chol_inverse_adjoint<TILE>(T1, T2, T3, nF, nF, LSf, nF, LSi, nF, -1.0, stg);
+    }
     // T3 = Sigmabar (symmetric): C0 and tau2 terms
     for (int t = threadIdx.x; t < nF * nF; t += NT) {
       int a = t / nF, b = t - a * nF;
