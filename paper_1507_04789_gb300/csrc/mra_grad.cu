@@ -27,6 +27,8 @@
 // sum Cbar_ij dC0_ij/dtheta, with dC0/dsigma2 = C0 / sigma2 and dC0/dkappa in
 // closed form for both families.  Sums over children and rows are in a fixed
 // order: the gradient is deterministic.
+#include <algorithm>
+
 #include "mra_emu.cuh"
 #include "mra_launch.h"
 
@@ -553,10 +555,18 @@ __global__ void __launch_bounds__(NT) leaf_partial_kernel(const Desc* __restrict
 // ---------------------------------------------------------------------------
 // Prior adjoint, level m (bottom-up): one CTA per region.
 // ---------------------------------------------------------------------------
-template <int TILE>
+// EMU: every r x r x r product (and the Cholesky/inverse adjoint) runs on the
+// emulation engine, whose staging buffers open the dynamic shared memory; a
+// timeout sets status.
+template <int TILE, bool EMU>
 __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __restrict__ D, GradState gs,
-                                                           long slot0) {
-  extern __shared__ double smem[];
+                                                           long slot0, int* status) {
+  extern __shared__ __align__(1024) double smem_all[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  __shared__ int rexp[EMU ? EM_REXP : 1], cexp[EMU ? EM_CEXP : 1];
+  double* smem = smem_all + (EMU ? EM_STAGE_BYTES / sizeof(double) : 0);
   const Desc& ds = D[0];
   const Shape sh = ds.sh;
   const Cov cv = ds.cv;
@@ -584,6 +594,40 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
     for (long c = cf; c < cf + cc; ++c) s += gs.Up[m + 1][(c * Tin + t) * (long)r * r + a * r + b];
     return s;
   };
+  EmCtx cx;
+  bool ok = true;
+  if (EMU) {
+    cx.stage = reinterpret_cast<uint16_t*>(smem_all);
+    cx.rexp = rexp;
+    cx.cexp = cexp;
+    cx.mbar = mbar;
+    cx.fail = &fail;
+    em_init(cx, &tmem_slot);
+  }
+  TileAcc<TILE> acc;
+  TcAcc ea;
+  // f(i, j, P(i, j)) for the r x r product P(i, j) = sum_{c < kk} A(i, c) B(j, c)
+  auto product = [&](const double* A, long sai, long sak, const double* B, long sbj, long sbk, int kk, auto&& f) {
+    if constexpr (EMU) {
+      if (ok) ok = em_mma(cx, ea, A, sai, sak, r, B, sbj, sbk, r, kk);
+      const int row = ea.row(), c0 = ea.col0();
+      if (ok && row < r) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (c0 + c < r) f(row, c0 + c, ea.v[c]);
+      }
+    } else {
+      acc.zero();
+      tile_mma<TILE>(acc, A, sai, sak, r, B, sbj, sbk, r, kk, stg);
+#pragma unroll
+      for (int p = 0; p < TileAcc<TILE>::RM; ++p)
+#pragma unroll
+        for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
+          const int row = acc.row(p), col = acc.col(q);
+          if (row < r && col < r) f(row, col, acc.v[p][q]);
+        }
+    }
+  };
   double g_s2 = 0.0, g_k = 0.0;
   load_knots(sh.bbox, m, st.mort[m][i], sh.gx, sh.gy, qx, qy);
   const double* L = st.L[m] + i * (long)r * r;
@@ -595,18 +639,13 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
     B1[a * ld + b] = incoming(m, m, a, b);
   }
   __syncthreads();
-  TileAcc<TILE> acc;
-  acc.zero();
-  tile_mma<TILE>(acc, B1, ld, 1, r, L, r, 1, r, r, stg);
-#pragma unroll
-  for (int p = 0; p < TileAcc<TILE>::RM; ++p)
-#pragma unroll
-    for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
-      int row = acc.row(p), col = acc.col(q);
-      if (row < r && col < r) B0[row * ld + col] = row >= col ? acc.v[p][q] : 0.0;
-    }
+  product(B1, ld, 1, L, r, 1, r, [&](int row, int col, double v) { B0[row * ld + col] = row >= col ? v : 0.0; });
   __syncthreads();
-  chol_inverse_adjoint<TILE>(B0, B1, B2, ld, r, L, r, Li, r, 0.0, stg);   // B2 = Wbar
+  if (EMU) {
+    if (ok) ok = chol_inverse_adjoint_em(cx, B0, B1, B2, ld, r, L, r, Li, r, 0.0);   // B2 = Wbar
+  } else {
+    chol_inverse_adjoint<TILE>(B0, B1, B2, ld, r, L, r, Li, r, 0.0, stg);
+  }
   for (int t = threadIdx.x; t < r * r; t += NT) {
     int a = t / r, b = t - a * r;
     double d1, d2;
@@ -617,17 +656,10 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
   double* VB = gs.VB[m] + i * (long)r * mr;
   double* XB = gs.XB[m] + i * (long)r * mr;
   // Vbar^k = incoming(m, k) - 2 Wbar V^k
-  for (int k = 0; k < m; ++k) {
-    acc.zero();
-    tile_mma<TILE>(acc, B2, ld, 1, r, V + k * r, 1, mr, r, r, stg);
-#pragma unroll
-    for (int p = 0; p < TileAcc<TILE>::RM; ++p)
-#pragma unroll
-      for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
-        int row = acc.row(p), col = acc.col(q);
-        if (row < r && col < r) VB[(long)row * mr + k * r + col] = incoming(m, k, row, col) - 2.0 * acc.v[p][q];
-      }
-  }
+  for (int k = 0; k < m; ++k)
+    product(B2, ld, 1, V + k * r, 1, mr, r, [&](int row, int col, double v) {
+      VB[(long)row * mr + k * r + col] = incoming(m, k, row, col) - 2.0 * v;
+    });
   // chain adjoint
   for (int l = m - 1; l >= 0; --l) {
     const long a = ancestor(st, m, i, l);
@@ -636,34 +668,17 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
     __syncthreads();
     load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
     __syncthreads();
-    acc.zero();
-    tile_mma<TILE>(acc, VB + l * r, mr, 1, r, Lia, 1, r, r, r, stg);
-#pragma unroll
-    for (int p = 0; p < TileAcc<TILE>::RM; ++p)
-#pragma unroll
-      for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
-        int row = acc.row(p), col = acc.col(q);
-        if (row < r && col < r) {
-          double xb = acc.v[p][q];
-          XB[(long)row * mr + l * r + col] = xb;
-          double d1, d2;
-          dcov0(cv, qx[row], qy[row], ax[col], ay[col], d1, d2);
-          g_s2 = fma(xb, d1, g_s2);
-          g_k = fma(xb, d2, g_k);
-        }
-      }
+    product(VB + l * r, mr, 1, Lia, 1, r, r, [&](int row, int col, double xb) {
+      XB[(long)row * mr + l * r + col] = xb;
+      double d1, d2;
+      dcov0(cv, qx[row], qy[row], ax[col], ay[col], d1, d2);
+      g_s2 = fma(xb, d1, g_s2);
+      g_k = fma(xb, d2, g_k);
+    });
     __syncthreads();
-    for (int k = 0; k < l; ++k) {
-      acc.zero();
-      tile_mma<TILE>(acc, XB + l * r, mr, 1, r, Va + k * r, 1, l * r, r, r, stg);
-#pragma unroll
-      for (int p = 0; p < TileAcc<TILE>::RM; ++p)
-#pragma unroll
-        for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
-          int row = acc.row(p), col = acc.col(q);
-          if (row < r && col < r) VB[(long)row * mr + k * r + col] -= acc.v[p][q];
-        }
-    }
+    for (int k = 0; k < l; ++k)
+      product(XB + l * r, mr, 1, Va + k * r, 1, l * r, r,
+              [&](int row, int col, double v) { VB[(long)row * mr + k * r + col] -= v; });
   }
   __syncthreads();
   // partial sums passed up: tiles (l, k), k <= l < m
@@ -672,26 +687,21 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
     double* Up = gs.Up[m] + i * (long)Tup * r * r;
     for (int l = 0; l < m; ++l)
       for (int k = 0; k <= l; ++k) {
-        acc.zero();
         const double* Ab = (k < l ? XB : VB) + l * r;
-        tile_mma<TILE>(acc, Ab, 1, mr, r, V + k * r, 1, mr, r, r, stg);
         double* out = Up + (long)tri_index(l, k) * r * r;
         const double sgn = k < l ? -1.0 : 1.0;
-#pragma unroll
-        for (int p = 0; p < TileAcc<TILE>::RM; ++p)
-#pragma unroll
-          for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
-            int row = acc.row(p), col = acc.col(q);
-            if (row < r && col < r) out[row * r + col] = incoming(l, k, row, col) + sgn * acc.v[p][q];
-          }
+        product(Ab, 1, mr, V + k * r, 1, mr, r,
+                [&](int row, int col, double v) { out[row * r + col] = incoming(l, k, row, col) + sgn * v; });
       }
   }
+  if (EMU) em_release(cx);
   g_s2 = block_sum(g_s2, red);
   g_k = block_sum(g_k, red);
   if (threadIdx.x == 0) {
     gs.gpart[3 * (slot0 + i) + 0] = g_s2;
     gs.gpart[3 * (slot0 + i) + 1] = g_k;
     gs.gpart[3 * (slot0 + i) + 2] = 0.0;
+    if (EMU && !ok) flag_error(status, ST_TIMEOUT, m, i);
   }
 }
 
@@ -740,6 +750,26 @@ static cudaError_t launch_leaf_adjoint(int tile, int nleaves, size_t sm, cudaStr
     MRA_LEAF_ADJ(64)
   }
 #undef MRA_LEAF_ADJ
+  return cudaGetLastError();
+}
+
+template <bool EMU>
+static cudaError_t launch_prior_adjoint(int tile, int m, int nregions, size_t sm, cudaStream_t s,
+                                        const Desc* d_desc, const GradState& gs, long slot0, int* status) {
+  cudaError_t e;
+#define MRA_PRIOR_ADJ(T)                                                                                      \
+  if ((e = cudaFuncSetAttribute(prior_adjoint_kernel<T, EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                (int)sm)))                                                                    \
+    return e;                                                                                                 \
+  prior_adjoint_kernel<T, EMU><<<nregions, NT, sm, s>>>(m, d_desc, gs, slot0, status);
+  if (tile == 16) {
+    MRA_PRIOR_ADJ(16)
+  } else if (tile == 32) {
+    MRA_PRIOR_ADJ(32)
+  } else {
+    MRA_PRIOR_ADJ(64)
+  }
+#undef MRA_PRIOR_ADJ
   return cudaGetLastError();
 }
 
@@ -796,8 +826,11 @@ cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs,
   long slot = slot_leaf;
   for (int m = M - 1; m >= 0; --m) {
     slot -= st.nreg[m];
-    size_t sm = sizeof(double) * (4 * MAX_R_DEV + 32) + sq + stg;
-    MRA_GRAD_LAUNCH(tile, prior_adjoint_kernel, dim3(st.nreg[m]), sm, s, m, d_desc, gs, slot);
+    const size_t sm = sizeof(double) * (4 * MAX_R_DEV + 32) + sq;
+    if (emu) e = launch_prior_adjoint<true>(tile, m, st.nreg[m], std::max(sm + EM_STAGE_BYTES, EM_SOLO_SMEM), s,
+                                            d_desc, gs, slot, status);
+    else e = launch_prior_adjoint<false>(tile, m, st.nreg[m], sm + stg, s, d_desc, gs, slot, status);
+    if (e) return e;
     ++*launches;
   }
   grad_reduce_kernel<<<1, NT, 0, s>>>(gs.gpart, slot_chain + ((em_parts & 2) ? st.nreg[M - 1] : 0), grad_out_dev);
