@@ -480,8 +480,11 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   B.want(&LS, (size_t)tail);
   B.want(&d, nreg[M]);
   B.want(&u, nreg[M]);
-  int32_t* hcol = nullptr;
-  if (cfg->precision == MRA_PREC_EMU) B.want(&hcol, nreg[M] * (int64_t)M * r);
+  int32_t *hcol = nullptr, *hrow = nullptr;
+  if (cfg->precision == MRA_PREC_EMU) {
+    B.want(&hcol, nreg[M] * (int64_t)M * r);
+    B.want(&hrow, n * (int64_t)((M * r + 127) / 128));
+  }
   B.want(&h->d_desc, 1);
   h->ls_cap = tail;
   if ((e = B.commit())) { mra_free(h); return fail(MRA_ERR_OOM, "device allocation (factors): %s", cudaGetErrorString(e)); }
@@ -506,6 +509,7 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   h->lf.d = d;
   h->lf.u = u;
   h->lf.hcol = hcol;
+  h->lf.hrow = hrow;
   single_plan(h);
   size_t need = cfg->precision != MRA_PREC_FP64 ? mra::leaf_tc_smem_bytes(h->nlmax, cfg->precision == MRA_PREC_EMU)
                                                  : mra::leaf_smem_bytes(r, h->nlmax);

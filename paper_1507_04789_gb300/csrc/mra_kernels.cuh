@@ -78,6 +78,8 @@ struct LeafState {
   double* LSf;            // ragged n_F x n_F: L_Sigma
   // column scales of H_F over the leaf's rows for the emulation engine (else null)
   int32_t* hcol;          // per active leaf x (M r)
+  // row scales of V_F per 128-column group from the emulated chain kernel (else null)
+  int32_t* hrow;          // n x ceil(M r / 128)
 };
 
 // Adjoint state of the gradient pass (mra_grad.cu).

@@ -67,7 +67,7 @@ size_t leaf_smem_bytes(int r, int nlmax);
 cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nblocks, int emu, int* status,
                             cudaStream_t s);
 cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int emu, int* status,
-                           cudaStream_t s);
+                           cudaStream_t s, const int2* w_par = nullptr, int n_par = 0);
 size_t leaf_tc_smem_bytes(int nlmax, int emu);
 cudaError_t launch_leaf_syrk_em(const Desc* d_desc, const int2* work, int nblocks, int maxM, int r, int* status,
                                 cudaStream_t s);

@@ -485,7 +485,11 @@ cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaS
   if (pl.n_leaf > 0) {
     tm->start(1, s);
     if (pl.mixed) {
-      if ((e = launch_leaf_tc(d_desc, pl.w_leaf, pl.n_leaf, pl.nlmax, pl.mixed == 2, status, s))) return e;
+      // (the emulated form's chain kernel runs per level-(M-1) region: the leaf_syrk work list)
+      if ((e = launch_leaf_tc(d_desc, pl.w_leaf, pl.n_leaf, pl.nlmax, pl.mixed == 2, status, s, pl.w_syrk,
+                              pl.n_syrk)))
+        return e;
+      if (pl.mixed == 2 && pl.n_syrk > 0) ++*launches;   // the chain kernel
     } else {
       MRA_LAUNCH(tile, leaf_kernel, pl.n_leaf, leaf_smem(tile, pl.nlmax), s, d_desc, pl.w_leaf, status);
     }

@@ -208,9 +208,116 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
   }
 }
 
+// Leaf chain of the emulated form, per level-(M-1) region P over the
+// contiguous rows of its children in 128-row tiles (their ancestors' V and
+// L^{-1} are the same, so one split of those serves up to 128 rows):
+//   V^l_F = (C0(S_F, Q_l) - sum_{k<l} V^k_F V^k_{R_l}') L_l^{-T},  l = 0..M-1,
+// written to H, with the row scales of every 128-column group exported to
+// lf.hrow for the leaf kernel.
+__global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __restrict__ D,
+                                                              const int2* __restrict__ work, int* status) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  __shared__ int rexp[EM_REXP], cexp[EM_CEXP];
+  __shared__ int hsc[EM_GMAX * TC_M], xsc[TC_M];
+  __shared__ double sx[TC_M], sy[TC_M], ax[MAX_R_DEV], ay[MAX_R_DEV];
+  const Item it = work_item(work);
+  const Desc& ds = D[it.d];
+  const Shape sh = ds.sh;
+  const Cov cv = ds.cv;
+  const LevelState& st = ds.st;
+  const LeafState& lf = ds.lf;
+  const int M = sh.M, r = sh.r, Mr = M * r, ng = (Mr + EM_KG - 1) / EM_KG;
+  const long P = it.i;
+  const long pm = st.mort[M - 1][P];
+  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
+  Engine<true> eng;
+  eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
+  TcAcc acc;
+  bool ok = true;
+  const int row = acc.row(), c0 = acc.col0();
+  for (long t0 = row0; t0 < row1 && ok; t0 += TC_M) {
+    const int na = (int)min((long)TC_M, row1 - t0);
+    double* Hrow = lf.H + t0 * Mr;
+    __syncthreads();                             // the previous tile's points and scales are no longer read
+    for (int t = threadIdx.x; t < na; t += NT) {
+      sx[t] = lf.xs[t0 + t];
+      sy[t] = lf.ys[t0 + t];
+    }
+    for (int t = threadIdx.x; t < EM_GMAX * TC_M; t += NT) hsc[t] = -2000;
+    for (int l = 0; l < M && ok; ++l) {
+      const long a = ancestor(st, M - 1, P, l);
+      __syncthreads();
+      load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
+      const double* Vanc = st.V[l] + a * (long)r * (l * r);
+      for (int t = threadIdx.x; t < TC_M; t += NT) xsc[t] = -2000;
+      __syncthreads();
+      // C0(S_F, Q_l) into block l (the product below reads only blocks < l)
+      for (int t = threadIdx.x; t < na * r; t += NT) {
+        const int fi = t / r, qj = t - fi * r;
+        const double v = cov0(cv, sx[fi], sy[fi], ax[qj], ay[qj]);
+        Hrow[(long)fi * Mr + l * r + qj] = v;
+        if (l == 0) atomicMax(xsc + fi, xexp_of(v));
+      }
+      acc.zero();
+      __syncthreads();
+      if (l > 0) {
+        const int* vsa = st.vexp[l] + a * (long)((l * r + 127) / 128) * r;
+        ok = eng.mma(acc, Hrow, Mr, 1, na, Vanc, l * r, 1, r, l * r, hsc, TC_M, vsa, r);
+        if (!ok) break;
+        if (row < na) {
+          int e = -2000;
+#pragma unroll
+          for (int c = 0; c < 32; ++c) {
+            const int col = c0 + c;
+            if (col < r) {
+              const double v = Hrow[(long)row * Mr + l * r + col] - acc.v[c];
+              Hrow[(long)row * Mr + l * r + col] = v;
+              e = max(e, xexp_of(v));
+            }
+          }
+          atomicMax(xsc + row, e);
+        }
+      }
+      __syncthreads();
+      acc.zero();
+      ok = eng.mma(acc, Hrow + l * r, Mr, 1, na, st.Li[l] + a * (long)r * r, r, 1, r, r, xsc, 0,
+                   st.liexp[l] + a * r, 0);
+      if (!ok) break;
+      if (row < na) {
+        int e0 = -2000, e1 = -2000;       // a thread's 32 columns touch at most two groups
+        const int gbase = (l * r + c0) / 128;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int col = c0 + c;
+          if (col < r) {
+            Hrow[(long)row * Mr + l * r + col] = acc.v[c];
+            const int e = xexp_of(acc.v[c]);
+            if ((l * r + col) / 128 == gbase) e0 = max(e0, e);
+            else e1 = max(e1, e);
+          }
+        }
+        atomicMax(hsc + gbase * TC_M + row, e0);
+        if (e1 > -2000) atomicMax(hsc + (gbase + 1) * TC_M + row, e1);
+      }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < na * ng; t += NT) {
+      const int i = t / ng, g = t - i * ng;
+      lf.hrow[(t0 + i) * ng + g] = hsc[g * TC_M + i];
+    }
+  }
+  eng.release();
+  if (!ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, M - 1, P);
+}
+
+// chain_done (emulated form): V_F and its row scales were formed by
+// chain_forward_kernel_em; the kernel starts at Sigma_F.
 template <bool EMU>
 __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D, const int2* __restrict__ work,
-                                                     int* status) {
+                                                     int* status, int chain_done) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
@@ -258,8 +365,16 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
   TcAcc acc;
   bool ok = true;
   const int row = acc.row(), c0 = acc.col0();
+  if (EMU && chain_done) {
+    const int ng = (Mr + EM_KG - 1) / EM_KG;
+    __syncthreads();                             // after the reset of hsc above
+    for (int t = threadIdx.x; t < nF * ng; t += NT) {
+      const int i = t / ng, g = t - i * ng;
+      hsc[g * TC_M + i] = lf.hrow[(o0 + i) * ng + g];
+    }
+  }
   // chain: V^l_F = (C0(S_F, Q_l) - sum_{k<l} V^k_F V^k_{R_l}') L_l^{-T}  (one 128-row tile)
-  for (int l = 0; l < M && ok; ++l) {
+  for (int l = 0; l < M && ok && !(EMU && chain_done); ++l) {
     const long a = ancestor(st, M, F, l);
     __syncthreads();
     load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
@@ -610,16 +725,25 @@ cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nbl
 }
 
 cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int emu, int* status,
-                           cudaStream_t s) {
+                           cudaStream_t s, const int2* w_par, int n_par) {
   cudaError_t e;
   if (emu) {
+    // the chain per parent first (work list: the level-(M-1) regions of every dataset)
+    const int chain_done = n_par > 0;
+    if (chain_done) {
+      if ((e = cudaFuncSetAttribute(chain_forward_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    EM_SOLO_SMEM)))
+        return e;
+      chain_forward_kernel_em<<<n_par, NT, EM_SOLO_SMEM, s>>>(d_desc, w_par, status);
+      if ((e = cudaGetLastError())) return e;
+    }
     const size_t sm = leaf_tc_smem<true>(nlmax);
     if ((e = cudaFuncSetAttribute(leaf_kernel_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-    leaf_kernel_tc<true><<<nblocks, NT, sm, s>>>(d_desc, work, status);
+    leaf_kernel_tc<true><<<nblocks, NT, sm, s>>>(d_desc, work, status, chain_done);
   } else {
     const size_t sm = leaf_tc_smem<false>(nlmax);
     if ((e = cudaFuncSetAttribute(leaf_kernel_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-    leaf_kernel_tc<false><<<nblocks, NT, sm, s>>>(d_desc, work, status);
+    leaf_kernel_tc<false><<<nblocks, NT, sm, s>>>(d_desc, work, status, 0);
   }
   return cudaGetLastError();
 }
