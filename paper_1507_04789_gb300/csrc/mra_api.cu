@@ -668,6 +668,7 @@ static int ensure_grad_arena(mra_handle* h) {
   // Hbar in FP64 from the ancestors' blocks directly)
   h->gs.SF = nullptr;
   h->gs.SFexp = nullptr;
+  h->gs.DC = nullptr;
   if (M > 0 && h->cfg.precision == MRA_PREC_EMU && (int64_t)nreg[M - 1] * M * r <= 4 * n) {
     const int64_t Mr = (int64_t)M * r;
     G.want(&h->gs.SF, (int64_t)nreg[M - 1] * Mr * Mr);
@@ -676,6 +677,7 @@ static int ensure_grad_arena(mra_handle* h) {
   G.want(&h->lf.VF, n * (int64_t)M * r);
   G.want(&h->lf.LSf, (size_t)h->ls_cap);
   G.want(&h->gs.HB, n * (int64_t)M * r);
+  if (h->cfg.precision == MRA_PREC_EMU && M > 0) G.want(&h->gs.DC, 2 * n * (int64_t)M * r);
   G.want(&h->gs.VBF, n * (int64_t)M * r);
   G.want(&h->gs.XBF, n * (int64_t)M * r);
   G.want(&h->gs.T, 3 * (size_t)h->ls_cap);
@@ -691,6 +693,7 @@ static int ensure_grad_arena(mra_handle* h) {
     h->lf.LSf = nullptr;
     h->gs.SF = nullptr;
     h->gs.SFexp = nullptr;
+    h->gs.DC = nullptr;
     return fail(MRA_ERR_OOM, "device allocation (gradient): %s", cudaGetErrorString(e));
   }
   h->have_grad_arena = true;
@@ -706,7 +709,10 @@ int mra_loglik_grad(mra_handle* h, const mra_params* theta, double* loglik_out, 
   if (rc) return rc;
   h->have_post = false;
   cudaError_t e;
-  if ((e = upload_desc(h, theta)) || (e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream)))
+  h->lf.dc = h->gs.DC;                 // the chain kernel stores its C0 derivatives (emulated form)
+  e = upload_desc(h, theta);
+  h->lf.dc = nullptr;                  // (the descriptor was copied: later loglik calls store nothing)
+  if (e || (e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream)))
     return cuda_fail(e, "descriptor");
   if ((e = mra::launch_loglik(h->plan, h->d_desc, h->status, h->stream, &g_launches, &h->timer)))
     return cuda_fail(e, "loglik launch");

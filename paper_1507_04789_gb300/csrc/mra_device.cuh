@@ -360,6 +360,29 @@ __device__ __forceinline__ void dcov0(const Cov& c, double x1, double y1, double
   dk = c.sigma2 * drho * gg * c.ik;
 }
 
+// C0 at one pair of points (rounded exactly as cov0) and, from the same
+// exponential, dcov0's two derivatives (rounded exactly as dcov0).
+__device__ __forceinline__ double cov0_d(const Cov& c, double x1, double y1, double x2, double y2, double& ds2,
+                                         double& dk) {
+  double rho, drho;
+  if (c.family == 0) {
+    const double h = dist_scaled(x1 - x2, y1 - y2, c.ik);
+    rho = exp_neg(h);
+    drho = rho * h;
+  } else {
+    const double a = dist_scaled(x1 - x2, y1 - y2, SQRT3 * c.ik);
+    const double e = exp_neg(a);
+    rho = fma(a, e, e);
+    drho = a * a * e;
+  }
+  const double gg = c.nonstat ? sqrt(gvar(x1) * gvar(x2)) : 1.0;
+  ds2 = rho * gg;
+  dk = c.sigma2 * drho * gg * c.ik;
+  double v = c.sigma2 * rho;
+  if (c.nonstat) v *= gg;
+  return v;
+}
+
 // Sum over the CTA; every thread gets the result.  red: 32 doubles of shared.
 __device__ __forceinline__ double block_sum(double v, double* red) {
   v = warp_sum(v);

@@ -80,6 +80,10 @@ struct LeafState {
   int32_t* hcol;          // per active leaf x (M r)
   // row scales of V_F per 128-column group from the emulated chain kernel (else null)
   int32_t* hrow;          // n x ceil(M r / 128)
+  // set for gradient calls of the emulated form only: the chain kernel stores,
+  // for every C0(s_o, q_j) of the chain blocks, (dC0/dsigma2, dC0/dkappa) at
+  // [o][l r + j][2], which the chain adjoint then reads
+  double* dc;             // n x (M r) x 2
 };
 
 // Adjoint state of the gradient pass (mra_grad.cu).
@@ -96,6 +100,7 @@ struct GradState {
   double* XBF;          // n x (M r): adjoint of X^l_F
   double* T;            // ragged 3 n_F^2 per leaf: scratch of the leaf adjoint
   double* gpart;        // 3 per CTA: partial d/d(sigma2, kappa, tau2)
+  double* DC;           // emulated form: n x (M r) x 2 derivative pairs of the leaf chain's C0 blocks
   // emulated form only (else null): per level-(M-1) region, the full symmetric
   // adjoint S of Ahat along its ancestor chain (M r x M r, row-major) and the
   // scales of its rows per 128-column group, for the leaves' Hbar = 2 H S

@@ -254,10 +254,18 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
       const double* Vanc = st.V[l] + a * (long)r * (l * r);
       for (int t = threadIdx.x; t < TC_M; t += NT) xsc[t] = -2000;
       __syncthreads();
-      // C0(S_F, Q_l) into block l (the product below reads only blocks < l)
+      // C0(S_F, Q_l) into block l (the product below reads only blocks < l); in
+      // gradient calls with its two derivatives
       for (int t = threadIdx.x; t < na * r; t += NT) {
         const int fi = t / r, qj = t - fi * r;
-        const double v = cov0(cv, sx[fi], sy[fi], ax[qj], ay[qj]);
+        double v;
+        if (lf.dc) {
+          double d1, d2;
+          v = cov0_d(cv, sx[fi], sy[fi], ax[qj], ay[qj], d1, d2);
+          *reinterpret_cast<double2*>(lf.dc + 2 * ((t0 + fi) * Mr + l * r + qj)) = make_double2(d1, d2);
+        } else {
+          v = cov0(cv, sx[fi], sy[fi], ax[qj], ay[qj]);
+        }
         Hrow[(long)fi * Mr + l * r + qj] = v;
         if (l == 0) atomicMax(xsc + fi, xexp_of(v));
       }
@@ -987,7 +995,13 @@ __global__ void __launch_bounds__(NT) chain_adjoint_kernel_em(const Desc* __rest
             const double xb = acc.v[c];
             XB[(long)row * Mr + l * r + col] = xb;
             double d1, d2;
-            dcov0(cv, so_x, so_y, ax[col], ay[col], d1, d2);
+            if (lf.dc) {   // stored by the forward chain kernel
+              const double2 dd = *reinterpret_cast<const double2*>(lf.dc + 2 * ((t0 + row) * Mr + l * r + col));
+              d1 = dd.x;
+              d2 = dd.y;
+            } else {
+              dcov0(cv, so_x, so_y, ax[col], ay[col], d1, d2);
+            }
             g_s2 = fma(xb, d1, g_s2);
             g_k = fma(xb, d2, g_k);
           }
