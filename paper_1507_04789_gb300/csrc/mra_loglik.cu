@@ -11,6 +11,7 @@
 //   post_level   m = M-1..0  Cholesky of I + Ahat^{m,m}, G, g, d_R, u_R (Sec. 3.3)
 //   aggregate    m = M-1..1  Atilde = Ahat - G' G summed into the parent (Eqs.
 //                            mainquantities, helpquantities), omega likewise
+#include "mra_emu.cuh"
 #include "mra_kernels.cuh"
 #include "mra_launch.h"
 
@@ -294,10 +295,27 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel(const Desc* __restrict__ 
 // g = Lt^{-1} omegahat^m; d_R = sum_children d + 2 sum log diag Lt;
 // u_R = sum_children u - g'g  (Sec. 3.3 in whitened form).
 // ---------------------------------------------------------------------------
-template <int TILE>
+// EMU: the products G^l = Lt^{-1} Ahat^{m,l} on the emulation engine (its
+// staging buffers open the dynamic shared memory).
+template <int TILE, bool EMU>
 __global__ void __launch_bounds__(NT) post_level_kernel(int m, const Desc* __restrict__ D,
                                                         const int2* __restrict__ work, int* status) {
-  extern __shared__ double smem[];
+  extern __shared__ __align__(1024) double smem_all[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  __shared__ int rexp[EMU ? EM_REXP : 1], cexp[EMU ? EM_CEXP : 1];
+  double* smem = smem_all + (EMU ? EM_STAGE_BYTES / sizeof(double) : 0);
+  EmCtx cx;
+  bool ok = true;
+  if (EMU) {
+    cx.stage = reinterpret_cast<uint16_t*>(smem_all);
+    cx.rexp = rexp;
+    cx.cexp = cexp;
+    cx.mbar = mbar;
+    cx.fail = &fail;
+    em_init(cx, &tmem_slot);
+  }
   const Item it = work_item(work);
   const Desc& ds = D[it.d];
   const Shape sh = ds.sh;
@@ -345,18 +363,32 @@ __global__ void __launch_bounds__(NT) post_level_kernel(int m, const Desc* __res
   gg = block_sum(gg, red);
   // G^l = Lt^{-1} Ahat^{m,l}, l < m.  Ahat^{m,l}(a, b) is stored row-major.
   double* Gr = st.G[m] + i * (long)r * mr;
-  TileAcc<TILE> acc;
-  for (int l = 0; l < m; ++l) {
-    const double* Aml = A + (long)tri_index(m, l) * r * r;
-    acc.zero();
-    tile_mma<TILE>(acc, W, ldw, 1, r, Aml, 1, r, r, r, stg);
+  if constexpr (EMU) {
+    TcAcc ea;
+    const int row = ea.row(), c0 = ea.col0();
+    for (int l = 0; l < m && ok; ++l) {
+      const double* Aml = A + (long)tri_index(m, l) * r * r;
+      ok = em_mma(cx, ea, W, ldw, 1, r, Aml, 1, r, r, r);
+      if (ok && row < r) {
 #pragma unroll
-    for (int a = 0; a < TileAcc<TILE>::RM; ++a)
-#pragma unroll
-      for (int b = 0; b < TileAcc<TILE>::RM; ++b) {
-        int row = acc.row(a), col = acc.col(b);
-        if (row < r && col < r) Gr[(long)row * mr + l * r + col] = acc.v[a][b];
+        for (int c = 0; c < 32; ++c)
+          if (c0 + c < r) Gr[(long)row * mr + l * r + c0 + c] = ea.v[c];
       }
+    }
+  } else {
+    TileAcc<TILE> acc;
+    for (int l = 0; l < m; ++l) {
+      const double* Aml = A + (long)tri_index(m, l) * r * r;
+      acc.zero();
+      tile_mma<TILE>(acc, W, ldw, 1, r, Aml, 1, r, r, r, stg);
+#pragma unroll
+      for (int a = 0; a < TileAcc<TILE>::RM; ++a)
+#pragma unroll
+        for (int b = 0; b < TileAcc<TILE>::RM; ++b) {
+          int row = acc.row(a), col = acc.col(b);
+          if (row < r && col < r) Gr[(long)row * mr + l * r + col] = acc.v[a][b];
+        }
+    }
   }
   if (st.gcol[m]) {   // emulation: column scales of G over its r rows, for the aggregation above
     __syncthreads();
@@ -376,6 +408,10 @@ __global__ void __launch_bounds__(NT) post_level_kernel(int m, const Desc* __res
     st.dd[m][i] = dsum + ld;
     st.uu[m][i] = usum - gg;
     if (bad) flag_error(status, ST_NOT_PD, m, i);
+  }
+  if (EMU) {
+    em_release(cx);
+    if (!ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, m, i);
   }
 }
 
@@ -465,6 +501,32 @@ static size_t syrk_smem(int tile) { return sizeof(double) * 2 * KC * (tile + 2);
   } while (0)
 
 
+static cudaError_t launch_post_level(bool emu, int tile, int m, int nblocks, cudaStream_t s, const Desc* d_desc,
+                                     const int2* work, int* status) {
+  cudaError_t e;
+  size_t sm = post_smem(tile);
+  if (emu) {
+    sm += EM_STAGE_BYTES;
+    if (sm < EM_SOLO_SMEM) sm = EM_SOLO_SMEM;
+  }
+#define MRA_POST(T, EMU)                                                                                  \
+  {                                                                                                       \
+    if ((e = cudaFuncSetAttribute(post_level_kernel<T, EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  (int)sm)))                                                              \
+      return e;                                                                                           \
+    post_level_kernel<T, EMU><<<nblocks, NT, sm, s>>>(m, d_desc, work, status);                           \
+  }
+  if (tile == 16) {
+    if (emu) MRA_POST(16, true) else MRA_POST(16, false)
+  } else if (tile == 32) {
+    if (emu) MRA_POST(32, true) else MRA_POST(32, false)
+  } else {
+    if (emu) MRA_POST(64, true) else MRA_POST(64, false)
+  }
+#undef MRA_POST
+  return cudaGetLastError();
+}
+
 cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaStream_t s, int64_t* launches,
                           Timer* tm) {
   const int tile = pl.tile;
@@ -511,7 +573,7 @@ cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaS
   for (int m = pl.maxM - 1; m >= 0; --m) {
     if (pl.n_lvl[m] > 0) {
       tm->start(3, s);
-      MRA_LAUNCH(tile, post_level_kernel, pl.n_lvl[m], post_smem(tile), s, m, d_desc, pl.w_lvl[m], status);
+      if ((e = launch_post_level(pl.mixed == 2, tile, m, pl.n_lvl[m], s, d_desc, pl.w_lvl[m], status))) return e;
       tm->stop(s);
       ++*launches;
     }

@@ -495,18 +495,33 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
     zz = block_sum(zz, red);
     // H^l = L_Sigma^{-1} V^l_F (whole block read before it is overwritten)
     int32_t* hcol = EMU ? lf.hcol + F * (long)Mr : nullptr;   // column scales of H_F for the Gram kernel
-    if (EMU)
+    if (EMU) {
       for (int t = threadIdx.x; t < Mr; t += NT) hcol[t] = -2000;
+      // hsc (the V_F row scales) is read no more: it collects the row scales of H_F
+      for (int t = threadIdx.x; t < EM_GMAX * TC_M; t += NT) hsc[t] = -2000;
+    }
     for (int l = 0; l < M && ok; ++l) {
       acc.zero();
       ok = eng.mma(acc, S, lds, 1, nF, Hrow + l * r, 1, Mr, r, nF, EMU ? ssc : nullptr, 0);
       if (!ok) break;
-      if (row < nF)
+      if (row < nF) {
+        int e0 = -2000, e1 = -2000;       // a thread's 32 columns touch at most two groups
+        const int gbase = (l * r + c0) / 128;
         #pragma unroll
         for (int c = 0; c < 32; ++c) {
           const int col = c0 + c;
-          if (col < r) Hrow[(long)row * Mr + l * r + col] = acc.v[c];
+          if (col < r) {
+            Hrow[(long)row * Mr + l * r + col] = acc.v[c];
+            const int e = xexp_of(acc.v[c]);
+            if ((l * r + col) / 128 == gbase) e0 = max(e0, e);
+            else e1 = max(e1, e);
+          }
         }
+        if (EMU) {
+          atomicMax(hsc + gbase * TC_M + row, e0);
+          if (e1 > -2000) atomicMax(hsc + (gbase + 1) * TC_M + row, e1);
+        }
+      }
       if (EMU && ((threadIdx.x >> 5) & 3) * 32 < nF) {   // warp-uniform: the warp holds a kept row
         const int lane = threadIdx.x & 31;
         #pragma unroll
@@ -516,6 +531,13 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
         }
       }
       __syncthreads();
+    }
+    if (EMU && lf.hrow && ok) {   // row scales of H_F per 128-column group (the gradient's Hbar operand)
+      const int ng = (Mr + EM_KG - 1) / EM_KG;
+      for (int t = threadIdx.x; t < nF * ng; t += NT) {
+        const int i = t / ng, g = t - i * ng;
+        lf.hrow[(o0 + i) * ng + g] = hsc[g * TC_M + i];
+      }
     }
   }
   eng.release();
@@ -851,14 +873,22 @@ __global__ void __launch_bounds__(NT) hbar_kernel_em(const Desc* __restrict__ D,
     const int na = (int)min((long)TC_M, row1 - t0);
     const double* Ht = lf.H + t0 * Mr;
     __syncthreads();                             // the previous tile's scales are no longer read
-    for (int i = warp; i < TC_M; i += NT / 32)
-      for (int g = 0; g < ng; ++g) {
-        int e = -2000;
-        if (i < na)
-          for (int c = g * EM_KG + lane; c < min(Mr, (g + 1) * EM_KG); c += 32) e = max(e, em_exp(Ht[(long)i * Mr + c]));
-        e = __reduce_max_sync(0xffffffffu, e);
-        if (lane == 0) hsc[g * TC_M + i] = e;
+    if (lf.hrow) {                               // exported by the leaf kernel
+      for (int t = threadIdx.x; t < TC_M * ng; t += NT) {
+        const int i = t / ng, g = t - i * ng;
+        hsc[g * TC_M + i] = i < na ? lf.hrow[(t0 + i) * ng + g] : -2000;
       }
+    } else {
+      for (int i = warp; i < TC_M; i += NT / 32)
+        for (int g = 0; g < ng; ++g) {
+          int e = -2000;
+          if (i < na)
+            for (int c = g * EM_KG + lane; c < min(Mr, (g + 1) * EM_KG); c += 32)
+              e = max(e, em_exp(Ht[(long)i * Mr + c]));
+          e = __reduce_max_sync(0xffffffffu, e);
+          if (lane == 0) hsc[g * TC_M + i] = e;
+        }
+    }
     __syncthreads();
     ok = eng.mma(acc, Ht, Mr, 1, na, Sl, Mr, 1, r, Mr, hsc, TC_M, Se, Mr);
     if (ok && row < na) {
