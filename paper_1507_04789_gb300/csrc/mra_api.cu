@@ -669,6 +669,7 @@ static int ensure_grad_arena(mra_handle* h) {
   h->gs.SF = nullptr;
   h->gs.SFexp = nullptr;
   h->gs.DC = nullptr;
+  h->gs.VFexp = h->gs.VBexp = h->gs.XBexp = nullptr;
   if (M > 0 && h->cfg.precision == MRA_PREC_EMU && (int64_t)nreg[M - 1] * M * r <= 4 * n) {
     const int64_t Mr = (int64_t)M * r;
     G.want(&h->gs.SF, (int64_t)nreg[M - 1] * Mr * Mr);
@@ -677,7 +678,12 @@ static int ensure_grad_arena(mra_handle* h) {
   G.want(&h->lf.VF, n * (int64_t)M * r);
   G.want(&h->lf.LSf, (size_t)h->ls_cap);
   G.want(&h->gs.HB, n * (int64_t)M * r);
-  if (h->cfg.precision == MRA_PREC_EMU && M > 0) G.want(&h->gs.DC, 2 * n * (int64_t)M * r);
+  if (h->cfg.precision == MRA_PREC_EMU && M > 0) {
+    G.want(&h->gs.DC, 2 * n * (int64_t)M * r);
+    G.want(&h->gs.VFexp, (int64_t)nreg[M - 1] * 4 * M * r);
+    G.want(&h->gs.VBexp, (int64_t)nreg[M - 1] * 4 * M * r);
+    G.want(&h->gs.XBexp, (int64_t)nreg[M - 1] * 4 * M * r);
+  }
   G.want(&h->gs.VBF, n * (int64_t)M * r);
   G.want(&h->gs.XBF, n * (int64_t)M * r);
   G.want(&h->gs.T, 3 * (size_t)h->ls_cap);
@@ -694,6 +700,7 @@ static int ensure_grad_arena(mra_handle* h) {
     h->gs.SF = nullptr;
     h->gs.SFexp = nullptr;
     h->gs.DC = nullptr;
+    h->gs.VFexp = h->gs.VBexp = h->gs.XBexp = nullptr;
     return fail(MRA_ERR_OOM, "device allocation (gradient): %s", cudaGetErrorString(e));
   }
   h->have_grad_arena = true;
@@ -710,8 +717,10 @@ int mra_loglik_grad(mra_handle* h, const mra_params* theta, double* loglik_out, 
   h->have_post = false;
   cudaError_t e;
   h->lf.dc = h->gs.DC;                 // the chain kernel stores its C0 derivatives (emulated form)
+  h->lf.vfexp = h->gs.VFexp;           // and the column scales of V_F per tile
   e = upload_desc(h, theta);
   h->lf.dc = nullptr;                  // (the descriptor was copied: later loglik calls store nothing)
+  h->lf.vfexp = nullptr;
   if (e || (e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream)))
     return cuda_fail(e, "descriptor");
   if ((e = mra::launch_loglik(h->plan, h->d_desc, h->status, h->stream, &g_launches, &h->timer)))

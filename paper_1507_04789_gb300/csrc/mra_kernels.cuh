@@ -84,6 +84,9 @@ struct LeafState {
   // for every C0(s_o, q_j) of the chain blocks, (dC0/dsigma2, dC0/dkappa) at
   // [o][l r + j][2], which the chain adjoint then reads
   double* dc;             // n x (M r) x 2
+  // set for gradient calls of the emulated form only: the exponent (|x| < 2^e)
+  // of every column of V_F over each 128-row tile of a level-(M-1) region's rows
+  int32_t* vfexp;         // per level-(M-1) region x 4 tiles x (M r)
 };
 
 // Adjoint state of the gradient pass (mra_grad.cu).
@@ -101,6 +104,13 @@ struct GradState {
   double* T;            // ragged 3 n_F^2 per leaf: scratch of the leaf adjoint
   double* gpart;        // 3 per CTA: partial d/d(sigma2, kappa, tau2)
   double* DC;           // emulated form: n x (M r) x 2 derivative pairs of the leaf chain's C0 blocks
+  // emulated form: column exponents per 128-row tile of each level-(M-1)
+  // region's rows (region x 4 x (M r)), the leaf partials' operand scales:
+  // of V_F (from the forward chain kernel), of Vbar_F and Xbar_F (from the
+  // chain adjoint)
+  int32_t* VFexp;
+  int32_t* VBexp;
+  int32_t* XBexp;
   // emulated form only (else null): per level-(M-1) region, the full symmetric
   // adjoint S of Ahat along its ancestor chain (M r x M r, row-major) and the
   // scales of its rows per 128-column group, for the leaves' Hbar = 2 H S

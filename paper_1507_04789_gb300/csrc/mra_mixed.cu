@@ -316,6 +316,14 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
       const int i = t / ng, g = t - i * ng;
       lf.hrow[(t0 + i) * ng + g] = hsc[g * TC_M + i];
     }
+    if (lf.vfexp) {   // gradient calls: column scales of V_F over the tile (the leaf partials' operand)
+      int32_t* out = lf.vfexp + (P * 4 + (t0 - row0) / TC_M) * (long)Mr;
+      for (int c = threadIdx.x; c < Mr; c += NT) {
+        int e = -2000;
+        for (int i = 0; i < na; ++i) e = max(e, xexp_of(Hrow[(long)i * Mr + c]));
+        out[c] = e;
+      }
+    }
   }
   eng.release();
   if (!ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, M - 1, P);
@@ -947,7 +955,12 @@ __global__ void __launch_bounds__(NT) leaf_partial_kernel_em(const Desc* __restr
   Engine<true> eng;
   eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
   TcAcc acc;
-  const bool ok = eng.mma(acc, A, 1, Mr, nl * r, B, 1, Mr, r, K);
+  // operand scales per 128-row group from the chain kernels, when they exported them
+  const bool tab = gs.VFexp != nullptr;
+  const long tb = p * 4 * (long)Mr;
+  const bool ok = eng.mma(acc, A, 1, Mr, nl * r, B, 1, Mr, r, K,
+                          tab ? (diag ? gs.VBexp : gs.XBexp) + tb + l0 * r : nullptr, Mr,
+                          tab ? gs.VFexp + tb + k * r : nullptr, Mr);
   const int row = acc.row(), c0 = acc.col0();
   if (ok && row < nl * r) {
     const int l = l0 + row / r, i = row % r;
@@ -1046,6 +1059,17 @@ __global__ void __launch_bounds__(NT) chain_adjoint_kernel_em(const Desc* __rest
           for (int c = 0; c < 32; ++c)
             if (c0 + c < r) out[c0 + c] -= acc.v[c];
         }
+      }
+    }
+    if (ok && gs.VBexp) {   // column scales of the final Vbar_F and Xbar_F over the tile (leaf partials)
+      __syncthreads();
+      const long base = (p * 4 + (t0 - row0) / TC_M) * (long)Mr;
+      for (int c = threadIdx.x; c < 2 * Mr; c += NT) {
+        const double* X = c < Mr ? VB : XB;
+        const int cc = c < Mr ? c : c - Mr;
+        int e = -2000;
+        for (int i = 0; i < na; ++i) e = max(e, xexp_of(X[(long)i * Mr + cc]));
+        (c < Mr ? gs.VBexp : gs.XBexp)[base + cc] = e;
       }
     }
   }
