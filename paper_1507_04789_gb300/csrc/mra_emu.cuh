@@ -437,4 +437,29 @@ __device__ inline bool em_mma(EmCtx& cx, TcAcc& acc, const double* A, long sai, 
   return true;
 }
 
+// Row blocks of r rows stacked into one 128-row tile.
+__host__ __device__ inline int em_stack(int r) { return r > 64 ? 1 : TC_M / r; }
+
+// Tiles of the packed lower blocks (l, k), k <= l < M, stacked S high along l:
+// per column block k, the diagonal tile (l = k) alone, then l = k+1.. in
+// stacks of S (the leaf and prior partial sums, whose diagonal tiles take
+// another operand).
+__host__ __device__ inline int partial_tiles(int M, int S) {
+  int n = 0;
+  for (int k = 0; k < M; ++k) n += 1 + (M - 1 - k + S - 1) / S;
+  return n;
+}
+__device__ inline bool partial_tile(int t, int M, int S, int& k, int& l0, int& nl) {
+  for (k = 0; k < M; ++k) {
+    const int nt = 1 + (M - 1 - k + S - 1) / S;
+    if (t < nt) {
+      l0 = t == 0 ? k : k + 1 + (t - 1) * S;
+      nl = t == 0 ? 1 : min(S, M - l0);
+      return true;
+    }
+    t -= nt;
+  }
+  return false;
+}
+
 }  // namespace mra

@@ -628,6 +628,19 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
         }
     }
   };
+  // EMU: f(i, j, P(i, j)) for P(i, j) = sum_{c < kk} A(i, c) B(j, c), i < na <= 128 (stacked
+  // row blocks), j < r
+  auto product_n = [&](const double* A, long sai, long sak, int na, const double* B, long sbj, long sbk, int kk,
+                       auto&& f) {
+    if (ok) ok = em_mma(cx, ea, A, sai, sak, na, B, sbj, sbk, r, kk);
+    const int row = ea.row(), c0 = ea.col0();
+    if (ok && row < na) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c0 + c < r) f(row, c0 + c, ea.v[c]);
+    }
+  };
+  const int S = em_stack(r);
   double g_s2 = 0.0, g_k = 0.0;
   load_knots(sh.bbox, m, st.mort[m][i], sh.gx, sh.gy, qx, qy);
   const double* L = st.L[m] + i * (long)r * r;
@@ -655,11 +668,20 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
   }
   double* VB = gs.VB[m] + i * (long)r * mr;
   double* XB = gs.XB[m] + i * (long)r * mr;
-  // Vbar^k = incoming(m, k) - 2 Wbar V^k
-  for (int k = 0; k < m; ++k)
-    product(B2, ld, 1, V + k * r, 1, mr, r, [&](int row, int col, double v) {
-      VB[(long)row * mr + k * r + col] = incoming(m, k, row, col) - 2.0 * v;
-    });
+  // Vbar^k = incoming(m, k) - 2 Wbar V^k (EMU: transposed, S blocks k per product: the
+  // columns of V are contiguous across its blocks)
+  if (EMU) {
+    for (int k0 = 0; k0 < m; k0 += S)
+      product_n(V + k0 * r, 1, mr, min(S, m - k0) * r, B2, ld, 1, r, [&](int ii, int row, double v) {
+        const int k = k0 + ii / r, col = ii % r;
+        VB[(long)row * mr + k * r + col] = incoming(m, k, row, col) - 2.0 * v;
+      });
+  } else {
+    for (int k = 0; k < m; ++k)
+      product(B2, ld, 1, V + k * r, 1, mr, r, [&](int row, int col, double v) {
+        VB[(long)row * mr + k * r + col] = incoming(m, k, row, col) - 2.0 * v;
+      });
+  }
   // chain adjoint
   for (int l = m - 1; l >= 0; --l) {
     const long a = ancestor(st, m, i, l);
@@ -676,16 +698,35 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
       g_k = fma(xb, d2, g_k);
     });
     __syncthreads();
-    for (int k = 0; k < l; ++k)
-      product(XB + l * r, mr, 1, Va + k * r, 1, l * r, r,
-              [&](int row, int col, double v) { VB[(long)row * mr + k * r + col] -= v; });
+    if (EMU) {   // Vbar^k -= Xbar^l V^k_a, transposed, S blocks k per product
+      for (int k0 = 0; k0 < l; k0 += S)
+        product_n(Va + k0 * r, 1, l * r, min(S, l - k0) * r, XB + l * r, mr, 1, r, [&](int ii, int row, double v) {
+          VB[(long)row * mr + (k0 + ii / r) * r + ii % r] -= v;
+        });
+    } else {
+      for (int k = 0; k < l; ++k)
+        product(XB + l * r, mr, 1, Va + k * r, 1, l * r, r,
+                [&](int row, int col, double v) { VB[(long)row * mr + k * r + col] -= v; });
+    }
   }
   __syncthreads();
   // partial sums passed up: tiles (l, k), k <= l < m
   if (m > 0) {
     const int Tup = m * (m + 1) / 2;
     double* Up = gs.Up[m] + i * (long)Tup * r * r;
-    for (int l = 0; l < m; ++l)
+    if (EMU) {   // tiles (l0.., k) stacked S high (diagonal tiles alone: their operand is Vbar)
+      for (int t = 0; t < partial_tiles(m, S); ++t) {
+        int k, l0, nl;
+        partial_tile(t, m, S, k, l0, nl);
+        const double* Ab = (l0 == k ? VB : XB) + l0 * r;
+        const double sgn = l0 == k ? 1.0 : -1.0;
+        product_n(Ab, 1, mr, nl * r, V + k * r, 1, mr, r, [&](int ii, int col, double v) {
+          const int l = l0 + ii / r, row = ii % r;
+          Up[(long)tri_index(l, k) * r * r + row * r + col] = incoming(l, k, row, col) + sgn * v;
+        });
+      }
+    }
+    for (int l = 0; l < m && !EMU; ++l)
       for (int k = 0; k <= l; ++k) {
         const double* Ab = (k < l ? XB : VB) + l * r;
         double* out = Up + (long)tri_index(l, k) * r * r;

@@ -564,7 +564,6 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
 // against one column block l, so the 128 rows of the MMA carry S output blocks
 // and the column block is split once for all of them.
 // ---------------------------------------------------------------------------
-__host__ __device__ inline int em_stack(int r) { return r > 64 ? 1 : TC_M / r; }
 
 // Tiles of the packed lower blocks (k >= l, k, l < nblk) for stack height S.
 __host__ __device__ inline int em_tiles(int nblk, int S) {
@@ -916,24 +915,6 @@ __global__ void __launch_bounds__(NT) hbar_kernel_em(const Desc* __restrict__ D,
 // (the FP64 leaf_partial_kernel's tiles).  Per column block k, the diagonal
 // tile (operand Vbar) runs alone and the tiles l > k (operand Xbar, adjacent
 // columns) are stacked em_stack(r) high.
-__host__ __device__ inline int partial_tiles(int M, int S) {
-  int n = 0;
-  for (int k = 0; k < M; ++k) n += 1 + (M - 1 - k + S - 1) / S;
-  return n;
-}
-__device__ inline bool partial_tile(int t, int M, int S, int& k, int& l0, int& nl) {
-  for (k = 0; k < M; ++k) {
-    const int nt = 1 + (M - 1 - k + S - 1) / S;
-    if (t < nt) {
-      l0 = t == 0 ? k : k + 1 + (t - 1) * S;
-      nl = t == 0 ? 1 : min(S, M - l0);
-      return true;
-    }
-    t -= nt;
-  }
-  return false;
-}
-
 __global__ void __launch_bounds__(NT) leaf_partial_kernel_em(const Desc* __restrict__ D, GradState gs, int* status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t mbar[2];
