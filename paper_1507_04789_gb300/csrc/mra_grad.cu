@@ -187,10 +187,30 @@ __device__ inline bool chol_inverse_adjoint_em(EmCtx& cx, double* B0, double* B1
 // ---------------------------------------------------------------------------
 // Posterior adjoint, level m (top-down).
 // ---------------------------------------------------------------------------
-template <int TILE>
+// EMU (launched only with gb_ready): Ltbar, the Cholesky/inverse adjoint of
+// I + Ahat^{m,m} and S^{m,l} = Lti' Gbar^l / 2 on the emulation engine; a
+// timeout sets status.
+template <int TILE, bool EMU>
 __global__ void __launch_bounds__(NT) post_adjoint_kernel(int m, const Desc* __restrict__ D, GradState gs,
-                                                          int gb_ready) {
-  extern __shared__ double smem[];
+                                                          int gb_ready, int* status) {
+  extern __shared__ __align__(1024) double smem_all[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  __shared__ int rexp[EMU ? EM_REXP : 1], cexp[EMU ? EM_CEXP : 1];
+  double* smem = smem_all + (EMU ? EM_STAGE_BYTES / sizeof(double) : 0);
+  EmCtx cx;
+  bool ok = true;
+  if (EMU) {
+    cx.stage = reinterpret_cast<uint16_t*>(smem_all);
+    cx.rexp = rexp;
+    cx.cexp = cexp;
+    cx.mbar = mbar;
+    cx.fail = &fail;
+    em_init(cx, &tmem_slot);
+  }
+  TcAcc ea;
+  const int erow = ea.row(), ec0 = ea.col0();
   const Desc& ds = D[0];
   const Shape sh = ds.sh;
   const LevelState& st = ds.st;
@@ -240,37 +260,75 @@ __global__ void __launch_bounds__(NT) post_adjoint_kernel(int m, const Desc* __r
   __syncthreads();
   // Ltbar = sum_l Gbar^l (Ahat^{m,l})' + gbar omegahat^m'   -> B0 (lower)
   const double* om = st.Om[m] + (i * (m + 1) + m) * (long)r;
-  acc.zero();
-  for (int l = 0; l < m; ++l)
-    tile_mma<TILE>(acc, GB + l * r, mr, 1, r, A + (long)tri_index(m, l) * r * r, r, 1, r, r, stg);
+  if (EMU) {   // one product per l, summed in B0 (each thread owns its entries)
+    for (int t = threadIdx.x; t < r * r; t += NT) B0[(t / r) * ld + t % r] = 0.0;
+    for (int l = 0; l < m && ok; ++l) {
+      ok = em_mma(cx, ea, GB + l * r, mr, 1, r, A + (long)tri_index(m, l) * r * r, r, 1, r, r);
+      if (ok && erow < r) {
 #pragma unroll
-  for (int p = 0; p < TileAcc<TILE>::RM; ++p)
-#pragma unroll
-    for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
-      int row = acc.row(p), col = acc.col(q);
-      if (row < r && col < r) B0[row * ld + col] = row >= col ? acc.v[p][q] + gbar[row] * om[col] : 0.0;
+        for (int c = 0; c < 32; ++c)
+          if (ec0 + c < r) B0[erow * ld + ec0 + c] += ea.v[c];
+      }
     }
+    __syncthreads();
+    for (int t = threadIdx.x; t < r * r; t += NT) {
+      const int row = t / r, col = t % r;
+      B0[row * ld + col] = row >= col ? B0[row * ld + col] + gbar[row] * om[col] : 0.0;
+    }
+  } else {
+    acc.zero();
+    for (int l = 0; l < m; ++l)
+      tile_mma<TILE>(acc, GB + l * r, mr, 1, r, A + (long)tri_index(m, l) * r * r, r, 1, r, r, stg);
+#pragma unroll
+    for (int p = 0; p < TileAcc<TILE>::RM; ++p)
+#pragma unroll
+      for (int q = 0; q < TileAcc<TILE>::RM; ++q) {
+        int row = acc.row(p), col = acc.col(q);
+        if (row < r && col < r) B0[row * ld + col] = row >= col ? acc.v[p][q] + gbar[row] * om[col] : 0.0;
+      }
+  }
   __syncthreads();
   const double* Ltf = st.Ltf[m] + i * (long)r * r;   // Cholesky factor of I + Ahat^{m,m}
   const double* Lti = st.Lt[m] + i * (long)r * r;    // its inverse
   // S^{m,m} = sym(Lti' Phi(Ltf' Lbar) Lti), Lbar = lower(-Lti' Ltbar Lti') - 1 / Ltf_ii
-  chol_inverse_adjoint<TILE>(B0, B1, B2, ld, r, Ltf, r, Lti, r, -1.0, stg);
+  if (EMU) {
+    if (ok) ok = chol_inverse_adjoint_em(cx, B0, B1, B2, ld, r, Ltf, r, Lti, r, -1.0);
+  } else {
+    chol_inverse_adjoint<TILE>(B0, B1, B2, ld, r, Ltf, r, Lti, r, -1.0, stg);
+  }
   double* Ab = gs.Abar[m] + i * (long)r * (mr + r);
   for (int t = threadIdx.x; t < r * r; t += NT) {
     int a = t / r, b = t - a * r;
     Ab[(long)a * (mr + r) + mr + b] = B2[a * ld + b];
   }
-  // S^{m,l} = 1/2 Lti' Gbar^l
-  for (int l = 0; l < m; ++l) {
-    acc.zero();
-    tile_mma<TILE>(acc, Lti, 1, r, r, GB + l * r, 1, mr, r, r, stg);
-    store_tile<TILE>(acc, Ab + l * r, mr + r, r, r, 0.5);
+  // S^{m,l} = 1/2 Lti' Gbar^l (EMU: transposed, 128/r blocks l per product)
+  if (EMU) {
+    const int S = em_stack(r);
+    for (int l0 = 0; l0 < m && ok; l0 += S) {
+      ok = em_mma(cx, ea, GB + l0 * r, 1, mr, min(S, m - l0) * r, Lti, 1, r, r, r);
+      if (ok && erow < min(S, m - l0) * r) {
+        const int l = l0 + erow / r, jj = erow % r;
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (ec0 + c < r) Ab[(long)(ec0 + c) * (mr + r) + l * r + jj] = 0.5 * ea.v[c];
+      }
+    }
+  } else {
+    for (int l = 0; l < m; ++l) {
+      acc.zero();
+      tile_mma<TILE>(acc, Lti, 1, r, r, GB + l * r, 1, mr, r, r, stg);
+      store_tile<TILE>(acc, Ab + l * r, mr + r, r, r, 0.5);
+    }
   }
   // omegahat^m bar = Lti' gbar
   for (int q = threadIdx.x; q < r; q += NT) {
     double s = 0.0;
     for (int c = q; c < r; ++c) s = fma(Lti[(long)c * r + q], gbar[c], s);
     gs.Obar[m][i * r + q] = s;
+  }
+  if (EMU) {
+    em_release(cx);
+    if (!ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, m, i);
   }
 }
 
@@ -795,6 +853,26 @@ static cudaError_t launch_leaf_adjoint(int tile, int nleaves, size_t sm, cudaStr
 }
 
 template <bool EMU>
+static cudaError_t launch_post_adjoint(int tile, int m, int nregions, size_t sm, cudaStream_t s, const Desc* d_desc,
+                                       const GradState& gs, int gb_ready, int* status) {
+  cudaError_t e;
+#define MRA_POST_ADJ(T)                                                                                       \
+  if ((e = cudaFuncSetAttribute(post_adjoint_kernel<T, EMU>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                (int)sm)))                                                                    \
+    return e;                                                                                                 \
+  post_adjoint_kernel<T, EMU><<<nregions, NT, sm, s>>>(m, d_desc, gs, gb_ready, status);
+  if (tile == 16) {
+    MRA_POST_ADJ(16)
+  } else if (tile == 32) {
+    MRA_POST_ADJ(32)
+  } else {
+    MRA_POST_ADJ(64)
+  }
+#undef MRA_POST_ADJ
+  return cudaGetLastError();
+}
+
+template <bool EMU>
 static cudaError_t launch_prior_adjoint(int tile, int m, int nregions, size_t sm, cudaStream_t s,
                                         const Desc* d_desc, const GradState& gs, long slot0, int* status) {
   cudaError_t e;
@@ -831,8 +909,11 @@ cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs,
     // emulated form with the per-region S buffer: Gbar on the tensor cores first
     const int gb_ready = emu && gs.SF != nullptr && m > 0;
     if (gb_ready && (e = launch_gbar_em(m, hd, d_desc, gs, status, s, launches))) return e;
-    size_t sm = sizeof(double) * (MAXL * MAX_R_DEV + MAX_R_DEV) + sq + stg;
-    MRA_GRAD_LAUNCH(tile, post_adjoint_kernel, dim3(st.nreg[m]), sm, s, m, d_desc, gs, gb_ready);
+    const size_t sm = sizeof(double) * (MAXL * MAX_R_DEV + MAX_R_DEV) + sq;
+    if (gb_ready) e = launch_post_adjoint<true>(tile, m, st.nreg[m], std::max(sm + EM_STAGE_BYTES, EM_SOLO_SMEM), s,
+                                                d_desc, gs, gb_ready, status);
+    else e = launch_post_adjoint<false>(tile, m, st.nreg[m], sm + stg, s, d_desc, gs, gb_ready, status);
+    if (e) return e;
     ++*launches;
   }
   // emulated form: Hbar on the tensor cores (when its per-parent S was allocated)
