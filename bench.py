@@ -123,15 +123,17 @@ def contraction_flops(M: int, r: int, nF, precision: str):
     return out
 
 
-# DRAM bytes per launch of a dominant kernel, from one ncu capture, valid only
+# DRAM bytes per launch (per stage, where the dominant entry is a stage of two
+# kernels) of the dominant kernel, from one ncu capture, valid only
 # while the kernel's sources are the ones it was taken from (else null).
 TRAFFIC = {
     ("emu", "leaf", "n1M_matern15_M7_r64"): {
-        "bytes": 5.44e9,
-        "how": "dram__bytes_read.sum + dram__bytes_write.sum of leaf_kernel_tc<1> at n = 2^18, M = 6 "
-               "(1.17 GB, profiles/leaf_kernel_tc_emu_n256k.md) scaled by n M r to n = 2^20, M = 7",
+        "bytes": 1.385e+10,
+        "how": "dram__bytes_read.sum + dram__bytes_write.sum of the leaf stage, chain_forward_kernel_em "
+               "(1.25 GB) + leaf_kernel_tc<1> (1.72 GB), at n = 2^18, M = 6 "
+               "(profiles/chain_forward_and_leaf_emu_n256k.md) scaled by n M r to n = 2^20, M = 7",
         "sources": ["mra_mixed.cu", "mra_emu.cuh", "mra_tc.cuh", "mra_device.cuh", "mra_kernels.cuh"],
-        "sha1": "05d1d8496653b9e8f8b064528ff76fc736fbd50b",
+        "sha1": "c2a5100d99499e4bfe60e12304072f1ea5f0d9d9",
     },
 }
 
@@ -517,6 +519,9 @@ def main():
     roofline["traffic"] = traffic
     if how:
         roofline["traffic_source"] = how
+    if best == "emu" and dom == "leaf":   # the stage is two kernels: the per-parent chain, then the leaves
+        roofline["stage_kernels"] = ["chain_forward_kernel_em", "leaf_kernel_tc<1>"]
+        dom_n *= 2
     roofline.update({"launches_per_step": dom_n / args.steps, "kernels": kernel_table(best),
                      "step_fp64_alg_tflops": total_flops / (head["ms_per_step"] * 1e-3) / 1e12})
 
