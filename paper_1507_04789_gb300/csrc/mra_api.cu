@@ -661,6 +661,11 @@ static int ensure_grad_arena(mra_handle* h) {
     G.want(&h->gs.VB[m], R * r * (int64_t)m * r);
     G.want(&h->gs.XB[m], R * r * (int64_t)m * r);
     G.want(&h->gs.Up[m], R * (int64_t)m * (m + 1) / 2 * r * r);
+    h->st.licol[m] = h->st.vcol[m] = nullptr;
+    if (h->cfg.precision == MRA_PREC_EMU) {
+      G.want(&h->st.licol[m], R * r);
+      if (m > 0) G.want(&h->st.vcol[m], R * (int64_t)m * r);
+    }
   }
   if (M > 0) G.want(&h->gs.PartLeaf, (int64_t)nreg[M - 1] * M * (M + 1) / 2 * r * r);
   // emulated form: the per-parent adjoint S for Hbar on the tensor cores, when
@@ -694,7 +699,11 @@ static int ensure_grad_arena(mra_handle* h) {
   G.want(&h->d_grad, 4);
   cudaError_t e = G.commit();
   if (e) {
-    for (int m = 0; m < M; ++m) { h->st.L[m] = nullptr; h->st.Ltf[m] = nullptr; }
+    for (int m = 0; m < M; ++m) {
+      h->st.L[m] = nullptr;
+      h->st.Ltf[m] = nullptr;
+      h->st.licol[m] = h->st.vcol[m] = nullptr;
+    }
     h->lf.VF = nullptr;
     h->lf.LSf = nullptr;
     h->gs.SF = nullptr;

@@ -804,6 +804,26 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
   }
 }
 
+// Emulated form: column exponents of every region's L^{-1} and V at level m
+// (the right operands of the chain adjoints), one CTA per region.
+__global__ void __launch_bounds__(NT) col_scales_kernel(int m, const Desc* __restrict__ D) {
+  const Desc& ds = D[0];
+  const LevelState& st = ds.st;
+  const int r = ds.sh.r, mr = m * r;
+  const long i = blockIdx.x;
+  const double* Li = st.Li[m] + i * (long)r * r;
+  const double* V = st.V[m] + i * (long)r * mr;
+  for (int c = threadIdx.x; c < r + mr; c += NT) {
+    int e = -2000;
+    if (c < r)
+      for (int a = 0; a < r; ++a) e = max(e, xexp_of(Li[(long)a * r + c]));
+    else
+      for (int a = 0; a < r; ++a) e = max(e, xexp_of(V[(long)a * mr + c - r]));
+    if (c < r) st.licol[m][i * r + c] = e;
+    else st.vcol[m][i * (long)mr + c - r] = e;
+  }
+}
+
 // Sum of the per-CTA partial gradients (fixed assignment: deterministic).
 __global__ void __launch_bounds__(NT) grad_reduce_kernel(const double* gpart, long nslots, double* out) {
   __shared__ double red[32];
@@ -905,6 +925,13 @@ cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs,
   for (int m = 0; m < M; ++m) slot_leaf += st.nreg[m];
   tm->start(6, s);
   const bool emu = hd.sh.mixed == 2 && M > 0;
+  if (emu && st.licol[0]) {   // column scales of L^{-1} and V for the emulated chain adjoints
+    for (int m = 0; m < M; ++m) {
+      col_scales_kernel<<<st.nreg[m], NT, 0, s>>>(m, d_desc);
+      ++*launches;
+    }
+    if ((e = cudaGetLastError())) return e;
+  }
   for (int m = 0; m < M; ++m) {
     // emulated form with the per-region S buffer: Gbar on the tensor cores first
     const int gb_ready = emu && gs.SF != nullptr && m > 0;

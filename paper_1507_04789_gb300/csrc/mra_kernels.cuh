@@ -54,6 +54,9 @@ struct LevelState {
   // saved for the gradient (null when no gradient is requested)
   double* L[MAXL];    // 4^m x r x r: L_R (prior Cholesky factor)
   double* Ltf[MAXL];  // 4^m x r x r: Lt (Cholesky factor of I + Ahat^{m,m})
+  // gradient of the emulated form: column exponents (|x| < 2^e over the r rows)
+  int32_t* licol[MAXL];  // 4^m x r: columns of L_R^{-1}
+  int32_t* vcol[MAXL];   // level m >= 1: 4^m x (m r): columns of V_R
 };
 
 // Compact id of the level-l ancestor of compact region c of level m.

@@ -983,6 +983,8 @@ __global__ void __launch_bounds__(NT) chain_adjoint_kernel_em(const Desc* __rest
   __shared__ int fail;
   __shared__ int rexp[EM_REXP], cexp[EM_CEXP];
   __shared__ double ax[MAX_R_DEV], ay[MAX_R_DEV], red[32];
+  // row scales (one 64-column block = one group) of the tile's Vbar blocks and of the current Xbar block
+  __shared__ int vbsc[MAXL * TC_M], xbsc[TC_M];
   const Desc& ds = D[0];
   const Shape sh = ds.sh;
   const Cov cv = ds.cv;
@@ -1003,14 +1005,31 @@ __global__ void __launch_bounds__(NT) chain_adjoint_kernel_em(const Desc* __rest
     double* VB = gs.VBF + t0 * Mr;
     double* XB = gs.XBF + t0 * Mr;
     const double so_x = row < na ? lf.xs[t0 + row] : 0.0, so_y = row < na ? lf.ys[t0 + row] : 0.0;
+    const bool tab = st.licol[0] != nullptr;     // column scales of the ancestors' L^{-1} and V
+    __syncthreads();                             // the previous tile's scales are no longer read
+    {   // row scales of Vbar^{M-1} (as the leaf adjoint left it): one warp per row
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int i = warp; i < TC_M; i += NT / 32) {
+        int e = -2000;
+        if (i < na)
+          for (int c = lane; c < r; c += 32) e = max(e, xexp_of(VB[(long)i * Mr + (M - 1) * r + c]));
+        e = __reduce_max_sync(0xffffffffu, e);
+        if (lane == 0) vbsc[(M - 1) * TC_M + i] = e;
+      }
+    }
     for (int l = M - 1; l >= 0 && ok; --l) {
       const long a = ancestor(st, M - 1, p, l);
       const double* Lia = st.Li[l] + a * (long)r * r;
       const double* Va = st.V[l] + a * (long)r * (l * r);
-      __syncthreads();                           // the previous level's knots are no longer read
+      __syncthreads();                           // the previous level's knots and Xbar scales are no longer read
       load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
+      for (int t = threadIdx.x; t < TC_M; t += NT) {
+        xbsc[t] = -2000;
+        if (l > 0) vbsc[(l - 1) * TC_M + t] = -2000;   // block l - 1 takes its last update at this level
+      }
       __syncthreads();
-      ok = eng.mma(acc, VB + l * r, Mr, 1, na, Lia, 1, r, r, r);
+      ok = eng.mma(acc, VB + l * r, Mr, 1, na, Lia, 1, r, r, r, vbsc + l * TC_M, 0,
+                   tab ? st.licol[l] + a * r : nullptr, 0);
       if (ok && row < na) {
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
@@ -1030,15 +1049,27 @@ __global__ void __launch_bounds__(NT) chain_adjoint_kernel_em(const Desc* __rest
             g_k = fma(xb, d2, g_k);
           }
         }
+        int e = -2000;   // row scale of Xbar^l (two threads per row)
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (c0 + c < r) e = max(e, xexp_of(acc.v[c]));
+        atomicMax(xbsc + row, e);
       }
       // (the next product's scale pass opens with a barrier: Xbar^l is complete)
       for (int k = 0; k < l && ok; ++k) {
-        ok = eng.mma(acc, XB + l * r, Mr, 1, na, Va + k * r, 1, l * r, r, r);
+        ok = eng.mma(acc, XB + l * r, Mr, 1, na, Va + k * r, 1, l * r, r, r, xbsc, 0,
+                     tab ? st.vcol[l] + a * (long)(l * r) + k * r : nullptr, 0);
         if (ok && row < na) {
           double* out = VB + (long)row * Mr + k * r;
+          int e = -2000;
 #pragma unroll
           for (int c = 0; c < 32; ++c)
-            if (c0 + c < r) out[c0 + c] -= acc.v[c];
+            if (c0 + c < r) {
+              const double v = out[c0 + c] - acc.v[c];
+              out[c0 + c] = v;
+              e = max(e, xexp_of(v));
+            }
+          if (k == l - 1) atomicMax(vbsc + k * TC_M + row, e);   // the last update of block k
         }
       }
     }
