@@ -688,9 +688,10 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
   };
   // EMU: f(i, j, P(i, j)) for P(i, j) = sum_{c < kk} A(i, c) B(j, c), i < na <= 128 (stacked
   // row blocks), j < r
+  // (pa, pb: the operands' row scales from their producers, one group since kk = r, or null)
   auto product_n = [&](const double* A, long sai, long sak, int na, const double* B, long sbj, long sbk, int kk,
-                       auto&& f) {
-    if (ok) ok = em_mma(cx, ea, A, sai, sak, na, B, sbj, sbk, r, kk);
+                       const int* pa, const int* pb, auto&& f) {
+    if (ok) ok = em_mma(cx, ea, A, sai, sak, na, B, sbj, sbk, r, kk, pa, 0, pb, 0);
     const int row = ea.row(), c0 = ea.col0();
     if (ok && row < na) {
 #pragma unroll
@@ -730,7 +731,8 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
   // columns of V are contiguous across its blocks)
   if (EMU) {
     for (int k0 = 0; k0 < m; k0 += S)
-      product_n(V + k0 * r, 1, mr, min(S, m - k0) * r, B2, ld, 1, r, [&](int ii, int row, double v) {
+      product_n(V + k0 * r, 1, mr, min(S, m - k0) * r, B2, ld, 1, r,
+                st.vcol[m] ? st.vcol[m] + i * (long)mr + k0 * r : nullptr, nullptr, [&](int ii, int row, double v) {
         const int k = k0 + ii / r, col = ii % r;
         VB[(long)row * mr + k * r + col] = incoming(m, k, row, col) - 2.0 * v;
       });
@@ -748,17 +750,23 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
     __syncthreads();
     load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
     __syncthreads();
-    product(VB + l * r, mr, 1, Lia, 1, r, r, [&](int row, int col, double xb) {
+    auto xbar_epi = [&](int row, int col, double xb) {
       XB[(long)row * mr + l * r + col] = xb;
       double d1, d2;
       dcov0(cv, qx[row], qy[row], ax[col], ay[col], d1, d2);
       g_s2 = fma(xb, d1, g_s2);
       g_k = fma(xb, d2, g_k);
-    });
+    };
+    if (EMU)
+      product_n(VB + l * r, mr, 1, r, Lia, 1, r, r, nullptr, st.licol[l] ? st.licol[l] + a * r : nullptr, xbar_epi);
+    else
+      product(VB + l * r, mr, 1, Lia, 1, r, r, xbar_epi);
     __syncthreads();
     if (EMU) {   // Vbar^k -= Xbar^l V^k_a, transposed, S blocks k per product
       for (int k0 = 0; k0 < l; k0 += S)
-        product_n(Va + k0 * r, 1, l * r, min(S, l - k0) * r, XB + l * r, mr, 1, r, [&](int ii, int row, double v) {
+        product_n(Va + k0 * r, 1, l * r, min(S, l - k0) * r, XB + l * r, mr, 1, r,
+                  st.vcol[l] ? st.vcol[l] + a * (long)(l * r) + k0 * r : nullptr, nullptr,
+                  [&](int ii, int row, double v) {
           VB[(long)row * mr + (k0 + ii / r) * r + ii % r] -= v;
         });
     } else {
@@ -778,7 +786,8 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
         partial_tile(t, m, S, k, l0, nl);
         const double* Ab = (l0 == k ? VB : XB) + l0 * r;
         const double sgn = l0 == k ? 1.0 : -1.0;
-        product_n(Ab, 1, mr, nl * r, V + k * r, 1, mr, r, [&](int ii, int col, double v) {
+        product_n(Ab, 1, mr, nl * r, V + k * r, 1, mr, r, nullptr,
+                  st.vcol[m] ? st.vcol[m] + i * (long)mr + k * r : nullptr, [&](int ii, int col, double v) {
           const int l = l0 + ii / r, row = ii % r;
           Up[(long)tri_index(l, k) * r * r + row * r + col] = incoming(l, k, row, col) + sgn * v;
         });
