@@ -130,10 +130,10 @@ TRAFFIC = {
     ("emu", "leaf", "n1M_matern15_M7_r64"): {
         "bytes": 1.385e+10,
         "how": "dram__bytes_read.sum + dram__bytes_write.sum of the leaf stage, chain_forward_kernel_em "
-               "(1.25 GB) + leaf_kernel_tc<1> (1.72 GB), at n = 2^18, M = 6 "
+               "(1.25 GB) + leaf_kernel_tc<1> (1.71 GB), at n = 2^18, M = 6 "
                "(profiles/chain_forward_and_leaf_emu_n256k.md) scaled by n M r to n = 2^20, M = 7",
         "sources": ["mra_mixed.cu", "mra_emu.cuh", "mra_tc.cuh", "mra_device.cuh", "mra_kernels.cuh"],
-        "sha1": "c2a5100d99499e4bfe60e12304072f1ea5f0d9d9",
+        "sha1": "1d4f8a62573148b860a150f28691675951a29f57",
     },
 }
 
