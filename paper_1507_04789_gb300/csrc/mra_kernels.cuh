@@ -180,4 +180,17 @@ __device__ __forceinline__ Item work_item(const int2* work) {
   return {0, (long)blockIdx.x};
 }
 
+// Tiled work on a flat grid of nt tiles per item, the tile index running
+// fastest, so that the tiles of one item (which read the same operand rows)
+// run together and share them in L2.
+__device__ __forceinline__ Item work_item_tiled(const int2* work, int nt, int& tile) {
+  const long b = blockIdx.x / nt;
+  tile = (int)(blockIdx.x - b * nt);
+  if (work) {
+    const int2 w = work[b];
+    return {w.x, (long)w.y};
+  }
+  return {0, b};
+}
+
 }  // namespace mra

@@ -586,13 +586,14 @@ __device__ inline bool em_tile(int t, int nblk, int S, int& l, int& k0) {
 }
 
 __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict__ D, const int2* __restrict__ work,
-                                                          int* status) {
+                                                          int nt, int* status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
   __shared__ int rexp[EM_REXP], cexp[EM_CEXP];
-  const Item it = work_item(work);
+  int tile;
+  const Item it = work_item_tiled(work, nt, tile);
   const Desc& ds = D[it.d];
   const int M = ds.sh.M, r = ds.sh.r, Mr = M * r;
   const LevelState& st = ds.st;
@@ -600,7 +601,7 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict
   const long p = it.i;
   const int S = em_stack(r);
   int l, k0;
-  if (!em_tile(blockIdx.y, M, S, l, k0)) return;     // fewer tiles in a shallower dataset
+  if (!em_tile(tile, M, S, l, k0)) return;     // fewer tiles in a shallower dataset
   const int nk = min(S, M - k0);                      // row blocks k0 .. k0 + nk - 1
   const long pm = st.mort[M - 1][p];
   const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
@@ -654,20 +655,21 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict
 }
 
 __global__ void __launch_bounds__(NT) aggregate_kernel_em(int m, const Desc* __restrict__ D,
-                                                          const int2* __restrict__ work, int* status) {
+                                                          const int2* __restrict__ work, int nt, int* status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
   __shared__ int rexp[EM_REXP], cexp[EM_CEXP];
-  const Item it = work_item(work);
+  int tile;
+  const Item it = work_item_tiled(work, nt, tile);
   const Desc& ds = D[it.d];
   const int r = ds.sh.r, mr = m * r;
   const LevelState& st = ds.st;
   const long p = it.i;
   const int S = em_stack(r);
   int l, k0;
-  if (!em_tile(blockIdx.y, m, S, l, k0)) return;
+  if (!em_tile(tile, m, S, l, k0)) return;
   const int nk = min(S, m - k0);
   const int Tc = (m + 1) * (m + 2) / 2, Tp = m * (m + 1) / 2;
   const long cf = st.cfirst[m - 1][p], cc = st.ccnt[m - 1][p];
@@ -790,7 +792,8 @@ cudaError_t launch_leaf_syrk_em(const Desc* d_desc, const int2* work, int nblock
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(leaf_syrk_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
     return e;
-  leaf_syrk_kernel_em<<<dim3(nblocks, em_tiles(maxM, em_stack(r))), NT, EM_SOLO_SMEM, s>>>(d_desc, work, status);
+  const int nt = em_tiles(maxM, em_stack(r));
+  leaf_syrk_kernel_em<<<nblocks * nt, NT, EM_SOLO_SMEM, s>>>(d_desc, work, nt, status);
   return cudaGetLastError();
 }
 
@@ -862,8 +865,8 @@ __global__ void __launch_bounds__(NT) hbar_kernel_em(const Desc* __restrict__ D,
   const int M = ds.sh.M, r = ds.sh.r, Mr = M * r, ng = (Mr + EM_KG - 1) / EM_KG;
   const LevelState& st = ds.st;
   const LeafState& lf = ds.lf;
-  const long p = blockIdx.x;
-  const int l = blockIdx.y;
+  const long p = blockIdx.x / M;               // the M column blocks of one region run together
+  const int l = (int)(blockIdx.x - p * M);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long pm = st.mort[M - 1][p];
   const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
@@ -924,9 +927,10 @@ __global__ void __launch_bounds__(NT) leaf_partial_kernel_em(const Desc* __restr
   const Desc& ds = D[0];
   const int M = ds.sh.M, r = ds.sh.r, Mr = M * r, T = M * (M + 1) / 2;
   const LeafState& lf = ds.lf;
-  const long p = blockIdx.x;
+  const int nt = partial_tiles(M, em_stack(r));
+  const long p = blockIdx.x / nt;
   int k, l0, nl;
-  if (!partial_tile(blockIdx.y, M, em_stack(r), k, l0, nl)) return;
+  if (!partial_tile((int)(blockIdx.x - p * nt), M, em_stack(r), k, l0, nl)) return;
   const bool diag = l0 == k;
   const long pm = ds.st.mort[M - 1][p];
   const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
@@ -963,7 +967,7 @@ cudaError_t launch_leaf_partial_em(const Desc& hd, const Desc* d_desc, const Gra
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(leaf_partial_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
     return e;
-  leaf_partial_kernel_em<<<dim3(np, partial_tiles(M, em_stack(r))), NT, EM_SOLO_SMEM, s>>>(d_desc, gs, status);
+  leaf_partial_kernel_em<<<np * partial_tiles(M, em_stack(r)), NT, EM_SOLO_SMEM, s>>>(d_desc, gs, status);
   return cudaGetLastError();
 }
 
@@ -1126,7 +1130,7 @@ cudaError_t launch_hbar_em(const Desc& hd, const Desc* d_desc, const GradState& 
   cudaError_t e;
   if ((e = launch_s_full(M - 1, hd, d_desc, gs, s))) return e;
   if ((e = cudaFuncSetAttribute(hbar_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM))) return e;
-  hbar_kernel_em<<<dim3(np, M), NT, EM_SOLO_SMEM, s>>>(d_desc, gs, status);
+  hbar_kernel_em<<<np * M, NT, EM_SOLO_SMEM, s>>>(d_desc, gs, status);
   *launches += 2;
   return cudaGetLastError();
 }
@@ -1146,8 +1150,8 @@ __global__ void __launch_bounds__(NT) gbar_kernel_em(int m, const Desc* __restri
   const Desc& ds = D[0];
   const int r = ds.sh.r, mr = m * r, ng = (mr + EM_KG - 1) / EM_KG;
   const LevelState& st = ds.st;
-  const long P = blockIdx.x;
-  const int l = blockIdx.y;
+  const long P = blockIdx.x / m;               // the m column blocks of one region run together
+  const int l = (int)(blockIdx.x - P * m);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long row0 = (long)st.cfirst[m - 1][P] * r, row1 = row0 + (long)st.ccnt[m - 1][P] * r;
   const long al = ancestor(st, m - 1, P, l);
@@ -1192,7 +1196,7 @@ cudaError_t launch_gbar_em(int m, const Desc& hd, const Desc* d_desc, const Grad
   cudaError_t e;
   if ((e = launch_s_full(m - 1, hd, d_desc, gs, s))) return e;
   if ((e = cudaFuncSetAttribute(gbar_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM))) return e;
-  gbar_kernel_em<<<dim3(np, m), NT, EM_SOLO_SMEM, s>>>(m, d_desc, gs, status);
+  gbar_kernel_em<<<np * m, NT, EM_SOLO_SMEM, s>>>(m, d_desc, gs, status);
   *launches += 2;
   return cudaGetLastError();
 }
@@ -1202,7 +1206,8 @@ cudaError_t launch_aggregate_em(int m, int r, const Desc* d_desc, const int2* wo
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(aggregate_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
     return e;
-  aggregate_kernel_em<<<dim3(nblocks, em_tiles(m, em_stack(r))), NT, EM_SOLO_SMEM, s>>>(m, d_desc, work, status);
+  const int nt = em_tiles(m, em_stack(r));
+  aggregate_kernel_em<<<nblocks * nt, NT, EM_SOLO_SMEM, s>>>(m, d_desc, work, nt, status);
   return cudaGetLastError();
 }
 
