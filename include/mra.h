@@ -66,9 +66,10 @@ extern "C" {
                                terms); factorisations, log-determinants, quadratic forms and
                                the Gram products of the posterior pass in binary64 */
 #define MRA_PREC_EMU      2 /* every large contraction (prior chain, leaf covariance and solve,
-                               leaf and child-to-parent Gram products) on the tensor cores as an
+                               leaf and child-to-parent Gram products, posterior G, and in
+                               mra_loglik_grad the adjoint's products) on the tensor cores as an
                                FP64-grade emulation: operands cut into seven 7-bit bf16 slices
-                               per 64-column group, exact FP32 accumulation, double-float sums
+                               per 128-column group, exact FP32 accumulation, double-float sums
                                (about 1e-14 relative error per product); factorisations and
                                the rest in binary64 */
 
@@ -147,7 +148,12 @@ int mra_loglik(mra_handle* h, const mra_params* theta, double* loglik_out);
  * d loglik / d(sigma2, range, tau2).  The paper gives no gradient; it serves
  * the numerical maximum-likelihood fit of Sec. 4.3.  The gradient is the exact
  * reverse-mode adjoint of the evaluation (Cholesky, triangular-solve and
- * A-update chains of Sec. 3.1-3.2 in reverse), in FP64.
+ * A-update chains of Sec. 3.1-3.2 in reverse), in FP64; with MRA_PREC_EMU its
+ * products run on the FP64 emulation of the tensor cores (gradient within
+ * 1e-9 relative of the FP64 form's).  The first call allocates the adjoint
+ * buffers (in the emulated form also a per-region S buffer of
+ * nreg[M-1] (M r)^2 doubles when that is at most four times the size of H, and
+ * n M r x 2 doubles of covariance derivatives).
  *   theta      : host pointer to one mra_params.
  *   loglik_out : host pointer to one double.
  *   grad_out   : host pointer to 3 doubles (d/dsigma2, d/drange, d/dtau2).
