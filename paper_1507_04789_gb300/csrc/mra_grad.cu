@@ -138,13 +138,16 @@ __device__ void chol_inverse_adjoint(double* B0, double* B1, double* B2, long ld
 // The same chain with its five n x n products on the emulation engine (n <=
 // 128; B0..B2 may live in global or shared memory).  Returns false (uniformly)
 // if a tensor-core wait timed out; the buffers are then incomplete.
+// (pa, pb: the operands' row scales from their producers, one group since n <= 128, or null)
 __device__ inline bool em_store_product(EmCtx& cx, const double* A, long sai, long sak, const double* B, long sbj,
-                                        long sbk, int n, double* C, long ldc, double scale) {
+                                        long sbk, int n, double* C, long ldc, double scale,
+                                        const int* pa = nullptr, const int* pb = nullptr) {
   TcAcc acc;
   const int row = acc.row(), c0 = acc.col0();
   for (int j0 = 0; j0 < n; j0 += TC_N) {
     const int nb = min(TC_N, n - j0);
-    if (!em_mma(cx, acc, A, sai, sak, n, B + (long)j0 * sbj, sbj, sbk, nb, n)) return false;
+    if (!em_mma(cx, acc, A, sai, sak, n, B + (long)j0 * sbj, sbj, sbk, nb, n, pa, 0, pb ? pb + j0 : nullptr, 0))
+      return false;
     if (row < n) {
 #pragma unroll
       for (int c = 0; c < 32; ++c)
@@ -155,23 +158,27 @@ __device__ inline bool em_store_product(EmCtx& cx, const double* A, long sai, lo
   return true;
 }
 
+// Optional scale tables (exponents over the n rows or columns, or null): y_r
+// rows of Ybar, li_r / li_c rows / columns of Li, l_c columns of L.
 __device__ inline bool chol_inverse_adjoint_em(EmCtx& cx, double* B0, double* B1, double* B2, long ld, int n,
-                                               const double* L, long ldl, const double* Li, long ldi, double dlog) {
+                                               const double* L, long ldl, const double* Li, long ldi, double dlog,
+                                               const int* y_r = nullptr, const int* li_r = nullptr,
+                                               const int* li_c = nullptr, const int* l_c = nullptr) {
   // B1 = Ybar Li'
-  if (!em_store_product(cx, B0, ld, 1, Li, ldi, 1, n, B1, ld, 1.0)) return false;
+  if (!em_store_product(cx, B0, ld, 1, Li, ldi, 1, n, B1, ld, 1.0, y_r, li_r)) return false;
   // B2 = lower(-Li' B1) + dlog / L_ii
-  if (!em_store_product(cx, Li, 1, ldi, B1, 1, ld, n, B2, ld, -1.0)) return false;
+  if (!em_store_product(cx, Li, 1, ldi, B1, 1, ld, n, B2, ld, -1.0, li_c)) return false;
   lower_inplace(B2, n, ld);
   if (dlog != 0.0)
     for (int t = threadIdx.x; t < n; t += NT) B2[t * ld + t] += dlog / L[t * ldl + t];
   __syncthreads();
   // B0 = Phi(L' B2)
-  if (!em_store_product(cx, L, 1, ldl, B2, 1, ld, n, B0, ld, 1.0)) return false;
+  if (!em_store_product(cx, L, 1, ldl, B2, 1, ld, n, B0, ld, 1.0, l_c)) return false;
   phi_inplace(B0, n, ld);
   // B1 = B0 Li
-  if (!em_store_product(cx, B0, ld, 1, Li, 1, ldi, n, B1, ld, 1.0)) return false;
+  if (!em_store_product(cx, B0, ld, 1, Li, 1, ldi, n, B1, ld, 1.0, nullptr, li_c)) return false;
   // B2 = Li' B1, then symmetrise in place
-  if (!em_store_product(cx, Li, 1, ldi, B1, 1, ld, n, B2, ld, 1.0)) return false;
+  if (!em_store_product(cx, Li, 1, ldi, B1, 1, ld, n, B2, ld, 1.0, li_c)) return false;
   for (int t = threadIdx.x; t < n * n; t += NT) {
     int i = t / n, j = t - i * n;
     if (j < i) {
@@ -347,6 +354,15 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
   __shared__ int rexp[EMU ? EM_REXP : 1], cexp[EMU ? EM_CEXP : 1];
+  // EMU: operand scales formed once per leaf (exponents, |x| < 2^e): rows of Hbar and of V_F per
+  // 128-column group, their columns over the leaf's rows, the rows and columns of L_Sigma^{-1}, the
+  // columns of L_Sigma, the rows of LSibar and of Sigmabar
+  constexpr int ET = EMU ? 1 : 0;
+  constexpr int NGMAX = (MAXL * MAX_R_DEV + EM_KG - 1) / EM_KG;   // 128-column groups of an M r row
+  __shared__ int hb_r[ET ? NGMAX * TC_M : 1], vf_r[ET ? NGMAX * TC_M : 1];
+  __shared__ int hb_c[ET ? MAXL * MAX_R_DEV : 1], vf_c[ET ? MAXL * MAX_R_DEV : 1];
+  __shared__ int li_r[ET ? TC_M : 1], li_c[ET ? TC_M : 1], l_c[ET ? TC_M : 1], t1_r[ET ? TC_M : 1],
+      t3_r[ET ? TC_M : 1];
   double* smem = smem_all + (EMU ? EM_STAGE_BYTES / sizeof(double) : 0);
   const Desc& ds = D[0];
   const Shape sh = ds.sh;
@@ -433,9 +449,50 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
       zb[t] = s;
     }
     __syncthreads();
+    if (EMU) {   // the operand scales, one pass over Hbar, V_F, L_Sigma^{-1} and L_Sigma
+      const int ng = (Mr + EM_KG - 1) / EM_KG;
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int t = threadIdx.x; t < TC_M; t += NT) t1_r[t] = -2000;
+      for (int o = warp; o < TC_M; o += NT / 32)   // rows per group: a warp per row
+        for (int g = 0; g < ng; ++g) {
+          int eh = -2000, ev = -2000;
+          if (o < nF)
+            for (int c = g * EM_KG + lane; c < min(Mr, (g + 1) * EM_KG); c += 32) {
+              eh = max(eh, xexp_of(HB[(long)o * Mr + c]));
+              ev = max(ev, xexp_of(VF[(long)o * Mr + c]));
+            }
+          eh = __reduce_max_sync(0xffffffffu, eh);
+          ev = __reduce_max_sync(0xffffffffu, ev);
+          if (lane == 0) {
+            hb_r[g * TC_M + o] = eh;
+            vf_r[g * TC_M + o] = ev;
+          }
+        }
+      for (int c = threadIdx.x; c < Mr; c += NT) {   // columns over the leaf's rows: a thread per column
+        int eh = -2000, ev = -2000;
+        for (int o = 0; o < nF; ++o) {
+          eh = max(eh, xexp_of(HB[(long)o * Mr + c]));
+          ev = max(ev, xexp_of(VF[(long)o * Mr + c]));
+        }
+        hb_c[c] = eh;
+        vf_c[c] = ev;
+      }
+      for (int j = threadIdx.x; j < nF; j += NT) {   // L_Sigma^{-1} (lower) and L_Sigma
+        int er = -2000, ec = -2000, el = -2000;
+        for (int q = 0; q < nF; ++q) {
+          er = max(er, xexp_of(LSi[(long)j * nF + q]));
+          ec = max(ec, xexp_of(LSi[(long)q * nF + j]));
+          el = max(el, xexp_of(LSf[(long)q * nF + j]));
+        }
+        li_r[j] = er;
+        li_c[j] = ec;
+        l_c[j] = el;
+      }
+      __syncthreads();
+    }
     // Vbar_F = LSi' Hbar
     for (int l = 0; l < M && EMU && ok; ++l) {
-      ok = em_mma(cx, ea, LSi, 1, nF, nF, HB + l * r, 1, Mr, r, nF);
+      ok = em_mma(cx, ea, LSi, 1, nF, nF, HB + l * r, 1, Mr, r, nF, li_c, 0, hb_c + l * r, 0);
       if (ok && erow < nF) {
         double* out = VB + (long)erow * Mr + l * r;
 #pragma unroll
@@ -453,13 +510,19 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
     // LSibar = lower(Hbar V_F' + zbar y')  -> T1
     for (int j0 = 0; j0 < nF && EMU && ok; j0 += TC_N) {
       const int nb = min(TC_N, nF - j0);
-      ok = em_mma(cx, ea, HB, Mr, 1, nF, VF + (long)j0 * Mr, Mr, 1, nb, Mr);
+      ok = em_mma(cx, ea, HB, Mr, 1, nF, VF + (long)j0 * Mr, Mr, 1, nb, Mr, hb_r, TC_M, vf_r + j0, TC_M);
       if (ok && erow < nF) {
+        int e = -2000;
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
           const int j = j0 + ec0 + c;
-          if (ec0 + c < nb) T1[(long)erow * nF + j] = erow >= j ? ea.v[c] + zb[erow] * yv[j] : 0.0;
+          if (ec0 + c < nb) {
+            const double v = erow >= j ? ea.v[c] + zb[erow] * yv[j] : 0.0;
+            T1[(long)erow * nF + j] = v;
+            e = max(e, xexp_of(v));
+          }
         }
+        atomicMax(t1_r + erow, e);   // rows of LSibar, the Cholesky adjoint's first operand
       }
     }
     for (int bi = 0; bi < nrt && !EMU; ++bi)
@@ -487,7 +550,17 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
     __syncthreads();
     // Cholesky/inverse adjoint of Sigma_F in the leaf's global scratch: T3 = Sigmabar
     if (EMU) {
-      if (ok) ok = chol_inverse_adjoint_em(cx, T1, T2, T3, nF, nF, LSf, nF, LSi, nF, -1.0);
+      if (ok) ok = chol_inverse_adjoint_em(cx, T1, T2, T3, nF, nF, LSf, nF, LSi, nF, -1.0, t1_r, li_r, li_c, l_c);
+      if (ok) {   // rows of Sigmabar for the product below
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int o = warp; o < TC_M; o += NT / 32) {
+          int e = -2000;
+          if (o < nF)
+            for (int c = lane; c < nF; c += 32) e = max(e, xexp_of(T3[(long)o * nF + c]));
+          e = __reduce_max_sync(0xffffffffu, e);
+          if (lane == 0) t3_r[o] = e;
+        }
+      }
     } else {
       chol_inverse_adjoint<TILE>(T1, T2, T3, nF, nF, LSf, nF, LSi, nF, -1.0, stg);
     }
@@ -503,7 +576,7 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
     }
     // Vbar_F -= 2 Sigmabar V_F
     for (int l = 0; l < M && EMU && ok; ++l) {
-      ok = em_mma(cx, ea, T3, nF, 1, nF, VF + l * r, 1, Mr, r, nF);
+      ok = em_mma(cx, ea, T3, nF, 1, nF, VF + l * r, 1, Mr, r, nF, t3_r, 0, vf_c + l * r, 0);
       if (ok && erow < nF) {
         double* out = VB + (long)erow * Mr + l * r;
 #pragma unroll
