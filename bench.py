@@ -15,7 +15,8 @@ observations per leaf).  Three forms are timed on the same steps:
 
 The headline is the fastest form whose log-likelihoods stay within
 |d loglik| / n <= 1e-6 of the FP64 form; the others are reported beside it,
-together with loglik + gradient evaluations ("gradient", FP64 adjoint).
+together with loglik + gradient evaluations ("gradient": the emulated form, forward and adjoint on the
+FP64 emulation, beside the FP64 form). `--grad-only` times only the emulated loglik + gradient.
 
   value        evals/s with the inputs resident in HBM (CUDA events on the
                library's stream, max over ranks)
@@ -442,7 +443,7 @@ def main():
             handles[prec].close()
     h64 = handles["fp64"]
 
-    # ---- loglik + gradient: forward in the emulated and in the FP64 form, FP64 adjoint ----
+    # ---- loglik + gradient: the emulated form (forward and adjoint on the engine) and the FP64 form ----
     def time_grad(h):
         g_steps = max(2, args.steps // 2)
         h.loglik_grad(theta0)
@@ -464,7 +465,8 @@ def main():
     g_emu = time_grad(handles["emu"])
     g_64 = time_grad(h64)
     gradient = dict(g_emu)
-    gradient["what"] = ("loglik + d/d(sigma2, range, tau2): emulated-FP64 forward pass, FP64 reverse-mode adjoint")
+    gradient["what"] = ("loglik + d/d(sigma2, range, tau2): forward pass and reverse-mode adjoint in the "
+                        "emulated-FP64 form")
     gradient["max_rel_diff_vs_fp64_form"] = max(abs(a - b) / max(abs(b), 1e-300)
                                                 for a, b in zip(g_emu["grad"], g_64["grad"]))
     gradient["fp64"] = g_64
