@@ -22,7 +22,7 @@ blocking, fusion or reformulation:
   L^M, V^P; posterior basis matrices B~^{l,k}; marginal predictive mean and
   variance of y (not of the noisy z, Sec. 4.3).
 
-Readings where the paper is silent or garbled (each also listed in the design doc):
+Readings where the paper is silent or garbled:
 
 * R1: the paper's -2 log L omits the Gaussian constant; ``loglik`` returns
   -(d + u)/2 - (n/2) log(2 pi).
