@@ -943,12 +943,16 @@ static cudaError_t launch_leaf_adjoint(int tile, int nleaves, size_t sm, cudaStr
                                 (int)sm)))                                                                    \
     return e;                                                                                                 \
   leaf_adjoint_kernel<T, EMU><<<nleaves, NT, sm, s>>>(d_desc, gs, slot0, em_parts, status);
-  if (tile == 16) {
-    MRA_LEAF_ADJ(16)
-  } else if (tile == 32) {
-    MRA_LEAF_ADJ(32)
-  } else {
+  if constexpr (EMU) {   // the emulated instances use 64-wide FP64 tiles only (fewer instantiations)
     MRA_LEAF_ADJ(64)
+  } else {
+    if (tile == 64) {
+      MRA_LEAF_ADJ(64)
+    } else if (tile == 32) {
+      MRA_LEAF_ADJ(32)
+    } else {
+      MRA_LEAF_ADJ(16)
+    }
   }
 #undef MRA_LEAF_ADJ
   return cudaGetLastError();
@@ -963,12 +967,16 @@ static cudaError_t launch_post_adjoint(int tile, int m, int nregions, size_t sm,
                                 (int)sm)))                                                                    \
     return e;                                                                                                 \
   post_adjoint_kernel<T, EMU><<<nregions, NT, sm, s>>>(m, d_desc, gs, gb_ready, status);
-  if (tile == 16) {
-    MRA_POST_ADJ(16)
-  } else if (tile == 32) {
-    MRA_POST_ADJ(32)
-  } else {
+  if constexpr (EMU) {   // the emulated instances use 64-wide FP64 tiles only (fewer instantiations)
     MRA_POST_ADJ(64)
+  } else {
+    if (tile == 64) {
+      MRA_POST_ADJ(64)
+    } else if (tile == 32) {
+      MRA_POST_ADJ(32)
+    } else {
+      MRA_POST_ADJ(16)
+    }
   }
 #undef MRA_POST_ADJ
   return cudaGetLastError();
@@ -983,12 +991,16 @@ static cudaError_t launch_prior_adjoint(int tile, int m, int nregions, size_t sm
                                 (int)sm)))                                                                    \
     return e;                                                                                                 \
   prior_adjoint_kernel<T, EMU><<<nregions, NT, sm, s>>>(m, d_desc, gs, slot0, status);
-  if (tile == 16) {
-    MRA_PRIOR_ADJ(16)
-  } else if (tile == 32) {
-    MRA_PRIOR_ADJ(32)
-  } else {
+  if constexpr (EMU) {   // the emulated instances use 64-wide FP64 tiles only (fewer instantiations)
     MRA_PRIOR_ADJ(64)
+  } else {
+    if (tile == 64) {
+      MRA_PRIOR_ADJ(64)
+    } else if (tile == 32) {
+      MRA_PRIOR_ADJ(32)
+    } else {
+      MRA_PRIOR_ADJ(16)
+    }
   }
 #undef MRA_PRIOR_ADJ
   return cudaGetLastError();
@@ -1030,8 +1042,8 @@ cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs,
   if ((em_parts & 1) && (e = launch_hbar_em(hd, d_desc, gs, status, s, launches))) return e;
   {
     size_t sm = sizeof(double) * (MAXL * MAX_R_DEV + 3 * 128 + 2 * MAX_R_DEV + 32) + stg;
-    if (emu) {
-      sm += EM_STAGE_BYTES;
+    if (emu) {   // (the emulated instance's FP64 tiles are 64 wide: its staging sized for them)
+      sm += EM_STAGE_BYTES + sizeof(double) * 2 * KC * (64 + 2) - stg;
       if (sm < EM_SOLO_SMEM) sm = EM_SOLO_SMEM;
       e = launch_leaf_adjoint<true>(tile, st.nreg[M], sm, s, d_desc, gs, slot_leaf, em_parts, status);
     } else {
