@@ -134,7 +134,7 @@ TRAFFIC = {
                "(1.25 GB) + leaf_kernel_tc<1> (1.71 GB), at n = 2^18, M = 6 "
                "(profiles/chain_forward_and_leaf_emu_n256k.md) scaled by n M r to n = 2^20, M = 7",
         "sources": ["mra_mixed.cu", "mra_emu.cuh", "mra_tc.cuh", "mra_device.cuh", "mra_kernels.cuh"],
-        "sha1": "965a8d1e31e8620472e67fc6e8f86550428dfed3",
+        "sha1": "7dcd3fdb34bb3d74f2585a95499f65a18edc1b69",
     },
 }
 

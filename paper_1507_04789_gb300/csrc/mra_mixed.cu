@@ -852,7 +852,7 @@ __global__ void __launch_bounds__(NT) s_full_kernel(int L, const Desc* __restric
   for (int t = threadIdx.x; t < ng * Mr; t += NT) E[t] = sexp[t];
 }
 
-// Grid (level-(M-1) regions, M): column block l of Hbar for all rows under region p.
+// One CTA per (level-(M-1) region p, column block l), l fastest: column block l of Hbar for all rows under p.
 __global__ void __launch_bounds__(NT) hbar_kernel_em(const Desc* __restrict__ D, GradState gs, int* status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t mbar[2];
