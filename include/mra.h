@@ -151,9 +151,10 @@ int mra_loglik(mra_handle* h, const mra_params* theta, double* loglik_out);
  * A-update chains of Sec. 3.1-3.2 in reverse), in FP64; with MRA_PREC_EMU its
  * products run on the FP64 emulation of the tensor cores (gradient within
  * 1e-9 relative of the FP64 form's).  The first call allocates the adjoint
- * buffers (in the emulated form also a per-region S buffer of
- * nreg[M-1] (M r)^2 doubles when that is at most four times the size of H, and
- * n M r x 2 doubles of covariance derivatives).
+ * buffers (in the emulated form also, where free device memory allows, a
+ * per-region S buffer of nreg[M-1] (M r)^2 doubles when that is at most four
+ * times the size of H, and n M r x 2 doubles of covariance derivatives; without
+ * them the same gradient is formed more slowly).
  *   theta      : host pointer to one mra_params.
  *   loglik_out : host pointer to one double.
  *   grad_out   : host pointer to 3 doubles (d/dsigma2, d/drange, d/dtau2).

@@ -668,23 +668,14 @@ static int ensure_grad_arena(mra_handle* h) {
     }
   }
   if (M > 0) G.want(&h->gs.PartLeaf, (int64_t)nreg[M - 1] * M * (M + 1) / 2 * r * r);
-  // emulated form: the per-parent adjoint S for Hbar on the tensor cores, when
-  // it takes at most four times the memory of H (else the leaf adjoint forms
-  // Hbar in FP64 from the ancestors' blocks directly)
   h->gs.SF = nullptr;
   h->gs.SFexp = nullptr;
   h->gs.DC = nullptr;
   h->gs.VFexp = h->gs.VBexp = h->gs.XBexp = nullptr;
-  if (M > 0 && h->cfg.precision == MRA_PREC_EMU && (int64_t)nreg[M - 1] * M * r <= 4 * n) {
-    const int64_t Mr = (int64_t)M * r;
-    G.want(&h->gs.SF, (int64_t)nreg[M - 1] * Mr * Mr);
-    G.want(&h->gs.SFexp, (int64_t)nreg[M - 1] * ((Mr + 127) / 128) * Mr + 8);   // + the rows the engine rounds up to 8
-  }
   G.want(&h->lf.VF, n * (int64_t)M * r);
   G.want(&h->lf.LSf, (size_t)h->ls_cap);
   G.want(&h->gs.HB, n * (int64_t)M * r);
   if (h->cfg.precision == MRA_PREC_EMU && M > 0) {
-    G.want(&h->gs.DC, 2 * n * (int64_t)M * r);
     G.want(&h->gs.VFexp, (int64_t)nreg[M - 1] * 4 * M * r);
     G.want(&h->gs.VBexp, (int64_t)nreg[M - 1] * 4 * M * r);
     G.want(&h->gs.XBexp, (int64_t)nreg[M - 1] * 4 * M * r);
@@ -696,6 +687,28 @@ static int ensure_grad_arena(mra_handle* h) {
   for (int m = 0; m <= M; ++m) slots += nreg[m];
   if (M > 0) slots += nreg[M - 1];   // the emulated chain adjoint's, one per level-(M-1) region
   G.want(&h->gs.gpart, 3 * slots);
+  // Emulated form, two optional buffers, each taken only while 85 % of the free
+  // device memory holds it after everything above (the kernels have paths
+  // without them): the per-parent adjoint S for Hbar and Gbar on the tensor
+  // cores, when it is also at most four times the size of H (else the FP64
+  // kernels form Hbar and Gbar from the ancestors' blocks), then the chain's
+  // covariance derivative pairs (else the chain adjoint evaluates them).
+  if (M > 0 && h->cfg.precision == MRA_PREC_EMU) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
+    size_t base = 0;
+    for (auto& q : G.plan) base += Arena::align(q.second);
+    int64_t budget = (int64_t)(0.85 * (double)fr) - (int64_t)base;
+    const int64_t Mr = (int64_t)M * r, P = nreg[M - 1];
+    const int64_t sfe = P * ((Mr + 127) / 128) * Mr + 8;   // + the rows the engine rounds up to 8
+    const int64_t sf = (int64_t)Arena::align(8 * P * Mr * Mr) + (int64_t)Arena::align(4 * sfe);
+    if (P * Mr <= 4 * n && sf <= budget) {
+      G.want(&h->gs.SF, P * Mr * Mr);
+      G.want(&h->gs.SFexp, sfe);
+      budget -= sf;
+    }
+    if ((int64_t)Arena::align(16 * n * Mr) <= budget) G.want(&h->gs.DC, 2 * n * Mr);
+  }
   G.want(&h->d_grad, 4);
   cudaError_t e = G.commit();
   if (e) {
