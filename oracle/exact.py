@@ -13,17 +13,72 @@ import this module; it shares no code with the CUDA library.
   region at resolution m* < M, and C0(s1, s2) inside one leaf).  It never runs
   the prior/posterior recursions of Sec. 3, so agreement with them checks those
   recursions.  Dense in all points: meant for n up to a few hundred.
+
+The checkers import nothing from ``mra_oracle``; they read only the knots and
+the bounding box of the tree they are given: their covariance ``c0`` is the general Matern
+correlation through the modified Bessel function K_nu (scipy.special.kv),
+which reduces to the exponential at nu = 1/2 and to Eq. (mat15) at nu = 3/2,
+and their point locator ``cell_index`` works on the integer cell grid of each
+level (Morton interleave of the cell coordinates), not by descending the
+partition.  A mistake in the oracle's own C0 or partition therefore shows up
+as a disagreement with these checkers.
 """
 from __future__ import annotations
 
 import math
 
 import numpy as np
-
-from . import mra_oracle as O
+from scipy.spatial.distance import cdist
+from scipy.special import gamma, kv
 
 __all__ = ["exact_loglik", "exact_predict", "bruteforce_cov", "bruteforce_loglik",
-           "bruteforce_predict", "gaussian_loglik", "kriging"]
+           "bruteforce_predict", "gaussian_loglik", "kriging", "c0", "matern", "cell_index"]
+
+NU = {"exp": 0.5, "matern15": 1.5}
+
+
+def matern(h, nu):
+    """Matern correlation 2^(1-nu)/Gamma(nu) (sqrt(2 nu) h)^nu K_nu(sqrt(2 nu) h),
+    h = distance / range (the parameterisation of Eq. mat15 at nu = 3/2); 1 at h = 0."""
+    h = np.asarray(h, dtype=np.float64)
+    x = math.sqrt(2.0 * nu) * h
+    with np.errstate(invalid="ignore", over="ignore"):
+        rho = (2.0 ** (1.0 - nu) / gamma(nu)) * x ** nu * kv(nu, x)
+    return np.where(x == 0.0, 1.0, rho)
+
+
+def c0(X1, X2, theta, family, nonstat=False):
+    """C0(X1, X2) = sigma2 rho(|s1 - s2| / range), optionally times the
+    nonstationary variance factor sqrt(g(s1) g(s2)), g(s) = 1 + sin(4 pi s_x) / 2."""
+    X1 = np.asarray(X1, dtype=np.float64)
+    X2 = np.asarray(X2, dtype=np.float64)
+    C = theta[0] * matern(cdist(X1, X2) / theta[1], NU[family])
+    if nonstat:
+        s1 = np.sqrt(1.0 + 0.5 * np.sin(4.0 * math.pi * X1[:, 0]))
+        s2 = np.sqrt(1.0 + 0.5 * np.sin(4.0 * math.pi * X2[:, 0]))
+        C = C * s1[:, None] * s2[None, :]
+    return C
+
+
+def cell_index(pts, bbox, J, m, dim):
+    """Index of the level-m region holding each point: the integer cell (the
+    box cut into J^m equal parts in 1-D, 2^m x 2^m in 2-D, the last cell closed
+    at the box maximum), with the two cell coordinates bit-interleaved in 2-D
+    (child j = b_x + 2 b_y at every level)."""
+    pts = np.asarray(pts, dtype=np.float64).reshape(-1, dim)
+    if dim == 1:
+        x0, x1 = bbox
+        k = J ** m
+        return np.clip(np.floor((pts[:, 0] - x0) / (x1 - x0) * k), 0, k - 1).astype(np.int64)
+    x0, x1, y0, y1 = bbox
+    k = 2 ** m
+    ix = np.clip(np.floor((pts[:, 0] - x0) / (x1 - x0) * k), 0, k - 1).astype(np.int64)
+    iy = np.clip(np.floor((pts[:, 1] - y0) / (y1 - y0) * k), 0, k - 1).astype(np.int64)
+    out = np.zeros(pts.shape[0], dtype=np.int64)
+    for b in range(m):
+        out |= ((ix >> b) & 1) << (2 * b)
+        out |= ((iy >> b) & 1) << (2 * b + 1)
+    return out
 
 
 def gaussian_loglik(C, y):
@@ -41,14 +96,14 @@ def kriging(C_SS, C_PS, c_PP, y):
 
 
 def exact_loglik(locs, y, theta, family, nonstat=False):
-    C = O.cov(locs, locs, theta[:2], family, nonstat) + theta[2] * np.eye(locs.shape[0])
+    C = c0(locs, locs, theta[:2], family, nonstat) + theta[2] * np.eye(locs.shape[0])
     return gaussian_loglik(C, y)
 
 
 def exact_predict(locs, y, plocs, theta, family, nonstat=False):
-    C = O.cov(locs, locs, theta[:2], family, nonstat) + theta[2] * np.eye(locs.shape[0])
-    CP = O.cov(plocs, locs, theta[:2], family, nonstat)
-    cPP = np.diag(O.cov(plocs, plocs, theta[:2], family, nonstat))
+    C = c0(locs, locs, theta[:2], family, nonstat) + theta[2] * np.eye(locs.shape[0])
+    CP = c0(plocs, locs, theta[:2], family, nonstat)
+    cPP = np.diag(c0(plocs, plocs, theta[:2], family, nonstat))
     return kriging(C, CP, cPP, y)
 
 
@@ -71,8 +126,8 @@ def bruteforce_cov(tree, pts, theta, family, nonstat=False):
     # region of every point of Z at every level, by location (Sec. 2.2)
     reg = np.zeros((M + 1, Z.shape[0]), dtype=np.int64)
     for m in range(1, M + 1):
-        reg[m] = O.locate(Z, tree.boxes, J, m, dim) if m else 0
-    v = O.cov(Z, Z, theta, family, nonstat)           # v_0 = C0
+        reg[m] = cell_index(Z, tree.boxes[0][0], J, m, dim)
+    v = c0(Z, Z, theta, family, nonstat)              # v_0 = C0
     CM = np.zeros((npts, npts), dtype=v.dtype)
     P = np.arange(npts)
     for m in range(M):

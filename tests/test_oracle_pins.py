@@ -142,10 +142,11 @@ def test_p6_one_level_full_scale_closed_form():
     theta = (1.0, 0.25, 0.1)
     p = O.Problem(locs, y, M=1, r=9, family="exp")
     Q = p.tree.knots[0][0]
-    C = O.cov(locs, locs, theta[:2], "exp")
-    CQ = O.cov(locs, Q, theta[:2], "exp")
-    low = CQ @ np.linalg.solve(O.cov(Q, Q, theta[:2], "exp"), CQ.T)
-    same = p.tree.leaf_of[:, None] == p.tree.leaf_of[None, :]
+    C = E.c0(locs, locs, theta[:2], "exp")
+    CQ = E.c0(locs, Q, theta[:2], "exp")
+    low = CQ @ np.linalg.solve(E.c0(Q, Q, theta[:2], "exp"), CQ.T)
+    cell = E.cell_index(locs, (0.0, 1.0, 0.0, 1.0), 4, 1, 2)   # the checker's own locator
+    same = cell[:, None] == cell[None, :]
     C1 = low + np.where(same, C - low, 0.0)
     ll = E.gaussian_loglik(C1 + theta[2] * np.eye(120), y)
     assert O.loglik(p, theta) == pytest.approx(ll, rel=1e-12)
