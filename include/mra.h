@@ -202,6 +202,20 @@ int mra_leaf_offsets(mra_handle* h, int64_t* off_out, int64_t* perm_out);
 int mra_set_stream(mra_handle* h, void* stream);
 
 /*
+ * mra_set_option -- tune how a handle spends device memory.  Options:
+ *   MRA_OPT_GRAD_BUFFERS (default 1): with MRA_PREC_EMU, mra_loglik_grad may
+ *     take two optional buffers when free device memory holds them (the
+ *     per-region adjoint S of nreg[M-1] (M r)^2 doubles and n M r x 2 doubles
+ *     of covariance derivatives), which make the gradient faster; 0 never
+ *     takes them (the same gradient, formed by kernels that need neither).
+ *     Changing it releases the gradient storage; the next mra_loglik_grad
+ *     allocates it again under the new setting.
+ * Errors: MRA_ERR_ARG (null handle, unknown option or value).
+ */
+#define MRA_OPT_GRAD_BUFFERS 0
+int mra_set_option(mra_handle* h, int option, int64_t value);
+
+/*
  * mra_build_batch -- many independent datasets evaluated together (each with
  * its own shape cfgs[d], locations locs[d] (n x 2 row-major), data ys[d] and
  * size ns[d], all in the memory space `where`).  Every dataset gets its own
@@ -264,8 +278,12 @@ int mra_kernel_times(mra_handle* h, int kind, double* total_ms, int64_t* launche
  * library image, MRA_NOALLOC_SCRATCH_BYTES per device, which every GPU that
  * loads the library holds until the process exits (enough for problems of
  * roughly n = 16k with M = 4, r = 16, or n = 4096 with M = 3, r = 64).
- *   cfg, theta : as for mra_build / mra_loglik (host).
- *   locs, y    : device pointers, n x 2 row-major locations and n data.
+ *   cfg, theta : as for mra_build / mra_loglik (host), except that only
+ *                precision = MRA_PREC_FP64 and prune = 0 (complete tree) are
+ *                supported; other values give MRA_ERR_ARG naming the field.
+ *   locs, y    : device (or managed) pointers, n x 2 row-major locations and
+ *                n data; host memory is refused with MRA_ERR_ARG before any
+ *                kernel runs.
  *   stream     : cudaStream_t (as void*, NULL = legacy default stream).
  *   loglik_out : host pointer to one double.
  * The first call on a device looks up the scratch array's device address

@@ -208,6 +208,7 @@ struct mra_handle {
   // gradient (arena 4, allocated by the first mra_loglik_grad)
   Arena grad;
   bool have_grad_arena = false;
+  int grad_buffers = 1;        // MRA_OPT_GRAD_BUFFERS
   mra::GradState gs{};
   double* d_grad = nullptr;
   // timing
@@ -369,6 +370,30 @@ int mra_set_stream(mra_handle* h, void* stream) {
     h->graph = nullptr;
   }
   return MRA_OK;
+}
+
+int mra_set_option(mra_handle* h, int option, int64_t value) {
+  g_err.clear();
+  if (!h) return fail(MRA_ERR_ARG, "null handle");
+  if (option == MRA_OPT_GRAD_BUFFERS) {
+    if (value != 0 && value != 1) return fail(MRA_ERR_ARG, "MRA_OPT_GRAD_BUFFERS takes 0 or 1");
+    if (h->grad_buffers != (int)value && h->have_grad_arena) {   // re-planned by the next gradient call
+      h->grad.release();
+      h->have_grad_arena = false;
+      h->gs = mra::GradState{};
+      for (int m = 0; m < mra::MAXL; ++m) {
+        h->st.L[m] = h->st.Ltf[m] = nullptr;
+        h->st.licol[m] = h->st.vcol[m] = nullptr;
+      }
+      h->lf.VF = h->lf.LSf = nullptr;
+      h->d_grad = nullptr;
+      h->have_post = false;
+    }
+    h->grad_buffers = (int)value;
+    for (mra_handle* p : h->parts) p->grad_buffers = (int)value;
+    return MRA_OK;
+  }
+  return fail(MRA_ERR_ARG, "unknown option %d", option);
 }
 
 int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_t n, int where,
@@ -693,9 +718,12 @@ static int ensure_grad_arena(mra_handle* h) {
   // cores, when it is also at most four times the size of H (else the FP64
   // kernels form Hbar and Gbar from the ancestors' blocks), then the chain's
   // covariance derivative pairs (else the chain adjoint evaluates them).
-  if (M > 0 && h->cfg.precision == MRA_PREC_EMU) {
+  if (M > 0 && h->cfg.precision == MRA_PREC_EMU && h->grad_buffers) {
     size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      fr = 0;
+      cudaGetLastError();   // else the next launch check would report this query's error
+    }
     size_t base = 0;
     for (auto& q : G.plan) base += Arena::align(q.second);
     int64_t budget = (int64_t)(0.85 * (double)fr) - (int64_t)base;

@@ -104,15 +104,36 @@ extern "C" int mra_loglik_noalloc(const mra_config* cfg, const mra_params* theta
   mra::set_last_error("");
   if (!cfg || !theta || !locs || !y || !loglik_out) return err(MRA_ERR_ARG, "null argument");
   if (n < 1) return err(MRA_ERR_ARG, "n must be >= 1");
-  if (cfg->M < 0 || cfg->M > MRA_MAX_M || cfg->J != 4 || cfg->r < 1 || cfg->r > MRA_MAX_R ||
-      (cfg->cov_family != MRA_COV_EXP && cfg->cov_family != MRA_COV_MATERN15) ||
-      (cfg->nonstat != 0 && cfg->nonstat != 1) || cfg->precision != MRA_PREC_FP64 || cfg->prune != 0 ||
-      !(cfg->bbox[0] < cfg->bbox[1]) || !(cfg->bbox[2] < cfg->bbox[3]))
-    return err(MRA_ERR_ARG, "invalid configuration");
+  if (cfg->M < 0 || cfg->M > MRA_MAX_M) return err(MRA_ERR_ARG, "M must be in [0, %d]", MRA_MAX_M);
+  if (cfg->J != 4) return err(MRA_ERR_ARG, "J must be 4 (2-D midpoint quadtree)");
+  if (cfg->r < 1 || cfg->r > MRA_MAX_R) return err(MRA_ERR_ARG, "r must be in [1, %d]", MRA_MAX_R);
+  if (cfg->cov_family != MRA_COV_EXP && cfg->cov_family != MRA_COV_MATERN15)
+    return err(MRA_ERR_ARG, "unknown covariance family %d", cfg->cov_family);
+  if (cfg->nonstat != 0 && cfg->nonstat != 1) return err(MRA_ERR_ARG, "nonstat must be 0 or 1");
+  if (cfg->precision != MRA_PREC_FP64)
+    return err(MRA_ERR_ARG, "precision must be MRA_PREC_FP64 in the allocation-free entry point (got %d)",
+               cfg->precision);
+  if (cfg->prune != 0)
+    return err(MRA_ERR_ARG, "prune must be 0 in the allocation-free entry point (complete tree only)");
+  if (!(cfg->bbox[0] < cfg->bbox[1]) || !(cfg->bbox[2] < cfg->bbox[3]))
+    return err(MRA_ERR_ARG, "empty or invalid bounding box");
   if (!(std::isfinite(theta->sigma2) && std::isfinite(theta->range) && std::isfinite(theta->tau2) &&
         theta->sigma2 > 0 && theta->range > 0 && theta->tau2 >= 0))
     return err(MRA_ERR_ARG, "theta needs sigma2 > 0, range > 0, tau2 >= 0, all finite");
 
+  // locs and y are read by kernels: refuse host memory here rather than let a
+  // kernel dereference it (cudaPointerGetAttributes allocates nothing)
+  for (int q = 0; q < 2; ++q) {
+    cudaPointerAttributes pa{};
+    const cudaError_t pe = cudaPointerGetAttributes(&pa, q == 0 ? (const void*)locs : (const void*)y);
+    if (pe != cudaSuccess) {
+      cudaGetLastError();   // a failed query leaves its error as the runtime's last error: clear it
+      return err(MRA_ERR_ARG, "%s is not a pointer the CUDA runtime knows: %s", q == 0 ? "locs" : "y",
+                 cudaGetErrorString(pe));
+    }
+    if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)
+      return err(MRA_ERR_ARG, "%s must be device (or managed) memory", q == 0 ? "locs" : "y");
+  }
   cudaStream_t s = (cudaStream_t)stream;
   int64_t* launches = mra::launch_counter();
   void* base = nullptr;

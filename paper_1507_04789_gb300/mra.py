@@ -26,6 +26,7 @@ MRA_PREC_FP64, MRA_PREC_MIXED, MRA_PREC_EMU = 0, 1, 2
 PRECISIONS = {"fp64": MRA_PREC_FP64, "mixed": MRA_PREC_MIXED, "emu": MRA_PREC_EMU}
 MRA_HOST, MRA_DEVICE = 0, 1
 MRA_MAX_LEAF = 128
+MRA_OPT_GRAD_BUFFERS = 0
 FAMILIES = {"exp": MRA_COV_EXP, "matern15": MRA_COV_MATERN15}
 KERNEL_KINDS = ("prior", "leaf", "leaf_syrk", "post", "aggregate", "predict", "grad")
 
@@ -77,6 +78,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "mra_region_terms": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
         "mra_leaf_offsets": (ctypes.c_int, [_P, _P, _P]),
         "mra_set_stream": (ctypes.c_int, [_P, _P]),
+        "mra_set_option": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
         "mra_free": (None, [_P]),
         "mra_last_error": (ctypes.c_char_p, []),
         "mra_launch_count": (ctypes.c_int64, [ctypes.c_int]),
@@ -181,6 +183,10 @@ class Handle:
         """Run on a ``torch.cuda.Stream`` (or a raw cudaStream_t integer, 0 = default)."""
         ptr = getattr(stream, "cuda_stream", stream)
         _check(self._lib.mra_set_stream(self._h, _P(int(ptr) if ptr else None)))
+
+    def set_option(self, option: int, value: int) -> None:
+        """mra_set_option: e.g. ``set_option(MRA_OPT_GRAD_BUFFERS, 0)``."""
+        _check(self._lib.mra_set_option(self._h, int(option), int(value)))
 
     def set_data(self, y) -> None:
         if _is_torch_cuda(y):

@@ -118,3 +118,25 @@ def test_emu_batch_on_swath_data(mra):
         assert np.array_equal(be.loglik(thetas), c)     # graph replay is deterministic
     print("emu batch relative error:", np.abs(ref - c) / np.abs(ref))
     np.testing.assert_allclose(c, ref, rtol=LL_RTOL)
+
+
+def test_emu_gradient_without_optional_buffers(mra):
+    """MRA_OPT_GRAD_BUFFERS = 0: no per-parent S and no stored C0 derivatives, so
+    Hbar and Gbar come from the FP64 kernels and the chain adjoint evaluates the
+    covariance derivatives itself; the gradient still meets the oracle's bar and
+    equals the buffered form's to rounding."""
+    w = synth.workload("n16k_matern15_M4_r64")
+    locs, y, _ = w.generate()
+    theta = np.array([w.sigma2, w.kappa, w.tau2])
+    _, g_o = O.loglik_grad(O.Problem(locs, y, M=w.M, r=w.r, family=w.family), theta)
+    with mra.Handle(locs, y, M=w.M, r=w.r, family=w.family, precision="emu") as h:
+        ll1, g1 = h.loglik_grad(theta)
+        h.set_option(mra.MRA_OPT_GRAD_BUFFERS, 0)
+        ll0, g0 = h.loglik_grad(theta)
+        h.set_option(mra.MRA_OPT_GRAD_BUFFERS, 1)
+        ll2, g2 = h.loglik_grad(theta)
+    for g in (g0, g1):
+        assert np.abs(g - g_o).max() / np.abs(g_o).max() <= 1e-8
+    assert ll0 == ll1 == ll2
+    np.testing.assert_array_equal(g1, g2)
+    np.testing.assert_allclose(g0, g1, rtol=1e-10, atol=1e-10 * np.abs(g1).max())

@@ -44,6 +44,7 @@ def test_noalloc_matches_handle_path_twice():
     locs2 = rng.random((3000, 2))
     y2 = rng.standard_normal(3000)
     cases.append((locs2, y2, 3, 64, "matern15", (1.1, 0.12, 0.02)))
+    calls = []
     for locs, y, M, r, fam, theta in cases:
         with mra.Handle(locs, y, M=M, r=r, family=fam) as h:
             ref = h.loglik(theta)
@@ -54,6 +55,44 @@ def test_noalloc_matches_handle_path_twice():
         dy = torch.tensor(y, device="cuda", dtype=torch.float64)
         got = _noalloc(lib, mra, cfg, p, dl, dy, locs.shape[0])
         assert got == pytest.approx(ref, rel=LL_RTOL, abs=0)
+        calls.append((cfg, p, dl, dy, locs.shape[0], got))
+    # the property the entry point exists for: once the scratch address is
+    # resolved and every kernel is loaded, a call takes no device memory
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    res0 = torch.cuda.memory_reserved()
+    for cfg, p, dl, dy, n, got in calls:
+        assert _noalloc(lib, mra, cfg, p, dl, dy, n) == got
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_reserved() == res0
+
+
+def test_noalloc_refuses_host_pointers_and_names_fields():
+    """Host arrays are refused on the host side (no kernel runs), and a
+    configuration the entry point does not support names the field."""
+    from paper_1507_04789_gb300 import mra
+    lib = mra.load_library()
+    rng = np.random.default_rng(23)
+    locs = np.ascontiguousarray(rng.random((500, 2)))
+    y = rng.standard_normal(500)
+    bbox = (ctypes.c_double * 4)(0.0, 1.0, 0.0, 1.0)
+    cfg = mra.MraConfig(2, 4, 16, mra.MRA_COV_EXP, 0, mra.MRA_PREC_FP64, 0, bbox)
+    p = mra.MraParams(1.0, 0.1, 0.01)
+    fn = lib.mra_loglik_noalloc
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.POINTER(mra.MraConfig), ctypes.POINTER(mra.MraParams), ctypes.c_void_p,
+                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    out = ctypes.c_double()
+    rc = fn(ctypes.byref(cfg), ctypes.byref(p), locs.ctypes.data, y.ctypes.data, 500, None, ctypes.byref(out))
+    assert rc == mra.MRA_ERR_ARG
+    assert "device" in lib.mra_last_error().decode()
+    for field, bad in (("precision", mra.MRA_PREC_EMU), ("prune", 1)):
+        c = mra.MraConfig(2, 4, 16, mra.MRA_COV_EXP, 0, mra.MRA_PREC_FP64, 0, bbox)
+        setattr(c, field, bad)
+        rc = fn(ctypes.byref(c), ctypes.byref(p), locs.ctypes.data, y.ctypes.data, 500, None, ctypes.byref(out))
+        assert rc == mra.MRA_ERR_ARG
+        assert field in lib.mra_last_error().decode()
 
 
 def test_noalloc_rejects_oversized_problems():
