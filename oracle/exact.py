@@ -32,7 +32,8 @@ from scipy.spatial.distance import cdist
 from scipy.special import gamma, kv
 
 __all__ = ["exact_loglik", "exact_predict", "bruteforce_cov", "bruteforce_loglik",
-           "bruteforce_predict", "gaussian_loglik", "kriging", "c0", "matern", "cell_index"]
+           "bruteforce_predict", "bruteforce_predict_joint", "gaussian_loglik", "kriging", "c0", "matern",
+           "cell_index"]
 
 NU = {"exp": 0.5, "matern15": 1.5}
 
@@ -162,3 +163,16 @@ def bruteforce_predict(prob, theta, plocs):
     C = bruteforce_cov(tree, allp, theta[:2], prob.family, prob.nonstat)
     C_SS = C[:n, :n] + theta[2] * np.eye(n)
     return kriging(C_SS, C[n:, :n], np.diag(C[n:, n:]), prob.y)
+
+
+def bruteforce_predict_joint(prob, theta, plocs):
+    """Joint kriging of y at plocs under the dense C_M: mean and full covariance
+    C_M(P, P) - C_M(P, S) (C_M(S, S) + tau2 I)^{-1} C_M(S, P)."""
+    tree = prob.tree
+    n = prob.locs.shape[0]
+    allp = np.concatenate([prob.locs, np.asarray(plocs).reshape(-1, tree.dim)], axis=0)
+    C = bruteforce_cov(tree, allp, theta[:2], prob.family, prob.nonstat)
+    C_SS = C[:n, :n] + theta[2] * np.eye(n)
+    C_PS = C[n:, :n]
+    W = np.linalg.solve(C_SS, C_PS.T)
+    return C_PS @ np.linalg.solve(C_SS, prob.y), C[n:, n:] - C_PS @ W

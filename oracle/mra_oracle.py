@@ -20,7 +20,8 @@ blocking, fusion or reformulation:
 * Sec. 3.3: d and u recursions; -2 log L = d + u at the root.
 * Sec. 3.4, Prop. 2 and Eq. (bfrecursion): prior prediction quantities U^l,
   L^M, V^P; posterior basis matrices B~^{l,k}; marginal predictive mean and
-  variance of y (not of the noisy z, Sec. 4.3).
+  variance of y (not of the noisy z, Sec. 4.3); the joint posterior predictive
+  covariance that Prop. 2 implies, and draws from it (conditional simulation).
 
 Readings where the paper is silent or garbled:
 
@@ -36,6 +37,14 @@ Readings where the paper is silent or garbled:
 * R9: regions split at their midpoint, half-open [lo, mid), [mid, hi]; child
   index j = b_x + 2 b_y in 2-D; in 1-D child j covers the j-th of J equal parts.
 * R10: an empty leaf contributes A~ = 0, omega~ = 0, d = u = 0.
+* R17: a draw of eta~_R ~ N(K~_R omega^m_R, K~_R) (Prop. 2) takes the square
+  root F_R = L_R^{-T} Lt_R^{-T} of K~_R, with L_R L_R' = K_R^{-1} and
+  Lt_R Lt_R' = I + L_R^{-1} A^{m,m}_R L_R^{-T} (both lower Cholesky factors), so
+  that F_R F_R' = (K_R^{-1} + A^{m,m}_R)^{-1}; a draw of delta~ in leaf F takes
+  the lower Cholesky factor of V^P - L^M Sigma^{-1} L^M' over the leaf's
+  prediction points in ascending order of their index.  The standard normals
+  are inputs: xi (r per region of levels 0..M-1, complete tree, regions in
+  level then index order) and zeta (one per prediction point).
 * R12: exponential C0 = s2 exp(-h/kappa); Matern-1.5 C0 = s2 (1 + sqrt3 h/kappa)
   exp(-sqrt3 h/kappa) (Eq. mat15); optional nonstationary variance
   s2 sqrt(g(s1) g(s2)), g(s) = 1 + 0.5 sin(4 pi s_x).
@@ -66,6 +75,9 @@ __all__ = [
     "loglik",
     "loglik_grad",
     "predict",
+    "predict_joint",
+    "simulate",
+    "xi_offsets",
     "region_terms",
 ]
 
@@ -487,3 +499,144 @@ def predict(prob: Problem, theta, plocs, state=None):
         mean[pidx] = np.real(mu)
         var[pidx] = np.real(Psi)
     return mean, var
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.4: joint posterior predictive distribution and conditional simulation
+# ---------------------------------------------------------------------------
+
+def _joint_leaf(prob, P, Q, th, f, SP):
+    """Per leaf f: the terms of Prop. 2 for its prediction points SP.
+
+    Returns (Btm, D, dmean): Btm[m] = B~^{m+1,m} (n_P x r_m) for m < M, the
+    covariance D = V^P - L^M Sigma^{-1} L^M' of delta~ (full n_P x n_P) and
+    its mean L^M Sigma^{-1} y_F."""
+    tree = prob.tree
+    J, M = tree.J, tree.M
+    anc = ancestors(M, f, J)
+    SF = prob.locs[tree.obs[f]]
+    yF = prob.y[tree.obs[f]]
+    U = []
+    for l, (ml, il) in enumerate(anc):
+        Ql = SF if l == M else tree.knots[ml][il]
+        X = cov(SP, Ql, th, prob.family, prob.nonstat)
+        for k in range(l):
+            X = X - U[k] @ P.K[anc[k]] @ P.W[(ml, il)][k].T
+        U.append(X)
+    LM = U[M]
+    VP = cov(SP, SP, th, prob.family, prob.nonstat)
+    for k in range(M):
+        VP = VP - U[k] @ P.K[anc[k]] @ U[k].T                     # reading R4
+    S = P.Sigma[f]
+    if S.shape[0]:
+        D = VP - LM @ solve(S, LM.T)
+        dmean = LM @ solve(S, yF)
+        Bt = {(M, k): U[k] - LM @ solve(S, P.W[(M, f)][k]) for k in range(M)}
+    else:
+        D = VP
+        dmean = np.zeros(SP.shape[0])
+        Bt = {(M, k): U[k] for k in range(M)}
+    for l in range(M - 1, 0, -1):
+        Rl = anc[l]
+        for k in range(l):
+            Bt[(l, k)] = Bt[(l + 1, k)] - Bt[(l + 1, l)] @ Q.Kt[Rl] @ Q.A[Rl][(l, k)]
+    return [Bt[(m + 1, m)] for m in range(M)], D, dmean
+
+
+def predict_joint(prob: Problem, theta, plocs, state=None):
+    """Joint posterior predictive distribution of y at ``plocs`` (Prop. 2).
+
+    Prop. 2 writes y(S^P_F) | data = sum_{m<M} B~^{m+1,m}_F eta~_{R_m} + delta~_F
+    with independent eta~_R ~ N(K~_R omega^m_R, K~_R) shared by every leaf under
+    R and independent delta~_F per leaf, so for s1 in leaf F1 and s2 in F2
+        Cov(s1, s2) = sum_{m<M: R_m(F1) = R_m(F2)} B~^{m+1,m}(s1) K~_{R_m} B~^{m+1,m}(s2)'
+                      + 1[F1 = F2] D_F(s1, s2).
+    Returns (mean, cov) with cov the full np x np matrix."""
+    tree = prob.tree
+    J, M = tree.J, tree.M
+    th, tau2 = _split_theta(theta)
+    if state is None:
+        _, P, Q = loglik(prob, theta, return_state=True)
+    else:
+        P, Q = state
+    plocs = np.asarray(plocs, dtype=np.float64).reshape(-1, tree.dim)
+    npts = plocs.shape[0]
+    pleaf = locate(plocs, tree.boxes, J, M, tree.dim)
+    mean = np.zeros(npts)
+    cov_out = np.zeros((npts, npts))
+    terms = {}
+    for f in np.unique(pleaf):
+        pidx = np.flatnonzero(pleaf == f)
+        Btm, D, dmean = _joint_leaf(prob, P, Q, th, f, plocs[pidx])
+        anc = ancestors(M, f, J)
+        mu = dmean.copy()
+        for m in range(M):
+            Rm = anc[m]
+            mu = mu + Btm[m] @ (Q.Kt[Rm] @ Q.omega[Rm][m])           # reading R5
+        mean[pidx] = np.real(mu)
+        cov_out[np.ix_(pidx, pidx)] += np.real(D)
+        terms[f] = (pidx, Btm, anc)
+    leaves = list(terms)
+    for f1 in leaves:
+        p1, B1, a1 = terms[f1]
+        for f2 in leaves:
+            p2, B2, a2 = terms[f2]
+            for m in range(M):
+                if a1[m] != a2[m]:
+                    break                          # no common ancestor below level m
+                cov_out[np.ix_(p1, p2)] += np.real(B1[m] @ Q.Kt[a1[m]] @ B2[m].T)
+    return mean, cov_out
+
+
+def xi_offsets(tree):
+    """Start of region (m, i)'s r_i normals in a draw's xi vector (reading R17):
+    regions of levels 0..M-1 in level, then index order."""
+    off, pos = {}, 0
+    for m in range(tree.M):
+        for i in range(tree.J ** m):
+            off[(m, i)] = pos
+            pos += tree.knots[m][i].shape[0]
+    return off, pos
+
+
+def simulate(prob: Problem, theta, plocs, xi, zeta, state=None):
+    """Draws from the joint posterior predictive distribution (Prop. 2) given the
+    standard normals xi (nsim x len) and zeta (nsim x np), reading R17:
+        eta~_R = K~_R omega^m_R + F_R xi_R,  F_R = L_R^{-T} Lt_R^{-T},
+        delta~_F = L^M Sigma^{-1} y_F + chol(D_F) zeta_F,
+        y*(S^P_F) = sum_{m<M} B~^{m+1,m}_F eta~_{R_m} + delta~_F."""
+    tree = prob.tree
+    J, M = tree.J, tree.M
+    th, tau2 = _split_theta(theta)
+    if state is None:
+        _, P, Q = loglik(prob, theta, return_state=True)
+    else:
+        P, Q = state
+    plocs = np.asarray(plocs, dtype=np.float64).reshape(-1, tree.dim)
+    xi = np.atleast_2d(np.asarray(xi, dtype=np.float64))
+    zeta = np.atleast_2d(np.asarray(zeta, dtype=np.float64))
+    nsim = xi.shape[0]
+    off, _ = xi_offsets(tree)
+    # the square roots F_R of K~_R, and the means K~_R omega^m_R
+    F, mK = {}, {}
+    for (m, i), Kt in Q.Kt.items():
+        L = chol(P.W[(m, i)][m])                      # L L' = K^{-1}
+        Li = np.linalg.inv(L)
+        Lt = chol(np.eye(L.shape[0]) + Li @ Q.A[(m, i)][(m, m)] @ Li.T)
+        F[(m, i)] = Li.T @ np.linalg.inv(Lt).T
+        mK[(m, i)] = Kt @ Q.omega[(m, i)][m]
+    pleaf = locate(plocs, tree.boxes, J, M, tree.dim)
+    draws = np.zeros((nsim, plocs.shape[0]))
+    for f in np.unique(pleaf):
+        pidx = np.flatnonzero(pleaf == f)
+        Btm, D, dmean = _joint_leaf(prob, P, Q, th, f, plocs[pidx])
+        Lc = chol(D)
+        anc = ancestors(M, f, J)
+        for s in range(nsim):
+            v = dmean + Lc @ zeta[s, pidx]
+            for m in range(M):
+                R = anc[m]
+                xr = xi[s, off[R]:off[R] + F[R].shape[1]]
+                v = v + Btm[m] @ (mK[R] + F[R] @ xr)
+            draws[s, pidx] = np.real(v)
+    return draws

@@ -245,3 +245,46 @@ def test_region_terms_add_up():
 def test_not_positive_definite_is_reported():
     with pytest.raises(O.NotPositiveDefinite):
         O.chol(np.array([[1.0, 2.0], [2.0, 1.0]]))
+
+
+# ---- P10: joint posterior predictive and conditional simulation (Prop. 2) ------
+
+@pytest.mark.parametrize("M,r,family", [(1, 4, "exp"), (2, 9, "matern15"), (3, 4, "exp")])
+def test_p10_joint_covariance_matches_bruteforce(M, r, family):
+    """The covariance Prop. 2 implies between prediction points equals joint
+    kriging under the dense C_M of the process definition; its diagonal is the
+    marginal variance of predict."""
+    locs, y = _data(200, 120 + M)
+    rng = np.random.default_rng(121 + M)
+    plocs = np.concatenate([rng.random((30, 2)), 0.26 + 0.02 * rng.random((6, 2))])   # a crowded leaf too
+    theta = TH_M15 if family == "matern15" else TH_EXP
+    p = O.Problem(locs, y, M=M, r=r, family=family)
+    mean, cov = O.predict_joint(p, theta, plocs)
+    mb, cb = E.bruteforce_predict_joint(p, theta, plocs)
+    np.testing.assert_allclose(mean, mb, rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(cov, cb, rtol=1e-8, atol=1e-10)
+    mu, var = O.predict(p, theta, plocs)
+    np.testing.assert_allclose(np.diag(cov), var, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(mean, mu, rtol=1e-10, atol=1e-12)
+    assert np.allclose(cov, cov.T, rtol=0, atol=1e-12)
+
+
+def test_p10_simulation_is_an_exact_linear_map():
+    """A draw is mean + A [xi; zeta]: with xi, zeta = 0 it is the mean, and the
+    map's columns (unit inputs) satisfy A A' = the joint covariance, i.e. the
+    draws of standard normal inputs have exactly the predictive distribution."""
+    locs, y = _data(150, 130)
+    rng = np.random.default_rng(131)
+    plocs = rng.random((12, 2))
+    theta = TH_M15
+    p = O.Problem(locs, y, M=2, r=4, family="matern15")
+    _, P, Q = O.loglik(p, theta, return_state=True)
+    mean, cov = O.predict_joint(p, theta, plocs, state=(P, Q))
+    _, nxi = O.xi_offsets(p.tree)
+    assert nxi == 4 * (1 + 4)
+    npts = plocs.shape[0]
+    zero = O.simulate(p, theta, plocs, np.zeros((1, nxi)), np.zeros((1, npts)), state=(P, Q))
+    np.testing.assert_allclose(zero[0], mean, rtol=1e-12, atol=1e-14)
+    eye = np.eye(nxi + npts)
+    A = O.simulate(p, theta, plocs, eye[:, :nxi], eye[:, nxi:], state=(P, Q)) - mean
+    np.testing.assert_allclose(A.T @ A, cov, rtol=1e-9, atol=1e-11)
