@@ -50,10 +50,12 @@ def matern(h, nu):
 
 def c0(X1, X2, theta, family, nonstat=False):
     """C0(X1, X2) = sigma2 rho(|s1 - s2| / range), optionally times the
-    nonstationary variance factor sqrt(g(s1) g(s2)), g(s) = 1 + sin(4 pi s_x) / 2."""
+    nonstationary variance factor sqrt(g(s1) g(s2)), g(s) = 1 + sin(4 pi s_x) / 2;
+    theta = (sigma2, range) or, for family "matern", (sigma2, range, nu)."""
     X1 = np.asarray(X1, dtype=np.float64)
     X2 = np.asarray(X2, dtype=np.float64)
-    C = theta[0] * matern(cdist(X1, X2) / theta[1], NU[family])
+    nu = theta[2] if family == "matern" else NU[family]
+    C = theta[0] * matern(cdist(X1, X2) / theta[1], nu)
     if nonstat:
         s1 = np.sqrt(1.0 + 0.5 * np.sin(4.0 * math.pi * X1[:, 0]))
         s2 = np.sqrt(1.0 + 0.5 * np.sin(4.0 * math.pi * X2[:, 0]))
@@ -96,15 +98,20 @@ def kriging(C_SS, C_PS, c_PP, y):
     return C_PS @ np.linalg.solve(C_SS, y), c_PP - np.sum(C_PS * W.T, axis=1)
 
 
+def _ct(theta):
+    """C0's parameters from theta = (sigma2, range, tau2[, nu])."""
+    return (theta[0], theta[1]) + ((theta[3],) if len(theta) > 3 else ())
+
+
 def exact_loglik(locs, y, theta, family, nonstat=False):
-    C = c0(locs, locs, theta[:2], family, nonstat) + theta[2] * np.eye(locs.shape[0])
+    C = c0(locs, locs, _ct(theta), family, nonstat) + theta[2] * np.eye(locs.shape[0])
     return gaussian_loglik(C, y)
 
 
 def exact_predict(locs, y, plocs, theta, family, nonstat=False):
-    C = c0(locs, locs, theta[:2], family, nonstat) + theta[2] * np.eye(locs.shape[0])
-    CP = c0(plocs, locs, theta[:2], family, nonstat)
-    cPP = np.diag(c0(plocs, plocs, theta[:2], family, nonstat))
+    C = c0(locs, locs, _ct(theta), family, nonstat) + theta[2] * np.eye(locs.shape[0])
+    CP = c0(plocs, locs, _ct(theta), family, nonstat)
+    cPP = np.diag(c0(plocs, plocs, _ct(theta), family, nonstat))
     return kriging(C, CP, cPP, y)
 
 
@@ -152,7 +159,7 @@ def bruteforce_cov(tree, pts, theta, family, nonstat=False):
 
 def bruteforce_loglik(prob, theta):
     tree = prob.tree
-    C = bruteforce_cov(tree, prob.locs, theta[:2], prob.family, prob.nonstat)
+    C = bruteforce_cov(tree, prob.locs, _ct(theta), prob.family, prob.nonstat)
     return gaussian_loglik(C + theta[2] * np.eye(prob.locs.shape[0]), prob.y)
 
 
@@ -160,7 +167,7 @@ def bruteforce_predict(prob, theta, plocs):
     tree = prob.tree
     n = prob.locs.shape[0]
     allp = np.concatenate([prob.locs, np.asarray(plocs).reshape(-1, tree.dim)], axis=0)
-    C = bruteforce_cov(tree, allp, theta[:2], prob.family, prob.nonstat)
+    C = bruteforce_cov(tree, allp, _ct(theta), prob.family, prob.nonstat)
     C_SS = C[:n, :n] + theta[2] * np.eye(n)
     return kriging(C_SS, C[n:, :n], np.diag(C[n:, n:]), prob.y)
 
@@ -171,7 +178,7 @@ def bruteforce_predict_joint(prob, theta, plocs):
     tree = prob.tree
     n = prob.locs.shape[0]
     allp = np.concatenate([prob.locs, np.asarray(plocs).reshape(-1, tree.dim)], axis=0)
-    C = bruteforce_cov(tree, allp, theta[:2], prob.family, prob.nonstat)
+    C = bruteforce_cov(tree, allp, _ct(theta), prob.family, prob.nonstat)
     C_SS = C[:n, :n] + theta[2] * np.eye(n)
     C_PS = C[n:, :n]
     W = np.linalg.solve(C_SS, C_PS.T)

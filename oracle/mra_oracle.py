@@ -48,6 +48,9 @@ Readings where the paper is silent or garbled:
 * R12: exponential C0 = s2 exp(-h/kappa); Matern-1.5 C0 = s2 (1 + sqrt3 h/kappa)
   exp(-sqrt3 h/kappa) (Eq. mat15); optional nonstationary variance
   s2 sqrt(g(s1) g(s2)), g(s) = 1 + 0.5 sin(4 pi s_x).
+* R13: the Matern family of free smoothness nu (Sec. 4.1's family) in the same
+  scaling, s2 2^(1-nu)/Gamma(nu) z^nu K_nu(z), z = sqrt(2 nu) h/kappa, with nu a
+  fourth parameter; it equals the exponential at nu = 1/2 and Eq. mat15 at 3/2.
 
 Every routine is written so that the parameters may be complex: the gradient is
 the complex-step derivative (Squire & Trapp 1998) of ``loglik``, exact to
@@ -61,6 +64,8 @@ from dataclasses import dataclass, field
 
 import numpy as np
 import scipy.linalg as sla
+from scipy.special import gamma as _gamma
+from scipy.special import kv as _kv
 
 __all__ = [
     "NotPositiveDefinite",
@@ -79,6 +84,7 @@ __all__ = [
     "simulate",
     "xi_offsets",
     "region_terms",
+    "posterior_coarse",
 ]
 
 SQRT3 = math.sqrt(3.0)
@@ -212,13 +218,21 @@ def _dist(X1, X2):
 
 
 def cov(X1, X2, theta, family, nonstat=False):
-    """C0(X1, X2) for theta = (sigma2, kappa, ...); complex theta allowed."""
+    """C0(X1, X2) for theta = (sigma2, kappa) or, for the family "matern" of
+    free smoothness, (sigma2, kappa, nu); complex sigma2, kappa allowed."""
     sigma2, kappa = theta[0], theta[1]
     h = _dist(X1, X2) / kappa
     if family == "exp":
         rho = np.exp(-h)
     elif family == "matern15":
         rho = (1.0 + SQRT3 * h) * np.exp(-SQRT3 * h)
+    elif family == "matern":
+        # Sec. 4.1's Matern family in Eq. mat15's scaling: 2^(1-nu)/Gamma(nu) z^nu K_nu(z),
+        # z = sqrt(2 nu) h; K_nu from the library (complex z for the complex step)
+        nu = float(np.real(theta[2]))
+        z = math.sqrt(2.0 * nu) * h
+        zs = np.where(z == 0.0, 1.0, z)
+        rho = np.where(z == 0.0, 1.0, (2.0 ** (1.0 - nu) / _gamma(nu)) * zs ** nu * _kv(nu, zs))
     else:
         raise ValueError(f"unknown covariance family {family!r}")
     C = sigma2 * rho
@@ -288,11 +302,12 @@ def _in_scope(tree, m, i, subtree):
     return i // J ** (m - k) == idx
 
 
-def prior(tree, locs, theta, family, tau2, nonstat=False, subtree=None):
-    """Eq. (priorw) for every region, top-down; Sec. 4.3 nugget on Sigma_leaf."""
+def prior(tree, locs, theta, family, tau2, nonstat=False, subtree=None, levels=None):
+    """Eq. (priorw) for every region, top-down; Sec. 4.3 nugget on Sigma_leaf.
+    ``levels``: only the levels 0..levels."""
     J, M = tree.J, tree.M
     P = Prior()
-    for m in range(M + 1):
+    for m in range(M + 1 if levels is None else levels + 1):
         for i in range(J ** m):
             if not _in_scope(tree, m, i, subtree):
                 continue
@@ -365,17 +380,42 @@ def posterior(tree, locs, y, P, subtree=None):
             kids = [(m + 1, J * i + j) for j in range(J) if (m + 1, J * i + j) in At]
             A = {(k, l): sum(At[c][(k, l)] for c in kids) for k in range(m + 1) for l in range(m + 1)}
             om = [sum(wt[c][k] for c in kids) for k in range(m + 1)]
-            Kinv = P.W[(m, i)][m]
-            Kt = inv(Kinv + A[(m, m)])
-            Q.A[(m, i)] = A
-            Q.omega[(m, i)] = om
-            Q.Kt[(m, i)] = Kt
-            At[(m, i)] = {(k, l): A[(k, l)] - A[(k, m)] @ Kt @ A[(m, l)]
-                          for k in range(m) for l in range(m)}
-            wt[(m, i)] = [om[k] - A[(k, m)] @ Kt @ om[m] for k in range(m)]
-            Q.d[(m, i)] = (logdet(Kinv + A[(m, m)]) - logdet(Kinv)
-                           + sum(Q.d[c] for c in kids))
-            Q.u[(m, i)] = -om[m] @ Kt @ om[m] + sum(Q.u[c] for c in kids)
+            _post_region(P, Q, At, wt, m, i, A, om, sum(Q.d[c] for c in kids), sum(Q.u[c] for c in kids))
+    return Q
+
+
+def _post_region(P, Q, At, wt, m, i, A, om, dkids, ukids):
+    """One region of Eqs. (posterior), (helpquantities) and the d, u recursion
+    of Sec. 3.3, given its A^{k,l}, omega^k (Eq. mainquantities) and the sums
+    of its children's d and u."""
+    Kinv = P.W[(m, i)][m]
+    Kt = inv(Kinv + A[(m, m)])
+    Q.A[(m, i)] = A
+    Q.omega[(m, i)] = om
+    Q.Kt[(m, i)] = Kt
+    At[(m, i)] = {(k, l): A[(k, l)] - A[(k, m)] @ Kt @ A[(m, l)]
+                  for k in range(m) for l in range(m)}
+    wt[(m, i)] = [om[k] - A[(k, m)] @ Kt @ om[m] for k in range(m)]
+    Q.d[(m, i)] = logdet(Kinv + A[(m, m)]) - logdet(Kinv) + dkids
+    Q.u[(m, i)] = -om[m] @ Kt @ om[m] + ukids
+
+
+def posterior_coarse(tree, P, s, A_s, omega_s, dkids_s, ukids_s):
+    """The posterior of levels s..0 (Eqs. mainquantities, posterior,
+    helpquantities; Sec. 3.3) from every level-s region's A^{k,l}, omega^k
+    (k, l <= s) and its children's d, u sums, as the level-s subtrees of a
+    sharded evaluation hand them up (Sec. 3.5).  P needs levels 0..s."""
+    J = tree.J
+    Q = Posterior()
+    At, wt = {}, {}
+    for i in range(J ** s):
+        _post_region(P, Q, At, wt, s, i, A_s[i], omega_s[i], dkids_s[i], ukids_s[i])
+    for m in range(s - 1, -1, -1):
+        for i in range(J ** m):
+            kids = [(m + 1, J * i + j) for j in range(J)]
+            A = {(k, l): sum(At[c][(k, l)] for c in kids) for k in range(m + 1) for l in range(m + 1)}
+            om = [sum(wt[c][k] for c in kids) for k in range(m + 1)]
+            _post_region(P, Q, At, wt, m, i, A, om, sum(Q.d[c] for c in kids), sum(Q.u[c] for c in kids))
     return Q
 
 
@@ -401,7 +441,10 @@ class Problem:
 
 
 def _split_theta(theta):
+    """theta = (sigma2, kappa, tau2) or (sigma2, kappa, tau2, nu): C0's parameters and tau2."""
     sigma2, kappa, tau2 = theta[0], theta[1], theta[2]
+    if len(theta) > 3:
+        return (sigma2, kappa, theta[3]), tau2
     return (sigma2, kappa), tau2
 
 
@@ -429,15 +472,27 @@ def region_terms(prob: Problem, theta, m, i):
 
 
 def loglik_grad(prob: Problem, theta, step=1e-30):
-    """(loglik, d loglik / d(sigma2, kappa, tau2)) by the complex step."""
+    """(loglik, d loglik / d(sigma2, kappa, tau2)) by the complex step; with a
+    fourth parameter nu (family "matern") also d/dnu, by central differences
+    extrapolated once (Richardson): the library Bessel function takes no
+    complex order, and the extrapolated difference is accurate to about 1e-9
+    relative."""
     theta = np.asarray(theta, dtype=np.float64)
     ll = loglik(prob, theta)
-    g = np.zeros(3)
+    g = np.zeros(len(theta))
     for a in range(3):
         tc = theta.astype(np.complex128)
         h = step * max(abs(theta[a]), 1.0)
         tc[a] += 1j * h
         g[a] = np.imag(loglik(prob, tc)) / h
+    if len(theta) > 3:
+        def cd(e):
+            tp, tm = theta.copy(), theta.copy()
+            tp[3] += e
+            tm[3] -= e
+            return (loglik(prob, tp) - loglik(prob, tm)) / (2.0 * e)
+        e = 2e-3 * theta[3]
+        g[3] = (4.0 * cd(0.5 * e) - cd(e)) / 3.0
     return ll, g
 
 

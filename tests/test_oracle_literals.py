@@ -124,3 +124,14 @@ def test_build_tree_leaf_lists_and_boxes():
     # stable: original order inside a leaf
     t2 = O.build_tree(np.array([[0.9, 0.9], [0.8, 0.8], [0.95, 0.99]]), M=1, r=4)
     np.testing.assert_array_equal(t2.obs[3], [0, 1, 2])
+
+
+@pytest.mark.parametrize("nu,table", [(0.5, EXP), (1.5, M15)])
+def test_free_smoothness_family_at_half_integers(nu, table):
+    """The family "matern" (Sec. 4.1) equals the closed forms at nu = 1/2 and 3/2."""
+    sigma2, kappa = 0.9, 0.3
+    s0 = np.array([[0.2, 0.1]])
+    for frac, rho in table.items():
+        s1 = s0 + np.array([[0.0, frac * kappa]])
+        assert O.cov(s0, s1, (sigma2, kappa, nu), "matern")[0, 0] == pytest.approx(sigma2 * rho, rel=1e-13)
+    assert O.cov(s0, s0, (sigma2, kappa, 2.7), "matern")[0, 0] == pytest.approx(sigma2, rel=1e-15)

@@ -288,3 +288,40 @@ def test_p10_simulation_is_an_exact_linear_map():
     eye = np.eye(nxi + npts)
     A = O.simulate(p, theta, plocs, eye[:, :nxi], eye[:, nxi:], state=(P, Q)) - mean
     np.testing.assert_allclose(A.T @ A, cov, rtol=1e-9, atol=1e-11)
+
+
+# ---- P11: the Matern family of free smoothness (Sec. 4.1) -----------------------
+
+TH_NU = (1.2, 0.15, 0.05, 2.3)
+
+
+def test_p11_free_smoothness_exact_and_bruteforce():
+    locs, y = _data(120, 150)
+    plocs, _ = _data(10, 151)
+    p0 = O.Problem(locs[:80], y[:80], M=0, r=4, family="matern")
+    assert O.loglik(p0, TH_NU) == pytest.approx(E.exact_loglik(locs[:80], y[:80], TH_NU, "matern"), rel=1e-12)
+    p = O.Problem(locs, y, M=2, r=9, family="matern")
+    assert O.loglik(p, TH_NU) == pytest.approx(E.bruteforce_loglik(p, TH_NU), rel=1e-11)
+    mu, var = O.predict(p, TH_NU, plocs)
+    mb, vb = E.bruteforce_predict(p, TH_NU, plocs)
+    np.testing.assert_allclose(mu, mb, rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(var, vb, rtol=1e-8, atol=1e-10)
+    # nu = 3/2 is Eq. mat15
+    p15 = O.Problem(locs, y, M=2, r=9, family="matern15")
+    assert O.loglik(p, (1.2, 0.15, 0.05, 1.5)) == pytest.approx(O.loglik(p15, (1.2, 0.15, 0.05)), rel=1e-12)
+
+
+def test_p11_free_smoothness_gradient():
+    locs, y = _data(150, 160)
+    p = O.Problem(locs, y, M=2, r=9, family="matern")
+    theta = np.array(TH_NU)
+    _, g = O.loglik_grad(p, theta)
+    assert g.shape == (4,)
+    for a in range(4):
+        tp, tm = theta.copy(), theta.copy()
+        tp[a] *= 1 + 1e-5
+        tm[a] *= 1 - 1e-5
+        fd = (O.loglik(p, tp) - O.loglik(p, tm)) / (tp[a] - tm[a])
+        assert g[a] == pytest.approx(fd, rel=1e-6, abs=1e-6 * np.abs(g).max())
+    _, _, Q = O.loglik(p, theta, return_state=True)
+    assert theta[0] * g[0] + theta[2] * g[2] == pytest.approx((Q.u[(0, 0)] - 150) / 2, rel=1e-10)
