@@ -61,7 +61,7 @@ BF16_PEAK_FALLBACK = 1900.0  # TFLOP/s, used only without a measured peak file
 TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 / bf16 tensor rates
 EMU_PAIRS = 28               # bf16 slice products per emulated FP64 MAC (7 slices, weights t <= 8)
 TF32_PAIRS = 3               # TF32 products per 3xTF32 MAC
-ORACLE_SAMPLE_LEVEL = 2     # cpu baseline: one level-2 subtree = 1/16 of the leaves
+ORACLE_SAMPLE_LEVEL = 3     # cpu baseline: level-3 subtrees, 1/64 of the leaves each
 
 
 # ---------------------------------------------------------------------------
@@ -222,11 +222,15 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle sample (run in a child process with one BLAS thread)
+# CPU oracle sample: level-k subtrees of the same problem on every host core
+# (a spawn pool of one-BLAS-thread processes, started before any GPU work)
 # ---------------------------------------------------------------------------
 
-def _oracle_sample_child(workload: str, level: int, reps: int, seed: int) -> None:
-    import numpy as np  # noqa: F401
+_POOL_PROB = None
+
+
+def _pool_init(workload: str, seed: int) -> None:
+    global _POOL_PROB
     from oracle import mra_oracle as O
     from paper_1507_04789_gb300 import synth
     w = synth.workload(workload)
@@ -234,29 +238,96 @@ def _oracle_sample_child(workload: str, level: int, reps: int, seed: int) -> Non
     locs, y, _ = w.generate()
     p = O.Problem(locs, y, M=w.M, r=w.r, family=w.family)
     _ = p.tree
-    theta = (w.sigma2, w.kappa, w.tau2)
-    times = []
-    for k in range(reps):
+    _POOL_PROB = (p, (w.sigma2, w.kappa, w.tau2))
+
+
+def _pool_subtree(task):
+    from oracle import mra_oracle as O
+    level, k = task
+    p, theta = _POOL_PROB
+    t0 = time.perf_counter()
+    d, u = O.region_terms(p, theta, level, k)
+    return k, float(d), float(u), time.perf_counter() - t0
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def host_cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
+class OraclePool:
+    """The oracle on `workers` host processes, each holding the problem once."""
+
+    def __init__(self, workload: str, seed: int, workers: int):
+        import multiprocessing as mp
+        keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "CUDA_VISIBLE_DEVICES")
+        saved = {k: os.environ.get(k) for k in keys}
+        os.environ.update({"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1",
+                           "CUDA_VISIBLE_DEVICES": ""})
+        try:
+            self.pool = mp.get_context("spawn").Pool(workers, initializer=_pool_init, initargs=(workload, seed))
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.workers = workers
+        self.pool.map(time.sleep, [0.0] * workers)     # every worker has built its problem
+
+    def subtrees(self, level: int, ks):
         t0 = time.perf_counter()
-        O.loglik(p, theta, subtree=(level, k % (4 ** level)))
-        times.append(time.perf_counter() - t0)
-    print(json.dumps({"times": times}), flush=True)
+        res = self.pool.map(_pool_subtree, [(level, k) for k in ks], chunksize=1)
+        return res, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
 
 
-def oracle_sample(workload: str, level: int, reps: int, seed: int):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    cmd = [sys.executable, os.path.abspath(__file__), "--_oracle-child", workload, str(level), str(reps), str(seed)]
-    res = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=3600)
-    if res.returncode != 0:
-        raise RuntimeError(f"oracle sample failed:\n{res.stderr[-2000:]}")
-    times = json.loads(res.stdout.strip().splitlines()[-1])["times"]
-    frac = 4 ** level                                   # sample = 1/4^level of the leaves
-    evals_per_s = [1.0 / (t * frac) for t in times]
-    return {"value": statistics.median(evals_per_s), "unit": "evals/s", "cores": 1, "kind": "oracle",
-            "sample": f"prior+posterior of one level-{level} subtree (1/{frac} of the leaves, "
-                      f"{reps} run(s), median {statistics.median(times):.2f} s) scaled by {frac}; "
-                      f"numpy FP64, one BLAS thread"}
+def pool_workers(level: int) -> int:
+    """One process per core, at most one per subtree and, at about 0.5 GB of
+    oracle state per level-3 subtree at n = 2^20, within half the host memory."""
+    try:
+        mem_gb = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES") / 2 ** 30
+    except (ValueError, OSError, AttributeError):
+        mem_gb = 16.0
+    return max(1, min(host_cores(), 4 ** level, int(mem_gb / 2 / 1.0)))
+
+
+def oracle_sample(workload: str, level: int, seed: int):
+    """cpu_baseline: `workers` level-`level` subtrees (one per process) timed
+    together; evals/s = (subtrees / 4^level) / wall time.  Also returns the
+    sampled regions' d_R, u_R for the oracle error of the GPU forms."""
+    workers = pool_workers(level)
+    pool = OraclePool(workload, seed, workers)
+    try:
+        res, wall = pool.subtrees(level, range(workers))
+    finally:
+        pool.close()
+    frac = workers / 4 ** level
+    cpu_s = sum(r[3] for r in res)
+    out = {"value": frac / wall, "unit": "evals/s", "cores": workers, "kind": "oracle",
+           "cpu_model": host_cpu_model(), "host_cores": host_cores(),
+           "sample": f"prior+posterior of {workers} level-{level} subtrees ({workers}/{4 ** level} of the leaves, "
+                     f"one per process on {workers} cores, {wall:.2f} s wall, {cpu_s:.1f} s CPU) scaled to one "
+                     f"evaluation; numpy FP64, one BLAS thread per process"}
+    terms = {"level": level, "regions": [r[0] for r in res], "d": [r[1] for r in res], "u": [r[2] for r in res]}
+    return out, terms
 
 
 # ---------------------------------------------------------------------------
@@ -272,22 +343,31 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    per = []
+    from paper_1507_04789_gb300 import synth
+    level = min(ORACLE_SAMPLE_LEVEL, synth.workload(args.workload).M)
+    workers = pool_workers(level)
     t_all = time.perf_counter()
-    for k in range(args.warmup + args.steps):
-        s = oracle_sample(args.workload, ORACLE_SAMPLE_LEVEL + 1, 1, 0)
-        if k >= args.warmup:
-            per.append(s["value"])
+    pool = OraclePool(args.workload, 0, workers)
+    per = []
+    try:
+        for k in range(args.warmup + args.steps):
+            ks = [(k * workers + j) % 4 ** level for j in range(workers)]
+            _, wall = pool.subtrees(level, ks)
+            if k >= args.warmup:
+                per.append((workers / 4 ** level) / wall)
+    finally:
+        pool.close()
     value = statistics.median(per)
-    w = args.workload
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w, "precision": "fp64"},
-        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                         "sample": f"one level-{ORACLE_SAMPLE_LEVEL + 1} subtree per step (1/"
-                                   f"{4 ** (ORACLE_SAMPLE_LEVEL + 1)} of the leaves) scaled; numpy FP64, one thread"},
+        "config": {"workload": args.workload, "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": workers, "kind": "oracle",
+                         "cpu_model": host_cpu_model(), "host_cores": host_cores(),
+                         "sample": f"per step {workers} level-{level} subtrees ({workers}/{4 ** level} of the "
+                                   f"leaves, one per process on {workers} cores) scaled to one evaluation; "
+                                   f"numpy FP64, one BLAS thread per process"},
         "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": time.perf_counter() - t_all,
     }
@@ -329,6 +409,245 @@ def run_batch(args, world, rank, mra, np, torch):
     return out
 
 
+# Stages whose contractions run on the tensor cores in each form (the others on the FP64 pipe).
+TENSOR_STAGES = {"fp64": set(), "mixed": {"prior", "leaf"},
+                 "emu": {"prior", "chain", "leaf", "leaf_syrk", "post", "aggregate"}}
+STAGE_KERNEL = {
+    "fp64": {"prior": "prior_level_kernel", "leaf": "leaf_kernel", "leaf_syrk": "leaf_syrk_kernel",
+             "post": "post_level_kernel", "aggregate": "aggregate_kernel"},
+    "mixed": {"prior": "prior_level_kernel_tc<0>", "leaf": "leaf_kernel_tc<0>", "leaf_syrk": "leaf_syrk_kernel",
+              "post": "post_level_kernel", "aggregate": "aggregate_kernel"},
+    "emu": {"prior": "prior_level_kernel_tc<1>", "chain": "chain_forward_kernel_em", "leaf": "leaf_kernel_tc<1>",
+            "leaf_syrk": "leaf_syrk_kernel_em", "post": "post_level_kernel<EMU>", "aggregate": "aggregate_kernel_em"},
+}
+
+
+def contraction_share(stage: str, m: int, M: int, r: int, nF):
+    """Contraction FLOPs of one (level, stage) of an evaluation: the part of the
+    algorithmic FLOPs (mra_stats) that is matrix products, i.e. what a
+    tensor-core form runs on the engine (factorisations and vector terms
+    excluded)."""
+    import numpy as np
+    c = np.asarray(nF, dtype=np.float64)
+    tri = r * (r + 1) / 2.0
+    Mr = M * r
+    R = 4.0 ** m
+    if stage == "prior":
+        return R * (sum(2.0 * r * r * (l * r) + 2.0 * r * tri for l in range(m)) + 2.0 * tri * (m * r))
+    if stage == "chain":
+        return float(sum((2.0 * c * r * (l * r) + 2.0 * c * tri).sum() for l in range(M)))
+    if stage == "leaf":
+        return float((c * (c + 1) * Mr + Mr * c * (c + 1)).sum())
+    if stage == "leaf_syrk":
+        return float(Mr * (Mr + 1) * c.sum())
+    if stage == "post":
+        return R * m * r * r * (r + 1)
+    if stage == "aggregate":
+        return R * (m * r) * (m * r + 1) * r
+    return 0.0
+
+
+def level_table(st, prec, M, r, nF, bf16_peak, hbm_peak):
+    """Per level and stage of one form: time per evaluation, algorithmic FLOPs and
+    bytes (mra_stats), their rates and the fraction of the pipe's peak."""
+    ev = max(1, st["evaluations"])
+    pairs = EMU_PAIRS if prec == "emu" else TF32_PAIRS
+    rows = []
+    for m, row in enumerate(st["levels"]):
+        for stage, v in row.items():
+            if not v["launches"]:
+                continue
+            sec = v["ms"] / ev * 1e-3
+            tensor = stage in TENSOR_STAGES[prec] or (prec == "mixed" and stage == "chain")
+            peak = bf16_peak * (1.0 if prec == "emu" else TF32_PER_BF16) if tensor else FP64_PEAK_TFLOPS
+            alg = v["flops"] / sec / 1e12
+            out = {"level": m, "stage": stage, "kernel": STAGE_KERNEL[prec].get(stage, stage),
+                   "ms_per_step": v["ms"] / ev, "launches_per_step": v["launches"] / ev, "units": v["units"],
+                   "flops": v["flops"], "bytes": v["bytes"], "alg_tflops": alg,
+                   "pipe": "tensor" if tensor else "alu", "peak": peak, "frac": alg / peak,
+                   "hbm_gbs": v["bytes"] / sec / 1e9, "hbm_frac": v["bytes"] / sec / 1e9 / hbm_peak,
+                   "per_unit": ("algorithmic FP64 FLOPs (mra_stats) of the level's units"
+                                + (" against the bf16 tensor peak" if tensor and prec == "emu" else ""))}
+            if tensor:
+                eng = pairs * contraction_share(stage, m, M, r, nF) / sec / 1e12
+                out["engine_tflops"] = eng
+                out["engine_frac"] = eng / peak
+            rows.append(out)
+    return rows
+
+
+def predict_flops_per_point(M: int, r: int, c: float) -> float:
+    """FP64 FLOPs of the prediction kernel per point in a leaf of c observations:
+    the Uhat chain, v^P, P = C0 L_Sigma^{-T} - Uhat H', Bhat^{M,k} = Uhat^k - P H^k,
+    the Bhat recursion with Lt^{-T} and G, and the mean / variance sums."""
+    chain = sum(2.0 * l * r * r + r * (r + 1) for l in range(M))
+    rec = sum(r * (r + 1) + 4.0 * r + 2.0 * l * r * r for l in range(M))
+    return chain + rec + 2.0 * M * r + c * (c + 1) + 2.0 * M * r * c + 4.0 * c + 2.0 * c * M * r
+
+
+def run_prediction(args, world, rank, mra, np, torch, stream, handles, w, theta0, off):
+    """Kriging throughput (points/s) and errors: 2^20 cell-centred grid points on
+    the n = 2^20 problem (emulated-form factors against the FP64 form's), and the
+    1024 uniform points of the n = 4096 workload against the oracle."""
+    from oracle import mra_oracle as O
+    from paper_1507_04789_gb300 import synth
+    out = {}
+    g = 1024
+    cc = (np.arange(g) + 0.5) / g
+    gx, gy = np.meshgrid(cc, cc, indexing="xy")
+    grid = np.ascontiguousarray(np.stack([gx.ravel(), gy.ravel()], axis=1))
+    dgrid = torch.tensor(grid, device="cuda")
+    res = {}
+    nF = np.diff(off)
+    pts_per_leaf = grid.shape[0] / 4 ** w.M
+    flops_pt = predict_flops_per_point(w.M, w.r, float(nF.mean()))
+    for p in ("emu", "fp64"):
+        h = handles[p]
+        h.loglik(theta0)
+        h.predict(theta0, dgrid)                  # grows the prediction buffers
+        reps = 3
+        h.enable_timing(True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            mean, var = h.predict(theta0, dgrid)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        kms = h.kernel_times()["predict"][0] / reps
+        h.enable_timing(False)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            mh, vh = h.predict(theta0, grid)      # host buffers: copies inside
+        e2e_s = (time.perf_counter() - t0) / reps
+        res[p] = (mean.cpu().numpy(), var.cpu().numpy())
+        alg = flops_pt * grid.shape[0] / (kms * 1e-3) / 1e12
+        out[p] = {"points_per_s": world * grid.shape[0] / (ms * 1e-3), "ms_per_call": ms,
+                  "kernel_ms": kms, "kernel_fp64_alg_tflops": alg,
+                  "kernel_frac": alg / FP64_PEAK_TFLOPS,
+                  "e2e": {"points_per_s": world * grid.shape[0] / e2e_s, "h2d_bytes_per_call": int(grid.nbytes),
+                          "d2h_bytes_per_call": int(2 * 8 * grid.shape[0])}}
+    m64, v64 = res["fp64"]
+    me, ve = res["emu"]
+    out["grid"] = {"points": int(grid.shape[0]), "layout": f"{g} x {g} cell-centred grid on [0,1]^2",
+                   "points_per_leaf": pts_per_leaf, "kernel": "predict_kernel (FP64 pipe)",
+                   "fp64_flops_per_point": flops_pt, "peak": FP64_PEAK_TFLOPS,
+                   "emu_vs_fp64": {"mean_max_abs": float(np.max(np.abs(me - m64))),
+                                   "mean_max_rel": float(np.max(np.abs(me - m64)) / np.max(np.abs(m64))),
+                                   "var_max_rel": float(np.max(np.abs(ve - v64) / np.abs(v64)))}}
+    # the n = 4096 workload: every form against the oracle
+    w1 = synth.workload("n4096_exp_M3_r16")
+    l1, y1, p1 = w1.generate()
+    th1 = (w1.sigma2, w1.kappa, w1.tau2)
+    mo, vo = O.predict(O.Problem(l1, y1, M=w1.M, r=w1.r, family=w1.family), th1, p1)
+    small = {"workload": w1.name, "points": int(p1.shape[0])}
+    for p in ("fp64", "mixed", "emu"):
+        with mra.Handle(l1, y1, M=w1.M, r=w1.r, family=w1.family, precision=p) as h1:
+            h1.set_stream(stream)
+            h1.loglik(th1)
+            mg, vg = h1.predict(th1, p1)
+            dp = torch.tensor(p1, device="cuda")
+            h1.predict(th1, dp)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                h1.predict(th1, dp)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms1 = e0.elapsed_time(e1) / 5
+        small[p] = {"mean_max_rel_err_vs_oracle": float(np.max(np.abs(mg - mo)) / np.max(np.abs(mo))),
+                    "var_max_rel_err_vs_oracle": float(np.max(np.abs(vg - vo) / np.abs(vo))),
+                    "ms_per_call": ms1, "points_per_s": p1.shape[0] / (ms1 * 1e-3)}
+    out["n4096"] = small
+    return out
+
+
+def run_large(args, mra, np, torch):
+    """The n = 2^24 swath field (M = 10, r = 64, complete tree): the log-likelihood
+    evaluated as streamed level-s subtrees in the emulated form, then kriging at
+    the 2^20 cell-centred grid points; device memory is sampled after every call."""
+    from paper_1507_04789_gb300 import synth
+    w = synth.workload(args.workload)
+    t0 = time.perf_counter()
+    locs, y, grid = w.generate()
+    gen_s = time.perf_counter() - t0
+    theta0 = (w.sigma2, w.kappa, w.tau2)
+    stream = torch.cuda.Stream()
+    free0, total = torch.cuda.mem_get_info()
+    used = []
+
+    def sample():
+        torch.cuda.synchronize()
+        used.append(free0 - torch.cuda.mem_get_info()[0])
+
+    t0 = time.perf_counter()
+    h = mra.Handle(locs, y, M=w.M, r=w.r, family=w.family, nonstat=w.nonstat, precision="emu",
+                   stream_level=args.stream_level)
+    build_s = time.perf_counter() - t0
+    h.set_stream(stream)
+    sample()
+    thetas = [(theta0[0], theta0[1] * (1.0 + 0.01 * k), theta0[2]) for k in range(args.warmup + args.steps)]
+    for k in range(args.warmup):
+        h.loglik(thetas[k])
+    sample()
+    h.enable_timing(True)
+    clk = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.warmup, args.warmup + args.steps):
+        ll = h.loglik(thetas[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = h.stats()
+    h.enable_timing(False)
+    sample()
+    flops = sum(v["flops"] for row in st["levels"] for v in row.values())
+    h.loglik(theta0)
+    dgrid = torch.tensor(grid, device="cuda")
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    mean, var = h.predict(theta0, dgrid)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    pred_ms = p0.elapsed_time(p1)
+    sample()
+    off = h.leaf_offsets()
+    nF = np.diff(off)
+    h.close()
+    line = {
+        "metric": f"M-RA loglik evals/s at n=2^24 swath field (M={w.M}, r={w.r}), streamed level-s subtrees",
+        "value": 1e3 / ms, "unit": "evals/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "dtype": "f64+bf16x7 (emulated f64)", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "M": w.M, "r": w.r, "family": w.family, "nonstat": w.nonstat,
+                   "sigma2": w.sigma2, "range": w.kappa, "tau2": w.tau2, "stream_level": args.stream_level,
+                   "tree": "complete (every region, so that every grid point has its ancestors)",
+                   "active_leaves": int((nF > 0).sum()), "leaves": int(nF.size), "max_leaf": int(nF.max())},
+        "loglik": ll, "flops_per_step": flops, "fp64_alg_tflops": flops / (ms * 1e-3) / 1e12,
+        "device_memory_gb_max": max(used) / 1e9, "device_memory_gb_total": total / 1e9,
+        "prediction": {"points": int(grid.shape[0]), "ms_per_call": pred_ms,
+                       "points_per_s": grid.shape[0] / (pred_ms * 1e-3),
+                       "what": "each chunk's factors formed again from the resident coarse levels, then its "
+                               "points predicted (about one more evaluation)",
+                       "var_min": float(var.min().item()), "var_max": float(var.max().item())},
+        "generate_s": gen_s, "build_s": build_s, "clocks": clocks, "gradient": "not available on a streamed handle",
+        "per_level": [{"level": m, "stage": k, "ms_per_step": v["ms"] / max(1, st["evaluations"]),
+                       "flops": v["flops"]} for m, row in enumerate(st["levels"]) for k, v in row.items()],
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -338,9 +657,10 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--oracle-reps", type=int, default=1)
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-dataset swath batch")
     ap.add_argument("--batch-datasets", type=int, default=64)
+    ap.add_argument("--stream-level", type=int, default=2,
+                    help="level of the streamed subtrees for the n = 2^24 swath workload")
     ap.add_argument("--grad-only", action="store_true",
                     help="time only loglik + gradient in the emulated form (the launch list of the gradient)")
     args = ap.parse_args()
@@ -351,15 +671,20 @@ def main():
 
     rank, world, local = dist_env()
     # CPU baseline first (child process, before any GPU work in this process)
-    cpu = None
+    cpu, oracle_terms = None, None
+    from paper_1507_04789_gb300 import synth as _synth
+    if _synth.workload(args.workload).layout == "swath200":
+        args.no_cpu_baseline = True          # (the oracle would take hours on a subtree of 2^24 points)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(args.workload, ORACLE_SAMPLE_LEVEL, args.oracle_reps, 0)
+        cpu, oracle_terms = oracle_sample(args.workload, min(ORACLE_SAMPLE_LEVEL, _synth.workload(args.workload).M), 0)
 
     import numpy as np
     import torch
     from paper_1507_04789_gb300 import mra, synth
 
     torch.cuda.set_device(local)
+    if synth.workload(args.workload).layout == "swath200":
+        return run_large(args, mra, np, torch)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -425,9 +750,10 @@ def main():
         ms = max_over_ranks(e0.elapsed_time(e1))
         launches = mra.launch_count(reset=True)
         kt = h.kernel_times()
+        st = h.stats()
         h.enable_timing(False)
         return h, {"ms_per_step": ms / args.steps, "value": world * 1e3 * args.steps / ms, "lls": lls,
-                   "kernels": kt, "launches": launches, "clocks": clocks}
+                   "kernels": kt, "launches": launches, "clocks": clocks, "stats": st}
 
     # ---- the three forms on the same steps ----
     forms, handles = {}, {}
@@ -473,6 +799,7 @@ def main():
 
     peaks = measured_peaks()
     bf16_peak = peaks["bf16_tflops_sustained"] if peaks else BF16_PEAK_FALLBACK
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     peak_src = "of measured (bf16 sustained, MEASURED_PEAKS.json)" if peaks else "of fallback (recipe)"
 
     def kernel_table(prec):
@@ -496,36 +823,50 @@ def main():
     if forms["fp64"]["ms_per_step"] < forms[best]["ms_per_step"]:
         best = "fp64"
     head = forms[best]
-    # roofline of the dominant kernel of the headline form
-    kt = head["kernels"]
-    dom = max((k for k in kt if kt[k][1] > 0 and k in flops), key=lambda k: kt[k][0])
-    dom_ms, dom_n = kt[dom]
-    sec = dom_ms * 1e-3 / args.steps
-    cf = contraction_flops(w.M, w.r, np.diff(off), best)
-    if dom in cf:
-        pairs = EMU_PAIRS if best == "emu" else TF32_PAIRS
-        peak = bf16_peak * (1.0 if best == "emu" else TF32_PER_BF16)
-        achieved = pairs * cf[dom] / sec / 1e12
-        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None, "kernel": dom,
-                    "peak_source": peak_src + ("" if best == "emu" else " x nominal TF32/bf16 ratio"),
-                    "per_unit": f"{pairs} {'bf16' if best == 'emu' else 'TF32'} MACs per FP64 MAC of the "
-                                f"kernel's contractions",
-                    "fp64_alg_tflops": flops[dom] / sec / 1e12}
-    else:
-        achieved = flops[dom] / sec / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": dom,
-                    "peak_source": "nominal FP64 pipe (recipe); DFMA loop measured 1.19 TFLOP/s at 1995 MHz"}
-    traffic, how = kernel_traffic(best, dom, w.name)
+    # roofline of the dominant kernel of the headline form, from the per-level stats
+    nF_leaf = np.diff(off)
+    lvl_tabs = {p: level_table(forms[p]["stats"], p, w.M, w.r, nF_leaf, bf16_peak, hbm_peak)
+                for p in ("emu", "mixed", "fp64")}
+    rows = lvl_tabs[best]
+    dom = max(rows, key=lambda r_: r_["ms_per_step"])
+    roofline = {"bound": dom["pipe"], "achieved": dom["alg_tflops"], "peak": dom["peak"], "unit": "TFLOP/s",
+                "frac": dom["frac"], "traffic": None, "kernel": dom["kernel"], "level": dom["level"],
+                "stage": dom["stage"],
+                "peak_source": (peak_src if dom["pipe"] == "tensor" else
+                                "nominal FP64 pipe (recipe unit counts x 2.07 GHz); profiles/fp64_dfma_peak.md"),
+                "per_unit": dom["per_unit"], "units_per_launch": dom["units"],
+                "algorithmic_flops_per_launch": dom["flops"], "ms_per_launch": dom["ms_per_step"],
+                "launches_per_step": 1.0}
+    if "engine_tflops" in dom:
+        roofline["engine_issued_tflops"] = dom["engine_tflops"]
+        roofline["engine_frac"] = dom["engine_frac"]
+        roofline["engine_note"] = (f"tensor work the engine issues: {EMU_PAIRS if best == 'emu' else TF32_PAIRS} "
+                                   f"slice MACs per FP64 MAC of the kernel's contractions")
+    traffic, how = kernel_traffic(best, dom["kernel"], w.name)
     roofline["traffic"] = traffic
     if how:
         roofline["traffic_source"] = how
-    if best == "emu" and dom == "leaf":   # the stage is two kernels: the per-parent chain, then the leaves
-        roofline["stage_kernels"] = ["chain_forward_kernel_em", "leaf_kernel_tc<1>"]
-        dom_n *= 2
-    roofline.update({"launches_per_step": dom_n / args.steps, "kernels": kernel_table(best),
+    roofline["algorithmic_bytes_per_launch"] = dom["bytes"]
+    roofline.update({"per_level": rows, "kernels": kernel_table(best),
                      "step_fp64_alg_tflops": total_flops / (head["ms_per_step"] * 1e-3) / 1e12})
+
+    # ---- oracle error of the GPU forms at full size: the sampled subtrees' d_R, u_R ----
+    oracle_check = None
+    if oracle_terms:
+        lvl = oracle_terms["level"]
+        ks = oracle_terms["regions"]
+        od, ou = np.array(oracle_terms["d"]), np.array(oracle_terms["u"])
+        oracle_check = {"level": lvl, "regions": ks, "theta": list(theta0)}
+        for p in ("emu", "fp64"):
+            handles[p].loglik(theta0)
+            d_g, u_g = handles[p].region_terms(lvl)
+            oracle_check[p] = {"d_max_rel_err": float(np.max(np.abs(d_g[ks] - od) / np.abs(od))),
+                               "u_max_rel_err": float(np.max(np.abs(u_g[ks] - ou) / np.abs(ou)))}
+        if cpu:
+            cpu["oracle_check"] = oracle_check
+
+    # ---- prediction (Sec. 3.4): 2^20 grid points on this problem and the 1024 points of the n = 4096 workload ----
+    prediction = run_prediction(args, world, rank, mra, np, torch, stream, handles, w, theta0, off)
 
     # ---- end to end through the C ABI with host inputs (headline form) ----
     h = handles[best] if best in ("emu", "fp64") else mra.Handle(locs, y, M=w.M, r=w.r, family=w.family,
@@ -575,8 +916,12 @@ def main():
             "clocks": head["clocks"],
             "emu": form_line("emu"), "mixed": form_line("mixed"), "fp64": form_line("fp64"),
             "gradient": gradient, "loglik": head["lls"][-1], "flops_per_step": total_flops,
-            "batch": batch,
+            "batch": batch, "prediction": prediction, "oracle_check": oracle_check,
         }
+        for p in ("emu", "mixed", "fp64"):
+            line[p]["per_level"] = [{k: r_[k] for k in ("level", "stage", "ms_per_step", "alg_tflops", "frac",
+                                                        "hbm_gbs") + (("engine_frac",) if "engine_frac" in r_ else ())}
+                                    for r_ in lvl_tabs[p]]
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -584,7 +929,4 @@ def main():
 
 
 if __name__ == "__main__":
-    if len(sys.argv) > 1 and sys.argv[1] == "--_oracle-child":
-        _oracle_sample_child(sys.argv[2], int(sys.argv[3]), int(sys.argv[4]), int(sys.argv[5]))
-        sys.exit(0)
     sys.exit(main())

@@ -59,6 +59,11 @@ extern "C" {
 /* ---- enumerations ------------------------------------------------------ */
 #define MRA_COV_EXP       0 /* C0 = sigma2 exp(-h / range) */
 #define MRA_COV_MATERN15  1 /* C0 = sigma2 (1 + sqrt3 h / range) exp(-sqrt3 h / range), Eq. mat15 */
+#define MRA_COV_MATERN    2 /* C0 = sigma2 2^(1-nu)/Gamma(nu) z^nu K_nu(z), z = sqrt(2 nu) h / range: the
+                               Matern of smoothness nu = mra_params.nu (Sec. 4.1's family; nu = 1.5 is
+                               Eq. mat15, 0.5 the exponential), K_nu by an exponentially convergent
+                               trapezoidal rule (relative error about 1e-13, 0.05 <= nu <= 20); about
+                               20-100 times the cost of the closed forms per evaluation of C0 */
 
 #define MRA_PREC_FP64     0 /* every step in binary64 */
 #define MRA_PREC_MIXED    1 /* prior chain, leaf covariance and leaf solve products on the
@@ -87,6 +92,17 @@ typedef struct {
     int    prune;       /* 1: keep only regions whose subtree holds observations (empty subtrees
                            contribute nothing to the likelihood); 0: complete tree */
     double bbox[4];     /* x0, x1, y0, y1 of the domain; every location must lie inside */
+    int    stream_level;/* subtree streaming: s in 1..M-1 evaluates the tree as its level-s
+                           subtrees one after another in buffers sized for the largest
+                           (the factors of levels > s and of the leaves are never all
+                           resident; levels <= s and every region's d, u are); 0 lets
+                           mra_build stream, at the smallest s that fits, only when the
+                           factors of every level would exceed 80 % of the free device
+                           memory; -1 never streams.  A streamed handle evaluates
+                           mra_loglik (and mra_region_terms, mra_stats) and mra_predict (which
+                           forms each chunk's factors again from the resident coarse ones,
+                           about one more evaluation); mra_loglik_grad, mra_predict_joint,
+                           mra_simulate and mra_update return MRA_ERR_STATE. */
 } mra_config;
 
 /* Covariance parameters theta and the measurement-error variance (Sec. 2.1, 4.3). */
@@ -94,6 +110,7 @@ typedef struct {
     double sigma2;      /* > 0 */
     double range;       /* kappa > 0 */
     double tau2;        /* >= 0 */
+    double nu;          /* smoothness, 0.05 <= nu <= 20, read for MRA_COV_MATERN only */
 } mra_params;
 
 typedef struct mra_handle mra_handle;
@@ -157,7 +174,8 @@ int mra_loglik(mra_handle* h, const mra_params* theta, double* loglik_out);
  * them the same gradient is formed more slowly).
  *   theta      : host pointer to one mra_params.
  *   loglik_out : host pointer to one double.
- *   grad_out   : host pointer to 3 doubles (d/dsigma2, d/drange, d/dtau2).
+ *   grad_out   : host pointer to 3 doubles (d/dsigma2, d/drange, d/dtau2), and a
+ *                fourth, d/dnu, when cov_family = MRA_COV_MATERN (4 doubles then).
  * The first call allocates the adjoint storage (about 4 n M r doubles plus the
  * per-level adjoints); later calls allocate nothing.  Also leaves the posterior
  * factors for mra_predict at theta.  Errors: as mra_loglik, and MRA_ERR_OOM.
@@ -167,17 +185,90 @@ int mra_loglik_grad(mra_handle* h, const mra_params* theta, double* loglik_out, 
 /*
  * mra_predict -- marginal posterior predictive mean and variance of the
  * process y (not of the noisy data, Sec. 4.3) at np locations (Sec. 3.4,
- * Prop. 2, Eq. bfrecursion).  Uses the factors of the last mra_loglik, which
- * must have been called with the same theta (else MRA_ERR_STATE).
+ * Prop. 2, Eq. bfrecursion).  Uses the posterior factors of the last
+ * mra_loglik (or mra_loglik_grad) when that was at the same theta; otherwise
+ * it first evaluates the log-likelihood at theta (as mra_loglik, whose
+ * factors then stay in the handle).
  *   plocs    : np x 2 row-major locations inside bbox, host or device per `where`.
  *   mean_out, var_out : np doubles each, same memory space as plocs, caller-owned.
  * The handle keeps a prediction buffer (about np (M r + 8) doubles) that is
  * allocated on the first call and grown when np exceeds every earlier call's.
- * Errors: MRA_ERR_ARG (a location outside bbox), MRA_ERR_STATE, MRA_ERR_OOM,
- * MRA_ERR_CUDA.
+ * Errors: MRA_ERR_ARG (theta out of range, a location outside bbox),
+ * MRA_ERR_STATE (a batch handle), MRA_ERR_NOT_PD, MRA_ERR_OOM, MRA_ERR_CUDA.
  */
 int mra_predict(mra_handle* h, const mra_params* theta, const double* plocs, int64_t np,
                 int where, double* mean_out, double* var_out);
+
+/*
+ * mra_predict_joint -- the joint posterior predictive distribution of y at np
+ * locations (Prop. 2): mean (as mra_predict) and the full covariance
+ *   Cov(s1, s2) = sum over the regions R_m (m < M) that contain both points of
+ *                 B~^{m+1,m}(s1) K~_{R_m} B~^{m+1,m}(s2)'
+ *                 + [same leaf] (V^P - L^M Sigma^{-1} L^M')(s1, s2),
+ * since eta~_{R_m} is shared by every leaf under R_m and delta~ is per leaf.
+ *   plocs    : np x 2 row-major, host or device per `where`; at most
+ *              MRA_MAX_JOINT_LEAF points per leaf, np <= MRA_MAX_JOINT_POINTS.
+ *   mean_out : np doubles; cov_out: np x np row-major (caller's point order),
+ *              both in the memory space of plocs, caller-owned.
+ * Uses the posterior factors at theta as mra_predict does.  Host mode stages
+ * the covariance in a handle buffer of np^2 doubles (grown on demand).
+ * Errors: as mra_predict; MRA_ERR_LIMIT (too many points in a leaf or in all).
+ */
+#define MRA_MAX_JOINT_LEAF   64
+#define MRA_MAX_JOINT_POINTS 32768
+int mra_predict_joint(mra_handle* h, const mra_params* theta, const double* plocs, int64_t np, int where,
+                      double* mean_out, double* cov_out);
+
+/*
+ * mra_simulate -- nsim conditional simulations: draws from the joint posterior
+ * predictive distribution of y at np locations (Prop. 2), given standard
+ * normal inputs (the caller draws them, so any generator may be used):
+ *   eta~_R   = K~_R omega^m_R + L_R^{-T} Lt_R^{-T} xi_R   for every region R
+ *              of levels 0..M-1 (L_R L_R' = K_R^{-1}, Lt_R Lt_R' = I +
+ *              L_R^{-1} A^{m,m}_R L_R^{-T}: a square root of K~_R),
+ *   delta~_F = L^M Sigma^{-1} y_F + chol(V^P - L^M Sigma^{-1} L^M') zeta_F
+ *              per leaf F (its points in ascending order of their index),
+ *   draw     = sum_{m<M} B~^{m+1,m} eta~_{R_m} + delta~_F.
+ *   xi    : nsim x len (mra_simulate_xi_len: r per region of levels 0..M-1 of
+ *           the complete tree, levels in order, regions by Morton index;
+ *           entries of regions without prediction points are not read);
+ *           may be NULL when M = 0.
+ *   zeta  : nsim x np, one normal per prediction point (caller's order).
+ *   draws_out : nsim x np.  xi, zeta, draws_out and plocs share `where`.
+ * Errors: as mra_predict_joint; MRA_ERR_NOT_PD when the Cholesky factor of a
+ * leaf's delta~ covariance meets a non-positive pivot (prediction points of a
+ * leaf that coincide make it singular).
+ */
+int mra_simulate(mra_handle* h, const mra_params* theta, const double* plocs, int64_t np, int where, int64_t nsim,
+                 const double* xi, const double* zeta, double* draws_out);
+int mra_simulate_xi_len(mra_handle* h, int64_t* len_out);
+
+/*
+ * Two-phase evaluation over the level-s subtrees of a streamed handle
+ * (stream_level = s >= 1), for sharding one problem over several GPUs: the
+ * regions of one resolution are independent (Sec. 3.5), so every process
+ * builds the same handle, evaluates its own range of the level-s subtrees,
+ * all processes exchange the subtrees' summaries (one all-gather), and each
+ * finishes the coarse levels s..0 itself.
+ *
+ * mra_summary_len -- doubles per summary (*len_out: the level-s region's
+ *   A-hat blocks, T_s r^2 with T_s = (s+1)(s+2)/2, its omega-hat, (s+1) r, and
+ *   the (d, u) of up to four children, 8) and the number of level-s regions
+ *   (*nsub_out, compact order).
+ * mra_loglik_subtrees -- at theta: the prior of levels 0..s, then the
+ *   subtrees of level-s regions [first, first + count) (prior, leaves,
+ *   posterior up to the level-s aggregation); out (host, count x len) gets
+ *   their summaries.  count = 0 is allowed.
+ * mra_loglik_combine -- all nsub summaries (host, nsub x len, in region
+ *   order, from any processes' mra_loglik_subtrees at the same theta) in, the
+ *   posterior of levels s..0 run, *loglik_out the log-likelihood (as
+ *   mra_loglik; region terms of levels <= s then readable).
+ * Errors: MRA_ERR_STATE (not a streamed handle), MRA_ERR_ARG, MRA_ERR_NOT_PD,
+ * MRA_ERR_CUDA.
+ */
+int mra_summary_len(mra_handle* h, int64_t* len_out, int64_t* nsub_out);
+int mra_loglik_subtrees(mra_handle* h, const mra_params* theta, int64_t first, int64_t count, double* out);
+int mra_loglik_combine(mra_handle* h, const mra_params* theta, const double* summaries, double* loglik_out);
 
 /*
  * mra_region_terms -- the per-region log-determinant d_R and quadratic form
@@ -240,6 +331,18 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
 int mra_loglik_batch(mra_handle* h, const mra_params* thetas, double* loglik_out);
 
 /*
+ * mra_loglik_grad_batch -- log-likelihood and gradient (as mra_loglik_grad)
+ * of every dataset of a batch handle at its own parameters: thetas[d] (host,
+ * ndata entries) -> loglik_out[d] and grad_out[3 d .. 3 d + 2] =
+ * d loglik_d / d(sigma2, range, tau2) (host).  The datasets are differentiated
+ * one after another on the batch's stream (the forward pass and adjoint of
+ * each are the single-dataset ones); the first call allocates every dataset's
+ * adjoint storage.  Errors: as mra_loglik_grad, with the failing dataset's
+ * index in the text; MRA_ERR_STATE if h is not a batch handle.
+ */
+int mra_loglik_grad_batch(mra_handle* h, const mra_params* thetas, double* loglik_out, double* grad_out);
+
+/*
  * mra_autotune -- time the evaluation with every tile size the kernels offer
  * for this r (16, 32 or 64 rows/columns per tile, at least r) at `thetas`
  * (one mra_params, or ndata for a batch handle) and keep the fastest;
@@ -265,6 +368,48 @@ int mra_batch_info(mra_handle* h, int* ndata_out, int* tile_out);
 #define MRA_K_GRAD       6  /* reverse-mode gradient pass (all adjoint kernels) */
 int mra_enable_timing(mra_handle* h, int on);
 int mra_kernel_times(mra_handle* h, int kind, double* total_ms, int64_t* launches);
+
+/*
+ * mra_stats -- per-level work and time of the log-likelihood evaluation, for
+ * roofline fractions per level kernel.  For every level m = 0..M and stage
+ * (below): the device time and launches summed over the evaluations timed
+ * since mra_enable_timing(h, 1) (CUDA events on the handle's stream; zero
+ * while timing is off), and the algorithmic work of ONE evaluation of the
+ * handle's current tree and leaf occupancy: FLOPs (multiply-add = 2,
+ * symmetric and triangular products counted once, factorisations r^3/3) and
+ * HBM bytes (every operand a unit of work reads and every result it writes,
+ * once per unit).  A batch handle sums its datasets' work per level.
+ * The units and their counts follow the paper's per-region cost (Sec. 3.6):
+ *   MRA_STAGE_PRIOR      level m < M, per region: W^l chain, L_m (Eq. priorw)
+ *   MRA_STAGE_CHAIN      level M, emulated form only: the leaves' chain B^l,
+ *                        run per level-(M-1) region (in the other forms it is
+ *                        part of MRA_STAGE_LEAF)
+ *   MRA_STAGE_LEAF       level M, per leaf: Sigma, its factor, H, z, d, u
+ *   MRA_STAGE_LEAF_SYRK  level M, per level-(M-1) region: the leaves' Gram
+ *                        products summed into A, omega (Eq. helpquantities at
+ *                        m = M and Eq. mainquantities)
+ *   MRA_STAGE_POST       level m < M, per region: K~ factor, G, d_m, u_m
+ *   MRA_STAGE_AGGREGATE  level m in 1..M-1, per level-(m-1) region: the
+ *                        children's A~, omega~ summed (Eq. mainquantities)
+ * Errors: MRA_ERR_ARG (null argument).
+ */
+#define MRA_STAGE_PRIOR      0
+#define MRA_STAGE_CHAIN      1
+#define MRA_STAGE_LEAF       2
+#define MRA_STAGE_LEAF_SYRK  3
+#define MRA_STAGE_POST       4
+#define MRA_STAGE_AGGREGATE  5
+#define MRA_STAGES           6
+typedef struct {
+    int     M;                                      /* deepest level (leaves) */
+    int64_t evaluations;                            /* evaluations timed */
+    double  ms[MRA_MAX_M + 1][MRA_STAGES];          /* device time, summed */
+    int64_t launches[MRA_MAX_M + 1][MRA_STAGES];    /* kernel launches, summed */
+    double  flops[MRA_MAX_M + 1][MRA_STAGES];       /* algorithmic FLOPs of one evaluation */
+    double  bytes[MRA_MAX_M + 1][MRA_STAGES];       /* algorithmic HBM bytes of one evaluation */
+    double  units[MRA_MAX_M + 1][MRA_STAGES];       /* units of work (regions, leaves) of one evaluation */
+} mra_stats_t;
+int mra_stats(mra_handle* h, mra_stats_t* out);
 
 /*
  * mra_loglik_noalloc -- the log-likelihood of mra_build + mra_loglik in one

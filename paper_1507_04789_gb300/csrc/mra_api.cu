@@ -18,10 +18,13 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/mra.h"
 #include "mra_launch.h"
+
+static_assert(mra::JOINT_TILE == MRA_MAX_JOINT_LEAF, "one CTA holds a leaf's prediction points");
 
 namespace {
 
@@ -85,11 +88,17 @@ bool params_ok(const mra_params* t) {
          t->range > 0 && t->tau2 >= 0;
 }
 
+// The smoothness of MRA_COV_MATERN must lie in the range its Bessel-function
+// evaluation is accurate on.
+bool nu_ok(int family, const mra_params* t) {
+  return family != MRA_COV_MATERN || (std::isfinite(t->nu) && t->nu >= 0.05 && t->nu <= 20.0);
+}
+
 int check_config(const mra_config* cfg) {
   if (cfg->M < 0 || cfg->M > MRA_MAX_M) return fail(MRA_ERR_ARG, "M must be in [0, %d]", MRA_MAX_M);
   if (cfg->J != 4) return fail(MRA_ERR_ARG, "J must be 4 (2-D midpoint quadtree)");
   if (cfg->r < 1 || cfg->r > MRA_MAX_R) return fail(MRA_ERR_ARG, "r must be in [1, %d]", MRA_MAX_R);
-  if (cfg->cov_family != MRA_COV_EXP && cfg->cov_family != MRA_COV_MATERN15)
+  if (cfg->cov_family != MRA_COV_EXP && cfg->cov_family != MRA_COV_MATERN15 && cfg->cov_family != MRA_COV_MATERN)
     return fail(MRA_ERR_ARG, "unknown covariance family %d", cfg->cov_family);
   if (cfg->nonstat != 0 && cfg->nonstat != 1) return fail(MRA_ERR_ARG, "nonstat must be 0 or 1");
   if (cfg->precision != MRA_PREC_FP64 && cfg->precision != MRA_PREC_MIXED && cfg->precision != MRA_PREC_EMU)
@@ -168,6 +177,19 @@ void set_last_error(const char* msg) { g_err = msg; }
 int64_t* launch_counter() { return &g_launches; }
 }  // namespace mra
 
+namespace {
+// One subtree of a streamed evaluation: a level-s region and everything below
+// it.  Its compact region ids of every level m > s form the range [c0, c1)
+// (compact ids keep Morton order), its observations [obs0, obs1) and its
+// leaves' factor blocks [ls0, ls1).
+struct Chunk {
+  int64_t c0[mra::MAXL], c1[mra::MAXL];
+  int64_t obs0, obs1, ls0, ls1;
+  int64_t f0, nf;        // its leaves by Morton id: [f0, f0 + nf)
+  mra::Plan plan;
+};
+}  // namespace
+
 struct mra_handle {
   mra_config cfg;
   int64_t n = 0;
@@ -199,12 +221,23 @@ struct mra_handle {
   mra::Plan plan;
   double* pinned = nullptr;    // small pinned readback buffer
   int64_t ls_cap = 0;          // capacity of the ragged leaf-factor store (doubles)
+  // subtree streaming (cfg.stream_level): level s, its chunks, their plans and
+  // descriptors (d_desc holds one per chunk; levels <= s are shared by all)
+  int s_lvl = 0;
+  std::vector<Chunk> chunks;
+  std::vector<mra::Desc> chunk_descs;
+  mra::Plan plan_coarse_prior, plan_coarse_post;
   // prediction points (arena 3, grown on demand by mra_predict)
   Arena pred;
   int64_t pred_cap = 0;
   double *p_in = nullptr, *p_xs = nullptr, *p_ys = nullptr, *p_U = nullptr, *p_mean = nullptr, *p_var = nullptr;
   int32_t *p_leaf = nullptr, *p_counts = nullptr, *p_cursor = nullptr, *p_max = nullptr;
   int64_t *p_off = nullptr, *p_sq = nullptr, *p_perm = nullptr;
+  // joint prediction and simulation (arena 5, grown on demand)
+  Arena joint;
+  int64_t joint_np = 0, joint_io = 0;
+  double *j_D = nullptr, *j_io = nullptr;      // per-leaf D blocks; staging of host inputs / outputs
+  int32_t* j_leaf = nullptr;
   // gradient (arena 4, allocated by the first mra_loglik_grad)
   Arena grad;
   bool have_grad_arena = false;
@@ -216,6 +249,10 @@ struct mra_handle {
   bool timer_events = false;
   double ktime[8] = {0};
   int64_t kcount[8] = {0};
+  double stime[MRA_MAX_M + 1][MRA_STAGES] = {};
+  int64_t scount[MRA_MAX_M + 1][MRA_STAGES] = {};
+  int64_t nevals = 0;
+  std::vector<int32_t> leaf_counts;   // observations per leaf (Morton order), for mra_stats
   bool have_post = false;
   mra_params last{};
   // batch of datasets
@@ -252,6 +289,11 @@ void collect_times(mra_handle* h) {
     if (cudaEventElapsedTime(&ms, h->timer.ev[2 * k], h->timer.ev[2 * k + 1]) == cudaSuccess) {
       h->ktime[h->timer.kind[k]] += ms;
       h->kcount[h->timer.kind[k]] += 1;
+      const int st = h->timer.stage[k], lv = h->timer.level[k];
+      if (st >= 0 && lv >= 0 && lv <= MRA_MAX_M) {
+        h->stime[lv][st] += ms;
+        h->scount[lv][st] += 1;
+      }
     }
   }
   h->timer.count = 0;
@@ -299,13 +341,62 @@ cudaError_t upload_desc(mra_handle* h, const mra_params* theta) {
   for (int k = 0; k < 4; ++k) h->hd.sh.bbox[k] = h->cfg.bbox[k];
   h->hd.sh.mixed = h->cfg.precision == MRA_PREC_MIXED ? 1 : (h->cfg.precision == MRA_PREC_EMU ? 2 : 0);
   if (theta) {
-    h->hd.cv = mra::make_cov(theta->sigma2, theta->range, h->cfg.cov_family, h->cfg.nonstat);
+    h->hd.cv = mra::make_cov(theta->sigma2, theta->range, h->cfg.cov_family, h->cfg.nonstat, theta->nu);
     h->hd.tau2 = theta->tau2;
   }
   h->hd.nlmax = h->nlmax;
   h->hd.st = h->st;
   h->hd.lf = h->lf;
-  return cudaMemcpyAsync(h->d_desc, &h->hd, sizeof(mra::Desc), cudaMemcpyHostToDevice, h->stream);
+  if (!h->s_lvl) return cudaMemcpyAsync(h->d_desc, &h->hd, sizeof(mra::Desc), cudaMemcpyHostToDevice, h->stream);
+  // Streamed: one descriptor per chunk.  The arrays of levels > s and the leaf
+  // stores hold one chunk at a time; a chunk's descriptor points them at
+  // (buffer - first id x stride), so the kernels' indexing by global compact id
+  // (or observation offset) lands in the buffer for the ids of that chunk,
+  // which are the only ones its work lists name.
+  const int M = h->M, s = h->s_lvl;
+  const int64_t r = h->r, Mr = (int64_t)M * r, ng = (Mr + 127) / 128;
+  auto shift = [](auto* p, int64_t first, int64_t stride) {
+    using T = std::remove_pointer_t<decltype(p)>;
+    return p ? reinterpret_cast<T*>(reinterpret_cast<uintptr_t>(p) - (uintptr_t)(first * stride * (int64_t)sizeof(T)))
+             : p;
+  };
+  h->chunk_descs.assign(h->chunks.size(), h->hd);
+  for (size_t g = 0; g < h->chunks.size(); ++g) {
+    const Chunk& c = h->chunks[g];
+    mra::Desc& D = h->chunk_descs[g];
+    for (int m = s + 1; m < M; ++m) {
+      const int64_t i0 = c.c0[m], T = int64_t(m + 1) * (m + 2) / 2;
+      D.st.V[m] = shift(D.st.V[m], i0, r * m * r);
+      D.st.Li[m] = shift(D.st.Li[m], i0, r * r);
+      D.st.Acc[m] = shift(D.st.Acc[m], i0, T * r * r);
+      D.st.Om[m] = shift(D.st.Om[m], i0, (m + 1) * r);
+      D.st.Lt[m] = shift(D.st.Lt[m], i0, r * r);
+      D.st.G[m] = shift(D.st.G[m], i0, r * m * r);
+      D.st.gv[m] = shift(D.st.gv[m], i0, r);
+      D.st.vexp[m] = shift(D.st.vexp[m], i0, ((m * r + 127) / 128) * r);
+      D.st.gcol[m] = shift(D.st.gcol[m], i0, m * r);
+      D.st.liexp[m] = shift(D.st.liexp[m], i0, r);
+    }
+    D.lf.H = shift(D.lf.H, c.obs0, Mr);
+    D.lf.z = shift(D.lf.z, c.obs0, 1);
+    D.lf.LS = shift(D.lf.LS, c.ls0, 1);
+    D.lf.hcol = shift(D.lf.hcol, c.c0[M], Mr);
+    D.lf.hrow = shift(D.lf.hrow, c.obs0, ng);
+  }
+  return cudaMemcpyAsync(h->d_desc, h->chunk_descs.data(), sizeof(mra::Desc) * h->chunk_descs.size(),
+                         cudaMemcpyHostToDevice, h->stream);
+}
+
+// The launches of one evaluation: the whole plan, or (streamed) the coarse
+// prior, every chunk's subtree, then the coarse posterior.
+cudaError_t launch_evaluation(mra_handle* h) {
+  if (!h->s_lvl) return mra::launch_loglik(h->plan, h->d_desc, h->status, h->stream, &g_launches, &h->timer);
+  cudaError_t e;
+  if ((e = mra::launch_loglik(h->plan_coarse_prior, h->d_desc, h->status, h->stream, &g_launches, &h->timer)))
+    return e;
+  for (const Chunk& c : h->chunks)
+    if ((e = mra::launch_loglik(c.plan, h->d_desc, h->status, h->stream, &g_launches, &h->timer))) return e;
+  return mra::launch_loglik(h->plan_coarse_post, h->d_desc, h->status, h->stream, &g_launches, &h->timer);
 }
 
 // Binning into an existing tree arena (used by mra_build and mra_update).
@@ -347,6 +438,7 @@ void mra_free(mra_handle* h) {
   h->tree.release();
   h->state.release();
   h->pred.release();
+  h->joint.release();
   h->grad.release();
   h->batch.release();
   if (h->pinned) cudaFreeHost(h->pinned);
@@ -467,8 +559,94 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
       mra_free(h); return cuda_fail(e, "leaf counts");
     }
     build_tables(M, cfg->prune != 0, counts, h->tab);
+    h->leaf_counts = counts;
   }
   const std::vector<int32_t>& nreg = h->tab.nreg;
+  const bool emu = cfg->precision == MRA_PREC_EMU;
+  // ---- subtree streaming: the level s and the chunks (one per level-s region) ----
+  int s_lvl = 0;
+  if (cfg->stream_level > 0) {
+    if (cfg->stream_level >= M) { mra_free(h); return fail(MRA_ERR_ARG, "stream_level must be < M"); }
+    s_lvl = cfg->stream_level;
+  }
+  std::vector<int64_t> obs_pref(nl + 1, 0), ls_pref(nl + 1, 0);   // by leaf Morton id
+  for (int64_t f = 0; f < nl; ++f) {
+    obs_pref[f + 1] = obs_pref[f] + h->leaf_counts[f];
+    ls_pref[f + 1] = ls_pref[f] + (int64_t)h->leaf_counts[f] * h->leaf_counts[f];
+  }
+  auto make_chunks = [&](int sl, std::vector<Chunk>& out, std::vector<int64_t>& cmax, int64_t& omax, int64_t& lmax) {
+    out.assign(nreg[sl], Chunk{});
+    cmax.assign(M + 1, 0);
+    omax = lmax = 0;
+    for (int32_t g = 0; g < nreg[sl]; ++g) {
+      Chunk& c = out[g];
+      const int64_t ms = h->tab.mort[sl][g];
+      for (int m = 0; m <= M; ++m) c.c0[m] = c.c1[m] = 0;
+      c.c0[sl] = g;
+      c.c1[sl] = g + 1;
+      for (int m = sl + 1; m <= M; ++m) {
+        const int64_t lo = ms << (2 * (m - sl)), hi = (ms + 1) << (2 * (m - sl));
+        const auto& mt = h->tab.mort[m];
+        c.c0[m] = std::lower_bound(mt.begin(), mt.end(), (int32_t)lo) - mt.begin();
+        c.c1[m] = std::lower_bound(mt.begin(), mt.end(), (int32_t)std::min<int64_t>(hi, INT32_MAX)) - mt.begin();
+        if (hi > INT32_MAX) c.c1[m] = (int64_t)mt.size();
+        cmax[m] = std::max(cmax[m], c.c1[m] - c.c0[m]);
+      }
+      const int64_t f0 = ms << (2 * (M - sl)), f1 = (ms + 1) << (2 * (M - sl));
+      c.f0 = f0;
+      c.nf = f1 - f0;
+      c.obs0 = obs_pref[f0];
+      c.obs1 = obs_pref[f1];
+      c.ls0 = ls_pref[f0];
+      c.ls1 = ls_pref[f1];
+      omax = std::max(omax, c.obs1 - c.obs0);
+      lmax = std::max(lmax, c.ls1 - c.ls0);
+    }
+  };
+  // bytes of the factors with rc[m] regions' storage at every level and the leaf stores sized (obs, ls, leaves)
+  auto factor_bytes = [&](const std::vector<int64_t>& rc, int64_t obs, int64_t ls, int64_t leaves) {
+    double b = 0;
+    for (int m = 0; m < M; ++m) {
+      const double R = (double)rc[m], T = (m + 1) * (m + 2) / 2.0;
+      b += 8.0 * R * ((double)r * m * r * 2 + r * r * 2 + T * r * r + (m + 1) * r + r);
+      if (emu) b += 4.0 * R * (((m * r + 127) / 128) * r + m * r + r);
+    }
+    b += 8.0 * ((double)obs * M * r + obs + ls) + (emu ? 4.0 * ((double)leaves * M * r + obs * ((M * r + 127) / 128)) : 0);
+    return b;
+  };
+  std::vector<int64_t> full(M + 1);
+  for (int m = 0; m <= M; ++m) full[m] = nreg[m];
+  if (cfg->stream_level == 0 && M >= 2) {   // automatic: stream only when the factors of every level do not fit
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      fr = SIZE_MAX;
+      cudaGetLastError();
+    }
+    if (factor_bytes(full, n, tail, nreg[M]) > 0.8 * (double)fr) {
+      for (int sl = 1; sl < M && !s_lvl; ++sl) {
+        std::vector<Chunk> ch;
+        std::vector<int64_t> cm;
+        int64_t om, lm;
+        make_chunks(sl, ch, cm, om, lm);
+        std::vector<int64_t> rc(M + 1);
+        for (int m = 0; m <= M; ++m) rc[m] = m <= sl ? nreg[m] : cm[m];
+        if (factor_bytes(rc, om, lm, cm[M]) <= 0.5 * (double)fr) s_lvl = sl;
+      }
+      if (!s_lvl) { mra_free(h); return fail(MRA_ERR_OOM, "the factors do not fit in device memory even streamed"); }
+    }
+  }
+  h->s_lvl = s_lvl;
+  std::vector<int64_t> cap(full);      // storage in regions (levels) and leaf stores
+  int64_t obs_cap = n, ls_cap = tail;
+  if (s_lvl) {
+    std::vector<int64_t> cm;
+    int64_t om, lm;
+    make_chunks(s_lvl, h->chunks, cm, om, lm);
+    for (int m = s_lvl + 1; m <= M; ++m) cap[m] = cm[m];
+    obs_cap = std::max<int64_t>(om, 1);
+    ls_cap = std::max<int64_t>(lm, 1);
+  }
+  const int ndesc = s_lvl ? nreg[s_lvl] : 1;
   // ---- arena 2: tables, factors of every level and of the leaves -------------
   Arena& B = h->state;
   for (int m = 0; m <= M; ++m) {
@@ -482,7 +660,7 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
     }
   }
   for (int m = 0; m < M; ++m) {
-    const int64_t R = nreg[m];
+    const int64_t R = cap[m];
     const int64_t T = int64_t(m + 1) * (m + 2) / 2;
     B.want(&h->st.V[m], R * r * (int64_t)m * r);
     B.want(&h->st.Li[m], R * r * r);
@@ -491,27 +669,37 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
     B.want(&h->st.Lt[m], R * r * r);
     B.want(&h->st.G[m], R * r * (int64_t)m * r);
     B.want(&h->st.gv[m], R * r);
-    B.want(&h->st.dd[m], R);
-    B.want(&h->st.uu[m], R);
-    if (cfg->precision == MRA_PREC_EMU) {
+    B.want(&h->st.dd[m], (int64_t)nreg[m]);     // region terms of every level stay whole
+    B.want(&h->st.uu[m], (int64_t)nreg[m]);
+    if (emu) {
       if (m > 0) B.want(&h->st.vexp[m], R * ((int64_t)(m * r + 127) / 128) * r);
       if (m > 0) B.want(&h->st.gcol[m], R * (int64_t)m * r);
       B.want(&h->st.liexp[m], R * r);
     }
   }
   double *H, *z, *LS, *d, *u;
-  B.want(&H, n * (int64_t)M * r);
-  B.want(&z, n);
-  B.want(&LS, (size_t)tail);
+  B.want(&H, obs_cap * (int64_t)M * r);
+  B.want(&z, obs_cap);
+  B.want(&LS, (size_t)ls_cap);
   B.want(&d, nreg[M]);
   B.want(&u, nreg[M]);
   int32_t *hcol = nullptr, *hrow = nullptr;
-  if (cfg->precision == MRA_PREC_EMU) {
-    B.want(&hcol, nreg[M] * (int64_t)M * r);
-    B.want(&hrow, n * (int64_t)((M * r + 127) / 128));
+  if (emu) {
+    B.want(&hcol, cap[M] * (int64_t)M * r);
+    B.want(&hrow, obs_cap * (int64_t)((M * r + 127) / 128));
   }
-  B.want(&h->d_desc, 1);
-  h->ls_cap = tail;
+  B.want(&h->d_desc, ndesc);
+  int2* d_work = nullptr;
+  std::vector<int2> work;
+  if (s_lvl) {   // work lists of every chunk: (chunk, compact region) per level, leaves, Gram products
+    for (size_t g = 0; g < h->chunks.size(); ++g) {
+      Chunk& c = h->chunks[g];
+      for (int m = s_lvl; m <= M; ++m)   // (level s: the chunk's own region, the parent of its aggregation)
+        for (int64_t i = c.c0[m]; i < c.c1[m]; ++i) work.push_back(make_int2((int)g, (int)i));
+    }
+    B.want(&d_work, std::max<size_t>(work.size(), 1));
+  }
+  h->ls_cap = ls_cap;
   if ((e = B.commit())) { mra_free(h); return fail(MRA_ERR_OOM, "device allocation (factors): %s", cudaGetErrorString(e)); }
   for (int m = 0; m <= M; ++m) {
     if ((e = cudaMemcpyAsync(h->st.mort[m], h->tab.mort[m].data(), sizeof(int32_t) * nreg[m], cudaMemcpyHostToDevice, h->stream)) ||
@@ -521,6 +709,10 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
         (m < M && (e = cudaMemcpyAsync(h->st.ccnt[m], h->tab.ccnt[m].data(), sizeof(int32_t) * nreg[m], cudaMemcpyHostToDevice, h->stream)))) {
       mra_free(h); return cuda_fail(e, "tree tables");
     }
+  }
+  if (!work.empty() &&
+      (e = cudaMemcpyAsync(d_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, h->stream))) {
+    mra_free(h); return cuda_fail(e, "chunk work lists");
   }
   if ((e = cudaStreamSynchronize(h->stream))) { mra_free(h); return cuda_fail(e, "tree tables"); }
   h->lf.off = h->off;
@@ -535,7 +727,47 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   h->lf.u = u;
   h->lf.hcol = hcol;
   h->lf.hrow = hrow;
+  if (s_lvl) {   // per-chunk plans over the work lists, and the two coarse plans
+    size_t w = 0;
+    for (size_t g = 0; g < h->chunks.size(); ++g) {
+      Chunk& c = h->chunks[g];
+      mra::Plan& p = c.plan;
+      p = mra::Plan();
+      p.maxM = M;
+      p.tile = mra::tile_for_r(r);
+      p.r = r;
+      p.mixed = cfg->precision == MRA_PREC_MIXED ? 1 : (emu ? 2 : 0);
+      p.nlmax = h->nlmax;
+      p.prior_lo = p.post_lo = s_lvl + 1;
+      const int2* at[mra::MAXL + 1];
+      for (int m = s_lvl; m <= M; ++m) {
+        at[m] = d_work + w;
+        w += c.c1[m] - c.c0[m];
+      }
+      for (int m = s_lvl + 1; m < M; ++m) {
+        p.n_lvl[m] = (int)(c.c1[m] - c.c0[m]);
+        p.w_lvl[m] = at[m];
+        p.n_agg[m] = (int)(c.c1[m - 1] - c.c0[m - 1]);
+        p.w_agg[m] = at[m - 1];
+      }
+      p.n_leaf = (int)(c.c1[M] - c.c0[M]);
+      p.w_leaf = at[M];
+      p.n_syrk = (int)(c.c1[M - 1] - c.c0[M - 1]);
+      p.w_syrk = at[M - 1];
+      p.t_syrk = M * (M + 1) / 2;
+    }
+  }
   single_plan(h);
+  if (s_lvl) {
+    h->plan_coarse_prior = h->plan;        // levels 0..s of the prior pass
+    h->plan_coarse_prior.prior_hi = s_lvl + 1;
+    h->plan_coarse_prior.leaves = false;
+    h->plan_coarse_prior.post_hi = 0;
+    h->plan_coarse_post = h->plan;         // levels s..0 of the posterior pass
+    h->plan_coarse_post.prior_hi = 0;
+    h->plan_coarse_post.leaves = false;
+    h->plan_coarse_post.post_hi = s_lvl + 1;
+  }
   size_t need = cfg->precision != MRA_PREC_FP64 ? mra::leaf_tc_smem_bytes(h->nlmax, cfg->precision == MRA_PREC_EMU)
                                                  : mra::leaf_smem_bytes(r, h->nlmax);
   int dev = 0, optin = 0;
@@ -571,23 +803,143 @@ int mra_loglik(mra_handle* h, const mra_params* theta, double* loglik_out) {
   g_err.clear();
   if (!h || !loglik_out) return fail(MRA_ERR_ARG, "null argument");
   if (!h->parts.empty()) return fail(MRA_ERR_STATE, "use mra_loglik_batch on a batch handle");
-  if (!params_ok(theta)) return fail(MRA_ERR_ARG, "theta needs sigma2 > 0, range > 0, tau2 >= 0, all finite");
+  if (!params_ok(theta) || !nu_ok(h->cfg.cov_family, theta)) return fail(MRA_ERR_ARG, "theta needs sigma2 > 0, range > 0, tau2 >= 0 (and 0.05 <= nu <= 20 for MRA_COV_MATERN), all finite");
   h->have_post = false;
   cudaError_t e;
   if ((e = upload_desc(h, theta)) || (e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream)))
     return cuda_fail(e, "descriptor");
-  if ((e = mra::launch_loglik(h->plan, h->d_desc, h->status, h->stream, &g_launches, &h->timer)))
-    return cuda_fail(e, "loglik launch");
+  if ((e = launch_evaluation(h))) return cuda_fail(e, "loglik launch");
   int hs[4];
   double du[2];
   const double* srcs[2];
   if (h->M > 0) { srcs[0] = h->st.dd[0]; srcs[1] = h->st.uu[0]; }
   else { srcs[0] = h->lf.d; srcs[1] = h->lf.u; }
   if ((e = sync_status(h, hs, du, 2, srcs))) return cuda_fail(e, "loglik");
+  if (h->timer.on) ++h->nevals;
   collect_times(h);
   if (hs[0]) return status_error(hs);
   *loglik_out = -0.5 * (du[0] + du[1]) - 0.5 * (double)h->n * std::log(2.0 * M_PI);
   h->have_post = true;
+  h->last = *theta;
+  return MRA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Two-phase evaluation over level-s subtrees (multi-GPU sharding)
+// ---------------------------------------------------------------------------
+// Summary of a level-s region R after its subtree: A-hat_R (T_s packed r x r
+// blocks), omega-hat_R ((s + 1) r) and the (d, u) of its (up to 4) children.
+static int64_t summary_len(const mra_handle* h) {
+  const int64_t s = h->s_lvl, r = h->r;
+  return (s + 1) * (s + 2) / 2 * r * r + (s + 1) * r + 8;
+}
+
+int mra_summary_len(mra_handle* h, int64_t* len_out, int64_t* nsub_out) {
+  g_err.clear();
+  if (!h || !len_out || !nsub_out) return fail(MRA_ERR_ARG, "null argument");
+  if (!h->s_lvl) return fail(MRA_ERR_STATE, "not a streamed handle (stream_level >= 1)");
+  *len_out = summary_len(h);
+  *nsub_out = (int64_t)h->chunks.size();
+  return MRA_OK;
+}
+
+int mra_loglik_subtrees(mra_handle* h, const mra_params* theta, int64_t first, int64_t count, double* out) {
+  g_err.clear();
+  if (!h || !theta || (count > 0 && !out)) return fail(MRA_ERR_ARG, "null argument");
+  if (!h->s_lvl) return fail(MRA_ERR_STATE, "not a streamed handle (stream_level >= 1)");
+  if (!params_ok(theta) || !nu_ok(h->cfg.cov_family, theta)) return fail(MRA_ERR_ARG, "theta needs sigma2 > 0, range > 0, tau2 >= 0 (and 0.05 <= nu <= 20 for MRA_COV_MATERN), all finite");
+  const int64_t nsub = (int64_t)h->chunks.size();
+  if (first < 0 || count < 0 || first + count > nsub)
+    return fail(MRA_ERR_ARG, "subtrees [%lld, %lld) outside [0, %lld)", (long long)first, (long long)(first + count),
+                (long long)nsub);
+  h->have_post = false;
+  cudaError_t e;
+  if ((e = upload_desc(h, theta)) || (e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream)))
+    return cuda_fail(e, "descriptor");
+  if ((e = mra::launch_loglik(h->plan_coarse_prior, h->d_desc, h->status, h->stream, &g_launches, &h->timer)))
+    return cuda_fail(e, "coarse prior");
+  for (int64_t g = first; g < first + count; ++g)
+    if ((e = mra::launch_loglik(h->chunks[g].plan, h->d_desc, h->status, h->stream, &g_launches, &h->timer)))
+      return cuda_fail(e, "subtree");
+  int hs[4];
+  if ((e = sync_status(h, hs, nullptr, 0, nullptr))) return cuda_fail(e, "subtrees");
+  collect_times(h);
+  if (hs[0]) return status_error(hs);
+  if (count == 0) return MRA_OK;
+  const int s = h->s_lvl, M = h->M;
+  const int64_t r = h->r, T = int64_t(s + 1) * (s + 2) / 2, L = summary_len(h);
+  std::vector<double> A(count * T * r * r), Om(count * (s + 1) * r);
+  const int32_t c_lo = h->tab.cfirst[s][first];
+  const int32_t c_hi = h->tab.cfirst[s][first + count - 1] + h->tab.ccnt[s][first + count - 1];
+  std::vector<double> dk(std::max(c_hi - c_lo, 1)), uk(dk.size());
+  const double* dsrc = s + 1 == M ? h->lf.d : h->st.dd[s + 1];
+  const double* usrc = s + 1 == M ? h->lf.u : h->st.uu[s + 1];
+  if ((e = cudaMemcpyAsync(A.data(), h->st.Acc[s] + first * T * r * r, sizeof(double) * A.size(),
+                           cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaMemcpyAsync(Om.data(), h->st.Om[s] + first * (s + 1) * r, sizeof(double) * Om.size(),
+                           cudaMemcpyDeviceToHost, h->stream)) ||
+      (c_hi > c_lo && (e = cudaMemcpyAsync(dk.data(), dsrc + c_lo, sizeof(double) * (c_hi - c_lo),
+                                           cudaMemcpyDeviceToHost, h->stream))) ||
+      (c_hi > c_lo && (e = cudaMemcpyAsync(uk.data(), usrc + c_lo, sizeof(double) * (c_hi - c_lo),
+                                           cudaMemcpyDeviceToHost, h->stream))) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return cuda_fail(e, "summaries");
+  for (int64_t k = 0; k < count; ++k) {
+    double* o = out + k * L;
+    memcpy(o, A.data() + k * T * r * r, sizeof(double) * T * r * r);
+    memcpy(o + T * r * r, Om.data() + k * (s + 1) * r, sizeof(double) * (s + 1) * r);
+    double* du = o + T * r * r + (s + 1) * r;
+    for (int j = 0; j < 8; ++j) du[j] = 0.0;
+    const int32_t cf = h->tab.cfirst[s][first + k], cc = h->tab.ccnt[s][first + k];
+    for (int32_t j = 0; j < cc; ++j) {
+      du[2 * j] = dk[cf + j - c_lo];
+      du[2 * j + 1] = uk[cf + j - c_lo];
+    }
+  }
+  return MRA_OK;
+}
+
+int mra_loglik_combine(mra_handle* h, const mra_params* theta, const double* summaries, double* loglik_out) {
+  g_err.clear();
+  if (!h || !theta || !summaries || !loglik_out) return fail(MRA_ERR_ARG, "null argument");
+  if (!h->s_lvl) return fail(MRA_ERR_STATE, "not a streamed handle (stream_level >= 1)");
+  if (!params_ok(theta) || !nu_ok(h->cfg.cov_family, theta)) return fail(MRA_ERR_ARG, "theta needs sigma2 > 0, range > 0, tau2 >= 0 (and 0.05 <= nu <= 20 for MRA_COV_MATERN), all finite");
+  const int s = h->s_lvl, M = h->M;
+  const int64_t nsub = (int64_t)h->chunks.size(), r = h->r, T = int64_t(s + 1) * (s + 2) / 2, L = summary_len(h);
+  std::vector<double> A(nsub * T * r * r), Om(nsub * (s + 1) * r);
+  const int64_t nkids = h->tab.nreg[s + 1];
+  std::vector<double> dk(std::max<int64_t>(nkids, 1), 0.0), uk(dk.size(), 0.0);
+  for (int64_t k = 0; k < nsub; ++k) {
+    const double* o = summaries + k * L;
+    memcpy(A.data() + k * T * r * r, o, sizeof(double) * T * r * r);
+    memcpy(Om.data() + k * (s + 1) * r, o + T * r * r, sizeof(double) * (s + 1) * r);
+    const double* du = o + T * r * r + (s + 1) * r;
+    const int32_t cf = h->tab.cfirst[s][k], cc = h->tab.ccnt[s][k];
+    for (int32_t j = 0; j < cc; ++j) {
+      dk[cf + j] = du[2 * j];
+      uk[cf + j] = du[2 * j + 1];
+    }
+  }
+  h->have_post = false;
+  cudaError_t e;
+  double* ddst = s + 1 == M ? h->lf.d : h->st.dd[s + 1];
+  double* udst = s + 1 == M ? h->lf.u : h->st.uu[s + 1];
+  if ((e = upload_desc(h, theta)) || (e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream)) ||
+      (e = cudaMemcpyAsync(h->st.Acc[s], A.data(), sizeof(double) * A.size(), cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaMemcpyAsync(h->st.Om[s], Om.data(), sizeof(double) * Om.size(), cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaMemcpyAsync(ddst, dk.data(), sizeof(double) * nkids, cudaMemcpyHostToDevice, h->stream)) ||
+      (e = cudaMemcpyAsync(udst, uk.data(), sizeof(double) * nkids, cudaMemcpyHostToDevice, h->stream)))
+    return cuda_fail(e, "summaries");
+  if ((e = mra::launch_loglik(h->plan_coarse_post, h->d_desc, h->status, h->stream, &g_launches, &h->timer)))
+    return cuda_fail(e, "coarse posterior");
+  int hs[4];
+  double du[2];
+  const double* srcs[2] = {h->st.dd[0], h->st.uu[0]};
+  if ((e = sync_status(h, hs, du, 2, srcs))) return cuda_fail(e, "combine");
+  collect_times(h);
+  if (hs[0]) return status_error(hs);
+  *loglik_out = -0.5 * (du[0] + du[1]) - 0.5 * (double)h->n * std::log(2.0 * M_PI);
+  h->have_post = true;    // (region terms of levels <= s are now the whole problem's)
   h->last = *theta;
   return MRA_OK;
 }
@@ -634,6 +986,7 @@ int mra_update(mra_handle* h, const double* locs, const double* y, int where) {
   g_err.clear();
   if (!h || !locs || !y) return fail(MRA_ERR_ARG, "null argument");
   if (!h->parts.empty()) return fail(MRA_ERR_STATE, "not available on a batch handle");
+  if (h->s_lvl) return fail(MRA_ERR_STATE, "a streamed handle keeps its partition: build a new handle");
   if (where != MRA_HOST && where != MRA_DEVICE) return fail(MRA_ERR_ARG, "where must be MRA_HOST or MRA_DEVICE");
   const int64_t n = h->n, nl = int64_t(1) << (2 * h->M);
   cudaError_t e;
@@ -655,15 +1008,15 @@ int mra_update(mra_handle* h, const double* locs, const double* y, int where) {
   if (mc > h->nlmax || tail > h->ls_cap)
     return fail(MRA_ERR_LIMIT, "new partition needs leaves of %d (handle has %d) or %lld leaf-factor doubles "
                 "(handle has %lld); build a new handle", mc, h->nlmax, (long long)tail, (long long)h->ls_cap);
-  if (h->cfg.prune) {   // the active regions must not change
-    std::vector<int32_t> counts(nl);
-    if ((e = cudaMemcpyAsync(counts.data(), h->counts, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost, h->stream)) ||
-        (e = cudaStreamSynchronize(h->stream)))
-      return cuda_fail(e, "leaf counts");
+  std::vector<int32_t> counts(nl);
+  if ((e = cudaMemcpyAsync(counts.data(), h->counts, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost, h->stream)) ||
+      (e = cudaStreamSynchronize(h->stream)))
+    return cuda_fail(e, "leaf counts");
+  if (h->cfg.prune)   // the active regions must not change
     for (int64_t f = 0; f < nl; ++f)
       if ((counts[f] > 0) != (h->tab.cid[h->M][f] >= 0))
         return fail(MRA_ERR_LIMIT, "the new data occupies other leaves than the pruned tree; build a new handle");
-  }
+  h->leaf_counts.swap(counts);
   return MRA_OK;
 }
 
@@ -711,7 +1064,7 @@ static int ensure_grad_arena(mra_handle* h) {
   int64_t slots = 0;
   for (int m = 0; m <= M; ++m) slots += nreg[m];
   if (M > 0) slots += nreg[M - 1];   // the emulated chain adjoint's, one per level-(M-1) region
-  G.want(&h->gs.gpart, 3 * slots);
+  G.want(&h->gs.gpart, mra::GP * slots);
   // Emulated form, two optional buffers, each taken only while 85 % of the free
   // device memory holds it after everything above (the kernels have paths
   // without them): the per-parent adjoint S for Hbar and Gbar on the tensor
@@ -735,7 +1088,8 @@ static int ensure_grad_arena(mra_handle* h) {
       G.want(&h->gs.SFexp, sfe);
       budget -= sf;
     }
-    if ((int64_t)Arena::align(16 * n * Mr) <= budget) G.want(&h->gs.DC, 2 * n * Mr);
+    if ((int64_t)Arena::align(16 * n * Mr) <= budget && h->cfg.cov_family != MRA_COV_MATERN)
+      G.want(&h->gs.DC, 2 * n * Mr);   // (pairs d/dsigma2, d/dkappa: the free-smoothness family also needs d/dnu)
   }
   G.want(&h->d_grad, 4);
   cudaError_t e = G.commit();
@@ -761,7 +1115,8 @@ int mra_loglik_grad(mra_handle* h, const mra_params* theta, double* loglik_out, 
   g_err.clear();
   if (!h || !loglik_out || !grad_out) return fail(MRA_ERR_ARG, "null argument");
   if (!h->parts.empty()) return fail(MRA_ERR_STATE, "not available on a batch handle");
-  if (!params_ok(theta)) return fail(MRA_ERR_ARG, "theta needs sigma2 > 0, range > 0, tau2 >= 0, all finite");
+  if (h->s_lvl) return fail(MRA_ERR_STATE, "the gradient is not available on a streamed handle (stream_level %d)", h->s_lvl);
+  if (!params_ok(theta) || !nu_ok(h->cfg.cov_family, theta)) return fail(MRA_ERR_ARG, "theta needs sigma2 > 0, range > 0, tau2 >= 0 (and 0.05 <= nu <= 20 for MRA_COV_MATERN), all finite");
   int rc = ensure_grad_arena(h);
   if (rc) return rc;
   h->have_post = false;
@@ -778,20 +1133,20 @@ int mra_loglik_grad(mra_handle* h, const mra_params* theta, double* loglik_out, 
   if ((e = mra::launch_grad(h->hd, h->d_desc, h->gs, h->d_grad, h->status, h->stream, &g_launches, &h->timer)))
     return cuda_fail(e, "gradient launch");
   int hs[4];
-  double vals[5];
-  const double* srcs[5];
+  double vals[6];
+  const double* srcs[6];
   if (h->M > 0) { srcs[0] = h->st.dd[0]; srcs[1] = h->st.uu[0]; }
   else { srcs[0] = h->lf.d; srcs[1] = h->lf.u; }
-  srcs[2] = h->d_grad;
-  srcs[3] = h->d_grad + 1;
-  srcs[4] = h->d_grad + 2;
-  if ((e = sync_status(h, hs, vals, 5, srcs))) return cuda_fail(e, "gradient");
+  for (int c = 0; c < 4; ++c) srcs[2 + c] = h->d_grad + c;
+  if ((e = sync_status(h, hs, vals, 6, srcs))) return cuda_fail(e, "gradient");
+  if (h->timer.on) ++h->nevals;
   collect_times(h);
   if (hs[0]) return status_error(hs);
   *loglik_out = -0.5 * (vals[0] + vals[1]) - 0.5 * (double)h->n * std::log(2.0 * M_PI);
   grad_out[0] = vals[2];
   grad_out[1] = vals[3];
   grad_out[2] = vals[4];
+  if (h->cfg.cov_family == MRA_COV_MATERN) grad_out[3] = vals[5];
   h->have_post = true;
   h->last = *theta;
   return MRA_OK;
@@ -813,6 +1168,9 @@ int mra_enable_timing(mra_handle* h, int on) {
   h->timer.on = on != 0;
   h->timer.count = 0;
   for (int k = 0; k < 8; ++k) { h->ktime[k] = 0.0; h->kcount[k] = 0; }
+  memset(h->stime, 0, sizeof h->stime);
+  memset(h->scount, 0, sizeof h->scount);
+  h->nevals = 0;
   return MRA_OK;
 }
 
@@ -825,19 +1183,113 @@ int mra_kernel_times(mra_handle* h, int kind, double* total_ms, int64_t* launche
   return MRA_OK;
 }
 
+// Algorithmic work of one evaluation per level and stage (mra_stats): FLOPs
+// with multiply-add = 2, symmetric and triangular products counted once and
+// factorisations (Cholesky with triangular inverse) 2 r^3 / 3; bytes = 8 x the
+// doubles each unit reads and writes once.  T_m = (m+1)(m+2)/2 packed blocks.
+static void stage_model(const mra_handle* p, double fl[][MRA_STAGES], double by[][MRA_STAGES],
+                        double un[][MRA_STAGES]) {
+  const int M = p->M;
+  const double r = p->r, r2 = r * r, tri = r * (r + 1) / 2.0, Mr = M * r;
+  const bool emu = p->cfg.precision == MRA_PREC_EMU;
+  const std::vector<int32_t>& nreg = p->tab.nreg;
+  for (int m = 0; m < M; ++m) {
+    const double R = nreg[m];
+    double f = 2.0 * tri * (m * r) + 2.0 * r * r2 / 3.0;
+    for (int l = 0; l < m; ++l) f += 2.0 * r2 * (l * r) + 2.0 * r * tri;
+    fl[m][MRA_STAGE_PRIOR] += R * f;
+    // reads: ancestors' V rows (r x l r, l < m) and L_l^{-1}; writes V (r x m r) and L^{-1}
+    by[m][MRA_STAGE_PRIOR] += 8.0 * R * (r2 * m * (m - 1) / 2.0 + m * r2 + m * r2 + r2);
+    un[m][MRA_STAGE_PRIOR] += R;
+    const double Tm = (m + 1) * (m + 2) / 2.0;
+    fl[m][MRA_STAGE_POST] += R * (2.0 * r * r2 / 3.0 + m * r2 * (r + 1) + r * (r + 1));
+    // reads A-hat (T_m blocks) and omega-hat; writes Lt^{-1}, G (r x m r), g, d, u
+    by[m][MRA_STAGE_POST] += 8.0 * R * (Tm * r2 + (m + 1) * r + r2 + m * r2 + r + 2);
+    un[m][MRA_STAGE_POST] += R;
+    if (m > 0) {
+      const double mr = m * r, Tp = m * (m + 1) / 2.0;
+      // per child: A~ = A-hat - G'G over its lower blocks (k, l < m), omega~
+      fl[m][MRA_STAGE_AGGREGATE] += R * (mr * (mr + 1) * r + 2.0 * mr * r);
+      // per child reads A-hat blocks (k, l < m), G, g, omega-hat; per parent writes A-hat, omega-hat
+      by[m][MRA_STAGE_AGGREGATE] += 8.0 * (R * (Tp * r2 + m * r2 + r + m * r) + nreg[m - 1] * (Tp * r2 + m * r));
+      un[m][MRA_STAGE_AGGREGATE] += nreg[m - 1];
+    }
+  }
+  double chain_f = 0, leaf_f = 0, leaf_b = 0, nobs = 0, nleaf = 0;
+  for (size_t f = 0; f < p->leaf_counts.size(); ++f) {
+    const double c = p->leaf_counts[f];
+    if (c == 0 && p->cfg.prune) continue;
+    nleaf += 1;
+    nobs += c;
+    double ch = 0;
+    for (int l = 0; l < M; ++l) ch += 2.0 * c * r * (l * r) + 2.0 * c * tri;
+    chain_f += ch;
+    leaf_f += c * (c + 1) * Mr + 2.0 * c * c * c / 3.0 + c * (c + 1) + Mr * c * (c + 1);
+    // reads x, y, data; writes H (c x M r), z, L_Sigma^{-1} (c^2), d, u
+    leaf_b += 8.0 * (3 * c + c * Mr + c + c * c + 2);
+  }
+  const double anc = r2 * (M * (M - 1) / 2.0 + M);   // the ancestors' V rows and L^{-1} of a leaf's chain
+  const double P = M > 0 ? nreg[M - 1] : 0;
+  if (emu && M > 0) {
+    fl[M][MRA_STAGE_CHAIN] += chain_f;
+    by[M][MRA_STAGE_CHAIN] += 8.0 * (2 * nobs + P * anc + nobs * Mr);
+    un[M][MRA_STAGE_CHAIN] += P;
+    fl[M][MRA_STAGE_LEAF] += leaf_f;
+    by[M][MRA_STAGE_LEAF] += leaf_b + 8.0 * nobs * Mr;           // V_F read back
+  } else {
+    fl[M][MRA_STAGE_LEAF] += chain_f + leaf_f;
+    by[M][MRA_STAGE_LEAF] += leaf_b + 8.0 * nleaf * anc;
+  }
+  un[M][MRA_STAGE_LEAF] += nleaf;
+  if (M > 0) {
+    const double T = M * (M + 1) / 2.0;
+    fl[M][MRA_STAGE_LEAF_SYRK] += (Mr * (Mr + 1) + 2.0 * Mr) * nobs;
+    // reads H and z; writes the parents' A-hat (T blocks) and omega-hat
+    by[M][MRA_STAGE_LEAF_SYRK] += 8.0 * (nobs * (Mr + 1) + P * (T * r2 + Mr));
+    un[M][MRA_STAGE_LEAF_SYRK] += P;
+  }
+}
+
+extern "C" int mra_stats(mra_handle* h, mra_stats_t* out) {
+  g_err.clear();
+  if (!h || !out) return fail(MRA_ERR_ARG, "null argument");
+  memset(out, 0, sizeof *out);
+  out->M = h->M;
+  out->evaluations = h->nevals;
+  for (int m = 0; m <= MRA_MAX_M; ++m)
+    for (int k = 0; k < MRA_STAGES; ++k) {
+      out->ms[m][k] = h->stime[m][k];
+      out->launches[m][k] = h->scount[m][k];
+    }
+  if (h->parts.empty()) {
+    stage_model(h, out->flops, out->bytes, out->units);
+  } else {
+    for (mra_handle* p : h->parts) stage_model(p, out->flops, out->bytes, out->units);
+  }
+  return MRA_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Prediction
 // ---------------------------------------------------------------------------
-int mra_predict(mra_handle* h, const mra_params* theta, const double* plocs, int64_t np, int where,
-                double* mean_out, double* var_out) {
-  g_err.clear();
-  if (!h || !theta || !plocs || !mean_out || !var_out) return fail(MRA_ERR_ARG, "null argument");
+// The steps every prediction entry point shares: the posterior factors at
+// theta, the prediction buffers, and the binning of the points by leaf (stable
+// for the joint modes, whose per-leaf factors depend on the points' order).
+static int pred_prepare(mra_handle* h, const mra_params* theta, const double* plocs, int64_t np, int where,
+                        bool stable, int32_t* maxp_out) {
   if (!h->parts.empty()) return fail(MRA_ERR_STATE, "not available on a batch handle");
+  if (h->s_lvl && stable)
+    return fail(MRA_ERR_STATE, "the joint predictive needs the factors of every level: not on a streamed handle");
   if (np < 1) return fail(MRA_ERR_ARG, "np must be >= 1");
   if (where != MRA_HOST && where != MRA_DEVICE) return fail(MRA_ERR_ARG, "where must be MRA_HOST or MRA_DEVICE");
-  if (!h->have_post) return fail(MRA_ERR_STATE, "call mra_loglik before mra_predict");
-  if (theta->sigma2 != h->last.sigma2 || theta->range != h->last.range || theta->tau2 != h->last.tau2)
-    return fail(MRA_ERR_STATE, "theta differs from the last mra_loglik; evaluate the log-likelihood at it first");
+  if (!params_ok(theta) || !nu_ok(h->cfg.cov_family, theta)) return fail(MRA_ERR_ARG, "theta needs sigma2 > 0, range > 0, tau2 >= 0 (and 0.05 <= nu <= 20 for MRA_COV_MATERN), all finite");
+  if (!h->have_post || theta->sigma2 != h->last.sigma2 || theta->range != h->last.range ||
+      theta->tau2 != h->last.tau2 || (h->cfg.cov_family == MRA_COV_MATERN && theta->nu != h->last.nu)) {
+    // the posterior factors of Sec. 3.2 at this theta: one evaluation first
+    double ll;
+    const int rc = mra_loglik(h, theta, &ll);
+    if (rc) return rc;
+  }
   const int M = h->M, r = h->r;
   const int64_t nl = int64_t(1) << (2 * M);
   cudaError_t e;
@@ -871,7 +1323,7 @@ int mra_predict(mra_handle* h, const mra_params* theta, const double* plocs, int
   }
   if ((e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream))) return cuda_fail(e, "memset");
   if ((e = mra::launch_bin(dp, np, h->bbox, M, h->p_leaf, h->p_counts, h->p_cursor, h->p_off, h->p_sq, h->p_max,
-                           h->p_perm, h->status, h->stream, &g_launches, false)) ||
+                           h->p_perm, h->status, h->stream, &g_launches, stable)) ||
       (e = mra::launch_gather(dp, nullptr, h->p_perm, np, h->p_xs, h->p_ys, nullptr, h->stream, &g_launches)))
     return cuda_fail(e, "binning prediction points");
   int hs[4];
@@ -879,18 +1331,56 @@ int mra_predict(mra_handle* h, const mra_params* theta, const double* plocs, int
   const double* srcs[1] = {(const double*)h->p_max};
   if ((e = sync_status(h, hs, got, 1, srcs))) return cuda_fail(e, "binning prediction points");
   if (hs[0]) return status_error(hs);
-  int32_t maxp;
-  memcpy(&maxp, &got[0], sizeof maxp);
-  mra::PredState ps;
+  memcpy(maxp_out, &got[0], sizeof(int32_t));
+  return MRA_OK;
+}
+
+static mra::PredState pred_state(mra_handle* h) {
+  mra::PredState ps{};
   ps.off = h->p_off;
   ps.perm = h->p_perm;
   ps.xs = h->p_xs;
   ps.ys = h->p_ys;
   ps.U = h->p_U;
+  ps.mean = h->p_mean;
+  ps.var = h->p_var;
+  return ps;
+}
+
+int mra_predict(mra_handle* h, const mra_params* theta, const double* plocs, int64_t np, int where,
+                double* mean_out, double* var_out) {
+  g_err.clear();
+  if (!h || !theta || !plocs || !mean_out || !var_out) return fail(MRA_ERR_ARG, "null argument");
+  int32_t maxp = 0;
+  int rc = pred_prepare(h, theta, plocs, np, where, false, &maxp);
+  if (rc) return rc;
+  const int M = h->M, r = h->r;
+  cudaError_t e;
+  int hs[4];
+  double got[1];
+  const double* srcs[1] = {(const double*)h->p_max};
+  mra::PredState ps = pred_state(h);
   ps.mean = where == MRA_DEVICE ? mean_out : h->p_mean;
   ps.var = where == MRA_DEVICE ? var_out : h->p_var;
-  if ((e = mra::launch_predict(h->d_desc, M, r, h->nlmax, ps, maxp, h->status, h->stream, &g_launches, &h->timer)))
-    return cuda_fail(e, "predict launch");
+  if (!h->s_lvl) {
+    if ((e = mra::launch_predict(h->d_desc, M, r, h->nlmax, ps, maxp, h->status, h->stream, &g_launches, &h->timer)))
+      return cuda_fail(e, "predict launch");
+  } else {
+    // Streamed: the coarse factors (levels <= s) are resident from the
+    // evaluation; each chunk's own factors are formed again from them (its
+    // prior, leaves and posterior, as in the evaluation, with the same
+    // results) and its leaves' points predicted before the next chunk reuses
+    // the buffers.
+    for (size_t g = 0; g < h->chunks.size(); ++g) {
+      const Chunk& c = h->chunks[g];
+      ps.desc = (int)g;
+      ps.leaf0 = (long)c.f0;
+      if ((e = mra::launch_loglik(c.plan, h->d_desc, h->status, h->stream, &g_launches, &h->timer)) ||
+          (e = mra::launch_predict(h->d_desc, M, r, h->nlmax, ps, maxp, h->status, h->stream, &g_launches, &h->timer,
+                                   (long)c.nf)))
+        return cuda_fail(e, "predict launch");
+    }
+  }
   if (where == MRA_HOST) {
     if ((e = cudaMemcpyAsync(mean_out, h->p_mean, sizeof(double) * np, cudaMemcpyDeviceToHost, h->stream)) ||
         (e = cudaMemcpyAsync(var_out, h->p_var, sizeof(double) * np, cudaMemcpyDeviceToHost, h->stream)))
@@ -899,6 +1389,125 @@ int mra_predict(mra_handle* h, const mra_params* theta, const double* plocs, int
   if ((e = sync_status(h, hs, got, 0, srcs))) return cuda_fail(e, "predict");
   collect_times(h);
   if (hs[0]) return status_error(hs);
+  return MRA_OK;
+}
+
+// Joint modes: D blocks (at most JOINT_TILE points per leaf, so sum n_P^2 <=
+// JOINT_TILE np), sorted leaf ids, and `io` doubles of staging for host data.
+static int ensure_joint(mra_handle* h, int64_t np, int64_t io) {
+  if (np <= h->joint_np && io <= h->joint_io) return MRA_OK;
+  h->joint.release();
+  h->joint_np = h->joint_io = 0;
+  Arena& A = h->joint;
+  A.want(&h->j_D, (int64_t)mra::JOINT_TILE * np);
+  A.want(&h->j_leaf, np);
+  A.want(&h->j_io, io);
+  cudaError_t e = A.commit();
+  if (e) return fail(MRA_ERR_OOM, "device allocation (joint prediction): %s", cudaGetErrorString(e));
+  h->joint_np = np;
+  h->joint_io = io;
+  return MRA_OK;
+}
+
+static int joint_factors(mra_handle* h, const mra_params* theta, const double* plocs, int64_t np, int where,
+                         int mode, int64_t io, mra::PredState* ps_out) {
+  int32_t maxp = 0;
+  int rc = pred_prepare(h, theta, plocs, np, where, true, &maxp);
+  if (rc) return rc;
+  if (maxp > mra::JOINT_TILE)
+    return fail(MRA_ERR_LIMIT, "a leaf holds %d prediction points; the joint predictive takes at most %d per "
+                "leaf", maxp, mra::JOINT_TILE);
+  if ((rc = ensure_joint(h, np, io))) return rc;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if ((size_t)optin < mra::joint_smem_bytes(h->r, h->nlmax))
+    return fail(MRA_ERR_LIMIT, "joint prediction needs more shared memory than the device allows");
+  mra::PredState ps = pred_state(h);
+  ps.sq_off = h->p_sq;
+  ps.D = h->j_D;
+  ps.leaf = h->j_leaf;
+  cudaError_t e;
+  if ((e = mra::launch_predict_joint(h->d_desc, h->M, h->r, h->nlmax, ps, mode, h->status, h->stream, &g_launches,
+                                     &h->timer)))
+    return cuda_fail(e, "joint prediction launch");
+  *ps_out = ps;
+  return MRA_OK;
+}
+
+int mra_predict_joint(mra_handle* h, const mra_params* theta, const double* plocs, int64_t np, int where,
+                      double* mean_out, double* cov_out) {
+  g_err.clear();
+  if (!h || !theta || !plocs || !mean_out || !cov_out) return fail(MRA_ERR_ARG, "null argument");
+  if (np > MRA_MAX_JOINT_POINTS)
+    return fail(MRA_ERR_LIMIT, "np = %lld exceeds MRA_MAX_JOINT_POINTS (%d)", (long long)np, MRA_MAX_JOINT_POINTS);
+  mra::PredState ps;
+  int rc = joint_factors(h, theta, plocs, np, where, 1, where == MRA_HOST ? np * np : 0, &ps);
+  if (rc) return rc;
+  cudaError_t e;
+  double* cov = where == MRA_HOST ? h->j_io : cov_out;
+  if ((e = mra::launch_joint_cov(h->d_desc, ps, np, cov, h->stream, &g_launches))) return cuda_fail(e, "joint covariance");
+  if (where == MRA_HOST) {
+    if ((e = cudaMemcpyAsync(mean_out, h->p_mean, sizeof(double) * np, cudaMemcpyDeviceToHost, h->stream)) ||
+        (e = cudaMemcpyAsync(cov_out, cov, sizeof(double) * np * np, cudaMemcpyDeviceToHost, h->stream)))
+      return cuda_fail(e, "copy joint prediction");
+  } else if ((e = cudaMemcpyAsync(mean_out, h->p_mean, sizeof(double) * np, cudaMemcpyDeviceToDevice, h->stream))) {
+    return cuda_fail(e, "copy joint prediction");
+  }
+  int hs[4];
+  if ((e = sync_status(h, hs, nullptr, 0, nullptr))) return cuda_fail(e, "joint prediction");
+  collect_times(h);
+  if (hs[0]) return status_error(hs);
+  return MRA_OK;
+}
+
+int mra_simulate_xi_len(mra_handle* h, int64_t* len_out) {
+  g_err.clear();
+  if (!h || !len_out) return fail(MRA_ERR_ARG, "null argument");
+  if (!h->parts.empty()) return fail(MRA_ERR_STATE, "not available on a batch handle");
+  int64_t regions = 0;
+  for (int m = 0; m < h->M; ++m) regions += int64_t(1) << (2 * m);
+  *len_out = regions * h->r;
+  return MRA_OK;
+}
+
+int mra_simulate(mra_handle* h, const mra_params* theta, const double* plocs, int64_t np, int where, int64_t nsim,
+                 const double* xi, const double* zeta, double* draws_out) {
+  g_err.clear();
+  if (!h || !theta || !plocs || !draws_out || (!xi && h->M > 0) || !zeta) return fail(MRA_ERR_ARG, "null argument");
+  if (nsim < 1) return fail(MRA_ERR_ARG, "nsim must be >= 1");
+  int64_t nxi = 0;
+  int rc = mra_simulate_xi_len(h, &nxi);
+  if (rc) return rc;
+  const int64_t io = where == MRA_HOST ? nsim * (nxi + 2 * np) : 0;
+  mra::PredState ps;
+  if ((rc = joint_factors(h, theta, plocs, np, where, 2, io, &ps))) return rc;
+  cudaError_t e;
+  const double *dxi = xi, *dz = zeta;
+  double* dd = draws_out;
+  if (where == MRA_HOST) {
+    double* x = h->j_io;
+    if ((nxi > 0 && (e = cudaMemcpyAsync(x, xi, sizeof(double) * nsim * nxi, cudaMemcpyHostToDevice, h->stream))) ||
+        (e = cudaMemcpyAsync(x + nsim * nxi, zeta, sizeof(double) * nsim * np, cudaMemcpyHostToDevice, h->stream)))
+      return cuda_fail(e, "copy normals");
+    dxi = x;
+    dz = x + nsim * nxi;
+    dd = x + nsim * (nxi + np);
+  }
+  if ((e = mra::launch_simulate(h->d_desc, h->M, ps, np, nsim, nxi, dxi, dz, dd, h->stream, &g_launches)))
+    return cuda_fail(e, "simulation launch");
+  if (where == MRA_HOST &&
+      (e = cudaMemcpyAsync(draws_out, dd, sizeof(double) * nsim * np, cudaMemcpyDeviceToHost, h->stream)))
+    return cuda_fail(e, "copy draws");
+  int hs[4];
+  if ((e = sync_status(h, hs, nullptr, 0, nullptr))) return cuda_fail(e, "simulation");
+  collect_times(h);
+  if (hs[0]) {
+    if (hs[0] == mra::ST_NOT_PD && hs[1] == h->M + 1)
+      return fail(MRA_ERR_NOT_PD, "the predictive covariance of the points in leaf %d is not positive definite "
+                  "(coincident or nearly coincident prediction points)", hs[2]);
+    return status_error(hs);
+  }
   return MRA_OK;
 }
 
@@ -926,6 +1535,11 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
       return fail(rc, "dataset %d: %s", d, msg.c_str());
     }
     h->parts.push_back(p);
+    if (p->s_lvl) {
+      mra_free(h);
+      return fail(MRA_ERR_ARG, "dataset %d: a batch evaluates its datasets whole (set stream_level = -1, or "
+                  "evaluate it on its own handle)", d);
+    }
     h->M = std::max(h->M, p->M);
     h->nlmax = std::max(h->nlmax, p->nlmax);
     h->n += p->n;
@@ -1040,8 +1654,10 @@ int batch_results(mra_handle* h, double* loglik_out) {
 
 int set_batch_params(mra_handle* h, const mra_params* thetas) {
   for (size_t d = 0; d < h->parts.size(); ++d) {
-    if (!params_ok(&thetas[d])) return fail(MRA_ERR_ARG, "theta of dataset %zu is invalid", d);
-    h->h_descs[d].cv = mra::make_cov(thetas[d].sigma2, thetas[d].range, h->parts[d]->cfg.cov_family, h->parts[d]->cfg.nonstat);
+    if (!params_ok(&thetas[d]) || !nu_ok(h->parts[d]->cfg.cov_family, &thetas[d]))
+      return fail(MRA_ERR_ARG, "theta of dataset %zu is invalid", d);
+    h->h_descs[d].cv = mra::make_cov(thetas[d].sigma2, thetas[d].range, h->parts[d]->cfg.cov_family,
+                                     h->parts[d]->cfg.nonstat, thetas[d].nu);
     h->h_descs[d].tau2 = thetas[d].tau2;
   }
   memcpy(h->pinned_descs, h->h_descs.data(), sizeof(mra::Desc) * h->parts.size());
@@ -1117,6 +1733,7 @@ int mra_loglik_batch(mra_handle* h, const mra_params* thetas, double* loglik_out
   cudaError_t e;
   if (h->timer.on) {   // per-kernel events: run the launches directly
     if ((e = batch_sequence(h)) || (e = cudaStreamSynchronize(h->stream))) return cuda_fail(e, "batch");
+    ++h->nevals;
     collect_times(h);
     return batch_results(h, loglik_out);
   }
@@ -1140,6 +1757,33 @@ int mra_loglik_batch(mra_handle* h, const mra_params* thetas, double* loglik_out
     return cuda_fail(e, "graph launch");
   g_launches += h->graph_launches;
   return batch_results(h, loglik_out);
+}
+
+int mra_loglik_grad_batch(mra_handle* h, const mra_params* thetas, double* loglik_out, double* grad_out) {
+  g_err.clear();
+  if (!h || !thetas || !loglik_out || !grad_out) return fail(MRA_ERR_ARG, "null argument");
+  if (h->parts.empty()) return fail(MRA_ERR_STATE, "not a batch handle (use mra_build_batch)");
+  for (size_t d = 0; d < h->parts.size(); ++d) {
+    if (!params_ok(&thetas[d]) || !nu_ok(h->parts[d]->cfg.cov_family, &thetas[d]))
+      return fail(MRA_ERR_ARG, "theta of dataset %zu is invalid", d);
+    if (h->parts[d]->cfg.cov_family == MRA_COV_MATERN)
+      return fail(MRA_ERR_ARG, "dataset %zu: the free-smoothness gradient has four components; use "
+                  "mra_loglik_grad on its own handle", d);
+  }
+  // Dataset by dataset on the batch's stream: the adjoint of each dataset keeps
+  // its own gradient storage (allocated by its first call).
+  for (size_t d = 0; d < h->parts.size(); ++d) {
+    mra_handle* p = h->parts[d];
+    cudaStream_t keep = p->stream;
+    p->stream = h->stream;
+    const int rc = mra_loglik_grad(p, &thetas[d], loglik_out + d, grad_out + 3 * d);
+    p->stream = keep;
+    if (rc) {
+      std::string msg = g_err;
+      return fail(rc, "dataset %zu: %s", d, msg.c_str());
+    }
+  }
+  return MRA_OK;
 }
 
 int mra_batch_info(mra_handle* h, int* ndata_out, int* tile_out) {

@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
   double* ay = ax + MAX_R_DEV;
   double* red = ay + MAX_R_DEV;
   double* stg = red + 32;
-  double g_s2 = 0.0, g_k = 0.0, g_t = 0.0;
+  double g_s2 = 0.0, g_k = 0.0, g_t = 0.0, g_nu = 0.0;
   EmCtx cx;
   bool ok = true;
   if (EMU) {
@@ -568,10 +568,11 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
     for (int t = threadIdx.x; t < nF * nF; t += NT) {
       int a = t / nF, b = t - a * nF;
       double sb = T3[t];
-      double d1, d2;
-      dcov0(cv, sx[a], sy[a], sx[b], sy[b], d1, d2);
+      double d1, d2, d3;
+      dcov0(cv, sx[a], sy[a], sx[b], sy[b], d1, d2, d3);
       g_s2 = fma(sb, d1, g_s2);
       g_k = fma(sb, d2, g_k);
+      g_nu = fma(sb, d3, g_nu);
       if (a == b) g_t += sb;
     }
     // Vbar_F -= 2 Sigmabar V_F
@@ -619,10 +620,11 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
               int o = rt * TILE + row;
               double xb = acc.v[p][q];
               XB[(long)o * Mr + l * r + col] = xb;
-              double d1, d2;
-              dcov0(cv, sx[o], sy[o], ax[col], ay[col], d1, d2);
+              double d1, d2, d3;
+              dcov0(cv, sx[o], sy[o], ax[col], ay[col], d1, d2, d3);
               g_s2 = fma(xb, d1, g_s2);
               g_k = fma(xb, d2, g_k);
+              g_nu = fma(xb, d3, g_nu);
             }
           }
       }
@@ -646,11 +648,13 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
   g_s2 = block_sum(g_s2, red);
   g_k = block_sum(g_k, red);
   g_t = block_sum(g_t, red);
+  g_nu = block_sum(g_nu, red);
   if (EMU && !ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, M, F);
   if (threadIdx.x == 0) {
-    gs.gpart[3 * (slot0 + F) + 0] = g_s2;
-    gs.gpart[3 * (slot0 + F) + 1] = g_k;
-    gs.gpart[3 * (slot0 + F) + 2] = g_t;
+    gs.gpart[GP * (slot0 + F) + 0] = g_s2;
+    gs.gpart[GP * (slot0 + F) + 1] = g_k;
+    gs.gpart[GP * (slot0 + F) + 2] = g_t;
+    gs.gpart[GP * (slot0 + F) + 3] = g_nu;
   }
 }
 
@@ -773,7 +777,7 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
     }
   };
   const int S = em_stack(r);
-  double g_s2 = 0.0, g_k = 0.0;
+  double g_s2 = 0.0, g_k = 0.0, g_nu = 0.0;
   load_knots(sh.bbox, m, st.mort[m][i], sh.gx, sh.gy, qx, qy);
   const double* L = st.L[m] + i * (long)r * r;
   const double* Li = st.Li[m] + i * (long)r * r;
@@ -793,10 +797,11 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
   }
   for (int t = threadIdx.x; t < r * r; t += NT) {
     int a = t / r, b = t - a * r;
-    double d1, d2;
-    dcov0(cv, qx[a], qy[a], qx[b], qy[b], d1, d2);
+    double d1, d2, d3;
+    dcov0(cv, qx[a], qy[a], qx[b], qy[b], d1, d2, d3);
     g_s2 = fma(B2[a * ld + b], d1, g_s2);
     g_k = fma(B2[a * ld + b], d2, g_k);
+    g_nu = fma(B2[a * ld + b], d3, g_nu);
   }
   double* VB = gs.VB[m] + i * (long)r * mr;
   double* XB = gs.XB[m] + i * (long)r * mr;
@@ -825,10 +830,11 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
     __syncthreads();
     auto xbar_epi = [&](int row, int col, double xb) {
       XB[(long)row * mr + l * r + col] = xb;
-      double d1, d2;
-      dcov0(cv, qx[row], qy[row], ax[col], ay[col], d1, d2);
+      double d1, d2, d3;
+      dcov0(cv, qx[row], qy[row], ax[col], ay[col], d1, d2, d3);
       g_s2 = fma(xb, d1, g_s2);
       g_k = fma(xb, d2, g_k);
+      g_nu = fma(xb, d3, g_nu);
     };
     if (EMU)
       product_n(VB + l * r, mr, 1, r, Lia, 1, r, r, nullptr, st.licol[l] ? st.licol[l] + a * r : nullptr, xbar_epi);
@@ -878,10 +884,12 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
   if (EMU) em_release(cx);
   g_s2 = block_sum(g_s2, red);
   g_k = block_sum(g_k, red);
+  g_nu = block_sum(g_nu, red);
   if (threadIdx.x == 0) {
-    gs.gpart[3 * (slot0 + i) + 0] = g_s2;
-    gs.gpart[3 * (slot0 + i) + 1] = g_k;
-    gs.gpart[3 * (slot0 + i) + 2] = 0.0;
+    gs.gpart[GP * (slot0 + i) + 0] = g_s2;
+    gs.gpart[GP * (slot0 + i) + 1] = g_k;
+    gs.gpart[GP * (slot0 + i) + 2] = 0.0;
+    gs.gpart[GP * (slot0 + i) + 3] = g_nu;
     if (EMU && !ok) flag_error(status, ST_TIMEOUT, m, i);
   }
 }
@@ -909,9 +917,9 @@ __global__ void __launch_bounds__(NT) col_scales_kernel(int m, const Desc* __res
 // Sum of the per-CTA partial gradients (fixed assignment: deterministic).
 __global__ void __launch_bounds__(NT) grad_reduce_kernel(const double* gpart, long nslots, double* out) {
   __shared__ double red[32];
-  for (int c = 0; c < 3; ++c) {
+  for (int c = 0; c < GP; ++c) {
     double s = 0.0;
-    for (long t = threadIdx.x; t < nslots; t += NT) s += gpart[3 * t + c];
+    for (long t = threadIdx.x; t < nslots; t += NT) s += gpart[GP * t + c];
     s = block_sum(s, red);
     if (threadIdx.x == 0) out[c] = s;
   }

@@ -92,6 +92,10 @@ struct LeafState {
   int32_t* vfexp;         // per level-(M-1) region x 4 tiles x (M r)
 };
 
+// Components of the gradient: d/d(sigma2, kappa, tau2) and, for the Matern
+// family of free smoothness, d/dnu (zero for the other families).
+constexpr int GP = 4;
+
 // Adjoint state of the gradient pass (mra_grad.cu).
 struct GradState {
   double* Abar[MAXL];   // 4^m x r x (m+1) r: row m of the symmetric adjoint of Ahat
@@ -105,7 +109,7 @@ struct GradState {
   double* VBF;          // n x (M r): adjoint of V_F
   double* XBF;          // n x (M r): adjoint of X^l_F
   double* T;            // ragged 3 n_F^2 per leaf: scratch of the leaf adjoint
-  double* gpart;        // 3 per CTA: partial d/d(sigma2, kappa, tau2)
+  double* gpart;        // GP per CTA: partial d/d(sigma2, kappa, tau2, nu)
   double* DC;           // emulated form: n x (M r) x 2 derivative pairs of the leaf chain's C0 blocks
   // emulated form: column exponents per 128-row tile of each level-(M-1)
   // region's rows (region x 4 x (M r)), the leaf partials' operand scales:
@@ -146,6 +150,19 @@ struct PredState {
   double* U;              // np x (M r) scratch: Uhat, then the posterior basis Bhat
   double* mean;           // np, caller's order
   double* var;            // np, caller's order
+  // joint modes only (mra_predict_joint, mra_simulate), else null: every leaf's
+  // points are sorted stably (ascending caller index) and, per leaf F with
+  // n_P points, D[sq_off[F] ..] holds its n_P x n_P delta~ covariance
+  // V^P - L^M Sigma^{-1} L^M' (joint covariance) or that matrix's lower
+  // Cholesky factor (simulation); U ends as [Y_0 .. Y_{M-1}] per point,
+  // Y_l = Bhat^{l+1,l} Lt_l^{-T}; leaf[p] = Morton id of sorted point p's leaf
+  const int64_t* sq_off;
+  double* D;
+  int32_t* leaf;
+  // the leaves a launch covers, [leaf0, leaf0 + gridDim.x) by Morton id, and the
+  // descriptor it reads (a streamed handle predicts chunk by chunk)
+  long leaf0;
+  int desc;
 };
 
 struct Shape {

@@ -6,16 +6,22 @@
 
 namespace mra {
 
-// Optional per-launch CUDA-event timing (kinds match MRA_K_* in mra.h).
-constexpr int MAX_TIMED = 256;
+// Optional per-launch CUDA-event timing (kinds match MRA_K_* in mra.h; the
+// stage and level of a record match MRA_STAGE_* and the level index of
+// mra_stats_t, or -1 where a launch has none).
+constexpr int MAX_TIMED = 2048;
 struct Timer {
   bool on = false;
   int count = 0;
   int kind[MAX_TIMED];
+  int stage[MAX_TIMED];
+  int level[MAX_TIMED];
   cudaEvent_t ev[2 * MAX_TIMED];
-  void start(int k, cudaStream_t s) {
+  void start(int k, cudaStream_t s, int st = -1, int lv = -1) {
     if (!on || count >= MAX_TIMED) return;
     kind[count] = k;
+    stage[count] = st;
+    level[count] = lv;
     cudaEventRecord(ev[2 * count], s);
   }
   void stop(cudaStream_t s) {
@@ -44,6 +50,12 @@ cudaError_t launch_gather_y(const double* y, const int64_t* perm, int64_t n, dou
 struct Plan {
   int maxM = 0, tile = 64, mixed = 0, nlmax = 1;   // mixed: 0 FP64, 1 3xTF32, 2 FP64 emulation
   int r = 0;
+  // the part of the pass this plan runs (subtree streaming splits a pass in
+  // three): prior levels [prior_lo, prior_hi), the leaves, and posterior
+  // levels [post_lo, post_hi) with the aggregation of each such level m > 0
+  // into level m - 1; prior_hi / post_hi < 0 mean maxM
+  int prior_lo = 0, prior_hi = -1, post_lo = 0, post_hi = -1;
+  bool leaves = true;
   const int2* w_lvl[MAXL] = {};
   int n_lvl[MAXL] = {};
   const int2* w_agg[MAXL] = {};
@@ -67,7 +79,8 @@ size_t leaf_smem_bytes(int r, int nlmax);
 cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nblocks, int emu, int* status,
                             cudaStream_t s);
 cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int emu, int* status,
-                           cudaStream_t s, const int2* w_par = nullptr, int n_par = 0);
+                           cudaStream_t s, const int2* w_par = nullptr, int n_par = 0, Timer* tm = nullptr,
+                           int leaf_level = -1);
 size_t leaf_tc_smem_bytes(int nlmax, int emu);
 cudaError_t launch_leaf_syrk_em(const Desc* d_desc, const int2* work, int nblocks, int maxM, int r, int* status,
                                 cudaStream_t s);
@@ -75,9 +88,21 @@ cudaError_t launch_aggregate_em(int m, int r, const Desc* d_desc, const int2* wo
                                 cudaStream_t s);
 
 // Prediction (Sec. 3.4, Prop. 2) at points binned into ps.
+// nleaf > 0: only the leaves [ps.leaf0, ps.leaf0 + nleaf) (a chunk of a streamed handle)
 cudaError_t launch_predict(const Desc* d_desc, int M, int r, int nlmax, const PredState& ps, int max_per_leaf,
-                           int* status, cudaStream_t s, int64_t* launches, Timer* tm);
+                           int* status, cudaStream_t s, int64_t* launches, Timer* tm, long nleaf = 0);
 size_t predict_smem_bytes(int r, int nlmax);
+// Joint posterior predictive (Prop. 2): mode 1 keeps D and the Y_l for the
+// covariance, mode 2 chol(D) and the Y_l for simulation (at most JOINT_TILE
+// points per leaf); then the covariance tiles or the draws.
+constexpr int JOINT_TILE = 64;
+size_t joint_smem_bytes(int r, int nlmax);
+cudaError_t launch_predict_joint(const Desc* d_desc, int M, int r, int nlmax, const PredState& ps, int mode,
+                                 int* status, cudaStream_t s, int64_t* launches, Timer* tm);
+cudaError_t launch_joint_cov(const Desc* d_desc, const PredState& ps, int64_t np, double* cov, cudaStream_t s,
+                             int64_t* launches);
+cudaError_t launch_simulate(const Desc* d_desc, int M, const PredState& ps, int64_t np, int64_t nsim, int64_t nxi,
+                            const double* xi, const double* zeta, double* draws, cudaStream_t s, int64_t* launches);
 
 // Reverse-mode gradient after a forward pass that saved L, Lt, V_F and L_Sigma.
 cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs, double* grad_out_dev, int* status,

@@ -531,10 +531,12 @@ cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaS
                           Timer* tm) {
   const int tile = pl.tile;
   cudaError_t e;
+  const int prior_hi = pl.prior_hi < 0 ? pl.maxM : pl.prior_hi;
+  const int post_hi = pl.post_hi < 0 ? pl.maxM : pl.post_hi;
   // prior pass, top-down
-  for (int m = 0; m < pl.maxM; ++m) {
+  for (int m = pl.prior_lo; m < prior_hi; ++m) {
     if (pl.n_lvl[m] == 0) continue;
-    tm->start(0, s);
+    tm->start(0, s, 0, m);
     if (pl.mixed) {
       if ((e = launch_prior_tc(m, d_desc, pl.w_lvl[m], pl.n_lvl[m], pl.mixed == 2, status, s))) return e;
     } else {
@@ -544,12 +546,13 @@ cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaS
     ++*launches;
   }
   // leaves
-  if (pl.n_leaf > 0) {
-    tm->start(1, s);
+  if (pl.leaves && pl.n_leaf > 0) {
+    const bool chain = pl.mixed == 2 && pl.n_syrk > 0;   // the emulated form's separate chain kernel
+    tm->start(1, s, chain ? 1 : 2, pl.maxM);
     if (pl.mixed) {
       // (the emulated form's chain kernel runs per level-(M-1) region: the leaf_syrk work list)
       if ((e = launch_leaf_tc(d_desc, pl.w_leaf, pl.n_leaf, pl.nlmax, pl.mixed == 2, status, s, pl.w_syrk,
-                              pl.n_syrk)))
+                              pl.n_syrk, tm, pl.maxM)))
         return e;
       if (pl.mixed == 2 && pl.n_syrk > 0) ++*launches;   // the chain kernel
     } else {
@@ -558,9 +561,9 @@ cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaS
     tm->stop(s);
     ++*launches;
   }
-  if (pl.n_syrk > 0) {
+  if (pl.leaves && pl.n_syrk > 0) {
     dim3 grid(pl.n_syrk, pl.t_syrk);
-    tm->start(2, s);
+    tm->start(2, s, 3, pl.maxM);
     if (pl.mixed == 2) {
       if ((e = launch_leaf_syrk_em(d_desc, pl.w_syrk, pl.n_syrk, pl.maxM, pl.r, status, s))) return e;
     } else {
@@ -570,16 +573,16 @@ cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaS
     ++*launches;
   }
   // posterior pass, bottom-up
-  for (int m = pl.maxM - 1; m >= 0; --m) {
+  for (int m = post_hi - 1; m >= pl.post_lo; --m) {
     if (pl.n_lvl[m] > 0) {
-      tm->start(3, s);
+      tm->start(3, s, 4, m);
       if ((e = launch_post_level(pl.mixed == 2, tile, m, pl.n_lvl[m], s, d_desc, pl.w_lvl[m], status))) return e;
       tm->stop(s);
       ++*launches;
     }
     if (m > 0 && pl.n_agg[m] > 0) {
       dim3 g2(pl.n_agg[m], m * (m + 1) / 2);
-      tm->start(4, s);
+      tm->start(4, s, 5, m);
       if (pl.mixed == 2) {
         if ((e = launch_aggregate_em(m, pl.r, d_desc, pl.w_agg[m], pl.n_agg[m], status, s))) return e;
       } else {

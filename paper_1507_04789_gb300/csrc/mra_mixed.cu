@@ -764,7 +764,7 @@ cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nbl
 }
 
 cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int emu, int* status,
-                           cudaStream_t s, const int2* w_par, int n_par) {
+                           cudaStream_t s, const int2* w_par, int n_par, Timer* tm, int leaf_level) {
   cudaError_t e;
   if (emu) {
     // the chain per parent first (work list: the level-(M-1) regions of every dataset)
@@ -775,6 +775,10 @@ cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, in
         return e;
       chain_forward_kernel_em<<<n_par, NT, EM_SOLO_SMEM, s>>>(d_desc, w_par, status);
       if ((e = cudaGetLastError())) return e;
+      if (tm) {   // the chain and the leaf kernel are timed as two records
+        tm->stop(s);
+        tm->start(1, s, 2, leaf_level);
+      }
     }
     const size_t sm = leaf_tc_smem<true>(nlmax);
     if ((e = cudaFuncSetAttribute(leaf_kernel_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
@@ -1002,7 +1006,7 @@ __global__ void __launch_bounds__(NT) chain_adjoint_kernel_em(const Desc* __rest
   eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
   TcAcc acc;
   const int row = acc.row(), c0 = acc.col0();
-  double g_s2 = 0.0, g_k = 0.0;
+  double g_s2 = 0.0, g_k = 0.0, g_nu = 0.0;
   bool ok = true;
   for (long t0 = row0; t0 < row1 && ok; t0 += TC_M) {
     const int na = (int)min((long)TC_M, row1 - t0);
@@ -1041,16 +1045,17 @@ __global__ void __launch_bounds__(NT) chain_adjoint_kernel_em(const Desc* __rest
           if (col < r) {
             const double xb = acc.v[c];
             XB[(long)row * Mr + l * r + col] = xb;
-            double d1, d2;
-            if (lf.dc) {   // stored by the forward chain kernel
+            double d1, d2, d3 = 0.0;
+            if (lf.dc) {   // stored by the forward chain kernel (families without d/dnu)
               const double2 dd = *reinterpret_cast<const double2*>(lf.dc + 2 * ((t0 + row) * Mr + l * r + col));
               d1 = dd.x;
               d2 = dd.y;
             } else {
-              dcov0(cv, so_x, so_y, ax[col], ay[col], d1, d2);
+              dcov0(cv, so_x, so_y, ax[col], ay[col], d1, d2, d3);
             }
             g_s2 = fma(xb, d1, g_s2);
             g_k = fma(xb, d2, g_k);
+            g_nu = fma(xb, d3, g_nu);
           }
         }
         int e = -2000;   // row scale of Xbar^l (two threads per row)
@@ -1092,10 +1097,12 @@ __global__ void __launch_bounds__(NT) chain_adjoint_kernel_em(const Desc* __rest
   eng.release();
   g_s2 = block_sum(g_s2, red);
   g_k = block_sum(g_k, red);
+  g_nu = block_sum(g_nu, red);
   if (threadIdx.x == 0) {
-    gs.gpart[3 * (slot0 + p) + 0] = g_s2;
-    gs.gpart[3 * (slot0 + p) + 1] = g_k;
-    gs.gpart[3 * (slot0 + p) + 2] = 0.0;
+    gs.gpart[GP * (slot0 + p) + 0] = g_s2;
+    gs.gpart[GP * (slot0 + p) + 1] = g_k;
+    gs.gpart[GP * (slot0 + p) + 2] = 0.0;
+    gs.gpart[GP * (slot0 + p) + 3] = g_nu;
     if (!ok) flag_error(status, ST_TIMEOUT, M - 1, p);
   }
 }

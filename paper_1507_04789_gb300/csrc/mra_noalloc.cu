@@ -107,14 +107,18 @@ extern "C" int mra_loglik_noalloc(const mra_config* cfg, const mra_params* theta
   if (cfg->M < 0 || cfg->M > MRA_MAX_M) return err(MRA_ERR_ARG, "M must be in [0, %d]", MRA_MAX_M);
   if (cfg->J != 4) return err(MRA_ERR_ARG, "J must be 4 (2-D midpoint quadtree)");
   if (cfg->r < 1 || cfg->r > MRA_MAX_R) return err(MRA_ERR_ARG, "r must be in [1, %d]", MRA_MAX_R);
-  if (cfg->cov_family != MRA_COV_EXP && cfg->cov_family != MRA_COV_MATERN15)
+  if (cfg->cov_family != MRA_COV_EXP && cfg->cov_family != MRA_COV_MATERN15 && cfg->cov_family != MRA_COV_MATERN)
     return err(MRA_ERR_ARG, "unknown covariance family %d", cfg->cov_family);
+  if (cfg->cov_family == MRA_COV_MATERN && !(std::isfinite(theta->nu) && theta->nu >= 0.05 && theta->nu <= 20.0))
+    return err(MRA_ERR_ARG, "MRA_COV_MATERN needs 0.05 <= nu <= 20");
   if (cfg->nonstat != 0 && cfg->nonstat != 1) return err(MRA_ERR_ARG, "nonstat must be 0 or 1");
   if (cfg->precision != MRA_PREC_FP64)
     return err(MRA_ERR_ARG, "precision must be MRA_PREC_FP64 in the allocation-free entry point (got %d)",
                cfg->precision);
   if (cfg->prune != 0)
     return err(MRA_ERR_ARG, "prune must be 0 in the allocation-free entry point (complete tree only)");
+  if (cfg->stream_level > 0)
+    return err(MRA_ERR_ARG, "stream_level must be 0 or -1 in the allocation-free entry point");
   if (!(cfg->bbox[0] < cfg->bbox[1]) || !(cfg->bbox[2] < cfg->bbox[3]))
     return err(MRA_ERR_ARG, "empty or invalid bounding box");
   if (!(std::isfinite(theta->sigma2) && std::isfinite(theta->range) && std::isfinite(theta->tau2) &&
@@ -232,7 +236,7 @@ extern "C" int mra_loglik_noalloc(const mra_config* cfg, const mra_params* theta
   sh.mixed = 0;
   mra::Desc hd{};
   hd.sh = sh;
-  hd.cv = mra::make_cov(theta->sigma2, theta->range, cfg->cov_family, cfg->nonstat);
+  hd.cv = mra::make_cov(theta->sigma2, theta->range, cfg->cov_family, cfg->nonstat, theta->nu);
   hd.tau2 = theta->tau2;
   hd.nlmax = nlmax;
   hd.st = st;

@@ -12,21 +12,36 @@
 //       Bhat^{l,k} -= Y_l G^k_l  for k < l                            (Eq. bfrecursion, recursion)
 // since K~_l = L_l^{-T} Lt_l^{-T} Lt_l^{-1} L_l^{-1}, K~_l omega^l = L_l^{-T} Lt_l^{-T} g_l
 // and K~_l A^{l,k} L_k^{-T} = L_l^{-T} Lt_l^{-T} G^k_l.
+//
+// The joint posterior predictive distribution of Prop. 2 (y(S^P_F) = sum_m
+// B~^{m+1,m}_F eta~_m + delta~_F, eta~ shared by the leaves under a region)
+// follows from the same quantities: with F_l = L_l^{-T} Lt_l^{-T} (F_l F_l' =
+// K~_l), B~^{l+1,l} F_l = Y_l, so
+//   Cov(s1, s2) = sum_{l: common level-l region} Y_l(s1) Y_l(s2)' + 1[same leaf] D(s1, s2),
+//   D = V^P - L^M Sigma^{-1} L^M' = C0(S^P, S^P) - Uhat Uhat' - P P',
+// and a draw is mean + sum_l Y_l xi_{R_l} + chol(D) zeta.  The joint modes of
+// predict_kernel keep the Y_l in place of the Bhat blocks and store D (or its
+// Cholesky factor) per leaf; joint_cov_kernel and simulate_kernel use them.
+#include <algorithm>
+
 #include "mra_launch.h"
 
 namespace mra {
 
-template <int TILE>
+// MODE 0: marginal mean and variance; 1: also D and the Y_l (joint
+// covariance); 2: also chol(D) and the Y_l (simulation).  In the joint modes
+// one CTA holds all points of its leaf (at most TILE).
+template <int TILE, int MODE>
 __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D, PredState ps, int* status) {
   extern __shared__ double smem[];
-  const Desc& ds = D[0];
+  const Desc& ds = D[ps.desc];
   const Shape sh = ds.sh;
   const Cov cv = ds.cv;
   const int nlmax = ds.nlmax;
   const LevelState& st = ds.st;
   const LeafState& lf = ds.lf;
   const int M = sh.M, r = sh.r, Mr = M * r;
-  const long F = blockIdx.x;                     // Morton id of the leaf
+  const long F = ps.leaf0 + blockIdx.x;          // Morton id of the leaf
   const long p0 = ps.off[F] + (long)blockIdx.y * TILE;
   const long p1 = min(ps.off[F + 1], p0 + TILE);
   if (p0 >= p1) return;
@@ -42,14 +57,15 @@ __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D,
   const long o0 = lf.off[F];
   const int nF = (int)(lf.off[F + 1] - o0);
   const int ldp = nlmax + 1, ldy = r + 1;
+  const int ldc = MODE ? (nlmax > TILE ? nlmax : TILE) + 1 : ldp;   // Cs later holds D (joint modes)
   double* px = smem;
   double* py = px + TILE;
   double* mu = py + TILE;
   double* va = mu + TILE;
   double* ax = va + TILE;
   double* ay = ax + MAX_R_DEV;
-  double* Cs = ay + MAX_R_DEV;                  // TILE x (nlmax + 1): C0(S^P, S_F)
-  double* Ps = Cs + (long)TILE * ldp;           // TILE x (nlmax + 1): P
+  double* Cs = ay + MAX_R_DEV;                  // TILE x ldc: C0(S^P, S_F), then D
+  double* Ps = Cs + (long)TILE * ldc;           // TILE x (nlmax + 1): P
   double* Ys = Ps + (long)TILE * ldp;           // TILE x (r + 1)
   double* stg = Ys + (long)TILE * ldy;
   for (int t = threadIdx.x; t < nP; t += NT) {
@@ -100,14 +116,14 @@ __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D,
     const double* HF = lf.H + o0 * Mr;
     for (int t = threadIdx.x; t < nP * nF; t += NT) {
       int i = t / nF, k = t - i * nF;
-      Cs[i * ldp + k] = cov0(cv, px[i], py[i], lf.xs[o0 + k], lf.ys[o0 + k]);
+      Cs[i * ldc + k] = cov0(cv, px[i], py[i], lf.xs[o0 + k], lf.ys[o0 + k]);
     }
     __syncthreads();
     const int nct = (nF + TILE - 1) / TILE;
     for (int ct = 0; ct < nct; ++ct) {
       const int ncol = min(TILE, nF - ct * TILE);
       acc.zero();
-      tile_mma<TILE>(acc, Cs, ldp, 1, nP, LS + (long)ct * TILE * nF, nF, 1, ncol, nF, stg);
+      tile_mma<TILE>(acc, Cs, ldc, 1, nP, LS + (long)ct * TILE * nF, nF, 1, ncol, nF, stg);
       if (M > 0) {
         TileAcc<TILE> sub;
         sub.zero();
@@ -136,6 +152,37 @@ __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D,
       mu[t] += m;
       va[t] -= q2;
     }
+  }
+  if (MODE) {
+    // D = C0(S^P, S^P) - Uhat Uhat' - P P' over the leaf's points (Cs is free)
+    __syncthreads();
+    acc.zero();
+    if (M > 0) tile_mma<TILE>(acc, U, Mr, 1, nP, U, Mr, 1, nP, Mr, stg);
+    if (nF > 0) tile_mma<TILE>(acc, Ps, ldp, 1, nP, Ps, ldp, 1, nP, nF, stg);
+#pragma unroll
+    for (int p = 0; p < RM; ++p)
+#pragma unroll
+      for (int q = 0; q < RM; ++q) {
+        int row = acc.row(p), col = acc.col(q);
+        if (row < nP && col < nP) Cs[row * ldc + col] = cov0(cv, px[row], py[row], px[col], py[col]) - acc.v[p][q];
+      }
+    __shared__ int bad;
+    if (MODE == 2) {
+      if (threadIdx.x == 0) bad = 0;
+      chol_smem(Cs, nP, ldc, &bad);
+      if (threadIdx.x == 0 && bad) flag_error(status, ST_NOT_PD, M + 1, F);
+    }
+    __syncthreads();
+    double* Dg = ps.D + ps.sq_off[F];
+    for (int t = threadIdx.x; t < nP * nP; t += NT) {
+      const int i = t / nP, j = t - i * nP;
+      Dg[t] = (MODE == 2 && j > i) ? 0.0 : Cs[i * ldc + j];
+    }
+    for (int t = threadIdx.x; t < nP; t += NT) ps.leaf[p0 + t] = (int32_t)F;
+  }
+  if (nF > 0) {
+    const double* HF = lf.H + o0 * Mr;
+    __syncthreads();
     // Bhat^{M,k} = Uhat^k - P H^k_F  (in place in U)
     for (int k = 0; k < M; ++k) {
       acc.zero();
@@ -174,6 +221,11 @@ __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D,
       mu[t] += m;
       va[t] += q2;
     }
+    if (MODE)                                    // keep Y_l in place of block l (no longer read)
+      for (int t = threadIdx.x; t < nP * r; t += NT) {
+        const int i = t / r, c = t - i * r;
+        U[(long)i * Mr + l * r + c] = Ys[i * ldy + c];
+      }
     const double* Gl = st.G[l] + a * (long)r * (l * r);
     for (int k = 0; k < l; ++k) {
       acc.zero();
@@ -203,25 +255,184 @@ size_t predict_smem_bytes(int r, int nlmax) {
                            (size_t)tile * (r + 1) + 2 * KC * (tile + 2));
 }
 
+// Joint modes: one 64-point tile per leaf; Cs wide enough to hold D.
+size_t joint_smem_bytes(int r, int nlmax) {
+  const size_t tile = JOINT_TILE, ldc = (size_t)(nlmax > JOINT_TILE ? nlmax : JOINT_TILE) + 1;
+  return sizeof(double) * (4 * tile + 2 * MAX_R_DEV + tile * ldc + tile * (nlmax + 1) + tile * (r + 1) +
+                           2 * KC * (tile + 2));
+}
+
 cudaError_t launch_predict(const Desc* d_desc, int M, int r, int nlmax, const PredState& ps, int max_per_leaf,
-                           int* status, cudaStream_t s, int64_t* launches, Timer* tm) {
+                           int* status, cudaStream_t s, int64_t* launches, Timer* tm, long nleaf) {
   const int tile = tile_of(r);
   const size_t sm = predict_smem_bytes(r, nlmax);
-  dim3 grid(1u << (2 * M), (unsigned)((max_per_leaf + tile - 1) / tile));
+  dim3 grid(nleaf > 0 ? (unsigned)nleaf : 1u << (2 * M), (unsigned)((max_per_leaf + tile - 1) / tile));
   if (grid.y == 0) return cudaSuccess;
   cudaError_t e;
   tm->start(5, s);
 #define MRA_PRED_LAUNCH(T)                                                                              \
   {                                                                                                     \
-    e = cudaFuncSetAttribute(predict_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);  \
+    e = cudaFuncSetAttribute(predict_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
     if (e) return e;                                                                                    \
-    predict_kernel<T><<<grid, NT, sm, s>>>(d_desc, ps, status);                                         \
+    predict_kernel<T, 0><<<grid, NT, sm, s>>>(d_desc, ps, status);                                      \
   }
   if (tile == 16) MRA_PRED_LAUNCH(16)
   else if (tile == 32) MRA_PRED_LAUNCH(32)
   else MRA_PRED_LAUNCH(64)
 #undef MRA_PRED_LAUNCH
   tm->stop(s);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+// ---- joint posterior predictive covariance ------------------------------------
+// cov[perm i][perm j] = sum_{l < M: i, j share their level-l region} Y_l(i) Y_l(j)'
+//                       + 1[same leaf] D(i, j), over 64 x 64 tiles of sorted points.
+__global__ void __launch_bounds__(NT) joint_cov_kernel(const Desc* __restrict__ D, PredState ps, int64_t np,
+                                                       double* cov) {
+  __shared__ double Ya[64][MAX_R_DEV + 1], Yb[64][MAX_R_DEV + 1];
+  __shared__ int32_t fa[64], fb[64];
+  const Desc& ds = D[0];
+  const int M = ds.sh.M, r = ds.sh.r, Mr = M * r;
+  const long i0 = (long)blockIdx.y * 64, j0 = (long)blockIdx.x * 64;
+  const int ni = (int)min((int64_t)64, np - i0), nj = (int)min((int64_t)64, np - j0);
+  for (int t = threadIdx.x; t < 64; t += NT) {
+    fa[t] = t < ni ? ps.leaf[i0 + t] : -1;
+    fb[t] = t < nj ? ps.leaf[j0 + t] : -2;
+  }
+  __syncthreads();                               // (read below even when M = 0)
+  const int ti = (threadIdx.x >> 4) * 4, tj = (threadIdx.x & 15) * 4;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int l = 0; l < M; ++l) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < 64 * r; t += NT) {
+      const int p = t / r, c = t - p * r;
+      Ya[p][c] = p < ni ? ps.U[(i0 + p) * Mr + l * r + c] : 0.0;
+      Yb[p][c] = p < nj ? ps.U[(j0 + p) * Mr + l * r + c] : 0.0;
+    }
+    __syncthreads();
+    const int sh = 2 * (M - l);
+    bool any = false;
+    bool same[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        same[a][b] = fa[ti + a] >= 0 && fb[tj + b] >= 0 && (fa[ti + a] >> sh) == (fb[tj + b] >> sh);
+        any |= same[a][b];
+      }
+    if (!any) continue;
+    for (int c = 0; c < r; ++c) {
+      double xa[4], xb[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) xa[a] = Ya[ti + a][c];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) xb[b] = Yb[tj + b][c];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (same[a][b]) acc[a][b] = fma(xa[a], xb[b], acc[a][b]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int i = ti + a, j = tj + b;
+      if (i >= ni || j >= nj) continue;
+      double v = acc[a][b];
+      const int32_t F = fa[i];
+      if (F == fb[j]) {
+        const long o = ps.off[F];
+        const long nP = ps.off[F + 1] - o;
+        v += ps.D[ps.sq_off[F] + (i0 + i - o) * nP + (j0 + j - o)];
+      }
+      cov[ps.perm[i0 + i] * np + ps.perm[j0 + j]] = v;
+    }
+}
+
+// ---- conditional simulation ------------------------------------------------------
+// draw[s][perm p] = mean[perm p] + sum_l Y_l(p) xi[s][(o_l + R_l) r ..] + sum_{q <= p in the leaf}
+// chol(D)(p, q) zeta[s][perm q]; o_l = (4^l - 1) / 3 regions before level l.  One CTA
+// per (leaf, chunk of 4 draws), one thread per (point, draw).
+__global__ void __launch_bounds__(NT) simulate_kernel(const Desc* __restrict__ D, PredState ps, int64_t np,
+                                                      int64_t nsim, int64_t nxi, const double* __restrict__ xi,
+                                                      const double* __restrict__ zeta, double* draws) {
+  __shared__ double xs[4][MAXL * MAX_R_DEV];
+  __shared__ double zs[4][JOINT_TILE];
+  const Desc& ds = D[0];
+  const int M = ds.sh.M, r = ds.sh.r, Mr = M * r;
+  const long F = blockIdx.x;
+  const long p0 = ps.off[F];
+  const int nP = (int)(ps.off[F + 1] - p0);
+  if (nP == 0) return;
+  const double* Lc = ps.D + ps.sq_off[F];
+  for (long s0 = (long)blockIdx.y * 4; s0 < nsim; s0 += 4L * gridDim.y) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < 4 * Mr; t += NT) {
+      const int d = t / Mr, c = t - d * Mr, l = c / r;
+      const long s = s0 + d;
+      const long reg = (((1L << (2 * l)) - 1) / 3) + (F >> (2 * (M - l)));
+      xs[d][c] = s < nsim ? xi[s * nxi + reg * r + (c - l * r)] : 0.0;
+    }
+    for (int t = threadIdx.x; t < 4 * nP; t += NT) {
+      const int d = t / nP, q = t - d * nP;
+      const long s = s0 + d;
+      zs[d][q] = s < nsim ? zeta[s * np + ps.perm[p0 + q]] : 0.0;
+    }
+    __syncthreads();
+    const int d = threadIdx.x / JOINT_TILE, p = threadIdx.x - d * JOINT_TILE;
+    const long s = s0 + d;
+    if (p < nP && s < nsim) {
+      const long orig = ps.perm[p0 + p];
+      double v = ps.mean[orig];
+      const double* Yp = ps.U + (p0 + p) * Mr;
+      for (int c = 0; c < Mr; ++c) v = fma(Yp[c], xs[d][c], v);
+      for (int q = 0; q <= p; ++q) v = fma(Lc[p * nP + q], zs[d][q], v);
+      draws[s * np + orig] = v;
+    }
+  }
+}
+
+cudaError_t launch_predict_joint(const Desc* d_desc, int M, int r, int nlmax, const PredState& ps, int mode,
+                                 int* status, cudaStream_t s, int64_t* launches, Timer* tm) {
+  const size_t sm = joint_smem_bytes(r, nlmax);
+  dim3 grid(1u << (2 * M), 1);
+  cudaError_t e;
+  tm->start(5, s);
+  if (mode == 1) {
+    if ((e = cudaFuncSetAttribute(predict_kernel<JOINT_TILE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm)))
+      return e;
+    predict_kernel<JOINT_TILE, 1><<<grid, NT, sm, s>>>(d_desc, ps, status);
+  } else {
+    if ((e = cudaFuncSetAttribute(predict_kernel<JOINT_TILE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm)))
+      return e;
+    predict_kernel<JOINT_TILE, 2><<<grid, NT, sm, s>>>(d_desc, ps, status);
+  }
+  tm->stop(s);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_joint_cov(const Desc* d_desc, const PredState& ps, int64_t np, double* cov, cudaStream_t s,
+                             int64_t* launches) {
+  const unsigned nb = (unsigned)((np + 63) / 64);
+  joint_cov_kernel<<<dim3(nb, nb), NT, 0, s>>>(d_desc, ps, np, cov);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_simulate(const Desc* d_desc, int M, const PredState& ps, int64_t np, int64_t nsim, int64_t nxi,
+                            const double* xi, const double* zeta, double* draws, cudaStream_t s, int64_t* launches) {
+  const unsigned gy = (unsigned)std::min<int64_t>((nsim + 3) / 4, 64);
+  simulate_kernel<<<dim3(1u << (2 * M), gy), NT, 0, s>>>(d_desc, ps, np, nsim, nxi, xi, zeta, draws);
   ++*launches;
   return cudaGetLastError();
 }

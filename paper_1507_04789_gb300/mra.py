@@ -21,13 +21,13 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libmra_gb300.so")
 
 MRA_OK, MRA_ERR_ARG, MRA_ERR_OOM, MRA_ERR_CUDA, MRA_ERR_NOT_PD, MRA_ERR_STATE, MRA_ERR_LIMIT = range(7)
-MRA_COV_EXP, MRA_COV_MATERN15 = 0, 1
+MRA_COV_EXP, MRA_COV_MATERN15, MRA_COV_MATERN = 0, 1, 2
 MRA_PREC_FP64, MRA_PREC_MIXED, MRA_PREC_EMU = 0, 1, 2
 PRECISIONS = {"fp64": MRA_PREC_FP64, "mixed": MRA_PREC_MIXED, "emu": MRA_PREC_EMU}
 MRA_HOST, MRA_DEVICE = 0, 1
 MRA_MAX_LEAF = 128
 MRA_OPT_GRAD_BUFFERS = 0
-FAMILIES = {"exp": MRA_COV_EXP, "matern15": MRA_COV_MATERN15}
+FAMILIES = {"exp": MRA_COV_EXP, "matern15": MRA_COV_MATERN15, "matern": MRA_COV_MATERN}
 KERNEL_KINDS = ("prior", "leaf", "leaf_syrk", "post", "aggregate", "predict", "grad")
 
 
@@ -42,11 +42,40 @@ class MRAError(RuntimeError):
 class MraConfig(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("J", ctypes.c_int), ("r", ctypes.c_int),
                 ("cov_family", ctypes.c_int), ("nonstat", ctypes.c_int),
-                ("precision", ctypes.c_int), ("prune", ctypes.c_int), ("bbox", ctypes.c_double * 4)]
+                ("precision", ctypes.c_int), ("prune", ctypes.c_int), ("bbox", ctypes.c_double * 4),
+                ("stream_level", ctypes.c_int)]
 
 
 class MraParams(ctypes.Structure):
-    _fields_ = [("sigma2", ctypes.c_double), ("range", ctypes.c_double), ("tau2", ctypes.c_double)]
+    _fields_ = [("sigma2", ctypes.c_double), ("range", ctypes.c_double), ("tau2", ctypes.c_double),
+                ("nu", ctypes.c_double)]
+
+
+MRA_MAX_M = 12
+STAGES = ("prior", "chain", "leaf", "leaf_syrk", "post", "aggregate")   # MRA_STAGE_* order
+
+
+class MraStats(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int), ("evaluations", ctypes.c_int64),
+                ("ms", (ctypes.c_double * 6) * (MRA_MAX_M + 1)),
+                ("launches", (ctypes.c_int64 * 6) * (MRA_MAX_M + 1)),
+                ("flops", (ctypes.c_double * 6) * (MRA_MAX_M + 1)),
+                ("bytes", (ctypes.c_double * 6) * (MRA_MAX_M + 1)),
+                ("units", (ctypes.c_double * 6) * (MRA_MAX_M + 1))]
+
+
+def _stats(lib, h) -> dict:
+    st = MraStats()
+    _check(lib.mra_stats(h, ctypes.byref(st)))
+    out = {"M": st.M, "evaluations": st.evaluations, "levels": []}
+    for m in range(st.M + 1):
+        row = {}
+        for k, name in enumerate(STAGES):
+            if st.units[m][k] or st.launches[m][k]:
+                row[name] = {"ms": st.ms[m][k], "launches": st.launches[m][k], "flops": st.flops[m][k],
+                             "bytes": st.bytes[m][k], "units": st.units[m][k]}
+        out["levels"].append(row)
+    return out
 
 
 _P = ctypes.c_void_p
@@ -88,6 +117,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "mra_loglik_batch": (ctypes.c_int, [_P, ctypes.POINTER(MraParams), _P]),
         "mra_autotune": (ctypes.c_int, [_P, ctypes.POINTER(MraParams), ctypes.POINTER(ctypes.c_int)]),
         "mra_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+        "mra_loglik_grad_batch": (ctypes.c_int, [_P, ctypes.POINTER(MraParams), _P, _P]),
+        "mra_stats": (ctypes.c_int, [_P, ctypes.POINTER(MraStats)]),
+        "mra_predict_joint": (ctypes.c_int, [_P, ctypes.POINTER(MraParams), _P, ctypes.c_int64, ctypes.c_int,
+                                             _P, _P]),
+        "mra_simulate": (ctypes.c_int, [_P, ctypes.POINTER(MraParams), _P, ctypes.c_int64, ctypes.c_int,
+                                        ctypes.c_int64, _P, _P, _P]),
+        "mra_simulate_xi_len": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+        "mra_summary_len": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "mra_loglik_subtrees": (ctypes.c_int, [_P, ctypes.POINTER(MraParams), ctypes.c_int64, ctypes.c_int64, _P]),
+        "mra_loglik_combine": (ctypes.c_int, [_P, ctypes.POINTER(MraParams), _P, _D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -131,13 +170,14 @@ class Handle:
     """One M-RA problem on the GPU: locations, data and the tree (Sec. 2.2)."""
 
     def __init__(self, locs, y, M: int, r: int, family: str = "exp", nonstat: bool = False,
-                 bbox=(0.0, 1.0, 0.0, 1.0), J: int = 4, precision="fp64", prune: bool = False):
+                 bbox=(0.0, 1.0, 0.0, 1.0), J: int = 4, precision="fp64", prune: bool = False,
+                 stream_level: int = 0):
         lib = load_library()
         self._lib = lib
         self._h = _P()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         cfg = MraConfig(M, J, r, FAMILIES[family] if isinstance(family, str) else int(family),
-                        int(bool(nonstat)), prec, int(bool(prune)), (ctypes.c_double * 4)(*bbox))
+                        int(bool(nonstat)), prec, int(bool(prune)), (ctypes.c_double * 4)(*bbox), int(stream_level))
         if _is_torch_cuda(locs):
             if locs.dim() != 2 or locs.shape[1] != 2:
                 raise ValueError("locs must be (n, 2)")
@@ -207,6 +247,11 @@ class Handle:
     def enable_timing(self, on: bool = True) -> None:
         _check(self._lib.mra_enable_timing(self._h, 1 if on else 0))
 
+    def stats(self) -> dict:
+        """mra_stats: per level and stage, summed device time and launches of the
+        timed evaluations and the algorithmic FLOPs / bytes of one evaluation."""
+        return _stats(self._lib, self._h)
+
     def kernel_times(self) -> dict:
         """{kind: (total_ms, launches)} since enable_timing."""
         out = {}
@@ -226,12 +271,14 @@ class Handle:
         return out.value
 
     def loglik_grad(self, theta):
-        """(loglik, d loglik / d(sigma2, range, tau2))."""
+        """(loglik, d loglik / d(sigma2, range, tau2)), and d/dnu as a fourth
+        component for the free-smoothness family (theta = (sigma2, range, tau2, nu))."""
         out = ctypes.c_double()
-        g = np.zeros(3)
+        four = self.family in ("matern", MRA_COV_MATERN)
+        g = np.zeros(4)
         p = MraParams(*[float(v) for v in theta])
         _check(self._lib.mra_loglik_grad(self._h, ctypes.byref(p), ctypes.byref(out), g.ctypes.data))
-        return out.value, g
+        return out.value, (g if four else g[:3].copy())
 
     def predict(self, theta, plocs):
         """Posterior predictive mean and variance of y at plocs (Sec. 3.4, Prop. 2)."""
@@ -250,6 +297,78 @@ class Handle:
         _check(self._lib.mra_predict(self._h, ctypes.byref(p), pa.ctypes.data, pa.shape[0], MRA_HOST,
                                      mean.ctypes.data, var.ctypes.data))
         return mean, var
+
+    def predict_joint(self, theta, plocs):
+        """Joint posterior predictive mean and np x np covariance of y (Prop. 2)."""
+        p = MraParams(*[float(v) for v in theta])
+        if _is_torch_cuda(plocs):
+            import torch
+            npred = plocs.shape[0]
+            mean = torch.empty(npred, dtype=torch.float64, device=plocs.device)
+            cov = torch.empty((npred, npred), dtype=torch.float64, device=plocs.device)
+            _check(self._lib.mra_predict_joint(self._h, ctypes.byref(p), _dev_ptr(plocs, "plocs"), npred,
+                                               MRA_DEVICE, mean.data_ptr(), cov.data_ptr()))
+            return mean, cov
+        pa = _host_f64(plocs, 2)
+        mean = np.empty(pa.shape[0])
+        cov = np.empty((pa.shape[0], pa.shape[0]))
+        _check(self._lib.mra_predict_joint(self._h, ctypes.byref(p), pa.ctypes.data, pa.shape[0], MRA_HOST,
+                                           mean.ctypes.data, cov.ctypes.data))
+        return mean, cov
+
+    def xi_len(self) -> int:
+        """Standard normals per draw for the regions (mra_simulate_xi_len)."""
+        n = ctypes.c_int64()
+        _check(self._lib.mra_simulate_xi_len(self._h, ctypes.byref(n)))
+        return n.value
+
+    def simulate(self, theta, plocs, xi, zeta):
+        """Conditional simulations (Prop. 2): draws (nsim x np) from the joint
+        posterior predictive given standard normals xi (nsim x xi_len) and zeta
+        (nsim x np).  Host arrays in, host array out; torch CUDA tensors in,
+        a CUDA tensor out."""
+        p = MraParams(*[float(v) for v in theta])
+        if _is_torch_cuda(plocs):
+            import torch
+            nsim, npred = zeta.shape
+            draws = torch.empty((nsim, npred), dtype=torch.float64, device=plocs.device)
+            _check(self._lib.mra_simulate(self._h, ctypes.byref(p), _dev_ptr(plocs, "plocs"), npred, MRA_DEVICE,
+                                          nsim, _dev_ptr(xi, "xi") if xi.numel() else None, _dev_ptr(zeta, "zeta"),
+                                          draws.data_ptr()))
+            return draws
+        pa = _host_f64(plocs, 2)
+        za = np.ascontiguousarray(np.atleast_2d(zeta), dtype=np.float64)
+        xa = np.ascontiguousarray(np.atleast_2d(xi), dtype=np.float64)
+        nsim = za.shape[0]
+        if za.shape[1] != pa.shape[0] or xa.shape[0] != nsim or xa.shape[1] != self.xi_len():
+            raise ValueError("xi must be nsim x xi_len() and zeta nsim x np")
+        draws = np.empty((nsim, pa.shape[0]))
+        _check(self._lib.mra_simulate(self._h, ctypes.byref(p), pa.ctypes.data, pa.shape[0], MRA_HOST, nsim,
+                                      xa.ctypes.data if xa.size else None, za.ctypes.data, draws.ctypes.data))
+        return draws
+
+    def summary_len(self):
+        """(doubles per level-s summary, number of level-s subtrees) of a streamed handle."""
+        n, k = ctypes.c_int64(), ctypes.c_int64()
+        _check(self._lib.mra_summary_len(self._h, ctypes.byref(n), ctypes.byref(k)))
+        return n.value, k.value
+
+    def loglik_subtrees(self, theta, first: int, count: int) -> np.ndarray:
+        """Summaries (count x len) of the level-s subtrees [first, first + count)."""
+        length, _ = self.summary_len()
+        out = np.empty((max(count, 0), length))
+        p = MraParams(*[float(v) for v in theta])
+        _check(self._lib.mra_loglik_subtrees(self._h, ctypes.byref(p), int(first), int(count),
+                                             out.ctypes.data if count else None))
+        return out
+
+    def loglik_combine(self, theta, summaries) -> float:
+        """Log-likelihood from the summaries of every level-s subtree."""
+        sa = np.ascontiguousarray(summaries, dtype=np.float64)
+        p = MraParams(*[float(v) for v in theta])
+        out = ctypes.c_double()
+        _check(self._lib.mra_loglik_combine(self._h, ctypes.byref(p), sa.ctypes.data, ctypes.byref(out)))
+        return out.value
 
     def region_terms(self, level: int):
         """(d_R, u_R) of every region at ``level`` from the last loglik (Sec. 3.3)."""
@@ -329,6 +448,13 @@ class Batch:
         _check(self._lib.mra_loglik_batch(self._h, self._params(thetas), out.ctypes.data))
         return out
 
+    def loglik_grad(self, thetas):
+        """Log-likelihood and gradient d/d(sigma2, range, tau2) of every dataset."""
+        ll = np.empty(self.ndata)
+        g = np.empty((self.ndata, 3))
+        _check(self._lib.mra_loglik_grad_batch(self._h, self._params(thetas), ll.ctypes.data, g.ctypes.data))
+        return ll, g
+
     def autotune(self, thetas) -> int:
         tile = ctypes.c_int()
         _check(self._lib.mra_autotune(self._h, self._params(thetas), ctypes.byref(tile)))
@@ -341,6 +467,11 @@ class Batch:
 
     def enable_timing(self, on: bool = True) -> None:
         _check(self._lib.mra_enable_timing(self._h, 1 if on else 0))
+
+    def stats(self) -> dict:
+        """mra_stats: per level and stage, summed device time and launches of the
+        timed evaluations and the algorithmic FLOPs / bytes of one evaluation."""
+        return _stats(self._lib, self._h)
 
     def kernel_times(self) -> dict:
         out = {}

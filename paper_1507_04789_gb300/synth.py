@@ -136,14 +136,29 @@ class Workload:
     seed: int = 0
     J: int = 4
     features: int = 4096     # random Fourier features of the field draw
+    # "uniform": locations uniform on [0,1]^2, uniform prediction points;
+    # "swath200": 200 parallel swaths of width 0.004 at a common angle drawn from
+    # 45 +- 5 degrees, cut into 0.05-long segments each dropped with probability
+    # 0.3 (the satellite tracks with gaps of Sec. 4.3's data), prediction points
+    # on the cell-centred sqrt(n_pred) x sqrt(n_pred) grid
+    layout: str = "uniform"
+    nonstat: bool = False    # field times sqrt(g(s)), g(s) = 1 + sin(4 pi s_x) / 2
 
     def generate(self):
         """Return (locs (n,2), y (n,), plocs (n_pred,2)), all float64."""
         nu = 0.5 if self.family == "exp" else 1.5
-        locs = uniform_locations(self.n, self.seed)
+        if self.layout == "swath200":
+            ang = np.random.default_rng(self.seed + 4).uniform(40.0, 50.0) * math.pi / 180.0
+            locs = swath_locations(self.n, 200, 0.004, self.seed, drop=0.3, angle=ang, segment=0.05)
+            g = int(round(math.sqrt(self.n_pred)))
+            plocs = grid_points(g)
+        else:
+            locs = uniform_locations(self.n, self.seed)
+            plocs = uniform_locations(self.n_pred, self.seed + 3)
         field = rff_field(locs, nu, self.kappa, self.sigma2, self.seed + 1, self.features)
+        if self.nonstat:
+            field *= np.sqrt(1.0 + 0.5 * np.sin(4.0 * math.pi * locs[:, 0]))
         y = noisy_observations(field, self.tau2, self.seed + 2)
-        plocs = uniform_locations(self.n_pred, self.seed + 3)
         return locs, y, plocs
 
 
@@ -160,6 +175,13 @@ WORKLOADS = {
                                       features=256),
     # n=2^14 with the same leaf shape (gradient parity size).
     "n16k_matern15_M4_r64": Workload("n16k_matern15_M4_r64", 1 << 14, 4, 64, "matern15", 1.0, 0.1, 0.01, 1024),
+    # n=2^24 on 200 diagonal swaths with gaps, exponential (Matern-0.5) with the
+    # nonstationary variance, range 0.1, tau2=0.02, M=10, r=64, 2^20 grid points.
+    "n16M_swath_M10_r64": Workload("n16M_swath_M10_r64", 1 << 24, 10, 64, "exp", 1.0, 0.1, 0.02, 1 << 20,
+                                   features=128, layout="swath200", nonstat=True),
+    # the same layout at n=2^18, M=7 (about the same observations per active leaf)
+    "n256k_swath_M7_r64": Workload("n256k_swath_M7_r64", 1 << 18, 7, 64, "exp", 1.0, 0.1, 0.02, 1 << 12,
+                                   features=128, layout="swath200", nonstat=True),
 }
 
 

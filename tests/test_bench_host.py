@@ -80,3 +80,25 @@ def test_flop_models():
         # the Gram product of the leaves is linear in the observations under each parent
         alg2 = bench.algorithmic_flops(M, r, 2 * nF)
         assert alg2["leaf_syrk"] == pytest.approx(2 * alg["leaf_syrk"])
+
+
+def test_per_level_models():
+    """The contraction part of every (level, stage) stays within its algorithmic
+    FLOPs as the library's model counts them (here the bench's own per-kind
+    model, split by level), and the prediction model grows with the leaf size."""
+    bench = _bench()
+    rng = np.random.default_rng(4)
+    for M, r in ((2, 16), (4, 64)):
+        nF = rng.integers(20, 90, size=4 ** M)
+        alg = bench.algorithmic_flops(M, r, nF)
+        tot = {k: 0.0 for k in alg}
+        for m in range(M):
+            tot["prior"] += bench.contraction_share("prior", m, M, r, nF)
+            tot["post"] += bench.contraction_share("post", m, M, r, nF)
+            if m > 0:
+                tot["aggregate"] += bench.contraction_share("aggregate", m, M, r, nF)
+        tot["leaf"] = bench.contraction_share("chain", M, M, r, nF) + bench.contraction_share("leaf", M, M, r, nF)
+        tot["leaf_syrk"] = bench.contraction_share("leaf_syrk", M, M, r, nF)
+        for k in alg:
+            assert 0 < tot[k] <= alg[k], (M, r, k)
+    assert bench.predict_flops_per_point(7, 64, 80.0) > bench.predict_flops_per_point(7, 64, 40.0) > 0

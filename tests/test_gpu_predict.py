@@ -86,17 +86,26 @@ def test_device_buffers_and_state(mra):
     plocs = rng.random((120, 2))
     theta = (1.0, 0.15, 0.03)
     with mra.Handle(locs, y, M=2, r=16) as h:
-        with pytest.raises(mra.MRAError) as ei:
-            h.predict(theta, plocs)
-        assert ei.value.code == mra.MRA_ERR_STATE
-        h.loglik(theta)
+        m_first, v_first = h.predict(theta, plocs)       # no evaluation yet: the call evaluates at theta
+        ll = h.loglik(theta)
         m_host, v_host = h.predict(theta, plocs)
+        np.testing.assert_array_equal(m_first, m_host)
+        np.testing.assert_array_equal(v_first, v_host)
         m_dev, v_dev = h.predict(theta, torch.tensor(plocs, device="cuda"))
         np.testing.assert_array_equal(m_dev.cpu().numpy(), m_host)
         np.testing.assert_array_equal(v_dev.cpu().numpy(), v_host)
+        theta2 = (1.0, 0.2, 0.03)                        # another theta: evaluated first, then predicted
+        m2, v2 = h.predict(theta2, plocs)
+        p = O.Problem(locs, y, M=2, r=16, family="exp")
+        mo, vo = O.predict(p, theta2, plocs)
+        np.testing.assert_allclose(m2, mo, rtol=RTOL, atol=RTOL)
+        np.testing.assert_allclose(v2, vo, rtol=RTOL, atol=RTOL)
+        assert h.region_terms(0)[0][0] == pytest.approx(O.region_terms(p, theta2, 0, 0)[0], rel=1e-10)
         with pytest.raises(mra.MRAError) as ei:
-            h.predict((1.0, 0.2, 0.03), plocs)
-        assert ei.value.code == mra.MRA_ERR_STATE
+            h.predict((1.0, -0.2, 0.03), plocs)
+        assert ei.value.code == mra.MRA_ERR_ARG
+        h.predict(theta, plocs)
+        assert h.loglik(theta) == ll
         big = rng.random((5000, 2))                      # grows the prediction buffer
         mb, vb = h.predict(theta, big)
         np.testing.assert_array_equal(h.predict(theta, plocs)[0], m_host)
