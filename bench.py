@@ -61,7 +61,7 @@ if ROOT not in sys.path:
 
 METRIC = "M-RA loglik(+grad) evals/s at n=2^20, mixed vs FP64 plain; % of TC/FP64 peak"
 WORKLOAD = "n1M_matern15_M7_r64"
-FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (nominal)
+FP64_PEAK_TFLOPS = 1.10     # GB300 FP64 pipe, measured: DMMA m8n8k4 1.103, DFMA 1.059 TFLOP/s (tests/peaks.cu)
 BF16_PEAK_FALLBACK = 1900.0  # TFLOP/s, used only without a measured peak file
 TF32_PER_BF16 = 1.1 / 2.25   # nominal dense TF32 / bf16 tensor rates
 EMU_PAIRS = 28               # bf16 slice products per emulated FP64 MAC (7 slices, weights t <= 8)
@@ -133,13 +133,15 @@ def contraction_flops(M: int, r: int, nF, precision: str):
 # kernels) of the dominant kernel, from one ncu capture, valid only
 # while the kernel's sources are the ones it was taken from (else null).
 TRAFFIC = {
-    ("emu", "leaf", "n1M_matern15_M7_r64"): {
-        "bytes": 1.385e+10,
-        "how": "dram__bytes_read.sum + dram__bytes_write.sum of the leaf stage, chain_forward_kernel_em "
-               "(1.25 GB) + leaf_kernel_tc<1> (1.71 GB), at n = 2^18, M = 6 "
-               "(profiles/chain_forward_and_leaf_emu_n256k.md) scaled by n M r to n = 2^20, M = 7",
+    ("emu", "chain_forward_kernel_em", "n1M_matern15_M7_r64"): {
+        "bytes": 5.835e+09,
+        "how": "dram__bytes_read.sum + dram__bytes_write.sum of chain_forward_kernel_em (486.9 + 763.6 MB) "
+               "at n = 2^18, M = 6 (profiles/leaf_stage_emu_n256k_matern15_M6_r64.md), scaled by n M r "
+               "(x 4.667) to n = 2^20, M = 7; the kernel writes V_F (8 B x n x M r) and reads the points "
+               "and the ancestors' factors, both in proportion to n M r; captured before the adjoint kernels "
+               "in the same file took a region base, which leaves this kernel untouched",
         "sources": ["mra_mixed.cu", "mra_emu.cuh", "mra_tc.cuh", "mra_device.cuh", "mra_kernels.cuh"],
-        "sha1": "7dcd3fdb34bb3d74f2585a95499f65a18edc1b69",
+        "sha1": "9ff20caf3e8db293e5623709c07daf39f54eb9c7",
     },
 }
 
@@ -895,7 +897,7 @@ def main():
                 "frac": dom["frac"], "traffic": None, "kernel": dom["kernel"], "level": dom["level"],
                 "stage": dom["stage"],
                 "peak_source": (peak_src if dom["pipe"] == "tensor" else
-                                "nominal FP64 pipe (recipe unit counts x 2.07 GHz); profiles/fp64_dfma_peak.md"),
+                                "of measured FP64 pipe (DMMA 1.10 TFLOP/s, tests/peaks.cu; profiles/pipe_peaks_gb300.md)"),
                 "per_unit": dom["per_unit"], "units_per_launch": dom["units"],
                 "algorithmic_flops_per_launch": dom["flops"], "ms_per_launch": dom["ms_per_step"],
                 "launches_per_step": 1.0}

@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(NT) post_adjoint_kernel(int m, const Desc* __r
   const Shape sh = ds.sh;
   const LevelState& st = ds.st;
   const int r = sh.r, mr = m * r;
-  const long i = blockIdx.x;
+  const long i = gs.rbase + blockIdx.x;
   const long ld = r + 1;
   double* wbar = smem;                       // m r: omega~ adjoint (from ancestors)
   double* gbar = wbar + MAXL * MAX_R_DEV;    // r
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
   const LevelState& st = ds.st;
   const LeafState& lf = ds.lf;
   const int M = sh.M, r = sh.r, Mr = M * r;
-  const long F = blockIdx.x;                     // compact leaf id
+  const long F = gs.rbase + blockIdx.x;         // compact leaf id
   const long Fm = st.mort[M][F];
   const long o0 = lf.off[Fm];
   const int nF = (int)(lf.off[Fm + 1] - o0);
@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(NT) leaf_partial_kernel(const Desc* __restrict
   const Shape sh = ds.sh;
   const LeafState& lf = ds.lf;
   const int M = sh.M, r = sh.r, Mr = M * r;
-  const long p = blockIdx.x;                     // compact id at level M-1
+  const long p = gs.rbase + blockIdx.x;         // compact id at level M-1
   const long pm = ds.st.mort[M - 1][p];
   const int t = blockIdx.y;
   int l = 0;
@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
   const Cov cv = ds.cv;
   const LevelState& st = ds.st;
   const int r = sh.r, mr = m * r;
-  const long i = blockIdx.x;
+  const long i = gs.rbase + blockIdx.x;
   const long ld = r + 1;
   double* qx = smem;
   double* qy = qx + MAX_R_DEV;
@@ -896,11 +896,11 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
 
 // Emulated form: column exponents of every region's L^{-1} and V at level m
 // (the right operands of the chain adjoints), one CTA per region.
-__global__ void __launch_bounds__(NT) col_scales_kernel(int m, const Desc* __restrict__ D) {
+__global__ void __launch_bounds__(NT) col_scales_kernel(int m, const Desc* __restrict__ D, long rbase) {
   const Desc& ds = D[0];
   const LevelState& st = ds.st;
   const int r = ds.sh.r, mr = m * r;
-  const long i = blockIdx.x;
+  const long i = rbase + blockIdx.x;
   const double* Li = st.Li[m] + i * (long)r * r;
   const double* V = st.V[m] + i * (long)r * mr;
   for (int c = threadIdx.x; c < r + mr; c += NT) {
@@ -1014,80 +1014,117 @@ static cudaError_t launch_prior_adjoint(int tile, int m, int nregions, size_t sm
   return cudaGetLastError();
 }
 
-cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs, double* grad_out_dev, int* status,
-                        cudaStream_t s, int64_t* launches, Timer* tm) {
+// Slots of the per-CTA gradient partials: the prior-adjoint CTAs of levels
+// 0..M-1, then the leaves, then one per level-(M-1) region for the emulated
+// chain adjoint.
+static long slot_of_level(const LevelState& st, int m) {
+  long s = 0;
+  for (int l = 0; l < m; ++l) s += st.nreg[l];
+  return s;
+}
+
+cudaError_t launch_grad_range(const Desc& hd, const Desc* d_desc, GradState gs, const GradRange& R, int* status,
+                              cudaStream_t s, int64_t* launches) {
   const int tile = tile_of(hd.sh.r);
   const int M = hd.sh.M;
   const LevelState& st = hd.st;
   cudaError_t e;
   const size_t stg = sizeof(double) * 2 * KC * (tile + 2);
   const size_t sq = sizeof(double) * 3 * MAX_R_DEV * (MAX_R_DEV + 1);
-  // slots: prior-adjoint CTAs of levels 0..M-1, then the leaves
-  long slot_leaf = 0;
-  for (int m = 0; m < M; ++m) slot_leaf += st.nreg[m];
-  tm->start(6, s);
+  const int post_hi = R.post_hi < 0 ? M : R.post_hi, prior_hi = R.prior_hi < 0 ? M : R.prior_hi;
+  auto base = [&](int m) { return R.count[m] < 0 ? 0L : R.base[m]; };
+  auto count = [&](int m) { return R.count[m] < 0 ? (long)st.nreg[m] : R.count[m]; };
+  const long slot_leaf = slot_of_level(st, M);
   const bool emu = hd.sh.mixed == 2 && M > 0;
   if (emu && st.licol[0]) {   // column scales of L^{-1} and V for the emulated chain adjoints
-    for (int m = 0; m < M; ++m) {
-      col_scales_kernel<<<st.nreg[m], NT, 0, s>>>(m, d_desc);
+    for (int m = R.prior_lo; m < prior_hi; ++m) {
+      if (count(m) == 0) continue;
+      col_scales_kernel<<<(unsigned)count(m), NT, 0, s>>>(m, d_desc, base(m));
       ++*launches;
     }
     if ((e = cudaGetLastError())) return e;
   }
-  for (int m = 0; m < M; ++m) {
+  for (int m = R.post_lo; m < post_hi; ++m) {
+    if (count(m) == 0) continue;
+    gs.rbase = base(m);
     // emulated form with the per-region S buffer: Gbar on the tensor cores first
     const int gb_ready = emu && gs.SF != nullptr && m > 0;
-    if (gb_ready && (e = launch_gbar_em(m, hd, d_desc, gs, status, s, launches))) return e;
+    if (gb_ready) {   // (over the level-(m-1) parents)
+      GradState gp = gs;
+      gp.rbase = base(m - 1);
+      if ((e = launch_gbar_em(m, hd, d_desc, gp, status, s, launches, count(m - 1)))) return e;
+    }
     const size_t sm = sizeof(double) * (MAXL * MAX_R_DEV + MAX_R_DEV) + sq;
-    if (gb_ready) e = launch_post_adjoint<true>(tile, m, st.nreg[m], std::max(sm + EM_STAGE_BYTES, EM_SOLO_SMEM), s,
+    if (gb_ready) e = launch_post_adjoint<true>(tile, m, (int)count(m), std::max(sm + EM_STAGE_BYTES, EM_SOLO_SMEM), s,
                                                 d_desc, gs, gb_ready, status);
-    else e = launch_post_adjoint<false>(tile, m, st.nreg[m], sm + stg, s, d_desc, gs, gb_ready, status);
+    else e = launch_post_adjoint<false>(tile, m, (int)count(m), sm + stg, s, d_desc, gs, gb_ready, status);
     if (e) return e;
     ++*launches;
   }
-  // emulated form: Hbar on the tensor cores (when its per-parent S was allocated)
   const int em_parts = (emu && gs.SF != nullptr ? 1 : 0) | (emu ? 2 : 0);
-  if ((em_parts & 1) && (e = launch_hbar_em(hd, d_desc, gs, status, s, launches))) return e;
-  {
+  if (R.leaves) {
+    // emulated form: Hbar on the tensor cores (when its per-parent S was allocated)
+    gs.rbase = M > 0 ? base(M - 1) : 0;
+    if ((em_parts & 1) && (e = launch_hbar_em(hd, d_desc, gs, status, s, launches, count(M - 1)))) return e;
+    gs.rbase = base(M);
     size_t sm = sizeof(double) * (MAXL * MAX_R_DEV + 3 * 128 + 2 * MAX_R_DEV + 32) + stg;
     if (emu) {   // (the emulated instance's FP64 tiles are 64 wide: its staging sized for them)
       sm += EM_STAGE_BYTES + sizeof(double) * 2 * KC * (64 + 2) - stg;
       if (sm < EM_SOLO_SMEM) sm = EM_SOLO_SMEM;
-      e = launch_leaf_adjoint<true>(tile, st.nreg[M], sm, s, d_desc, gs, slot_leaf, em_parts, status);
+      e = launch_leaf_adjoint<true>(tile, (int)count(M), sm, s, d_desc, gs, slot_leaf, em_parts, status);
     } else {
-      e = launch_leaf_adjoint<false>(tile, st.nreg[M], sm, s, d_desc, gs, slot_leaf, em_parts, status);
+      e = launch_leaf_adjoint<false>(tile, (int)count(M), sm, s, d_desc, gs, slot_leaf, em_parts, status);
     }
     if (e) return e;
     ++*launches;
+    // slots after the leaves': the emulated chain adjoint's, one per level-(M-1) region
+    const long slot_chain = slot_leaf + st.nreg[M];
+    gs.rbase = M > 0 ? base(M - 1) : 0;
+    if (em_parts & 2) {
+      if ((e = launch_chain_adjoint_em(hd, d_desc, gs, slot_chain, status, s, count(M - 1)))) return e;
+      ++*launches;
+    }
+    if (M > 0 && hd.sh.mixed == 2) {
+      if ((e = launch_leaf_partial_em(hd, d_desc, gs, status, s, count(M - 1)))) return e;
+      ++*launches;
+    } else if (M > 0) {
+      dim3 grid((unsigned)count(M - 1), M * (M + 1) / 2);
+      MRA_GRAD_LAUNCH(tile, leaf_partial_kernel, grid, stg, s, d_desc, gs);
+      ++*launches;
+    }
   }
-  // slots after the leaves': the emulated chain adjoint's, one per level-(M-1) region
-  const long slot_chain = slot_leaf + st.nreg[M];
-  if (em_parts & 2) {
-    if ((e = launch_chain_adjoint_em(hd, d_desc, gs, slot_chain, status, s))) return e;
-    ++*launches;
-  }
-  if (M > 0 && hd.sh.mixed == 2) {
-    if ((e = launch_leaf_partial_em(hd, d_desc, gs, status, s))) return e;
-    ++*launches;
-  } else if (M > 0) {
-    dim3 grid(st.nreg[M - 1], M * (M + 1) / 2);
-    MRA_GRAD_LAUNCH(tile, leaf_partial_kernel, grid, stg, s, d_desc, gs);
-    ++*launches;
-  }
-  long slot = slot_leaf;
-  for (int m = M - 1; m >= 0; --m) {
-    slot -= st.nreg[m];
+  for (int m = prior_hi - 1; m >= R.prior_lo; --m) {
+    if (count(m) == 0) continue;
+    gs.rbase = base(m);
+    const long slot = slot_of_level(st, m);
     const size_t sm = sizeof(double) * (4 * MAX_R_DEV + 32) + sq;
-    if (emu) e = launch_prior_adjoint<true>(tile, m, st.nreg[m], std::max(sm + EM_STAGE_BYTES, EM_SOLO_SMEM), s,
+    if (emu) e = launch_prior_adjoint<true>(tile, m, (int)count(m), std::max(sm + EM_STAGE_BYTES, EM_SOLO_SMEM), s,
                                             d_desc, gs, slot, status);
-    else e = launch_prior_adjoint<false>(tile, m, st.nreg[m], sm + stg, s, d_desc, gs, slot, status);
+    else e = launch_prior_adjoint<false>(tile, m, (int)count(m), sm + stg, s, d_desc, gs, slot, status);
     if (e) return e;
     ++*launches;
   }
-  grad_reduce_kernel<<<1, NT, 0, s>>>(gs.gpart, slot_chain + ((em_parts & 2) ? st.nreg[M - 1] : 0), grad_out_dev);
-  ++*launches;
-  tm->stop(s);
   return cudaGetLastError();
+}
+
+cudaError_t launch_grad_reduce(const Desc& hd, const GradState& gs, double* grad_out_dev, cudaStream_t s,
+                               int64_t* launches) {
+  const int M = hd.sh.M;
+  const bool emu = hd.sh.mixed == 2 && M > 0;
+  const long nslots = slot_of_level(hd.st, M) + hd.st.nreg[M] + (emu ? hd.st.nreg[M - 1] : 0);
+  grad_reduce_kernel<<<1, NT, 0, s>>>(gs.gpart, nslots, grad_out_dev);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs, double* grad_out_dev, int* status,
+                        cudaStream_t s, int64_t* launches, Timer* tm) {
+  GradRange all;
+  tm->start(6, s);
+  cudaError_t e = launch_grad_range(hd, d_desc, gs, all, status, s, launches);
+  if (!e) e = launch_grad_reduce(hd, gs, grad_out_dev, s, launches);
+  tm->stop(s);
+  return e;
 }
 
 }  // namespace mra

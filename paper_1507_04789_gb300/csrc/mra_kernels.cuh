@@ -123,6 +123,9 @@ struct GradState {
   // scales of its rows per 128-column group, for the leaves' Hbar = 2 H S
   double* SF;
   int32_t* SFexp;       // [region][group][M r]
+  // first compact region id of the launch (block b works on region rbase + b);
+  // 0 except for the chunks of a streamed gradient
+  long rbase;
 };
 
 // Symmetric adjoint block (k, l) of region chain `anc` (ancestor index per

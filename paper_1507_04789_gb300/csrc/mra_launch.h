@@ -107,21 +107,36 @@ cudaError_t launch_simulate(const Desc* d_desc, int M, const PredState& ps, int6
 // Reverse-mode gradient after a forward pass that saved L, Lt, V_F and L_Sigma.
 cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs, double* grad_out_dev, int* status,
                         cudaStream_t s, int64_t* launches, Timer* tm);
+// A part of the reverse pass (a streamed gradient runs it in three): posterior
+// adjoint levels [post_lo, post_hi) top-down, the leaves' adjoints, prior
+// adjoint levels [prior_lo, prior_hi) bottom-up; per level the regions
+// [base, base + count) (count < 0: every region of the level); hi < 0 means M.
+struct GradRange {
+  int post_lo = 0, post_hi = -1, prior_lo = 0, prior_hi = -1;
+  bool leaves = true;
+  long base[MAXL] = {}, count[MAXL] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+};
+cudaError_t launch_grad_range(const Desc& hd, const Desc* d_desc, GradState gs, const GradRange& R, int* status,
+                              cudaStream_t s, int64_t* launches);
+// Sum of every CTA's partial gradient into grad_out_dev[0..GP).
+cudaError_t launch_grad_reduce(const Desc& hd, const GradState& gs, double* grad_out_dev, cudaStream_t s,
+                               int64_t* launches);
 // Emulated form: Hbar = 2 H S + z omegabar' of every leaf on the tensor cores
 // (mra_mixed.cu), from the assembled per-parent S of GradState.
 // Emulated form: the leaves' partial ancestor adjoints (leaf_partial_kernel's tiles).
+// (nregions < 0: every level-(M-1) region; else that many from gs.rbase)
 cudaError_t launch_leaf_partial_em(const Desc& hd, const Desc* d_desc, const GradState& gs, int* status,
-                                   cudaStream_t s);
+                                   cudaStream_t s, long nregions = -1);
 // Emulated form: the leaves' chain adjoint (Xbar and the Vbar updates), per parent;
 // its C0 terms go to gradient slots slot0 .. slot0 + nreg[M-1] - 1.
 cudaError_t launch_chain_adjoint_em(const Desc& hd, const Desc* d_desc, const GradState& gs, long slot0,
-                                    int* status, cudaStream_t s);
+                                    int* status, cudaStream_t s, long nregions = -1);
 // Emulated form: Gbar of level m (1 <= m < M) per level-(m-1) region, from its
 // assembled S (mra_mixed.cu); post_adjoint_kernel then skips its own product.
 cudaError_t launch_gbar_em(int m, const Desc& hd, const Desc* d_desc, const GradState& gs, int* status,
-                           cudaStream_t s, int64_t* launches);
+                           cudaStream_t s, int64_t* launches, long nregions = -1);
 cudaError_t launch_hbar_em(const Desc& hd, const Desc* d_desc, const GradState& gs, int* status, cudaStream_t s,
-                           int64_t* launches);
+                           int64_t* launches, long nregions = -1);
 
 // Identity tables of a complete tree with M levels (for callers without host tables).
 cudaError_t launch_identity_tree(const LevelState& st, int M, cudaStream_t s, int64_t* launches);

@@ -821,7 +821,7 @@ __global__ void __launch_bounds__(NT) s_full_kernel(int L, const Desc* __restric
   const int M = L + 1, r = ds.sh.r, Mr = M * r, ng = (Mr + EM_KG - 1) / EM_KG;
   int* sexp = reinterpret_cast<int*>(tile + r * (r + 1));   // [group][row] exponents
   const LevelState& st = ds.st;
-  const long p = blockIdx.x;
+  const long p = gs.rbase + blockIdx.x;
   const int lane = threadIdx.x & 31;
   long anc[MAXL];
   for (int l = 0; l < M; ++l) anc[l] = ancestor(st, L, p, l);
@@ -869,8 +869,8 @@ __global__ void __launch_bounds__(NT) hbar_kernel_em(const Desc* __restrict__ D,
   const int M = ds.sh.M, r = ds.sh.r, Mr = M * r, ng = (Mr + EM_KG - 1) / EM_KG;
   const LevelState& st = ds.st;
   const LeafState& lf = ds.lf;
-  const long p = blockIdx.x / M;               // the M column blocks of one region run together
-  const int l = (int)(blockIdx.x - p * M);
+  const long p = gs.rbase + blockIdx.x / M;    // the M column blocks of one region run together
+  const int l = (int)(blockIdx.x % M);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long pm = st.mort[M - 1][p];
   const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
@@ -932,9 +932,9 @@ __global__ void __launch_bounds__(NT) leaf_partial_kernel_em(const Desc* __restr
   const int M = ds.sh.M, r = ds.sh.r, Mr = M * r, T = M * (M + 1) / 2;
   const LeafState& lf = ds.lf;
   const int nt = partial_tiles(M, em_stack(r));
-  const long p = blockIdx.x / nt;
+  const long p = gs.rbase + blockIdx.x / nt;
   int k, l0, nl;
-  if (!partial_tile((int)(blockIdx.x - p * nt), M, em_stack(r), k, l0, nl)) return;
+  if (!partial_tile((int)(blockIdx.x % nt), M, em_stack(r), k, l0, nl)) return;
   const bool diag = l0 == k;
   const long pm = ds.st.mort[M - 1][p];
   const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
@@ -964,9 +964,9 @@ __global__ void __launch_bounds__(NT) leaf_partial_kernel_em(const Desc* __restr
 }
 
 cudaError_t launch_leaf_partial_em(const Desc& hd, const Desc* d_desc, const GradState& gs, int* status,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, long nregions) {
   const int M = hd.sh.M, r = hd.sh.r;
-  const int np = hd.st.nreg[M - 1];
+  const int np = nregions < 0 ? hd.st.nreg[M - 1] : (int)nregions;
   if (np == 0) return cudaSuccess;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(leaf_partial_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
@@ -999,7 +999,7 @@ __global__ void __launch_bounds__(NT) chain_adjoint_kernel_em(const Desc* __rest
   const int M = sh.M, r = sh.r, Mr = M * r;
   const LevelState& st = ds.st;
   const LeafState& lf = ds.lf;
-  const long p = blockIdx.x;
+  const long p = gs.rbase + blockIdx.x;
   const long pm = st.mort[M - 1][p];
   const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
   Engine<true> eng;
@@ -1108,9 +1108,9 @@ __global__ void __launch_bounds__(NT) chain_adjoint_kernel_em(const Desc* __rest
 }
 
 cudaError_t launch_chain_adjoint_em(const Desc& hd, const Desc* d_desc, const GradState& gs, long slot0,
-                                    int* status, cudaStream_t s) {
+                                    int* status, cudaStream_t s, long nregions) {
   const int M = hd.sh.M;
-  const int np = hd.st.nreg[M - 1];
+  const int np = nregions < 0 ? hd.st.nreg[M - 1] : (int)nregions;
   if (np == 0) return cudaSuccess;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(chain_adjoint_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
@@ -1119,23 +1119,24 @@ cudaError_t launch_chain_adjoint_em(const Desc& hd, const Desc* d_desc, const Gr
   return cudaGetLastError();
 }
 
-// St of every region of level L into gs.SF / gs.SFexp.
-static cudaError_t launch_s_full(int L, const Desc& hd, const Desc* d_desc, const GradState& gs, cudaStream_t s) {
+// St of the regions [gs.rbase, gs.rbase + n) of level L into gs.SF / gs.SFexp.
+static cudaError_t launch_s_full(int L, const Desc& hd, const Desc* d_desc, const GradState& gs, cudaStream_t s,
+                                 int n) {
   const int r = hd.sh.r, Mr = (L + 1) * r;
   const size_t sm = sizeof(double) * r * (r + 1) + sizeof(int) * ((Mr + EM_KG - 1) / EM_KG) * Mr;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(s_full_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-  s_full_kernel<<<hd.st.nreg[L], NT, sm, s>>>(L, d_desc, gs);
+  s_full_kernel<<<n, NT, sm, s>>>(L, d_desc, gs);
   return cudaGetLastError();
 }
 
 cudaError_t launch_hbar_em(const Desc& hd, const Desc* d_desc, const GradState& gs, int* status, cudaStream_t s,
-                           int64_t* launches) {
+                           int64_t* launches, long nregions) {
   const int M = hd.sh.M;
-  const int np = hd.st.nreg[M - 1];
+  const int np = nregions < 0 ? hd.st.nreg[M - 1] : (int)nregions;
   if (np == 0) return cudaSuccess;
   cudaError_t e;
-  if ((e = launch_s_full(M - 1, hd, d_desc, gs, s))) return e;
+  if ((e = launch_s_full(M - 1, hd, d_desc, gs, s, np))) return e;
   if ((e = cudaFuncSetAttribute(hbar_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM))) return e;
   hbar_kernel_em<<<np * M, NT, EM_SOLO_SMEM, s>>>(d_desc, gs, status);
   *launches += 2;
@@ -1157,8 +1158,8 @@ __global__ void __launch_bounds__(NT) gbar_kernel_em(int m, const Desc* __restri
   const Desc& ds = D[0];
   const int r = ds.sh.r, mr = m * r, ng = (mr + EM_KG - 1) / EM_KG;
   const LevelState& st = ds.st;
-  const long P = blockIdx.x / m;               // the m column blocks of one region run together
-  const int l = (int)(blockIdx.x - P * m);
+  const long P = gs.rbase + blockIdx.x / m;    // the m column blocks of one region run together
+  const int l = (int)(blockIdx.x % m);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long row0 = (long)st.cfirst[m - 1][P] * r, row1 = row0 + (long)st.ccnt[m - 1][P] * r;
   const long al = ancestor(st, m - 1, P, l);
@@ -1197,11 +1198,11 @@ __global__ void __launch_bounds__(NT) gbar_kernel_em(int m, const Desc* __restri
 }
 
 cudaError_t launch_gbar_em(int m, const Desc& hd, const Desc* d_desc, const GradState& gs, int* status,
-                           cudaStream_t s, int64_t* launches) {
-  const int np = hd.st.nreg[m - 1];
+                           cudaStream_t s, int64_t* launches, long nregions) {
+  const int np = nregions < 0 ? hd.st.nreg[m - 1] : (int)nregions;
   if (np == 0) return cudaSuccess;
   cudaError_t e;
-  if ((e = launch_s_full(m - 1, hd, d_desc, gs, s))) return e;
+  if ((e = launch_s_full(m - 1, hd, d_desc, gs, s, np))) return e;
   if ((e = cudaFuncSetAttribute(gbar_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM))) return e;
   gbar_kernel_em<<<np * m, NT, EM_SOLO_SMEM, s>>>(m, d_desc, gs, status);
   *launches += 2;
