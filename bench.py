@@ -629,7 +629,8 @@ def run_sharded(args, rank, world, local, mra, np, torch):
 def run_large(args, mra, np, torch):
     """The n = 2^24 swath field (M = 10, r = 64, complete tree): the log-likelihood
     evaluated as streamed level-s subtrees in the emulated form, then kriging at
-    the 2^20 cell-centred grid points; device memory is sampled after every call."""
+    the 2^20 cell-centred grid points and one log-likelihood + gradient call;
+    device memory is sampled after every call."""
     from paper_1507_04789_gb300 import synth
     w = synth.workload(args.workload)
     t0 = time.perf_counter()
@@ -682,6 +683,17 @@ def run_large(args, mra, np, torch):
     torch.cuda.synchronize()
     pred_ms = p0.elapsed_time(p1)
     sample()
+    # loglik + gradient on the streamed handle: each chunk's factors formed again before its adjoint
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    g0.record(stream)
+    ll_g, grad = h.loglik_grad(theta0)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    grad_ms = g0.elapsed_time(g1)
+    sample()
+    ll0 = h.loglik(theta0)
     off = h.leaf_offsets()
     nF = np.diff(off)
     h.close()
@@ -700,7 +712,12 @@ def run_large(args, mra, np, torch):
                        "what": "each chunk's factors formed again from the resident coarse levels, then its "
                                "points predicted (about one more evaluation)",
                        "var_min": float(var.min().item()), "var_max": float(var.max().item())},
-        "generate_s": gen_s, "build_s": build_s, "clocks": clocks, "gradient": "not available on a streamed handle",
+        "generate_s": gen_s, "build_s": build_s, "clocks": clocks,
+        "gradient": {"ms_per_call": grad_ms, "evals_per_s": 1e3 / grad_ms, "grad": [float(v) for v in grad],
+                     "loglik": ll_g, "loglik_rel_diff_vs_plain_eval": abs(ll_g - ll0) / abs(ll0),
+                     "what": "loglik + d/d(sigma2, range, tau2) in the emulated form, streamed: the forward "
+                             "evaluation, the coarse posterior adjoint, per chunk its factors formed again "
+                             "(the last one reused) and its adjoints, then the coarse prior adjoint"},
         "per_level": [{"level": m, "stage": k, "ms_per_step": v["ms"] / max(1, st["evaluations"]),
                        "flops": v["flops"]} for m, row in enumerate(st["levels"]) for k, v in row.items()],
     }
@@ -719,8 +736,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-dataset swath batch")
     ap.add_argument("--batch-datasets", type=int, default=64)
-    ap.add_argument("--stream-level", type=int, default=2,
-                    help="level of the streamed subtrees for the n = 2^24 swath workload")
+    ap.add_argument("--stream-level", type=int, default=3,
+                    help="level of the streamed subtrees for the n = 2^24 swath workload (3: 64 subtrees, so "
+                         "that the gradient's chunk buffers keep the run within 180 GB)")
     ap.add_argument("--grad-only", action="store_true",
                     help="time only loglik + gradient in the emulated form (the launch list of the gradient)")
     args = ap.parse_args()

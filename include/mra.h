@@ -99,9 +99,13 @@ typedef struct {
                            mra_build stream, at the smallest s that fits, only when the
                            factors of every level would exceed 80 % of the free device
                            memory; -1 never streams.  A streamed handle evaluates
-                           mra_loglik (and mra_region_terms, mra_stats) and mra_predict (which
+                           mra_loglik (and mra_region_terms, mra_stats), mra_predict (which
                            forms each chunk's factors again from the resident coarse ones,
-                           about one more evaluation); mra_loglik_grad, mra_predict_joint,
+                           about one more evaluation) and mra_loglik_grad (each chunk's
+                           factors formed again before its adjoint, the last chunk's
+                           reused: about one more forward evaluation; the adjoint state of
+                           levels > s is chunk-sized too, and the emulated form's optional
+                           gradient buffers are not taken); mra_predict_joint,
                            mra_simulate and mra_update return MRA_ERR_STATE. */
 } mra_config;
 

@@ -221,6 +221,8 @@ struct mra_handle {
   mra::Plan plan;
   double* pinned = nullptr;    // small pinned readback buffer
   int64_t ls_cap = 0;          // capacity of the ragged leaf-factor store (doubles)
+  int64_t obs_cap = 0;         // capacity of the per-observation leaf stores (rows)
+  std::vector<int64_t> cap;    // storage of every level in regions (levels > s: one chunk's)
   // subtree streaming (cfg.stream_level): level s, its chunks, their plans and
   // descriptors (d_desc holds one per chunk; levels <= s are shared by all)
   int s_lvl = 0;
@@ -376,7 +378,15 @@ cudaError_t upload_desc(mra_handle* h, const mra_params* theta) {
       D.st.vexp[m] = shift(D.st.vexp[m], i0, ((m * r + 127) / 128) * r);
       D.st.gcol[m] = shift(D.st.gcol[m], i0, m * r);
       D.st.liexp[m] = shift(D.st.liexp[m], i0, r);
+      D.st.L[m] = shift(D.st.L[m], i0, r * r);        // (saved for the gradient)
+      D.st.Ltf[m] = shift(D.st.Ltf[m], i0, r * r);
+      D.st.licol[m] = shift(D.st.licol[m], i0, r);
+      D.st.vcol[m] = shift(D.st.vcol[m], i0, m * r);
     }
+    D.lf.VF = shift(D.lf.VF, c.obs0, Mr);
+    D.lf.LSf = shift(D.lf.LSf, c.ls0, 1);
+    D.lf.dc = shift(D.lf.dc, c.obs0, 2 * Mr);
+    if (M - 1 > s) D.lf.vfexp = shift(D.lf.vfexp, c.c0[M - 1], 4 * Mr);
     D.lf.H = shift(D.lf.H, c.obs0, Mr);
     D.lf.z = shift(D.lf.z, c.obs0, 1);
     D.lf.LS = shift(D.lf.LS, c.ls0, 1);
@@ -700,6 +710,8 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
     B.want(&d_work, std::max<size_t>(work.size(), 1));
   }
   h->ls_cap = ls_cap;
+  h->obs_cap = obs_cap;
+  h->cap = cap;
   if ((e = B.commit())) { mra_free(h); return fail(MRA_ERR_OOM, "device allocation (factors): %s", cudaGetErrorString(e)); }
   for (int m = 0; m <= M; ++m) {
     if ((e = cudaMemcpyAsync(h->st.mort[m], h->tab.mort[m].data(), sizeof(int32_t) * nreg[m], cudaMemcpyHostToDevice, h->stream)) ||
@@ -1029,8 +1041,15 @@ static int ensure_grad_arena(mra_handle* h) {
   const int64_t n = h->n;
   const std::vector<int32_t>& nreg = h->tab.nreg;
   Arena& G = h->grad;
+  // Streamed handles (stream level s): the levels > s and the leaf stores hold
+  // one chunk at a time, as the forward factors do; the ancestor adjoints that
+  // level s+1 passes up and the leaves' partials of a level-s parent are read
+  // by the coarse adjoint after every chunk, so they stay whole.
+  const int s = h->s_lvl;
+  auto rcap = [&](int m) -> int64_t { return s && m > s ? h->cap[m] : (int64_t)nreg[m]; };
+  const int64_t nobs = s ? h->obs_cap : n;
   for (int m = 0; m < M; ++m) {
-    const int64_t R = nreg[m];
+    const int64_t R = rcap(m);
     G.want(&h->st.L[m], R * r * r);
     G.want(&h->st.Ltf[m], R * r * r);
     G.want(&h->gs.Abar[m], R * r * (int64_t)(m + 1) * r);
@@ -1038,28 +1057,28 @@ static int ensure_grad_arena(mra_handle* h) {
     G.want(&h->gs.GB[m], R * r * (int64_t)m * r);
     G.want(&h->gs.VB[m], R * r * (int64_t)m * r);
     G.want(&h->gs.XB[m], R * r * (int64_t)m * r);
-    G.want(&h->gs.Up[m], R * (int64_t)m * (m + 1) / 2 * r * r);
+    G.want(&h->gs.Up[m], (m == s + 1 ? (int64_t)nreg[m] : R) * (int64_t)m * (m + 1) / 2 * r * r);
     h->st.licol[m] = h->st.vcol[m] = nullptr;
     if (h->cfg.precision == MRA_PREC_EMU) {
       G.want(&h->st.licol[m], R * r);
       if (m > 0) G.want(&h->st.vcol[m], R * (int64_t)m * r);
     }
   }
-  if (M > 0) G.want(&h->gs.PartLeaf, (int64_t)nreg[M - 1] * M * (M + 1) / 2 * r * r);
+  if (M > 0) G.want(&h->gs.PartLeaf, rcap(M - 1) * M * (M + 1) / 2 * r * r);
   h->gs.SF = nullptr;
   h->gs.SFexp = nullptr;
   h->gs.DC = nullptr;
   h->gs.VFexp = h->gs.VBexp = h->gs.XBexp = nullptr;
-  G.want(&h->lf.VF, n * (int64_t)M * r);
+  G.want(&h->lf.VF, nobs * (int64_t)M * r);
   G.want(&h->lf.LSf, (size_t)h->ls_cap);
-  G.want(&h->gs.HB, n * (int64_t)M * r);
+  G.want(&h->gs.HB, nobs * (int64_t)M * r);
   if (h->cfg.precision == MRA_PREC_EMU && M > 0) {
-    G.want(&h->gs.VFexp, (int64_t)nreg[M - 1] * 4 * M * r);
-    G.want(&h->gs.VBexp, (int64_t)nreg[M - 1] * 4 * M * r);
-    G.want(&h->gs.XBexp, (int64_t)nreg[M - 1] * 4 * M * r);
+    G.want(&h->gs.VFexp, rcap(M - 1) * 4 * M * r);
+    G.want(&h->gs.VBexp, rcap(M - 1) * 4 * M * r);
+    G.want(&h->gs.XBexp, rcap(M - 1) * 4 * M * r);
   }
-  G.want(&h->gs.VBF, n * (int64_t)M * r);
-  G.want(&h->gs.XBF, n * (int64_t)M * r);
+  G.want(&h->gs.VBF, nobs * (int64_t)M * r);
+  G.want(&h->gs.XBF, nobs * (int64_t)M * r);
   G.want(&h->gs.T, 3 * (size_t)h->ls_cap);
   int64_t slots = 0;
   for (int m = 0; m <= M; ++m) slots += nreg[m];
@@ -1071,7 +1090,8 @@ static int ensure_grad_arena(mra_handle* h) {
   // cores, when it is also at most four times the size of H (else the FP64
   // kernels form Hbar and Gbar from the ancestors' blocks), then the chain's
   // covariance derivative pairs (else the chain adjoint evaluates them).
-  if (M > 0 && h->cfg.precision == MRA_PREC_EMU && h->grad_buffers) {
+  // Streamed handles take neither.
+  if (M > 0 && h->cfg.precision == MRA_PREC_EMU && h->grad_buffers && !s) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
       fr = 0;
@@ -1111,11 +1131,102 @@ static int ensure_grad_arena(mra_handle* h) {
   return MRA_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Adjoint state of one chunk of a streamed handle: the arrays of levels > s
+// and the per-observation and ragged leaf stores point at (buffer - first id x
+// stride), as the chunk's descriptor does for the forward factors.
+template <class T>
+T* shifted(T* p, int64_t first, int64_t stride) {
+  return p ? reinterpret_cast<T*>(reinterpret_cast<uintptr_t>(p) - (uintptr_t)(first * stride * (int64_t)sizeof(T)))
+           : p;
+}
+
+mra::GradState chunk_grad_state(const mra_handle* h, const Chunk& c) {
+  const int M = h->M, s = h->s_lvl;
+  const int64_t r = h->r, Mr = (int64_t)M * r;
+  mra::GradState g = h->gs;
+  for (int m = s + 1; m < M; ++m) {
+    const int64_t i0 = c.c0[m];
+    g.Abar[m] = shifted(g.Abar[m], i0, r * (m + 1) * r);
+    g.Obar[m] = shifted(g.Obar[m], i0, r);
+    g.GB[m] = shifted(g.GB[m], i0, r * m * r);
+    g.VB[m] = shifted(g.VB[m], i0, r * m * r);
+    g.XB[m] = shifted(g.XB[m], i0, r * m * r);
+    if (m > s + 1) g.Up[m] = shifted(g.Up[m], i0, (int64_t)m * (m + 1) / 2 * r * r);
+  }
+  if (M - 1 > s) {
+    const int64_t p0 = c.c0[M - 1];
+    g.PartLeaf = shifted(g.PartLeaf, p0, (int64_t)M * (M + 1) / 2 * r * r);
+    g.VFexp = shifted(g.VFexp, p0, 4 * Mr);
+    g.VBexp = shifted(g.VBexp, p0, 4 * Mr);
+    g.XBexp = shifted(g.XBexp, p0, 4 * Mr);
+  }
+  g.HB = shifted(g.HB, c.obs0, Mr);
+  g.VBF = shifted(g.VBF, c.obs0, Mr);
+  g.XBF = shifted(g.XBF, c.obs0, Mr);
+  g.T = shifted(g.T, c.ls0, 3);
+  return g;
+}
+
+// Reverse pass of a streamed handle, after its forward evaluation: the
+// posterior adjoint of the coarse levels 0..s, then per chunk (last first: the
+// last chunk's forward factors are still resident, the others' are recomputed
+// from the coarse levels, which stay whole) the posterior adjoint of its levels
+// > s, its leaves' adjoints and its prior adjoint up to level s+1, and last the
+// prior adjoint of the coarse levels s..0.
+cudaError_t streamed_grad(mra_handle* h) {
+  const int M = h->M, s = h->s_lvl;
+  cudaError_t e;
+  mra::GradRange coarse_post;
+  coarse_post.post_hi = s + 1;
+  coarse_post.leaves = false;
+  coarse_post.prior_hi = 0;
+  coarse_post.cs_lo = 0;                 // (the column scales of levels <= s serve every chunk)
+  coarse_post.cs_hi = s + 1;
+  h->timer.start(6, h->stream);
+  e = mra::launch_grad_range(h->hd, h->d_desc, h->gs, coarse_post, h->status, h->stream, &g_launches);
+  h->timer.stop(h->stream);
+  if (e) return e;
+  for (size_t k = h->chunks.size(); k-- > 0;) {
+    const Chunk& c = h->chunks[k];
+    if (k + 1 < h->chunks.size() &&
+        (e = mra::launch_loglik(c.plan, h->d_desc, h->status, h->stream, &g_launches, &h->timer)))
+      return e;
+    mra::GradRange R;
+    R.post_lo = R.prior_lo = s + 1;
+    for (int m = s; m <= M; ++m) {
+      R.base[m] = c.c0[m];
+      R.count[m] = c.c1[m] - c.c0[m];
+    }
+    h->timer.start(6, h->stream);
+    e = mra::launch_grad_range(h->chunk_descs[k], h->d_desc + k, chunk_grad_state(h, c), R, h->status, h->stream,
+                               &g_launches);
+    h->timer.stop(h->stream);
+    if (e) return e;
+  }
+  mra::GradRange coarse_prior;
+  coarse_prior.post_hi = 0;
+  coarse_prior.leaves = false;
+  coarse_prior.prior_hi = s + 1;
+  coarse_prior.cs_lo = coarse_prior.cs_hi = 0;
+  h->timer.start(6, h->stream);
+  e = mra::launch_grad_range(h->hd, h->d_desc, h->gs, coarse_prior, h->status, h->stream, &g_launches);
+  if (!e) e = mra::launch_grad_reduce(h->hd, h->gs, h->d_grad, h->stream, &g_launches);
+  h->timer.stop(h->stream);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
 int mra_loglik_grad(mra_handle* h, const mra_params* theta, double* loglik_out, double* grad_out) {
   g_err.clear();
   if (!h || !loglik_out || !grad_out) return fail(MRA_ERR_ARG, "null argument");
   if (!h->parts.empty()) return fail(MRA_ERR_STATE, "not available on a batch handle");
-  if (h->s_lvl) return fail(MRA_ERR_STATE, "the gradient is not available on a streamed handle (stream_level %d)", h->s_lvl);
   if (!params_ok(theta) || !nu_ok(h->cfg.cov_family, theta)) return fail(MRA_ERR_ARG, "theta needs sigma2 > 0, range > 0, tau2 >= 0 (and 0.05 <= nu <= 20 for MRA_COV_MATERN), all finite");
   int rc = ensure_grad_arena(h);
   if (rc) return rc;
@@ -1128,10 +1239,10 @@ int mra_loglik_grad(mra_handle* h, const mra_params* theta, double* loglik_out, 
   h->lf.vfexp = nullptr;
   if (e || (e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream)))
     return cuda_fail(e, "descriptor");
-  if ((e = mra::launch_loglik(h->plan, h->d_desc, h->status, h->stream, &g_launches, &h->timer)))
-    return cuda_fail(e, "loglik launch");
-  if ((e = mra::launch_grad(h->hd, h->d_desc, h->gs, h->d_grad, h->status, h->stream, &g_launches, &h->timer)))
-    return cuda_fail(e, "gradient launch");
+  if ((e = launch_evaluation(h))) return cuda_fail(e, "loglik launch");
+  if (h->s_lvl) e = streamed_grad(h);
+  else e = mra::launch_grad(h->hd, h->d_desc, h->gs, h->d_grad, h->status, h->stream, &g_launches, &h->timer);
+  if (e) return cuda_fail(e, "gradient launch");
   int hs[4];
   double vals[6];
   const double* srcs[6];

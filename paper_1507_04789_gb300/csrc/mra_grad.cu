@@ -1037,7 +1037,9 @@ cudaError_t launch_grad_range(const Desc& hd, const Desc* d_desc, GradState gs, 
   const long slot_leaf = slot_of_level(st, M);
   const bool emu = hd.sh.mixed == 2 && M > 0;
   if (emu && st.licol[0]) {   // column scales of L^{-1} and V for the emulated chain adjoints
-    for (int m = R.prior_lo; m < prior_hi; ++m) {
+    const int cs_lo = R.cs_lo < 0 ? R.prior_lo : R.cs_lo;
+    const int cs_hi = R.cs_lo < 0 ? prior_hi : (R.cs_hi < 0 ? M : R.cs_hi);
+    for (int m = cs_lo; m < cs_hi; ++m) {
       if (count(m) == 0) continue;
       col_scales_kernel<<<(unsigned)count(m), NT, 0, s>>>(m, d_desc, base(m));
       ++*launches;

@@ -111,8 +111,12 @@ cudaError_t launch_grad(const Desc& hd, const Desc* d_desc, const GradState& gs,
 // adjoint levels [post_lo, post_hi) top-down, the leaves' adjoints, prior
 // adjoint levels [prior_lo, prior_hi) bottom-up; per level the regions
 // [base, base + count) (count < 0: every region of the level); hi < 0 means M.
+// The emulated form's column scales of L^{-1} and V (read by the leaves' and
+// the prior levels' adjoints) are formed for levels [cs_lo, cs_hi), by default
+// (cs_lo < 0) the prior adjoint's levels.
 struct GradRange {
   int post_lo = 0, post_hi = -1, prior_lo = 0, prior_hi = -1;
+  int cs_lo = -1, cs_hi = -1;
   bool leaves = true;
   long base[MAXL] = {}, count[MAXL] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
 };

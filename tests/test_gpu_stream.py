@@ -38,6 +38,41 @@ def test_streamed_equals_whole_tree(mra, precision):
             assert hs.loglik((theta[0], theta[1] * 1.1, theta[2])) != lls   # a new theta is evaluated
 
 
+@pytest.mark.parametrize("precision", ["fp64", "emu"])
+def test_streamed_gradient_equals_whole_tree(mra, precision):
+    """The streamed reverse pass (coarse posterior adjoint, then per chunk its
+    factors formed again and its levels' adjoints, then the coarse prior
+    adjoint) gives the whole-tree gradient, at every stream level."""
+    w = synth.workload("n16k_matern15_M4_r64")
+    locs, y, _ = w.generate()
+    theta = (w.sigma2, w.kappa, w.tau2)
+    with mra.Handle(locs, y, M=w.M, r=w.r, family=w.family, precision=precision, stream_level=-1) as h:
+        ll, g = h.loglik_grad(theta)
+    for s in (1, 2, 3):
+        with mra.Handle(locs, y, M=w.M, r=w.r, family=w.family, precision=precision, stream_level=s) as hs:
+            lls, gs = hs.loglik_grad(theta)
+            assert lls == pytest.approx(ll, rel=1e-13), s
+            np.testing.assert_allclose(gs, g, rtol=1e-11, atol=1e-11 * np.abs(g).max(), err_msg=f"s={s}")
+            # a plain evaluation and a second gradient on the same handle agree
+            assert hs.loglik(theta) == pytest.approx(ll, rel=1e-13)
+            lls2, gs2 = hs.loglik_grad(theta)
+            np.testing.assert_allclose(gs2, gs, rtol=1e-13, atol=0)
+
+
+def test_streamed_gradient_pruned_swath_matches_oracle(mra):
+    """Streamed gradient on a pruned swath tree against the oracle's gradient."""
+    from paper_1507_04789_gb300 import plan
+    data = synth.swath_batch(1, seed=31, n_min=6e3, n_max=8e3)[0]
+    locs, y = data["locs"], data["y"]
+    theta = (1.0, data["kappa"], data["tau2"])
+    M = plan.choose_levels(locs, 64)
+    g_o = O.loglik_grad(O.Problem(locs, y, M=M, r=16, family="exp"), theta)[1]
+    for precision in ("fp64", "emu"):
+        with mra.Handle(locs, y, M=M, r=16, family="exp", precision=precision, prune=True, stream_level=2) as h:
+            g = h.loglik_grad(theta)[1]
+        np.testing.assert_allclose(g, g_o, rtol=1e-8, atol=1e-8 * np.abs(g_o).max(), err_msg=precision)
+
+
 def test_streamed_pruned_swath_matches_oracle(mra):
     from paper_1507_04789_gb300 import plan
     data = synth.swath_batch(1, seed=31, n_min=6e3, n_max=8e3)[0]
@@ -60,8 +95,7 @@ def test_streamed_handle_limits(mra):
     assert ei.value.code == mra.MRA_ERR_ARG
     with mra.Handle(locs, y, M=3, r=16, stream_level=1) as h:
         h.loglik((1.0, 0.1, 0.01))
-        for call in (lambda: h.loglik_grad((1.0, 0.1, 0.01)), lambda: h.predict_joint((1.0, 0.1, 0.01), locs[:10]),
-                     lambda: h.update(locs, y)):
+        for call in (lambda: h.predict_joint((1.0, 0.1, 0.01), locs[:10]), lambda: h.update(locs, y)):
             with pytest.raises(mra.MRAError) as ei:
                 call()
             assert ei.value.code == mra.MRA_ERR_STATE
