@@ -104,8 +104,8 @@ typedef struct {
                            about one more evaluation) and mra_loglik_grad (each chunk's
                            factors formed again before its adjoint, the last chunk's
                            reused: about one more forward evaluation; the adjoint state of
-                           levels > s is chunk-sized too, and the emulated form's optional
-                           gradient buffers are not taken); mra_predict_joint,
+                           levels > s and the emulated form's optional gradient buffers are
+                           chunk-sized too); mra_predict_joint,
                            mra_simulate and mra_update return MRA_ERR_STATE. */
 } mra_config;
 

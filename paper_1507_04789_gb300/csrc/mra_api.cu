@@ -1089,9 +1089,10 @@ static int ensure_grad_arena(mra_handle* h) {
   // without them): the per-parent adjoint S for Hbar and Gbar on the tensor
   // cores, when it is also at most four times the size of H (else the FP64
   // kernels form Hbar and Gbar from the ancestors' blocks), then the chain's
-  // covariance derivative pairs (else the chain adjoint evaluates them).
-  // Streamed handles take neither.
-  if (M > 0 && h->cfg.precision == MRA_PREC_EMU && h->grad_buffers && !s) {
+  // covariance derivative pairs (else the chain adjoint evaluates them).  On a
+  // streamed handle both are chunk-sized: S holds the parents of one launch
+  // (a chunk's, or a coarse level's), the pairs one chunk's observations.
+  if (M > 0 && h->cfg.precision == MRA_PREC_EMU && h->grad_buffers) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
       fr = 0;
@@ -1100,16 +1101,25 @@ static int ensure_grad_arena(mra_handle* h) {
     size_t base = 0;
     for (auto& q : G.plan) base += Arena::align(q.second);
     int64_t budget = (int64_t)(0.85 * (double)fr) - (int64_t)base;
-    const int64_t Mr = (int64_t)M * r, P = nreg[M - 1];
-    const int64_t sfe = P * ((Mr + 127) / 128) * Mr + 8;   // + the rows the engine rounds up to 8
-    const int64_t sf = (int64_t)Arena::align(8 * P * Mr * Mr) + (int64_t)Arena::align(4 * sfe);
-    if (P * Mr <= 4 * n && sf <= budget) {
-      G.want(&h->gs.SF, P * Mr * Mr);
+    const int64_t Mr = (int64_t)M * r;
+    // parents of one S launch at level L (Gbar of level L + 1, Hbar for L = M - 1)
+    auto parents = [&](int L) -> int64_t { return !s || L < s ? (int64_t)nreg[L] : (L == s ? 1 : h->cap[L]); };
+    int64_t sfd = 0, sfe = 0;
+    for (int L = 0; L < M; ++L) {
+      const int64_t w = (int64_t)(L + 1) * r;
+      sfd = std::max(sfd, parents(L) * w * w);
+      sfe = std::max(sfe, parents(L) * ((w + 127) / 128) * w);
+    }
+    sfe += 8;                                               // + the rows the engine rounds up to 8
+    const int64_t P = parents(M - 1);
+    const int64_t sf = (int64_t)Arena::align(8 * sfd) + (int64_t)Arena::align(4 * sfe);
+    if (P * Mr <= 4 * nobs && sf <= budget) {
+      G.want(&h->gs.SF, sfd);
       G.want(&h->gs.SFexp, sfe);
       budget -= sf;
     }
-    if ((int64_t)Arena::align(16 * n * Mr) <= budget && h->cfg.cov_family != MRA_COV_MATERN)
-      G.want(&h->gs.DC, 2 * n * Mr);   // (pairs d/dsigma2, d/dkappa: the free-smoothness family also needs d/dnu)
+    if ((int64_t)Arena::align(16 * nobs * Mr) <= budget && h->cfg.cov_family != MRA_COV_MATERN)
+      G.want(&h->gs.DC, 2 * nobs * Mr);   // (pairs d/dsigma2, d/dkappa: the free-smoothness family also needs d/dnu)
   }
   G.want(&h->d_grad, 4);
   cudaError_t e = G.commit();
@@ -1197,6 +1207,7 @@ cudaError_t streamed_grad(mra_handle* h) {
       return e;
     mra::GradRange R;
     R.post_lo = R.prior_lo = s + 1;
+    R.local_sf = true;
     for (int m = s; m <= M; ++m) {
       R.base[m] = c.c0[m];
       R.count[m] = c.c1[m] - c.c0[m];

@@ -226,6 +226,196 @@ __device__ __forceinline__ double cov0(const Cov& c, double x1, double y1, doubl
   return v;
 }
 
+// ---- C0 with few FP64 operations (families 0 and 1) -------------------------
+// GB300 retires about 2 FP64 FMA per clock per SM against 128 FP32 operations,
+// and the emulated form's kernels evaluate n M r covariances per evaluation,
+// so these form C0 from the squared scaled distance u = (s dx)^2 + (s dy)^2
+// (s = 1/kappa for the exponential, sqrt(3)/kappa for Matern-1.5) and a
+// variance factor sc with 8 (exponential) or 9 (Matern-1.5) FP64 operations,
+// the rest on the FP32 and integer pipes:
+//  * a = sqrt(u): an FP32 reciprocal square root corrected once in
+//    double-float arithmetic (Dekker, "A floating-point technique for
+//    extending the available precision", Numer. Math. 18, 1971), which is
+//    good to about 2^-44, then one FP64 Newton step;
+//  * e^{-a} = 2^{-m} 2^{-j/4096} e^{-r} with k = 4096 m + j the nearest
+//    integer to a 4096/ln2 (from the double-float seed), r = a - k ln2/4096 in
+//    FP64 with ln2/4096 split so that k C1 is exact (Cody & Waite), and
+//    e^{-r} - 1 = -r + r^2/2 - r^3/6 + r^4/24 in double-float (|r| <= 8.5e-5:
+//    truncation below 2^-70); 2^{-j/4096} from a 4096-entry table and 2^{-m}
+//    folded into sc through the exponent field.
+// Error within a few ulp of the exactly rounded value, plus a 2^-53 relative
+// (as for any evaluation from a rounded distance); a > 708 gives 0, as
+// exp_neg does.
+constexpr int C0_GMAX = 16;                    // knot-grid sides whose squared offsets the kernels tabulate
+
+constexpr long double exp2n_frac(int j, int den) {   // 2^{-j/den} by its Taylor series
+  long double x = -(long double)j / (long double)den * MRA_LN2L, term = 1.0L, sum = 1.0L;
+  for (int k = 1; k < 40; ++k) {
+    term *= x / (long double)k;
+    sum += term;
+  }
+  return sum;
+}
+struct C0Tab {
+  double v[4096];
+};
+constexpr C0Tab make_c0_tab() {              // 2^{-j/4096} = 2^{-(j>>6)/64} 2^{-(j&63)/4096}
+  C0Tab t{};
+  for (int j = 0; j < 4096; ++j) t.v[j] = (double)(exp2n_frac(j >> 6, 64) * exp2n_frac(j & 63, 4096));
+  return t;
+}
+static __device__ const C0Tab k_c0_tab = make_c0_tab();
+constexpr long double MRA_C0_L = MRA_LN2L / 4096.0L;
+constexpr double MRA_C0_C1 = (double)((long double)(long long)(MRA_C0_L * 8796093022208.0L) /
+                                      8796093022208.0L);          // ln2/4096 to 2^-43: k C1 exact for k < 2^22
+constexpr double MRA_C0_C2 = (double)(MRA_C0_L - (long double)MRA_C0_C1);
+constexpr float MRA_C0_I1 = (float)(1.0L / MRA_C0_L);                // 4096/ln2 as two floats
+constexpr float MRA_C0_I2 = (float)(1.0L / MRA_C0_L - (long double)MRA_C0_I1);
+
+__host__ __device__ inline uint64_t c0_dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return (uint64_t)__double_as_longlong(x);
+#else
+  uint64_t b;
+  memcpy(&b, &x, 8);
+  return b;
+#endif
+}
+__host__ __device__ inline double c0_bitsd(uint64_t b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  memcpy(&x, &b, 8);
+  return x;
+#endif
+}
+__host__ __device__ inline uint32_t c0_bitsf(float f) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(f);
+#else
+  uint32_t b;
+  memcpy(&b, &f, 4);
+  return b;
+#endif
+}
+__host__ __device__ inline float c0_fbits(uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float f;
+  memcpy(&f, &b, 4);
+  return f;
+#endif
+}
+// Exact float -> double by bit moves (0 for zero and subnormal floats).
+__host__ __device__ inline double c0_widen(float f) {
+  const uint32_t u = c0_bitsf(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0) return 0.0;
+  return c0_bitsd(((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
+                  ((uint64_t)(u & 0x7FFFFFu) << 29));
+}
+// x = hi + lo: hi the leading 24 bits of x, lo the other 29 rounded to 24, for
+// 2^-70 <= |x| < 2^127 (both 0 below).
+__host__ __device__ inline void c0_split(double x, float& hi, float& lo) {
+  const uint64_t b = c0_dbits(x);
+  const uint32_t h = (uint32_t)(b >> 32);
+  const int be = (int)((h >> 20) & 0x7FFu);
+  if (be < 953) {
+    hi = lo = 0.f;
+    return;
+  }
+  const uint32_t sg = h & 0x80000000u;
+  hi = c0_fbits(sg | ((uint32_t)(be - 896) << 23) | ((uint32_t)(b >> 29) & 0x7FFFFFu));
+  const float rem = (float)(uint32_t)(b & 0x1FFFFFFFu) * c0_fbits((uint32_t)(be - 948) << 23);   // x 2^(be-1075)
+  lo = sg ? -rem : rem;
+}
+
+// C0 (v), sc e^{-a} (e) and a = sqrt(u), from which the gradient's derivative
+// pairs follow: dC0/dsigma2 = v / sigma2, dC0/dkappa = e a / kappa
+// (exponential) or e a^2 / kappa (Matern-1.5).
+struct C0Val {
+  double v, e, a;
+};
+
+__host__ __device__ inline C0Val c0_eval(int family, double u, double sc) {
+  float uh, ul;
+  c0_split(u, uh, ul);
+  if (!(uh >= 0x1p-60f)) {                     // zero or tiny distance: the plain evaluation
+#ifdef __CUDA_ARCH__
+    const double a = u > 0.0 ? sqrt(u) : 0.0;
+    const double e = sc * exp_neg_tab(a, k_exp2_tab);
+#else
+    const double a = u > 0.0 ? std::sqrt(u) : 0.0;
+    const double e = sc * exp_neg_tab(a, k_exp2_tab_host);
+#endif
+    return C0Val{family == 0 ? e : fma(a, e, e), e, a};
+  }
+  if (uh > 501264.0f) return C0Val{0.0, 0.0, 708.0};   // a > 708
+#ifdef __CUDA_ARCH__
+  const float y = rsqrtf(uh);
+  const double* tab = k_c0_tab.v;
+#else
+  const float y = 1.0f / std::sqrt(uh);
+  static constexpr C0Tab tabh = make_c0_tab();
+  const double* tab = tabh.v;
+#endif
+  // a = sqrt(u): double-float seed (ah, al), then one FP64 Newton step
+  const float ah = uh * y, hy = 0.5f * y;
+  const float p = ah * ah, pe = fmaf(ah, ah, -p);
+  const float al = (((uh - p) - pe) + ul) * hy;
+  const double a0 = c0_widen(ah) + c0_widen(al);
+  const double a = fma(c0_widen(hy), fma(-a0, a0, u), a0);
+  // k = nearest integer to a 4096/ln2, from the seed in double-float
+  const float th = ah * MRA_C0_I1;
+  const float tl = fmaf(ah, MRA_C0_I1, -th) + fmaf(ah, MRA_C0_I2, al * MRA_C0_I1);
+  float kf = rintf(th);
+  const float fr = (th - kf) + tl;
+  kf += fr > 0.5f ? 1.0f : (fr < -0.5f ? -1.0f : 0.0f);
+  const int k = (int)kf;
+  const double kd = c0_widen(kf);
+  double rr = fma(kd, -MRA_C0_C1, a);
+  rr = fma(kd, -MRA_C0_C2, rr);
+  // g = e^{-r} - 1 = -r + r^2/2 - r^3/6 + r^4/24, r = rh + rl, as gh + gl
+  float rh, rl;
+  c0_split(rr, rh, rl);
+  const float p2 = rh * rh, e2 = fmaf(rh, rh, -p2);
+  const float hp = 0.5f * p2;
+  const float gh = hp - rh;                    // two-sum of -rh and hp
+  const float bb = gh - hp;
+  const float er = (hp - (gh - bb)) + (-rh - bb);
+  const float small = fmaf(0.5f, e2, fmaf(rh, rl, -rl)) + p2 * fmaf(p2, 1.0f / 24.0f, -rh * (1.0f / 6.0f));
+  const double gd = c0_widen(gh) + c0_widen(er + small);
+  // sc 2^{-m} by the exponent field (sc > 0 normal), then sc e^{-a}
+  const int j = k & 4095, m = k >> 12;
+  const uint64_t sb = c0_dbits(sc);
+  if ((int)(sb >> 52) <= m) return C0Val{0.0, 0.0, a};   // below 2^-1022
+#ifdef __CUDA_ARCH__
+  const double tj = __ldg(tab + j);
+#else
+  const double tj = tab[j];
+#endif
+  const double tw = tj * c0_bitsd(sb - ((uint64_t)m << 52));
+  const double E = fma(tw, gd, tw);
+  return C0Val{family == 0 ? E : fma(a, E, E), E, a};   // Matern-1.5: (1 + a) e^{-a}
+}
+
+__host__ __device__ inline double c0_fast(int family, double u, double sc) { return c0_eval(family, u, sc).v; }
+
+// Variance factor of C0 at a point: sqrt(1 + 0.5 sin(4 pi x)) for the
+// nonstationary variance (so that C0's factor is the product at the two
+// points), else 1.
+__device__ __forceinline__ double c0_vfac(const Cov& c, double x) { return c.nonstat ? sqrt(gvar(x)) : 1.0; }
+
+// Scale s of the squared distance c0_fast takes.
+__host__ __device__ inline double c0_scale(const Cov& c) { return c.family == 0 ? c.ik : SQRT3 * c.ik; }
+
+// Whether the kernels may use c0_fast on a knot grid of gx x gy.
+__host__ __device__ inline bool c0_fast_ok(const Cov& c, int gx, int gy) {
+  return c.family != 2 && gx <= C0_GMAX && gy <= C0_GMAX;
+}
+
 // Binary exponent e with |x| < 2^e (-2000 for zero): the row and column
 // scales of the FP64-emulation engine.
 __device__ __forceinline__ int xexp_of(double x) {

@@ -1023,6 +1023,16 @@ static long slot_of_level(const LevelState& st, int m) {
   return s;
 }
 
+// The per-parent S buffer seen from the parents [base, ...) of a range whose S
+// rows are (w x w) blocks, w = (parent level + 1) r: the range's first parent
+// lands at the buffer's start.
+static void local_s(GradState& g, long base, long w) {
+  const long ng = (w + EM_KG - 1) / EM_KG;
+  g.SF = reinterpret_cast<double*>(reinterpret_cast<uintptr_t>(g.SF) - (uintptr_t)(base * w * w * (long)sizeof(double)));
+  g.SFexp = reinterpret_cast<int32_t*>(reinterpret_cast<uintptr_t>(g.SFexp) -
+                                       (uintptr_t)(base * ng * w * (long)sizeof(int32_t)));
+}
+
 cudaError_t launch_grad_range(const Desc& hd, const Desc* d_desc, GradState gs, const GradRange& R, int* status,
                               cudaStream_t s, int64_t* launches) {
   const int tile = tile_of(hd.sh.r);
@@ -1054,6 +1064,7 @@ cudaError_t launch_grad_range(const Desc& hd, const Desc* d_desc, GradState gs, 
     if (gb_ready) {   // (over the level-(m-1) parents)
       GradState gp = gs;
       gp.rbase = base(m - 1);
+      if (R.local_sf) local_s(gp, base(m - 1), (long)m * hd.sh.r);
       if ((e = launch_gbar_em(m, hd, d_desc, gp, status, s, launches, count(m - 1)))) return e;
     }
     const size_t sm = sizeof(double) * (MAXL * MAX_R_DEV + MAX_R_DEV) + sq;
@@ -1067,7 +1078,11 @@ cudaError_t launch_grad_range(const Desc& hd, const Desc* d_desc, GradState gs, 
   if (R.leaves) {
     // emulated form: Hbar on the tensor cores (when its per-parent S was allocated)
     gs.rbase = M > 0 ? base(M - 1) : 0;
-    if ((em_parts & 1) && (e = launch_hbar_em(hd, d_desc, gs, status, s, launches, count(M - 1)))) return e;
+    if (em_parts & 1) {
+      GradState gh = gs;
+      if (R.local_sf) local_s(gh, base(M - 1), (long)M * hd.sh.r);
+      if ((e = launch_hbar_em(hd, d_desc, gh, status, s, launches, count(M - 1)))) return e;
+    }
     gs.rbase = base(M);
     size_t sm = sizeof(double) * (MAXL * MAX_R_DEV + 3 * 128 + 2 * MAX_R_DEV + 32) + stg;
     if (emu) {   // (the emulated instance's FP64 tiles are 64 wide: its staging sized for them)

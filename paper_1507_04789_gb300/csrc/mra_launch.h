@@ -118,6 +118,9 @@ struct GradRange {
   int post_lo = 0, post_hi = -1, prior_lo = 0, prior_hi = -1;
   int cs_lo = -1, cs_hi = -1;
   bool leaves = true;
+  // the emulated form's per-parent S buffer holds only the parents of this
+  // range (a streamed chunk): its launches address it from the range's base
+  bool local_sf = false;
   long base[MAXL] = {}, count[MAXL] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
 };
 cudaError_t launch_grad_range(const Desc& hd, const Desc* d_desc, GradState gs, const GradRange& R, int* status,

@@ -76,12 +76,24 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
   __shared__ int rexp[EMU ? EM_REXP : 1], cexp[EMU ? EM_CEXP : 1];
   // emulation: row scales of this region's V rows per 128-column group, and of the current X^l block
   __shared__ int vsc[EMU ? EM_GMAX * MAX_R_DEV : 1], xsc[EMU ? MAX_R_DEV : 1];
+  // c0_fast on two knot grids: squared scaled offsets between their columns and
+  // between their rows, variance factors of the columns (sigma2 in pgp), and the
+  // column and row of every knot
+  __shared__ double pdx[C0_GMAX * C0_GMAX], pdy[C0_GMAX * C0_GMAX], pgp[C0_GMAX], pgq[C0_GMAX];
+  __shared__ unsigned char qcol[MAX_R_DEV], qrow[MAX_R_DEV];
   const Item it = work_item(work);
   const Desc& ds = D[it.d];
   const Shape sh = ds.sh;
   const Cov cv = ds.cv;
   const LevelState& st = ds.st;
   const int r = sh.r, mr = m * r;
+  const int gx = sh.gx, gy = sh.gy;
+  const bool fast = c0_fast_ok(cv, gx, gy);
+  const double c0s = c0_scale(cv);
+  for (int q = threadIdx.x; q < r; q += NT) {
+    qcol[q] = (unsigned char)(q % gx);
+    qrow[q] = (unsigned char)(q / gx);
+  }
   if (EMU)
     for (int t = threadIdx.x; t < EM_GMAX * MAX_R_DEV; t += NT) vsc[t] = -2000;
   const long i = it.i;
@@ -91,6 +103,24 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
   double* ay = ax + MAX_R_DEV;
   double* tmp = ay + MAX_R_DEV;
   double* W = tmp + MAX_R_DEV;                 // r x (r + 1)
+  // offsets between the knot grid (qx, qy) and the grid (bx, by) (all threads;
+  // the caller synchronises before and after)
+  auto grid_offsets = [&](const double* bx, const double* by) {
+    for (int t = threadIdx.x; t < gx * gx + gy * gy; t += NT) {
+      if (t < gx * gx) {
+        const double d = c0s * (qx[t / gx] - bx[t % gx]);
+        pdx[t] = d * d;
+      } else {
+        const int u = t - gx * gx;
+        const double d = c0s * (qy[(u / gy) * gx] - by[(u % gy) * gx]);
+        pdy[u] = d * d;
+      }
+    }
+    for (int c = threadIdx.x; c < gx; c += NT) {
+      pgp[c] = cv.sigma2 * c0_vfac(cv, qx[c]);
+      pgq[c] = c0_vfac(cv, bx[c]);
+    }
+  };
   if (threadIdx.x == 0) bad = 0;
   Engine<EMU> eng;
   eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
@@ -107,11 +137,18 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
     if (EMU)
       for (int t = threadIdx.x; t < MAX_R_DEV; t += NT) xsc[t] = -2000;
     __syncthreads();
+    if (fast) {
+      grid_offsets(ax, ay);
+      __syncthreads();
+    }
     // C0(Q_R, Q_{R_l}) into block l, spread over every warp (the FP64 pipe of
     // every SM sub-partition); the product below reads only blocks < l
     for (int t = threadIdx.x; t < r * r; t += NT) {
       const int qi = t / r, qj = t - qi * r;
-      const double v = cov0(cv, qx[qi], qy[qi], ax[qj], ay[qj]);
+      const int ci = qcol[qi], cj = qcol[qj];
+      const double v = fast ? c0_fast(cv.family, pdx[ci * gx + cj] + pdy[qrow[qi] * gy + qrow[qj]],
+                                      cv.nonstat ? pgp[ci] * pgq[cj] : cv.sigma2)
+                            : cov0(cv, qx[qi], qy[qi], ax[qj], ay[qj]);
       Vrow[(long)qi * mr + l * r + qj] = v;
       if (EMU && l == 0) atomicMax(xsc + qi, xexp_of(v));
     }
@@ -161,11 +198,18 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
   }
   __syncthreads();                             // knots loaded, chain blocks written
   const int ldw = r + 1;
+  if (fast) {
+    grid_offsets(qx, qy);
+    __syncthreads();
+  }
   // lower triangle of C0(Q_R, Q_R), every warp
   for (int t = threadIdx.x; t < r * (r + 1) / 2; t += NT) {
     int qi, qj;
     tri_decode(t, qi, qj);
-    W[qi * ldw + qj] = cov0(cv, qx[qi], qy[qi], qx[qj], qy[qj]);
+    const int ci = qcol[qi], cj = qcol[qj];
+    W[qi * ldw + qj] = fast ? c0_fast(cv.family, pdx[ci * gx + cj] + pdy[qrow[qi] * gy + qrow[qj]],
+                                      cv.nonstat ? pgp[ci] * pgq[cj] : cv.sigma2)
+                            : cov0(cv, qx[qi], qy[qi], qx[qj], qy[qj]);
   }
   __syncthreads();
   if (ok) {
@@ -223,6 +267,11 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
   __shared__ int rexp[EM_REXP], cexp[EM_CEXP];
   __shared__ int hsc[EM_GMAX * TC_M], xsc[TC_M];
   __shared__ double sx[TC_M], sy[TC_M], ax[MAX_R_DEV], ay[MAX_R_DEV];
+  // c0_fast: squared scaled offsets of the tile's points to the knot grid's
+  // columns and rows, the points' variance factors (sigma2 included) and the
+  // knot columns'; the column and row of every knot
+  __shared__ double c0dx[TC_M * C0_GMAX], c0dy[TC_M * C0_GMAX], c0gp[TC_M], c0gq[C0_GMAX];
+  __shared__ unsigned char qcol[MAX_R_DEV], qrow[MAX_R_DEV];
   const Item it = work_item(work);
   const Desc& ds = D[it.d];
   const Shape sh = ds.sh;
@@ -233,6 +282,13 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
   const long P = it.i;
   const long pm = st.mort[M - 1][P];
   const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
+  const int gx = sh.gx, gy = sh.gy;
+  const bool fast = c0_fast_ok(cv, gx, gy);
+  const double c0s = c0_scale(cv), is2 = 1.0 / cv.sigma2;
+  for (int q = threadIdx.x; q < r; q += NT) {
+    qcol[q] = (unsigned char)(q % gx);
+    qrow[q] = (unsigned char)(q / gx);
+  }
   Engine<true> eng;
   eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
   TcAcc acc;
@@ -245,6 +301,7 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
     for (int t = threadIdx.x; t < na; t += NT) {
       sx[t] = lf.xs[t0 + t];
       sy[t] = lf.ys[t0 + t];
+      if (fast) c0gp[t] = cv.sigma2 * c0_vfac(cv, sx[t]);
     }
     for (int t = threadIdx.x; t < EM_GMAX * TC_M; t += NT) hsc[t] = -2000;
     for (int l = 0; l < M && ok; ++l) {
@@ -254,12 +311,32 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
       const double* Vanc = st.V[l] + a * (long)r * (l * r);
       for (int t = threadIdx.x; t < TC_M; t += NT) xsc[t] = -2000;
       __syncthreads();
+      if (fast) {   // offsets to the knot grid's gx columns and gy rows, knot columns' variance factors
+        const int gs = gx + gy;
+        for (int t = threadIdx.x; t < na * gs; t += NT) {
+          const int fi = t / gs, c = t - fi * gs;
+          const double d = c < gx ? c0s * (sx[fi] - ax[c]) : c0s * (sy[fi] - ay[(c - gx) * gx]);
+          (c < gx ? c0dx + fi * gx + c : c0dy + fi * gy + (c - gx))[0] = d * d;
+        }
+        for (int c = threadIdx.x; c < gx; c += NT) c0gq[c] = c0_vfac(cv, ax[c]);
+        __syncthreads();
+      }
       // C0(S_F, Q_l) into block l (the product below reads only blocks < l); in
       // gradient calls with its two derivatives
       for (int t = threadIdx.x; t < na * r; t += NT) {
         const int fi = t / r, qj = t - fi * r;
         double v;
-        if (lf.dc) {
+        if (fast) {
+          const int qc = qcol[qj];
+          const C0Val cz = c0_eval(cv.family, c0dx[fi * gx + qc] + c0dy[fi * gy + qrow[qj]],
+                                   cv.nonstat ? c0gp[fi] * c0gq[qc] : cv.sigma2);
+          v = cz.v;
+          if (lf.dc) {   // (dC0/dsigma2, dC0/dkappa)
+            const double ea = cz.e * cz.a * cv.ik;
+            *reinterpret_cast<double2*>(lf.dc + 2 * ((t0 + fi) * Mr + l * r + qj)) =
+                make_double2(v * is2, cv.family == 0 ? ea : ea * cz.a);
+          }
+        } else if (lf.dc) {
           double d1, d2;
           v = cov0_d(cv, sx[fi], sy[fi], ax[qj], ay[qj], d1, d2);
           *reinterpret_cast<double2*>(lf.dc + 2 * ((t0 + fi) * Mr + l * r + qj)) = make_double2(d1, d2);
@@ -453,10 +530,25 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
   __syncthreads();                             // points loaded, chain blocks written
   // Sigma_F = C0(S_F, S_F) - V_F V_F' + tau2 I (lower triangle), the
   // covariance by every warp first, then the product 64 columns at a time
+  const bool fast = c0_fast_ok(cv, 1, 1);
+  const double c0s = c0_scale(cv), c0s2 = c0s * c0s;
+  static_assert(TC_M <= 2 * MAX_R_DEV, "the leaf's variance factors reuse ax and ay");
+  double* lgq = ax;                              // the points' variance factors (ax, ay: 2 MAX_R_DEV >= nF doubles)
+  if (fast && cv.nonstat) {
+    for (int t = threadIdx.x; t < nF; t += NT) lgq[t] = c0_vfac(cv, sx[t]);
+    __syncthreads();
+  }
   for (int t = threadIdx.x; t < nF * (nF + 1) / 2; t += NT) {
     int fi, fj;
     tri_decode(t, fi, fj);
-    S[fi * lds + fj] = cov0(cv, sx[fi], sy[fi], sx[fj], sy[fj]) + (fi == fj ? tau2 : 0.0);
+    double v;
+    if (fast) {
+      const double dx = sx[fi] - sx[fj], dy = sy[fi] - sy[fj];
+      v = c0_fast(cv.family, c0s2 * fma(dx, dx, dy * dy), cv.nonstat ? cv.sigma2 * lgq[fi] * lgq[fj] : cv.sigma2);
+    } else {
+      v = cov0(cv, sx[fi], sy[fi], sx[fj], sy[fj]);
+    }
+    S[fi * lds + fj] = v + (fi == fj ? tau2 : 0.0);
   }
   __syncthreads();
   const int nct = (nF + TC_N - 1) / TC_N;

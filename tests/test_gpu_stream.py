@@ -52,7 +52,11 @@ def test_streamed_gradient_equals_whole_tree(mra, precision):
         with mra.Handle(locs, y, M=w.M, r=w.r, family=w.family, precision=precision, stream_level=s) as hs:
             lls, gs = hs.loglik_grad(theta)
             assert lls == pytest.approx(ll, rel=1e-13), s
-            np.testing.assert_allclose(gs, g, rtol=1e-11, atol=1e-11 * np.abs(g).max(), err_msg=f"s={s}")
+            # (FP64: the same arithmetic up to summation order; emulated: the per-parent S
+            # buffer of a chunk may be left out where the whole tree's is taken, and the
+            # engine's products round at about 1e-14 relative)
+            tol = 1e-11 if precision == "fp64" else 1e-10
+            np.testing.assert_allclose(gs, g, rtol=tol, atol=tol * np.abs(g).max(), err_msg=f"s={s}")
             # a plain evaluation and a second gradient on the same handle agree
             assert hs.loglik(theta) == pytest.approx(ll, rel=1e-13)
             lls2, gs2 = hs.loglik_grad(theta)
