@@ -132,16 +132,25 @@ def contraction_flops(M: int, r: int, nF, precision: str):
 # DRAM bytes per launch (per stage, where the dominant entry is a stage of two
 # kernels) of the dominant kernel, from one ncu capture, valid only
 # while the kernel's sources are the ones it was taken from (else null).
+SOURCES_EMU = ["mra_mixed.cu", "mra_emu.cuh", "mra_tc.cuh", "mra_device.cuh", "mra_kernels.cuh"]
 TRAFFIC = {
     ("emu", "chain_forward_kernel_em", "n1M_matern15_M7_r64"): {
-        "bytes": 5.835e+09,
-        "how": "dram__bytes_read.sum + dram__bytes_write.sum of chain_forward_kernel_em (486.9 + 763.6 MB) "
+        "bytes": 5.894e+09,
+        "how": "dram__bytes_read.sum + dram__bytes_write.sum of chain_forward_kernel_em (498.0 + 765.3 MB) "
                "at n = 2^18, M = 6 (profiles/leaf_stage_emu_n256k_matern15_M6_r64.md), scaled by n M r "
                "(x 4.667) to n = 2^20, M = 7; the kernel writes V_F (8 B x n x M r) and reads the points "
-               "and the ancestors' factors, both in proportion to n M r; captured before the adjoint kernels "
-               "in the same file took a region base, which leaves this kernel untouched",
-        "sources": ["mra_mixed.cu", "mra_emu.cuh", "mra_tc.cuh", "mra_device.cuh", "mra_kernels.cuh"],
-        "sha1": "9ff20caf3e8db293e5623709c07daf39f54eb9c7",
+               "and the ancestors' factors, both in proportion to n M r",
+        "sources": SOURCES_EMU,
+        "sha1": "97f96c0727e2c26251a67c94ac8a62c7121d5810",
+    },
+    ("emu", "leaf_kernel_tc<1>", "n1M_matern15_M7_r64"): {
+        "bytes": 7.996e+09,
+        "how": "dram__bytes_read.sum + dram__bytes_write.sum of leaf_kernel_tc<1> (815.6 + 897.8 MB) at "
+               "n = 2^18, M = 6 (profiles/leaf_stage_emu_n256k_matern15_M6_r64.md), scaled by n M r (x 4.667) "
+               "to n = 2^20, M = 7; the kernel reads V_F and writes H (8 B x n x M r each) and the "
+               "L_Sigma^{-1} blocks (8 B x sum n_F^2, about 1/7 of it)",
+        "sources": SOURCES_EMU,
+        "sha1": "97f96c0727e2c26251a67c94ac8a62c7121d5810",
     },
 }
 
