@@ -115,6 +115,24 @@ struct Tables {
   std::vector<int32_t> nreg;
 };
 
+// Groups of leaves for the emulated leaf kernel: consecutive children of one
+// level-(M-1) region, at most LGRP_MAX of them and MRA_MAX_LEAF observations in
+// all (the kernel stacks a group in one 128-row tile).  Parents [p0, p1).
+void leaf_groups(const Tables& T, int M, const std::vector<int32_t>& counts, int64_t p0, int64_t p1, int chunk,
+                 std::vector<int2>& items, std::vector<int>& cnt) {
+  for (int64_t p = p0; p < p1; ++p) {
+    const int32_t cf = T.cfirst[M - 1][p], ce = cf + T.ccnt[M - 1][p];
+    for (int32_t F = cf; F < ce;) {
+      int g = 1, rows = counts[T.mort[M][F]];
+      while (F + g < ce && g < mra::LGRP_MAX && rows + counts[T.mort[M][F + g]] <= MRA_MAX_LEAF)
+        rows += counts[T.mort[M][F + g++]];
+      items.push_back(make_int2(chunk, F));
+      cnt.push_back(g);
+      F += g;
+    }
+  }
+}
+
 void build_tables(int M, bool prune, const std::vector<int32_t>& counts, Tables& T) {
   T.mort.assign(M + 1, {});
   T.par.assign(M + 1, {});
@@ -255,6 +273,15 @@ struct mra_handle {
   int64_t scount[MRA_MAX_M + 1][MRA_STAGES] = {};
   int64_t nevals = 0;
   std::vector<int32_t> leaf_counts;   // observations per leaf (Morton order), for mra_stats
+  // emulated form: groups of leaves for the leaf kernel (work item (chunk, first
+  // compact leaf), leaf count), per chunk from goff[g]; device copies with room
+  // for one group per leaf; lrows = the rows of the kernel's layout (0: none)
+  std::vector<int2> gitems;
+  std::vector<int> gcnt;
+  std::vector<int64_t> goff;
+  int2* d_gitems = nullptr;
+  int* d_gcnt = nullptr;
+  int lrows = 0;
   bool have_post = false;
   mra_params last{};
   // batch of datasets
@@ -347,6 +374,7 @@ cudaError_t upload_desc(mra_handle* h, const mra_params* theta) {
     h->hd.tau2 = theta->tau2;
   }
   h->hd.nlmax = h->nlmax;
+  h->hd.lrows = h->lrows;
   h->hd.st = h->st;
   h->hd.lf = h->lf;
   if (!h->s_lvl) return cudaMemcpyAsync(h->d_desc, &h->hd, sizeof(mra::Desc), cudaMemcpyHostToDevice, h->stream);
@@ -699,6 +727,24 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
     B.want(&hrow, obs_cap * (int64_t)((M * r + 127) / 128));
   }
   B.want(&h->d_desc, ndesc);
+  if (emu && M > 0) {   // groups of leaves (the emulated leaf kernel), with room for one per leaf
+    h->gitems.clear();
+    h->gcnt.clear();
+    h->goff.assign(1, 0);
+    if (!s_lvl) {
+      leaf_groups(h->tab, M, h->leaf_counts, 0, nreg[M - 1], 0, h->gitems, h->gcnt);
+      h->goff.push_back((int64_t)h->gitems.size());
+    } else {
+      for (size_t g = 0; g < h->chunks.size(); ++g) {
+        leaf_groups(h->tab, M, h->leaf_counts, h->chunks[g].c0[M - 1], h->chunks[g].c1[M - 1], (int)g, h->gitems,
+                    h->gcnt);
+        h->goff.push_back((int64_t)h->gitems.size());
+      }
+    }
+    B.want(&h->d_gitems, std::max<int64_t>(nreg[M], 1));
+    B.want(&h->d_gcnt, std::max<int64_t>(nreg[M], 1));
+    h->lrows = MRA_MAX_LEAF;
+  }
   int2* d_work = nullptr;
   std::vector<int2> work;
   if (s_lvl) {   // work lists of every chunk: (chunk, compact region) per level, leaves, Gram products
@@ -725,6 +771,13 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   if (!work.empty() &&
       (e = cudaMemcpyAsync(d_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, h->stream))) {
     mra_free(h); return cuda_fail(e, "chunk work lists");
+  }
+  if (!h->gitems.empty() &&
+      ((e = cudaMemcpyAsync(h->d_gitems, h->gitems.data(), sizeof(int2) * h->gitems.size(), cudaMemcpyHostToDevice,
+                            h->stream)) ||
+       (e = cudaMemcpyAsync(h->d_gcnt, h->gcnt.data(), sizeof(int) * h->gcnt.size(), cudaMemcpyHostToDevice,
+                            h->stream)))) {
+    mra_free(h); return cuda_fail(e, "leaf groups");
   }
   if ((e = cudaStreamSynchronize(h->stream))) { mra_free(h); return cuda_fail(e, "tree tables"); }
   h->lf.off = h->off;
@@ -764,12 +817,24 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
       }
       p.n_leaf = (int)(c.c1[M] - c.c0[M]);
       p.w_leaf = at[M];
+      if (h->lrows) {   // the chunk's groups of leaves
+        p.w_leaf = h->d_gitems + h->goff[g];
+        p.c_leaf = h->d_gcnt + h->goff[g];
+        p.n_leaf = (int)(h->goff[g + 1] - h->goff[g]);
+        p.lrows = h->lrows;
+      }
       p.n_syrk = (int)(c.c1[M - 1] - c.c0[M - 1]);
       p.w_syrk = at[M - 1];
       p.t_syrk = M * (M + 1) / 2;
     }
   }
   single_plan(h);
+  if (h->lrows && !s_lvl) {
+    h->plan.w_leaf = h->d_gitems;
+    h->plan.c_leaf = h->d_gcnt;
+    h->plan.n_leaf = (int)h->gitems.size();
+    h->plan.lrows = h->lrows;
+  }
   if (s_lvl) {
     h->plan_coarse_prior = h->plan;        // levels 0..s of the prior pass
     h->plan_coarse_prior.prior_hi = s_lvl + 1;
@@ -780,8 +845,9 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
     h->plan_coarse_post.leaves = false;
     h->plan_coarse_post.post_hi = s_lvl + 1;
   }
-  size_t need = cfg->precision != MRA_PREC_FP64 ? mra::leaf_tc_smem_bytes(h->nlmax, cfg->precision == MRA_PREC_EMU)
-                                                 : mra::leaf_smem_bytes(r, h->nlmax);
+  size_t need = cfg->precision != MRA_PREC_FP64
+                    ? mra::leaf_tc_smem_bytes(std::max(h->nlmax, h->lrows), cfg->precision == MRA_PREC_EMU)
+                    : mra::leaf_smem_bytes(r, h->nlmax);
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -1029,6 +1095,19 @@ int mra_update(mra_handle* h, const double* locs, const double* y, int where) {
       if ((counts[f] > 0) != (h->tab.cid[h->M][f] >= 0))
         return fail(MRA_ERR_LIMIT, "the new data occupies other leaves than the pruned tree; build a new handle");
   h->leaf_counts.swap(counts);
+  if (h->lrows) {   // the groups of leaves follow the new occupancy
+    h->gitems.clear();
+    h->gcnt.clear();
+    leaf_groups(h->tab, h->M, h->leaf_counts, 0, h->tab.nreg[h->M - 1], 0, h->gitems, h->gcnt);
+    h->goff.assign({0, (int64_t)h->gitems.size()});
+    if ((e = cudaMemcpyAsync(h->d_gitems, h->gitems.data(), sizeof(int2) * h->gitems.size(), cudaMemcpyHostToDevice,
+                             h->stream)) ||
+        (e = cudaMemcpyAsync(h->d_gcnt, h->gcnt.data(), sizeof(int) * h->gcnt.size(), cudaMemcpyHostToDevice,
+                             h->stream)) ||
+        (e = cudaStreamSynchronize(h->stream)))
+      return cuda_fail(e, "leaf groups");
+    h->plan.n_leaf = (int)h->gitems.size();
+  }
   return MRA_OK;
 }
 
@@ -1696,9 +1775,35 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
       if (h->parts[d]->M > 0)
         for (int32_t c = 0; c < h->parts[d]->tab.nreg[h->parts[d]->M - 1]; ++c) items.push_back(make_int2(d, c));
   });
+  // emulated form: the datasets' groups of leaves, as one list
+  std::vector<int2> bgi;
+  std::vector<int> bgc;
+  if (h->cfg.precision == MRA_PREC_EMU) {
+    h->lrows = MRA_MAX_LEAF;
+    for (int d = 0; d < ndata; ++d) {
+      const mra_handle* q = h->parts[d];
+      if (q->lrows) {
+        for (size_t k = 0; k < q->gitems.size(); ++k) {
+          bgi.push_back(make_int2(d, q->gitems[k].y));
+          bgc.push_back(q->gcnt[k]);
+        }
+      } else {
+        for (int32_t c = 0; c < q->tab.nreg[q->M]; ++c) {
+          bgi.push_back(make_int2(d, c));
+          bgc.push_back(1);
+        }
+      }
+    }
+  }
   int2* d_items = nullptr;
+  int2* d_bgi = nullptr;
+  int* d_bgc = nullptr;
   Arena& A = h->batch;
   A.want(&d_items, std::max<size_t>(items.size(), 1));
+  if (!bgi.empty()) {
+    A.want(&d_bgi, bgi.size());
+    A.want(&d_bgc, bgc.size());
+  }
   A.want(&h->d_descs, ndata);
   A.want(&h->d_roots, 2 * (size_t)ndata);
   A.want(&h->status, 4);
@@ -1714,6 +1819,10 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
       (e = cudaMemcpy(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice))) {
     mra_free(h); return cuda_fail(e, "work lists");
   }
+  if (!bgi.empty() && ((e = cudaMemcpy(d_bgi, bgi.data(), sizeof(int2) * bgi.size(), cudaMemcpyHostToDevice)) ||
+                       (e = cudaMemcpy(d_bgc, bgc.data(), sizeof(int) * bgc.size(), cudaMemcpyHostToDevice)))) {
+    mra_free(h); return cuda_fail(e, "leaf groups");
+  }
   mra::Plan& p = h->plan;
   p = mra::Plan();
   p.maxM = maxM;
@@ -1725,6 +1834,12 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
   for (int m = 0; m < maxM; ++m, ++li) { p.n_lvl[m] = lists[li].first; p.w_lvl[m] = d_items + lists[li].second; }
   for (int m = 1; m < maxM; ++m, ++li) { p.n_agg[m] = lists[li].first; p.w_agg[m] = d_items + lists[li].second; }
   p.n_leaf = lists[li].first; p.w_leaf = d_items + lists[li].second; ++li;
+  if (!bgi.empty()) {
+    p.n_leaf = (int)bgi.size();
+    p.w_leaf = d_bgi;
+    p.c_leaf = d_bgc;
+    p.lrows = h->lrows;
+  }
   p.n_syrk = lists[li].first; p.w_syrk = d_items + lists[li].second; ++li;
   for (int d = 0; d < ndata; ++d) p.t_syrk = std::max(p.t_syrk, h->parts[d]->M * (h->parts[d]->M + 1) / 2);
   h->h_descs.resize(ndata);
@@ -1734,9 +1849,11 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
     upload_desc(q, &th);               // fills q->hd (the copy to q's own descriptor is harmless)
     h->h_descs[d] = q->hd;
     h->h_descs[d].nlmax = h->nlmax;    // one shared-memory layout for the whole batch
+    h->h_descs[d].lrows = h->lrows;
   }
   if ((e = cudaDeviceSynchronize())) { mra_free(h); return cuda_fail(e, "batch set-up"); }
-  size_t need = p.mixed ? mra::leaf_tc_smem_bytes(h->nlmax, p.mixed == 2) : mra::leaf_smem_bytes(h->r, h->nlmax);
+  size_t need = p.mixed ? mra::leaf_tc_smem_bytes(std::max(h->nlmax, h->lrows), p.mixed == 2)
+                        : mra::leaf_smem_bytes(h->r, h->nlmax);
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -584,6 +584,137 @@ __device__ inline void chol_smem(double* A, int n, int lda, int* bad) {
   __syncthreads();
 }
 
+// ---- block-diagonal factorisations (a group of leaves in one CTA) ---------
+// The nb diagonal blocks of A start at rows seg[0] = 0 <= seg[1] <= ... <=
+// seg[nb] (= the order of A).  chol_seg factorises every block in place as
+// chol_smem factorises one matrix and leaves every entry outside the blocks'
+// lower triangles zero; trinv_seg inverts every block's lower triangle as
+// trinv_smem does (the same operations per entry, so a block's factors are
+// those of the single-matrix routines).  The steps of all blocks run together,
+// so the barriers are those of the largest block alone.  pv: nb doubles of
+// shared memory (the blocks' pivots), tmp: seg[nb] doubles.
+constexpr int LGRP_MAX = 4;        // leaves of one group (the children of one parent)
+
+__device__ __forceinline__ int seg_block(const int* seg, int nb, int i) {   // block of row i
+  int b = 0;
+  while (b + 1 < nb && i >= seg[b + 1]) ++b;
+  return b;
+}
+
+__device__ inline void chol_seg(double* A, int lda, const int* seg, int nb, int* bad, double* pv) {
+  __syncthreads();
+  int nmax = 0;
+  for (int b = 0; b < nb; ++b) nmax = max(nmax, seg[b + 1] - seg[b]);
+  if (threadIdx.x < nb && seg[threadIdx.x + 1] > seg[threadIdx.x]) {
+    const int s0 = seg[threadIdx.x];
+    const double d = A[s0 * lda + s0];
+    const bool ok = d > 0.0;
+    const double rs = ok ? rsqrt(d) : 1.0;
+    if (!ok) *bad = 1;
+    A[s0 * lda + s0] = ok ? d * rs : 1.0;
+    pv[threadIdx.x] = rs;
+  }
+  __syncthreads();
+  for (int j = 0; j < nmax; ++j) {
+    int tot = 0, tri = 0;
+    for (int b = 0; b < nb; ++b) {
+      const int m = max(0, seg[b + 1] - seg[b] - j - 1);
+      tot += m;
+      tri += m * (m + 1) / 2;
+    }
+    for (int t = threadIdx.x; t < tot; t += NT) {   // column j of every block scaled
+      int b = 0, u = t;
+      for (int m = max(0, seg[1] - seg[0] - j - 1); u >= m; m = max(0, seg[b + 1] - seg[b] - j - 1)) {
+        u -= m;
+        ++b;
+      }
+      const int s0 = seg[b];
+      A[(s0 + j + 1 + u) * lda + s0 + j] *= pv[b];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < tri; t += NT) {   // trailing lower triangles; element 0: the next pivot
+      int b = 0, u = t;
+      for (int m = max(0, seg[1] - seg[0] - j - 1); u >= m * (m + 1) / 2; m = max(0, seg[b + 1] - seg[b] - j - 1)) {
+        u -= m * (m + 1) / 2;
+        ++b;
+      }
+      int ii, kk;
+      tri_decode(u, ii, kk);
+      const int s0 = seg[b], jc = s0 + j, i = jc + 1 + ii, k = jc + 1 + kk;
+      const double v = fma(-A[i * lda + jc], A[k * lda + jc], A[i * lda + k]);
+      if (u == 0) {
+        const bool ok = v > 0.0;
+        const double rs = ok ? rsqrt(v) : 1.0;
+        if (!ok) *bad = 1;
+        A[i * lda + k] = ok ? v * rs : 1.0;
+        pv[b] = rs;
+      } else {
+        A[i * lda + k] = v;
+      }
+    }
+    __syncthreads();
+  }
+  const int n = seg[nb];
+  for (int t = threadIdx.x; t < n * n; t += NT) {
+    const int i = t / n, k = t - i * n;
+    if (k > i || k < seg[seg_block(seg, nb, i)]) A[i * lda + k] = 0.0;
+  }
+  __syncthreads();
+}
+
+__device__ inline void trinv_seg(double* A, int lda, const int* seg, int nb, double* tmp, double* pv) {
+  __syncthreads();
+  int nmax = 0;
+  for (int b = 0; b < nb; ++b) nmax = max(nmax, seg[b + 1] - seg[b]);
+  if (threadIdx.x < nb && seg[threadIdx.x + 1] > seg[threadIdx.x]) {
+    const int s0 = seg[threadIdx.x];
+    pv[threadIdx.x] = 1.0 / A[s0 * lda + s0];
+  }
+  __syncthreads();
+  for (int k = 0; k < nmax; ++k) {
+    // phase 1, every block with k < n_b: row k scaled by 1 / L_kk (X_kk = 1 / L_kk), and
+    // column k below the diagonal saved
+    int tot = 0, upd = 0;
+    for (int b = 0; b < nb; ++b) {
+      const int nbk = seg[b + 1] - seg[b];
+      if (k < nbk) {
+        tot += nbk;
+        upd += (nbk - k - 1) * (k + 1);
+      }
+    }
+    for (int t = threadIdx.x; t < tot; t += NT) {
+      int b = 0, u = t;
+      for (int c = k < seg[1] - seg[0] ? seg[1] - seg[0] : 0; u >= c;
+           c = k < seg[b + 1] - seg[b] ? seg[b + 1] - seg[b] : 0) {
+        u -= c;
+        ++b;
+      }
+      const int s0 = seg[b], gk = s0 + k;
+      if (u <= k) A[gk * lda + s0 + u] = u < k ? A[gk * lda + s0 + u] * pv[b] : pv[b];
+      else tmp[s0 + u] = A[(s0 + u) * lda + gk];
+    }
+    __syncthreads();
+    if (threadIdx.x < nb) {   // the next step's reciprocals (diagonal entries phase 2 does not write)
+      const int s0 = seg[threadIdx.x];
+      if (k + 1 < seg[threadIdx.x + 1] - s0) pv[threadIdx.x] = 1.0 / A[(s0 + k + 1) * lda + s0 + k + 1];
+    }
+    // phase 2: X_ij -= L_ik X_kj for i > k, j <= k, within every block
+    const int w = k + 1;
+    for (int t = threadIdx.x; t < upd; t += NT) {
+      int b = 0, u = t;
+      for (int c = k < seg[1] - seg[0] ? (seg[1] - seg[0] - k - 1) * w : 0; u >= c;
+           c = k < seg[b + 1] - seg[b] ? (seg[b + 1] - seg[b] - k - 1) * w : 0) {
+        u -= c;
+        ++b;
+      }
+      const int s0 = seg[b], ii = u / w, j = u - ii * w, i = s0 + k + 1 + ii;
+      const double x0 = j == k ? 0.0 : A[i * lda + s0 + j];
+      A[i * lda + s0 + j] = fma(-tmp[i], A[(s0 + k) * lda + s0 + j], x0);
+    }
+    __syncthreads();
+  }
+}
+
 // Lower-triangular L in place -> L^{-1}, by forward substitution on the rows
 // of the identity (right-looking): step k scales row k by 1 / L_kk and
 // subtracts L_ik times it from every row i > k.  Each step is a rank-1 update

@@ -182,7 +182,7 @@ struct Desc {
   Cov cv;
   double tau2;
   int nlmax;          // largest leaf occupancy (shared-memory layout of the leaf kernels)
-  int pad;
+  int lrows;          // rows of the emulated leaf kernel's layout: the largest group of leaves (>= nlmax), or 0
   LevelState st;
   LeafState lf;
 };

@@ -62,6 +62,10 @@ struct Plan {
   int n_agg[MAXL] = {};
   const int2* w_leaf = nullptr;
   int n_leaf = 0;
+  // emulated form: groups of leaves (c_leaf[b] leaves from compact id w_leaf[b].y;
+  // n_leaf counts groups), laid out for lrows rows; null: one leaf per item
+  const int* c_leaf = nullptr;
+  int lrows = 0;
   const int2* w_syrk = nullptr;
   int n_syrk = 0, t_syrk = 1;
 };
@@ -80,7 +84,7 @@ cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nbl
                             cudaStream_t s);
 cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int emu, int* status,
                            cudaStream_t s, const int2* w_par = nullptr, int n_par = 0, Timer* tm = nullptr,
-                           int leaf_level = -1);
+                           int leaf_level = -1, const int* gcnt = nullptr, int lrows = 0);
 size_t leaf_tc_smem_bytes(int nlmax, int emu);
 cudaError_t launch_leaf_syrk_em(const Desc* d_desc, const int2* work, int nblocks, int maxM, int r, int* status,
                                 cudaStream_t s);

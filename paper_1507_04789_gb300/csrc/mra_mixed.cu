@@ -407,10 +407,16 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
 }
 
 // chain_done (emulated form): V_F and its row scales were formed by
-// chain_forward_kernel_em; the kernel starts at Sigma_F.
+// chain_forward_kernel_em; the kernel starts at Sigma_F.  gcnt (emulated form
+// with chain_done, else null): the work item is a group of gcnt[b] leaves with
+// consecutive compact ids starting at it.i (children of one parent, at most
+// LGRP_MAX, at most ds.lrows observations in all), stacked in one tile: their
+// Sigma_F are the diagonal blocks of one block-diagonal matrix, factorised and
+// inverted block by block (chol_seg, trinv_seg), and H = L^{-1} V_F is one
+// product for all of them (the inverse is zero outside the blocks).
 template <bool EMU>
 __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D, const int2* __restrict__ work,
-                                                     int* status, int chain_done) {
+                                                     int* status, int chain_done, const int* __restrict__ gcnt) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
@@ -423,16 +429,21 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
   const Shape sh = ds.sh;
   const Cov cv = ds.cv;
   const double tau2 = ds.tau2;
-  const int nlmax = ds.nlmax;
+  const int nlmax = max(ds.nlmax, ds.lrows);     // rows of the layout
   const LevelState& st = ds.st;
   const LeafState& lf = ds.lf;
   const int M = sh.M, r = sh.r, Mr = M * r;
-  const long F = it.i;                           // compact leaf id
+  const long F = it.i;                           // compact leaf id (the group's first)
+  const int G = EMU && gcnt ? gcnt[blockIdx.x] : 1;
   const long Fm = st.mort[M][F];
   const long o0 = lf.off[Fm];
-  const int nF = (int)(lf.off[Fm + 1] - o0);
+  const int nF = (int)(lf.off[st.mort[M][F + G - 1] + 1] - o0);
   if (nF == 0) {
-    if (threadIdx.x == 0) { lf.d[F] = 0.0; lf.u[F] = 0.0; }
+    if (threadIdx.x < G) { lf.d[F + threadIdx.x] = 0.0; lf.u[F + threadIdx.x] = 0.0; }
+    return;
+  }
+  if (nF > nlmax) {                              // (a group larger than the layout: never formed by the host)
+    if (threadIdx.x == 0) flag_error(status, ST_LIMIT, M, F);
     return;
   }
   const int lds = nlmax + 1;
@@ -442,9 +453,21 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
   double* tmp = sv + nlmax;
   double* ax = tmp + nlmax;
   double* ay = ax + MAX_R_DEV;
-  double* red = ay + MAX_R_DEV;
+  double* red = ay + MAX_R_DEV;                 // block sums (red[0..7]) or a group's pivots (red[0..3])
   double* S = red + 32;                         // nlmax x (nlmax + 1)
-  if (threadIdx.x == 0) bad = 0;
+  // a group's leaves: rows gseg[k] .. gseg[k + 1] - 1, and the leaf of every row
+  int* gseg = reinterpret_cast<int*>(red + 8);
+  unsigned char* growb = reinterpret_cast<unsigned char*>(red + 16);
+  static_assert(TC_M <= 16 * sizeof(double) && LGRP_MAX + 1 <= 8 * sizeof(double) / sizeof(int),
+                "the group tables fit in red[8..31]");
+  if (threadIdx.x == 0) {
+    bad = 0;
+    gseg[0] = 0;
+    for (int k = 0; k < G; ++k) gseg[k + 1] = (int)(lf.off[st.mort[M][F + k] + 1] - o0);
+  }
+  __syncthreads();
+  if (EMU)
+    for (int t = threadIdx.x; t < nF; t += NT) growb[t] = (unsigned char)seg_block(gseg, G, t);
   Engine<EMU> eng;
   eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
   for (int t = threadIdx.x; t < nF; t += NT) {
@@ -538,9 +561,18 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
     for (int t = threadIdx.x; t < nF; t += NT) lgq[t] = c0_vfac(cv, sx[t]);
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < nF * (nF + 1) / 2; t += NT) {
+  int tri_all = 0;                               // lower triangles of the group's diagonal blocks
+  for (int k = 0; k < G; ++k) tri_all += (gseg[k + 1] - gseg[k]) * (gseg[k + 1] - gseg[k] + 1) / 2;
+  for (int t = threadIdx.x; t < tri_all; t += NT) {
+    int b = 0, u = t;
+    for (int c = gseg[1] * (gseg[1] + 1) / 2; u >= c; c = (gseg[b + 1] - gseg[b]) * (gseg[b + 1] - gseg[b] + 1) / 2) {
+      u -= c;
+      ++b;
+    }
     int fi, fj;
-    tri_decode(t, fi, fj);
+    tri_decode(u, fi, fj);
+    fi += gseg[b];
+    fj += gseg[b];
     double v;
     if (fast) {
       const double dx = sx[fi] - sx[fj], dy = sy[fi] - sy[fj];
@@ -562,41 +594,84 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
       #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const int oj = ct * TC_N + c0 + c;
-        if (c0 + c < ncol && oj <= row) S[row * lds + oj] -= acc.v[c];
+        if (c0 + c < ncol && oj <= row && (G == 1 || oj >= gseg[growb[row]])) S[row * lds + oj] -= acc.v[c];
       }
   }
-  double ld = 0.0, zz = 0.0;
+  double ld = 0.0, zz = 0.0;   // (a group: leaf k's in thread k)
+  // the leaves' square blocks of S (n_k x n_k, row-major) to dst + sq_off of each leaf
+  auto store_blocks = [&](double* dst) {
+    int tot = 0;
+    for (int k = 0; k < G; ++k) tot += (gseg[k + 1] - gseg[k]) * (gseg[k + 1] - gseg[k]);
+    for (int t = threadIdx.x; t < tot; t += NT) {
+      int b = 0, u = t;
+      for (int c = gseg[1] * gseg[1]; u >= c; c = (gseg[b + 1] - gseg[b]) * (gseg[b + 1] - gseg[b])) {
+        u -= c;
+        ++b;
+      }
+      const int nb = gseg[b + 1] - gseg[b], i = u / nb, j = u - i * nb;
+      dst[lf.sq_off[st.mort[M][F + b]] + u] = S[(gseg[b] + i) * lds + gseg[b] + j];
+    }
+  };
+  // sum over the rows of leaf k of tmp (thread k)
+  auto leaf_sum = [&]() {
+    double v = 0.0;
+    if (threadIdx.x < G)
+      for (int i = gseg[threadIdx.x]; i < gseg[threadIdx.x + 1]; ++i) v += tmp[i];
+    return v;
+  };
   if (ok) {
-    chol_smem(S, nF, lds, &bad);
-    for (int t = threadIdx.x; t < nF; t += NT) ld += log(S[t * lds + t]);
-    ld = 2.0 * block_sum(ld, red);
+    if (G == 1) {
+      chol_smem(S, nF, lds, &bad);
+      for (int t = threadIdx.x; t < nF; t += NT) ld += log(S[t * lds + t]);
+      ld = 2.0 * block_sum(ld, red);
+    } else {
+      chol_seg(S, lds, gseg, G, &bad, red);
+      for (int t = threadIdx.x; t < nF; t += NT) tmp[t] = log(S[t * lds + t]);
+      __syncthreads();
+      ld = 2.0 * leaf_sum();
+    }
     if (lf.LSf) {
-      double* Lf = lf.LSf + lf.sq_off[Fm];
-      for (int t = threadIdx.x; t < nF * nF; t += NT) Lf[t] = S[(t / nF) * lds + (t % nF)];
+      if (G == 1) {
+        double* Lf = lf.LSf + lf.sq_off[Fm];
+        for (int t = threadIdx.x; t < nF * nF; t += NT) Lf[t] = S[(t / nF) * lds + (t % nF)];
+      } else {
+        store_blocks(lf.LSf);
+      }
     }
     if (lf.VF)
       for (long t = threadIdx.x; t < (long)nF * Mr; t += NT) lf.VF[o0 * Mr + t] = Hrow[t];
-    trinv_smem(S, nF, lds, tmp);
+    if (G == 1) trinv_smem(S, nF, lds, tmp);
+    else trinv_seg(S, lds, gseg, G, tmp, red);
     if (EMU) {   // row scales of L_Sigma^{-1} (lower triangular) for the solve below
       for (int t = threadIdx.x; t < nF; t += NT) {
         int e = -2000;
-        for (int q = 0; q <= t; ++q) e = max(e, xexp_of(S[t * lds + q]));
+        for (int q = G == 1 ? 0 : gseg[growb[t]]; q <= t; ++q) e = max(e, xexp_of(S[t * lds + q]));
         ssc[t] = e;
       }
     }
-    double* LS = lf.LS + lf.sq_off[Fm];
-    for (int t = threadIdx.x; t < nF * nF; t += NT) LS[t] = S[(t / nF) * lds + (t % nF)];
+    if (G == 1) {
+      double* LS = lf.LS + lf.sq_off[Fm];
+      for (int t = threadIdx.x; t < nF * nF; t += NT) LS[t] = S[(t / nF) * lds + (t % nF)];
+    } else {
+      store_blocks(lf.LS);
+    }
     for (int t = threadIdx.x; t < nF; t += NT) {
       double s = 0.0;
-      for (int k = 0; k <= t; ++k) s = fma(S[t * lds + k], sv[k], s);
+      for (int k = G == 1 ? 0 : gseg[growb[t]]; k <= t; ++k) s = fma(S[t * lds + k], sv[k], s);
       lf.z[o0 + t] = s;
-      zz = fma(s, s, zz);
+      if (G == 1) zz = fma(s, s, zz);
+      else tmp[t] = s * s;
     }
-    zz = block_sum(zz, red);
+    if (G == 1) {
+      zz = block_sum(zz, red);
+    } else {
+      __syncthreads();
+      zz = leaf_sum();
+    }
     // H^l = L_Sigma^{-1} V^l_F (whole block read before it is overwritten)
     int32_t* hcol = EMU ? lf.hcol + F * (long)Mr : nullptr;   // column scales of H_F for the Gram kernel
     if (EMU) {
-      for (int t = threadIdx.x; t < Mr; t += NT) hcol[t] = -2000;
+      for (int t = threadIdx.x; t < G * Mr; t += NT) hcol[t] = -2000;   // (the group's leaves are consecutive)
       // hsc (the V_F row scales) is read no more: it collects the row scales of H_F
       for (int t = threadIdx.x; t < EM_GMAX * TC_M; t += NT) hsc[t] = -2000;
     }
@@ -622,12 +697,22 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
           if (e1 > -2000) atomicMax(hsc + (gbase + 1) * TC_M + row, e1);
         }
       }
-      if (EMU && ((threadIdx.x >> 5) & 3) * 32 < nF) {   // warp-uniform: the warp holds a kept row
+      if (EMU && G == 1 && ((threadIdx.x >> 5) & 3) * 32 < nF) {   // warp-uniform: the warp holds a kept row
         const int lane = threadIdx.x & 31;
         #pragma unroll
         for (int c = 0; c < 32; ++c) {
           const int e = __reduce_max_sync(0xffffffffu, row < nF ? xexp_of(acc.v[c]) : -2000);
           if (lane == c && c0 + c < r && e > -2000) atomicMax(hcol + l * r + c0 + c, e);
+        }
+      } else if (EMU && G > 1 && ((threadIdx.x >> 5) & 3) * 32 < nF) {   // per leaf: the lanes of each leaf reduce
+        const int lane = threadIdx.x & 31;
+        const int lk = row < nF ? (int)growb[row] : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, lk);
+        #pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const int e = __reduce_max_sync(grp, row < nF ? xexp_of(acc.v[c]) : -2000);
+          if (lk >= 0 && lane == __ffs(grp) - 1 && c0 + c < r && e > -2000)
+            atomicMax(hcol + (long)lk * Mr + l * r + c0 + c, e);
         }
       }
       __syncthreads();
@@ -641,9 +726,11 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
     }
   }
   eng.release();
+  if (threadIdx.x < G) {
+    lf.d[F + threadIdx.x] = ld;
+    lf.u[F + threadIdx.x] = zz;
+  }
   if (threadIdx.x == 0) {
-    lf.d[F] = ld;
-    lf.u[F] = zz;
     if (!ok) flag_error(status, ST_TIMEOUT, M, F);
     else if (bad) flag_error(status, ST_NOT_PD, M, F);
   }
@@ -856,7 +943,8 @@ cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nbl
 }
 
 cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int emu, int* status,
-                           cudaStream_t s, const int2* w_par, int n_par, Timer* tm, int leaf_level) {
+                           cudaStream_t s, const int2* w_par, int n_par, Timer* tm, int leaf_level, const int* gcnt,
+                           int lrows) {
   cudaError_t e;
   if (emu) {
     // the chain per parent first (work list: the level-(M-1) regions of every dataset)
@@ -872,13 +960,14 @@ cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, in
         tm->start(1, s, 2, leaf_level);
       }
     }
-    const size_t sm = leaf_tc_smem<true>(nlmax);
+    if (gcnt && !chain_done) return cudaErrorInvalidValue;   // (groups need the per-parent chain kernel)
+    const size_t sm = leaf_tc_smem<true>(std::max(nlmax, chain_done ? lrows : 0));
     if ((e = cudaFuncSetAttribute(leaf_kernel_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-    leaf_kernel_tc<true><<<nblocks, NT, sm, s>>>(d_desc, work, status, chain_done);
+    leaf_kernel_tc<true><<<nblocks, NT, sm, s>>>(d_desc, work, status, chain_done, chain_done ? gcnt : nullptr);
   } else {
     const size_t sm = leaf_tc_smem<false>(nlmax);
     if ((e = cudaFuncSetAttribute(leaf_kernel_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-    leaf_kernel_tc<false><<<nblocks, NT, sm, s>>>(d_desc, work, status, 0);
+    leaf_kernel_tc<false><<<nblocks, NT, sm, s>>>(d_desc, work, status, 0, nullptr);
   }
   return cudaGetLastError();
 }
