@@ -133,6 +133,19 @@ void leaf_groups(const Tables& T, int M, const std::vector<int32_t>& counts, int
   }
 }
 
+// Groups of sibling regions of level m >= 1 for the prior kernel: consecutive
+// children of one level-(m-1) region, at most gmax of them.  Parents [p0, p1).
+void prior_groups(const Tables& T, int m, int gmax, int64_t p0, int64_t p1, int chunk, std::vector<int2>& items,
+                  std::vector<int>& cnt) {
+  for (int64_t p = p0; p < p1; ++p) {
+    const int32_t cf = T.cfirst[m - 1][p], ce = cf + T.ccnt[m - 1][p];
+    for (int32_t c = cf; c < ce; c += gmax) {
+      items.push_back(make_int2(chunk, c));
+      cnt.push_back(std::min(gmax, ce - c));
+    }
+  }
+}
+
 void build_tables(int M, bool prune, const std::vector<int32_t>& counts, Tables& T) {
   T.mort.assign(M + 1, {});
   T.par.assign(M + 1, {});
@@ -282,6 +295,16 @@ struct mra_handle {
   int2* d_gitems = nullptr;
   int* d_gcnt = nullptr;
   int lrows = 0;
+  // emulated form: groups of sibling regions for the prior levels, whole-level
+  // lists (pwo[m], pwn[m]) and (streamed) each chunk's levels > s (pco[g][m],
+  // pcn[g][m]), all in pitems / pcnt; prcap = the rows of the kernel's layout
+  std::vector<int2> pitems;
+  std::vector<int> pcnt;
+  int64_t pwo[mra::MAXL] = {}, pwn[mra::MAXL] = {};
+  std::vector<std::vector<int64_t>> pco, pcn;
+  int2* d_pitems = nullptr;
+  int* d_pcnt = nullptr;
+  int prcap = 0;
   bool have_post = false;
   mra_params last{};
   // batch of datasets
@@ -744,6 +767,30 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
     B.want(&h->d_gitems, std::max<int64_t>(nreg[M], 1));
     B.want(&h->d_gcnt, std::max<int64_t>(nreg[M], 1));
     h->lrows = MRA_MAX_LEAF;
+    // and groups of sibling regions for the prior levels, stacked up to 128 rows
+    const int gmax = std::min(mra::LGRP_MAX, 128 / r);
+    if (gmax > 1) {
+      h->pitems.clear();
+      h->pcnt.clear();
+      for (int m = 1; m < M; ++m) {
+        h->pwo[m] = (int64_t)h->pitems.size();
+        prior_groups(h->tab, m, gmax, 0, nreg[m - 1], 0, h->pitems, h->pcnt);
+        h->pwn[m] = (int64_t)h->pitems.size() - h->pwo[m];
+      }
+      if (s_lvl) {
+        h->pco.assign(h->chunks.size(), std::vector<int64_t>(M + 1, 0));
+        h->pcn.assign(h->chunks.size(), std::vector<int64_t>(M + 1, 0));
+        for (size_t g = 0; g < h->chunks.size(); ++g)
+          for (int m = s_lvl + 1; m < M; ++m) {
+            h->pco[g][m] = (int64_t)h->pitems.size();
+            prior_groups(h->tab, m, gmax, h->chunks[g].c0[m - 1], h->chunks[g].c1[m - 1], (int)g, h->pitems, h->pcnt);
+            h->pcn[g][m] = (int64_t)h->pitems.size() - h->pco[g][m];
+          }
+      }
+      B.want(&h->d_pitems, std::max<size_t>(h->pitems.size(), 1));
+      B.want(&h->d_pcnt, std::max<size_t>(h->pcnt.size(), 1));
+      h->prcap = gmax * r;
+    }
   }
   int2* d_work = nullptr;
   std::vector<int2> work;
@@ -771,6 +818,13 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   if (!work.empty() &&
       (e = cudaMemcpyAsync(d_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, h->stream))) {
     mra_free(h); return cuda_fail(e, "chunk work lists");
+  }
+  if (!h->pitems.empty() &&
+      ((e = cudaMemcpyAsync(h->d_pitems, h->pitems.data(), sizeof(int2) * h->pitems.size(), cudaMemcpyHostToDevice,
+                            h->stream)) ||
+       (e = cudaMemcpyAsync(h->d_pcnt, h->pcnt.data(), sizeof(int) * h->pcnt.size(), cudaMemcpyHostToDevice,
+                            h->stream)))) {
+    mra_free(h); return cuda_fail(e, "prior groups");
   }
   if (!h->gitems.empty() &&
       ((e = cudaMemcpyAsync(h->d_gitems, h->gitems.data(), sizeof(int2) * h->gitems.size(), cudaMemcpyHostToDevice,
@@ -823,12 +877,28 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
         p.n_leaf = (int)(h->goff[g + 1] - h->goff[g]);
         p.lrows = h->lrows;
       }
+      if (h->prcap) {   // the chunk's groups of sibling regions
+        for (int m = s_lvl + 1; m < M; ++m) {
+          p.w_pri[m] = h->d_pitems + h->pco[g][m];
+          p.c_pri[m] = h->d_pcnt + h->pco[g][m];
+          p.n_pri[m] = (int)h->pcn[g][m];
+        }
+        p.rcap = h->prcap;
+      }
       p.n_syrk = (int)(c.c1[M - 1] - c.c0[M - 1]);
       p.w_syrk = at[M - 1];
       p.t_syrk = M * (M + 1) / 2;
     }
   }
   single_plan(h);
+  if (h->prcap) {   // whole-level groups of sibling regions (also the coarse levels of a streamed handle)
+    for (int m = 1; m < M; ++m) {
+      h->plan.w_pri[m] = h->d_pitems + h->pwo[m];
+      h->plan.c_pri[m] = h->d_pcnt + h->pwo[m];
+      h->plan.n_pri[m] = (int)h->pwn[m];
+    }
+    h->plan.rcap = h->prcap;
+  }
   if (h->lrows && !s_lvl) {
     h->plan.w_leaf = h->d_gitems;
     h->plan.c_leaf = h->d_gcnt;
@@ -1795,14 +1865,47 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
       }
     }
   }
+  // and their groups of sibling regions per prior level
+  std::vector<int2> bpi;
+  std::vector<int> bpc;
+  int64_t bpo[mra::MAXL] = {}, bpn[mra::MAXL] = {};
+  int brcap = 0;
+  if (h->cfg.precision == MRA_PREC_EMU) {
+    for (int m = 1; m < h->M; ++m) {
+      bpo[m] = (int64_t)bpi.size();
+      for (int d = 0; d < ndata; ++d) {
+        const mra_handle* q = h->parts[d];
+        if (q->M <= m) continue;
+        if (q->prcap) {
+          brcap = std::max(brcap, q->prcap);
+          for (int64_t k = q->pwo[m]; k < q->pwo[m] + q->pwn[m]; ++k) {
+            bpi.push_back(make_int2(d, q->pitems[k].y));
+            bpc.push_back(q->pcnt[k]);
+          }
+        } else {
+          for (int32_t c = 0; c < q->tab.nreg[m]; ++c) {
+            bpi.push_back(make_int2(d, c));
+            bpc.push_back(1);
+          }
+        }
+      }
+      bpn[m] = (int64_t)bpi.size() - bpo[m];
+    }
+  }
   int2* d_items = nullptr;
   int2* d_bgi = nullptr;
   int* d_bgc = nullptr;
+  int2* d_bpi = nullptr;
+  int* d_bpc = nullptr;
   Arena& A = h->batch;
   A.want(&d_items, std::max<size_t>(items.size(), 1));
   if (!bgi.empty()) {
     A.want(&d_bgi, bgi.size());
     A.want(&d_bgc, bgc.size());
+  }
+  if (!bpi.empty()) {
+    A.want(&d_bpi, bpi.size());
+    A.want(&d_bpc, bpc.size());
   }
   A.want(&h->d_descs, ndata);
   A.want(&h->d_roots, 2 * (size_t)ndata);
@@ -1823,6 +1926,10 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
                        (e = cudaMemcpy(d_bgc, bgc.data(), sizeof(int) * bgc.size(), cudaMemcpyHostToDevice)))) {
     mra_free(h); return cuda_fail(e, "leaf groups");
   }
+  if (!bpi.empty() && ((e = cudaMemcpy(d_bpi, bpi.data(), sizeof(int2) * bpi.size(), cudaMemcpyHostToDevice)) ||
+                       (e = cudaMemcpy(d_bpc, bpc.data(), sizeof(int) * bpc.size(), cudaMemcpyHostToDevice)))) {
+    mra_free(h); return cuda_fail(e, "prior groups");
+  }
   mra::Plan& p = h->plan;
   p = mra::Plan();
   p.maxM = maxM;
@@ -1839,6 +1946,14 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
     p.w_leaf = d_bgi;
     p.c_leaf = d_bgc;
     p.lrows = h->lrows;
+  }
+  if (!bpi.empty() && brcap) {
+    for (int m = 1; m < maxM; ++m) {
+      p.w_pri[m] = d_bpi + bpo[m];
+      p.c_pri[m] = d_bpc + bpo[m];
+      p.n_pri[m] = (int)bpn[m];
+    }
+    p.rcap = brcap;
   }
   p.n_syrk = lists[li].first; p.w_syrk = d_items + lists[li].second; ++li;
   for (int d = 0; d < ndata; ++d) p.t_syrk = std::max(p.t_syrk, h->parts[d]->M * (h->parts[d]->M + 1) / 2);

@@ -592,7 +592,9 @@ __device__ inline void chol_smem(double* A, int n, int lda, int* bad) {
 // trinv_smem does (the same operations per entry, so a block's factors are
 // those of the single-matrix routines).  The steps of all blocks run together,
 // so the barriers are those of the largest block alone.  pv: nb doubles of
-// shared memory (the blocks' pivots), tmp: seg[nb] doubles.
+// shared memory (the blocks' pivots), tmp: seg[nb] doubles.  STK (stacked
+// storage): row i holds only its block's columns, entry (i, k) of block b at
+// A[i lda + k - seg[b]], lda >= the largest block.
 constexpr int LGRP_MAX = 4;        // leaves of one group (the children of one parent)
 
 __device__ __forceinline__ int seg_block(const int* seg, int nb, int i) {   // block of row i
@@ -601,17 +603,18 @@ __device__ __forceinline__ int seg_block(const int* seg, int nb, int i) {   // b
   return b;
 }
 
+template <bool STK = false>
 __device__ inline void chol_seg(double* A, int lda, const int* seg, int nb, int* bad, double* pv) {
   __syncthreads();
   int nmax = 0;
   for (int b = 0; b < nb; ++b) nmax = max(nmax, seg[b + 1] - seg[b]);
   if (threadIdx.x < nb && seg[threadIdx.x + 1] > seg[threadIdx.x]) {
-    const int s0 = seg[threadIdx.x];
-    const double d = A[s0 * lda + s0];
+    const int s0 = seg[threadIdx.x], cs = STK ? s0 : 0;
+    const double d = A[s0 * lda + s0 - cs];
     const bool ok = d > 0.0;
     const double rs = ok ? rsqrt(d) : 1.0;
     if (!ok) *bad = 1;
-    A[s0 * lda + s0] = ok ? d * rs : 1.0;
+    A[s0 * lda + s0 - cs] = ok ? d * rs : 1.0;
     pv[threadIdx.x] = rs;
   }
   __syncthreads();
@@ -628,8 +631,8 @@ __device__ inline void chol_seg(double* A, int lda, const int* seg, int nb, int*
         u -= m;
         ++b;
       }
-      const int s0 = seg[b];
-      A[(s0 + j + 1 + u) * lda + s0 + j] *= pv[b];
+      const int s0 = seg[b], cs = STK ? s0 : 0;
+      A[(s0 + j + 1 + u) * lda + s0 + j - cs] *= pv[b];
     }
     __syncthreads();
     for (int t = threadIdx.x; t < tri; t += NT) {   // trailing lower triangles; element 0: the next pivot
@@ -640,35 +643,43 @@ __device__ inline void chol_seg(double* A, int lda, const int* seg, int nb, int*
       }
       int ii, kk;
       tri_decode(u, ii, kk);
-      const int s0 = seg[b], jc = s0 + j, i = jc + 1 + ii, k = jc + 1 + kk;
-      const double v = fma(-A[i * lda + jc], A[k * lda + jc], A[i * lda + k]);
+      const int s0 = seg[b], cs = STK ? s0 : 0, jc = s0 + j, i = jc + 1 + ii, k = jc + 1 + kk;
+      const double v = fma(-A[i * lda + jc - cs], A[k * lda + jc - cs], A[i * lda + k - cs]);
       if (u == 0) {
         const bool ok = v > 0.0;
         const double rs = ok ? rsqrt(v) : 1.0;
         if (!ok) *bad = 1;
-        A[i * lda + k] = ok ? v * rs : 1.0;
+        A[i * lda + k - cs] = ok ? v * rs : 1.0;
         pv[b] = rs;
       } else {
-        A[i * lda + k] = v;
+        A[i * lda + k - cs] = v;
       }
     }
     __syncthreads();
   }
   const int n = seg[nb];
-  for (int t = threadIdx.x; t < n * n; t += NT) {
-    const int i = t / n, k = t - i * n;
-    if (k > i || k < seg[seg_block(seg, nb, i)]) A[i * lda + k] = 0.0;
+  if (STK) {                                   // (stacked: row i holds its block's columns only, lda of them)
+    for (int t = threadIdx.x; t < n * lda; t += NT) {
+      const int i = t / lda, k = t - i * lda;
+      if (k > i - seg[seg_block(seg, nb, i)]) A[t] = 0.0;
+    }
+  } else {
+    for (int t = threadIdx.x; t < n * n; t += NT) {
+      const int i = t / n, k = t - i * n;
+      if (k > i || k < seg[seg_block(seg, nb, i)]) A[i * lda + k] = 0.0;
+    }
   }
   __syncthreads();
 }
 
+template <bool STK = false>
 __device__ inline void trinv_seg(double* A, int lda, const int* seg, int nb, double* tmp, double* pv) {
   __syncthreads();
   int nmax = 0;
   for (int b = 0; b < nb; ++b) nmax = max(nmax, seg[b + 1] - seg[b]);
   if (threadIdx.x < nb && seg[threadIdx.x + 1] > seg[threadIdx.x]) {
     const int s0 = seg[threadIdx.x];
-    pv[threadIdx.x] = 1.0 / A[s0 * lda + s0];
+    pv[threadIdx.x] = 1.0 / A[s0 * lda + (STK ? 0 : s0)];
   }
   __syncthreads();
   for (int k = 0; k < nmax; ++k) {
@@ -689,14 +700,14 @@ __device__ inline void trinv_seg(double* A, int lda, const int* seg, int nb, dou
         u -= c;
         ++b;
       }
-      const int s0 = seg[b], gk = s0 + k;
-      if (u <= k) A[gk * lda + s0 + u] = u < k ? A[gk * lda + s0 + u] * pv[b] : pv[b];
-      else tmp[s0 + u] = A[(s0 + u) * lda + gk];
+      const int s0 = seg[b], cs = STK ? s0 : 0, gk = s0 + k;
+      if (u <= k) A[gk * lda + s0 + u - cs] = u < k ? A[gk * lda + s0 + u - cs] * pv[b] : pv[b];
+      else tmp[s0 + u] = A[(s0 + u) * lda + gk - cs];
     }
     __syncthreads();
     if (threadIdx.x < nb) {   // the next step's reciprocals (diagonal entries phase 2 does not write)
-      const int s0 = seg[threadIdx.x];
-      if (k + 1 < seg[threadIdx.x + 1] - s0) pv[threadIdx.x] = 1.0 / A[(s0 + k + 1) * lda + s0 + k + 1];
+      const int s0 = seg[threadIdx.x], cs = STK ? s0 : 0;
+      if (k + 1 < seg[threadIdx.x + 1] - s0) pv[threadIdx.x] = 1.0 / A[(s0 + k + 1) * lda + s0 + k + 1 - cs];
     }
     // phase 2: X_ij -= L_ik X_kj for i > k, j <= k, within every block
     const int w = k + 1;
@@ -707,9 +718,9 @@ __device__ inline void trinv_seg(double* A, int lda, const int* seg, int nb, dou
         u -= c;
         ++b;
       }
-      const int s0 = seg[b], ii = u / w, j = u - ii * w, i = s0 + k + 1 + ii;
-      const double x0 = j == k ? 0.0 : A[i * lda + s0 + j];
-      A[i * lda + s0 + j] = fma(-tmp[i], A[(s0 + k) * lda + s0 + j], x0);
+      const int s0 = seg[b], cs = STK ? s0 : 0, ii = u / w, j = u - ii * w, i = s0 + k + 1 + ii;
+      const double x0 = j == k ? 0.0 : A[i * lda + s0 + j - cs];
+      A[i * lda + s0 + j - cs] = fma(-tmp[i], A[(s0 + k) * lda + s0 + j - cs], x0);
     }
     __syncthreads();
   }

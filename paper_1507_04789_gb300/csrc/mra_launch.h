@@ -66,6 +66,13 @@ struct Plan {
   // n_leaf counts groups), laid out for lrows rows; null: one leaf per item
   const int* c_leaf = nullptr;
   int lrows = 0;
+  // prior levels on the tensor cores: groups of sibling regions (c_pri[m][b]
+  // regions from compact id w_pri[m][b].y; n_pri[m] groups), stacked at most
+  // rcap rows; null: the level's regions one by one (w_lvl, n_lvl)
+  const int2* w_pri[MAXL] = {};
+  const int* c_pri[MAXL] = {};
+  int n_pri[MAXL] = {};
+  int rcap = 0;
   const int2* w_syrk = nullptr;
   int n_syrk = 0, t_syrk = 1;
 };
@@ -81,7 +88,7 @@ size_t leaf_smem_bytes(int r, int nlmax);
 // Mixed-precision prior level and leaf pass (tensor cores, mra_mixed.cu).
 // emu = 1: FP64-grade bf16-slice emulation engine; 0: 3xTF32.
 cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nblocks, int emu, int* status,
-                            cudaStream_t s);
+                            cudaStream_t s, const int* gcnt = nullptr, int rcap = 0);
 cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int emu, int* status,
                            cudaStream_t s, const int2* w_par = nullptr, int n_par = 0, Timer* tm = nullptr,
                            int leaf_level = -1, const int* gcnt = nullptr, int lrows = 0);

@@ -538,7 +538,13 @@ cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaS
     if (pl.n_lvl[m] == 0) continue;
     tm->start(0, s, 0, m);
     if (pl.mixed) {
-      if ((e = launch_prior_tc(m, d_desc, pl.w_lvl[m], pl.n_lvl[m], pl.mixed == 2, status, s))) return e;
+      if (pl.c_pri[m]) {
+        if ((e = launch_prior_tc(m, d_desc, pl.w_pri[m], pl.n_pri[m], pl.mixed == 2, status, s, pl.c_pri[m],
+                                 pl.rcap)))
+          return e;
+      } else if ((e = launch_prior_tc(m, d_desc, pl.w_lvl[m], pl.n_lvl[m], pl.mixed == 2, status, s))) {
+        return e;
+      }
     } else {
       MRA_LAUNCH(tile, prior_level_kernel, pl.n_lvl[m], prior_smem(tile), s, m, d_desc, pl.w_lvl[m], status);
     }

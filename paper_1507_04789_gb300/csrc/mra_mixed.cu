@@ -66,66 +66,100 @@ struct Engine<true> {
 
 constexpr int EM_GMAX = 6;   // 128-column groups of a row of at most MRA_MAX_M x MAX_R_DEV = 768 columns
 
+// Prior of level m on the tensor cores.  gcnt (else null): the work item is a
+// group of gcnt[b] sibling regions with consecutive compact ids from it.i
+// (children of one parent, so with the same ancestors), stacked G r <= rcap
+// rows deep: their chain blocks are one product per ancestor level (the
+// ancestor's V and L^{-1} split once for all of them), and their W blocks are
+// factorised and inverted block by block (chol_seg / trinv_seg, stacked rows).
 template <bool EMU>
 __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* __restrict__ D,
-                                                             const int2* __restrict__ work, int* status) {
+                                                             const int2* __restrict__ work, int* status,
+                                                             const int* __restrict__ gcnt, int rcap) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int fail, bad;
   __shared__ int rexp[EMU ? EM_REXP : 1], cexp[EMU ? EM_CEXP : 1];
-  // emulation: row scales of this region's V rows per 128-column group, and of the current X^l block
-  __shared__ int vsc[EMU ? EM_GMAX * MAX_R_DEV : 1], xsc[EMU ? MAX_R_DEV : 1];
+  // emulation: row scales of the stacked V rows per 128-column group, and of the current X^l block
+  __shared__ int vsc[EMU ? EM_GMAX * TC_M : 1], xsc[EMU ? TC_M : 1];
   // c0_fast on two knot grids: squared scaled offsets between their columns and
-  // between their rows, variance factors of the columns (sigma2 in pgp), and the
-  // column and row of every knot
-  __shared__ double pdx[C0_GMAX * C0_GMAX], pdy[C0_GMAX * C0_GMAX], pgp[C0_GMAX], pgq[C0_GMAX];
+  // between their rows (per stacked region), variance factors of the columns
+  // (sigma2 in pgp), and the column and row of every knot
+  __shared__ double pdx[LGRP_MAX * C0_GMAX * C0_GMAX], pdy[LGRP_MAX * C0_GMAX * C0_GMAX];
+  __shared__ double pgp[LGRP_MAX * C0_GMAX], pgq[LGRP_MAX * C0_GMAX];
   __shared__ unsigned char qcol[MAX_R_DEV], qrow[MAX_R_DEV];
+  __shared__ int gseg[LGRP_MAX + 1];
+  __shared__ double gpv[LGRP_MAX];
   const Item it = work_item(work);
   const Desc& ds = D[it.d];
   const Shape sh = ds.sh;
   const Cov cv = ds.cv;
   const LevelState& st = ds.st;
   const int r = sh.r, mr = m * r;
+  const int G = gcnt ? gcnt[blockIdx.x] : 1;
+  const int R = G * r;                         // stacked rows
   const int gx = sh.gx, gy = sh.gy;
   const bool fast = c0_fast_ok(cv, gx, gy);
   const double c0s = c0_scale(cv);
+  if (R > rcap || R > TC_M) {                  // (a group larger than the layout: never formed by the host)
+    if (threadIdx.x == 0) flag_error(status, ST_LIMIT, m, it.i);
+    return;
+  }
   for (int q = threadIdx.x; q < r; q += NT) {
     qcol[q] = (unsigned char)(q % gx);
     qrow[q] = (unsigned char)(q / gx);
   }
+  if (threadIdx.x <= G) gseg[threadIdx.x] = threadIdx.x * r;
   if (EMU)
-    for (int t = threadIdx.x; t < EM_GMAX * MAX_R_DEV; t += NT) vsc[t] = -2000;
-  const long i = it.i;
-  double* qx = reinterpret_cast<double*>(dsm + Engine<EMU>::STAGE);
-  double* qy = qx + MAX_R_DEV;
-  double* ax = qy + MAX_R_DEV;
+    for (int t = threadIdx.x; t < EM_GMAX * TC_M; t += NT) vsc[t] = -2000;
+  const long i = it.i;                          // the first region of the group
+  double* qx = reinterpret_cast<double*>(dsm + Engine<EMU>::STAGE);   // the group's knots, rcap each
+  double* qy = qx + rcap;
+  double* ax = qy + rcap;
   double* ay = ax + MAX_R_DEV;
-  double* tmp = ay + MAX_R_DEV;
-  double* W = tmp + MAX_R_DEV;                 // r x (r + 1)
-  // offsets between the knot grid (qx, qy) and the grid (bx, by) (all threads;
-  // the caller synchronises before and after)
-  auto grid_offsets = [&](const double* bx, const double* by) {
-    for (int t = threadIdx.x; t < gx * gx + gy * gy; t += NT) {
-      if (t < gx * gx) {
-        const double d = c0s * (qx[t / gx] - bx[t % gx]);
-        pdx[t] = d * d;
+  double* tmp = ay + MAX_R_DEV;                 // rcap
+  double* W = tmp + rcap;                       // rcap x (r + 1): region g's block in rows g r .. g r + r - 1
+  // offsets between every stacked region's knot grid (qx, qy) + g r and the grid
+  // (bx, by), or (self) the region's own grid (all threads; the caller
+  // synchronises before and after)
+  const int gsz = gx * gx + gy * gy;
+  auto grid_offsets = [&](const double* bx, const double* by, bool self) {
+    for (int t = threadIdx.x; t < G * gsz; t += NT) {
+      const int g = t / gsz, u = t - g * gsz;
+      const double* ox = qx + g * r;
+      const double* oy = qy + g * r;
+      const double* px = self ? ox : bx;
+      const double* py = self ? oy : by;
+      if (u < gx * gx) {
+        const double d = c0s * (ox[u / gx] - px[u % gx]);
+        pdx[g * C0_GMAX * C0_GMAX + u] = d * d;
       } else {
-        const int u = t - gx * gx;
-        const double d = c0s * (qy[(u / gy) * gx] - by[(u % gy) * gx]);
-        pdy[u] = d * d;
+        const int v = u - gx * gx;
+        const double d = c0s * (oy[(v / gy) * gx] - py[(v % gy) * gx]);
+        pdy[g * C0_GMAX * C0_GMAX + v] = d * d;
       }
     }
-    for (int c = threadIdx.x; c < gx; c += NT) {
-      pgp[c] = cv.sigma2 * c0_vfac(cv, qx[c]);
-      pgq[c] = c0_vfac(cv, bx[c]);
+    for (int t = threadIdx.x; t < G * gx; t += NT) {
+      const int g = t / gx, c = t - g * gx;
+      pgp[t] = cv.sigma2 * c0_vfac(cv, qx[g * r + c]);
+      pgq[t] = c0_vfac(cv, self ? qx[g * r + c] : bx[c]);
     }
+  };
+  // C0 between row qi of the stack (region qi / r) and knot qj of the grid the offsets were formed for
+  auto c0_at = [&](int qi, int qj, const double* bx, const double* by) {
+    const int g = qi / r, ql = qi - g * r;
+    const int ci = qcol[ql], cj = qcol[qj];
+    return fast ? c0_fast(cv.family, pdx[g * C0_GMAX * C0_GMAX + ci * gx + cj] +
+                                         pdy[g * C0_GMAX * C0_GMAX + qrow[ql] * gy + qrow[qj]],
+                          cv.nonstat ? pgp[g * gx + ci] * pgq[g * gx + cj] : cv.sigma2)
+                : cov0(cv, qx[qi], qy[qi], bx[qj], by[qj]);
   };
   if (threadIdx.x == 0) bad = 0;
   Engine<EMU> eng;
   eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
-  load_knots(sh.bbox, m, st.mort[m][i], sh.gx, sh.gy, qx, qy);
-  double* Vrow = st.V[m] + i * (long)r * mr;
+  for (int g = 0; g < G; ++g) load_knots(sh.bbox, m, st.mort[m][i + g], sh.gx, sh.gy, qx + g * r, qy + g * r);
+  double* Vrow = st.V[m] + i * (long)r * mr;   // the group's rows are consecutive
   TcAcc acc;
   bool ok = true;
   const int row = acc.row(), c0 = acc.col0();
@@ -135,20 +169,17 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
     load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
     const double* Vanc = st.V[l] + a * (long)r * (l * r);
     if (EMU)
-      for (int t = threadIdx.x; t < MAX_R_DEV; t += NT) xsc[t] = -2000;
+      for (int t = threadIdx.x; t < TC_M; t += NT) xsc[t] = -2000;
     __syncthreads();
     if (fast) {
-      grid_offsets(ax, ay);
+      grid_offsets(ax, ay, false);
       __syncthreads();
     }
     // C0(Q_R, Q_{R_l}) into block l, spread over every warp (the FP64 pipe of
     // every SM sub-partition); the product below reads only blocks < l
-    for (int t = threadIdx.x; t < r * r; t += NT) {
+    for (int t = threadIdx.x; t < R * r; t += NT) {
       const int qi = t / r, qj = t - qi * r;
-      const int ci = qcol[qi], cj = qcol[qj];
-      const double v = fast ? c0_fast(cv.family, pdx[ci * gx + cj] + pdy[qrow[qi] * gy + qrow[qj]],
-                                      cv.nonstat ? pgp[ci] * pgq[cj] : cv.sigma2)
-                            : cov0(cv, qx[qi], qy[qi], ax[qj], ay[qj]);
+      const double v = c0_at(qi, qj, ax, ay);
       Vrow[(long)qi * mr + l * r + qj] = v;
       if (EMU && l == 0) atomicMax(xsc + qi, xexp_of(v));
     }
@@ -156,9 +187,9 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
     __syncthreads();
     if (l > 0) {
       const int* vsa = EMU ? st.vexp[l] + a * (long)((l * r + 127) / 128) * r : nullptr;
-      ok = eng.mma(acc, Vrow, mr, 1, r, Vanc, l * r, 1, r, l * r, vsc, MAX_R_DEV, vsa, r);
+      ok = eng.mma(acc, Vrow, mr, 1, R, Vanc, l * r, 1, r, l * r, vsc, TC_M, vsa, r);
       if (!ok) break;
-      if (row < r) {
+      if (row < R) {
         int e = -2000;
         #pragma unroll
         for (int c = 0; c < 32; ++c) {
@@ -174,10 +205,10 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
     }
     __syncthreads();
     acc.zero();
-    ok = eng.mma(acc, Vrow + l * r, mr, 1, r, st.Li[l] + a * (long)r * r, r, 1, r, r, xsc, 0,
+    ok = eng.mma(acc, Vrow + l * r, mr, 1, R, st.Li[l] + a * (long)r * r, r, 1, r, r, xsc, 0,
                  EMU ? st.liexp[l] + a * r : nullptr, 0);
     if (!ok) break;
-    if (row < r) {
+    if (row < R) {
       int e0 = -2000, e1 = -2000;       // a thread's 32 columns touch at most two groups
       const int gbase = (l * r + c0) / 128;
       #pragma unroll
@@ -191,57 +222,68 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
         }
       }
       if (EMU) {
-        atomicMax(vsc + gbase * MAX_R_DEV + row, e0);
-        if (e1 > -2000) atomicMax(vsc + (gbase + 1) * MAX_R_DEV + row, e1);
+        atomicMax(vsc + gbase * TC_M + row, e0);
+        if (e1 > -2000) atomicMax(vsc + (gbase + 1) * TC_M + row, e1);
       }
     }
   }
   __syncthreads();                             // knots loaded, chain blocks written
   const int ldw = r + 1;
   if (fast) {
-    grid_offsets(qx, qy);
+    grid_offsets(qx, qy, true);
     __syncthreads();
   }
-  // lower triangle of C0(Q_R, Q_R), every warp
-  for (int t = threadIdx.x; t < r * (r + 1) / 2; t += NT) {
+  // lower triangle of every region's C0(Q_R, Q_R), every warp
+  const int T1 = r * (r + 1) / 2;
+  for (int t = threadIdx.x; t < G * T1; t += NT) {
+    const int g = t / T1;
     int qi, qj;
-    tri_decode(t, qi, qj);
-    const int ci = qcol[qi], cj = qcol[qj];
-    W[qi * ldw + qj] = fast ? c0_fast(cv.family, pdx[ci * gx + cj] + pdy[qrow[qi] * gy + qrow[qj]],
-                                      cv.nonstat ? pgp[ci] * pgq[cj] : cv.sigma2)
-                            : cov0(cv, qx[qi], qy[qi], qx[qj], qy[qj]);
+    tri_decode(t - g * T1, qi, qj);
+    W[(g * r + qi) * ldw + qj] = c0_at(g * r + qi, qj, qx + g * r, qy + g * r);
   }
   __syncthreads();
-  if (ok) {
+  // W_R -= V_R V_R' of every region (the diagonal blocks of the stacked product)
+  const int nct = (R + TC_N - 1) / TC_N;
+  for (int ct = 0; ct < nct && ok && m > 0; ++ct) {
+    const int ncol = min(TC_N, R - ct * TC_N);
     acc.zero();
-    if (m > 0) ok = eng.mma(acc, Vrow, mr, 1, r, Vrow, mr, 1, r, mr, vsc, MAX_R_DEV, vsc, MAX_R_DEV);
-  }
-  if (ok) {
-    if (m > 0 && row < r)
+    ok = eng.mma(acc, Vrow, mr, 1, R, Vrow + (long)ct * TC_N * mr, mr, 1, ncol, mr, vsc, TC_M, vsc + ct * TC_N,
+                 TC_M);
+    if (!ok) break;
+    if (row < R) {
+      const int rb = (row / r) * r;           // the row's block
       #pragma unroll
       for (int c = 0; c < 32; ++c) {
-        const int col = c0 + c;
-        if (col <= row) W[row * ldw + col] -= acc.v[c];
+        const int oj = ct * TC_N + c0 + c;
+        if (c0 + c < ncol && oj >= rb && oj <= row) W[row * ldw + oj - rb] -= acc.v[c];
       }
-    chol_smem(W, r, ldw, &bad);
+    }
+    __syncthreads();
+  }
+  if (ok) {
+    if (G == 1) chol_smem(W, r, ldw, &bad);
+    else chol_seg<true>(W, ldw, gseg, G, &bad, gpv);
     if (st.L[m]) {
       double* Lr = st.L[m] + i * (long)r * r;
-      for (int t = threadIdx.x; t < r * r; t += NT) Lr[t] = W[(t / r) * ldw + (t % r)];
+      for (int t = threadIdx.x; t < R * r; t += NT) Lr[t] = W[(t / r) * ldw + (t % r)];
       __syncthreads();
     }
-    trinv_smem(W, r, ldw, tmp);
+    if (G == 1) trinv_smem(W, r, ldw, tmp);
+    else trinv_seg<true>(W, ldw, gseg, G, tmp, gpv);
     double* Li = st.Li[m] + i * (long)r * r;
-    for (int t = threadIdx.x; t < r * r; t += NT) Li[t] = W[(t / r) * ldw + (t % r)];
+    for (int t = threadIdx.x; t < R * r; t += NT) Li[t] = W[(t / r) * ldw + (t % r)];
     if (EMU) {   // row scales of V_R and L_R^{-1} for the descendants' products
-      for (int t = threadIdx.x; t < r; t += NT) {
+      for (int t = threadIdx.x; t < R; t += NT) {
         int e = -2000;
-        for (int k = 0; k <= t; ++k) e = max(e, xexp_of(W[t * ldw + k]));
+        for (int k = 0; k <= t % r; ++k) e = max(e, xexp_of(W[t * ldw + k]));
         st.liexp[m][i * r + t] = e;
       }
       if (m > 0) {
         const int ng = (mr + 127) / 128;
-        for (int t = threadIdx.x; t < ng * r; t += NT)
-          st.vexp[m][(i * ng + t / r) * (long)r + t % r] = vsc[(t / r) * MAX_R_DEV + t % r];
+        for (int t = threadIdx.x; t < ng * R; t += NT) {   // region g = q / r, group t / R, row q % r
+          const int grp = t / R, q = t - grp * R, g = q / r;
+          st.vexp[m][((i + g) * ng + grp) * (long)r + (q - g * r)] = vsc[grp * TC_M + q];
+        }
       }
     }
   }
@@ -908,8 +950,9 @@ __global__ void __launch_bounds__(NT) aggregate_kernel_em(int m, const Desc* __r
 
 
 template <bool EMU>
-static size_t prior_tc_smem() {
-  const size_t b = Engine<EMU>::STAGE + sizeof(double) * (5 * MAX_R_DEV + MAX_R_DEV * (MAX_R_DEV + 1));
+static size_t prior_tc_smem(int rcap) {     // knots (2 rcap), ancestor knots, scratch (rcap), W (rcap x (r + 1))
+  const size_t b = Engine<EMU>::STAGE + sizeof(double) * (3 * (size_t)rcap + 2 * MAX_R_DEV +
+                                                          (size_t)rcap * (MAX_R_DEV + 1));
   return EMU ? std::max(b, EM_SOLO_SMEM) : b;
 }
 template <bool EMU>
@@ -926,18 +969,20 @@ size_t leaf_tc_smem_bytes(int nlmax, int emu) {
 
 
 cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nblocks, int emu, int* status,
-                            cudaStream_t s) {
+                            cudaStream_t s, const int* gcnt, int rcap) {
   cudaError_t e;
+  rcap = gcnt ? std::max(rcap, MAX_R_DEV) : MAX_R_DEV;
+  if (rcap > TC_M) return cudaErrorInvalidValue;
   if (emu) {
-    const size_t sm = prior_tc_smem<true>();
+    const size_t sm = prior_tc_smem<true>(rcap);
     if ((e = cudaFuncSetAttribute(prior_level_kernel_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
       return e;
-    prior_level_kernel_tc<true><<<nblocks, NT, sm, s>>>(m, d_desc, work, status);
+    prior_level_kernel_tc<true><<<nblocks, NT, sm, s>>>(m, d_desc, work, status, gcnt, rcap);
   } else {
-    const size_t sm = prior_tc_smem<false>();
+    const size_t sm = prior_tc_smem<false>(rcap);
     if ((e = cudaFuncSetAttribute(prior_level_kernel_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
       return e;
-    prior_level_kernel_tc<false><<<nblocks, NT, sm, s>>>(m, d_desc, work, status);
+    prior_level_kernel_tc<false><<<nblocks, NT, sm, s>>>(m, d_desc, work, status, gcnt, rcap);
   }
   return cudaGetLastError();
 }
