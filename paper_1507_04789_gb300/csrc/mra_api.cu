@@ -146,6 +146,29 @@ void prior_groups(const Tables& T, int m, int gmax, int64_t p0, int64_t p1, int 
   }
 }
 
+// Groups of sibling level-(M-1) regions for the leaf chain kernel: consecutive
+// children of one level-(M-2) region q, q in [p0, p1), at most LGRP_MAX of them
+// and 128 observations in all (obs_pref: prefix sums of the leaf counts by
+// Morton id); a region of more than 128 is a group of its own.
+void chain_groups(const Tables& T, int M, const std::vector<int64_t>& obs_pref, int64_t p0, int64_t p1, int chunk,
+                  std::vector<int2>& items, std::vector<int>& cnt) {
+  auto rows = [&](int32_t P) {
+    const int64_t pm = T.mort[M - 1][P];
+    return obs_pref[4 * pm + 4] - obs_pref[4 * pm];
+  };
+  for (int64_t q = p0; q < p1; ++q) {
+    const int32_t cf = T.cfirst[M - 2][q], ce = cf + T.ccnt[M - 2][q];
+    for (int32_t P = cf; P < ce;) {
+      int g = 1;
+      int64_t n = rows(P);
+      while (P + g < ce && g < mra::LGRP_MAX && n + rows(P + g) <= 128) n += rows(P + g++);
+      items.push_back(make_int2(chunk, P));
+      cnt.push_back(g);
+      P += g;
+    }
+  }
+}
+
 void build_tables(int M, bool prune, const std::vector<int32_t>& counts, Tables& T) {
   T.mort.assign(M + 1, {});
   T.par.assign(M + 1, {});
@@ -305,6 +328,14 @@ struct mra_handle {
   int2* d_pitems = nullptr;
   int* d_pcnt = nullptr;
   int prcap = 0;
+  // and of sibling level-(M-1) regions for the leaf chain (one 128-row tile each),
+  // whole (cwo, cwn) and per chunk (cco[g], ccn[g]), in citems / ccnt
+  std::vector<int2> citems;
+  std::vector<int> ccnt;
+  int64_t cwo = 0, cwn = 0;
+  std::vector<int64_t> cco, ccn;
+  int2* d_citems = nullptr;
+  int* d_ccnt = nullptr;
   bool have_post = false;
   mra_params last{};
   // batch of datasets
@@ -791,6 +822,32 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
       B.want(&h->d_pcnt, std::max<size_t>(h->pcnt.size(), 1));
       h->prcap = gmax * r;
     }
+    // and groups of sibling level-(M-1) regions for the leaf chain
+    h->citems.clear();
+    h->ccnt.clear();
+    if (M >= 2) {
+      h->cwo = 0;
+      chain_groups(h->tab, M, obs_pref, 0, nreg[M - 2], 0, h->citems, h->ccnt);
+      h->cwn = (int64_t)h->citems.size();
+      if (s_lvl) {
+        h->cco.assign(h->chunks.size(), 0);
+        h->ccn.assign(h->chunks.size(), 0);
+        for (size_t g = 0; g < h->chunks.size(); ++g) {
+          h->cco[g] = (int64_t)h->citems.size();
+          if (M - 1 > s_lvl) {
+            chain_groups(h->tab, M, obs_pref, h->chunks[g].c0[M - 2], h->chunks[g].c1[M - 2], (int)g, h->citems,
+                         h->ccnt);
+          } else {   // (the chunk is one level-(M-1) region)
+            h->citems.push_back(make_int2((int)g, (int)h->chunks[g].c0[M - 1]));
+            h->ccnt.push_back(1);
+          }
+          h->ccn[g] = (int64_t)h->citems.size() - h->cco[g];
+        }
+      }
+      // (room for one group per region: mra_update regroups for the new occupancy)
+      B.want(&h->d_citems, std::max<size_t>(h->citems.size(), (size_t)nreg[M - 1]));
+      B.want(&h->d_ccnt, std::max<size_t>(h->ccnt.size(), (size_t)nreg[M - 1]));
+    }
   }
   int2* d_work = nullptr;
   std::vector<int2> work;
@@ -818,6 +875,13 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   if (!work.empty() &&
       (e = cudaMemcpyAsync(d_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice, h->stream))) {
     mra_free(h); return cuda_fail(e, "chunk work lists");
+  }
+  if (!h->citems.empty() &&
+      ((e = cudaMemcpyAsync(h->d_citems, h->citems.data(), sizeof(int2) * h->citems.size(), cudaMemcpyHostToDevice,
+                            h->stream)) ||
+       (e = cudaMemcpyAsync(h->d_ccnt, h->ccnt.data(), sizeof(int) * h->ccnt.size(), cudaMemcpyHostToDevice,
+                            h->stream)))) {
+    mra_free(h); return cuda_fail(e, "chain groups");
   }
   if (!h->pitems.empty() &&
       ((e = cudaMemcpyAsync(h->d_pitems, h->pitems.data(), sizeof(int2) * h->pitems.size(), cudaMemcpyHostToDevice,
@@ -877,6 +941,11 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
         p.n_leaf = (int)(h->goff[g + 1] - h->goff[g]);
         p.lrows = h->lrows;
       }
+      if (!h->citems.empty()) {   // the chunk's groups for the leaf chain
+        p.w_chn = h->d_citems + h->cco[g];
+        p.c_chn = h->d_ccnt + h->cco[g];
+        p.n_chn = (int)h->ccn[g];
+      }
       if (h->prcap) {   // the chunk's groups of sibling regions
         for (int m = s_lvl + 1; m < M; ++m) {
           p.w_pri[m] = h->d_pitems + h->pco[g][m];
@@ -898,6 +967,11 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
       h->plan.n_pri[m] = (int)h->pwn[m];
     }
     h->plan.rcap = h->prcap;
+  }
+  if (!h->citems.empty() && !s_lvl) {
+    h->plan.w_chn = h->d_citems + h->cwo;
+    h->plan.c_chn = h->d_ccnt + h->cwo;
+    h->plan.n_chn = (int)h->cwn;
   }
   if (h->lrows && !s_lvl) {
     h->plan.w_leaf = h->d_gitems;
@@ -1177,6 +1251,22 @@ int mra_update(mra_handle* h, const double* locs, const double* y, int where) {
         (e = cudaStreamSynchronize(h->stream)))
       return cuda_fail(e, "leaf groups");
     h->plan.n_leaf = (int)h->gitems.size();
+  }
+  if (!h->citems.empty()) {   // and the leaf chain's groups
+    std::vector<int64_t> obs_pref(h->leaf_counts.size() + 1, 0);
+    for (size_t f = 0; f < h->leaf_counts.size(); ++f) obs_pref[f + 1] = obs_pref[f] + h->leaf_counts[f];
+    h->citems.clear();
+    h->ccnt.clear();
+    chain_groups(h->tab, h->M, obs_pref, 0, h->tab.nreg[h->M - 2], 0, h->citems, h->ccnt);
+    h->cwo = 0;
+    h->cwn = (int64_t)h->citems.size();
+    if ((e = cudaMemcpyAsync(h->d_citems, h->citems.data(), sizeof(int2) * h->citems.size(), cudaMemcpyHostToDevice,
+                             h->stream)) ||
+        (e = cudaMemcpyAsync(h->d_ccnt, h->ccnt.data(), sizeof(int) * h->ccnt.size(), cudaMemcpyHostToDevice,
+                             h->stream)) ||
+        (e = cudaStreamSynchronize(h->stream)))
+      return cuda_fail(e, "chain groups");
+    h->plan.n_chn = (int)h->cwn;
   }
   return MRA_OK;
 }
@@ -1892,11 +1982,33 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
       bpn[m] = (int64_t)bpi.size() - bpo[m];
     }
   }
+  // and their groups for the leaf chain
+  std::vector<int2> bci;
+  std::vector<int> bcc;
+  if (h->cfg.precision == MRA_PREC_EMU) {
+    for (int d = 0; d < ndata; ++d) {
+      const mra_handle* q = h->parts[d];
+      if (q->M == 0) continue;
+      if (!q->citems.empty()) {
+        for (size_t k = 0; k < q->citems.size(); ++k) {
+          bci.push_back(make_int2(d, q->citems[k].y));
+          bcc.push_back(q->ccnt[k]);
+        }
+      } else {
+        for (int32_t c = 0; c < q->tab.nreg[q->M - 1]; ++c) {
+          bci.push_back(make_int2(d, c));
+          bcc.push_back(1);
+        }
+      }
+    }
+  }
   int2* d_items = nullptr;
   int2* d_bgi = nullptr;
   int* d_bgc = nullptr;
   int2* d_bpi = nullptr;
   int* d_bpc = nullptr;
+  int2* d_bci = nullptr;
+  int* d_bcc = nullptr;
   Arena& A = h->batch;
   A.want(&d_items, std::max<size_t>(items.size(), 1));
   if (!bgi.empty()) {
@@ -1906,6 +2018,10 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
   if (!bpi.empty()) {
     A.want(&d_bpi, bpi.size());
     A.want(&d_bpc, bpc.size());
+  }
+  if (!bci.empty()) {
+    A.want(&d_bci, bci.size());
+    A.want(&d_bcc, bcc.size());
   }
   A.want(&h->d_descs, ndata);
   A.want(&h->d_roots, 2 * (size_t)ndata);
@@ -1925,6 +2041,10 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
   if (!bgi.empty() && ((e = cudaMemcpy(d_bgi, bgi.data(), sizeof(int2) * bgi.size(), cudaMemcpyHostToDevice)) ||
                        (e = cudaMemcpy(d_bgc, bgc.data(), sizeof(int) * bgc.size(), cudaMemcpyHostToDevice)))) {
     mra_free(h); return cuda_fail(e, "leaf groups");
+  }
+  if (!bci.empty() && ((e = cudaMemcpy(d_bci, bci.data(), sizeof(int2) * bci.size(), cudaMemcpyHostToDevice)) ||
+                       (e = cudaMemcpy(d_bcc, bcc.data(), sizeof(int) * bcc.size(), cudaMemcpyHostToDevice)))) {
+    mra_free(h); return cuda_fail(e, "chain groups");
   }
   if (!bpi.empty() && ((e = cudaMemcpy(d_bpi, bpi.data(), sizeof(int2) * bpi.size(), cudaMemcpyHostToDevice)) ||
                        (e = cudaMemcpy(d_bpc, bpc.data(), sizeof(int) * bpc.size(), cudaMemcpyHostToDevice)))) {
@@ -1946,6 +2066,11 @@ int mra_build_batch(const mra_config* cfgs, const double* const* locs, const dou
     p.w_leaf = d_bgi;
     p.c_leaf = d_bgc;
     p.lrows = h->lrows;
+  }
+  if (!bci.empty()) {
+    p.w_chn = d_bci;
+    p.c_chn = d_bcc;
+    p.n_chn = (int)bci.size();
   }
   if (!bpi.empty() && brcap) {
     for (int m = 1; m < maxM; ++m) {

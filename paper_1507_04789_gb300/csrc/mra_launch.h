@@ -73,6 +73,11 @@ struct Plan {
   const int* c_pri[MAXL] = {};
   int n_pri[MAXL] = {};
   int rcap = 0;
+  // the emulated leaf chain: groups of sibling level-(M-1) regions (c_chn[b]
+  // regions from w_chn[b].y, one 128-row tile); null: the leaf_syrk list
+  const int2* w_chn = nullptr;
+  const int* c_chn = nullptr;
+  int n_chn = 0;
   const int2* w_syrk = nullptr;
   int n_syrk = 0, t_syrk = 1;
 };
@@ -91,7 +96,8 @@ cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nbl
                             cudaStream_t s, const int* gcnt = nullptr, int rcap = 0);
 cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int emu, int* status,
                            cudaStream_t s, const int2* w_par = nullptr, int n_par = 0, Timer* tm = nullptr,
-                           int leaf_level = -1, const int* gcnt = nullptr, int lrows = 0);
+                           int leaf_level = -1, const int* gcnt = nullptr, int lrows = 0,
+                           const int* gpar = nullptr);
 size_t leaf_tc_smem_bytes(int nlmax, int emu);
 cudaError_t launch_leaf_syrk_em(const Desc* d_desc, const int2* work, int nblocks, int maxM, int r, int* status,
                                 cudaStream_t s);

@@ -557,8 +557,9 @@ cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaS
     tm->start(1, s, chain ? 1 : 2, pl.maxM);
     if (pl.mixed) {
       // (the emulated form's chain kernel runs per level-(M-1) region: the leaf_syrk work list)
-      if ((e = launch_leaf_tc(d_desc, pl.w_leaf, pl.n_leaf, pl.nlmax, pl.mixed == 2, status, s, pl.w_syrk,
-                              pl.n_syrk, tm, pl.maxM, pl.c_leaf, pl.lrows)))
+      if ((e = launch_leaf_tc(d_desc, pl.w_leaf, pl.n_leaf, pl.nlmax, pl.mixed == 2, status, s,
+                              pl.c_chn ? pl.w_chn : pl.w_syrk, pl.c_chn ? pl.n_chn : pl.n_syrk, tm, pl.maxM,
+                              pl.c_leaf, pl.lrows, pl.c_chn)))
         return e;
       if (pl.mixed == 2 && pl.n_syrk > 0) ++*launches;   // the chain kernel
     } else {

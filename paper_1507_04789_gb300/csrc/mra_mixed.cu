@@ -299,9 +299,13 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
 // L^{-1} are the same, so one split of those serves up to 128 rows):
 //   V^l_F = (C0(S_F, Q_l) - sum_{k<l} V^k_F V^k_{R_l}') L_l^{-T},  l = 0..M-1,
 // written to H, with the row scales of every 128-column group exported to
-// lf.hrow for the leaf kernel.
+// lf.hrow for the leaf kernel.  gcnt (else null): the work item is a group of
+// gcnt[b] sibling regions from P = it.i with at most 128 rows in all, one
+// tile: the levels l < M - 1 (their common ancestors) are one product per
+// level for the whole tile, level M - 1 one product per region on its rows.
 __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __restrict__ D,
-                                                              const int2* __restrict__ work, int* status) {
+                                                              const int2* __restrict__ work, int* status,
+                                                              const int* __restrict__ gcnt) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
@@ -314,6 +318,7 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
   // knot columns'; the column and row of every knot
   __shared__ double c0dx[TC_M * C0_GMAX], c0dy[TC_M * C0_GMAX], c0gp[TC_M], c0gq[C0_GMAX];
   __shared__ unsigned char qcol[MAX_R_DEV], qrow[MAX_R_DEV];
+  __shared__ int gseg[LGRP_MAX + 1];             // a group's regions: tile rows gseg[g] .. gseg[g + 1] - 1
   const Item it = work_item(work);
   const Desc& ds = D[it.d];
   const Shape sh = ds.sh;
@@ -322,8 +327,15 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
   const LeafState& lf = ds.lf;
   const int M = sh.M, r = sh.r, Mr = M * r, ng = (Mr + EM_KG - 1) / EM_KG;
   const long P = it.i;
+  const int G = gcnt ? gcnt[blockIdx.x] : 1;
   const long pm = st.mort[M - 1][P];
-  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
+  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * (long)st.mort[M - 1][P + G - 1] + 4];
+  if (G > 1 && row1 - row0 > TC_M) {             // (a group of more than one tile: never formed by the host)
+    if (threadIdx.x == 0) flag_error(status, ST_LIMIT, M - 1, P);
+    return;
+  }
+  if (threadIdx.x <= G)
+    gseg[threadIdx.x] = (int)((threadIdx.x < G ? lf.off[4 * (long)st.mort[M - 1][P + threadIdx.x]] : row1) - row0);
   const int gx = sh.gx, gy = sh.gy;
   const bool fast = c0_fast_ok(cv, gx, gy);
   const double c0s = c0_scale(cv), is2 = 1.0 / cv.sigma2;
@@ -346,8 +358,13 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
       if (fast) c0gp[t] = cv.sigma2 * c0_vfac(cv, sx[t]);
     }
     for (int t = threadIdx.x; t < EM_GMAX * TC_M; t += NT) hsc[t] = -2000;
-    for (int l = 0; l < M && ok; ++l) {
-      const long a = ancestor(st, M - 1, P, l);
+    for (int l = 0; l < M && ok; ++l)
+    for (int sg = 0; sg < (G > 1 && l == M - 1 ? G : 1) && ok; ++sg) {   // (level M - 1 of a group: per region)
+      const bool per = G > 1 && l == M - 1;
+      const long a = per ? P + sg : ancestor(st, M - 1, P, l);
+      const int ra = per ? gseg[sg] : 0, nr = per ? gseg[sg + 1] - gseg[sg] : na;   // this product's rows
+      if (nr == 0) continue;                     // (uniform: a region without observations)
+      double* Hseg = Hrow + (long)ra * Mr;
       __syncthreads();
       load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
       const double* Vanc = st.V[l] + a * (long)r * (l * r);
@@ -355,8 +372,8 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
       __syncthreads();
       if (fast) {   // offsets to the knot grid's gx columns and gy rows, knot columns' variance factors
         const int gs = gx + gy;
-        for (int t = threadIdx.x; t < na * gs; t += NT) {
-          const int fi = t / gs, c = t - fi * gs;
+        for (int t = threadIdx.x; t < nr * gs; t += NT) {
+          const int fi = ra + t / gs, c = t - (t / gs) * gs;
           const double d = c < gx ? c0s * (sx[fi] - ax[c]) : c0s * (sy[fi] - ay[(c - gx) * gx]);
           (c < gx ? c0dx + fi * gx + c : c0dy + fi * gy + (c - gx))[0] = d * d;
         }
@@ -365,8 +382,8 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
       }
       // C0(S_F, Q_l) into block l (the product below reads only blocks < l); in
       // gradient calls with its two derivatives
-      for (int t = threadIdx.x; t < na * r; t += NT) {
-        const int fi = t / r, qj = t - fi * r;
+      for (int t = threadIdx.x; t < nr * r; t += NT) {
+        const int fi = ra + t / r, qj = t - (t / r) * r;
         double v;
         if (fast) {
           const int qc = qcol[qj];
@@ -392,42 +409,42 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
       __syncthreads();
       if (l > 0) {
         const int* vsa = st.vexp[l] + a * (long)((l * r + 127) / 128) * r;
-        ok = eng.mma(acc, Hrow, Mr, 1, na, Vanc, l * r, 1, r, l * r, hsc, TC_M, vsa, r);
+        ok = eng.mma(acc, Hseg, Mr, 1, nr, Vanc, l * r, 1, r, l * r, hsc + ra, TC_M, vsa, r);
         if (!ok) break;
-        if (row < na) {
+        if (row < nr) {
           int e = -2000;
 #pragma unroll
           for (int c = 0; c < 32; ++c) {
             const int col = c0 + c;
             if (col < r) {
-              const double v = Hrow[(long)row * Mr + l * r + col] - acc.v[c];
-              Hrow[(long)row * Mr + l * r + col] = v;
+              const double v = Hseg[(long)row * Mr + l * r + col] - acc.v[c];
+              Hseg[(long)row * Mr + l * r + col] = v;
               e = max(e, xexp_of(v));
             }
           }
-          atomicMax(xsc + row, e);
+          atomicMax(xsc + ra + row, e);
         }
       }
       __syncthreads();
       acc.zero();
-      ok = eng.mma(acc, Hrow + l * r, Mr, 1, na, st.Li[l] + a * (long)r * r, r, 1, r, r, xsc, 0,
+      ok = eng.mma(acc, Hseg + l * r, Mr, 1, nr, st.Li[l] + a * (long)r * r, r, 1, r, r, xsc + ra, 0,
                    st.liexp[l] + a * r, 0);
       if (!ok) break;
-      if (row < na) {
+      if (row < nr) {
         int e0 = -2000, e1 = -2000;       // a thread's 32 columns touch at most two groups
         const int gbase = (l * r + c0) / 128;
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
           const int col = c0 + c;
           if (col < r) {
-            Hrow[(long)row * Mr + l * r + col] = acc.v[c];
+            Hseg[(long)row * Mr + l * r + col] = acc.v[c];
             const int e = xexp_of(acc.v[c]);
             if ((l * r + col) / 128 == gbase) e0 = max(e0, e);
             else e1 = max(e1, e);
           }
         }
-        atomicMax(hsc + gbase * TC_M + row, e0);
-        if (e1 > -2000) atomicMax(hsc + (gbase + 1) * TC_M + row, e1);
+        atomicMax(hsc + gbase * TC_M + ra + row, e0);
+        if (e1 > -2000) atomicMax(hsc + (gbase + 1) * TC_M + ra + row, e1);
       }
     }
     __syncthreads();
@@ -435,12 +452,15 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
       const int i = t / ng, g = t - i * ng;
       lf.hrow[(t0 + i) * ng + g] = hsc[g * TC_M + i];
     }
-    if (lf.vfexp) {   // gradient calls: column scales of V_F over the tile (the leaf partials' operand)
-      int32_t* out = lf.vfexp + (P * 4 + (t0 - row0) / TC_M) * (long)Mr;
-      for (int c = threadIdx.x; c < Mr; c += NT) {
-        int e = -2000;
-        for (int i = 0; i < na; ++i) e = max(e, xexp_of(Hrow[(long)i * Mr + c]));
-        out[c] = e;
+    if (lf.vfexp) {   // gradient calls: column scales of V_F over each region's tile (the leaf partials' operand)
+      for (int g = 0; g < G; ++g) {
+        const int ra = G > 1 ? gseg[g] : 0, rb = G > 1 ? gseg[g + 1] : na;
+        int32_t* out = lf.vfexp + ((P + g) * 4 + (G > 1 ? 0 : (t0 - row0) / TC_M)) * (long)Mr;
+        for (int c = threadIdx.x; c < Mr; c += NT) {
+          int e = -2000;
+          for (int i = ra; i < rb; ++i) e = max(e, xexp_of(Hrow[(long)i * Mr + c]));
+          out[c] = e;
+        }
       }
     }
   }
@@ -989,7 +1009,7 @@ cudaError_t launch_prior_tc(int m, const Desc* d_desc, const int2* work, int nbl
 
 cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, int nlmax, int emu, int* status,
                            cudaStream_t s, const int2* w_par, int n_par, Timer* tm, int leaf_level, const int* gcnt,
-                           int lrows) {
+                           int lrows, const int* gpar) {
   cudaError_t e;
   if (emu) {
     // the chain per parent first (work list: the level-(M-1) regions of every dataset)
@@ -998,7 +1018,7 @@ cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, in
       if ((e = cudaFuncSetAttribute(chain_forward_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     EM_SOLO_SMEM)))
         return e;
-      chain_forward_kernel_em<<<n_par, NT, EM_SOLO_SMEM, s>>>(d_desc, w_par, status);
+      chain_forward_kernel_em<<<n_par, NT, EM_SOLO_SMEM, s>>>(d_desc, w_par, status, gpar);
       if ((e = cudaGetLastError())) return e;
       if (tm) {   // the chain and the leaf kernel are timed as two records
         tm->stop(s);
