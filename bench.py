@@ -418,9 +418,18 @@ def run_batch(args, world, rank, mra, np, torch):
             lls[prec] = b.loglik([(t[0], t[1] * (1.0 + 0.01 * k), t[2]) for t in thetas])
         dt = (time.perf_counter() - t0) / reps
         nd, tile = b.info()
+        # one more evaluation with per-launch events (direct launches, not the graph): time per stage
+        b.enable_timing(True)
+        b.loglik(thetas)
+        st = b.stats()
+        b.enable_timing(False)
         b.close()
+        stages = {}
+        for row in st["levels"]:
+            for k, v in row.items():
+                stages[k] = stages.get(k, 0.0) + v["ms"] / max(1, st["evaluations"])
         out[prec] = {"ms_per_batch": dt * 1e3, "dataset_evals_per_s": world * nd / dt, "autotuned_tile": tile,
-                     "first_call_s": t_first}
+                     "first_call_s": t_first, "stage_ms": {k: round(v, 2) for k, v in stages.items()}}
     out["emu_max_rel_dloglik_vs_fp64"] = float(np.max(np.abs(lls["emu"] - lls["fp64"]) / np.abs(lls["fp64"])))
     return out
 
