@@ -109,3 +109,27 @@ def test_device_buffers_and_state(mra):
         big = rng.random((5000, 2))                      # grows the prediction buffer
         mb, vb = h.predict(theta, big)
         np.testing.assert_array_equal(h.predict(theta, plocs)[0], m_host)
+
+
+@pytest.mark.parametrize("r,M", [(64, 3), (16, 3), (32, 3)])
+def test_sparse_points_take_the_short_tile(mra, r, M):
+    """At most 16 points per leaf run in 16-row tiles (the n = 2^24 grid has about
+    one point per leaf): the same points give the same means and variances,
+    bitwise, as inside a crowded set that takes the full tiles, and the oracle's."""
+    rng = np.random.default_rng(2 + r)
+    n = 3000
+    locs = rng.random((n, 2))
+    y = rng.standard_normal(n)
+    theta = (1.0, 0.2, 0.05)
+    sparse = rng.random((60, 2))                  # 64 leaves at M = 3: about one point per leaf
+    crowded = np.concatenate([sparse, rng.random((4000, 2))])
+    with mra.Handle(locs, y, M=M, r=r, family="matern15") as h:
+        h.loglik(theta)
+        m1, v1 = h.predict(theta, sparse)
+        m2, v2 = h.predict(theta, crowded)
+    np.testing.assert_array_equal(m1, m2[:60])
+    np.testing.assert_array_equal(v1, v2[:60])
+    p = O.Problem(locs, y, M=M, r=r, family="matern15")
+    mo, vo = O.predict(p, theta, sparse)
+    np.testing.assert_allclose(m1, mo, rtol=RTOL, atol=RTOL * np.abs(mo).max())
+    np.testing.assert_allclose(v1, vo, rtol=RTOL, atol=RTOL * theta[0] * 1e-3)
