@@ -524,6 +524,54 @@ __device__ void tile_mma(TileAcc<TILE>& acc, const double* A, long sai, long sak
   __syncthreads();
 }
 
+// The same product on a TR x TC output tile (TR, TC multiples of 16): the 16 x
+// 16 thread grid gives every thread an (TR / 16) x (TC / 16) block, so a tile
+// of few rows (prediction points) against TC columns wastes no FMA lanes on
+// empty rows.
+template <int TR, int TC>
+struct TileAccR {
+  static constexpr int RR = TR / 16, RC = TC / 16;
+  double v[RR][RC];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int a = 0; a < RR; ++a)
+#pragma unroll
+      for (int b = 0; b < RC; ++b) v[a][b] = 0.0;
+  }
+  __device__ __forceinline__ int row(int a) const { return (threadIdx.x >> 4) * RR + a; }
+  __device__ __forceinline__ int col(int b) const { return (threadIdx.x & 15) * RC + b; }
+};
+
+template <int TR, int TC>
+__device__ void tile_mma_r(TileAccR<TR, TC>& acc, const double* A, long sai, long sak, int na, const double* B,
+                           long sbj, long sbk, int nb, int K, double* smem) {
+  constexpr int LDA = TR + 2, LDB = TC + 2;
+  constexpr int RR = TR / 16, RC = TC / 16;
+  double* sA = smem;
+  double* sB = smem + KC * LDA;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    int kn = min(KC, K - k0);
+    __syncthreads();
+    stage<TR>(sA, A, sai, sak, na, k0, kn);
+    stage<TC>(sB, B, sbj, sbk, nb, k0, kn);
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < kn; ++k) {
+      double a[RR], b[RC];
+#pragma unroll
+      for (int q = 0; q < RR; ++q) a[q] = sA[k * LDA + ty * RR + q];
+#pragma unroll
+      for (int q = 0; q < RC; ++q) b[q] = sB[k * LDB + tx * RC + q];
+#pragma unroll
+      for (int p = 0; p < RR; ++p)
+#pragma unroll
+        for (int q = 0; q < RC; ++q) acc.v[p][q] = fma(a[p], b[q], acc.v[p][q]);
+    }
+  }
+  __syncthreads();
+}
+
 // ---- factorisations in shared memory ----------------------------------------
 // Lower Cholesky factor in place (A = L L'); the strict upper triangle is set
 // to zero.  A non-positive (or NaN) pivot sets *bad and is replaced by 1 so

@@ -583,7 +583,10 @@ cudaError_t launch_loglik(const Plan& pl, const Desc* d_desc, int* status, cudaS
   for (int m = post_hi - 1; m >= pl.post_lo; --m) {
     if (pl.n_lvl[m] > 0) {
       tm->start(3, s, 4, m);
-      if ((e = launch_post_level(pl.mixed == 2, tile, m, pl.n_lvl[m], s, d_desc, pl.w_lvl[m], status))) return e;
+      // (the emulated form's G = Lt^{-1} Ahat products have K = r: at r <= 32 the engine's fixed cost per
+      // product exceeds the FP64 tile product, measured 208 against 104 ms on the ragged batch)
+      if ((e = launch_post_level(pl.mixed == 2 && pl.r > 32, tile, m, pl.n_lvl[m], s, d_desc, pl.w_lvl[m], status)))
+        return e;
       tm->stop(s);
       ++*launches;
     }

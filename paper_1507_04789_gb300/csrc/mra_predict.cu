@@ -30,9 +30,12 @@ namespace mra {
 
 // MODE 0: marginal mean and variance; 1: also D and the Y_l (joint
 // covariance); 2: also chol(D) and the Y_l (simulation).  In the joint modes
-// one CTA holds all points of its leaf (at most TILE).
-template <int TILE, int MODE>
+// one CTA holds all points of its leaf (at most TILE).  TP: the points of one
+// CTA (TILE, or 16 in mode 0 where leaves hold few points): the products are
+// TP x TILE tiles, the TILE columns covering the r knots of a block.
+template <int TP, int TILE, int MODE>
 __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D, PredState ps, int* status) {
+  static_assert(MODE == 0 || TP == TILE, "the joint modes take whole leaves in square tiles");
   extern __shared__ double smem[];
   const Desc& ds = D[ps.desc];
   const Shape sh = ds.sh;
@@ -42,8 +45,8 @@ __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D,
   const LeafState& lf = ds.lf;
   const int M = sh.M, r = sh.r, Mr = M * r;
   const long F = ps.leaf0 + blockIdx.x;          // Morton id of the leaf
-  const long p0 = ps.off[F] + (long)blockIdx.y * TILE;
-  const long p1 = min(ps.off[F + 1], p0 + TILE);
+  const long p0 = ps.off[F] + (long)blockIdx.y * TP;
+  const long p1 = min(ps.off[F + 1], p0 + TP);
   if (p0 >= p1) return;
   const int nP = (int)(p1 - p0);
   long anc[MAXL];                                // compact ids of the ancestors
@@ -59,23 +62,23 @@ __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D,
   const int ldp = nlmax + 1, ldy = r + 1;
   const int ldc = MODE ? (nlmax > TILE ? nlmax : TILE) + 1 : ldp;   // Cs later holds D (joint modes)
   double* px = smem;
-  double* py = px + TILE;
-  double* mu = py + TILE;
-  double* va = mu + TILE;
-  double* ax = va + TILE;
+  double* py = px + TP;
+  double* mu = py + TP;
+  double* va = mu + TP;
+  double* ax = va + TP;
   double* ay = ax + MAX_R_DEV;
-  double* Cs = ay + MAX_R_DEV;                  // TILE x ldc: C0(S^P, S_F), then D
-  double* Ps = Cs + (long)TILE * ldc;           // TILE x (nlmax + 1): P
-  double* Ys = Ps + (long)TILE * ldp;           // TILE x (r + 1)
-  double* stg = Ys + (long)TILE * ldy;
+  double* Cs = ay + MAX_R_DEV;                  // TP x ldc: C0(S^P, S_F), then D
+  double* Ps = Cs + (long)TP * ldc;             // TP x (nlmax + 1): P
+  double* Ys = Ps + (long)TP * ldp;             // TP x (r + 1)
+  double* stg = Ys + (long)TP * ldy;
   for (int t = threadIdx.x; t < nP; t += NT) {
     px[t] = ps.xs[p0 + t];
     py[t] = ps.ys[p0 + t];
   }
   __syncthreads();
   double* U = ps.U + p0 * Mr;                   // nP x (M r), row-major
-  TileAcc<TILE> acc;
-  constexpr int RM = TileAcc<TILE>::RM;
+  TileAccR<TP, TILE> acc;
+  constexpr int RR = TileAccR<TP, TILE>::RR, RC = TileAccR<TP, TILE>::RC;
   // ---- Uhat chain (same recursion as the leaf basis) --------------------------
   for (int l = 0; l < M; ++l) {
     const long a = anc[l];
@@ -83,21 +86,21 @@ __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D,
     load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
     __syncthreads();
     acc.zero();
-    if (l > 0) tile_mma<TILE>(acc, U, Mr, 1, nP, st.V[l] + a * (long)r * (l * r), l * r, 1, r, l * r, stg);
+    if (l > 0) tile_mma_r<TP, TILE>(acc, U, Mr, 1, nP, st.V[l] + a * (long)r * (l * r), l * r, 1, r, l * r, stg);
 #pragma unroll
-    for (int p = 0; p < RM; ++p)
+    for (int p = 0; p < RR; ++p)
 #pragma unroll
-      for (int q = 0; q < RM; ++q) {
+      for (int q = 0; q < RC; ++q) {
         int row = acc.row(p), col = acc.col(q);
         if (row < nP && col < r) U[(long)row * Mr + l * r + col] = cov0(cv, px[row], py[row], ax[col], ay[col]) - acc.v[p][q];
       }
     __syncthreads();
     acc.zero();
-    tile_mma<TILE>(acc, U + l * r, Mr, 1, nP, st.Li[l] + a * (long)r * r, r, 1, r, r, stg);
+    tile_mma_r<TP, TILE>(acc, U + l * r, Mr, 1, nP, st.Li[l] + a * (long)r * r, r, 1, r, r, stg);
 #pragma unroll
-    for (int p = 0; p < RM; ++p)
+    for (int p = 0; p < RR; ++p)
 #pragma unroll
-      for (int q = 0; q < RM; ++q) {
+      for (int q = 0; q < RC; ++q) {
         int row = acc.row(p), col = acc.col(q);
         if (row < nP && col < r) U[(long)row * Mr + l * r + col] = acc.v[p][q];
       }
@@ -123,20 +126,20 @@ __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D,
     for (int ct = 0; ct < nct; ++ct) {
       const int ncol = min(TILE, nF - ct * TILE);
       acc.zero();
-      tile_mma<TILE>(acc, Cs, ldc, 1, nP, LS + (long)ct * TILE * nF, nF, 1, ncol, nF, stg);
+      tile_mma_r<TP, TILE>(acc, Cs, ldc, 1, nP, LS + (long)ct * TILE * nF, nF, 1, ncol, nF, stg);
       if (M > 0) {
-        TileAcc<TILE> sub;
+        TileAccR<TP, TILE> sub;
         sub.zero();
-        tile_mma<TILE>(sub, U, Mr, 1, nP, HF + (long)ct * TILE * Mr, Mr, 1, ncol, Mr, stg);
+        tile_mma_r<TP, TILE>(sub, U, Mr, 1, nP, HF + (long)ct * TILE * Mr, Mr, 1, ncol, Mr, stg);
 #pragma unroll
-        for (int p = 0; p < RM; ++p)
+        for (int p = 0; p < RR; ++p)
 #pragma unroll
-          for (int q = 0; q < RM; ++q) acc.v[p][q] -= sub.v[p][q];
+          for (int q = 0; q < RC; ++q) acc.v[p][q] -= sub.v[p][q];
       }
 #pragma unroll
-      for (int p = 0; p < RM; ++p)
+      for (int p = 0; p < RR; ++p)
 #pragma unroll
-        for (int q = 0; q < RM; ++q) {
+        for (int q = 0; q < RC; ++q) {
           int row = acc.row(p), col = acc.col(q);
           if (row < nP && col < ncol) Ps[row * ldp + ct * TILE + col] = acc.v[p][q];
         }
@@ -157,12 +160,12 @@ __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D,
     // D = C0(S^P, S^P) - Uhat Uhat' - P P' over the leaf's points (Cs is free)
     __syncthreads();
     acc.zero();
-    if (M > 0) tile_mma<TILE>(acc, U, Mr, 1, nP, U, Mr, 1, nP, Mr, stg);
-    if (nF > 0) tile_mma<TILE>(acc, Ps, ldp, 1, nP, Ps, ldp, 1, nP, nF, stg);
+    if (M > 0) tile_mma_r<TP, TILE>(acc, U, Mr, 1, nP, U, Mr, 1, nP, Mr, stg);
+    if (nF > 0) tile_mma_r<TP, TILE>(acc, Ps, ldp, 1, nP, Ps, ldp, 1, nP, nF, stg);
 #pragma unroll
-    for (int p = 0; p < RM; ++p)
+    for (int p = 0; p < RR; ++p)
 #pragma unroll
-      for (int q = 0; q < RM; ++q) {
+      for (int q = 0; q < RC; ++q) {
         int row = acc.row(p), col = acc.col(q);
         if (row < nP && col < nP) Cs[row * ldc + col] = cov0(cv, px[row], py[row], px[col], py[col]) - acc.v[p][q];
       }
@@ -186,11 +189,11 @@ __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D,
     // Bhat^{M,k} = Uhat^k - P H^k_F  (in place in U)
     for (int k = 0; k < M; ++k) {
       acc.zero();
-      tile_mma<TILE>(acc, Ps, ldp, 1, nP, HF + k * r, 1, Mr, r, nF, stg);
+      tile_mma_r<TP, TILE>(acc, Ps, ldp, 1, nP, HF + k * r, 1, Mr, r, nF, stg);
 #pragma unroll
-      for (int p = 0; p < RM; ++p)
+      for (int p = 0; p < RR; ++p)
 #pragma unroll
-        for (int q = 0; q < RM; ++q) {
+        for (int q = 0; q < RC; ++q) {
           int row = acc.row(p), col = acc.col(q);
           if (row < nP && col < r) U[(long)row * Mr + k * r + col] -= acc.v[p][q];
         }
@@ -201,11 +204,11 @@ __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D,
     const long a = anc[l];
     __syncthreads();
     acc.zero();
-    tile_mma<TILE>(acc, U + l * r, Mr, 1, nP, st.Lt[l] + a * (long)r * r, r, 1, r, r, stg);
+    tile_mma_r<TP, TILE>(acc, U + l * r, Mr, 1, nP, st.Lt[l] + a * (long)r * r, r, 1, r, r, stg);
 #pragma unroll
-    for (int p = 0; p < RM; ++p)
+    for (int p = 0; p < RR; ++p)
 #pragma unroll
-      for (int q = 0; q < RM; ++q) {
+      for (int q = 0; q < RC; ++q) {
         int row = acc.row(p), col = acc.col(q);
         if (row < nP && col < r) Ys[row * ldy + col] = acc.v[p][q];
       }
@@ -229,11 +232,11 @@ __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D,
     const double* Gl = st.G[l] + a * (long)r * (l * r);
     for (int k = 0; k < l; ++k) {
       acc.zero();
-      tile_mma<TILE>(acc, Ys, ldy, 1, nP, Gl + k * r, 1, l * r, r, r, stg);
+      tile_mma_r<TP, TILE>(acc, Ys, ldy, 1, nP, Gl + k * r, 1, l * r, r, r, stg);
 #pragma unroll
-      for (int p = 0; p < RM; ++p)
+      for (int p = 0; p < RR; ++p)
 #pragma unroll
-        for (int q = 0; q < RM; ++q) {
+        for (int q = 0; q < RC; ++q) {
           int row = acc.row(p), col = acc.col(q);
           if (row < nP && col < r) U[(long)row * Mr + k * r + col] -= acc.v[p][q];
         }
@@ -249,11 +252,12 @@ __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D,
 
 static int tile_of(int r) { return r <= 16 ? 16 : (r <= 32 ? 32 : 64); }
 
-size_t predict_smem_bytes(int r, int nlmax) {
+static size_t predict_smem_tp(int tp, int r, int nlmax) {
   const int tile = tile_of(r);
-  return sizeof(double) * (4 * (size_t)tile + 2 * MAX_R_DEV + 2 * (size_t)tile * (nlmax + 1) +
-                           (size_t)tile * (r + 1) + 2 * KC * (tile + 2));
+  return sizeof(double) * (4 * (size_t)tp + 2 * MAX_R_DEV + 2 * (size_t)tp * (nlmax + 1) +
+                           (size_t)tp * (r + 1) + KC * (tp + 2) + KC * (tile + 2));
 }
+size_t predict_smem_bytes(int r, int nlmax) { return predict_smem_tp(tile_of(r), r, nlmax); }
 
 // Joint modes: one 64-point tile per leaf; Cs wide enough to hold D.
 size_t joint_smem_bytes(int r, int nlmax) {
@@ -265,20 +269,25 @@ size_t joint_smem_bytes(int r, int nlmax) {
 cudaError_t launch_predict(const Desc* d_desc, int M, int r, int nlmax, const PredState& ps, int max_per_leaf,
                            int* status, cudaStream_t s, int64_t* launches, Timer* tm, long nleaf) {
   const int tile = tile_of(r);
-  const size_t sm = predict_smem_bytes(r, nlmax);
-  dim3 grid(nleaf > 0 ? (unsigned)nleaf : 1u << (2 * M), (unsigned)((max_per_leaf + tile - 1) / tile));
+  // points per CTA: a 16-row tile where the leaves hold few points (one TILE-wide column tile still
+  // covers a block's r knots)
+  const int tp = max_per_leaf <= 16 ? 16 : tile;
+  const size_t sm = predict_smem_tp(tp, r, nlmax);
+  dim3 grid(nleaf > 0 ? (unsigned)nleaf : 1u << (2 * M), (unsigned)((max_per_leaf + tp - 1) / tp));
   if (grid.y == 0) return cudaSuccess;
   cudaError_t e;
   tm->start(5, s);
-#define MRA_PRED_LAUNCH(T)                                                                              \
-  {                                                                                                     \
-    e = cudaFuncSetAttribute(predict_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-    if (e) return e;                                                                                    \
-    predict_kernel<T, 0><<<grid, NT, sm, s>>>(d_desc, ps, status);                                      \
+#define MRA_PRED_LAUNCH(P, T)                                                                                 \
+  {                                                                                                           \
+    e = cudaFuncSetAttribute(predict_kernel<P, T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);  \
+    if (e) return e;                                                                                          \
+    predict_kernel<P, T, 0><<<grid, NT, sm, s>>>(d_desc, ps, status);                                         \
   }
-  if (tile == 16) MRA_PRED_LAUNCH(16)
-  else if (tile == 32) MRA_PRED_LAUNCH(32)
-  else MRA_PRED_LAUNCH(64)
+  if (tile == 16) MRA_PRED_LAUNCH(16, 16)
+  else if (tile == 32 && tp == 16) MRA_PRED_LAUNCH(16, 32)
+  else if (tile == 32) MRA_PRED_LAUNCH(32, 32)
+  else if (tp == 16) MRA_PRED_LAUNCH(16, 64)
+  else MRA_PRED_LAUNCH(64, 64)
 #undef MRA_PRED_LAUNCH
   tm->stop(s);
   ++*launches;
@@ -406,15 +415,15 @@ cudaError_t launch_predict_joint(const Desc* d_desc, int M, int r, int nlmax, co
   cudaError_t e;
   tm->start(5, s);
   if (mode == 1) {
-    if ((e = cudaFuncSetAttribute(predict_kernel<JOINT_TILE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(predict_kernel<JOINT_TILE, JOINT_TILE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm)))
       return e;
-    predict_kernel<JOINT_TILE, 1><<<grid, NT, sm, s>>>(d_desc, ps, status);
+    predict_kernel<JOINT_TILE, JOINT_TILE, 1><<<grid, NT, sm, s>>>(d_desc, ps, status);
   } else {
-    if ((e = cudaFuncSetAttribute(predict_kernel<JOINT_TILE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(predict_kernel<JOINT_TILE, JOINT_TILE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sm)))
       return e;
-    predict_kernel<JOINT_TILE, 2><<<grid, NT, sm, s>>>(d_desc, ps, status);
+    predict_kernel<JOINT_TILE, JOINT_TILE, 2><<<grid, NT, sm, s>>>(d_desc, ps, status);
   }
   tm->stop(s);
   ++*launches;
