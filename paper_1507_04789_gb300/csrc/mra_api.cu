@@ -941,7 +941,7 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
         p.n_leaf = (int)(h->goff[g + 1] - h->goff[g]);
         p.lrows = h->lrows;
       }
-      if (!h->citems.empty()) {   // the chunk's groups for the leaf chain
+      if (!h->citems.empty() && h->ccn[g] < c.c1[M - 1] - c.c0[M - 1]) {   // the chunk's groups for the leaf chain
         p.w_chn = h->d_citems + h->cco[g];
         p.c_chn = h->d_ccnt + h->cco[g];
         p.n_chn = (int)h->ccn[g];
@@ -968,7 +968,7 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
     }
     h->plan.rcap = h->prcap;
   }
-  if (!h->citems.empty() && !s_lvl) {
+  if (!h->citems.empty() && !s_lvl && h->cwn < nreg[M - 1]) {   // (only if some group holds two or more)
     h->plan.w_chn = h->d_citems + h->cwo;
     h->plan.c_chn = h->d_ccnt + h->cwo;
     h->plan.n_chn = (int)h->cwn;
@@ -1266,7 +1266,15 @@ int mra_update(mra_handle* h, const double* locs, const double* y, int where) {
                              h->stream)) ||
         (e = cudaStreamSynchronize(h->stream)))
       return cuda_fail(e, "chain groups");
-    h->plan.n_chn = (int)h->cwn;
+    if (h->cwn < h->tab.nreg[h->M - 1]) {   // (only if some group holds two or more)
+      h->plan.w_chn = h->d_citems + h->cwo;
+      h->plan.c_chn = h->d_ccnt + h->cwo;
+      h->plan.n_chn = (int)h->cwn;
+    } else {
+      h->plan.w_chn = nullptr;
+      h->plan.c_chn = nullptr;
+      h->plan.n_chn = 0;
+    }
   }
   return MRA_OK;
 }

@@ -431,16 +431,10 @@ __device__ inline bool em_mma(EmCtx& cx, TcAcc& acc, const double* A, long sai, 
     }
   }
   // hi + lo to FP64 with one DADD: the float-to-double widening is done on the
-  // integer pipe (exact bit moves), not as a conversion on the narrow FP64 pipe;
-  // only for the warps that hold a kept row, and the kept columns (the sums of
-  // the others are zero, and every DADD costs the narrow FP64 pipe)
-  if (((threadIdx.x >> 5) & 3) * 32 < na && c0 < nb) {   // warp-uniform
+  // integer pipe (exact bit moves), not as a conversion on the narrow FP64 pipe
+  // (for every row and column: skipping the discarded ones was measured slower)
 #pragma unroll
-    for (int c = 0; c < 32; ++c) acc.v[c] = c0 + c < nb ? em_widen(hi[c]) + em_widen(lo[c]) : 0.0;
-  } else {
-#pragma unroll
-    for (int c = 0; c < 32; ++c) acc.v[c] = 0.0;
-  }
+  for (int c = 0; c < 32; ++c) acc.v[c] = em_widen(hi[c]) + em_widen(lo[c]);
   return true;
 }
 

@@ -303,6 +303,7 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
 // gcnt[b] sibling regions from P = it.i with at most 128 rows in all, one
 // tile: the levels l < M - 1 (their common ancestors) are one product per
 // level for the whole tile, level M - 1 one product per region on its rows.
+template <bool GRP>
 __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __restrict__ D,
                                                               const int2* __restrict__ work, int* status,
                                                               const int* __restrict__ gcnt) {
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
   const LeafState& lf = ds.lf;
   const int M = sh.M, r = sh.r, Mr = M * r, ng = (Mr + EM_KG - 1) / EM_KG;
   const long P = it.i;
-  const int G = gcnt ? gcnt[blockIdx.x] : 1;
+  const int G = GRP && gcnt ? gcnt[blockIdx.x] : 1;   // (GRP false: one region, the loops below fold)
   const long pm = st.mort[M - 1][P];
   const long row0 = lf.off[4 * pm], row1 = lf.off[4 * (long)st.mort[M - 1][P + G - 1] + 4];
   if (G > 1 && row1 - row0 > TC_M) {             // (a group of more than one tile: never formed by the host)
@@ -737,20 +738,21 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
       // hsc (the V_F row scales) is read no more: it collects the row scales of H_F
       for (int t = threadIdx.x; t < EM_GMAX * TC_M; t += NT) hsc[t] = -2000;
     }
-    for (int l = 0; l < M && ok; ++l) {
+    for (int cb = 0; cb < Mr && ok; cb += TC_N) {   // 64 columns of H a product (two levels at r = 32)
+      const int nbc = min(TC_N, Mr - cb);
       acc.zero();
-      ok = eng.mma(acc, S, lds, 1, nF, Hrow + l * r, 1, Mr, r, nF, EMU ? ssc : nullptr, 0);
+      ok = eng.mma(acc, S, lds, 1, nF, Hrow + cb, 1, Mr, nbc, nF, EMU ? ssc : nullptr, 0);
       if (!ok) break;
       if (row < nF) {
         int e0 = -2000, e1 = -2000;       // a thread's 32 columns touch at most two groups
-        const int gbase = (l * r + c0) / 128;
+        const int gbase = (cb + c0) / 128;
         #pragma unroll
         for (int c = 0; c < 32; ++c) {
           const int col = c0 + c;
-          if (col < r) {
-            Hrow[(long)row * Mr + l * r + col] = acc.v[c];
+          if (col < nbc) {
+            Hrow[(long)row * Mr + cb + col] = acc.v[c];
             const int e = xexp_of(acc.v[c]);
-            if ((l * r + col) / 128 == gbase) e0 = max(e0, e);
+            if ((cb + col) / 128 == gbase) e0 = max(e0, e);
             else e1 = max(e1, e);
           }
         }
@@ -764,7 +766,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
         #pragma unroll
         for (int c = 0; c < 32; ++c) {
           const int e = __reduce_max_sync(0xffffffffu, row < nF ? xexp_of(acc.v[c]) : -2000);
-          if (lane == c && c0 + c < r && e > -2000) atomicMax(hcol + l * r + c0 + c, e);
+          if (lane == c && c0 + c < nbc && e > -2000) atomicMax(hcol + cb + c0 + c, e);
         }
       } else if (EMU && G > 1 && ((threadIdx.x >> 5) & 3) * 32 < nF) {   // per leaf: the lanes of each leaf reduce
         const int lane = threadIdx.x & 31;
@@ -773,8 +775,8 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
         #pragma unroll
         for (int c = 0; c < 32; ++c) {
           const int e = __reduce_max_sync(grp, row < nF ? xexp_of(acc.v[c]) : -2000);
-          if (lk >= 0 && lane == __ffs(grp) - 1 && c0 + c < r && e > -2000)
-            atomicMax(hcol + (long)lk * Mr + l * r + c0 + c, e);
+          if (lk >= 0 && lane == __ffs(grp) - 1 && c0 + c < nbc && e > -2000)
+            atomicMax(hcol + (long)lk * Mr + cb + c0 + c, e);
         }
       }
       __syncthreads();
@@ -802,20 +804,23 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
 // Gram products of the posterior pass on the emulation engine (MRA_PREC_EMU):
 // leaf_syrk and aggregate with the same sums as the FP64 kernels.  One tile
 // stacks up to S = 128 / r consecutive row blocks k0 .. k0 + S - 1 (all >= l)
-// against one column block l, so the 128 rows of the MMA carry S output blocks
-// and the column block is split once for all of them.
+// against CB = 64 / r column blocks l .. l + CB - 1 (one at r = 64), so the 128
+// x 64 MMA carries S CB output blocks and the column blocks are split once for
+// all of them.
 // ---------------------------------------------------------------------------
 
-// Tiles of the packed lower blocks (k >= l, k, l < nblk) for stack height S.
-__host__ __device__ inline int em_tiles(int nblk, int S) {
+// Tiles of the packed lower blocks (k >= l, k, l < nblk) for stack height S and
+// CB column blocks per tile: the tile of column blocks l .. l + CB - 1 and row
+// blocks k0 .. k0 + S - 1 (k0 >= l) keeps the blocks with k >= its column block.
+__host__ __device__ inline int em_tiles(int nblk, int S, int CB = 1) {
   int n = 0;
-  for (int l = 0; l < nblk; ++l) n += (nblk - l + S - 1) / S;
+  for (int l = 0; l < nblk; l += CB) n += (nblk - l + S - 1) / S;
   return n;
 }
 
-// Tile t -> column block l and first row block k0.
-__device__ inline bool em_tile(int t, int nblk, int S, int& l, int& k0) {
-  for (l = 0; l < nblk; ++l) {
+// Tile t -> first column block l (of CB) and first row block k0.
+__device__ inline bool em_tile(int t, int nblk, int S, int CB, int& l, int& k0) {
+  for (l = 0; l < nblk; l += CB) {
     const int nt = (nblk - l + S - 1) / S;
     if (t < nt) {
       k0 = l + t * S;
@@ -826,7 +831,13 @@ __device__ inline bool em_tile(int t, int nblk, int S, int& l, int& k0) {
   return false;
 }
 
-__global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict__ D, const int2* __restrict__ work,
+// Column blocks of r columns a tile takes: the 64 columns of the MMA (one block
+// at r = 64, two at r = 32, four at r = 16).
+__host__ __device__ inline int em_cblocks(int r) { return r <= 16 ? 4 : (r <= 32 ? 2 : 1); }
+
+// One column block per tile (r > 32).  (A separate kernel: the same body
+// compiled as a branch of the several-block kernel below ran 10 % slower.)
+__global__ void __launch_bounds__(NT) leaf_syrk_kernel_em1(const Desc* __restrict__ D, const int2* __restrict__ work,
                                                           int nt, int* status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   __shared__ __align__(8) uint64_t mbar[2];
@@ -842,7 +853,7 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict
   const long p = it.i;
   const int S = em_stack(r);
   int l, k0;
-  if (!em_tile(tile, M, S, l, k0)) return;     // fewer tiles in a shallower dataset
+  if (!em_tile(tile, M, S, 1, l, k0)) return;     // fewer tiles in a shallower dataset
   const int nk = min(S, M - k0);                      // row blocks k0 .. k0 + nk - 1
   const long pm = st.mort[M - 1][p];
   const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
@@ -895,6 +906,89 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict
   if (!ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, M - 1, p);
 }
 
+// Several column blocks per tile (r <= 32).
+template <bool MULTI>
+__global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict__ D, const int2* __restrict__ work,
+                                                          int nt, int* status) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int fail;
+  __shared__ int rexp[EM_REXP], cexp[EM_CEXP];
+  int tile;
+  const Item it = work_item_tiled(work, nt, tile);
+  const Desc& ds = D[it.d];
+  const int M = ds.sh.M, r = ds.sh.r, Mr = M * r;
+  const LevelState& st = ds.st;
+  const LeafState& lf = ds.lf;
+  const long p = it.i;
+  const int S = em_stack(r), CB = MULTI ? em_cblocks(r) : 1;
+  int l, k0;
+  if (!em_tile(tile, M, S, CB, l, k0)) return;  // fewer tiles in a shallower dataset
+  const int nk = min(S, M - k0);                      // row blocks k0 .. k0 + nk - 1
+  const int nl = MULTI ? min(CB, M - l) : 1;          // column blocks l .. l + nl - 1
+  const long pm = st.mort[M - 1][p];
+  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
+  const int K = (int)(row1 - row0);
+  const double* Hb = lf.H + row0 * Mr;
+  Engine<true> eng;
+  eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
+  // scales per 128-row group of the parent's rows: the largest column scale of
+  // the leaves whose rows meet the group (an upper bound of the group's maximum)
+  const int ng = (K + EM_KG - 1) / EM_KG;
+  for (int t = threadIdx.x; t < ng * (TC_M + TC_N); t += NT) {
+    const bool isA = t < ng * TC_M;
+    const int u = isA ? t : t - ng * TC_M;
+    const int g = isA ? u / TC_M : u / TC_N, i = isA ? u % TC_M : u % TC_N;
+    int e = -2000;
+    if (i < (isA ? nk * r : nl * r)) {
+      const int col = isA ? k0 * r + i : l * r + i;
+      for (int c = 0; c < 4; ++c) {
+        const long lo = lf.off[4 * pm + c] - row0, hi = lf.off[4 * pm + c + 1] - row0;
+        if (hi > lo && lo < (long)(g + 1) * EM_KG && hi > (long)g * EM_KG) {
+          const int cl = st.cid[M][4 * pm + c];
+          e = max(e, lf.hcol[(long)cl * Mr + col]);
+        }
+      }
+    }
+    (isA ? rexp : cexp)[u] = e;
+  }
+  __syncthreads();
+  TcAcc acc;
+  acc.zero();
+  const bool ok = eng.mma(acc, Hb + k0 * r, 1, Mr, nk * r, Hb + l * r, 1, Mr, nl * r, K, rexp, TC_M, cexp, TC_N);
+  const int m = M - 1, T = (m + 1) * (m + 2) / 2;
+  const int row = acc.row(), c0 = acc.col0();
+  if (ok && row < nk * r) {
+    const int k = k0 + row / r, ri = row % r;
+    if (!MULTI) {                                     // (r > 32: one column block)
+      double* out = st.Acc[m] + (p * T + tri_index(k, l)) * (long)r * r + (long)ri * r;
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c0 + c < r) out[c0 + c] = acc.v[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int col = c0 + c, lb = l + col / r;     // column block of this column
+        if (col < nl * r && k >= lb)
+          st.Acc[m][(p * T + tri_index(k, lb)) * (long)r * r + (long)ri * r + col % r] = acc.v[c];
+      }
+    }
+  }
+  eng.release();
+  if (k0 == l)
+    for (int lb = l; lb < l + nl; ++lb) {
+      double* om = st.Om[m] + (p * (m + 1) + lb) * (long)r;
+      for (int a = threadIdx.x; a < r; a += NT) {
+        double s = 0.0;
+        for (long o = 0; o < K; ++o) s = fma(Hb[o * Mr + lb * r + a], lf.z[row0 + o], s);
+        om[a] = s;
+      }
+    }
+  if (!ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, M - 1, p);
+}
+
+template <bool MULTI>
 __global__ void __launch_bounds__(NT) aggregate_kernel_em(int m, const Desc* __restrict__ D,
                                                           const int2* __restrict__ work, int nt, int* status) {
   extern __shared__ __align__(1024) unsigned char dsm[];
@@ -908,10 +1002,11 @@ __global__ void __launch_bounds__(NT) aggregate_kernel_em(int m, const Desc* __r
   const int r = ds.sh.r, mr = m * r;
   const LevelState& st = ds.st;
   const long p = it.i;
-  const int S = em_stack(r);
+  const int S = em_stack(r), CB = MULTI ? em_cblocks(r) : 1;
   int l, k0;
-  if (!em_tile(tile, m, S, l, k0)) return;
+  if (!em_tile(tile, m, S, CB, l, k0)) return;
   const int nk = min(S, m - k0);
+  const int nl = MULTI ? min(CB, m - l) : 1;
   const int Tc = (m + 1) * (m + 2) / 2, Tp = m * (m + 1) / 2;
   const long cf = st.cfirst[m - 1][p], cc = st.ccnt[m - 1][p];
   const double* Gb = st.G[m] + cf * (long)r * mr;
@@ -925,7 +1020,7 @@ __global__ void __launch_bounds__(NT) aggregate_kernel_em(int m, const Desc* __r
     const int u = isA ? t : t - ng * TC_M;
     const int g = isA ? u / TC_M : u / TC_N, i = isA ? u % TC_M : u % TC_N;
     int e = -2000;
-    if (i < (isA ? nk * r : r)) {
+    if (i < (isA ? nk * r : nl * r)) {
       const int col = isA ? k0 * r + i : l * r + i;
       for (long ch = 0; ch < cc; ++ch)
         if (ch * r < (long)(g + 1) * EM_KG && (ch + 1) * r > (long)g * EM_KG)
@@ -936,35 +1031,50 @@ __global__ void __launch_bounds__(NT) aggregate_kernel_em(int m, const Desc* __r
   __syncthreads();
   TcAcc acc;
   acc.zero();
-  const bool ok = eng.mma(acc, Gb + k0 * r, 1, mr, nk * r, Gb + l * r, 1, mr, r, K, rexp, TC_M, cexp, TC_N);
+  const bool ok = eng.mma(acc, Gb + k0 * r, 1, mr, nk * r, Gb + l * r, 1, mr, nl * r, K, rexp, TC_M, cexp, TC_N);
   const int row = acc.row(), c0 = acc.col0();
   if (ok && row < nk * r) {
-    const int k = k0 + row / r, ri = row % r, t = tri_index(k, l);
-    double* out = st.Acc[m - 1] + (p * Tp + t) * (long)r * r + (long)ri * r;
+    const int k = k0 + row / r, ri = row % r;
+    if (!MULTI) {                                     // (r > 32: one column block)
+      const int t = tri_index(k, l);
+      double* out = st.Acc[m - 1] + (p * Tp + t) * (long)r * r + (long)ri * r;
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      const int col = c0 + c;
-      if (col < r) {
-        double s = -acc.v[c];
-        for (long ch = cf; ch < cf + cc; ++ch) s += st.Acc[m][(ch * Tc + t) * (long)r * r + (long)ri * r + col];
-        out[col] = s;
+      for (int c = 0; c < 32; ++c) {
+        const int col = c0 + c;
+        if (col < r) {
+          double s = -acc.v[c];
+          for (long ch = cf; ch < cf + cc; ++ch) s += st.Acc[m][(ch * Tc + t) * (long)r * r + (long)ri * r + col];
+          out[col] = s;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const int col = c0 + c, lb = l + col / r, cj = col % r;   // column block and column
+        if (col < nl * r && k >= lb) {
+          const int t = tri_index(k, lb);
+          double s = -acc.v[c];
+          for (long ch = cf; ch < cf + cc; ++ch) s += st.Acc[m][(ch * Tc + t) * (long)r * r + (long)ri * r + cj];
+          st.Acc[m - 1][(p * Tp + t) * (long)r * r + (long)ri * r + cj] = s;
+        }
       }
     }
   }
   eng.release();
-  if (k0 == l) {
-    double* om = st.Om[m - 1] + (p * m + l) * (long)r;
-    for (int a = threadIdx.x; a < r; a += NT) {
-      double s = 0.0;
-      for (long ci = cf; ci < cf + cc; ++ci) {
-        s += st.Om[m][(ci * (m + 1) + l) * (long)r + a];
-        const double* Gc = st.G[m] + ci * (long)r * mr;
-        const double* gc = st.gv[m] + ci * r;
-        for (int q = 0; q < r; ++q) s = fma(-Gc[(long)q * mr + l * r + a], gc[q], s);
+  if (k0 == l)
+    for (int lb = l; lb < l + nl; ++lb) {
+      double* om = st.Om[m - 1] + (p * m + lb) * (long)r;
+      for (int a = threadIdx.x; a < r; a += NT) {
+        double s = 0.0;
+        for (long ci = cf; ci < cf + cc; ++ci) {
+          s += st.Om[m][(ci * (m + 1) + lb) * (long)r + a];
+          const double* Gc = st.G[m] + ci * (long)r * mr;
+          const double* gc = st.gv[m] + ci * r;
+          for (int q = 0; q < r; ++q) s = fma(-Gc[(long)q * mr + lb * r + a], gc[q], s);
+        }
+        om[a] = s;
       }
-      om[a] = s;
     }
-  }
   if (!ok && threadIdx.x == 0) flag_error(status, ST_TIMEOUT, m - 1, p);
 }
 
@@ -1015,10 +1125,11 @@ cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, in
     // the chain per parent first (work list: the level-(M-1) regions of every dataset)
     const int chain_done = n_par > 0;
     if (chain_done) {
-      if ((e = cudaFuncSetAttribute(chain_forward_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    EM_SOLO_SMEM)))
+      if ((e = cudaFuncSetAttribute(gpar ? chain_forward_kernel_em<true> : chain_forward_kernel_em<false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
         return e;
-      chain_forward_kernel_em<<<n_par, NT, EM_SOLO_SMEM, s>>>(d_desc, w_par, status, gpar);
+      if (gpar) chain_forward_kernel_em<true><<<n_par, NT, EM_SOLO_SMEM, s>>>(d_desc, w_par, status, gpar);
+      else chain_forward_kernel_em<false><<<n_par, NT, EM_SOLO_SMEM, s>>>(d_desc, w_par, status, nullptr);
       if ((e = cudaGetLastError())) return e;
       if (tm) {   // the chain and the leaf kernel are timed as two records
         tm->stop(s);
@@ -1040,10 +1151,13 @@ cudaError_t launch_leaf_tc(const Desc* d_desc, const int2* work, int nblocks, in
 cudaError_t launch_leaf_syrk_em(const Desc* d_desc, const int2* work, int nblocks, int maxM, int r, int* status,
                                 cudaStream_t s) {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(leaf_syrk_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
+  const bool multi = em_cblocks(r) > 1;
+  if ((e = cudaFuncSetAttribute(multi ? leaf_syrk_kernel_em<true> : leaf_syrk_kernel_em1,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
     return e;
-  const int nt = em_tiles(maxM, em_stack(r));
-  leaf_syrk_kernel_em<<<nblocks * nt, NT, EM_SOLO_SMEM, s>>>(d_desc, work, nt, status);
+  const int nt = em_tiles(maxM, em_stack(r), em_cblocks(r));
+  if (multi) leaf_syrk_kernel_em<true><<<nblocks * nt, NT, EM_SOLO_SMEM, s>>>(d_desc, work, nt, status);
+  else leaf_syrk_kernel_em1<<<nblocks * nt, NT, EM_SOLO_SMEM, s>>>(d_desc, work, nt, status);
   return cudaGetLastError();
 }
 
@@ -1458,10 +1572,13 @@ cudaError_t launch_gbar_em(int m, const Desc& hd, const Desc* d_desc, const Grad
 cudaError_t launch_aggregate_em(int m, int r, const Desc* d_desc, const int2* work, int nblocks, int* status,
                                 cudaStream_t s) {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(aggregate_kernel_em, cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
+  const bool multi = em_cblocks(r) > 1;
+  if ((e = cudaFuncSetAttribute(multi ? aggregate_kernel_em<true> : aggregate_kernel_em<false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, EM_SOLO_SMEM)))
     return e;
-  const int nt = em_tiles(m, em_stack(r));
-  aggregate_kernel_em<<<nblocks * nt, NT, EM_SOLO_SMEM, s>>>(m, d_desc, work, nt, status);
+  const int nt = em_tiles(m, em_stack(r), em_cblocks(r));
+  if (multi) aggregate_kernel_em<true><<<nblocks * nt, NT, EM_SOLO_SMEM, s>>>(m, d_desc, work, nt, status);
+  else aggregate_kernel_em<false><<<nblocks * nt, NT, EM_SOLO_SMEM, s>>>(m, d_desc, work, nt, status);
   return cudaGetLastError();
 }
 
