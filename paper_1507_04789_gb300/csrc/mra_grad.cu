@@ -421,8 +421,26 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
     double* T3 = T2 + (long)nF * nF;
     const int nrt = (nF + TILE - 1) / TILE;
     TileAcc<TILE> acc;
-    // Hbar = 2 H S_p + z omegabar' (already in HB when the emulated form formed it)
-    for (int rt = 0; rt < nrt && !(em_parts & 1); ++rt) {
+    // Hbar = 2 H S_p + z omegabar' (already in HB when the emulated form formed it); a leaf
+    // of at most 16 observations in one 16-row tile (sparse leaves: no FMA lanes on empty rows)
+    if (!(em_parts & 1) && TILE > 16 && nF <= 16) {
+      TileAccR<16, TILE> a16;
+      for (int l = 0; l < M; ++l) {
+        a16.zero();
+        for (int k = 0; k < M; ++k) {
+          SRef b = sblock(gs, anc, r, k, l);
+          tile_mma_r<16, TILE>(a16, H + k * r, Mr, 1, nF, b.p, b.sj, b.sk, r, r, stg);
+        }
+#pragma unroll
+        for (int p = 0; p < TileAccR<16, TILE>::RR; ++p)
+#pragma unroll
+          for (int q = 0; q < TileAccR<16, TILE>::RC; ++q) {
+            const int row = a16.row(p), col = a16.col(q);
+            if (row < nF && col < r) HB[(long)row * Mr + l * r + col] = 2.0 * a16.v[p][q] + z[row] * wbar[l * r + col];
+          }
+      }
+    }
+    for (int rt = 0; rt < nrt && !(em_parts & 1) && !(TILE > 16 && nF <= 16); ++rt) {
       const int nrow = min(TILE, nF - rt * TILE);
       for (int l = 0; l < M; ++l) {
         acc.zero();
