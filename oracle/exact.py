@@ -19,8 +19,10 @@ the bounding box of the tree they are given: their covariance ``c0`` is the gene
 correlation through the modified Bessel function K_nu (scipy.special.kv),
 which reduces to the exponential at nu = 1/2 and to Eq. (mat15) at nu = 3/2,
 and their point locator ``cell_index`` works on the integer cell grid of each
-level (Morton interleave of the cell coordinates), not by descending the
-partition.  A mistake in the oracle's own C0 or partition therefore shows up
+level (the cell coordinates' bits regrouped into per-level child digits), not
+by descending the partition.  For level-varying J (reading R18) the level-m
+grid is 2^ceil(L/2) x 2^floor(L/2) cells, L = log2(J_1 ... J_m): the halvings
+alternate x, y, x, ... over the whole sequence.  A mistake in the oracle's own C0 or partition therefore shows up
 as a disagreement with these checkers.
 """
 from __future__ import annotations
@@ -63,24 +65,37 @@ def c0(X1, X2, theta, family, nonstat=False):
     return C
 
 
+def _J(J, k):
+    return int(J) if np.isscalar(J) else int(J[k - 1])
+
+
 def cell_index(pts, bbox, J, m, dim):
     """Index of the level-m region holding each point: the integer cell (the
-    box cut into J^m equal parts in 1-D, 2^m x 2^m in 2-D, the last cell closed
-    at the box maximum), with the two cell coordinates bit-interleaved in 2-D
-    (child j = b_x + 2 b_y at every level)."""
+    box cut into J_1 ... J_m equal parts in 1-D; in 2-D into 2^ceil(L/2) x
+    2^floor(L/2) cells, L = log2(J_1 ... J_m); the last cell closed at the box
+    maximum), the cell coordinates' bits then read as per-level child digits
+    j = c_x + s_x c_y (x bits first, coarse levels in the high bits)."""
     pts = np.asarray(pts, dtype=np.float64).reshape(-1, dim)
     if dim == 1:
         x0, x1 = bbox
-        k = J ** m
+        k = 1
+        for l in range(1, m + 1):
+            k *= _J(J, l)
         return np.clip(np.floor((pts[:, 0] - x0) / (x1 - x0) * k), 0, k - 1).astype(np.int64)
     x0, x1, y0, y1 = bbox
-    k = 2 ** m
-    ix = np.clip(np.floor((pts[:, 0] - x0) / (x1 - x0) * k), 0, k - 1).astype(np.int64)
-    iy = np.clip(np.floor((pts[:, 1] - y0) / (y1 - y0) * k), 0, k - 1).astype(np.int64)
+    L = [0]
+    for l in range(1, m + 1):
+        L.append(L[-1] + int(round(math.log2(_J(J, l)))))
+    NX, NY = (L[m] + 1) // 2, L[m] // 2
+    ix = np.clip(np.floor((pts[:, 0] - x0) / (x1 - x0) * 2 ** NX), 0, 2 ** NX - 1).astype(np.int64)
+    iy = np.clip(np.floor((pts[:, 1] - y0) / (y1 - y0) * 2 ** NY), 0, 2 ** NY - 1).astype(np.int64)
     out = np.zeros(pts.shape[0], dtype=np.int64)
-    for b in range(m):
-        out |= ((ix >> b) & 1) << (2 * b)
-        out |= ((iy >> b) & 1) << (2 * b + 1)
+    for l in range(1, m + 1):
+        a = (L[l] + 1) // 2 - (L[l - 1] + 1) // 2          # x halvings of level l
+        b = L[l] // 2 - L[l - 1] // 2                      # y halvings
+        cx = (ix >> (NX - (L[l] + 1) // 2)) & ((1 << a) - 1)
+        cy = (iy >> (NY - L[l] // 2)) & ((1 << b) - 1)
+        out = out * _J(J, l) + cx + (cy << a)
     return out
 
 
@@ -118,6 +133,9 @@ def exact_predict(locs, y, plocs, theta, family, nonstat=False):
 def bruteforce_cov(tree, pts, theta, family, nonstat=False):
     """C_M(pts, pts) from the definition of the M-RA process (Sec. 2.3)."""
     J, M, dim = tree.J, tree.M, tree.dim
+    nreg = [1]
+    for l in range(1, M + 1):
+        nreg.append(nreg[-1] * _J(J, l))
     pts = np.asarray(pts, dtype=np.float64).reshape(-1, dim)
     npts = pts.shape[0]
     # Z = the requested points followed by every knot of every internal region
@@ -125,7 +143,7 @@ def bruteforce_cov(tree, pts, theta, family, nonstat=False):
     Z = [pts]
     off = npts
     for m in range(M):
-        for i in range(J ** m):
+        for i in range(nreg[m]):
             q = tree.knots[m][i]
             knot_slices[(m, i)] = np.arange(off, off + q.shape[0])
             Z.append(q)
@@ -140,7 +158,7 @@ def bruteforce_cov(tree, pts, theta, family, nonstat=False):
     P = np.arange(npts)
     for m in range(M):
         vn = np.zeros_like(v)
-        for i in range(J ** m):
+        for i in range(nreg[m]):
             idx = np.flatnonzero(reg[m] == i)
             q = knot_slices[(m, i)]
             K = np.linalg.inv(v[np.ix_(q, q)])             # K_R = v_m(Q, Q)^{-1}

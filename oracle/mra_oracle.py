@@ -36,6 +36,14 @@ Readings where the paper is silent or garbled:
 * R8: knots form a cell-centred g_x x g_y grid inside each region.
 * R9: regions split at their midpoint, half-open [lo, mid), [mid, hi]; child
   index j = b_x + 2 b_y in 2-D; in 1-D child j covers the j-th of J equal parts.
+* R18: J may vary with the level (Sec. 2.2; Sec. 4.3 takes (J_1, ..., J_6) =
+  (2, 2, 4, 8, 8, 16)).  In 2-D every J_m is a power of two and every level-(m-1)
+  region splits the same way, into an s_x x s_y grid of equal children (s_x s_y
+  = J_m), each side cut by repeated midpoint halving with R9's half-open rule.
+  The log2 J_m halvings of level m go one at a time to the axis that has been
+  halved fewer times over levels 1..m so far, x on ties (so J = 4 is R9's
+  quadtree and (2, 2, 4, 8, 8, 16) ends on a 128 x 128 grid of square leaves);
+  child j = c_x + s_x c_y for the child in column c_x and row c_y.
 * R10: an empty leaf contributes A~ = 0, omega~ = 0, d = u = 0.
 * R17: a draw of eta~_R ~ N(K~_R omega^m_R, K~_R) (Prop. 2) takes the square
   root F_R = L_R^{-T} Lt_R^{-T} of K~_R, with L_R L_R' = K_R^{-1} and
@@ -102,48 +110,104 @@ class NotPositiveDefinite(ArithmeticError):
 class Tree:
     """Recursive partition of the domain (Sec. 2.2) and its knots.
 
-    Region i at level m has children J*i + j, j = 0..J-1; level 0 is the whole
-    bounding box.  ``boxes[m][i]`` is (x0, x1) in 1-D and (x0, x1, y0, y1) in
-    2-D.  ``knots[m][i]`` is the (r_i, d) array of knots for m < M; leaves use
-    their observations (``obs[i]`` indexes into the data).
+    ``J`` is one number (every level) or the sequence (J_1, ..., J_M) (reading
+    R18).  Region i at level m has children J_{m+1} i + j, j = 0..J_{m+1}-1;
+    level 0 is the whole bounding box.  ``boxes[m][i]`` is (x0, x1) in 1-D and
+    (x0, x1, y0, y1) in 2-D.  ``knots[m][i]`` is the (r_i, d) array of knots for
+    m < M; leaves use their observations (``obs[i]`` indexes into the data).
     """
     dim: int
-    J: int
+    J: object
     M: int
     boxes: list
     knots: list
     leaf_of: np.ndarray          # leaf index of every observation
     obs: list                    # observation indices per leaf, original order
 
+    def nreg(self, m):
+        """Regions at level m: J_1 ... J_m."""
+        return n_regions(self.J, m)
 
-def _child_boxes(box, J, dim):
-    if dim == 1:
-        x0, x1 = box
-        w = x1 - x0
-        return [(x0 + j * w / J, x0 + (j + 1) * w / J) for j in range(J)]
-    if J != 4:
-        raise ValueError("2-D partition is the midpoint quadtree (J = 4)")
-    x0, x1, y0, y1 = box
-    xm = 0.5 * (x0 + x1)
-    ym = 0.5 * (y0 + y1)
-    out = []
-    for j in range(4):
-        bx, by = j & 1, j >> 1
-        out.append((xm if bx else x0, x1 if bx else xm, ym if by else y0, y1 if by else ym))
+
+def J_at(J, m):
+    """J_m: the children of every level-(m-1) region (m >= 1)."""
+    return int(J) if np.isscalar(J) else int(J[m - 1])
+
+
+def n_regions(J, m):
+    out = 1
+    for k in range(1, m + 1):
+        out *= J_at(J, k)
     return out
 
 
-def _child_index(pts, boxes_of_pts, J, dim):
-    """Child j of each point inside its current box (reading R9)."""
+def halvings(J, m):
+    """(a, b): the x and y midpoint halvings of level m in 2-D (reading R18)."""
+    nx = ny = 0
+    for k in range(1, m + 1):
+        jk = J_at(J, k)
+        bits = jk.bit_length() - 1
+        if jk < 2 or (1 << bits) != jk:
+            raise ValueError("in 2-D every J_m must be a power of two >= 2")
+        a = b = 0
+        for _ in range(bits):
+            if nx <= ny:
+                nx += 1
+                a += 1
+            else:
+                ny += 1
+                b += 1
+    return a, b
+
+
+def _halve(lo, hi, t):
+    """The 2^t equal parts of [lo, hi] by t rounds of midpoint halving."""
+    parts = [(lo, hi)]
+    for _ in range(t):
+        nxt = []
+        for a, b in parts:
+            mid = 0.5 * (a + b)
+            nxt.extend([(a, mid), (mid, b)])
+        parts = nxt
+    return parts
+
+
+def _child_boxes(box, J, m, dim):
+    """Children of a level-(m-1) region, in child order (readings R9, R18)."""
+    Jm = J_at(J, m)
+    if dim == 1:
+        x0, x1 = box
+        w = x1 - x0
+        return [(x0 + j * w / Jm, x0 + (j + 1) * w / Jm) for j in range(Jm)]
+    a, b = halvings(J, m)
+    x0, x1, y0, y1 = box
+    xs, ys = _halve(x0, x1, a), _halve(y0, y1, b)
+    return [xs[cx] + ys[cy] for cy in range(len(ys)) for cx in range(len(xs))]
+
+
+def _child_index(pts, boxes_of_pts, J, m, dim):
+    """Child j of each point inside its current level-(m-1) box (R9, R18)."""
+    Jm = J_at(J, m)
     if dim == 1:
         x0, x1 = boxes_of_pts[:, 0], boxes_of_pts[:, 1]
-        j = np.floor((pts[:, 0] - x0) * J / (x1 - x0)).astype(np.int64)
-        return np.clip(j, 0, J - 1)
-    xm = 0.5 * (boxes_of_pts[:, 0] + boxes_of_pts[:, 1])
-    ym = 0.5 * (boxes_of_pts[:, 2] + boxes_of_pts[:, 3])
-    bx = (pts[:, 0] >= xm).astype(np.int64)
-    by = (pts[:, 1] >= ym).astype(np.int64)
-    return bx + 2 * by
+        j = np.floor((pts[:, 0] - x0) * Jm / (x1 - x0)).astype(np.int64)
+        return np.clip(j, 0, Jm - 1)
+    a, b = halvings(J, m)
+
+    def side(v, lo, hi, t):
+        lo, hi = lo.copy(), hi.copy()
+        c = np.zeros(v.shape[0], dtype=np.int64)
+        for _ in range(t):
+            mid = 0.5 * (lo + hi)
+            up = v >= mid
+            lo = np.where(up, mid, lo)
+            hi = np.where(up, hi, mid)
+            c = 2 * c + up
+        return c
+
+    cx = side(pts[:, 0], boxes_of_pts[:, 0], boxes_of_pts[:, 1], a)
+    cy = side(pts[:, 1], boxes_of_pts[:, 2], boxes_of_pts[:, 3], b)
+    return cx + (1 << a) * cy
 
 
 def locate(pts, tree_boxes, J, M, dim):
@@ -151,8 +215,8 @@ def locate(pts, tree_boxes, J, M, dim):
     pts = np.asarray(pts, dtype=np.float64).reshape(-1, dim)
     idx = np.zeros(pts.shape[0], dtype=np.int64)
     for m in range(M):
-        b = np.asarray(tree_boxes[m], dtype=np.float64).reshape(J ** m, -1)[idx]
-        idx = J * idx + _child_index(pts, b, J, dim)
+        b = np.asarray(tree_boxes[m], dtype=np.float64).reshape(n_regions(J, m), -1)[idx]
+        idx = J_at(J, m + 1) * idx + _child_index(pts, b, J, m + 1, dim)
     return idx
 
 
@@ -173,19 +237,24 @@ def grid_knots(box, r, dim):
 def build_tree(locs, M, J=4, r=16, bbox=None, knots_fn=None):
     """Partition (Sec. 2.2) with ``r`` grid knots per region, or ``knots_fn``.
 
+    ``J``: children per region, one number or (J_1, ..., J_M) (reading R18).
     ``knots_fn(m, i, box)`` may return any (r_i, d) array of knots for region
     (m, i); it is used for the exactness pins (boundary knots, knots equal to
     the data).
     """
     locs = np.asarray(locs, dtype=np.float64)
     dim = locs.shape[1]
+    if not np.isscalar(J):
+        J = tuple(int(j) for j in J)
+        if len(J) != M:
+            raise ValueError("J needs one entry per level 1..M")
     if bbox is None:
         bbox = (0.0, 1.0) if dim == 1 else (0.0, 1.0, 0.0, 1.0)
     boxes = [[tuple(bbox)]]
     for m in range(M):
         nxt = []
         for b in boxes[m]:
-            nxt.extend(_child_boxes(b, J, dim))
+            nxt.extend(_child_boxes(b, J, m + 1, dim))
         boxes.append(nxt)
     knots = []
     for m in range(M):
@@ -195,15 +264,20 @@ def build_tree(locs, M, J=4, r=16, bbox=None, knots_fn=None):
                       if knots_fn is not None else grid_knots(b, r, dim))
         knots.append(km)
     leaf_of = locate(locs, boxes, J, M, dim)
+    nl = n_regions(J, M)
     order = np.argsort(leaf_of, kind="stable")         # original order within a leaf
-    cuts = np.searchsorted(leaf_of[order], np.arange(J ** M + 1))
-    obs = [order[cuts[i]:cuts[i + 1]] for i in range(J ** M)]
+    cuts = np.searchsorted(leaf_of[order], np.arange(nl + 1))
+    obs = [order[cuts[i]:cuts[i + 1]] for i in range(nl)]
     return Tree(dim, J, M, boxes, knots, leaf_of, obs)
 
 
 def ancestors(m, i, J):
     """(level, index) of the ancestors R_0, ..., R_m of region (m, i)."""
-    return [(l, i // J ** (m - l)) for l in range(m + 1)]
+    out = [(m, i)]
+    for l in range(m, 0, -1):
+        i //= J_at(J, l)
+        out.append((l - 1, i))
+    return out[::-1]
 
 
 # ---------------------------------------------------------------------------
@@ -296,10 +370,9 @@ def _in_scope(tree, m, i, subtree):
     if subtree is None:
         return True
     k, idx = subtree
-    J = tree.J
     if m <= k:
-        return i == idx // J ** (k - m)
-    return i // J ** (m - k) == idx
+        return i == ancestors(k, idx, tree.J)[m][1]
+    return ancestors(m, i, tree.J)[k][1] == idx
 
 
 def prior(tree, locs, theta, family, tau2, nonstat=False, subtree=None, levels=None):
@@ -308,7 +381,7 @@ def prior(tree, locs, theta, family, tau2, nonstat=False, subtree=None, levels=N
     J, M = tree.J, tree.M
     P = Prior()
     for m in range(M + 1 if levels is None else levels + 1):
-        for i in range(J ** m):
+        for i in range(tree.nreg(m)):
             if not _in_scope(tree, m, i, subtree):
                 continue
             anc = ancestors(m, i, J)
@@ -353,14 +426,14 @@ def posterior(tree, locs, y, P, subtree=None):
     Q = Posterior()
     At, wt = {}, {}          # A~ and omega~ handed to the parent
     dtype = np.result_type(*[P.Sigma[i] for i in P.Sigma]) if P.Sigma else np.float64
-    for i in range(J ** M):
+    for i in range(tree.nreg(M)):
         if not _in_scope(tree, M, i, subtree):
             continue
         B = P.W[(M, i)][:M]
         yi = y[tree.obs[i]]
         S = P.Sigma[i]
         if S.shape[0] == 0:                       # R10: empty leaf
-            rs = _dims(tree, M - 1, i // J) if M > 0 else []
+            rs = _dims(tree, M - 1, i // J_at(J, M)) if M > 0 else []
             At[(M, i)] = {(k, l): np.zeros((rs[k], rs[l]), dtype=dtype)
                           for k in range(M) for l in range(M)}
             wt[(M, i)] = [np.zeros(rs[k], dtype=dtype) for k in range(M)]
@@ -374,10 +447,11 @@ def posterior(tree, locs, y, P, subtree=None):
         Q.d[(M, i)] = logdet(S)
         Q.u[(M, i)] = yi @ Siy
     for m in range(M - 1, -1, -1):
-        for i in range(J ** m):
+        Jc = J_at(J, m + 1)
+        for i in range(tree.nreg(m)):
             if not _in_scope(tree, m, i, subtree):
                 continue
-            kids = [(m + 1, J * i + j) for j in range(J) if (m + 1, J * i + j) in At]
+            kids = [(m + 1, Jc * i + j) for j in range(Jc) if (m + 1, Jc * i + j) in At]
             A = {(k, l): sum(At[c][(k, l)] for c in kids) for k in range(m + 1) for l in range(m + 1)}
             om = [sum(wt[c][k] for c in kids) for k in range(m + 1)]
             _post_region(P, Q, At, wt, m, i, A, om, sum(Q.d[c] for c in kids), sum(Q.u[c] for c in kids))
@@ -408,11 +482,12 @@ def posterior_coarse(tree, P, s, A_s, omega_s, dkids_s, ukids_s):
     J = tree.J
     Q = Posterior()
     At, wt = {}, {}
-    for i in range(J ** s):
+    for i in range(tree.nreg(s)):
         _post_region(P, Q, At, wt, s, i, A_s[i], omega_s[i], dkids_s[i], ukids_s[i])
     for m in range(s - 1, -1, -1):
-        for i in range(J ** m):
-            kids = [(m + 1, J * i + j) for j in range(J)]
+        Jc = J_at(J, m + 1)
+        for i in range(tree.nreg(m)):
+            kids = [(m + 1, Jc * i + j) for j in range(Jc)]
             A = {(k, l): sum(At[c][(k, l)] for c in kids) for k in range(m + 1) for l in range(m + 1)}
             om = [sum(wt[c][k] for c in kids) for k in range(m + 1)]
             _post_region(P, Q, At, wt, m, i, A, om, sum(Q.d[c] for c in kids), sum(Q.u[c] for c in kids))
@@ -425,7 +500,7 @@ class Problem:
     locs: np.ndarray
     y: np.ndarray
     M: int
-    J: int = 4
+    J: object = 4                 # one number, or (J_1, ..., J_M) (reading R18)
     r: int = 16
     family: str = "exp"
     nonstat: bool = False
@@ -648,7 +723,7 @@ def xi_offsets(tree):
     regions of levels 0..M-1 in level, then index order."""
     off, pos = {}, 0
     for m in range(tree.M):
-        for i in range(tree.J ** m):
+        for i in range(tree.nreg(m)):
             off[(m, i)] = pos
             pos += tree.knots[m][i].shape[0]
     return off, pos

@@ -135,3 +135,59 @@ def test_free_smoothness_family_at_half_integers(nu, table):
         s1 = s0 + np.array([[0.0, frac * kappa]])
         assert O.cov(s0, s1, (sigma2, kappa, nu), "matern")[0, 0] == pytest.approx(sigma2 * rho, rel=1e-13)
     assert O.cov(s0, s0, (sigma2, kappa, 2.7), "matern")[0, 0] == pytest.approx(sigma2, rel=1e-15)
+
+
+# Reading R18: level-varying J (Sec. 2.2; Sec. 4.3's (2, 2, 4, 8, 8, 16)).  Each
+# level's log2 J_m midpoint halvings go to the axis halved fewer times so far
+# (x on ties); child j = c_x + s_x c_y.  Values worked by hand.
+def test_level_varying_J_halvings():
+    assert [O.halvings((2, 2, 4, 8, 8, 16), m) for m in range(1, 7)] == \
+        [(1, 0), (0, 1), (1, 1), (2, 1), (1, 2), (2, 2)]          # 128 x 128 square leaves
+    assert [O.halvings(4, m) for m in range(1, 4)] == [(1, 1)] * 3   # the quadtree
+    with pytest.raises(ValueError):
+        O.halvings((2, 6), 2)
+
+
+def test_level_varying_J_boxes():
+    t = O.build_tree(np.array([[0.1, 0.1]]), M=2, J=(2, 8), r=4)
+    assert t.boxes[1] == [(0.0, 0.5, 0.0, 1.0), (0.5, 1.0, 0.0, 1.0)]
+    want = {0: (0.0, 0.25, 0.0, 0.25), 1: (0.25, 0.5, 0.0, 0.25), 2: (0.0, 0.25, 0.25, 0.5),
+            7: (0.25, 0.5, 0.75, 1.0), 8: (0.5, 0.75, 0.0, 0.25), 15: (0.75, 1.0, 0.75, 1.0)}
+    for i, b in want.items():
+        assert t.boxes[2][i] == b
+    assert len(t.boxes[2]) == 16 and t.nreg(2) == 16
+    assert O.ancestors(2, 13, (2, 8)) == [(0, 0), (1, 1), (2, 13)]
+
+
+# (point, leaf under J = (2, 8), leaf under J = (16,): the 4 x 4 grid, j = floor(4x) + 4 floor(4y))
+PTS_J = [((0.5, 0.25), 10, 6), ((1.0, 1.0), 15, 15), ((0.25, 0.75), 7, 13), ((0.0, 0.0), 0, 0),
+         ((0.49, 0.74), 5, 9), ((0.75, 0.5), 13, 11), ((0.1, 0.3), 2, 4)]
+
+
+@pytest.mark.parametrize("impl", ["oracle", "checker"])
+def test_level_varying_J_literal_leaves(impl):
+    pts = np.array([p for p, _, _ in PTS_J])
+    for J, col in (((2, 8), 1), ((16,), 2)):
+        want = [w[col] for w in PTS_J]
+        M = len(J)
+        if impl == "oracle":
+            got = O.locate(pts, O.build_tree(pts, M=M, J=J, r=4).boxes, J, M, 2)
+        else:
+            got = E.cell_index(pts, (0.0, 1.0, 0.0, 1.0), J, M, 2)
+        np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("J", [(2, 2, 4, 8), (8, 2), (16, 4), (4, 4, 4), (2, 16)])
+def test_level_varying_J_locators_agree(J):
+    """The oracle's descent and the checker's integer-cell locator (two
+    independent statements of R18) agree at every level, on random points and on
+    every cell boundary of the finest grid."""
+    rng = np.random.default_rng(len(J) + sum(J))
+    L = int(round(np.log2(np.prod(J))))
+    gx, gy = 2 ** ((L + 1) // 2), 2 ** (L // 2)
+    edge = np.array([[i / gx, j / gy] for i in range(gx + 1) for j in range(gy + 1)])
+    pts = np.concatenate([rng.random((400, 2)), edge])
+    t = O.build_tree(pts, M=len(J), J=J, r=4)
+    for m in range(1, len(J) + 1):
+        np.testing.assert_array_equal(O.locate(pts, t.boxes, J[:m], m, 2), E.cell_index(pts, (0, 1, 0, 1), J, m, 2))
+    assert sum(len(o) for o in t.obs) == pts.shape[0]

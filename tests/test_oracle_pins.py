@@ -108,6 +108,37 @@ def test_p4_recursions_match_bruteforce(M, r, family, nonstat):
     np.testing.assert_allclose(var, var_b, rtol=1e-8, atol=1e-10)
 
 
+@pytest.mark.parametrize("J,r,family", [((2, 8), 4, "exp"), ((2, 2, 4), 9, "matern15"), ((16, 2), 4, "exp"),
+                                         ((8,), 9, "matern15")])
+def test_p4_level_varying_J_matches_bruteforce(J, r, family):
+    """P4 on partitions with level-varying J (reading R18): the recursions of
+    Sec. 3 against the dense C_M of the process definition."""
+    locs, y = _data(220, 40 + sum(J))
+    plocs, _ = _data(25, 41 + sum(J))
+    theta = TH_M15 if family == "matern15" else TH_EXP
+    p = O.Problem(locs, y, M=len(J), J=J, r=r, family=family)
+    assert O.loglik(p, theta) == pytest.approx(E.bruteforce_loglik(p, theta), rel=1e-11)
+    mu, var = O.predict(p, theta, plocs)
+    mu_b, var_b = E.bruteforce_predict(p, theta, plocs)
+    np.testing.assert_allclose(mu, mu_b, rtol=1e-8, atol=1e-10)
+    np.testing.assert_allclose(var, var_b, rtol=1e-8, atol=1e-10)
+    mean, cov = O.predict_joint(p, theta, plocs)
+    mb, cb = E.bruteforce_predict_joint(p, theta, plocs)
+    np.testing.assert_allclose(cov, cb, rtol=1e-8, atol=1e-10)
+
+
+def test_p2_level_varying_J_data_knots_exact():
+    """P2 on a level-varying partition: knots equal to the data at resolution 0."""
+    locs, y = _data(40, 5)
+    theta = (1.0, 0.3, 0.2)
+
+    def knots(m, i, box):
+        return locs if m == 0 else O.grid_knots(box, 4, 2)
+
+    p = O.Problem(locs, y, M=2, J=(2, 8), family="exp", knots_fn=knots)
+    assert O.loglik(p, theta) == pytest.approx(E.exact_loglik(locs, y, theta, "exp"), rel=1e-9)
+
+
 def test_p4_bruteforce_differs_from_exact():
     """Control for P4: C_M is a genuine approximation on this tree."""
     locs, y = _data(220, 30)
