@@ -1334,11 +1334,12 @@ static int ensure_grad_arena(mra_handle* h) {
   // Emulated form, two optional buffers, each taken only while 85 % of the free
   // device memory holds it after everything above (the kernels have paths
   // without them): the per-parent adjoint S for Hbar and Gbar on the tensor
-  // cores, when it is also at most four times the size of H (else the FP64
-  // kernels form Hbar and Gbar from the ancestors' blocks), then the chain's
-  // covariance derivative pairs (else the chain adjoint evaluates them).  On a
-  // streamed handle both are chunk-sized: S holds the parents of one launch
-  // (a chunk's, or a coarse level's), the pairs one chunk's observations.
+  // cores (else the FP64 kernels form Hbar and Gbar from the ancestors'
+  // blocks; slower even where S is many times the size of H, as on sparse
+  // leaves), then the chain's covariance derivative pairs (else the chain
+  // adjoint evaluates them).  On a streamed handle both are chunk-sized: S
+  // holds the parents of one launch (a chunk's, or a coarse level's), the
+  // pairs one chunk's observations.
   if (M > 0 && h->cfg.precision == MRA_PREC_EMU && h->grad_buffers) {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
@@ -1358,9 +1359,8 @@ static int ensure_grad_arena(mra_handle* h) {
       sfe = std::max(sfe, parents(L) * ((w + 127) / 128) * w);
     }
     sfe += 8;                                               // + the rows the engine rounds up to 8
-    const int64_t P = parents(M - 1);
     const int64_t sf = (int64_t)Arena::align(8 * sfd) + (int64_t)Arena::align(4 * sfe);
-    if (P * Mr <= 4 * nobs && sf <= budget) {
+    if (sf <= budget) {
       G.want(&h->gs.SF, sfd);
       G.want(&h->gs.SFexp, sfe);
       budget -= sf;

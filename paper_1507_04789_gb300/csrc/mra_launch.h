@@ -9,7 +9,7 @@ namespace mra {
 // Optional per-launch CUDA-event timing (kinds match MRA_K_* in mra.h; the
 // stage and level of a record match MRA_STAGE_* and the level index of
 // mra_stats_t, or -1 where a launch has none).
-constexpr int MAX_TIMED = 2048;
+constexpr int MAX_TIMED = 8192;
 struct Timer {
   bool on = false;
   int count = 0;
