@@ -83,8 +83,10 @@ extern "C" {
 
 /* Problem shape (Sec. 2.2).  Plain data, owned by the caller, copied by mra_build. */
 typedef struct {
-    int    M;           /* levels; leaves are the 4^M regions of level M; 0 <= M <= MRA_MAX_M */
-    int    J;           /* children per region; must be 4 (2-D midpoint quadtree) */
+    int    M;           /* levels; leaves are the J_1 ... J_M (4^M for the quadtree) regions of level M;
+                           0 <= M <= MRA_MAX_M */
+    int    J;           /* children per region at every level: must be 4 (2-D midpoint quadtree);
+                           not read when J_level[0] != 0 */
     int    r;           /* knots per internal region, 1 <= r <= MRA_MAX_R */
     int    cov_family;  /* MRA_COV_EXP or MRA_COV_MATERN15 */
     int    nonstat;     /* 1: variance sigma2 * sqrt(g(s1) g(s2)), g(s) = 1 + 0.5 sin(4 pi x) */
@@ -107,6 +109,17 @@ typedef struct {
                            levels > s and the emulated form's optional gradient buffers are
                            chunk-sized too); mra_predict_joint,
                            mra_simulate and mra_update return MRA_ERR_STATE. */
+    int    J_level[MRA_MAX_M];
+                        /* level-varying J (Sec. 2.2; Sec. 4.3 uses (2, 2, 4, 8, 8, 16)):
+                           J_level[m-1] = J_m, the children of every level-(m-1) region,
+                           m = 1..M, each 2, 4, 8 or 16, J_M (the leaves' level) 2 or 4, and
+                           J_1 ... J_M <= 2^24; entries past M zero.  All zero: J at every
+                           level.  Every region of a level splits the same way, into an
+                           s_x x s_y grid of equal children (s_x s_y = J_m) by repeated
+                           midpoint halving (half-open, last cell closed): with L_m =
+                           log2(J_1 ... J_m), level m halves ceil(L_m/2) - ceil(L_{m-1}/2)
+                           times in x and floor(L_m/2) - floor(L_{m-1}/2) times in y; child
+                           j = c_x + s_x c_y.  mra_loglik_noalloc takes the quadtree only. */
 } mra_config;
 
 /* Covariance parameters theta and the measurement-error variance (Sec. 2.1, 4.3). */
@@ -278,15 +291,17 @@ int mra_loglik_combine(mra_handle* h, const mra_params* theta, const double* sum
  * mra_region_terms -- the per-region log-determinant d_R and quadratic form
  * u_R (Sec. 3.3) of every region of `level` (0..M) from the last mra_loglik.
  * d_R = log|Sigma_R| and u_R = y_R' Sigma_R^{-1} y_R of the data in region R
- * given the weights of coarser levels.  d_out, u_out: host arrays of 4^level.
+ * given the weights of coarser levels.  d_out, u_out: host arrays of
+ * J_1 ... J_level entries (4^level for the quadtree).
  * Errors: MRA_ERR_ARG, MRA_ERR_STATE, MRA_ERR_CUDA.
  */
 int mra_region_terms(mra_handle* h, int level, double* d_out, double* u_out);
 
 /*
  * mra_leaf_offsets -- the leaf partition of the observations: off_out (host,
- * 4^M + 1 int64) receives the start of every leaf in leaf order, perm_out
- * (host, n int64, may be NULL) the original index of every sorted observation.
+ * J_1 ... J_M + 1 int64, 4^M + 1 for the quadtree) receives the start of every
+ * leaf in leaf order, perm_out (host, n int64, may be NULL) the original index
+ * of every sorted observation.
  */
 int mra_leaf_offsets(mra_handle* h, int64_t* off_out, int64_t* perm_out);
 

@@ -94,9 +94,46 @@ bool nu_ok(int family, const mra_params* t) {
   return family != MRA_COV_MATERN || (std::isfinite(t->nu) && t->nu >= 0.05 && t->nu <= 20.0);
 }
 
+// Per-level midpoint halvings of a configuration (Sec. 2.2; J may vary with the
+// level, Sec. 4.3): with L_m = log2(J_1 ... J_m), level m halves
+// ceil(L_m / 2) - ceil(L_{m-1} / 2) times in x and floor(L_m / 2) -
+// floor(L_{m-1} / 2) times in y (the halvings alternate x, y, x, ... over the
+// whole sequence, so J = 4 is the quadtree).  Packed 4 bits per level.
+void config_halvings(const mra_config* cfg, unsigned long long& hx, unsigned long long& hy) {
+  hx = hy = 0;
+  int L = 0;
+  for (int m = 1; m <= cfg->M; ++m) {
+    const int Jm = cfg->J_level[0] ? cfg->J_level[m - 1] : 4;
+    int b = 0;
+    while ((1 << b) < Jm) ++b;
+    const int L1 = L + b;
+    hx |= (unsigned long long)((L1 + 1) / 2 - (L + 1) / 2) << (4 * m);
+    hy |= (unsigned long long)(L1 / 2 - L / 2) << (4 * m);
+    L = L1;
+  }
+}
+
 int check_config(const mra_config* cfg) {
   if (cfg->M < 0 || cfg->M > MRA_MAX_M) return fail(MRA_ERR_ARG, "M must be in [0, %d]", MRA_MAX_M);
-  if (cfg->J != 4) return fail(MRA_ERR_ARG, "J must be 4 (2-D midpoint quadtree)");
+  if (cfg->J_level[0] == 0) {
+    if (cfg->J != 4) return fail(MRA_ERR_ARG, "J must be 4 (2-D midpoint quadtree), or J_level set");
+    for (int m = 1; m < MRA_MAX_M; ++m)
+      if (cfg->J_level[m]) return fail(MRA_ERR_ARG, "J_level[0] is 0 but J_level[%d] is not", m);
+  } else {
+    int L = 0;
+    for (int m = 1; m <= MRA_MAX_M; ++m) {
+      const int Jm = cfg->J_level[m - 1];
+      if (m > cfg->M) {
+        if (Jm) return fail(MRA_ERR_ARG, "J_level[%d] set beyond level M = %d", m - 1, cfg->M);
+        continue;
+      }
+      if (Jm != 2 && Jm != 4 && Jm != 8 && Jm != 16)
+        return fail(MRA_ERR_ARG, "J_level[%d] = %d: each J_m must be 2, 4, 8 or 16", m - 1, Jm);
+      if (m == cfg->M && Jm > 4) return fail(MRA_ERR_ARG, "J_M (the leaves' level) must be 2 or 4");
+      L += Jm == 2 ? 1 : Jm == 4 ? 2 : Jm == 8 ? 3 : 4;
+    }
+    if (L > 24) return fail(MRA_ERR_ARG, "J_1 ... J_M = 2^%d leaves: at most 2^24", L);
+  }
   if (cfg->r < 1 || cfg->r > MRA_MAX_R) return fail(MRA_ERR_ARG, "r must be in [1, %d]", MRA_MAX_R);
   if (cfg->cov_family != MRA_COV_EXP && cfg->cov_family != MRA_COV_MATERN15 && cfg->cov_family != MRA_COV_MATERN)
     return fail(MRA_ERR_ARG, "unknown covariance family %d", cfg->cov_family);
@@ -113,6 +150,7 @@ int check_config(const mra_config* cfg) {
 struct Tables {
   std::vector<std::vector<int32_t>> mort, par, cfirst, ccnt, cid;
   std::vector<int32_t> nreg;
+  std::vector<int> bits;   // level m: log2 J_m (bits of the child digit); entry 0 unused
 };
 
 // Groups of leaves for the emulated leaf kernel: consecutive children of one
@@ -154,7 +192,7 @@ void chain_groups(const Tables& T, int M, const std::vector<int64_t>& obs_pref, 
                   std::vector<int2>& items, std::vector<int>& cnt) {
   auto rows = [&](int32_t P) {
     const int64_t pm = T.mort[M - 1][P];
-    return obs_pref[4 * pm + 4] - obs_pref[4 * pm];
+    return obs_pref[(pm + 1) << T.bits[M]] - obs_pref[pm << T.bits[M]];
   };
   for (int64_t q = p0; q < p1; ++q) {
     const int32_t cf = T.cfirst[M - 2][q], ce = cf + T.ccnt[M - 2][q];
@@ -169,7 +207,10 @@ void chain_groups(const Tables& T, int M, const std::vector<int64_t>& obs_pref, 
   }
 }
 
-void build_tables(int M, bool prune, const std::vector<int32_t>& counts, Tables& T) {
+void build_tables(int M, unsigned long long hx, unsigned long long hy, bool prune, const std::vector<int32_t>& counts,
+                  Tables& T) {
+  T.bits.assign(M + 1, 0);
+  for (int m = 1; m <= M; ++m) T.bits[m] = mra::lvl_bits(hx, hy, m);
   T.mort.assign(M + 1, {});
   T.par.assign(M + 1, {});
   T.cfirst.assign(M + 1, {});
@@ -180,14 +221,18 @@ void build_tables(int M, bool prune, const std::vector<int32_t>& counts, Tables&
   act[M].resize(counts.size());
   for (size_t f = 0; f < counts.size(); ++f) act[M][f] = !prune || counts[f] > 0;
   for (int m = M - 1; m >= 0; --m) {
-    const size_t cnt = size_t(1) << (2 * m);
+    const size_t cnt = size_t(1) << mra::lvl_depth(hx, hy, m);
+    const int bc = T.bits[m + 1];
     act[m].assign(cnt, 0);
-    for (size_t i = 0; i < cnt; ++i)
-      act[m][i] = !prune || act[m + 1][4 * i] || act[m + 1][4 * i + 1] || act[m + 1][4 * i + 2] || act[m + 1][4 * i + 3];
+    for (size_t i = 0; i < cnt; ++i) {
+      bool a = !prune;
+      for (size_t j = 0; j < (size_t(1) << bc) && !a; ++j) a = act[m + 1][(i << bc) + j];
+      act[m][i] = a;
+    }
   }
   act[0][0] = 1;
   for (int m = 0; m <= M; ++m) {
-    const size_t cnt = size_t(1) << (2 * m);
+    const size_t cnt = size_t(1) << mra::lvl_depth(hx, hy, m);
     T.cid[m].assign(cnt, -1);
     for (size_t i = 0; i < cnt; ++i)
       if (act[m][i]) {
@@ -200,15 +245,15 @@ void build_tables(int M, bool prune, const std::vector<int32_t>& counts, Tables&
     const int32_t n = T.nreg[m];
     if (m > 0) {
       T.par[m].resize(n);
-      for (int32_t c = 0; c < n; ++c) T.par[m][c] = T.cid[m - 1][T.mort[m][c] >> 2];
+      for (int32_t c = 0; c < n; ++c) T.par[m][c] = T.cid[m - 1][T.mort[m][c] >> T.bits[m]];
     }
     if (m < M) {
       T.cfirst[m].assign(n, 0);
       T.ccnt[m].assign(n, 0);
       for (int32_t c = 0; c < n; ++c) {
-        const size_t base = 4 * (size_t)T.mort[m][c];
+        const size_t base = (size_t)T.mort[m][c] << T.bits[m + 1];
         int32_t first = -1, k = 0;
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < (1 << T.bits[m + 1]); ++j) {
           const int32_t id = T.cid[m + 1][base + j];
           if (id >= 0) {
             if (first < 0) first = id;
@@ -248,6 +293,9 @@ struct mra_handle {
   mra_config cfg;
   int64_t n = 0;
   int M = 0, r = 0, gx = 0, gy = 0;
+  unsigned long long hx = mra::QUAD_HALVINGS, hy = mra::QUAD_HALVINGS;   // per-level halvings of the partition
+  // regions of level m in the complete tree: 2^(log2 J_1 + ... + log2 J_m)
+  int64_t nfull(int m) const { return int64_t(1) << mra::lvl_depth(hx, hy, m); }
   int nlmax = 0;
   cudaStream_t stream = nullptr;
   Arena tree, state;
@@ -421,6 +469,8 @@ cudaError_t upload_desc(mra_handle* h, const mra_params* theta) {
   h->hd.sh.r = h->r;
   h->hd.sh.gx = h->gx;
   h->hd.sh.gy = h->gy;
+  h->hd.sh.hx = h->hx;
+  h->hd.sh.hy = h->hy;
   for (int k = 0; k < 4; ++k) h->hd.sh.bbox[k] = h->cfg.bbox[k];
   h->hd.sh.mixed = h->cfg.precision == MRA_PREC_MIXED ? 1 : (h->cfg.precision == MRA_PREC_EMU ? 2 : 0);
   if (theta) {
@@ -493,10 +543,10 @@ cudaError_t launch_evaluation(mra_handle* h) {
 
 // Binning into an existing tree arena (used by mra_build and mra_update).
 cudaError_t bin(mra_handle* h, const double* dl, const double* dy, int* hs, int64_t* tail, int32_t* mc) {
-  const int64_t nl = int64_t(1) << (2 * h->M);
+  const int64_t nl = h->nfull(h->M);
   cudaError_t e;
   if ((e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream))) return e;
-  if ((e = mra::launch_bin(dl, h->n, h->bbox, h->M, h->leaf_id, h->counts, h->cursor, h->off, h->sq_off,
+  if ((e = mra::launch_bin(dl, h->n, h->bbox, h->M, h->hx, h->hy, h->leaf_id, h->counts, h->cursor, h->off, h->sq_off,
                            h->max_count, h->perm, h->status, h->stream, &g_launches)) ||
       (e = mra::launch_gather(dl, dy, h->perm, h->n, h->xs, h->ys, h->yv, h->stream, &g_launches)))
     return e;
@@ -598,8 +648,9 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   h->r = cfg->r;
   h->gx = gx_for(cfg->r);
   h->gy = cfg->r / h->gx;
+  config_halvings(cfg, h->hx, h->hy);
   const int M = h->M, r = h->r;
-  const int64_t nl = int64_t(1) << (2 * M);
+  const int64_t nl = h->nfull(M);
   cudaError_t e;
   int hs[4];
 
@@ -650,7 +701,7 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
         (e = cudaStreamSynchronize(h->stream))) {
       mra_free(h); return cuda_fail(e, "leaf counts");
     }
-    build_tables(M, cfg->prune != 0, counts, h->tab);
+    build_tables(M, h->hx, h->hy, cfg->prune != 0, counts, h->tab);
     h->leaf_counts = counts;
   }
   const std::vector<int32_t>& nreg = h->tab.nreg;
@@ -677,14 +728,16 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
       c.c0[sl] = g;
       c.c1[sl] = g + 1;
       for (int m = sl + 1; m <= M; ++m) {
-        const int64_t lo = ms << (2 * (m - sl)), hi = (ms + 1) << (2 * (m - sl));
+        const int dm = mra::lvl_depth(h->hx, h->hy, m) - mra::lvl_depth(h->hx, h->hy, sl);
+        const int64_t lo = ms << dm, hi = (ms + 1) << dm;
         const auto& mt = h->tab.mort[m];
         c.c0[m] = std::lower_bound(mt.begin(), mt.end(), (int32_t)lo) - mt.begin();
         c.c1[m] = std::lower_bound(mt.begin(), mt.end(), (int32_t)std::min<int64_t>(hi, INT32_MAX)) - mt.begin();
         if (hi > INT32_MAX) c.c1[m] = (int64_t)mt.size();
         cmax[m] = std::max(cmax[m], c.c1[m] - c.c0[m]);
       }
-      const int64_t f0 = ms << (2 * (M - sl)), f1 = (ms + 1) << (2 * (M - sl));
+      const int dM = mra::lvl_depth(h->hx, h->hy, M) - mra::lvl_depth(h->hx, h->hy, sl);
+      const int64_t f0 = ms << dM, f1 = (ms + 1) << dM;
       c.f0 = f0;
       c.nf = f1 - f0;
       c.obs0 = obs_pref[f0];
@@ -744,7 +797,7 @@ int mra_build(const mra_config* cfg, const double* locs, const double* y, int64_
   for (int m = 0; m <= M; ++m) {
     h->st.nreg[m] = nreg[m];
     B.want(&h->st.mort[m], nreg[m]);
-    B.want(&h->st.cid[m], size_t(1) << (2 * m));
+    B.want(&h->st.cid[m], (size_t)h->nfull(m));
     if (m > 0) B.want(&h->st.par[m], nreg[m]);
     if (m < M) {
       B.want(&h->st.cfirst[m], nreg[m]);
@@ -1172,7 +1225,7 @@ int mra_region_terms(mra_handle* h, int level, double* d_out, double* u_out) {
   if (!h->parts.empty()) return fail(MRA_ERR_STATE, "not available on a batch handle");
   if (level < 0 || level > h->M) return fail(MRA_ERR_ARG, "level must be in [0, M]");
   if (!h->have_post) return fail(MRA_ERR_STATE, "no log-likelihood evaluated yet");
-  const int64_t full = int64_t(1) << (2 * level);
+  const int64_t full = h->nfull(level);
   const int32_t cnt = h->tab.nreg[level];
   const double* d = level == h->M ? h->lf.d : h->st.dd[level];
   const double* u = level == h->M ? h->lf.u : h->st.uu[level];
@@ -1194,7 +1247,7 @@ int mra_leaf_offsets(mra_handle* h, int64_t* off_out, int64_t* perm_out) {
   g_err.clear();
   if (!h || !off_out) return fail(MRA_ERR_ARG, "null argument");
   if (!h->parts.empty()) return fail(MRA_ERR_STATE, "not available on a batch handle");
-  const int64_t nl = int64_t(1) << (2 * h->M);
+  const int64_t nl = h->nfull(h->M);
   cudaError_t e;
   if ((e = cudaMemcpyAsync(off_out, h->off, sizeof(int64_t) * (nl + 1), cudaMemcpyDeviceToHost, h->stream)))
     return cuda_fail(e, "offsets");
@@ -1210,7 +1263,7 @@ int mra_update(mra_handle* h, const double* locs, const double* y, int where) {
   if (!h->parts.empty()) return fail(MRA_ERR_STATE, "not available on a batch handle");
   if (h->s_lvl) return fail(MRA_ERR_STATE, "a streamed handle keeps its partition: build a new handle");
   if (where != MRA_HOST && where != MRA_DEVICE) return fail(MRA_ERR_ARG, "where must be MRA_HOST or MRA_DEVICE");
-  const int64_t n = h->n, nl = int64_t(1) << (2 * h->M);
+  const int64_t n = h->n, nl = h->nfull(h->M);
   cudaError_t e;
   const double* dl = locs;
   const double* dy = y;
@@ -1660,7 +1713,7 @@ static int pred_prepare(mra_handle* h, const mra_params* theta, const double* pl
     if (rc) return rc;
   }
   const int M = h->M, r = h->r;
-  const int64_t nl = int64_t(1) << (2 * M);
+  const int64_t nl = h->nfull(M);
   cudaError_t e;
   if (np > h->pred_cap) {
     h->pred.release();
@@ -1691,7 +1744,7 @@ static int pred_prepare(mra_handle* h, const mra_params* theta, const double* pl
     dp = h->p_in;
   }
   if ((e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream))) return cuda_fail(e, "memset");
-  if ((e = mra::launch_bin(dp, np, h->bbox, M, h->p_leaf, h->p_counts, h->p_cursor, h->p_off, h->p_sq, h->p_max,
+  if ((e = mra::launch_bin(dp, np, h->bbox, M, h->hx, h->hy, h->p_leaf, h->p_counts, h->p_cursor, h->p_off, h->p_sq, h->p_max,
                            h->p_perm, h->status, h->stream, &g_launches, stable)) ||
       (e = mra::launch_gather(dp, nullptr, h->p_perm, np, h->p_xs, h->p_ys, nullptr, h->stream, &g_launches)))
     return cuda_fail(e, "binning prediction points");
@@ -1713,6 +1766,7 @@ static mra::PredState pred_state(mra_handle* h) {
   ps.U = h->p_U;
   ps.mean = h->p_mean;
   ps.var = h->p_var;
+  ps.nleaves = (long)h->nfull(h->M);
   return ps;
 }
 
@@ -1835,7 +1889,7 @@ int mra_simulate_xi_len(mra_handle* h, int64_t* len_out) {
   if (!h || !len_out) return fail(MRA_ERR_ARG, "null argument");
   if (!h->parts.empty()) return fail(MRA_ERR_STATE, "not available on a batch handle");
   int64_t regions = 0;
-  for (int m = 0; m < h->M; ++m) regions += int64_t(1) << (2 * m);
+  for (int m = 0; m < h->M; ++m) regions += h->nfull(m);
   *len_out = regions * h->r;
   return MRA_OK;
 }

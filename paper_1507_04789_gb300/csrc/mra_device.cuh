@@ -424,17 +424,43 @@ __device__ __forceinline__ int xexp_of(double x) {
 }
 
 // ---- partition and knots (Sec. 2.2) -----------------------------------------
-// Region i of level m: child digits j_t = bits (2t+1, 2t) of i counted from the
-// top level, b_x = j & 1, b_y = j >> 1; boxes are halved at their midpoint.
+// Every level-(m-1) region splits the same way: into an s_x x s_y grid of equal
+// children, s_x = 2^hx_m, s_y = 2^hy_m (J_m = s_x s_y; the midpoint quadtree is
+// hx_m = hy_m = 1), each side cut by repeated midpoint halving, half-open with
+// the last cell closed.  Child digit j = c_x + s_x c_y; region i of level m
+// holds its digits from the top level down, level t's in the hx_t + hy_t bits
+// below those of the levels above.  hx_m and hy_m sit in bits 4m..4m+3 of two
+// packed words (levels 1..12).
 struct Box { double x0, x1, y0, y1; };
 
-__device__ __forceinline__ Box region_box(const double* bbox, int m, long i) {
+__host__ __device__ __forceinline__ int lvl_hx(unsigned long long hx, int m) { return (int)((hx >> (4 * m)) & 15ull); }
+__host__ __device__ __forceinline__ int lvl_bits(unsigned long long hx, unsigned long long hy, int m) {
+  return lvl_hx(hx, m) + lvl_hx(hy, m);
+}
+// bits of a level-m region id: hx_1 + hy_1 + ... + hx_m + hy_m
+__host__ __device__ __forceinline__ int lvl_depth(unsigned long long hx, unsigned long long hy, int m) {
+  int d = 0;
+  for (int t = 1; t <= m; ++t) d += lvl_bits(hx, hy, t);
+  return d;
+}
+
+__device__ __forceinline__ Box region_box(const double* bbox, unsigned long long hx, unsigned long long hy, int m,
+                                          long i) {
   Box b{bbox[0], bbox[1], bbox[2], bbox[3]};
-  for (int t = 0; t < m; ++t) {
-    int j = (int)((i >> (2 * (m - 1 - t))) & 3);
-    double xm = 0.5 * (b.x0 + b.x1), ym = 0.5 * (b.y0 + b.y1);
-    if (j & 1) b.x0 = xm; else b.x1 = xm;
-    if (j & 2) b.y0 = ym; else b.y1 = ym;
+  int sh = lvl_depth(hx, hy, m);
+  for (int t = 1; t <= m; ++t) {
+    const int a = lvl_hx(hx, t), c = lvl_hx(hy, t);
+    sh -= a + c;
+    const long j = (i >> sh) & ((1L << (a + c)) - 1);
+    const long cx = j & ((1L << a) - 1), cy = j >> a;
+    for (int q = a - 1; q >= 0; --q) {
+      const double xm = 0.5 * (b.x0 + b.x1);
+      if ((cx >> q) & 1) b.x0 = xm; else b.x1 = xm;
+    }
+    for (int q = c - 1; q >= 0; --q) {
+      const double ym = 0.5 * (b.y0 + b.y1);
+      if ((cy >> q) & 1) b.y0 = ym; else b.y1 = ym;
+    }
   }
   return b;
 }
@@ -444,13 +470,6 @@ __device__ __forceinline__ void knot_xy(const Box& b, int gx, int gy, int q, dou
   int a = q % gx, c = q / gx;
   x = b.x0 + ((a + 0.5) * (b.x1 - b.x0)) / gx;
   y = b.y0 + ((c + 0.5) * (b.y1 - b.y0)) / gy;
-}
-
-// Fill sx/sy (shared) with the r knots of region (m, i).
-__device__ __forceinline__ void load_knots(const double* bbox, int m, long i, int gx, int gy,
-                                           double* sx, double* sy) {
-  Box b = region_box(bbox, m, i);
-  for (int q = threadIdx.x; q < gx * gy; q += NT) knot_xy(b, gx, gy, q, sx[q], sy[q]);
 }
 
 // ---- register-blocked tile product ------------------------------------------

@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(NT) leaf_adjoint_kernel(const Desc* __restrict
       const double* Lia = st.Li[l] + a * (long)r * r;
       const double* Va = st.V[l] + a * (long)r * (l * r);
       __syncthreads();
-      load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
+      load_knots(sh, l, st.mort[l][a], ax, ay);
       __syncthreads();
       for (int rt = 0; rt < nrt; ++rt) {
         const int nrow = min(TILE, nF - rt * TILE);
@@ -694,7 +694,7 @@ __global__ void __launch_bounds__(NT) leaf_partial_kernel(const Desc* __restrict
   int l = 0;
   while (tri_index(l + 1, 0) <= t) ++l;
   const int k = t - tri_index(l, 0);
-  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
+  const long row0 = lf.off[pm << leaf_bits(ds.sh)], row1 = lf.off[(pm + 1) << leaf_bits(ds.sh)];
   const int K = (int)(row1 - row0);
   const double* Ab = (k < l ? gs.XBF : gs.VBF) + row0 * Mr + l * r;
   const double* Bb = lf.VF + row0 * Mr + k * r;
@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
   };
   const int S = em_stack(r);
   double g_s2 = 0.0, g_k = 0.0, g_nu = 0.0;
-  load_knots(sh.bbox, m, st.mort[m][i], sh.gx, sh.gy, qx, qy);
+  load_knots(sh, m, st.mort[m][i], qx, qy);
   const double* L = st.L[m] + i * (long)r * r;
   const double* Li = st.Li[m] + i * (long)r * r;
   const double* V = st.V[m] + i * (long)r * mr;
@@ -844,7 +844,7 @@ __global__ void __launch_bounds__(NT) prior_adjoint_kernel(int m, const Desc* __
     const double* Lia = st.Li[l] + a * (long)r * r;
     const double* Va = st.V[l] + a * (long)r * (l * r);
     __syncthreads();
-    load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
+    load_knots(sh, l, st.mort[l][a], ax, ay);
     __syncthreads();
     auto xbar_epi = [&](int row, int col, double xb) {
       XB[(long)row * mr + l * r + col] = xb;

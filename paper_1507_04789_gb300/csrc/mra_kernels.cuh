@@ -146,7 +146,7 @@ __device__ __forceinline__ SRef sblock(const GradState& gs, const long* anc, int
 
 // Prediction points of one mra_predict call, sorted by leaf.
 struct PredState {
-  const int64_t* off;     // 4^M + 1 offsets of the prediction points per leaf
+  const int64_t* off;     // (leaves + 1) offsets of the prediction points per leaf (4^M leaves for the quadtree)
   const int64_t* perm;    // sorted position -> caller's index
   const double* xs;
   const double* ys;
@@ -166,13 +166,27 @@ struct PredState {
   // descriptor it reads (a streamed handle predicts chunk by chunk)
   long leaf0;
   int desc;
+  long nleaves;           // leaves of the complete tree (the launch's grid where it covers them all)
 };
 
 struct Shape {
   int M, r, gx, gy;
   double bbox[4];
   int mixed;              // 1: tensor-core (3xTF32) prior and leaf contractions
+  unsigned long long hx, hy;   // per-level midpoint halvings in x and y (4 bits per level)
 };
+
+// log2 J_M: the bits of a leaf's digit below its level-(M-1) parent (2 for the quadtree)
+__host__ __device__ __forceinline__ int leaf_bits(const Shape& sh) { return lvl_bits(sh.hx, sh.hy, sh.M); }
+
+// Quadtree halvings (one in x and one in y at every level).
+constexpr unsigned long long QUAD_HALVINGS = 0x1111111111110ull;
+
+// Fill sx/sy (shared) with the r knots of region (m, i).
+__device__ __forceinline__ void load_knots(const Shape& sh, int m, long i, double* sx, double* sy) {
+  Box b = region_box(sh.bbox, sh.hx, sh.hy, m, i);
+  for (int q = threadIdx.x; q < sh.gx * sh.gy; q += NT) knot_xy(b, sh.gx, sh.gy, q, sx[q], sy[q]);
+}
 
 // Everything a kernel needs about one dataset, in device memory.  A single
 // problem is a batch of one; batched launches map every CTA to a (dataset,

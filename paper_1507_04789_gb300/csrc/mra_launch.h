@@ -32,8 +32,8 @@ struct Timer {
 };
 
 // Tree build (Sec. 2.2): leaf of every observation, stable counting sort by leaf.
-cudaError_t launch_bin(const double* locs, int64_t n, const double* bbox_dev, int M,
-                       int32_t* leaf_id, int32_t* counts, int32_t* cursor, int64_t* off,
+cudaError_t launch_bin(const double* locs, int64_t n, const double* bbox_dev, int M, unsigned long long hx,
+                       unsigned long long hy, int32_t* leaf_id, int32_t* counts, int32_t* cursor, int64_t* off,
                        int64_t* sq_off, int32_t* max_count, int64_t* perm, int* status,
                        cudaStream_t s, int64_t* launches, bool stable = true);
 // Gather the sorted observations: xs, ys, yv from row-major locs (n x 2) and y.
@@ -163,7 +163,8 @@ cudaError_t launch_hbar_em(const Desc& hd, const Desc* d_desc, const GradState& 
                            int64_t* launches, long nregions = -1);
 
 // Identity tables of a complete tree with M levels (for callers without host tables).
-cudaError_t launch_identity_tree(const LevelState& st, int M, cudaStream_t s, int64_t* launches);
+cudaError_t launch_identity_tree(const LevelState& st, int M, unsigned long long hx, unsigned long long hy,
+                                 cudaStream_t s, int64_t* launches);
 
 // Error text and launch counter shared by every entry point (mra_api.cu).
 void set_last_error(const char* msg);

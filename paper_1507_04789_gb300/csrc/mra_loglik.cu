@@ -41,13 +41,13 @@ __global__ void __launch_bounds__(NT) prior_level_kernel(int m, const Desc* __re
   double* stg = W + MAX_R_DEV * (MAX_R_DEV + 1);
   __shared__ int bad;
   if (threadIdx.x == 0) bad = 0;
-  load_knots(sh.bbox, m, st.mort[m][i], sh.gx, sh.gy, qx, qy);
+  load_knots(sh, m, st.mort[m][i], qx, qy);
   double* Vrow = st.V[m] + i * (long)r * mr;
   TileAcc<TILE> acc;
   for (int l = 0; l < m; ++l) {
     const long a = ancestor(st, m, i, l);
     __syncthreads();
-    load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
+    load_knots(sh, l, st.mort[l][a], ax, ay);
     const double* Vanc = st.V[l] + a * (long)r * (l * r);
     acc.zero();
     if (l > 0) tile_mma<TILE>(acc, Vrow, mr, 1, r, Vanc, l * r, 1, r, l * r, stg);
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel(const Desc* __restrict__ D, co
   for (int l = 0; l < M; ++l) {
     const long a = ancestor(st, M, F, l);
     __syncthreads();
-    load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
+    load_knots(sh, l, st.mort[l][a], ax, ay);
     const double* Vanc = st.V[l] + a * (long)r * (l * r);
     __syncthreads();
     for (int rt = 0; rt < nrt; ++rt) {
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel(const Desc* __restrict__ 
   int k = 0;
   while (tri_index(k + 1, 0) <= t) ++k;
   const int l = t - tri_index(k, 0);
-  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
+  const long row0 = lf.off[pm << leaf_bits(ds.sh)], row1 = lf.off[(pm + 1) << leaf_bits(ds.sh)];
   const int K = (int)(row1 - row0);
   const double* Hb = lf.H + row0 * Mr;
   TileAcc<TILE> acc;

@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
   if (threadIdx.x == 0) bad = 0;
   Engine<EMU> eng;
   eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
-  for (int g = 0; g < G; ++g) load_knots(sh.bbox, m, st.mort[m][i + g], sh.gx, sh.gy, qx + g * r, qy + g * r);
+  for (int g = 0; g < G; ++g) load_knots(sh, m, st.mort[m][i + g], qx + g * r, qy + g * r);
   double* Vrow = st.V[m] + i * (long)r * mr;   // the group's rows are consecutive
   TcAcc acc;
   bool ok = true;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(NT) prior_level_kernel_tc(int m, const Desc* _
   for (int l = 0; l < m && ok; ++l) {
     const long a = ancestor(st, m, i, l);
     __syncthreads();
-    load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
+    load_knots(sh, l, st.mort[l][a], ax, ay);
     const double* Vanc = st.V[l] + a * (long)r * (l * r);
     if (EMU)
       for (int t = threadIdx.x; t < TC_M; t += NT) xsc[t] = -2000;
@@ -330,13 +330,13 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
   const long P = it.i;
   const int G = GRP && gcnt ? gcnt[blockIdx.x] : 1;   // (GRP false: one region, the loops below fold)
   const long pm = st.mort[M - 1][P];
-  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * (long)st.mort[M - 1][P + G - 1] + 4];
+  const long row0 = lf.off[pm << leaf_bits(ds.sh)], row1 = lf.off[((long)st.mort[M - 1][P + G - 1] + 1) << leaf_bits(ds.sh)];
   if (G > 1 && row1 - row0 > TC_M) {             // (a group of more than one tile: never formed by the host)
     if (threadIdx.x == 0) flag_error(status, ST_LIMIT, M - 1, P);
     return;
   }
   if (threadIdx.x <= G)
-    gseg[threadIdx.x] = (int)((threadIdx.x < G ? lf.off[4 * (long)st.mort[M - 1][P + threadIdx.x]] : row1) - row0);
+    gseg[threadIdx.x] = (int)((threadIdx.x < G ? lf.off[(long)st.mort[M - 1][P + threadIdx.x] << leaf_bits(ds.sh)] : row1) - row0);
   const int gx = sh.gx, gy = sh.gy;
   const bool fast = c0_fast_ok(cv, gx, gy);
   const double c0s = c0_scale(cv), is2 = 1.0 / cv.sigma2;
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(NT) chain_forward_kernel_em(const Desc* __rest
       if (nr == 0) continue;                     // (uniform: a region without observations)
       double* Hseg = Hrow + (long)ra * Mr;
       __syncthreads();
-      load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
+      load_knots(sh, l, st.mort[l][a], ax, ay);
       const double* Vanc = st.V[l] + a * (long)r * (l * r);
       for (int t = threadIdx.x; t < TC_M; t += NT) xsc[t] = -2000;
       __syncthreads();
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(NT) leaf_kernel_tc(const Desc* __restrict__ D,
   for (int l = 0; l < M && ok && !(EMU && chain_done); ++l) {
     const long a = ancestor(st, M, F, l);
     __syncthreads();
-    load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
+    load_knots(sh, l, st.mort[l][a], ax, ay);
     const double* Vanc = st.V[l] + a * (long)r * (l * r);
     if (EMU)
       for (int t = threadIdx.x; t < TC_M; t += NT) xsc[t] = -2000;
@@ -856,7 +856,7 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em1(const Desc* __restric
   if (!em_tile(tile, M, S, 1, l, k0)) return;     // fewer tiles in a shallower dataset
   const int nk = min(S, M - k0);                      // row blocks k0 .. k0 + nk - 1
   const long pm = st.mort[M - 1][p];
-  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
+  const long row0 = lf.off[pm << leaf_bits(ds.sh)], row1 = lf.off[(pm + 1) << leaf_bits(ds.sh)];
   const int K = (int)(row1 - row0);
   const double* Hb = lf.H + row0 * Mr;
   Engine<true> eng;
@@ -871,10 +871,10 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em1(const Desc* __restric
     int e = -2000;
     if (i < (isA ? nk * r : r)) {
       const int col = isA ? k0 * r + i : l * r + i;
-      for (int c = 0; c < 4; ++c) {
-        const long lo = lf.off[4 * pm + c] - row0, hi = lf.off[4 * pm + c + 1] - row0;
+      for (int c = 0; c < (1 << leaf_bits(ds.sh)); ++c) {
+        const long lo = lf.off[(pm << leaf_bits(ds.sh)) + c] - row0, hi = lf.off[(pm << leaf_bits(ds.sh)) + c + 1] - row0;
         if (hi > lo && lo < (long)(g + 1) * EM_KG && hi > (long)g * EM_KG) {
-          const int cl = st.cid[M][4 * pm + c];
+          const int cl = st.cid[M][(pm << leaf_bits(ds.sh)) + c];
           e = max(e, lf.hcol[(long)cl * Mr + col]);
         }
       }
@@ -928,7 +928,7 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict
   const int nk = min(S, M - k0);                      // row blocks k0 .. k0 + nk - 1
   const int nl = MULTI ? min(CB, M - l) : 1;          // column blocks l .. l + nl - 1
   const long pm = st.mort[M - 1][p];
-  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
+  const long row0 = lf.off[pm << leaf_bits(ds.sh)], row1 = lf.off[(pm + 1) << leaf_bits(ds.sh)];
   const int K = (int)(row1 - row0);
   const double* Hb = lf.H + row0 * Mr;
   Engine<true> eng;
@@ -943,10 +943,10 @@ __global__ void __launch_bounds__(NT) leaf_syrk_kernel_em(const Desc* __restrict
     int e = -2000;
     if (i < (isA ? nk * r : nl * r)) {
       const int col = isA ? k0 * r + i : l * r + i;
-      for (int c = 0; c < 4; ++c) {
-        const long lo = lf.off[4 * pm + c] - row0, hi = lf.off[4 * pm + c + 1] - row0;
+      for (int c = 0; c < (1 << leaf_bits(ds.sh)); ++c) {
+        const long lo = lf.off[(pm << leaf_bits(ds.sh)) + c] - row0, hi = lf.off[(pm << leaf_bits(ds.sh)) + c + 1] - row0;
         if (hi > lo && lo < (long)(g + 1) * EM_KG && hi > (long)g * EM_KG) {
-          const int cl = st.cid[M][4 * pm + c];
+          const int cl = st.cid[M][(pm << leaf_bits(ds.sh)) + c];
           e = max(e, lf.hcol[(long)cl * Mr + col]);
         }
       }
@@ -1233,7 +1233,7 @@ __global__ void __launch_bounds__(NT) hbar_kernel_em(const Desc* __restrict__ D,
   const int l = (int)(blockIdx.x % M);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long pm = st.mort[M - 1][p];
-  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
+  const long row0 = lf.off[pm << leaf_bits(ds.sh)], row1 = lf.off[(pm + 1) << leaf_bits(ds.sh)];
   const long al = ancestor(st, M - 1, p, l);
   for (int t = threadIdx.x; t < r; t += NT) wb[t] = gs.Obar[l][al * r + t];
   Engine<true> eng;
@@ -1297,7 +1297,7 @@ __global__ void __launch_bounds__(NT) leaf_partial_kernel_em(const Desc* __restr
   if (!partial_tile((int)(blockIdx.x % nt), M, em_stack(r), k, l0, nl)) return;
   const bool diag = l0 == k;
   const long pm = ds.st.mort[M - 1][p];
-  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
+  const long row0 = lf.off[pm << leaf_bits(ds.sh)], row1 = lf.off[(pm + 1) << leaf_bits(ds.sh)];
   const int K = (int)(row1 - row0);
   const double* A = (diag ? gs.VBF : gs.XBF) + row0 * Mr + l0 * r;
   const double* B = lf.VF + row0 * Mr + k * r;
@@ -1361,7 +1361,7 @@ __global__ void __launch_bounds__(NT) chain_adjoint_kernel_em(const Desc* __rest
   const LeafState& lf = ds.lf;
   const long p = gs.rbase + blockIdx.x;
   const long pm = st.mort[M - 1][p];
-  const long row0 = lf.off[4 * pm], row1 = lf.off[4 * pm + 4];
+  const long row0 = lf.off[pm << leaf_bits(ds.sh)], row1 = lf.off[(pm + 1) << leaf_bits(ds.sh)];
   Engine<true> eng;
   eng.init(dsm, mbar, &tmem_slot, &fail, rexp, cexp);
   TcAcc acc;
@@ -1390,7 +1390,7 @@ __global__ void __launch_bounds__(NT) chain_adjoint_kernel_em(const Desc* __rest
       const double* Lia = st.Li[l] + a * (long)r * r;
       const double* Va = st.V[l] + a * (long)r * (l * r);
       __syncthreads();                           // the previous level's knots and Xbar scales are no longer read
-      load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
+      load_knots(sh, l, st.mort[l][a], ax, ay);
       for (int t = threadIdx.x; t < TC_M; t += NT) {
         xbsc[t] = -2000;
         if (l > 0) vbsc[(l - 1) * TC_M + t] = -2000;   // block l - 1 takes its last update at this level

@@ -106,6 +106,8 @@ extern "C" int mra_loglik_noalloc(const mra_config* cfg, const mra_params* theta
   if (n < 1) return err(MRA_ERR_ARG, "n must be >= 1");
   if (cfg->M < 0 || cfg->M > MRA_MAX_M) return err(MRA_ERR_ARG, "M must be in [0, %d]", MRA_MAX_M);
   if (cfg->J != 4) return err(MRA_ERR_ARG, "J must be 4 (2-D midpoint quadtree)");
+  if (cfg->J_level[0] != 0)
+    return err(MRA_ERR_ARG, "level-varying J needs mra_build (the allocation-free entry point takes the quadtree)");
   if (cfg->r < 1 || cfg->r > MRA_MAX_R) return err(MRA_ERR_ARG, "r must be in [1, %d]", MRA_MAX_R);
   if (cfg->cov_family != MRA_COV_EXP && cfg->cov_family != MRA_COV_MATERN15 && cfg->cov_family != MRA_COV_MATERN)
     return err(MRA_ERR_ARG, "unknown covariance family %d", cfg->cov_family);
@@ -166,7 +168,8 @@ extern "C" int mra_loglik_noalloc(const mra_config* cfg, const mra_params* theta
   if ((e = cudaMemcpyAsync(bbox, cfg->bbox, sizeof(double) * 4, cudaMemcpyHostToDevice, s)) ||
       (e = cudaMemsetAsync(status, 0, sizeof(int) * 4, s)))
     return cuda_err(e, "init");
-  if ((e = mra::launch_bin(locs, n, bbox, M, leaf_id, counts, cursor, off, sq_off, max_count, perm, status, s,
+  if ((e = mra::launch_bin(locs, n, bbox, M, mra::QUAD_HALVINGS, mra::QUAD_HALVINGS, leaf_id, counts, cursor, off,
+                           sq_off, max_count, perm, status, s,
                            launches)))
     return cuda_err(e, "binning");
   int hs[4];
@@ -234,6 +237,7 @@ extern "C" int mra_loglik_noalloc(const mra_config* cfg, const mra_params* theta
   sh.gy = r / sh.gx;
   for (int k = 0; k < 4; ++k) sh.bbox[k] = cfg->bbox[k];
   sh.mixed = 0;
+  sh.hx = sh.hy = mra::QUAD_HALVINGS;
   mra::Desc hd{};
   hd.sh = sh;
   hd.cv = mra::make_cov(theta->sigma2, theta->range, cfg->cov_family, cfg->nonstat, theta->nu);
@@ -256,7 +260,7 @@ extern "C" int mra_loglik_noalloc(const mra_config* cfg, const mra_params* theta
     plan.t_syrk = M * (M + 1) / 2;
   }
   mra::Timer no_timer;
-  if ((e = mra::launch_identity_tree(st, M, s, launches)) ||
+  if ((e = mra::launch_identity_tree(st, M, mra::QUAD_HALVINGS, mra::QUAD_HALVINGS, s, launches)) ||
       (e = cudaMemcpyAsync(d_desc, &hd, sizeof hd, cudaMemcpyHostToDevice, s)) ||
       (e = mra::launch_gather(locs, y, perm, n, xs, ys, yv, s, launches)) ||
       (e = mra::launch_loglik(plan, d_desc, status, s, launches, &no_timer)))

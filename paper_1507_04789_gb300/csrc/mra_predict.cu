@@ -50,8 +50,9 @@ __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D,
   if (p0 >= p1) return;
   const int nP = (int)(p1 - p0);
   long anc[MAXL];                                // compact ids of the ancestors
+  const int dM = lvl_depth(sh.hx, sh.hy, M);
   for (int l = 0; l < M; ++l) {
-    anc[l] = st.cid[l][F >> (2 * (M - l))];
+    anc[l] = st.cid[l][F >> (dM - lvl_depth(sh.hx, sh.hy, l))];
     if (anc[l] < 0) {                            // pruned tree: no data above this point
       if (threadIdx.x == 0) flag_error(status, ST_ARG, l, F);
       return;
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(NT) predict_kernel(const Desc* __restrict__ D,
   for (int l = 0; l < M; ++l) {
     const long a = anc[l];
     __syncthreads();
-    load_knots(sh.bbox, l, st.mort[l][a], sh.gx, sh.gy, ax, ay);
+    load_knots(sh, l, st.mort[l][a], ax, ay);
     __syncthreads();
     acc.zero();
     if (l > 0) tile_mma_r<TP, TILE>(acc, U, Mr, 1, nP, st.V[l] + a * (long)r * (l * r), l * r, 1, r, l * r, stg);
@@ -273,7 +274,7 @@ cudaError_t launch_predict(const Desc* d_desc, int M, int r, int nlmax, const Pr
   // covers a block's r knots)
   const int tp = max_per_leaf <= 16 ? 16 : tile;
   const size_t sm = predict_smem_tp(tp, r, nlmax);
-  dim3 grid(nleaf > 0 ? (unsigned)nleaf : 1u << (2 * M), (unsigned)((max_per_leaf + tp - 1) / tp));
+  dim3 grid(nleaf > 0 ? (unsigned)nleaf : (unsigned)ps.nleaves, (unsigned)((max_per_leaf + tp - 1) / tp));
   if (grid.y == 0) return cudaSuccess;
   cudaError_t e;
   tm->start(5, s);
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(NT) joint_cov_kernel(const Desc* __restrict__ 
       Yb[p][c] = p < nj ? ps.U[(j0 + p) * Mr + l * r + c] : 0.0;
     }
     __syncthreads();
-    const int sh = 2 * (M - l);
+    const int sh = lvl_depth(ds.sh.hx, ds.sh.hy, M) - lvl_depth(ds.sh.hx, ds.sh.hy, l);
     bool any = false;
     bool same[4][4];
 #pragma unroll
@@ -367,7 +368,8 @@ __global__ void __launch_bounds__(NT) joint_cov_kernel(const Desc* __restrict__ 
 
 // ---- conditional simulation ------------------------------------------------------
 // draw[s][perm p] = mean[perm p] + sum_l Y_l(p) xi[s][(o_l + R_l) r ..] + sum_{q <= p in the leaf}
-// chol(D)(p, q) zeta[s][perm q]; o_l = (4^l - 1) / 3 regions before level l.  One CTA
+// chol(D)(p, q) zeta[s][perm q]; o_l = the regions of the complete tree's levels < l
+// ((4^l - 1) / 3 for the quadtree).  One CTA
 // per (leaf, chunk of 4 draws), one thread per (point, draw).
 __global__ void __launch_bounds__(NT) simulate_kernel(const Desc* __restrict__ D, PredState ps, int64_t np,
                                                       int64_t nsim, int64_t nxi, const double* __restrict__ xi,
@@ -378,6 +380,18 @@ __global__ void __launch_bounds__(NT) simulate_kernel(const Desc* __restrict__ D
   const int M = ds.sh.M, r = ds.sh.r, Mr = M * r;
   const long F = blockIdx.x;
   const long p0 = ps.off[F];
+  __shared__ long o_reg[MAXL];                   // regions before level l, and the shift to the level-l id
+  __shared__ int d_reg[MAXL];
+  if (threadIdx.x == 0) {
+    const int dM = lvl_depth(ds.sh.hx, ds.sh.hy, M);
+    long o = 0;
+    for (int l = 0; l < M; ++l) {
+      o_reg[l] = o;
+      d_reg[l] = dM - lvl_depth(ds.sh.hx, ds.sh.hy, l);
+      o += 1L << lvl_depth(ds.sh.hx, ds.sh.hy, l);
+    }
+  }
+  __syncthreads();
   const int nP = (int)(ps.off[F + 1] - p0);
   if (nP == 0) return;
   const double* Lc = ps.D + ps.sq_off[F];
@@ -386,7 +400,7 @@ __global__ void __launch_bounds__(NT) simulate_kernel(const Desc* __restrict__ D
     for (int t = threadIdx.x; t < 4 * Mr; t += NT) {
       const int d = t / Mr, c = t - d * Mr, l = c / r;
       const long s = s0 + d;
-      const long reg = (((1L << (2 * l)) - 1) / 3) + (F >> (2 * (M - l)));
+      const long reg = o_reg[l] + (F >> d_reg[l]);
       xs[d][c] = s < nsim ? xi[s * nxi + reg * r + (c - l * r)] : 0.0;
     }
     for (int t = threadIdx.x; t < 4 * nP; t += NT) {
@@ -411,7 +425,7 @@ __global__ void __launch_bounds__(NT) simulate_kernel(const Desc* __restrict__ D
 cudaError_t launch_predict_joint(const Desc* d_desc, int M, int r, int nlmax, const PredState& ps, int mode,
                                  int* status, cudaStream_t s, int64_t* launches, Timer* tm) {
   const size_t sm = joint_smem_bytes(r, nlmax);
-  dim3 grid(1u << (2 * M), 1);
+  dim3 grid((unsigned)ps.nleaves, 1);
   cudaError_t e;
   tm->start(5, s);
   if (mode == 1) {
@@ -441,7 +455,7 @@ cudaError_t launch_joint_cov(const Desc* d_desc, const PredState& ps, int64_t np
 cudaError_t launch_simulate(const Desc* d_desc, int M, const PredState& ps, int64_t np, int64_t nsim, int64_t nxi,
                             const double* xi, const double* zeta, double* draws, cudaStream_t s, int64_t* launches) {
   const unsigned gy = (unsigned)std::min<int64_t>((nsim + 3) / 4, 64);
-  simulate_kernel<<<dim3(1u << (2 * M), gy), NT, 0, s>>>(d_desc, ps, np, nsim, nxi, xi, zeta, draws);
+  simulate_kernel<<<dim3((unsigned)ps.nleaves, gy), NT, 0, s>>>(d_desc, ps, np, nsim, nxi, xi, zeta, draws);
   ++*launches;
   return cudaGetLastError();
 }

@@ -1,18 +1,20 @@
 // mra_tree.cu -- partition of the observations (Sec. 2.2) on the device.
 //
-// Every point descends the midpoint quadtree to its leaf (reading: half-open
-// cells [lo, mid), [mid, hi], child j = b_x + 2 b_y, the last cell closed at
-// the bounding box), then a counting sort by leaf gives contiguous, Morton-
-// ordered leaves; a per-leaf rank sort restores the original order inside a
+// Every point descends the partition to its leaf (reading: half-open cells
+// [lo, mid), [mid, hi], the last cell closed at the bounding box; level m cuts
+// every region into 2^hx_m x 2^hy_m children by repeated midpoint halving, child
+// j = c_x + 2^hx_m c_y; the quadtree is hx = hy = 1, j = b_x + 2 b_y), then a
+// counting sort by leaf gives contiguous leaves in region-id (for the quadtree
+// Morton) order; a per-leaf rank sort restores the original order inside a
 // leaf so that the result does not depend on atomic ordering.
 #include "mra_launch.h"
 
 namespace mra {
 
 __global__ void leaf_id_kernel(const double* __restrict__ locs, int64_t n,
-                               const double* __restrict__ bbox, int M,
-                               int32_t* __restrict__ leaf_id, int32_t* __restrict__ counts,
-                               int* status) {
+                               const double* __restrict__ bbox, int M, unsigned long long hx,
+                               unsigned long long hy, int32_t* __restrict__ leaf_id,
+                               int32_t* __restrict__ counts, int* status) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double x = locs[2 * i], y = locs[2 * i + 1];
@@ -23,12 +25,22 @@ __global__ void leaf_id_kernel(const double* __restrict__ locs, int64_t n,
     return;
   }
   int32_t idx = 0;
-  for (int t = 0; t < M; ++t) {
-    double xm = 0.5 * (x0 + x1), ym = 0.5 * (y0 + y1);
-    int bx = x >= xm, by = y >= ym;
-    if (bx) x0 = xm; else x1 = xm;
-    if (by) y0 = ym; else y1 = ym;
-    idx = 4 * idx + bx + 2 * by;
+  for (int t = 1; t <= M; ++t) {
+    const int a = lvl_hx(hx, t), c = lvl_hx(hy, t);
+    int cx = 0, cy = 0;
+    for (int q = 0; q < a; ++q) {
+      const double xm = 0.5 * (x0 + x1);
+      const int b = x >= xm;
+      if (b) x0 = xm; else x1 = xm;
+      cx = 2 * cx + b;
+    }
+    for (int q = 0; q < c; ++q) {
+      const double ym = 0.5 * (y0 + y1);
+      const int b = y >= ym;
+      if (b) y0 = ym; else y1 = ym;
+      cy = 2 * cy + b;
+    }
+    idx = (idx << (a + c)) + cx + (cy << a);
   }
   leaf_id[i] = idx;
   atomicAdd(&counts[idx], 1);
@@ -130,15 +142,15 @@ __global__ void gather_y_kernel(const double* __restrict__ y, const int64_t* __r
 
 static unsigned blocks_for(int64_t n) { return (unsigned)((n + 255) / 256); }
 
-cudaError_t launch_bin(const double* locs, int64_t n, const double* bbox_dev, int M,
-                       int32_t* leaf_id, int32_t* counts, int32_t* cursor, int64_t* off,
+cudaError_t launch_bin(const double* locs, int64_t n, const double* bbox_dev, int M, unsigned long long hx,
+                       unsigned long long hy, int32_t* leaf_id, int32_t* counts, int32_t* cursor, int64_t* off,
                        int64_t* sq_off, int32_t* max_count, int64_t* perm, int* status,
                        cudaStream_t s, int64_t* launches, bool stable) {
-  const int64_t nl = int64_t(1) << (2 * M);
+  const int64_t nl = int64_t(1) << lvl_depth(hx, hy, M);
   cudaError_t e;
   if ((e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * nl, s))) return e;
   if ((e = cudaMemsetAsync(cursor, 0, sizeof(int32_t) * nl, s))) return e;
-  leaf_id_kernel<<<blocks_for(n), 256, 0, s>>>(locs, n, bbox_dev, M, leaf_id, counts, status);
+  leaf_id_kernel<<<blocks_for(n), 256, 0, s>>>(locs, n, bbox_dev, M, hx, hy, leaf_id, counts, status);
   scan_kernel<<<1, 1024, 0, s>>>(counts, nl, off, sq_off, max_count);
   scatter_kernel<<<blocks_for(n), 256, 0, s>>>(leaf_id, n, off, cursor, perm);
   if (stable) segsort_kernel<<<(unsigned)nl, 256, 0, s>>>(off, perm, status);
@@ -165,23 +177,25 @@ cudaError_t launch_gather_y(const double* y, const int64_t* perm, int64_t n, dou
 namespace mra {
 
 // Tables of a complete tree (every region active): identity maps.
-__global__ void identity_tree_kernel(LevelState st, int M) {
+__global__ void identity_tree_kernel(LevelState st, int M, unsigned long long hx, unsigned long long hy) {
   for (int m = 0; m <= M; ++m) {
-    const long cnt = 1L << (2 * m);
+    const long cnt = 1L << lvl_depth(hx, hy, m);
+    const int bm = m > 0 ? lvl_bits(hx, hy, m) : 0, bc = m < M ? lvl_bits(hx, hy, m + 1) : 0;
     for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < cnt; c += (long)gridDim.x * blockDim.x) {
       st.mort[m][c] = (int32_t)c;
       st.cid[m][c] = (int32_t)c;
-      if (m > 0) st.par[m][c] = (int32_t)(c >> 2);
+      if (m > 0) st.par[m][c] = (int32_t)(c >> bm);
       if (m < M) {
-        st.cfirst[m][c] = (int32_t)(4 * c);
-        st.ccnt[m][c] = 4;
+        st.cfirst[m][c] = (int32_t)(c << bc);
+        st.ccnt[m][c] = 1 << bc;
       }
     }
   }
 }
 
-cudaError_t launch_identity_tree(const LevelState& st, int M, cudaStream_t s, int64_t* launches) {
-  identity_tree_kernel<<<256, 256, 0, s>>>(st, M);
+cudaError_t launch_identity_tree(const LevelState& st, int M, unsigned long long hx, unsigned long long hy,
+                                 cudaStream_t s, int64_t* launches) {
+  identity_tree_kernel<<<256, 256, 0, s>>>(st, M, hx, hy);
   *launches += 1;
   return cudaGetLastError();
 }

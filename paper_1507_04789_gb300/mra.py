@@ -39,11 +39,27 @@ class MRAError(RuntimeError):
         self.code = code
 
 
+MRA_MAX_M = 12
+
+
 class MraConfig(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("J", ctypes.c_int), ("r", ctypes.c_int),
                 ("cov_family", ctypes.c_int), ("nonstat", ctypes.c_int),
                 ("precision", ctypes.c_int), ("prune", ctypes.c_int), ("bbox", ctypes.c_double * 4),
-                ("stream_level", ctypes.c_int)]
+                ("stream_level", ctypes.c_int), ("J_level", ctypes.c_int * MRA_MAX_M)]
+
+
+def _set_J(cfg: MraConfig, J, M: int) -> None:
+    """J: children per region, one number for every level or (J_1, ..., J_M)."""
+    if isinstance(J, (int, np.integer)):
+        cfg.J = int(J)
+        return
+    Js = tuple(int(j) for j in J)
+    if len(Js) != M:
+        raise ValueError("J needs one entry per level 1..M")
+    cfg.J = 4
+    for k, j in enumerate(Js):
+        cfg.J_level[k] = j
 
 
 class MraParams(ctypes.Structure):
@@ -51,7 +67,6 @@ class MraParams(ctypes.Structure):
                 ("nu", ctypes.c_double)]
 
 
-MRA_MAX_M = 12
 STAGES = ("prior", "chain", "leaf", "leaf_syrk", "post", "aggregate")   # MRA_STAGE_* order
 
 
@@ -170,14 +185,16 @@ class Handle:
     """One M-RA problem on the GPU: locations, data and the tree (Sec. 2.2)."""
 
     def __init__(self, locs, y, M: int, r: int, family: str = "exp", nonstat: bool = False,
-                 bbox=(0.0, 1.0, 0.0, 1.0), J: int = 4, precision="fp64", prune: bool = False,
+                 bbox=(0.0, 1.0, 0.0, 1.0), J=4, precision="fp64", prune: bool = False,
                  stream_level: int = 0):
+        """J: children per region, 4 (the quadtree) or a level-varying (J_1, ..., J_M)."""
         lib = load_library()
         self._lib = lib
         self._h = _P()
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-        cfg = MraConfig(M, J, r, FAMILIES[family] if isinstance(family, str) else int(family),
+        cfg = MraConfig(M, 4, r, FAMILIES[family] if isinstance(family, str) else int(family),
                         int(bool(nonstat)), prec, int(bool(prune)), (ctypes.c_double * 4)(*bbox), int(stream_level))
+        _set_J(cfg, J, M)
         if _is_torch_cuda(locs):
             if locs.dim() != 2 or locs.shape[1] != 2:
                 raise ValueError("locs must be (n, 2)")
@@ -372,14 +389,20 @@ class Handle:
 
     def region_terms(self, level: int):
         """(d_R, u_R) of every region at ``level`` from the last loglik (Sec. 3.3)."""
-        cnt = 4 ** level
+        cnt = self.nregions(level)
         d = np.empty(cnt)
         u = np.empty(cnt)
         _check(self._lib.mra_region_terms(self._h, level, d.ctypes.data, u.ctypes.data))
         return d, u
 
+    def nregions(self, level: int) -> int:
+        """Regions of ``level`` in the complete tree: J_1 ... J_level."""
+        if isinstance(self.J, (int, np.integer)):
+            return int(self.J) ** level
+        return int(np.prod([int(j) for j in self.J[:level]], dtype=np.int64))
+
     def leaf_offsets(self, with_perm: bool = False):
-        off = np.empty(4 ** self.M + 1, dtype=np.int64)
+        off = np.empty(self.nregions(self.M) + 1, dtype=np.int64)
         perm = np.empty(self.n, dtype=np.int64) if with_perm else None
         _check(self._lib.mra_leaf_offsets(self._h, off.ctypes.data, perm.ctypes.data if with_perm else None))
         return (off, perm) if with_perm else off
@@ -412,6 +435,7 @@ class Batch:
             cfgs[d] = MraConfig(int(ds["M"]), 4, r, FAMILIES[fam] if isinstance(fam, str) else int(fam),
                                 int(bool(ds.get("nonstat", False))), prec, int(bool(ds.get("prune", True))),
                                 (ctypes.c_double * 4)(*ds.get("bbox", (0.0, 1.0, 0.0, 1.0))))
+            _set_J(cfgs[d], ds.get("J", 4), int(ds["M"]))
             lp[d] = la.ctypes.data
             yp[d] = ya.ctypes.data
             ns[d] = la.shape[0]

@@ -55,3 +55,16 @@ def test_argument_errors_need_no_gpu(lib):
     assert ei.value.code == mra.MRA_ERR_ARG
     with pytest.raises(mra.MRAError):
         mra.Handle(np.zeros((4, 2)), np.zeros(4), M=13, r=16)
+
+
+@pytest.mark.parametrize("M,J", [(2, (2, 6)), (2, (4, 8)), (2, (16, 16)), (7, (16,) * 6 + (4,)), (1, (1,))])
+def test_level_varying_J_errors_need_no_gpu(lib, M, J):
+    """Level-varying J (Sec. 2.2): each J_m in {2, 4, 8, 16}, J_M (the leaves'
+    level) 2 or 4, at most 2^24 leaves; rejected on the host."""
+    from paper_1507_04789_gb300 import mra
+    import numpy as np
+    with pytest.raises(mra.MRAError) as ei:
+        mra.Handle(np.zeros((4, 2)), np.zeros(4), M=M, r=16, J=J)
+    assert ei.value.code == mra.MRA_ERR_ARG
+    with pytest.raises(ValueError):
+        mra.Handle(np.zeros((4, 2)), np.zeros(4), M=3, r=16, J=(2, 4))   # one J_m per level
