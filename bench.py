@@ -135,22 +135,22 @@ def contraction_flops(M: int, r: int, nF, precision: str):
 SOURCES_EMU = ["mra_mixed.cu", "mra_emu.cuh", "mra_tc.cuh", "mra_device.cuh", "mra_kernels.cuh"]
 TRAFFIC = {
     ("emu", "chain_forward_kernel_em", "n1M_matern15_M7_r64"): {
-        "bytes": 5.880e+09,
-        "how": "dram__bytes_read.sum + dram__bytes_write.sum of chain_forward_kernel_em (495.3 + 764.7 MB) "
+        "bytes": 5.8848e+09,
+        "how": "dram__bytes_read.sum + dram__bytes_write.sum of chain_forward_kernel_em (496.9 + 764.1 MB) "
                "at n = 2^18, M = 6 (profiles/leaf_stage_emu_n256k_matern15_M6_r64.md), scaled by n M r "
                "(x 4.667) to n = 2^20, M = 7; the kernel writes V_F (8 B x n x M r) and reads the points "
                "and the ancestors' factors, both in proportion to n M r",
         "sources": SOURCES_EMU,
-        "sha1": "198514b731991d5f3e0f4e0131fcd1d99210d12c",
+        "sha1": "b81bedf3ad29b200868afd73e315bd8a28f3e961",
     },
     ("emu", "leaf_kernel_tc<1>", "n1M_matern15_M7_r64"): {
-        "bytes": 8.032e+09,
-        "how": "dram__bytes_read.sum + dram__bytes_write.sum of leaf_kernel_tc<1> (823.2 + 897.8 MB) at "
+        "bytes": 8.0241e+09,
+        "how": "dram__bytes_read.sum + dram__bytes_write.sum of leaf_kernel_tc<1> (824.8 + 894.6 MB) at "
                "n = 2^18, M = 6 (profiles/leaf_stage_emu_n256k_matern15_M6_r64.md), scaled by n M r (x 4.667) "
                "to n = 2^20, M = 7; the kernel reads V_F and writes H (8 B x n x M r each) and the "
                "L_Sigma^{-1} blocks (8 B x sum n_F^2, about 1/7 of it)",
         "sources": SOURCES_EMU,
-        "sha1": "198514b731991d5f3e0f4e0131fcd1d99210d12c",
+        "sha1": "b81bedf3ad29b200868afd73e315bd8a28f3e961",
     },
 }
 
