@@ -591,6 +591,42 @@ def run_prediction(args, world, rank, mra, np, torch, stream, handles, w, theta0
     return out
 
 
+# Sec. 4.3's level-varying J_m = (2, 2, 4, 8, 8, 16) with its last level taken as two quadtree levels
+# (J_M = 16 at the leaves is not supported): the same 16384 leaves (a 128 x 128 grid) as the paper's
+# sequence and as the M = 7 quadtree, about 64 observations each at n = 2^20.
+LEVEL_J = (2, 2, 4, 8, 8, 4, 4)
+
+
+def run_level_J(args, mra, np, torch, stream, locs, y, w, thetas):
+    """The same observations on a level-varying partition: the emulated form's
+    log-likelihood rate (CUDA events, inputs resident) and its difference from
+    the FP64 form's at one theta."""
+    if args.no_level_j:
+        return None
+    steps = max(2, args.steps // 2)
+    with mra.Handle(locs, y, M=len(LEVEL_J), r=w.r, J=LEVEL_J, family=w.family, precision="emu") as h, \
+            mra.Handle(locs, y, M=len(LEVEL_J), r=w.r, J=LEVEL_J, family=w.family) as h64:
+        h.set_stream(stream)
+        for k in range(args.warmup):
+            h.loglik(thetas[k])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(steps):
+            ll = h.loglik(thetas[k])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        ll64 = h64.loglik(thetas[steps - 1])
+        off = h.leaf_offsets()
+    cnt = np.diff(off)
+    return {"J": list(LEVEL_J), "M": len(LEVEL_J), "r": w.r, "leaves": int(cnt.shape[0]),
+            "max_leaf": int(cnt.max()), "precision": "emu", "ms_per_step": ms, "value": 1e3 / ms,
+            "unit": "evals/s", "dloglik_per_obs_vs_fp64": abs(ll - ll64) / w.n,
+            "what": "the headline's observations on Sec. 4.3's J structure (last J = 16 as 4 x 4)"}
+
+
 def run_sharded(args, rank, world, local, mra, np, torch):
     """N > 1: one n = 2^20 problem sharded over the ranks' GPUs by level-2 subtrees."""
     import torch.distributed as dist
@@ -758,6 +794,7 @@ def main():
                     help="level of the streamed subtrees for the n = 2^24 swath workload (3: 64 subtrees, so "
                          "that the gradient's chunk buffers keep the run within 180 GB)")
     ap.add_argument("--no-mle", action="store_true", help="skip the 20-step maximum-likelihood fit")
+    ap.add_argument("--no-level-j", action="store_true", help="skip the level-varying J partition")
     ap.add_argument("--grad-only", action="store_true",
                     help="time only loglik + gradient in the emulated form (the launch list of the gradient)")
     args = ap.parse_args()
@@ -1008,6 +1045,7 @@ def main():
         if handles[p] is not h:
             handles[p].close()
     batch = None if args.no_batch else run_batch(args, world, rank, mra, np, torch)
+    level_J = run_level_J(args, mra, np, torch, stream, locs, y, w, thetas)
 
     if rank == 0:
         dtypes = {"fp64": "f64", "mixed": "f64+tf32x3", "emu": "f64+bf16x7 (emulated f64)"}
@@ -1032,7 +1070,7 @@ def main():
             "clocks": head["clocks"],
             "emu": form_line("emu"), "mixed": form_line("mixed"), "fp64": form_line("fp64"),
             "gradient": gradient, "loglik": head["lls"][-1], "flops_per_step": total_flops,
-            "batch": batch, "prediction": prediction, "oracle_check": oracle_check,
+            "batch": batch, "prediction": prediction, "oracle_check": oracle_check, "level_J": level_J,
         }
         for p in ("emu", "mixed", "fp64"):
             line[p]["per_level"] = [{k: r_[k] for k in ("level", "stage", "ms_per_step", "alg_tflops", "frac",

@@ -443,8 +443,9 @@ int mra_stats(mra_handle* h, mra_stats_t* out);
  * loads the library holds until the process exits (enough for problems of
  * roughly n = 16k with M = 4, r = 16, or n = 4096 with M = 3, r = 64).
  *   cfg, theta : as for mra_build / mra_loglik (host), except that only
- *                precision = MRA_PREC_FP64 and prune = 0 (complete tree) are
- *                supported; other values give MRA_ERR_ARG naming the field.
+ *                precision = MRA_PREC_FP64, prune = 0 (complete tree) and the
+ *                quadtree (J_level all zero) are supported; other values give
+ *                MRA_ERR_ARG naming the field.
  *   locs, y    : device (or managed) pointers, n x 2 row-major locations and
  *                n data; host memory is refused with MRA_ERR_ARG before any
  *                kernel runs.
