@@ -270,8 +270,8 @@ int mra_simulate_xi_len(mra_handle* h, int64_t* len_out);
  *
  * mra_summary_len -- doubles per summary (*len_out: the level-s region's
  *   A-hat blocks, T_s r^2 with T_s = (s+1)(s+2)/2, its omega-hat, (s+1) r, and
- *   the (d, u) of up to four children, 8) and the number of level-s regions
- *   (*nsub_out, compact order).
+ *   the (d, u) of up to J_{s+1} children, 2 J_{s+1}: 8 for the quadtree) and
+ *   the number of level-s regions (*nsub_out, compact order).
  * mra_loglik_subtrees -- at theta: the prior of levels 0..s, then the
  *   subtrees of level-s regions [first, first + count) (prior, leaves,
  *   posterior up to the level-s aggregation); out (host, count x len) gets

@@ -1104,9 +1104,11 @@ int mra_loglik(mra_handle* h, const mra_params* theta, double* loglik_out) {
 // ---------------------------------------------------------------------------
 // Summary of a level-s region R after its subtree: A-hat_R (T_s packed r x r
 // blocks), omega-hat_R ((s + 1) r) and the (d, u) of its (up to 4) children.
+// Ahat and omegahat of a level-s region, then the (d, u) of each of its J_{s+1}
+// possible children (8 doubles for the quadtree).
 static int64_t summary_len(const mra_handle* h) {
   const int64_t s = h->s_lvl, r = h->r;
-  return (s + 1) * (s + 2) / 2 * r * r + (s + 1) * r + 8;
+  return (s + 1) * (s + 2) / 2 * r * r + (s + 1) * r + 2 * (int64_t(1) << h->tab.bits[s + 1]);
 }
 
 int mra_summary_len(mra_handle* h, int64_t* len_out, int64_t* nsub_out) {
@@ -1164,7 +1166,7 @@ int mra_loglik_subtrees(mra_handle* h, const mra_params* theta, int64_t first, i
     memcpy(o, A.data() + k * T * r * r, sizeof(double) * T * r * r);
     memcpy(o + T * r * r, Om.data() + k * (s + 1) * r, sizeof(double) * (s + 1) * r);
     double* du = o + T * r * r + (s + 1) * r;
-    for (int j = 0; j < 8; ++j) du[j] = 0.0;
+    for (int j = 0; j < 2 << h->tab.bits[s + 1]; ++j) du[j] = 0.0;
     const int32_t cf = h->tab.cfirst[s][first + k], cc = h->tab.ccnt[s][first + k];
     for (int32_t j = 0; j < cc; ++j) {
       du[2 * j] = dk[cf + j - c_lo];

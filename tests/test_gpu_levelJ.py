@@ -153,3 +153,21 @@ def test_batch_of_mixed_partitions(mra):
         ref = [O.loglik(O.Problem(d["locs"], d["y"], M=d["M"], J=d["J"], r=16, family="exp"), d["theta"])
                for d in datasets]
         np.testing.assert_allclose(lls, ref, rtol=1e-10)
+
+
+def test_two_phase_subtrees(mra):
+    """The sharded two-phase evaluation (Sec. 3.5) on a level-varying tree: every
+    level-1 region has J_2 = 8 children, whose (d, u) the summaries carry."""
+    from paper_1507_04789_gb300 import shard
+    J = (2, 8, 2)
+    locs, y = _data(2000, 71)
+    theta = TH_EXP
+    ll_o = O.loglik(O.Problem(locs, y, M=3, J=J, r=16, family="exp"), theta)
+    with mra.Handle(locs, y, M=3, r=16, J=J, precision="emu", stream_level=1) as h0, \
+            mra.Handle(locs, y, M=3, r=16, J=J, precision="emu", stream_level=1) as h1:
+        length, nsub = h0.summary_len()
+        assert nsub == 2 and length == 3 * 16 * 16 + 2 * 16 + 2 * 8
+        parts = [hk.loglik_subtrees(theta, *shard.subtree_range(nsub, k, 2)) for k, hk in enumerate((h0, h1))]
+        joined = np.concatenate(parts)
+        for hk in (h0, h1):
+            assert hk.loglik_combine(theta, joined) == pytest.approx(ll_o, rel=1e-10)

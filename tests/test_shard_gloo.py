@@ -26,8 +26,8 @@ class OracleSubtrees:
         self.r = prob.r
 
     def summary_len(self):
-        s, r = self.s, self.r
-        return (s + 1) ** 2 * r * r + (s + 1) * r + 8, 4 ** s
+        s, r, tree = self.s, self.r, self.p.tree
+        return (s + 1) ** 2 * r * r + (s + 1) * r + 2 * O.J_at(tree.J, s + 1), tree.nreg(s)
 
     def loglik_subtrees(self, theta, first, count):
         p, s, tree = self.p, self.s, self.p.tree
@@ -37,7 +37,8 @@ class OracleSubtrees:
             P = O.prior(tree, p.locs, th, p.family, tau2, p.nonstat, subtree=(s, i))
             Q = O.posterior(tree, p.locs, p.y, P, subtree=(s, i))
             A, om = Q.A[(s, i)], Q.omega[(s, i)]
-            kids = [(s + 1, 4 * i + j) for j in range(4)]
+            Jc = O.J_at(tree.J, s + 1)
+            kids = [(s + 1, Jc * i + j) for j in range(Jc)]
             parts = [A[(k, l)].ravel() for k in range(s + 1) for l in range(s + 1)] + [om[k] for k in range(s + 1)]
             parts.append(np.array([v for c in kids for v in (Q.d[c], Q.u[c])]))
             rows.append(np.concatenate([np.asarray(x, dtype=np.complex128) for x in parts]))
@@ -60,7 +61,7 @@ class OracleSubtrees:
             for k in range(s + 1):
                 om.append(row[o:o + r])
                 o += r
-            du = row[o:o + 8]
+            du = row[o:o + 2 * O.J_at(tree.J, s + 1)]
             A_s.append(A)
             om_s.append(om)
             dk.append(du[0::2].sum())
@@ -70,23 +71,23 @@ class OracleSubtrees:
         return -0.5 * (Q.d[(0, 0)] + Q.u[(0, 0)]) - 0.5 * n * math.log(2.0 * math.pi)
 
 
-def _problem():
+def _problem(J=4):
     rng = np.random.default_rng(140)
     locs = rng.random((500, 2))
     y = rng.standard_normal(500)
-    return O.Problem(locs, y, M=3, r=4, family="matern15")
+    return O.Problem(locs, y, M=3, J=J, r=4, family="matern15")
 
 
 THETA = np.array([1.1, 0.2, 0.06])
 
 
-def _rank(rank, world, port, out_dir):
+def _rank(rank, world, port, out_dir, J, s):
     import torch.distributed as dist
 
     from paper_1507_04789_gb300 import shard
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
     try:
-        ev = OracleSubtrees(_problem(), 2)
+        ev = OracleSubtrees(_problem(J), s)
         ll = shard.sharded_loglik(ev, THETA, rank, world)
         g = []
         for a in range(3):
@@ -108,13 +109,14 @@ def test_subtree_ranges_cover_once():
             assert all(got[k][0] + got[k][1] == got[k + 1][0] for k in range(world - 1))
 
 
-def test_two_ranks_reproduce_single_process(tmp_path):
+@pytest.mark.parametrize("J,s", [(4, 2), ((2, 8, 2), 1)])   # the quadtree; level-varying J, 8 children per subtree
+def test_two_ranks_reproduce_single_process(tmp_path, J, s):
     import torch.multiprocessing as tmp
     with socket.socket() as sk:
         sk.bind(("127.0.0.1", 0))
         port = sk.getsockname()[1]
-    tmp.start_processes(_rank, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
-    p = _problem()
+    tmp.start_processes(_rank, args=(2, port, str(tmp_path), J, s), nprocs=2, join=True, start_method="spawn")
+    p = _problem(J)
     ll, g = O.loglik_grad(p, THETA)
     for k in range(2):
         v = np.load(tmp_path / f"rank{k}.npy")
