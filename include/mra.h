@@ -112,8 +112,8 @@ typedef struct {
     int    J_level[MRA_MAX_M];
                         /* level-varying J (Sec. 2.2; Sec. 4.3 uses (2, 2, 4, 8, 8, 16)):
                            J_level[m-1] = J_m, the children of every level-(m-1) region,
-                           m = 1..M, each 2, 4, 8 or 16, J_M (the leaves' level) 2 or 4, and
-                           J_1 ... J_M <= 2^24; entries past M zero.  All zero: J at every
+                           m = 1..M, each 2, 4, 8 or 16 (J_M, the leaves' level, 2 or 4 for
+                           MRA_PREC_EMU), and J_1 ... J_M <= 2^24; entries past M zero.  All zero: J at every
                            level.  Every region of a level splits the same way, into an
                            s_x x s_y grid of equal children (s_x s_y = J_m) by repeated
                            midpoint halving (half-open, last cell closed): with L_m =

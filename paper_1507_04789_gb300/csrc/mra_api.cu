@@ -129,7 +129,8 @@ int check_config(const mra_config* cfg) {
       }
       if (Jm != 2 && Jm != 4 && Jm != 8 && Jm != 16)
         return fail(MRA_ERR_ARG, "J_level[%d] = %d: each J_m must be 2, 4, 8 or 16", m - 1, Jm);
-      if (m == cfg->M && Jm > 4) return fail(MRA_ERR_ARG, "J_M (the leaves' level) must be 2 or 4");
+      if (m == cfg->M && Jm > 4 && cfg->precision == MRA_PREC_EMU)   // (a parent's leaves in at most four 128-row tiles)
+        return fail(MRA_ERR_ARG, "J_M (the leaves' level) must be 2 or 4 in the emulated form");
       L += Jm == 2 ? 1 : Jm == 4 ? 2 : Jm == 8 ? 3 : 4;
     }
     if (L > 24) return fail(MRA_ERR_ARG, "J_1 ... J_M = 2^%d leaves: at most 2^24", L);

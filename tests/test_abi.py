@@ -57,14 +57,15 @@ def test_argument_errors_need_no_gpu(lib):
         mra.Handle(np.zeros((4, 2)), np.zeros(4), M=13, r=16)
 
 
-@pytest.mark.parametrize("M,J", [(2, (2, 6)), (2, (4, 8)), (2, (16, 16)), (7, (16,) * 6 + (4,)), (1, (1,))])
-def test_level_varying_J_errors_need_no_gpu(lib, M, J):
+@pytest.mark.parametrize("M,J,prec", [(2, (2, 6), "fp64"), (2, (4, 8), "emu"), (2, (16, 16), "emu"),
+                                      (7, (16,) * 6 + (4,), "fp64"), (1, (1,), "fp64")])
+def test_level_varying_J_errors_need_no_gpu(lib, M, J, prec):
     """Level-varying J (Sec. 2.2): each J_m in {2, 4, 8, 16}, J_M (the leaves'
-    level) 2 or 4, at most 2^24 leaves; rejected on the host."""
+    level) 2 or 4 in the emulated form, at most 2^24 leaves; rejected on the host."""
     from paper_1507_04789_gb300 import mra
     import numpy as np
     with pytest.raises(mra.MRAError) as ei:
-        mra.Handle(np.zeros((4, 2)), np.zeros(4), M=M, r=16, J=J)
+        mra.Handle(np.zeros((4, 2)), np.zeros(4), M=M, r=16, J=J, precision=prec)
     assert ei.value.code == mra.MRA_ERR_ARG
     with pytest.raises(ValueError):
         mra.Handle(np.zeros((4, 2)), np.zeros(4), M=3, r=16, J=(2, 4))   # one J_m per level

@@ -171,3 +171,51 @@ def test_two_phase_subtrees(mra):
         joined = np.concatenate(parts)
         for hk in (h0, h1):
             assert hk.loglik_combine(theta, joined) == pytest.approx(ll_o, rel=1e-10)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_paper_sequence_with_sixteen_leaves_per_parent(mra, precision):
+    """Sec. 4.3's own (J_1, ..., J_6) = (2, 2, 4, 8, 8, 16): 16384 leaves, sixteen
+    per level-5 region (J_M > 4 is open to the FP64 and 3xTF32 forms)."""
+    J = (2, 2, 4, 8, 8, 16)
+    locs, y = _data(30000, 81)
+    p = O.Problem(locs, y, M=6, J=J, r=4, family="exp")
+    ll_o, _, Q = O.loglik(p, TH_EXP, return_state=True)
+    with mra.Handle(locs, y, M=6, r=4, J=J, family="exp", precision=precision) as h:
+        off, perm = h.leaf_offsets(with_perm=True)
+        assert off.shape[0] == 16385
+        for i in range(0, 16384, 97):
+            np.testing.assert_array_equal(perm[off[i]:off[i + 1]], p.tree.obs[i])
+        ll = h.loglik(TH_EXP)
+        if precision == "mixed":
+            # measured 3.2e-6 per observation: r = 4 and about two observations per leaf, where the
+            # 3xTF32 products' rounding weighs more per observation than on the n = 2^20, r = 64 workload
+            assert abs(ll - ll_o) <= 5e-6 * 30000
+            return
+        assert ll == pytest.approx(ll_o, rel=1e-10)
+        scale = abs(Q.d[(0, 0)]) + abs(Q.u[(0, 0)]) + 1.0
+        for m in (0, 3, 5, 6):
+            d_g, u_g = h.region_terms(m)
+            d_o = np.array([Q.d.get((m, i), 0.0) for i in range(p.tree.nreg(m))])
+            u_o = np.array([Q.u.get((m, i), 0.0) for i in range(p.tree.nreg(m))])
+            np.testing.assert_allclose(d_g, d_o, rtol=1e-10, atol=1e-11 * scale)
+            np.testing.assert_allclose(u_g, u_o, rtol=1e-10, atol=1e-11 * scale)
+
+
+def test_sixteen_leaves_per_parent_gradient_and_prediction(mra):
+    J = (2, 4, 16)
+    locs, y = _data(3000, 91)
+    theta = np.array(TH_M15)
+    p = O.Problem(locs, y, M=3, J=J, r=9, family="matern15")
+    ll_o, g_o = O.loglik_grad(p, theta)
+    plocs = np.random.default_rng(92).random((150, 2))
+    mo, vo = O.predict(p, tuple(theta), plocs)
+    with mra.Handle(locs, y, M=3, r=9, J=J, family="matern15") as h:
+        ll, g = h.loglik_grad(theta)
+        mg, vg = h.predict(tuple(theta), plocs)
+    assert ll == pytest.approx(ll_o, rel=1e-10)
+    np.testing.assert_allclose(g, g_o, rtol=1e-8, atol=1e-8 * np.abs(g_o).max())
+    np.testing.assert_allclose(mg, mo, rtol=1e-9, atol=1e-9 * np.abs(mo).max())
+    np.testing.assert_allclose(vg, vo, rtol=1e-9, atol=1e-9 * np.abs(vo).max())
+    with pytest.raises(mra.MRAError):
+        mra.Handle(locs, y, M=3, r=9, J=J, precision="emu")
