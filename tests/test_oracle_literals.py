@@ -191,3 +191,22 @@ def test_level_varying_J_locators_agree(J):
     for m in range(1, len(J) + 1):
         np.testing.assert_array_equal(O.locate(pts, t.boxes, J[:m], m, 2), E.cell_index(pts, (0, 1, 0, 1), J, m, 2))
     assert sum(len(o) for o in t.obs) == pts.shape[0]
+
+
+@pytest.mark.parametrize("J", [(2, 8, 2), (16, 4), (2, 2, 4, 8, 8, 16)])
+def test_level_varying_J_points_lie_in_their_boxes(J):
+    """Every point lies in the half-open box of its region at every level (closed
+    at the bounding box maximum), and the boxes of a level tile the domain: the
+    partition's boxes and its point locator state the same regions."""
+    rng = np.random.default_rng(sum(J))
+    pts = np.concatenate([rng.random((300, 2)), [[1.0, 1.0], [0.0, 1.0], [1.0, 0.0], [0.5, 0.5]]])
+    M = len(J)
+    t = O.build_tree(pts, M=M, J=J, r=4)
+    for m in range(1, M + 1):
+        b = np.asarray(t.boxes[m])
+        assert np.isclose(np.sum((b[:, 1] - b[:, 0]) * (b[:, 3] - b[:, 2])), 1.0, rtol=0, atol=1e-12)
+        leaf = O.locate(pts, t.boxes, J[:m], m, 2)
+        x0, x1, y0, y1 = b[leaf].T
+        inx = (pts[:, 0] >= x0) & ((pts[:, 0] < x1) | (x1 == 1.0))
+        iny = (pts[:, 1] >= y0) & ((pts[:, 1] < y1) | (y1 == 1.0))
+        assert inx.all() and iny.all()
