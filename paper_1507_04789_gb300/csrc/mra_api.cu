@@ -147,7 +147,8 @@ int check_config(const mra_config* cfg) {
   return MRA_OK;
 }
 
-// Host tree tables (Sec. 2.2): active regions of every level in Morton order.
+// Host tree tables (Sec. 2.2): active regions of every level in region-id order
+// (the per-level child digits; Morton order for the quadtree).
 struct Tables {
   std::vector<std::vector<int32_t>> mort, par, cfirst, ccnt, cid;
   std::vector<int32_t> nreg;
@@ -547,8 +548,8 @@ cudaError_t bin(mra_handle* h, const double* dl, const double* dy, int* hs, int6
   const int64_t nl = h->nfull(h->M);
   cudaError_t e;
   if ((e = cudaMemsetAsync(h->status, 0, sizeof(int) * 4, h->stream))) return e;
-  if ((e = mra::launch_bin(dl, h->n, h->bbox, h->M, h->hx, h->hy, h->leaf_id, h->counts, h->cursor, h->off, h->sq_off,
-                           h->max_count, h->perm, h->status, h->stream, &g_launches)) ||
+  if ((e = mra::launch_bin(dl, h->n, h->bbox, h->M, h->hx, h->hy, h->leaf_id, h->counts, h->cursor, h->off,
+                           h->sq_off, h->max_count, h->perm, h->status, h->stream, &g_launches)) ||
       (e = mra::launch_gather(dl, dy, h->perm, h->n, h->xs, h->ys, h->yv, h->stream, &g_launches)))
     return e;
   double got[2];
@@ -1104,8 +1105,7 @@ int mra_loglik(mra_handle* h, const mra_params* theta, double* loglik_out) {
 // Two-phase evaluation over level-s subtrees (multi-GPU sharding)
 // ---------------------------------------------------------------------------
 // Summary of a level-s region R after its subtree: A-hat_R (T_s packed r x r
-// blocks), omega-hat_R ((s + 1) r) and the (d, u) of its (up to 4) children.
-// Ahat and omegahat of a level-s region, then the (d, u) of each of its J_{s+1}
+// blocks), omega-hat_R ((s + 1) r) and the (d, u) of each of its J_{s+1}
 // possible children (8 doubles for the quadtree).
 static int64_t summary_len(const mra_handle* h) {
   const int64_t s = h->s_lvl, r = h->r;
