@@ -12,7 +12,8 @@
  *     exponential or Matern-1.5 (Eq. mat15), optionally with the
  *     nonstationary variance sigma2 * sqrt(g(s1) g(s2)), g(s) = 1 + 0.5 sin(4 pi x);
  *   - M levels of a recursive partition with J = 4 children per region
- *     (midpoint quadtree, child j = b_x + 2 b_y, half-open cells), Sec. 2.2;
+ *     (midpoint quadtree, child j = b_x + 2 b_y, half-open cells), or J_m
+ *     children at level m (mra_config.J_level), Sec. 2.2;
  *   - r knots per region on a cell-centred gx x gy grid (gx = smallest divisor
  *     of r with gx^2 >= r), leaves using their observations as knots (Sec. 2.2);
  *   - measurement-error variance tau2 added to the leaf covariance (Sec. 4.3).
@@ -140,8 +141,8 @@ typedef struct mra_handle mra_handle;
  *   n      : number of observations, n >= 1.
  *   where  : MRA_HOST or MRA_DEVICE.
  *   out    : receives a new handle (host pointer to a handle pointer).
- * Allocates the handle's device memory (about 8 n M r + 4^M M^2 r^2 doubles for
- * the factors of all levels), copies and sorts the observations by leaf on the
+ * Allocates the handle's device memory (about 8 n M r + R M^2 r^2 doubles for
+ * the factors of all levels, R = the leaves' count, 4^M for the quadtree), copies and sorts the observations by leaf on the
  * device (stable within a leaf).  Errors: MRA_ERR_ARG (bad config, n < 1, a
  * location outside bbox), MRA_ERR_LIMIT (a leaf above MRA_MAX_LEAF: raise M),
  * MRA_ERR_OOM, MRA_ERR_CUDA.  On error *out is NULL and nothing is leaked.
