@@ -69,3 +69,33 @@ def test_level_varying_J_errors_need_no_gpu(lib, M, J, prec):
     assert ei.value.code == mra.MRA_ERR_ARG
     with pytest.raises(ValueError):
         mra.Handle(np.zeros((4, 2)), np.zeros(4), M=3, r=16, J=(2, 4))   # one J_m per level
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structs have the header's size and field offsets
+    (a C program compiled against include/mra.h prints them)."""
+    import shutil
+    import subprocess
+    from paper_1507_04789_gb300 import mra
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"mra_config": mra.MraConfig, "mra_params": mra.MraParams, "mra_stats_t": mra.MraStats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "mra.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, f, v = line.split()
+        got[(cname, f)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
